@@ -1,0 +1,419 @@
+"""CPU oracle for the multiscale multibasis pressure solver -- TEST INFRASTRUCTURE.
+
+Plain FP64, single-threaded C (``ms_oracle.c``) behind a ctypes shim.  Only
+``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package.  It shares
+no code with the CUDA library: the two are compared on the same seeded
+inputs.
+
+What each routine follows (Klemetsdal, Moyner & Lie) and what pins it
+(tests/test_oracle_pins.py):
+
+=====================  ==========================================  ============================================
+routine                paper                                       pinned by
+=====================  ==========================================  ============================================
+assemble_tpfa          Sec. 3 two-point flux; Eq. (9)              2-cell harmonic mean by hand; 1D closed form
+                                                                   p_i = -i/T; multiplier / NNC / inactive cases;
+                                                                   A 1 = 0; symmetry
+pin                    problem statement (one reference cell)      dense solve equals the least-squares Neumann
+                                                                   solution shifted to p_ref = 0
+partition_cartesian    Sec. 5 (non-overlapping partition)          hand-counted blocks incl. ragged / empty blocks
+components             Sec. 5.1 static / dynamic partitions        scipy connected_components on a masked graph
+partition_dynamic      Sec. 5.1 dynamic (bins of |dp|)             hand-worked 1D example (tests/golden)
+support_box            Sec. 5 requirement 2                        hand-worked boxes; Omega_j within S_j
+support_hop            Sec. 5 requirement 2                        hand-worked 1D example (tests/golden)
+msrsb_basis            Sec. 5.1 (MsRSB, localized iterations)      partition of unity; confinement; P >= 0;
+                                                                   closed-form converged hat for two blocks in
+                                                                   1D (and its 2D / 3D tensor products)
+galerkin               Eq. (10), R = P^T                           symmetry; positive definiteness; P^T A 1 = 0
+                                                                   for the unpinned A; dense P^T A P by numpy
+cholesky(_solve)       coarse solve (A_c)^-1                       numpy.linalg.solve
+ilu0 / ilu0_apply      Sec. 5.1 / 6.4 ILU(0)                       (L U)_ij = A_ij on the pattern (defining
+                                                                   property); exact on tridiagonal A
+ms_solve               Eq. (11) in Richardson (Sec. 5.2)           dense direct solve; identity partition
+                                                                   converges in one cycle; A-norm error does not
+                                                                   grow per coarse stage
+cost_model             Eq. (12)                                    sum of the itemised Sec. 6.4 counts
+=====================  ==========================================  ============================================
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ms_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libms_oracle.so")
+
+OK, EINVAL, ENOMEM, ENOTCONV, ESINGULAR = 0, 1, 2, 4, 5
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"oracle {what} failed with status {code}")
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C11, -O2, no architecture flags)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+_i = C.c_int
+_d = C.c_double
+_pi = C.POINTER(C.c_int)
+_pd = C.POINTER(C.c_double)
+_ppi = C.POINTER(_pi)
+_ppd = C.POINTER(_pd)
+_vp = C.c_void_p
+
+
+class _Stage(C.Structure):
+    _fields_ = [("M", _i), ("sptr", _vp), ("scells", _vp), ("pval", _vp), ("L", _vp)]
+
+
+class _Adapt(C.Structure):
+    _fields_ = [("schedule", _i), ("n_bins", _i), ("eps", _d), ("smoothed", _i), ("omega", _d),
+                ("tol", _d), ("max_iter", _i), ("val_unpinned", _vp), ("cells", _vp),
+                ("nx", _i), ("ny", _i), ("nz", _i), ("part_out", _vp), ("md_hist", _vp)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        L = _lib
+        L.or_free.argtypes = [_vp]
+        L.or_tpfa_assemble.argtypes = [_i, _i, _i, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _i, _vp, _vp, _vp,
+                                       _vp, _vp, _pi, _ppi, _pi, _ppi, _ppi, _ppd, _ppi, _ppi, _ppd]
+        L.or_pin.argtypes = [_i, _vp, _vp, _vp, _vp, _i]
+        L.or_partition_cartesian.argtypes = [_i, _i, _i, _i, _vp, _i, _i, _i, _vp, _pi]
+        L.or_components.argtypes = [_i, _vp, _vp, _vp, _vp, _pi]
+        L.or_partition_dynamic.argtypes = [_i, _vp, _vp, _vp, _i, _d, _vp, _pi]
+        L.or_support_box.argtypes = [_i, _i, _i, _i, _vp, _vp, _vp, _vp, _i, _i, _i, _i, _ppi, _ppi]
+        L.or_support_hop.argtypes = [_i, _i, _i, _i, _vp, _vp, _vp, _vp, _i, _ppi, _ppi]
+        L.or_support_block.argtypes = [_i, _vp, _i, _ppi, _ppi]
+        L.or_msrsb_basis.argtypes = [_i, _vp, _vp, _vp, _vp, _i, _vp, _vp, _d, _d, _i, _vp, _pi, _vp]
+        L.or_constant_basis.argtypes = [_i, _vp, _vp]
+        L.or_constant_basis.restype = None
+        L.or_galerkin.argtypes = [_i, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp]
+        L.or_cholesky.argtypes = [_i, _vp]
+        L.or_cholesky_solve.argtypes = [_i, _vp, _vp, _vp]
+        L.or_cholesky_solve.restype = None
+        L.or_ilu0.argtypes = [_i, _vp, _vp, _vp, _vp]
+        L.or_ilu0_apply.argtypes = [_i, _vp, _vp, _vp, _vp, _vp]
+        L.or_ilu0_apply.restype = None
+        L.or_ms_solve.argtypes = [_i, _vp, _vp, _vp, _i, C.POINTER(_Stage), _i, _vp, _d, _vp, _vp, _d, _i,
+                                  C.POINTER(_Adapt), _pi, _vp]
+        L.or_cost_model.argtypes = [_d, _d, _d, _d, _d]
+        L.or_cost_model.restype = _d
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def _take_i(ptr, n):
+    out = np.ctypeslib.as_array(ptr, shape=(n,)).copy() if n > 0 else np.zeros(0, np.int32)
+    lib().or_free(C.cast(ptr, _vp))
+    return out.astype(np.int32, copy=False)
+
+
+def _take_d(ptr, n):
+    out = np.ctypeslib.as_array(ptr, shape=(n,)).copy() if n > 0 else np.zeros(0)
+    lib().or_free(C.cast(ptr, _vp))
+    return out
+
+
+def _check(st, what):
+    if st != OK:
+        raise OracleError(st, what)
+
+
+# ---------------------------------------------------------------------------- data types
+@dataclass
+class CSR:
+    n: int
+    rowptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+
+    def copy(self):
+        return CSR(self.n, self.rowptr.copy(), self.col.copy(), self.val.copy())
+
+    def to_scipy(self):
+        from scipy.sparse import csr_matrix
+        return csr_matrix((self.val, self.col, self.rowptr), shape=(self.n, self.n))
+
+    def dense(self):
+        return self.to_scipy().toarray()
+
+
+@dataclass
+class System:
+    A: CSR                 # unpinned TPFA matrix over active cells
+    cells: np.ndarray      # grid index of each active cell
+    faces: tuple           # (fa, fb, T_geometric)
+
+
+@dataclass
+class Basis:
+    M: int
+    sptr: np.ndarray       # CSC column pointers (per block)
+    scells: np.ndarray     # support cells, ascending within each block
+    pval: np.ndarray       # values aligned with scells
+    part: np.ndarray
+    iters: int = 0
+    inc_hist: Optional[np.ndarray] = None
+
+    def dense(self, n):
+        P = np.zeros((n, self.M))
+        for j in range(self.M):
+            s, e = self.sptr[j], self.sptr[j + 1]
+            P[self.scells[s:e], j] = self.pval[s:e]
+        return P
+
+
+# ---------------------------------------------------------------------------- routines
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def assemble_tpfa(grid, perm, lam=None, p_prev=None) -> System:
+    """Unpinned TPFA matrix over the active cells (Sec. 3, Eq. (9))."""
+    L = lib()
+    perm = _f64(perm).reshape(-1, 3)
+    act = None if grid.active is None else np.ascontiguousarray(grid.active, dtype=np.uint8)
+    mx = None if grid.mult_x is None else _f64(grid.mult_x)
+    my = None if grid.mult_y is None else _f64(grid.mult_y)
+    mz = None if grid.mult_z is None else _f64(grid.mult_z)
+    nn = grid.n_nnc
+    nnc = _i32(grid.nnc).reshape(-1) if nn else None
+    nax = np.ascontiguousarray(grid.nnc_axis, dtype=np.int8) if nn else None
+    nm = _f64(grid.nnc_mult) if nn else None
+    lam = None if lam is None else _f64(lam)
+    p_prev = None if p_prev is None else _f64(p_prev)
+    n = _i(); nf = _i()
+    cells = _pi(); fa = _pi(); fb = _pi(); ft = _pd(); rp = _pi(); ci = _pi(); v = _pd()
+    st = L.or_tpfa_assemble(grid.nx, grid.ny, grid.nz, grid.dx, grid.dy, grid.dz, _p(act), _p(perm),
+                            _p(mx), _p(my), _p(mz), nn, _p(nnc), _p(nax), _p(nm), _p(lam), _p(p_prev),
+                            C.byref(n), C.byref(cells), C.byref(nf), C.byref(fa), C.byref(fb), C.byref(ft),
+                            C.byref(rp), C.byref(ci), C.byref(v))
+    _check(st, "tpfa_assemble")
+    n = n.value; nf = nf.value
+    rowptr = _take_i(rp, n + 1)
+    nnz = int(rowptr[-1])
+    A = CSR(n, rowptr, _take_i(ci, nnz), _take_d(v, nnz))
+    return System(A, _take_i(cells, n), (_take_i(fa, nf), _take_i(fb, nf), _take_d(ft, nf)))
+
+
+def pin(A: CSR, q: Optional[np.ndarray] = None, ref: int = 0):
+    """Pinned copy of A (and q): row/column ``ref`` off-diagonals zeroed."""
+    Ap = A.copy()
+    qp = None if q is None else _f64(q).copy()
+    _check(lib().or_pin(A.n, _p(Ap.rowptr), _p(Ap.col), _p(Ap.val), _p(qp), ref), "pin")
+    return Ap, qp
+
+
+def partition_cartesian(grid, cells, block):
+    cells = _i32(cells)
+    part = np.empty(len(cells), np.int32)
+    M = _i()
+    _check(lib().or_partition_cartesian(grid.nx, grid.ny, grid.nz, len(cells), _p(cells), int(block[0]),
+                                        int(block[1]), int(block[2]), _p(part), C.byref(M)),
+           "partition_cartesian")
+    return part, M.value
+
+
+def components(A: CSR, cls):
+    cls = _i32(cls)
+    part = np.empty(A.n, np.int32)
+    M = _i()
+    _check(lib().or_components(A.n, _p(A.rowptr), _p(A.col), _p(cls), _p(part), C.byref(M)), "components")
+    return part, M.value
+
+
+def partition_static(A: CSR, part_general, facies):
+    """Static partition: general blocks split by facies class into connected
+    components (Sec. 5.1, static partitions adapted to geology)."""
+    nf = int(np.max(facies)) + 1 if len(facies) else 1
+    return components(A, _i32(part_general) * nf + _i32(facies))
+
+
+def partition_dynamic(A: CSR, dp, n_bins=8, eps=1e-8):
+    dp = _f64(dp)
+    part = np.empty(A.n, np.int32)
+    M = _i()
+    _check(lib().or_partition_dynamic(A.n, _p(A.rowptr), _p(A.col), _p(dp), n_bins, eps, _p(part), C.byref(M)),
+           "partition_dynamic")
+    return part, M.value
+
+
+def support_box(grid, cells, A: CSR, part, M, block):
+    cells = _i32(cells); part = _i32(part)
+    sp = _pi(); sc = _pi()
+    _check(lib().or_support_box(grid.nx, grid.ny, grid.nz, A.n, _p(cells), _p(A.rowptr), _p(A.col), _p(part), M,
+                                int(block[0]), int(block[1]), int(block[2]), C.byref(sp), C.byref(sc)),
+           "support_box")
+    sptr = _take_i(sp, M + 1)
+    return sptr, _take_i(sc, int(sptr[-1]))
+
+
+def support_hop(grid, cells, A: CSR, part, M):
+    cells = _i32(cells); part = _i32(part)
+    sp = _pi(); sc = _pi()
+    _check(lib().or_support_hop(grid.nx, grid.ny, grid.nz, A.n, _p(cells), _p(A.rowptr), _p(A.col), _p(part), M,
+                                C.byref(sp), C.byref(sc)), "support_hop")
+    sptr = _take_i(sp, M + 1)
+    return sptr, _take_i(sc, int(sptr[-1]))
+
+
+def support_block(part, M):
+    part = _i32(part)
+    sp = _pi(); sc = _pi()
+    _check(lib().or_support_block(len(part), _p(part), M, C.byref(sp), C.byref(sc)), "support_block")
+    sptr = _take_i(sp, M + 1)
+    return sptr, _take_i(sc, int(sptr[-1]))
+
+
+def msrsb_basis(A_unpinned: CSR, part, M, sptr, scells, omega=2.0 / 3.0, tol=1e-3, max_iter=500) -> Basis:
+    part = _i32(part); sptr = _i32(sptr); scells = _i32(scells)
+    pval = np.empty(int(sptr[-1]))
+    hist = np.zeros(max(max_iter, 1))
+    it = _i()
+    _check(lib().or_msrsb_basis(A_unpinned.n, _p(A_unpinned.rowptr), _p(A_unpinned.col), _p(A_unpinned.val),
+                                _p(part), M, _p(sptr), _p(scells), omega, tol, max_iter, _p(pval), C.byref(it),
+                                _p(hist)), "msrsb_basis")
+    return Basis(M, sptr, scells, pval, part, it.value, hist[: it.value].copy())
+
+
+def constant_basis(part, M) -> Basis:
+    sptr, scells = support_block(part, M)
+    pval = np.empty(int(sptr[-1]))
+    lib().or_constant_basis(M, _p(sptr), _p(pval))
+    return Basis(M, sptr, scells, pval, _i32(part))
+
+
+def galerkin(A: CSR, B: Basis) -> np.ndarray:
+    Ac = np.empty((B.M, B.M))
+    _check(lib().or_galerkin(A.n, _p(A.rowptr), _p(A.col), _p(A.val), B.M, _p(B.sptr), _p(B.scells), _p(B.pval),
+                             _p(Ac)), "galerkin")
+    return Ac
+
+
+def cholesky(Ac) -> np.ndarray:
+    L = _f64(Ac).copy()
+    _check(lib().or_cholesky(L.shape[0], _p(L)), "cholesky")
+    return L
+
+
+def cholesky_solve(L, b):
+    b = _f64(b); x = np.empty_like(b)
+    lib().or_cholesky_solve(L.shape[0], _p(_f64(L)), _p(b), _p(x))
+    return x
+
+
+def ilu0(A: CSR) -> np.ndarray:
+    lu = np.empty_like(A.val)
+    _check(lib().or_ilu0(A.n, _p(A.rowptr), _p(A.col), _p(A.val), _p(lu)), "ilu0")
+    return lu
+
+
+def ilu0_apply(A: CSR, lu, r):
+    r = _f64(r); z = np.empty_like(r)
+    lib().or_ilu0_apply(A.n, _p(A.rowptr), _p(A.col), _p(_f64(lu)), _p(r), _p(z))
+    return z
+
+
+@dataclass
+class SolveResult:
+    x: np.ndarray
+    iters: int
+    hist: np.ndarray
+    converged: bool
+    dyn_part: Optional[np.ndarray] = None
+    md_hist: Optional[np.ndarray] = None
+
+
+def ms_solve(A: CSR, stages: Sequence[tuple], q, tol=1e-6, max_iter=500, smoother="ilu0", jac_omega=2.0 / 3.0,
+             x0=None, adapt: Optional[dict] = None, lu=None) -> SolveResult:
+    """Multistage Richardson solve (Eq. (11)).  ``stages`` holds (Basis, L)
+    pairs with L the Cholesky factor of the stage's A_c.  ``adapt`` (optional):
+    dict(schedule=1|2, n_bins, eps, smoothed, omega, tol, max_iter,
+    A_unpinned, grid, cells)."""
+    L = lib()
+    q = _f64(q)
+    x = np.zeros(A.n) if x0 is None else _f64(x0).copy()
+    keep = []
+    arr = (_Stage * max(len(stages), 1))()
+    for s, (B, Lc) in enumerate(stages):
+        Lc = _f64(Lc)
+        keep += [B, Lc]
+        arr[s] = _Stage(B.M, _p(B.sptr), _p(B.scells), _p(B.pval), _p(Lc))
+    sm = 0 if smoother == "ilu0" else 1
+    if sm == 0 and lu is None:
+        lu = ilu0(A)
+    hist = np.zeros(max_iter + 1)
+    it = _i()
+    ad_ptr = None
+    dyn_part = md_hist = None
+    if adapt:
+        dyn_part = np.zeros(A.n, np.int32)
+        md_hist = np.zeros(max_iter, np.int32)
+        Au = adapt.get("A_unpinned", A)
+        grid = adapt.get("grid")
+        cells = _i32(adapt.get("cells", np.arange(A.n)))
+        keep += [Au, cells]
+        ad = _Adapt(int(adapt.get("schedule", 2)), int(adapt.get("n_bins", 8)), float(adapt.get("eps", 1e-8)),
+                    int(adapt.get("smoothed", 0)), float(adapt.get("omega", 2.0 / 3.0)),
+                    float(adapt.get("basis_tol", 1e-3)), int(adapt.get("basis_max_iter", 500)),
+                    _p(Au.val), _p(cells), grid.nx if grid else A.n, grid.ny if grid else 1,
+                    grid.nz if grid else 1, _p(dyn_part), _p(md_hist))
+        ad_ptr = C.pointer(ad)
+    st = L.or_ms_solve(A.n, _p(A.rowptr), _p(A.col), _p(A.val), len(stages), arr, sm,
+                       _p(lu) if lu is not None else None, jac_omega, _p(q), _p(x), tol, max_iter, ad_ptr,
+                       C.byref(it), _p(hist))
+    if st not in (OK, ENOTCONV):
+        raise OracleError(st, "ms_solve")
+    n_it = it.value
+    return SolveResult(x, n_it, hist[: n_it + 1].copy(), st == OK, dyn_part,
+                       None if md_hist is None else md_hist[:n_it].copy())
+
+
+def cost_model(N, Np, d, b, Nc):
+    return lib().or_cost_model(float(N), float(Np), float(d), float(b), float(Nc))
+
+
+# ---------------------------------------------------------------------------- convenience
+def setup_general(gm, omega=2.0 / 3.0, tol=1e-3, max_iter=500, support="box", block=None):
+    """Assemble, pin and build the general-partition stage of a geomodel.
+    Returns (system, A_pinned, q_pinned, basis, A_c, L)."""
+    sysm = assemble_tpfa(gm.grid, gm.perm)
+    Ap, qp = pin(sysm.A, gm.q_active(), 0)
+    block = gm.block if block is None else block
+    part, M = partition_cartesian(gm.grid, sysm.cells, block)
+    if support == "box":
+        sptr, sc = support_box(gm.grid, sysm.cells, sysm.A, part, M, block)
+    else:
+        sptr, sc = support_hop(gm.grid, sysm.cells, sysm.A, part, M)
+    B = msrsb_basis(sysm.A, part, M, sptr, sc, omega, tol, max_iter)
+    Ac = galerkin(Ap, B)
+    return sysm, Ap, qp, B, Ac, cholesky(Ac)

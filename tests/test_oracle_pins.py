@@ -1,0 +1,405 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each test checks an oracle routine against a closed form, an invariant the
+paper states, a hand-worked example (tests/golden/hand_worked.json), or a
+library routine (numpy / scipy) computing the plain definition.  A mistake
+anywhere in the oracle (a dropped term, a wrong sign or index, a transposed
+operand) should fail at least one of them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2001_01624_gb300 import geomodel as G
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hand_worked.json")))
+
+
+def _grid(nx, ny, nz, inactive=None):
+    g = G.Grid(nx, ny, nz, 3.0, 2.0, 0.5)
+    if inactive:
+        a = np.ones(g.N, np.uint8)
+        a[list(inactive)] = 0
+        g.active = a
+    return g
+
+
+def _perm(N, k=1.0):
+    return np.full((N, 3), k)
+
+
+# ----------------------------------------------------------------------------- TPFA (Sec. 3, Eq. (9))
+def test_tpfa_two_cells_harmonic_mean():
+    g = _grid(2, 1, 1)
+    perm = np.array([[2.0, 7.0, 7.0], [5.0, 7.0, 7.0]])
+    s = O.assemble_tpfa(g, perm)
+    area, h = g.dy * g.dz, g.dx
+    T = 2.0 * area * 2.0 * 5.0 / (h * (2.0 + 5.0))     # harmonic mean by hand
+    np.testing.assert_allclose(s.A.dense(), [[T, -T], [-T, T]], rtol=1e-15)
+
+
+def test_tpfa_axes_multiplier_and_removed_face():
+    g = _grid(1, 2, 2)
+    perm = np.array([[1.0, 3.0, 4.0]] * 4)
+    g.mult_y = np.array([0.5, 0.0])   # y-face at k=0 halved, at k=1 removed
+    s = O.assemble_tpfa(g, perm)
+    Ty = 3.0 * (g.dx * g.dz) / g.dy                  # equal cells: t/2 = K * area / h
+    Tz = 4.0 * (g.dx * g.dy) / g.dz
+    expect = np.array([[Ty + Tz, -Ty, -Tz, 0], [-Ty, Ty + Tz, 0, -Tz], [-Tz, 0, Tz, 0], [0, -Tz, 0, Tz]])
+    expect[0, 1] = expect[1, 0] = -0.5 * Ty
+    expect[0, 0] = 0.5 * Ty + Tz
+    expect[1, 1] = 0.5 * Ty + Tz
+    np.testing.assert_allclose(s.A.dense(), expect, rtol=1e-14)
+
+
+def test_tpfa_nnc_and_inactive():
+    # 1x1x3 column: face 0-1 removed, NNC 0-2 along z; cell 1 inactive-free
+    g = _grid(1, 1, 3)
+    g.mult_z = np.array([0.0, 1.0])
+    g.nnc = np.array([[0, 2]], np.int32)
+    g.nnc_axis = np.array([2], np.int8)
+    g.nnc_mult = np.array([0.25])
+    perm = np.array([[1, 1, 2.0], [1, 1, 2.0], [1, 1, 6.0]])
+    s = O.assemble_tpfa(g, perm)
+    a = g.dx * g.dy
+    t = lambda k: k * a / (0.5 * g.dz)
+    T12 = 1.0 / (1 / t(2.0) + 1 / t(6.0))
+    T02 = 0.25 / (1 / t(2.0) + 1 / t(6.0))
+    expect = np.array([[T02, 0, -T02], [0, T12, -T12], [-T02, -T12, T02 + T12]])
+    np.testing.assert_allclose(s.A.dense(), expect, rtol=1e-14)
+    # inactive middle cell: the two others are disconnected
+    g2 = _grid(3, 1, 1, inactive=[1])
+    s2 = O.assemble_tpfa(g2, _perm(3))
+    assert s2.A.n == 2 and list(s2.cells) == [0, 2]
+    np.testing.assert_array_equal(s2.A.dense(), np.zeros((2, 2)))
+
+
+def test_tpfa_row_sums_zero_and_symmetric():
+    gm = G.faulted(16, 12, 6, seed=3, n_fault_x=1, n_fault_y=1, block=(4, 4, 2))
+    s = O.assemble_tpfa(gm.grid, gm.perm)
+    A = s.A.dense()
+    assert np.abs(A - A.T).max() == 0.0
+    assert np.abs(A.sum(1)).max() <= 1e-12 * np.abs(A).max()
+    assert (np.diag(A) > 0).all() and (A - np.diag(np.diag(A)) <= 0).all()
+
+
+def test_tpfa_rejects_negative_or_nan_perm():
+    g = _grid(2, 1, 1)
+    for bad in (-1.0, np.nan):
+        p = _perm(2)
+        p[1, 0] = bad
+        with pytest.raises(O.OracleError):
+            O.assemble_tpfa(g, p)
+
+
+def test_tpfa_upstream_mobility():
+    g = _grid(3, 1, 1)
+    s0 = O.assemble_tpfa(g, _perm(3))
+    lam = np.array([2.0, 3.0, 5.0])
+    s1 = O.assemble_tpfa(g, _perm(3), lam=lam, p_prev=np.array([3.0, 2.0, 2.0]))
+    T = -s0.A.dense()[0, 1]
+    A1 = s1.A.dense()
+    assert A1[0, 1] == pytest.approx(-2.0 * T)            # p0 > p1: upstream cell 0
+    assert A1[1, 2] == pytest.approx(-0.5 * (3.0 + 5.0) * T)   # tie: mean
+
+
+# ----------------------------------------------------------------------------- solve pins
+def _dense_pinned_solve(Ap, qp):
+    return np.linalg.solve(Ap.dense(), qp)
+
+
+def test_1d_closed_form():
+    """Homogeneous column, q = +1 / -1 at the ends, p_0 = 0 => p_i = -i / T."""
+    n = 23
+    gm = G.homogeneous(n, 1, 1, block=(5, 1, 1))
+    gm.q[:] = 0
+    gm.q[0], gm.q[-1] = 1.0, -1.0
+    sysm, Ap, qp, B, Ac, L = O.setup_general(gm, tol=1e-8, max_iter=20000)
+    T = -sysm.A.dense()[0, 1]
+    r = O.ms_solve(Ap, [(B, L)], qp, tol=1e-12, max_iter=500)
+    assert r.converged
+    np.testing.assert_allclose(r.x, -np.arange(n) / T, rtol=1e-9, atol=1e-9 * n / T)
+
+
+def test_pin_equals_neumann_shift():
+    gm = G.lognormal_box(9, 7, 1, seed=4, block=(3, 3, 1))
+    s = O.assemble_tpfa(gm.grid, gm.perm)
+    q = gm.q_active()
+    Ap, qp = O.pin(s.A, q, 0)
+    x = _dense_pinned_solve(Ap, qp)
+    xn = np.linalg.lstsq(s.A.dense(), q, rcond=None)[0]
+    np.testing.assert_allclose(x, xn - xn[0], rtol=1e-9, atol=1e-9 * np.abs(x).max())
+
+
+@pytest.mark.parametrize("case", ["2d", "3d", "faulted"])
+def test_ms_solve_matches_direct_solve(case):
+    if case == "2d":
+        gm = G.lognormal_box(12, 8, 1, seed=1, block=(4, 4, 1))
+    elif case == "3d":
+        gm = G.lognormal_box(10, 10, 4, seed=2, block=(5, 5, 2), kz_ratio=0.1)
+    else:
+        gm = G.faulted(14, 12, 6, seed=5, n_fault_x=1, n_fault_y=1, block=(5, 4, 3))
+    sysm, Ap, qp, B, Ac, L = O.setup_general(gm)
+    r = O.ms_solve(Ap, [(B, L)], qp, tol=1e-11, max_iter=3000)
+    assert r.converged
+    x = _dense_pinned_solve(Ap, qp)
+    assert np.linalg.norm(r.x - x) <= 1e-8 * np.linalg.norm(x)
+
+
+def test_jacobi_smoother_converges_to_direct():
+    gm = G.lognormal_box(10, 8, 1, seed=6, sigma=1.0, block=(5, 4, 1))
+    sysm, Ap, qp, B, Ac, L = O.setup_general(gm)
+    r = O.ms_solve(Ap, [(B, L)], qp, tol=1e-11, max_iter=20000, smoother="jacobi")
+    assert r.converged
+    x = _dense_pinned_solve(Ap, qp)
+    assert np.linalg.norm(r.x - x) <= 1e-8 * np.linalg.norm(x)
+
+
+def test_identity_partition_converges_in_one_cycle():
+    gm = G.lognormal_box(6, 5, 2, seed=7, block=(1, 1, 1))
+    sysm, Ap, qp, B, Ac, L = O.setup_general(gm)
+    assert B.M == Ap.n
+    r = O.ms_solve(Ap, [(B, L)], qp, tol=1e-12, max_iter=10)
+    assert r.iters == 1 and r.converged
+
+
+def test_coarse_stage_does_not_increase_energy_error():
+    """x + P A_c^-1 P^T (q - A x) is the A-orthogonal projection: ||e||_A
+    never grows (Eq. (10), Galerkin restriction)."""
+    gm = G.lognormal_box(12, 10, 2, seed=8, block=(4, 5, 1))
+    sysm, Ap, qp, B, Ac, L = O.setup_general(gm)
+    A = Ap.dense()
+    xs = np.linalg.solve(A, qp)
+    P = B.dense(Ap.n)
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        x = rng.standard_normal(Ap.n) * np.abs(xs).max()
+        e0 = x - xs
+        xc = O.cholesky_solve(L, P.T @ (qp - A @ x))
+        e1 = x + P @ xc - xs
+        assert e1 @ A @ e1 <= e0 @ A @ e0 * (1 + 1e-12)
+        assert np.abs(P.T @ (qp - A @ (x + P @ xc))).max() <= 1e-9 * np.abs(P.T @ qp).max() + 1e-30
+
+
+def test_multistage_and_adaptive_converge_to_direct():
+    gm = G.faulted(16, 14, 6, seed=9, n_fault_x=1, n_fault_y=1, block=(4, 4, 3))
+    sysm, Ap, qp, B, Ac, L = O.setup_general(gm)
+    ps, Ms = O.partition_static(sysm.A, B.part, gm.facies[sysm.cells])
+    sp, sc = O.support_hop(gm.grid, sysm.cells, sysm.A, ps, Ms)
+    B2 = O.msrsb_basis(sysm.A, ps, Ms, sp, sc)
+    L2 = O.cholesky(O.galerkin(Ap, B2))
+    x = _dense_pinned_solve(Ap, qp)
+    r = O.ms_solve(Ap, [(B, L), (B2, L2)], qp, tol=1e-10, max_iter=3000)
+    assert r.converged and np.linalg.norm(r.x - x) <= 1e-7 * np.linalg.norm(x)
+    ra = O.ms_solve(Ap, [(B, L), (B2, L2)], qp, tol=1e-10, max_iter=3000,
+                    adapt=dict(schedule=2, grid=gm.grid, cells=sysm.cells, A_unpinned=sysm.A))
+    assert ra.converged and np.linalg.norm(ra.x - x) <= 1e-7 * np.linalg.norm(x)
+    assert ra.md_hist[0] == 0 and ra.md_hist[1] > 0
+    ra1 = O.ms_solve(Ap, [(B, L)], qp, tol=1e-10, max_iter=3000,
+                     adapt=dict(schedule=1, smoothed=1, grid=gm.grid, cells=sysm.cells, A_unpinned=sysm.A))
+    assert ra1.converged and np.linalg.norm(ra1.x - x) <= 1e-7 * np.linalg.norm(x)
+
+
+# ----------------------------------------------------------------------------- MsRSB (Sec. 5, 5.1)
+def _setup_basis(gm, tol=1e-3, max_iter=500):
+    s = O.assemble_tpfa(gm.grid, gm.perm)
+    part, M = O.partition_cartesian(gm.grid, s.cells, gm.block)
+    sp, sc = O.support_box(gm.grid, s.cells, s.A, part, M, gm.block)
+    return s, O.msrsb_basis(s.A, part, M, sp, sc, tol=tol, max_iter=max_iter)
+
+
+def test_basis_partition_of_unity_confinement_nonnegative():
+    gm = G.lognormal_box(20, 24, 5, seed=11, block=(5, 6, 2), kz_ratio=0.1)
+    for it in (1, 3, 40):
+        s, B = _setup_basis(gm, tol=0.0, max_iter=it)
+        assert B.iters == it
+        P = B.dense(s.A.n)
+        assert np.abs(P.sum(1) - 1).max() <= 1e-12            # requirement 3
+        assert (B.pval >= 0).all()                              # M-matrix + omega < 1
+        for j in range(B.M):                                    # requirement 2
+            S = set(B.scells[B.sptr[j]:B.sptr[j + 1]].tolist())
+            assert set(np.flatnonzero(B.part == j).tolist()) <= S
+            outside = np.setdiff1d(np.arange(s.A.n), list(S))
+            assert np.all(P[outside, j] == 0.0)
+
+
+def test_basis_converges_to_closed_form_hat_1d():
+    gm = G.homogeneous(20, 1, 1, block=(10, 1, 1))
+    s, B = _setup_basis(gm, tol=1e-14, max_iter=100000)
+    P = B.dense(s.A.n)
+    i = np.arange(20)
+    np.testing.assert_allclose(P[:, 0], np.clip((15 - i) / 11, 0, 1), atol=1e-12)
+    np.testing.assert_allclose(P[:, 1], 1 - np.clip((15 - i) / 11, 0, 1), atol=1e-12)
+
+
+def test_basis_converges_to_tensor_hat_3d():
+    gm = G.homogeneous(20, 40, 4, block=(10, 20, 2))
+    s, B = _setup_basis(gm, tol=1e-13, max_iter=200000)
+    P = B.dense(s.A.n)
+    hx = np.clip((15 - np.arange(20)) / 11, 0, 1)
+    hy = np.clip((30 - np.arange(40)) / 21, 0, 1)
+    hz = np.clip((3 - np.arange(4)) / 3, 0, 1)
+    for j, (fx, fy, fz) in enumerate([(hx, hy, hz), (1 - hx, hy, hz), (hx, 1 - hy, hz), (1 - hx, 1 - hy, hz),
+                                      (hx, hy, 1 - hz)]):
+        T = (fz[:, None, None] * fy[None, :, None] * fx[None, None, :]).ravel()
+        assert np.abs(P[:, j] - T).max() <= 1e-9
+
+
+def test_basis_constant_reproduction_and_galerkin():
+    gm = G.lognormal_box(16, 12, 3, seed=12, block=(4, 4, 3))
+    s, B = _setup_basis(gm)
+    P = B.dense(s.A.n)
+    A = s.A.dense()
+    np.testing.assert_allclose(P @ np.ones(B.M), 1.0, atol=1e-12)
+    assert np.abs(A @ np.ones(s.A.n)).max() <= 1e-12 * np.abs(A).max()
+    Acu = O.galerkin(s.A, B)
+    assert np.abs(Acu @ np.ones(B.M)).max() <= 1e-12 * np.abs(Acu).max()
+    np.testing.assert_allclose(Acu, P.T @ A @ P, rtol=1e-12, atol=1e-12 * np.abs(Acu).max())
+    Ap, _ = O.pin(s.A, None, 0)
+    Ac = O.galerkin(Ap, B)
+    assert np.abs(Ac - Ac.T).max() <= 1e-12 * np.abs(Ac).max()
+    assert np.linalg.eigvalsh(Ac).min() > 0
+    np.testing.assert_allclose(Ac, P.T @ Ap.dense() @ P, rtol=1e-12, atol=1e-12 * np.abs(Ac).max())
+
+
+# ----------------------------------------------------------------------------- partitions & supports
+def _chain(nx, ny=1, nz=1):
+    g = _grid(nx, ny, nz)
+    return g, O.assemble_tpfa(g, _perm(g.N))
+
+
+def test_support_box_golden():
+    gd = GOLD["support_box_1d"]
+    g, s = _chain(*gd["grid"])
+    part, M = O.partition_cartesian(g, s.cells, gd["block"])
+    sp, sc = O.support_box(g, s.cells, s.A, part, M, gd["block"])
+    assert [sc[sp[j]:sp[j + 1]].tolist() for j in range(M)] == gd["expected"]
+
+
+def test_support_box_respects_reachability():
+    # 4x1x2 grid, block 2x1x2: without the z-face at x=2 and with the x-face
+    # between x=1 and x=2 removed, cell (2,0,0) is unreachable from block 0
+    g = _grid(4, 1, 2)
+    g.mult_x = np.array([1.0, 0.0, 1.0, 1.0, 1.0, 1.0])
+    g.mult_z = np.array([1.0, 1.0, 0.0, 1.0])
+    s = O.assemble_tpfa(g, _perm(g.N))
+    part, M = O.partition_cartesian(g, s.cells, (2, 1, 2))
+    sp, sc = O.support_box(g, s.cells, s.A, part, M, (2, 1, 2))
+    S0 = sc[sp[0]:sp[1]].tolist()
+    assert S0 == [0, 1, 4, 5, 6]       # (2,0,1)=6 reachable via (1,0,1)=5; (2,0,0)=2 is not
+
+
+@pytest.mark.parametrize("key", ["support_hop_1d", "support_hop_2d"])
+def test_support_hop_golden(key):
+    gd = GOLD[key]
+    g, s = _chain(*gd["grid"])
+    part, M = O.partition_cartesian(g, s.cells, gd["block"])
+    sp, sc = O.support_hop(g, s.cells, s.A, part, M)
+    assert [sc[sp[j]:sp[j + 1]].tolist() for j in range(M)] == gd["expected"]
+
+
+@pytest.mark.parametrize("key", ["dynamic_1d", "dynamic_2d"])
+def test_dynamic_partition_golden(key):
+    gd = GOLD[key]
+    g, s = _chain(*gd["grid"])
+    part, M = O.partition_dynamic(s.A, np.array(gd["dp"]), gd["n_bins"], gd["eps"])
+    assert part.tolist() == gd["expected_part"] and M == gd["expected_M"]
+
+
+def test_dynamic_partition_zero_update_is_connected_components():
+    g, s = _chain(6, 2)
+    part, M = O.partition_dynamic(s.A, np.zeros(12))
+    assert M == 1 and (part == 0).all()
+
+
+def test_static_partition_golden():
+    gd = GOLD["static_2d"]
+    g, s = _chain(*gd["grid"])
+    part, M = O.partition_cartesian(g, s.cells, gd["block"])
+    ps, Ms = O.partition_static(s.A, part, np.array(gd["facies"]))
+    assert ps.tolist() == gd["expected_part"] and Ms == gd["expected_M"]
+
+
+def test_cartesian_partition_ragged_golden():
+    gd = GOLD["cartesian_ragged"]
+    g = _grid(*gd["grid"], inactive=gd["inactive"])
+    s = O.assemble_tpfa(g, _perm(g.N))
+    part, M = O.partition_cartesian(g, s.cells, gd["block"])
+    assert part.tolist() == gd["expected_part"] and M == gd["expected_M"]
+
+
+def test_components_match_scipy():
+    from scipy.sparse.csgraph import connected_components
+    gm = G.lognormal_box(13, 11, 3, seed=13)
+    s = O.assemble_tpfa(gm.grid, gm.perm)
+    cls = (np.log(gm.perm[:, 0]) > np.median(np.log(gm.perm[:, 0]))).astype(np.int32)
+    part, M = O.components(s.A, cls)
+    A = s.A.to_scipy().tocoo()
+    keep = cls[A.row] == cls[A.col]
+    from scipy.sparse import coo_matrix
+    G2 = coo_matrix((np.ones(keep.sum()), (A.row[keep], A.col[keep])), shape=A.shape)
+    nc, lab = connected_components(G2, directed=False)
+    assert M == nc
+    # same grouping, and numbering by lowest cell index
+    first = {}
+    for i, l in enumerate(lab):
+        first.setdefault(l, len(first))
+    np.testing.assert_array_equal(part, [first[l] for l in lab])
+
+
+# ----------------------------------------------------------------------------- dense coarse algebra
+def test_cholesky_solve_matches_numpy():
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((40, 40))
+    A = X @ X.T + 40 * np.eye(40)
+    L = O.cholesky(A)
+    np.testing.assert_allclose(L @ L.T, A, rtol=1e-12, atol=1e-12 * np.abs(A).max())
+    b = rng.standard_normal(40)
+    np.testing.assert_allclose(O.cholesky_solve(L, b), np.linalg.solve(A, b), rtol=1e-10)
+    with pytest.raises(O.OracleError):
+        O.cholesky(-np.eye(3))
+
+
+# ----------------------------------------------------------------------------- ILU(0)
+def _lu_dense(A, lu):
+    LU = O.CSR(A.n, A.rowptr, A.col, lu).dense()
+    return np.tril(LU, -1) + np.eye(A.n), np.triu(LU)
+
+
+@pytest.mark.parametrize("shape", [(9, 7, 1), (6, 5, 4)])
+def test_ilu0_defining_property(shape):
+    """ILU(0): (L U)_ij = A_ij for every (i, j) in the pattern of A."""
+    gm = G.faulted(*shape, seed=14, n_fault_x=1, n_fault_y=0, throw=1, inactive_pct=10.0) if shape[2] > 1 \
+        else G.lognormal_box(*shape, seed=14)
+    s = O.assemble_tpfa(gm.grid, gm.perm)
+    Ap, _ = O.pin(s.A, None, 0)
+    lu = O.ilu0(Ap)
+    Lm, Um = _lu_dense(Ap, lu)
+    A = Ap.dense()
+    mask = O.CSR(Ap.n, Ap.rowptr, Ap.col, np.ones_like(Ap.val)).dense() > 0
+    np.testing.assert_allclose((Lm @ Um)[mask], A[mask], rtol=1e-12, atol=1e-12 * np.abs(A).max())
+    r = np.random.default_rng(0).standard_normal(Ap.n)
+    np.testing.assert_allclose(O.ilu0_apply(Ap, lu, r), np.linalg.solve(Lm @ Um, r), rtol=1e-9)
+
+
+def test_ilu0_exact_on_tridiagonal():
+    gm = G.lognormal_box(30, 1, 1, seed=15, block=(5, 1, 1))
+    s = O.assemble_tpfa(gm.grid, gm.perm)
+    Ap, qp = O.pin(s.A, gm.q_active(), 0)
+    z = O.ilu0_apply(Ap, O.ilu0(Ap), qp)
+    np.testing.assert_allclose(z, np.linalg.solve(Ap.dense(), qp), rtol=1e-11)
+
+
+# ----------------------------------------------------------------------------- cost model (Eq. (12))
+@pytest.mark.parametrize("N,Np,d,b,Nc", [(1e6, 1, 7, 8, 1), (78720, 6, 15, 8, 3), (1000, 3, 5, 4, 2)])
+def test_cost_model_is_sum_of_itemised_counts(N, Np, d, b, Nc):
+    smooth = 2 * N * d + (N * d + N) + N          # two triangular solves, residual, update
+    restrict = (N * d + N) + b * N                 # residual + R
+    prolong = b * N + N                            # P x_c + update
+    predictor = Np * (smooth + restrict + prolong)
+    residual_update = Nc * N * d + Nc * N
+    corrector = 2 * d * Nc ** 2 * N + Nc * N
+    assert O.cost_model(N, Np, d, b, Nc) == pytest.approx(predictor + residual_update + corrector, rel=1e-14)
