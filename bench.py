@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Benchmark of the multiscale multibasis pressure solver on one GB300.
+
+Metric: fine-cell unknowns per second to a 1e-6 relative residual, for one
+pass of the whole hot path per step on the 3D 60x220x85 geomodel
+(1,122,000 cells; top 35 layers lognormal with Kz = 0.1 Kx, bottom 50 layers
+1000:1 binary channels; 6x11x17 coarse blocks of 10x20x5):
+
+    TPFA assembly -> MsRSB basis smoothing from the block indicator to
+    increment 1e-3 -> Galerkin A_c = P^T A P -> dense coarse factor/inverse ->
+    multiscale + ILU(0) Richardson solve from p = 0 to ||q - A p|| <= 1e-6 ||q||
+
+Inputs (permeability, sources) are resident in HBM when the timed region
+starts; the integer analysis (connection list, wavefront levels, support
+patterns) is done once per grid before timing.  The headline is the plain
+FP64 form; the mixed form (FP32 basis / smoother / coarse inverse, FP64 outer
+residual and refinement) is reported beside it.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank solves its own seeded geomodel (replicas; weak scaling).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = ("3D 60x220x85 Cartesian (1,122,000 cells), TPFA 7-point, top 35 layers lognormal "
+            "(ln K ~ N(ln 100 mD, 2^2), corr 8 cells, Kz=0.1Kx), bottom 50 layers binary channels 1000:1 "
+            "(Kz=0.1Kx); 6x11x17 coarse blocks of 10x20x5; MsRSB omega 2/3 to 1e-3; MS+ILU(0) Richardson to 1e-6")
+METRIC = "fine-cell unknowns/sec to 1e-6 rel residual (full hot path per step)"
+UNIT = "unknowns/s"
+ORACLE_GOLD = os.path.join(ROOT, "tests", "golden", "oracle_c2_seed0.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="run N extra untimed steps only (for ncu launch lists)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from profiles/ncu_traffic.txt, or None
+    when absent or when the kernel's source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for ln in open(path):
+        f = ln.split()
+        if len(f) >= 4 and f[0] == kernel:
+            src = os.path.join(ROOT, "paper_2001_01624_gb300", "csrc", f[2])
+            if not os.path.exists(src):
+                return None
+            h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+            return float(f[1]) if h == f[3] else None
+    return None
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- oracle leg
+def oracle_sample(gm, basis_iters, cycles, full_basis, full_cycles):
+    """Time the CPU oracle on a bounded sample of the step and scale the
+    iteration phases to the full iteration counts.  Returns (seconds for a
+    full step, description)."""
+    import oracle as O
+    t = {}
+    t0 = time.perf_counter()
+    s = O.assemble_tpfa(gm.grid, gm.perm)
+    Ap, qp = O.pin(s.A, gm.q_active(), 0)
+    part, M = O.partition_cartesian(gm.grid, s.cells, gm.block)
+    sp, sc = O.support_box(gm.grid, s.cells, s.A, part, M, gm.block)
+    t["fixed"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    B = O.msrsb_basis(s.A, part, M, sp, sc, 2.0 / 3.0, 0.0, basis_iters)
+    t["basis"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    L = O.cholesky(O.galerkin(Ap, B))
+    lu = O.ilu0(Ap)
+    t["fixed"] += time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.ms_solve(Ap, [(B, L)], qp, tol=0.0, max_iter=cycles, lu=lu)
+    t["solve"] = time.perf_counter() - t0
+    full = t["fixed"] + t["basis"] * full_basis / basis_iters + t["solve"] * full_cycles / cycles
+    desc = (f"oracle (plain C, FP64, 1 thread) on the same workload: assembly, pin, partition, supports, "
+            f"Galerkin, Cholesky, ILU(0) factor in full; {basis_iters} of {full_basis} basis iterations and "
+            f"{cycles} of {full_cycles} Richardson cycles timed, scaled to the full counts "
+            f"(measured {t['fixed'] + t['basis'] + t['solve']:.1f} s)")
+    return full, desc
+
+
+def full_counts():
+    try:
+        g = json.load(open(ORACLE_GOLD))
+        return int(g["basis_iters"]), int(g["cycles"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2001_01624_gb300 import geomodel as G
+    import oracle as O
+    O.build()
+    gm = G.config2(0)
+    counts = full_counts()
+    if counts is None:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle iteration counts file missing"}))
+        return 0
+    fb, fc = counts
+    n = gm.grid.n_active()
+    for _ in range(args.warmup):
+        oracle_sample(gm, 8, 12, fb, fc)
+    secs = []
+    desc = ""
+    for _ in range(args.steps):
+        s, desc = oracle_sample(gm, 8, 12, fb, fc)
+        secs.append(s)
+    tot = sum(secs)
+    v = n * len(secs) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": n, "precision": "fp64", "parallelism": "replicas"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU leg
+class Plan:
+    """Handles for one geomodel and one precision: analysis done once."""
+
+    def __init__(self, ms, ctx, gm, prec, dev, torch):
+        self.ms, self.ctx, self.prec = ms, ctx, prec
+        self.sys = ms.ms_system_create(ctx, gm.grid, 0)
+        self.perm = torch.from_numpy(gm.perm.ravel().copy()).to(dev)
+        self.q = torch.from_numpy(gm.q_active()).to(dev)
+        self.p = torch.zeros_like(self.q)
+        ms.ms_assemble_tpfa(ctx, self.sys, self.perm)
+        part, M = ms.ms_partition_cartesian(ctx, self.sys, gm.block)
+        self.basis, _ = ms.ms_build_basis(ctx, self.sys, part, M, block=gm.block, precision=prec)
+        self.coarse = ms.ms_galerkin(ctx, self.sys, self.basis, prec)
+        self.n = ms.ms_system_get_info(self.sys)["n"]
+        self.M = M
+
+    def step(self, perm=None, q=None, p=None):
+        ms, ctx = self.ms, self.ctx
+        ms.ms_assemble_tpfa(ctx, self.sys, self.perm if perm is None else perm)
+        bit = ms.ms_basis_rebuild(ctx, self.sys, self.basis)
+        ms.ms_coarse_refresh(ctx, self.sys, self.coarse)
+        info = ms.ms_solve(ctx, self.sys, [self.coarse], self.q if q is None else q, self.p if p is None else p,
+                           tol=1e-6, max_iter=5000, precision=self.prec)
+        info["basis_iters"] = bit
+        return info
+
+    def release(self):
+        self.ms.ms_coarse_release(self.coarse)
+        self.ms.ms_basis_release(self.basis)
+        self.ms.ms_system_release(self.sys)
+
+
+def timed_steps(torch, plan, stream, K, dist, world):
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = [plan.step() for _ in range(K)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_tot = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms_tot], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_tot = float(t.item())
+        dist.barrier()
+    return ms_tot, infos
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import numpy as np
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2001_01624_gb300 as ms
+    from paper_2001_01624_gb300 import geomodel as G
+
+    gm = G.config2(rank)
+    stream = torch.cuda.Stream(dev)
+    ctx = ms.ms_create(local, stream)
+    precs = [ms.MS_PREC_FP64] + ([] if args.no_mixed else [ms.MS_PREC_MIXED])
+    plans = {p: Plan(ms, ctx, gm, p, dev, torch) for p in precs}
+    n = plans[ms.MS_PREC_FP64].n
+
+    if args.profile_steps:
+        for _ in range(args.profile_steps):
+            plans[ms.MS_PREC_FP64].step()
+        torch.cuda.synchronize()
+        return 0
+
+    results = {}
+    clocks = None
+    for prec, plan in plans.items():
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                plan.step()
+        ms.ms_profile_reset()
+        ms.ms_profile_enable(True)
+        sampler = ClockSampler(local) if prec == ms.MS_PREC_FP64 else None
+        if sampler:
+            sampler.start()
+        ms_tot, infos = timed_steps(torch, plan, stream, args.steps, dist, world)
+        if sampler:
+            clocks = sampler.stop()
+        ms.ms_profile_enable(False)
+        prof = ms.ms_profile_read()
+        results[prec] = dict(ms=ms_tot, infos=infos, prof=prof)
+
+    r64 = results[ms.MS_PREC_FP64]
+    K = args.steps
+    value = n * K * world / (r64["ms"] * 1e-3)
+    prof = r64["prof"]
+    launches = prof.pop("_total_launches")
+    # dominant kernel (by device time) and its roofline
+    kernels = {k: v for k, v in prof.items() if v["timed_launches"] > 0}
+    dom = max(kernels, key=lambda k: kernels[k]["total_ms"])
+    dk = kernels[dom]
+    peak, peak_src = measured_peak()
+    avg_ms = dk["total_ms"] / dk["timed_launches"]
+    bytes_launch = dk["bytes"] / dk["timed_launches"]
+    achieved = bytes_launch / (avg_ms * 1e-3) / 1e9
+    traffic = ncu_traffic(dom)
+    info0 = r64["infos"][-1]
+    solve_ms = info0["seconds"] * 1e3
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": r64["ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": n, "coarse_blocks": plans[ms.MS_PREC_FP64].M,
+                   "precision": "fp64", "parallelism": "replicas (one independent seeded geomodel per GPU)",
+                   "l2": "no flush: working set of each step (A, ILU factors, 8-slot basis, vectors) exceeds the "
+                         "129 MB L2"},
+        "solve": {"cycles": info0["iters"], "basis_iters": info0["basis_iters"],
+                  "rel_residual": info0["rel_residual"], "solve_ms": solve_ms,
+                  "solve_unknowns_per_s": n / (solve_ms * 1e-3)},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs",
+                     "traffic": traffic, "algorithmic_bytes_per_launch": bytes_launch,
+                     "avg_launch_ms": avg_ms, "launches": dk["timed_launches"]},
+        "kernels": {k: {"launches": v["timed_launches"], "ms": round(v["total_ms"], 3),
+                        "share": round(v["total_ms"] / sum(x["total_ms"] for x in kernels.values()), 4),
+                        "GBps": (round(v["bytes"] / (v["total_ms"] * 1e-3) / 1e9, 1) if v["bytes"] else None)}
+                    for k, v in sorted(kernels.items(), key=lambda kv: -kv[1]["total_ms"])},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if ms.MS_PREC_MIXED in results:
+        rm = results[ms.MS_PREC_MIXED]
+        im = rm["infos"][-1]
+        line["mixed"] = {"value": n * K * world / (rm["ms"] * 1e-3), "unit": UNIT, "ms_per_step": rm["ms"] / K,
+                         "dtype": "f32 bulk + f64 residual/refinement", "cycles": im["iters"],
+                         "basis_iters": im["basis_iters"], "solve_ms": im["seconds"] * 1e3,
+                         "rel_residual": im["rel_residual"]}
+        pm = plans[ms.MS_PREC_MIXED].p.cpu().numpy()
+        p64 = plans[ms.MS_PREC_FP64].p.cpu().numpy()
+        line["mixed"]["rel_err_vs_fp64"] = float(np.linalg.norm(pm - p64) / np.linalg.norm(p64))
+
+    # end to end through the C ABI with pinned host buffers
+    if not args.no_e2e:
+        plan = plans[ms.MS_PREC_FP64]
+        perm_h = torch.from_numpy(gm.perm.ravel().copy()).pin_memory().numpy()
+        q_h = torch.from_numpy(gm.q_active()).pin_memory().numpy()
+        p_h = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
+        plan.step(perm_h, q_h, p_h)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            plan.step(perm_h, q_h, p_h)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        line["e2e"] = {"value": n * K * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(perm_h.nbytes + q_h.nbytes),
+                       "d2h_bytes_per_step": int(p_h.nbytes), "ms_per_step": 1e3 * e2e_s / K}
+
+    # CPU oracle baseline (rank 0, N = 1 only)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        counts = full_counts()
+        if counts:
+            secs, desc = oracle_sample(gm, 40, 60, counts[0], counts[1])
+            line["cpu_baseline"] = {"value": n / secs, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        else:
+            line["cpu_baseline"] = None
+
+    for p in plans.values():
+        p.release()
+    ms.ms_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

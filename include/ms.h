@@ -1,0 +1,300 @@
+/*
+ * ms.h -- C ABI of the GB300 multiscale multibasis pressure solver.
+ *
+ * The library solves the linear pressure system A p = q (Eq. (9) of
+ * Klemetsdal, Moyner & Lie, "Accelerating Multiscale Simulation of Complex
+ * Geomodels by Use of Dynamically Adapted Basis Functions") obtained from a
+ * two-point flux (TPFA) discretisation of div(K grad p) = q on a Cartesian
+ * grid with optional inactive cells, face multipliers and non-neighbour
+ * connections (Sec. 3).  It builds restriction-smoothed (MsRSB) prolongation
+ * operators P on coarse partitions (Sec. 5, Sec. 5.1), Galerkin coarse
+ * operators A_c = P^T A P (Eq. (10)), dynamically adapted extra bases from
+ * pressure updates (Sec. 5.1), and runs the multiscale multibasis iteration
+ * (Eq. (11)) inside a Richardson loop (Sec. 5.2) on one GPU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Cells.   Grid cell (i,j,k) has grid index i + nx*(j + ny*k).  The unknowns
+ *          are the ACTIVE cells in increasing grid index ("active index").
+ *          Vectors over unknowns (q, p, dp, mobility) use active indexing.
+ * Memory.  Array arguments marked "host or device" may point to host memory
+ *          (pageable or pinned) or to device memory of the context's device;
+ *          the library detects which.  Arrays marked "host" must be host
+ *          memory.  The caller keeps ownership of every array it passes; the
+ *          library reads or writes it only during the call (in stream order
+ *          for device arrays: results are complete when the context's stream
+ *          reaches the end of the call; host results are complete on return).
+ * Handles. ms_ctx, ms_system, ms_basis and ms_coarse are owned by the
+ *          library and hold device memory until released.  A handle is used
+ *          by one host thread and one stream at a time.
+ * Errors.  Every call returns an ms_status.  On error no output handle is
+ *          created and ms_last_error() describes the failure.  Device-side
+ *          waits are bounded; a wait that runs out returns MS_ERR_TIMEOUT.
+ * Precision. MS_PREC_FP64 computes everything in double precision.
+ *          MS_PREC_MIXED stores and applies the basis, the smoother and the
+ *          coarse inverse in single precision (single-precision accumulation)
+ *          and keeps the outer residual, the convergence check and the
+ *          coarse-solve refinement in double precision.
+ */
+#ifndef MS_H
+#define MS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MS_ABI_VERSION 1
+
+typedef enum {
+    MS_OK = 0,
+    MS_ERR_INVALID_ARG = 1,     /* bad size, pointer, option or input value      */
+    MS_ERR_OOM = 2,             /* device or host allocation failed              */
+    MS_ERR_CUDA = 3,            /* a CUDA runtime call failed                    */
+    MS_ERR_NOT_CONVERGED = 4,   /* iteration cap reached; outputs hold last iterate */
+    MS_ERR_COARSE_SINGULAR = 5, /* coarse Cholesky met a non-positive pivot      */
+    MS_ERR_TIMEOUT = 6,         /* a bounded device-side wait ran out            */
+    MS_ERR_STATE = 7            /* call made on a handle in the wrong state      */
+} ms_status;
+
+typedef enum { MS_PREC_FP64 = 0, MS_PREC_MIXED = 1 } ms_precision;
+typedef enum { MS_SMOOTHER_ILU0 = 0, MS_SMOOTHER_JACOBI = 1 } ms_smoother;
+typedef enum {
+    MS_SUPPORT_BOX = 0,   /* Cartesian block box grown by floor(b/2) per side, cells reachable inside it */
+    MS_SUPPORT_HOP = 1,   /* general partitions: block + neighbour-block cells nearer (in hops) to the
+                             block than to the neighbour's centre cell                                */
+    MS_SUPPORT_BLOCK = 2  /* support = the block (constant basis functions)                           */
+} ms_support_rule;
+
+typedef struct ms_ctx ms_ctx;
+typedef struct ms_system ms_system;
+typedef struct ms_basis ms_basis;
+typedef struct ms_coarse ms_coarse;
+
+/* Grid description (all arrays host memory, read during ms_system_create).
+ * Face multiplier layouts: x-face (i,j,k)-(i+1,j,k) at i + (nx-1)*(j + ny*k);
+ * y-face (i,j,k)-(i,j+1,k) at i + nx*(j + (ny-1)*k); z-face (i,j,k)-(i,j,k+1)
+ * at i + nx*(j + ny*k).  A multiplier <= 0 removes the face.  A
+ * non-neighbour connection e joins grid cells nnc[2e], nnc[2e+1]; its
+ * transmissibility uses the permeability component, face area and cell
+ * length of axis nnc_axis[e] (0,1,2) and multiplier nnc_mult[e]. */
+typedef struct {
+    int32_t nx, ny, nz;
+    double dx, dy, dz;            /* cell sizes (m)                              */
+    const uint8_t *active;        /* nx*ny*nz, nonzero = active; NULL = all       */
+    const double *mult_x;         /* (nx-1)*ny*nz or NULL (all 1)                */
+    const double *mult_y;         /* nx*(ny-1)*nz or NULL                        */
+    const double *mult_z;         /* nx*ny*(nz-1) or NULL                        */
+    int32_t n_nnc;
+    const int32_t *nnc;           /* 2*n_nnc grid indices                        */
+    const int8_t *nnc_axis;       /* n_nnc                                       */
+    const double *nnc_mult;       /* n_nnc                                       */
+} ms_grid;
+
+typedef struct {
+    int64_t n;          /* active cells (unknowns)                      */
+    int64_t n_faces;    /* two-point connections                        */
+    int32_t ell_width;  /* off-diagonal slots per row in device storage */
+    int32_t n_levels;   /* wavefront levels of the natural-order ILU(0) */
+    int32_t ref_cell;   /* pinned reference cell (active index)         */
+} ms_system_info;
+
+typedef struct {
+    double omega;       /* Jacobi relaxation of the basis smoothing (reading: 2/3)   */
+    double tol;         /* stop when max |P_new - P_old| < tol (reading: 1e-3)       */
+    int32_t max_iter;   /* iteration cap (reading: 500)                               */
+    int32_t precision;  /* ms_precision                                               */
+    int32_t support;    /* ms_support_rule                                            */
+    int32_t bx, by, bz; /* Cartesian block size, used by MS_SUPPORT_BOX               */
+} ms_basis_opts;
+
+typedef struct {
+    int32_t M;          /* coarse blocks                                 */
+    int64_t nnz;        /* sum of support sizes (entries of P)           */
+    int32_t max_overlap;/* b: largest number of bases covering one cell  */
+    int32_t iters;      /* smoothing iterations of the last build/update */
+    double last_increment;
+} ms_basis_info;
+
+typedef struct {
+    int32_t n_bins;     /* bins of log10|dp| (reading: 8)                        */
+    double eps;         /* |dp| floored at eps * max|dp| (reading: 1e-8)          */
+    int32_t smoothed;   /* 0: constant basis (the paper's); 1: MsRSB on hop supports */
+    double omega, tol;  /* smoothing parameters when smoothed                     */
+    int32_t max_iter;
+} ms_adapt_opts;
+
+typedef struct {
+    double tol;            /* relative residual ||q - A p||_2 / ||q||_2 target (1e-6) */
+    int32_t max_iter;      /* Richardson cycle cap                                    */
+    int32_t smoother;      /* ms_smoother                                             */
+    int32_t precision;     /* ms_precision                                            */
+    double jacobi_omega;   /* relaxation of the Jacobi smoother (reading: 2/3)       */
+    int32_t adapt_schedule;/* 0 none; 1 rebuild the dynamic stage after every cycle; */
+                           /* 2 after cycles 1 and 2 only (Sec. 5.1 schedule)          */
+    ms_adapt_opts adapt;   /* dynamic-stage options (used when adapt_schedule != 0)  */
+    int32_t use_x0;        /* 1: p holds the initial guess; 0: start from p = 0      */
+} ms_solve_opts;
+
+typedef struct {
+    int32_t iters;         /* Richardson cycles performed                 */
+    int32_t converged;     /* 1 if rel_residual <= tol                    */
+    double rel_residual;   /* final ||q - A p||_2 / ||q||_2 (pinned system) */
+    double *history;       /* caller array of max_iter+1 entries or NULL:
+                              relative residual before cycle 1 and after each cycle */
+    int32_t *dyn_blocks;   /* caller array of max_iter entries or NULL:
+                              blocks of the dynamic stage used in each cycle (0 = none) */
+    double seconds;        /* wall time of the call                       */
+} ms_solve_info;
+
+/* ---------------------------------------------------------------- context */
+/* Create a context on CUDA device `device` that launches on `stream`
+ * (a cudaStream_t, or NULL for the default stream). */
+ms_status ms_create(ms_ctx **ctx, int32_t device, void *stream);
+ms_status ms_destroy(ms_ctx *ctx);
+ms_status ms_set_stream(ms_ctx *ctx, void *stream);
+const char *ms_status_string(ms_status s);
+/* Detail of the last failure on this context (empty string if none). */
+const char *ms_last_error(const ms_ctx *ctx);
+int32_t ms_abi_version(void);
+
+/* ----------------------------------------------------------------- system */
+/* Analyse the grid (host): active-cell numbering, two-point connection list
+ * (Sec. 3), device ELL storage of A's pattern, and the wavefront levels of
+ * the natural-order ILU(0).  `ref_cell` is the active index of the cell whose
+ * pressure is fixed at 0 (the problem statement's reference cell; row and
+ * column ref_cell lose their off-diagonal entries and q[ref_cell] is taken as
+ * 0).  No values are computed until ms_assemble_tpfa. */
+ms_status ms_system_create(ms_ctx *ctx, const ms_grid *grid, int32_t ref_cell, ms_system **out);
+ms_status ms_system_release(ms_system *sys);
+ms_status ms_system_get_info(const ms_system *sys, ms_system_info *info);
+
+/* Two-point flux assembly (Sec. 3; Eq. (9)) on the GPU.  perm: host or
+ * device, 3*nx*ny*nz doubles, (Kx,Ky,Kz) of each grid cell in m^2, all
+ * finite and >= 0.  For each connection, T = mult / (1/t_a + 1/t_b) with
+ * half transmissibility t = K_axis * face_area / (cell_length / 2).
+ * mobility: host or device, n doubles (total mobility per active cell) or
+ * NULL; when given, T is multiplied by the face mobility, taken from the
+ * upstream cell by the sign of p_prev[a] - p_prev[b] (single-point upstream
+ * weighting) or the mean of the two cells when p_prev is NULL or on a tie.
+ * Writes A (unpinned, for basis smoothing) and its pinned copy (for the
+ * Galerkin operators and the solve).  Invalid permeability (negative, NaN or
+ * infinite) returns MS_ERR_INVALID_ARG. */
+ms_status ms_assemble_tpfa(ms_ctx *ctx, ms_system *sys, const double *perm, const double *mobility,
+                           const double *p_prev);
+
+/* Copy A out in ELL form (host arrays): col[w*n + i] and val[w*n + i] for the
+ * w-th off-diagonal slot of row i (padding slots have col = i, val = 0),
+ * diag[i].  pinned selects the pinned (1) or unpinned (0) values. */
+ms_status ms_system_get_matrix(ms_ctx *ctx, const ms_system *sys, int32_t pinned, int32_t *col, double *val,
+                               double *diag);
+
+/* y = A x with the pinned matrix (x, y host or device, n doubles). */
+ms_status ms_spmv(ms_ctx *ctx, const ms_system *sys, const double *x, double *y);
+
+/* z = (L U)^{-1} r with the natural-order ILU(0) factors of the pinned A
+ * (Sec. 5.1 smoother; Sec. 6.4): forward then backward triangular sweep.
+ * Factors are computed on first use after each assembly.  precision selects
+ * FP64 or FP32 factors. */
+ms_status ms_ilu_apply(ms_ctx *ctx, ms_system *sys, int32_t precision, const double *r, double *z);
+
+/* ------------------------------------------------------------- partitions */
+/* General structured partition (Sec. 5: non-overlapping coarse blocks;
+ * Sec. 5.1 general partitions): cell (i,j,k) goes to Cartesian block
+ * (i/bx, j/by, k/bz); blocks without active cells are dropped and the rest
+ * numbered in increasing Cartesian block order (x fastest).  part: host, n
+ * int32; *n_blocks receives the block count. */
+ms_status ms_partition_cartesian(ms_ctx *ctx, const ms_system *sys, int32_t bx, int32_t by, int32_t bz,
+                                 int32_t *part, int32_t *n_blocks);
+
+/* Face-connected components of cells with equal class (host or device cls,
+ * n int32), numbered by their lowest active index (Sec. 5.1 static
+ * partitions: class = general block x facies).  part: host or device, n
+ * int32 output; *n_blocks receives the number of components. */
+ms_status ms_partition_components(ms_ctx *ctx, const ms_system *sys, const int32_t *cls, int32_t *part,
+                                  int32_t *n_blocks);
+
+/* Dynamic partition from a pressure update (Sec. 5.1): bin
+ * log10(max(|dp|, eps*max|dp|)) into n_bins equal bins, then face-connected
+ * components per bin numbered by lowest active index.  dp host or device
+ * (n doubles); part host or device (n int32). */
+ms_status ms_partition_dynamic(ms_ctx *ctx, const ms_system *sys, const double *dp, int32_t n_bins, double eps,
+                               int32_t *part, int32_t *n_blocks);
+
+/* ------------------------------------------------------------------ basis */
+/* Build the prolongation P for a partition (host int32[n], block ids in
+ * [0, n_blocks), every block non-empty) (Sec. 5 requirements 1-3):
+ * supports by opts->support, then MsRSB smoothing from the block indicator
+ * until the largest increment falls below opts->tol (MS_SUPPORT_BLOCK gives
+ * the constant basis and no smoothing).  *iters receives the smoothing
+ * iterations (may be NULL).  Requires an assembled system. */
+ms_status ms_build_basis(ms_ctx *ctx, ms_system *sys, const int32_t *partition, int32_t n_blocks,
+                         const ms_basis_opts *opts, ms_basis **out, int32_t *iters);
+/* Recompute the basis values of an existing basis from the block indicator
+ * with the system's current A (same pattern, no allocation). */
+ms_status ms_basis_rebuild(ms_ctx *ctx, ms_system *sys, ms_basis *basis, int32_t *iters);
+/* Local basis update (Sec. 5.1): continue smoothing from the current values
+ * with the system's current A for at most max_iter iterations or until the
+ * increment falls below tol. */
+ms_status ms_basis_update(ms_ctx *ctx, ms_system *sys, ms_basis *basis, double tol, int32_t max_iter,
+                          int32_t *iters);
+ms_status ms_basis_release(ms_basis *basis);
+ms_status ms_basis_get_info(const ms_basis *basis, ms_basis_info *info);
+/* Copy P out column by column (host arrays): cptr[M+1], cells[nnz] (active
+ * indices ascending within each column), val[nnz]. */
+ms_status ms_basis_get(ms_ctx *ctx, const ms_basis *basis, int32_t *cptr, int32_t *cells, double *val);
+
+/* Dynamically adapted extra basis (Sec. 5.1): dynamic partition of dp
+ * (host or device, n doubles) and its constant basis (opts->smoothed = 0,
+ * the paper's) or an MsRSB basis on hop supports (opts->smoothed = 1). */
+ms_status ms_add_adaptive_basis(ms_ctx *ctx, ms_system *sys, const double *dp, const ms_adapt_opts *opts,
+                                ms_basis **out);
+
+/* --------------------------------------------------------- coarse operator */
+/* Galerkin coarse operator A_c = P^T A P with the pinned A (Eq. (10),
+ * R = P^T) and its dense Cholesky factorisation and inverse for the coarse
+ * solve.  precision MS_PREC_MIXED factors in FP32 and refines in FP64. */
+ms_status ms_galerkin(ms_ctx *ctx, ms_system *sys, const ms_basis *basis, int32_t precision, ms_coarse **out);
+/* Recompute A_c and its factors in place from the basis and the current A. */
+ms_status ms_coarse_refresh(ms_ctx *ctx, ms_system *sys, ms_coarse *coarse);
+ms_status ms_coarse_release(ms_coarse *coarse);
+/* Copy A_c out (host, M*M doubles, row-major). */
+ms_status ms_coarse_get(ms_ctx *ctx, const ms_coarse *coarse, double *Ac, int32_t *M);
+
+/* ------------------------------------------------------------------ solve */
+/* Multiscale multibasis iteration (Eq. (11)) in a Richardson loop
+ * (Sec. 5.2).  Per cycle, for each stage l = 0..n_stages-1 (then the
+ * dynamic stage, if any):  p += S(q - A p);  p += P_l A_c,l^{-1} P_l^T (q - A p).
+ * After each cycle the cycle stops when ||q - A p||_2 <= tol ||q||_2.
+ * q: host or device, n doubles; p: host or device, n doubles (initial guess
+ * if opts->use_x0, else overwritten from 0; holds the last iterate on
+ * return, also on MS_ERR_NOT_CONVERGED).  stages: coarse operators built on
+ * this system.  info may be NULL. */
+ms_status ms_solve(ms_ctx *ctx, ms_system *sys, ms_coarse *const *stages, int32_t n_stages, const double *q,
+                   double *p, const ms_solve_opts *opts, ms_solve_info *info);
+
+/* ---------------------------------------------------------------- tracing */
+/* Process-wide kernel tracing.  Launch counts are always kept; when enabled,
+ * each launch is also timed with a pair of CUDA events recorded on the
+ * stream it runs on, and its algorithmic bytes (what the method must move
+ * for that launch in this library's storage layout) are accumulated. */
+typedef struct {
+    char name[32];           /* kernel family                                   */
+    int64_t launches;        /* launches since the last reset                   */
+    int64_t timed_launches;  /* launches timed with events (tracing enabled)    */
+    double total_ms;         /* summed device time of the timed launches        */
+    double bytes;            /* summed algorithmic bytes of the timed launches  */
+} ms_kernel_stat;
+
+ms_status ms_profile_enable(int32_t on);
+ms_status ms_profile_reset(void);
+/* Fills up to `capacity` entries (out may be NULL to query the count);
+ * *count receives the number of kernel families, *total_launches the launch
+ * count over all families.  Waits for the timed launches to finish. */
+ms_status ms_profile_read(ms_kernel_stat *out, int32_t capacity, int32_t *count, int64_t *total_launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MS_H */

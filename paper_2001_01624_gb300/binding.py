@@ -1,0 +1,388 @@
+"""ctypes binding of the C ABI in include/ms.h -- argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own: it converts arguments (numpy arrays are passed as host
+pointers, torch tensors as device pointers, torch streams as cudaStream_t),
+calls the library, and raises :class:`MsError` on a failing status.  There is
+no fallback: if the CUDA library has not been built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmsgb.so")
+
+MS_OK, MS_ERR_INVALID_ARG, MS_ERR_OOM, MS_ERR_CUDA, MS_ERR_NOT_CONVERGED = 0, 1, 2, 3, 4
+MS_ERR_COARSE_SINGULAR, MS_ERR_TIMEOUT, MS_ERR_STATE = 5, 6, 7
+MS_PREC_FP64, MS_PREC_MIXED = 0, 1
+MS_SMOOTHER_ILU0, MS_SMOOTHER_JACOBI = 0, 1
+MS_SUPPORT_BOX, MS_SUPPORT_HOP, MS_SUPPORT_BLOCK = 0, 1, 2
+
+_vp, _i32, _i64, _d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+
+
+class MsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+class ms_grid(C.Structure):
+    _fields_ = [("nx", _i32), ("ny", _i32), ("nz", _i32), ("dx", _d), ("dy", _d), ("dz", _d),
+                ("active", _vp), ("mult_x", _vp), ("mult_y", _vp), ("mult_z", _vp),
+                ("n_nnc", _i32), ("nnc", _vp), ("nnc_axis", _vp), ("nnc_mult", _vp)]
+
+
+class ms_system_info(C.Structure):
+    _fields_ = [("n", _i64), ("n_faces", _i64), ("ell_width", _i32), ("n_levels", _i32), ("ref_cell", _i32)]
+
+
+class ms_basis_opts(C.Structure):
+    _fields_ = [("omega", _d), ("tol", _d), ("max_iter", _i32), ("precision", _i32), ("support", _i32),
+                ("bx", _i32), ("by", _i32), ("bz", _i32)]
+
+
+class ms_basis_info(C.Structure):
+    _fields_ = [("M", _i32), ("nnz", _i64), ("max_overlap", _i32), ("iters", _i32), ("last_increment", _d)]
+
+
+class ms_adapt_opts(C.Structure):
+    _fields_ = [("n_bins", _i32), ("eps", _d), ("smoothed", _i32), ("omega", _d), ("tol", _d), ("max_iter", _i32)]
+
+
+class ms_solve_opts(C.Structure):
+    _fields_ = [("tol", _d), ("max_iter", _i32), ("smoother", _i32), ("precision", _i32), ("jacobi_omega", _d),
+                ("adapt_schedule", _i32), ("adapt", ms_adapt_opts), ("use_x0", _i32)]
+
+
+class ms_kernel_stat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", _i64), ("timed_launches", _i64), ("total_ms", _d),
+                ("bytes", _d)]
+
+
+class ms_solve_info(C.Structure):
+    _fields_ = [("iters", _i32), ("converged", _i32), ("rel_residual", _d), ("history", _vp),
+                ("dyn_blocks", _vp), ("seconds", _d)]
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built ({LIB_PATH} missing): run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    P = C.POINTER
+    sig = {
+        "ms_abi_version": ([], _i32),
+        "ms_status_string": ([_i32], C.c_char_p),
+        "ms_last_error": ([_vp], C.c_char_p),
+        "ms_create": ([P(_vp), _i32, _vp], _i32),
+        "ms_destroy": ([_vp], _i32),
+        "ms_set_stream": ([_vp, _vp], _i32),
+        "ms_system_create": ([_vp, P(ms_grid), _i32, P(_vp)], _i32),
+        "ms_system_release": ([_vp], _i32),
+        "ms_system_get_info": ([_vp, P(ms_system_info)], _i32),
+        "ms_assemble_tpfa": ([_vp, _vp, _vp, _vp, _vp], _i32),
+        "ms_system_get_matrix": ([_vp, _vp, _i32, _vp, _vp, _vp], _i32),
+        "ms_spmv": ([_vp, _vp, _vp, _vp], _i32),
+        "ms_ilu_apply": ([_vp, _vp, _i32, _vp, _vp], _i32),
+        "ms_partition_cartesian": ([_vp, _vp, _i32, _i32, _i32, _vp, P(_i32)], _i32),
+        "ms_partition_components": ([_vp, _vp, _vp, _vp, P(_i32)], _i32),
+        "ms_partition_dynamic": ([_vp, _vp, _vp, _i32, _d, _vp, P(_i32)], _i32),
+        "ms_build_basis": ([_vp, _vp, _vp, _i32, P(ms_basis_opts), P(_vp), P(_i32)], _i32),
+        "ms_basis_rebuild": ([_vp, _vp, _vp, P(_i32)], _i32),
+        "ms_basis_update": ([_vp, _vp, _vp, _d, _i32, P(_i32)], _i32),
+        "ms_basis_release": ([_vp], _i32),
+        "ms_basis_get_info": ([_vp, P(ms_basis_info)], _i32),
+        "ms_basis_get": ([_vp, _vp, _vp, _vp, _vp], _i32),
+        "ms_add_adaptive_basis": ([_vp, _vp, _vp, P(ms_adapt_opts), P(_vp)], _i32),
+        "ms_galerkin": ([_vp, _vp, _vp, _i32, P(_vp)], _i32),
+        "ms_coarse_refresh": ([_vp, _vp, _vp], _i32),
+        "ms_coarse_release": ([_vp], _i32),
+        "ms_coarse_get": ([_vp, _vp, _vp, P(_i32)], _i32),
+        "ms_solve": ([_vp, _vp, P(_vp), _i32, _vp, _vp, P(ms_solve_opts), P(ms_solve_info)], _i32),
+        "ms_profile_enable": ([_i32], _i32),
+        "ms_profile_reset": ([], _i32),
+        "ms_profile_read": ([_vp, _i32, P(_i32), P(_i64)], _i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def exported_symbols() -> Sequence[str]:
+    return ["ms_abi_version", "ms_status_string", "ms_last_error", "ms_create", "ms_destroy", "ms_set_stream",
+            "ms_system_create", "ms_system_release", "ms_system_get_info", "ms_assemble_tpfa",
+            "ms_system_get_matrix", "ms_spmv", "ms_ilu_apply", "ms_partition_cartesian", "ms_partition_components", "ms_partition_dynamic",
+            "ms_build_basis", "ms_basis_rebuild", "ms_basis_update", "ms_basis_release", "ms_basis_get_info",
+            "ms_basis_get", "ms_add_adaptive_basis", "ms_galerkin", "ms_coarse_refresh", "ms_coarse_release",
+            "ms_coarse_get", "ms_solve", "ms_profile_enable", "ms_profile_reset", "ms_profile_read"]
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check(st, ctx=None):
+    if st != MS_OK:
+        msg = lib().ms_last_error(ctx).decode() if ctx else ""
+        name = lib().ms_status_string(st).decode()
+        raise MsError(st, f"{name}: {msg}" if msg else name)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream        # torch.cuda.Stream
+
+
+def _as(a, dtype):
+    if a is None or hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# ------------------------------------------------------------------ context
+def ms_abi_version() -> int:
+    return lib().ms_abi_version()
+
+
+def ms_status_string(status: int) -> str:
+    return lib().ms_status_string(status).decode()
+
+
+def ms_last_error(ctx) -> str:
+    return lib().ms_last_error(ctx).decode()
+
+
+def ms_create(device: int = 0, stream=None):
+    h = _vp()
+    _check(lib().ms_create(C.byref(h), device, _stream_handle(stream)))
+    return h
+
+
+def ms_destroy(ctx):
+    lib().ms_destroy(ctx)
+
+
+def ms_set_stream(ctx, stream):
+    _check(lib().ms_set_stream(ctx, _stream_handle(stream)), ctx)
+
+
+# ------------------------------------------------------------------- system
+def ms_system_create(ctx, grid, ref_cell: int = 0):
+    keep = []
+
+    def arr(a, dt):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return a.ctypes.data
+
+    g = ms_grid(grid.nx, grid.ny, grid.nz, grid.dx, grid.dy, grid.dz, arr(grid.active, np.uint8),
+                arr(grid.mult_x, np.float64), arr(grid.mult_y, np.float64), arr(grid.mult_z, np.float64),
+                grid.n_nnc, arr(grid.nnc, np.int32) if grid.n_nnc else None,
+                arr(grid.nnc_axis, np.int8) if grid.n_nnc else None,
+                arr(grid.nnc_mult, np.float64) if grid.n_nnc else None)
+    h = _vp()
+    _check(lib().ms_system_create(ctx, C.byref(g), ref_cell, C.byref(h)), ctx)
+    return h
+
+
+def ms_system_release(sys):
+    lib().ms_system_release(sys)
+
+
+def ms_system_get_info(sys) -> dict:
+    i = ms_system_info()
+    _check(lib().ms_system_get_info(sys, C.byref(i)))
+    return dict(n=i.n, n_faces=i.n_faces, ell_width=i.ell_width, n_levels=i.n_levels, ref_cell=i.ref_cell)
+
+
+def ms_assemble_tpfa(ctx, sys, perm, mobility=None, p_prev=None):
+    perm, mobility, p_prev = _as(perm, np.float64), _as(mobility, np.float64), _as(p_prev, np.float64)
+    _check(lib().ms_assemble_tpfa(ctx, sys, _ptr(perm), _ptr(mobility), _ptr(p_prev)), ctx)
+
+
+def ms_system_get_matrix(ctx, sys, pinned: bool = True):
+    info = ms_system_get_info(sys)
+    n, W = info["n"], info["ell_width"]
+    col = np.empty(max(W * n, 1), np.int32)
+    val = np.empty(max(W * n, 1))
+    diag = np.empty(n)
+    _check(lib().ms_system_get_matrix(ctx, sys, int(pinned), _ptr(col), _ptr(val), _ptr(diag)), ctx)
+    return col[: W * n].reshape(W, n), val[: W * n].reshape(W, n), diag
+
+
+def ms_spmv(ctx, sys, x, y):
+    _check(lib().ms_spmv(ctx, sys, _ptr(_as(x, np.float64)), _ptr(y)), ctx)
+
+
+def ms_ilu_apply(ctx, sys, r, z, precision: int = MS_PREC_FP64):
+    _check(lib().ms_ilu_apply(ctx, sys, precision, _ptr(_as(r, np.float64)), _ptr(z)), ctx)
+
+
+# --------------------------------------------------------------- partitions
+def ms_partition_cartesian(ctx, sys, block):
+    n = ms_system_get_info(sys)["n"]
+    part = np.empty(n, np.int32)
+    m = _i32()
+    _check(lib().ms_partition_cartesian(ctx, sys, int(block[0]), int(block[1]), int(block[2]), _ptr(part),
+                                        C.byref(m)), ctx)
+    return part, m.value
+
+
+def ms_partition_components(ctx, sys, cls, part) -> int:
+    m = _i32()
+    _check(lib().ms_partition_components(ctx, sys, _ptr(_as(cls, np.int32)), _ptr(part), C.byref(m)), ctx)
+    return m.value
+
+
+def ms_partition_dynamic(ctx, sys, dp, part, n_bins: int = 8, eps: float = 1e-8) -> int:
+    m = _i32()
+    _check(lib().ms_partition_dynamic(ctx, sys, _ptr(_as(dp, np.float64)), n_bins, eps, _ptr(part), C.byref(m)),
+           ctx)
+    return m.value
+
+
+# -------------------------------------------------------------------- basis
+def ms_build_basis(ctx, sys, partition, n_blocks: int, omega=2.0 / 3.0, tol=1e-3, max_iter=500,
+                   precision=MS_PREC_FP64, support=MS_SUPPORT_BOX, block=(1, 1, 1)):
+    o = ms_basis_opts(omega, tol, max_iter, precision, support, int(block[0]), int(block[1]), int(block[2]))
+    h = _vp()
+    it = _i32()
+    part = np.ascontiguousarray(partition, dtype=np.int32)
+    _check(lib().ms_build_basis(ctx, sys, _ptr(part), n_blocks, C.byref(o), C.byref(h), C.byref(it)), ctx)
+    return h, it.value
+
+
+def ms_basis_rebuild(ctx, sys, basis) -> int:
+    it = _i32()
+    _check(lib().ms_basis_rebuild(ctx, sys, basis, C.byref(it)), ctx)
+    return it.value
+
+
+def ms_basis_update(ctx, sys, basis, tol: float, max_iter: int) -> int:
+    it = _i32()
+    _check(lib().ms_basis_update(ctx, sys, basis, tol, max_iter, C.byref(it)), ctx)
+    return it.value
+
+
+def ms_basis_release(basis):
+    lib().ms_basis_release(basis)
+
+
+def ms_basis_get_info(basis) -> dict:
+    i = ms_basis_info()
+    _check(lib().ms_basis_get_info(basis, C.byref(i)))
+    return dict(M=i.M, nnz=i.nnz, max_overlap=i.max_overlap, iters=i.iters, last_increment=i.last_increment)
+
+
+def ms_basis_get(ctx, basis):
+    info = ms_basis_get_info(basis)
+    cptr = np.empty(info["M"] + 1, np.int32)
+    cells = np.empty(max(info["nnz"], 1), np.int32)
+    val = np.empty(max(info["nnz"], 1))
+    _check(lib().ms_basis_get(ctx, basis, _ptr(cptr), _ptr(cells), _ptr(val)), ctx)
+    return cptr, cells[: info["nnz"]], val[: info["nnz"]]
+
+
+def ms_add_adaptive_basis(ctx, sys, dp, n_bins=8, eps=1e-8, smoothed=0, omega=2.0 / 3.0, tol=1e-3, max_iter=500):
+    o = ms_adapt_opts(n_bins, eps, smoothed, omega, tol, max_iter)
+    h = _vp()
+    _check(lib().ms_add_adaptive_basis(ctx, sys, _ptr(_as(dp, np.float64)), C.byref(o), C.byref(h)), ctx)
+    return h
+
+
+# ------------------------------------------------------------------- coarse
+def ms_galerkin(ctx, sys, basis, precision=MS_PREC_FP64):
+    h = _vp()
+    _check(lib().ms_galerkin(ctx, sys, basis, precision, C.byref(h)), ctx)
+    return h
+
+
+def ms_coarse_refresh(ctx, sys, coarse):
+    _check(lib().ms_coarse_refresh(ctx, sys, coarse), ctx)
+
+
+def ms_coarse_release(coarse):
+    lib().ms_coarse_release(coarse)
+
+
+def ms_coarse_get(ctx, coarse):
+    m = _i32()
+    _check(lib().ms_coarse_get(ctx, coarse, None, C.byref(m)), ctx)
+    Ac = np.empty((m.value, m.value))
+    _check(lib().ms_coarse_get(ctx, coarse, _ptr(Ac), C.byref(m)), ctx)
+    return Ac
+
+
+# -------------------------------------------------------------------- solve
+def ms_solve(ctx, sys, stages, q, p, tol=1e-6, max_iter=500, smoother=MS_SMOOTHER_ILU0, precision=MS_PREC_FP64,
+             jacobi_omega=2.0 / 3.0, adapt_schedule=0, adapt: Optional[dict] = None, use_x0=False,
+             raise_not_converged=False) -> dict:
+    """Returns dict(status, iters, converged, rel_residual, history, dyn_blocks, seconds)."""
+    ad = dict(n_bins=8, eps=1e-8, smoothed=0, omega=2.0 / 3.0, tol=1e-3, max_iter=500)
+    ad.update(adapt or {})
+    o = ms_solve_opts(tol, max_iter, smoother, precision, jacobi_omega, adapt_schedule,
+                      ms_adapt_opts(ad["n_bins"], ad["eps"], ad["smoothed"], ad["omega"], ad["tol"], ad["max_iter"]),
+                      int(use_x0))
+    hist = np.zeros(max_iter + 1)
+    dyn = np.zeros(max(max_iter, 1), np.int32)
+    info = ms_solve_info(0, 0, 0.0, hist.ctypes.data, dyn.ctypes.data, 0.0)
+    arr = (_vp * max(len(stages), 1))(*[s.value if isinstance(s, _vp) else s for s in stages])
+    q = _as(q, np.float64)
+    st = lib().ms_solve(ctx, sys, arr, len(stages), _ptr(q), _ptr(p), C.byref(o), C.byref(info))
+    if st not in (MS_OK, MS_ERR_NOT_CONVERGED) or (st == MS_ERR_NOT_CONVERGED and raise_not_converged):
+        _check(st, ctx)
+    return dict(status=st, iters=info.iters, converged=bool(info.converged), rel_residual=info.rel_residual,
+                history=hist[: info.iters + 1].copy(), dyn_blocks=dyn[: info.iters].copy(), seconds=info.seconds)
+
+
+# ------------------------------------------------------------------ tracing
+def ms_profile_enable(on: bool = True):
+    _check(lib().ms_profile_enable(int(on)))
+
+
+def ms_profile_reset():
+    _check(lib().ms_profile_reset())
+
+
+def ms_profile_read() -> dict:
+    """Per kernel family: dict(launches, timed_launches, total_ms, bytes); key
+    '_total_launches' holds the launch count over all families."""
+    cnt = _i32()
+    tot = _i64()
+    _check(lib().ms_profile_read(None, 0, C.byref(cnt), C.byref(tot)))
+    arr = (ms_kernel_stat * max(cnt.value, 1))()
+    _check(lib().ms_profile_read(arr, cnt.value, C.byref(cnt), C.byref(tot)))
+    out = {a.name.decode(): dict(launches=a.launches, timed_launches=a.timed_launches, total_ms=a.total_ms,
+                                 bytes=a.bytes) for a in arr[: cnt.value]}
+    out["_total_launches"] = tot.value
+    return out

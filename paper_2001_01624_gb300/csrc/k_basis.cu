@@ -1,0 +1,307 @@
+// Prolongation bases and Galerkin coarse operators.
+//
+// MsRSB smoothing (Sec. 5.1; Sec. 5 requirements 2-3): from the block
+// indicator, every iteration updates each basis on its support from the old
+// values,  P_ij <- P_ij - omega (A P_j)_i / A_ii  (i in S_j; 0 elsewhere),
+// then renormalises every cell so that sum_j P_ij = 1.  One thread per cell
+// does both steps for all bases covering the cell: the cell's slot list and
+// its neighbours' slot lists are sorted by block id, so (A P_j)_i is a merge
+// of at most 1 + W short sorted lists.  Supports are implicit in the slot
+// pattern (a cell without a slot for block j is outside S_j), so confinement
+// holds by construction.
+//
+// Galerkin operator (Eq. (10), R = P^T): (A P)_il is formed per cell as the
+// merge of the slot lists of the cell and its neighbours; then row j of
+// A_c = P^T (A P) is accumulated by one warp over the support of block j in
+// shared memory, in a fixed order (deterministic), and A_c is symmetrised.
+#include "ms_internal.h"
+
+namespace msgb {
+
+namespace {
+
+constexpr int kThreads = 256;
+inline int blocks_for(int64_t n, int t = kThreads) { return (int)((n + t - 1) / t); }
+
+__global__ void k_basis_init(int64_t total, const unsigned char *__restrict__ is_home, double *pv) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; e < total; e += (int64_t)gridDim.x * blockDim.x) pv[e] = is_home[e] ? 1.0 : 0.0;
+}
+
+__global__ void k_basis_init32(int64_t total, const unsigned char *__restrict__ is_home, float *pv) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; e < total; e += (int64_t)gridDim.x * blockDim.x) pv[e] = is_home[e] ? 1.0f : 0.0f;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, double v) {
+    atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// One MsRSB iteration for all bases, fused with the partition-of-unity pass.
+template <typename T, int BM>
+__global__ void __launch_bounds__(kThreads) k_msrsb(int n, int W, int B, const int *__restrict__ col,
+                                                    const T *__restrict__ off, const T *__restrict__ diag,
+                                                    const int *__restrict__ pid, const T *__restrict__ pin,
+                                                    T *__restrict__ pout, T omega, unsigned long long *maxinc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    T inc = 0;
+    if (i < n) {
+        int ids[BM];
+        T v[BM], acc[BM];
+        const T d = diag[i];
+#pragma unroll
+        for (int s = 0; s < BM; ++s) {
+            ids[s] = s < B ? pid[(int64_t)s * n + i] : kSlotPad;
+            v[s] = ids[s] != kSlotPad ? pin[(int64_t)s * n + i] : T(0);
+            acc[s] = d * v[s];
+        }
+        for (int w = 0; w < W; ++w) {
+            const int k = col[(int64_t)w * n + i];
+            if (k == i) continue;
+            const T a = off[(int64_t)w * n + i];
+            int t = 0;
+            int kid = pid[k];
+#pragma unroll
+            for (int s = 0; s < BM; ++s) {
+                if (ids[s] != kSlotPad) {
+                    while (kid < ids[s]) {
+                        ++t;
+                        kid = t < B ? pid[(int64_t)t * n + k] : kSlotPad;
+                    }
+                    if (kid == ids[s]) acc[s] += a * pin[(int64_t)t * n + k];
+                }
+            }
+        }
+        T sum = 0;
+#pragma unroll
+        for (int s = 0; s < BM; ++s) {
+            if (ids[s] != kSlotPad) {
+                acc[s] = v[s] - omega * acc[s] / d;
+                sum += acc[s];
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < BM; ++s) {
+            if (ids[s] != kSlotPad) {
+                const T nv = acc[s] / sum;
+                const T dv = nv > v[s] ? nv - v[s] : v[s] - nv;
+                inc = dv > inc ? dv : inc;
+                pout[(int64_t)s * n + i] = nv;
+            }
+        }
+    }
+    // CTA max then one atomic per CTA
+    __shared__ double wmax[kThreads / 32];
+    double m = (double)inc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mm = 0.0;
+        for (int q = 0; q < kThreads / 32; ++q) mm = fmax(mm, wmax[q]);
+        atomic_max_nonneg(maxinc, mm);
+    }
+}
+
+template <typename T>
+__global__ void k_gather_columns(int64_t nnz, const int *__restrict__ csrc, const T *__restrict__ pval,
+                                 T *__restrict__ cval) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; e < nnz; e += (int64_t)gridDim.x * blockDim.x) cval[e] = pval[csrc[e]];
+}
+
+__global__ void k_widen(int64_t nnz, const float *a, double *b) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; e < nnz; e += (int64_t)gridDim.x * blockDim.x) b[e] = (double)a[e];
+}
+
+// ---------------------------------------------------------------- (A P)
+// Merge of the sorted slot lists of cell i (weight diag) and of its
+// neighbours (weights off).  COUNT only counts distinct blocks; otherwise
+// the union ids and values (A P)_il are written, padded to WAP.
+constexpr int kMaxNbr = 32;
+
+template <bool COUNT>
+__global__ void __launch_bounds__(128) k_ap(int n, int W, int B, const int *__restrict__ col,
+                                            const double *__restrict__ off, const double *__restrict__ diag,
+                                            const int *__restrict__ pid, const double *__restrict__ pval, int WAP,
+                                            int *__restrict__ apid, double *__restrict__ apval, int *cnt_max) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int count = 0;
+    if (i < n) {
+        int src[kMaxNbr + 1];
+        double wgt[kMaxNbr + 1];
+        int pos[kMaxNbr + 1];
+        int head[kMaxNbr + 1];
+        int L = 0;
+        src[L] = i; wgt[L] = diag[i]; pos[L] = 0; head[L] = pid[i]; ++L;
+        for (int w = 0; w < W && L <= kMaxNbr; ++w) {
+            const int k = col[(int64_t)w * n + i];
+            if (k == i) continue;
+            src[L] = k; wgt[L] = off[(int64_t)w * n + i]; pos[L] = 0; head[L] = pid[k]; ++L;
+        }
+        while (true) {
+            int l = kSlotPad;
+            for (int q = 0; q < L; ++q) l = min(l, head[q]);
+            if (l == kSlotPad) break;
+            double val = 0.0;
+            for (int q = 0; q < L; ++q) {
+                if (head[q] == l) {
+                    if (!COUNT) val += wgt[q] * pval[(int64_t)pos[q] * n + src[q]];
+                    ++pos[q];
+                    head[q] = pos[q] < B ? pid[(int64_t)pos[q] * n + src[q]] : kSlotPad;
+                }
+            }
+            if (!COUNT) {
+                apid[(int64_t)count * n + i] = l;
+                apval[(int64_t)count * n + i] = val;
+            }
+            ++count;
+        }
+        if (!COUNT)
+            for (int c = count; c < WAP; ++c) {
+                apid[(int64_t)c * n + i] = kSlotPad;
+                apval[(int64_t)c * n + i] = 0.0;
+            }
+    }
+    if (COUNT) {
+        __shared__ int m;
+        if (threadIdx.x == 0) m = 0;
+        __syncthreads();
+        atomicMax(&m, count);
+        __syncthreads();
+        if (threadIdx.x == 0) atomicMax(cnt_max, m);
+    }
+}
+
+// Row j of A_c: warp-per-block accumulation over the support of block j.
+__global__ void k_rap(int n, int M, int WAP, const int *__restrict__ cptr, const int *__restrict__ ccell,
+                      const double *__restrict__ cval, const int *__restrict__ apid,
+                      const double *__restrict__ apval, double *__restrict__ Ac) {
+    extern __shared__ double acc_all[];
+    const int warps = blockDim.x >> 5;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * warps + wid;
+    double *acc = acc_all + (size_t)wid * M;
+    if (j >= M) return;
+    for (int l = lane; l < M; l += 32) acc[l] = 0.0;
+    __syncwarp();
+    for (int e = cptr[j]; e < cptr[j + 1]; ++e) {
+        const int i = ccell[e];
+        const double p = cval[e];
+        for (int w = lane; w < WAP; w += 32) {
+            const int l = apid[(int64_t)w * n + i];
+            if (l != kSlotPad) acc[l] += p * apval[(int64_t)w * n + i];
+        }
+        __syncwarp();
+    }
+    for (int l = lane; l < M; l += 32) Ac[(int64_t)j * M + l] = acc[l];
+}
+
+__global__ void k_symmetrise(int M, double *Ac) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)M * M) return;
+    const int r = (int)(e / M), c = (int)(e % M);
+    if (c <= r) return;
+    const double a = Ac[(int64_t)r * M + c], b = Ac[(int64_t)c * M + r];
+    const double m = 0.5 * (a + b);
+    Ac[(int64_t)r * M + c] = m;
+    Ac[(int64_t)c * M + r] = m;
+}
+
+}  // namespace
+
+void launch_basis_init(ms_basis &b, int n, cudaStream_t st) {
+    const int64_t total = (int64_t)b.B * n;
+    const int blocks = (int)std::min<int64_t>((total + kThreads - 1) / kThreads, 8192);
+    KernelScope ks_(st, "basis_init", (double)total * (1 + (b.precision == MS_PREC_MIXED ? 4 : 8)));
+    if (b.precision == MS_PREC_MIXED) k_basis_init32<<<blocks, kThreads, 0, st>>>(total, b.is_home.p, b.pval32.p);
+    else k_basis_init<<<blocks, kThreads, 0, st>>>(total, b.is_home.p, b.pval.p);
+    MS_CHECK_LAUNCH();
+}
+
+template <typename T>
+static void msrsb_dispatch(const ms_system &s, int B, const int *pid, const T *off, const T *diag, const T *pin,
+                           T *pout, T omega, unsigned long long *maxinc, cudaStream_t st) {
+    const int g = blocks_for(s.n);
+    // A (unpinned) once, slot ids and old values once, new values written
+    KernelScope ks_(st, sizeof(T) == 8 ? "msrsb" : "msrsb32",
+                    (double)s.n * sizeof(T) + (double)s.W * s.n * (4 + sizeof(T)) +
+                        (double)B * s.n * (4 + 2 * sizeof(T)));
+    if (B <= 4) k_msrsb<T, 4><<<g, kThreads, 0, st>>>(s.n, s.W, B, s.col.p, off, diag, pid, pin, pout, omega, maxinc);
+    else if (B <= 8) k_msrsb<T, 8><<<g, kThreads, 0, st>>>(s.n, s.W, B, s.col.p, off, diag, pid, pin, pout, omega, maxinc);
+    else if (B <= 16) k_msrsb<T, 16><<<g, kThreads, 0, st>>>(s.n, s.W, B, s.col.p, off, diag, pid, pin, pout, omega, maxinc);
+    else if (B <= 32) k_msrsb<T, 32><<<g, kThreads, 0, st>>>(s.n, s.W, B, s.col.p, off, diag, pid, pin, pout, omega, maxinc);
+    else throw Error{MS_ERR_INVALID_ARG, "basis overlap above 32 per cell is not supported"};
+    MS_CHECK_LAUNCH();
+}
+
+// One iteration; the new values end up in pval (buffers swapped).
+void launch_msrsb_iter(const ms_system &s, ms_basis &b, bool fp32, unsigned long long *maxinc, cudaStream_t st) {
+    if (fp32) {
+        msrsb_dispatch<float>(s, b.B, b.pid.p, s.off_u32.p, s.diag32.p, b.pval32.p, b.pval32_tmp.p, (float)b.omega,
+                              maxinc, st);
+        std::swap(b.pval32.p, b.pval32_tmp.p);
+    } else {
+        msrsb_dispatch<double>(s, b.B, b.pid.p, s.off_u.p, s.diag.p, b.pval.p, b.pval_tmp.p, b.omega, maxinc, st);
+        std::swap(b.pval.p, b.pval_tmp.p);
+    }
+}
+
+// Column view values from the cell-major slots (and an FP64 copy of FP32
+// bases, used by the Galerkin product).
+void launch_basis_columns(ms_basis &b, cudaStream_t st) {
+    const int blocks = (int)std::min<int64_t>((b.nnz + kThreads - 1) / kThreads, 8192);
+    if (b.nnz == 0) return;
+    KernelScope ks_(st, "basis_columns", (double)b.nnz * 16);
+    if (b.precision == MS_PREC_MIXED) {
+        k_gather_columns<float><<<blocks, kThreads, 0, st>>>(b.nnz, b.csrc.p, b.pval32.p, b.cval32.p);
+        k_widen<<<blocks, kThreads, 0, st>>>(b.nnz, b.cval32.p, b.cval.p);
+        const int64_t tot = (int64_t)b.B * (int64_t)(b.pval.n / std::max(b.B, 1));   // FP64 slot copy for the Galerkin product
+        const int bb = (int)std::min<int64_t>((tot + kThreads - 1) / kThreads, 8192);
+        if (tot) k_widen<<<bb, kThreads, 0, st>>>(tot, b.pval32.p, b.pval.p);
+    } else {
+        k_gather_columns<double><<<blocks, kThreads, 0, st>>>(b.nnz, b.csrc.p, b.pval.p, b.cval.p);
+    }
+    MS_CHECK_LAUNCH();
+}
+
+int launch_ap_count(const ms_system &s, const ms_basis &b, int *cnt_max, int *host_pinned, cudaStream_t st) {
+    MS_REQUIRE(s.W <= kMaxNbr, MS_ERR_INVALID_ARG, "too many connections per cell for the Galerkin kernel");
+    MS_CUDA(cudaMemsetAsync(cnt_max, 0, sizeof(int), st));
+    KernelScope ks_(st, "ap_count", 0.0);
+    k_ap<true><<<blocks_for(s.n, 128), 128, 0, st>>>(s.n, s.W, b.B, s.col.p, s.off_p.p, s.diag.p, b.pid.p, b.pval.p,
+                                                      0, nullptr, nullptr, cnt_max);
+    MS_CHECK_LAUNCH();
+    MS_CUDA(cudaMemcpyAsync(host_pinned, cnt_max, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MS_CUDA(cudaStreamSynchronize(st));
+    return *host_pinned;
+}
+
+void launch_ap_fill(const ms_system &s, const ms_basis &b, ms_coarse &c, cudaStream_t st) {
+    KernelScope ks_(st, "ap_fill", 0.0);
+    k_ap<false><<<blocks_for(s.n, 128), 128, 0, st>>>(s.n, s.W, b.B, s.col.p, s.off_p.p, s.diag.p, b.pid.p,
+                                                       b.pval.p, c.WAP, c.apid.p, c.apval.p, nullptr);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_rap(const ms_system &s, const ms_basis &b, ms_coarse &c, cudaStream_t st) {
+    const int M = c.M;
+    const size_t per_warp = (size_t)M * sizeof(double);
+    MS_REQUIRE(per_warp <= 200 * 1024, MS_ERR_INVALID_ARG, "coarse system too large for the Galerkin kernel");
+    int warps = (int)std::max<size_t>(1, std::min<size_t>(8, (48 * 1024) / per_warp));
+    size_t smem = per_warp * warps;
+    if (smem > 48 * 1024) {
+        MS_CUDA(cudaFuncSetAttribute(k_rap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    KernelScope ks_(st, "rap", 0.0);
+    k_rap<<<(M + warps - 1) / warps, 32 * warps, smem, st>>>(s.n, M, c.WAP, b.cptr.p, b.ccell.p, b.cval.p, c.apid.p,
+                                                            c.apval.p, c.Ac.p);
+    MS_CHECK_LAUNCH();
+    const int64_t MM = (int64_t)M * M;
+    k_symmetrise<<<(int)((MM + kThreads - 1) / kThreads), kThreads, 0, st>>>(M, c.Ac.p);
+    MS_CHECK_LAUNCH();
+}
+
+}  // namespace msgb

@@ -1,0 +1,329 @@
+// Dense coarse-system algebra: the coarse solve x_c = A_c^{-1} d of Eq. (11).
+//
+// A_c (M x M, SPD by Galerkin construction, Eq. (10)) is factored once per
+// coarse refresh by a blocked right-looking Cholesky (32-wide panels:
+// diagonal block in shared memory, panel triangular solve, trailing
+// symmetric update), then inverted as A_c^{-1} = L^{-T} L^{-1} (blocked
+// forward substitution on the identity, then a Gram product), so every
+// cycle's coarse solve is one dense matrix-vector product.
+//
+// FP32 path (mixed precision): A_c is symmetrically equilibrated,
+// s_i = 1/sqrt(A_ii), factored and inverted in FP32, and the inverse is
+// scaled back; the solve refines x_c in FP64 against the FP64 A_c.
+#include <cmath>
+
+#include "ms_internal.h"
+
+namespace msgb {
+
+namespace {
+
+constexpr int NB = 32;
+
+template <typename T>
+__device__ __forceinline__ T dsqrt(T v);
+template <>
+__device__ __forceinline__ double dsqrt<double>(double v) { return sqrt(v); }
+template <>
+__device__ __forceinline__ float dsqrt<float>(float v) { return sqrtf(v); }
+
+// Factor the diagonal block A[k0:k0+nb, k0:k0+nb] in place (lower).
+template <typename T>
+__global__ void k_potrf_diag(T *A, int M, int k0, int nb, int *err) {
+    __shared__ T a[NB][NB + 1];
+    const int r = threadIdx.y, c = threadIdx.x;
+    if (r < nb && c <= r) a[r][c] = A[(int64_t)(k0 + r) * M + k0 + c];
+    for (int p = 0; p < nb; ++p) {
+        __syncthreads();
+        if (r == p && c == p) {
+            T d = a[p][p];
+            if (!(d > T(0))) {
+                atomicOr(err, kErrSingular);
+                d = T(1);
+            }
+            a[p][p] = dsqrt<T>(d);
+        }
+        __syncthreads();
+        if (c == p && r > p && r < nb) a[r][p] /= a[p][p];
+        __syncthreads();
+        if (r > p && r < nb && c > p && c <= r) a[r][c] -= a[r][p] * a[c][p];
+    }
+    __syncthreads();
+    if (r < nb && c <= r) A[(int64_t)(k0 + r) * M + k0 + c] = a[r][c];
+}
+
+// Rows below the diagonal block: L_rk = A_rk L_kk^{-T}.  One warp per row
+// (lanes hold the 32 panel entries), 8 rows per CTA.
+template <typename T>
+__global__ void k_trsm_panel(T *A, int M, int k0, int nb) {
+    __shared__ T L[NB][NB + 1];
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int r = e / NB, c = e % NB;
+        L[r][c] = (r < nb && c <= r) ? A[(int64_t)(k0 + r) * M + k0 + c] : T(0);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int row = k0 + nb + blockIdx.x * (blockDim.x >> 5) + w;
+    if (row >= M) return;
+    T x = lane < nb ? A[(int64_t)row * M + k0 + lane] : T(0);
+    for (int c = 0; c < nb; ++c) {
+        // x_c = (a_c - sum_{p<c} x_p L_cp) / L_cc   (x_p already final for p < c)
+        T s = lane < c ? x * L[c][lane] : T(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == c) x = (x - s) / L[c][c];
+    }
+    if (lane < nb) A[(int64_t)row * M + k0 + lane] = x;
+}
+
+// Trailing update of the lower triangle: A_ij -= sum_p L_ip L_jp over the panel.
+template <typename T>
+__global__ void k_syrk(T *A, int M, int k0, int nb) {
+    const int k1 = k0 + nb;
+    const int t = (M - k1 + NB - 1) / NB;
+    // lower-triangular tile index
+    int idx = blockIdx.x, bi = 0;
+    while (idx > bi) { idx -= bi + 1; ++bi; }
+    const int bj = idx;
+    (void)t;
+    __shared__ T Li[NB][NB + 1], Lj[NB][NB + 1];
+    const int r = threadIdx.y, c = threadIdx.x;
+    const int gi = k1 + bi * NB + r, gj = k1 + bj * NB + r;
+    Li[r][c] = (gi < M && c < nb) ? A[(int64_t)gi * M + k0 + c] : T(0);
+    Lj[r][c] = (gj < M && c < nb) ? A[(int64_t)gj * M + k0 + c] : T(0);
+    __syncthreads();
+    const int row = k1 + bi * NB + r, colj = k1 + bj * NB + c;
+    if (row < M && colj < M && colj <= row) {
+        T s = 0;
+#pragma unroll 8
+        for (int p = 0; p < NB; ++p) s += Li[r][p] * Lj[c][p];
+        A[(int64_t)row * M + colj] -= s;
+    }
+}
+
+// Y = L^{-1}: right-looking forward substitution on the identity.
+// Step 1: rows k0..k0+nb of Y: X = L_kk^{-1} Y_k for columns c < k0+nb.
+template <typename T>
+__global__ void k_trsm_rows(const T *L, T *Y, int M, int k0, int nb) {
+    __shared__ T Lk[NB][NB + 1];
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int r = e / NB, c = e % NB;
+        Lk[r][c] = (r < nb && c <= r) ? L[(int64_t)(k0 + r) * M + k0 + c] : T(0);
+    }
+    __syncthreads();
+    const int cidx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cidx >= k0 + nb) return;
+    T x[NB];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) x[r] = r < nb ? Y[(int64_t)(k0 + r) * M + cidx] : T(0);
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+        if (r < nb) {
+            T s = x[r];
+#pragma unroll
+            for (int p = 0; p < r; ++p) s -= Lk[r][p] * x[p];
+            x[r] = s / Lk[r][r];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NB; ++r)
+        if (r < nb) Y[(int64_t)(k0 + r) * M + cidx] = x[r];
+}
+
+// Step 2: Y[i][c] -= sum_p L[i][k0+p] Y[k0+p][c] for i >= k0+nb, c < k0+nb.
+template <typename T>
+__global__ void k_trsm_update(const T *L, T *Y, int M, int k0, int nb) {
+    const int k1 = k0 + nb;
+    __shared__ T Ls[NB][NB + 1], Ys[NB][NB + 1];
+    const int r = threadIdx.y, c = threadIdx.x;
+    const int gi = k1 + blockIdx.y * NB + r;
+    const int gc = blockIdx.x * NB + c;
+    Ls[r][c] = (gi < M && c < nb) ? L[(int64_t)gi * M + k0 + c] : T(0);
+    Ys[r][c] = (r < nb && gc < k1) ? Y[(int64_t)(k0 + r) * M + gc] : T(0);
+    __syncthreads();
+    if (gi < M && gc < k1) {
+        T s = 0;
+#pragma unroll 8
+        for (int p = 0; p < NB; ++p) s += Ls[r][p] * Ys[p][c];
+        Y[(int64_t)gi * M + gc] -= s;
+    }
+}
+
+// X = Y^T Y restricted to k >= max(a, b) (Y lower triangular).
+template <typename T>
+__global__ void k_gram(const T *Y, T *X, int M) {
+    __shared__ T Ya[NB][NB + 1], Yb[NB][NB + 1];
+    const int r = threadIdx.y, c = threadIdx.x;
+    const int a0 = blockIdx.y * NB, b0 = blockIdx.x * NB;
+    const int ka = max(a0, b0);
+    T s = 0;
+    for (int k0 = (ka / NB) * NB; k0 < M; k0 += NB) {
+        const int gk = k0 + r;
+        Ya[r][c] = (gk < M && a0 + c < M) ? Y[(int64_t)gk * M + a0 + c] : T(0);
+        Yb[r][c] = (gk < M && b0 + c < M) ? Y[(int64_t)gk * M + b0 + c] : T(0);
+        __syncthreads();
+#pragma unroll 8
+        for (int p = 0; p < NB; ++p) s += Ya[p][r] * Yb[p][c];
+        __syncthreads();
+    }
+    if (a0 + r < M && b0 + c < M) X[(int64_t)(a0 + r) * M + b0 + c] = s;
+}
+
+template <typename T>
+__global__ void k_identity(T *Y, int M) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < (int64_t)M * M) Y[e] = (e / M == e % M) ? T(1) : T(0);
+}
+
+// FP32 equilibrated copy: S_ij = s_i A_ij s_j with s_i = 1/sqrt(A_ii).
+__global__ void k_equilibrate(const double *A, float *S, double *scale, int M) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)M * M) return;
+    const int r = (int)(e / M), c = (int)(e % M);
+    const double sr = 1.0 / sqrt(A[(int64_t)r * M + r]), sc = 1.0 / sqrt(A[(int64_t)c * M + c]);
+    S[e] = (float)(sr * A[e] * sc);
+    if (c == 0) scale[r] = sr;
+}
+
+__global__ void k_unscale(float *X, const double *scale, int M) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)M * M) return;
+    const int r = (int)(e / M), c = (int)(e % M);
+    X[e] = (float)((double)X[e] * scale[r] * scale[c]);
+}
+
+__global__ void k_check_diag(const double *A, int M, int *err) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < M && !(A[(int64_t)r * M + r] > 0.0)) atomicOr(err, kErrSingular);
+}
+
+// y = A x, one warp per row.
+template <typename T>
+__global__ void k_gemv(const T *__restrict__ A, int M, const T *__restrict__ x, T *__restrict__ y) {
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= M) return;
+    T s = 0;
+    const T *a = A + (int64_t)row * M;
+    for (int c = lane; c < M; c += 32) s += a[c] * x[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) y[row] = s;
+}
+
+// rc = d - A x (FP64), and its FP32 copy.
+__global__ void k_dense_residual(const double *__restrict__ A, int M, const double *__restrict__ d,
+                                 const double *__restrict__ x, double *__restrict__ rc, float *__restrict__ rc32) {
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= M) return;
+    double s = 0;
+    const double *a = A + (int64_t)row * M;
+    for (int c = lane; c < M; c += 32) s += a[c] * x[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        const double r = d[row] - s;
+        rc[row] = r;
+        rc32[row] = (float)r;
+    }
+}
+
+__global__ void k_axpy_f32(int M, const float *t, double *x, int assign) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M) x[i] = (assign ? 0.0 : x[i]) + (double)t[i];
+}
+
+__global__ void k_d2f(int M, const double *a, float *b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M) b[i] = (float)a[i];
+}
+
+template <typename T>
+void factor_inverse(T *A, T *Y, T *X, int M, int *err, cudaStream_t st) {
+    KernelScope ks_(st, sizeof(T) == 8 ? "coarse_factor_inverse" : "coarse_factor_inverse32", 0.0);
+    const dim3 tile(NB, NB);
+    for (int k0 = 0; k0 < M; k0 += NB) {
+        const int nb = std::min(NB, M - k0);
+        k_potrf_diag<T><<<1, tile, 0, st>>>(A, M, k0, nb, err);
+        const int rest = M - k0 - nb;
+        if (rest > 0) {
+            k_trsm_panel<T><<<(rest + 7) / 8, 256, 0, st>>>(A, M, k0, nb);
+            const int t = (rest + NB - 1) / NB;
+            k_syrk<T><<<t * (t + 1) / 2, tile, 0, st>>>(A, M, k0, nb);
+        }
+    }
+    MS_CHECK_LAUNCH();
+    const int64_t MM = (int64_t)M * M;
+    k_identity<T><<<(int)((MM + 255) / 256), 256, 0, st>>>(Y, M);
+    for (int k0 = 0; k0 < M; k0 += NB) {
+        const int nb = std::min(NB, M - k0);
+        const int k1 = k0 + nb;
+        k_trsm_rows<T><<<(k1 + 127) / 128, 128, 0, st>>>(A, Y, M, k0, nb);
+        if (M - k1 > 0) {
+            dim3 g((k1 + NB - 1) / NB, (M - k1 + NB - 1) / NB);
+            k_trsm_update<T><<<g, tile, 0, st>>>(A, Y, M, k0, nb);
+        }
+    }
+    dim3 g((M + NB - 1) / NB, (M + NB - 1) / NB);
+    k_gram<T><<<g, tile, 0, st>>>(Y, X, M);
+    MS_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+// FP64: work64 holds [L | Y] (2 M^2), inv64 the inverse.
+void dense_factor_inverse64(ms_coarse &c, int *err, cudaStream_t st) {
+    const int M = c.M;
+    const int64_t MM = (int64_t)M * M;
+    c.work64.alloc(2 * MM);
+    c.inv64.alloc(MM);
+    k_check_diag<<<(M + 255) / 256, 256, 0, st>>>(c.Ac.p, M, err);
+    MS_CUDA(cudaMemcpyAsync(c.work64.p, c.Ac.p, MM * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    factor_inverse<double>(c.work64.p, c.work64.p + MM, c.inv64.p, M, err, st);
+}
+
+// FP32: equilibrate, factor and invert in FP32, scale back.
+void dense_factor_inverse32(ms_coarse &c, int *err, cudaStream_t st) {
+    const int M = c.M;
+    const int64_t MM = (int64_t)M * M;
+    c.work32.alloc(2 * MM);
+    c.inv32.alloc(MM);
+    c.work64.alloc(M);   // scale vector
+    k_check_diag<<<(M + 255) / 256, 256, 0, st>>>(c.Ac.p, M, err);
+    k_equilibrate<<<(int)((MM + 255) / 256), 256, 0, st>>>(c.Ac.p, c.work32.p, c.work64.p, M);
+    MS_CHECK_LAUNCH();
+    factor_inverse<float>(c.work32.p, c.work32.p + MM, c.inv32.p, M, err, st);
+    k_unscale<<<(int)((MM + 255) / 256), 256, 0, st>>>(c.inv32.p, c.work64.p, M);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_gemv64(const double *A, int M, const double *x, double *y, cudaStream_t st) {
+    KernelScope ks_(st, "coarse_gemv", (double)M * M * 8 + (double)M * 16);
+    k_gemv<double><<<(M + 7) / 8, 256, 0, st>>>(A, M, x, y);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_gemv32(const float *A, int M, const float *x, float *y, cudaStream_t st) {
+    k_gemv<float><<<(M + 7) / 8, 256, 0, st>>>(A, M, x, y);
+    MS_CHECK_LAUNCH();
+}
+
+// x_c = A_c^{-1} d with the FP32 inverse and `steps` FP64 refinement steps:
+// x <- x + inv32 (d - A_c x).
+void launch_coarse_refine(const ms_coarse &c, const double *d, double *xc, double *rc, float *t32a, float *t32b,
+                          int steps, cudaStream_t st) {
+    const int M = c.M;
+    KernelScope ks_(st, "coarse_refine", (double)M * M * (4 + steps * 12));
+    k_d2f<<<(M + 255) / 256, 256, 0, st>>>(M, d, t32a);
+    k_gemv<float><<<(M + 7) / 8, 256, 0, st>>>(c.inv32.p, M, t32a, t32b);
+    k_axpy_f32<<<(M + 255) / 256, 256, 0, st>>>(M, t32b, xc, 1);
+    for (int s = 0; s < steps; ++s) {
+        k_dense_residual<<<(M + 7) / 8, 256, 0, st>>>(c.Ac.p, M, d, xc, rc, t32a);
+        k_gemv<float><<<(M + 7) / 8, 256, 0, st>>>(c.inv32.p, M, t32a, t32b);
+        k_axpy_f32<<<(M + 255) / 256, 256, 0, st>>>(M, t32b, xc, 0);
+    }
+    MS_CHECK_LAUNCH();
+}
+
+}  // namespace msgb

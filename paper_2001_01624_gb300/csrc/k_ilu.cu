@@ -1,0 +1,225 @@
+// ILU(0) smoother (Sec. 5.1 smoother S; Sec. 6.4 "Smooth": two triangular
+// solves).  Incomplete LU with zero fill-in on A's pattern in natural row
+// order, IKJ form:  for each row i and each k < i in row i (ascending):
+// a_ik /= u_kk, then a_ij -= a_ik u_kj for every j > k in both rows.
+//
+// GPU scheme: rows are visited in wavefront-level order (levels padded to
+// whole warps so a warp never holds two levels).  Each thread owns one row,
+// waits for the rows it depends on through per-row completion flags
+// (acquire/release), computes, and publishes its own flag.  CTAs take their
+// work in ticket order, so a CTA only ever waits on rows owned by CTAs that
+// started before it: the sweep cannot deadlock.  Every wait is bounded; a
+// wait that runs out raises an error bit and the sweep drains without
+// further waiting.  Flags hold a sweep counter, so no reset pass is needed.
+#include "ms_internal.h"
+
+namespace msgb {
+
+namespace {
+
+constexpr int kSweepThreads = 128;
+constexpr long long kSpinLimit = 1ll << 22;
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Returns the sweep target value; *vb receives this CTA's ticket.
+__device__ __forceinline__ int sweep_begin(int *sync, int *vb) {
+    __shared__ int s_vb, s_tgt;
+    if (threadIdx.x == 0) {
+        s_vb = atomicAdd(&sync[1], 1);
+        s_tgt = *((volatile int *)&sync[0]) + 1;
+    }
+    __syncthreads();
+    *vb = s_vb;
+    return s_tgt;
+}
+
+__device__ __forceinline__ void sweep_end(int *sync) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        int prev = atomicAdd(&sync[2], 1);
+        if (prev == (int)gridDim.x - 1) {
+            sync[1] = 0;
+            sync[2] = 0;
+            __threadfence();
+            atomicAdd(&sync[0], 1);
+        }
+    }
+}
+
+// Bounded wait for flags[k] == tgt.  Gives up (and stops all later waits)
+// once the error word is set.
+__device__ __forceinline__ bool wait_row(const int *flags, int k, int tgt, int *sync) {
+    long long spins = 0;
+    while (ld_acquire(&flags[k]) != tgt) {
+        if ((++spins & 1023) == 0) {
+            if (*((volatile int *)&sync[3]) != 0) return false;
+            if (spins > kSpinLimit) {
+                atomicOr(&sync[3], kErrTimeout);
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
+// IKJ ILU(0) of the pinned A (values in FP64).  lu gets L (lower slots) and
+// U (upper slots); udiag the U diagonal, dinv its reciprocal.
+__global__ void __launch_bounds__(kSweepThreads) k_ilu_factor(int n, int W, int ntot, const int *__restrict__ lperm,
+                                                              const int *__restrict__ col,
+                                                              const double *__restrict__ off,
+                                                              const double *__restrict__ diag, double *lu,
+                                                              double *udiag, double *dinv, int *flags, int *sync) {
+    int vb;
+    const int tgt = sweep_begin(sync, &vb);
+    const int t = vb * blockDim.x + threadIdx.x;
+    const int i = t < ntot ? lperm[t] : -1;
+    if (i >= 0) {
+        for (int w = 0; w < W; ++w) lu[(int64_t)w * n + i] = off[(int64_t)w * n + i];
+        double d = diag[i];
+        bool ok = true;
+        for (int w = 0; w < W && ok; ++w) {
+            const int k = col[(int64_t)w * n + i];
+            if (k >= i) break;     // lower slots come first (ascending); then upper slots / padding
+            ok = wait_row(flags, k, tgt, sync);
+            if (!ok) break;
+            const double ukk = __ldcg(&udiag[k]);
+            const double lik = lu[(int64_t)w * n + i] / ukk;
+            lu[(int64_t)w * n + i] = lik;
+            if (lik == 0.0) continue;
+            // a_ij -= l_ik u_kj for j > k present in row k (upper part of row k)
+            for (int v = 0; v < W; ++v) {
+                const int j = __ldcg(&col[(int64_t)v * n + k]);
+                if (j <= k) continue;
+                const double ukj = __ldcg(&lu[(int64_t)v * n + k]);
+                if (j == i) {
+                    d -= lik * ukj;
+                } else {
+                    for (int w2 = w + 1; w2 < W; ++w2)
+                        if (col[(int64_t)w2 * n + i] == j) { lu[(int64_t)w2 * n + i] -= lik * ukj; break; }
+                }
+            }
+        }
+        if (!(d != 0.0) || !(d == d)) atomicOr(&sync[3], kErrSingular);
+        udiag[i] = d;
+        dinv[i] = 1.0 / d;
+        st_release(&flags[i], tgt);
+    }
+    sweep_end(sync);
+}
+
+// Forward sweep L y = r (unit lower triangular).
+template <typename T, typename TR>
+__global__ void __launch_bounds__(kSweepThreads) k_ilu_fwd(int n, int W, int ntot, const int *__restrict__ lperm,
+                                                           const int *__restrict__ col, const T *__restrict__ lu,
+                                                           const TR *__restrict__ r, T *y, int *flags, int *sync) {
+    int vb;
+    const int tgt = sweep_begin(sync, &vb);
+    const int t = vb * blockDim.x + threadIdx.x;
+    const int i = t < ntot ? lperm[t] : -1;
+    if (i >= 0) {
+        T s = (T)r[i];
+        for (int w = 0; w < W; ++w) {
+            const int k = col[(int64_t)w * n + i];
+            if (k >= i) break;
+            if (!wait_row(flags, k, tgt, sync)) break;
+            s -= lu[(int64_t)w * n + i] * __ldcg(&y[k]);
+        }
+        y[i] = s;
+        st_release(&flags[i], tgt);
+    }
+    sweep_end(sync);
+}
+
+// Backward sweep U z = y, rows in reverse level order.
+template <typename T>
+__global__ void __launch_bounds__(kSweepThreads) k_ilu_bwd(int n, int W, int ntot, const int *__restrict__ lperm,
+                                                           const int *__restrict__ col, const T *__restrict__ lu,
+                                                           const T *__restrict__ dinv, const T *__restrict__ y, T *z,
+                                                           int *flags, int *sync) {
+    int vb;
+    const int tgt = sweep_begin(sync, &vb);
+    const int t = vb * blockDim.x + threadIdx.x;
+    const int i = t < ntot ? lperm[ntot - 1 - t] : -1;
+    if (i >= 0) {
+        T s = y[i];
+        for (int w = 0; w < W; ++w) {
+            const int k = col[(int64_t)w * n + i];
+            if (k <= i) continue;
+            if (!wait_row(flags, k, tgt, sync)) break;
+            s -= lu[(int64_t)w * n + i] * __ldcg(&z[k]);
+        }
+        z[i] = s * dinv[i];
+        st_release(&flags[i], tgt);
+    }
+    sweep_end(sync);
+}
+
+__global__ void k_copy_f32(const double *a, float *b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i < n; i += (int64_t)gridDim.x * blockDim.x) b[i] = (float)a[i];
+}
+
+inline int sweep_blocks(const ms_system &s) { return (s.ntot + kSweepThreads - 1) / kSweepThreads; }
+
+}  // namespace
+
+void launch_ilu_factor(ms_system &s, bool fp32, cudaStream_t st) {
+    const size_t en = std::max<size_t>((size_t)s.W * s.n, 1);
+    s.lu64.alloc(en);
+    s.dinv64.alloc(s.n);
+    s.w_y.alloc(s.n);   // U diagonal scratch
+    if (!s.ilu64_valid) {
+        KernelScope ks_(st, "ilu_factor", (double)s.n * (8 + 8 + 8 + 4) + (double)s.W * s.n * (4 + 8 + 8));
+        k_ilu_factor<<<sweep_blocks(s), kSweepThreads, 0, st>>>(s.n, s.W, s.ntot, s.lperm.p, s.col.p, s.off_p.p,
+                                                                 s.diag.p, s.lu64.p, s.w_y.p, s.dinv64.p, s.flags.p,
+                                                                 s.sync.p);
+        MS_CHECK_LAUNCH();
+    }
+    if (fp32) {
+        s.lu32.alloc(en);
+        s.dinv32.alloc(s.n);
+        k_copy_f32<<<1024, 256, 0, st>>>(s.lu64.p, s.lu32.p, (int64_t)en);
+        k_copy_f32<<<256, 256, 0, st>>>(s.dinv64.p, s.dinv32.p, s.n);
+        MS_CHECK_LAUNCH();
+    }
+}
+
+void launch_ilu_apply64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st) {
+    const double nl = (double)s.nnz_lower;
+    {
+    KernelScope ks_(st, "ilu_fwd", nl * (4 + 8) + (double)s.n * (8 + 8));
+    k_ilu_fwd<double, double><<<sweep_blocks(s), kSweepThreads, 0, st>>>(s.n, s.W, s.ntot, s.lperm.p, s.col.p,
+                                                                          s.lu64.p, r, y, s.flags.p, s.sync.p);
+    MS_CHECK_LAUNCH();
+    }
+    KernelScope ks_(st, "ilu_bwd", nl * (4 + 8) + (double)s.n * (8 + 8 + 8));
+    k_ilu_bwd<double><<<sweep_blocks(s), kSweepThreads, 0, st>>>(s.n, s.W, s.ntot, s.lperm.p, s.col.p, s.lu64.p,
+                                                                 s.dinv64.p, y, z, s.flags.p, s.sync.p);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_ilu_apply32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st) {
+    const double nl = (double)s.nnz_lower;
+    {
+    KernelScope ks_(st, "ilu_fwd32", nl * (4 + 4) + (double)s.n * (8 + 4));
+    k_ilu_fwd<float, double><<<sweep_blocks(s), kSweepThreads, 0, st>>>(s.n, s.W, s.ntot, s.lperm.p, s.col.p,
+                                                                         s.lu32.p, r, y, s.flags.p, s.sync.p);
+    MS_CHECK_LAUNCH();
+    }
+    KernelScope ks_(st, "ilu_bwd32", nl * (4 + 4) + (double)s.n * (4 + 4 + 4));
+    k_ilu_bwd<float><<<sweep_blocks(s), kSweepThreads, 0, st>>>(s.n, s.W, s.ntot, s.lperm.p, s.col.p, s.lu32.p,
+                                                                s.dinv32.p, y, z, s.flags.p, s.sync.p);
+    MS_CHECK_LAUNCH();
+}
+
+}  // namespace msgb

@@ -1,0 +1,391 @@
+// Row-parallel kernels on the ELL storage of A: two-point flux assembly
+// (Sec. 3), residuals / SpMV with deterministic norms, the Jacobi smoother,
+// restriction d = P^T r and prolongation x += P x_c (Eq. (11)).
+//
+// Layout: slot w of row i lives at [w*n + i], so a warp reading slot w of 32
+// consecutive rows issues one coalesced 128/256-byte access.  Every
+// reduction uses a fixed tree and a fixed block order, so results do not
+// depend on scheduling.
+#include <cfloat>
+
+#include "ms_internal.h"
+
+namespace msgb {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int blocks_for(int64_t n, int t = kThreads) { return (int)((n + t - 1) / t); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum of v over the CTA (result valid in thread 0); fixed order.
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double part[32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) part[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (wid == 0) {
+        s = (lane < (int)(blockDim.x >> 5)) ? part[lane] : 0.0;
+        s = warp_sum(s);
+    }
+    __syncthreads();
+    return s;
+}
+
+// Deterministic two-level reduction: each CTA stores its partial; the last
+// CTA to finish adds the partials in index order and writes sqrt(sum).
+__device__ __forceinline__ void finish_norm(double blk, double *red, unsigned int *cnt, double *out) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        red[blockIdx.x] = blk;
+        __threadfence();
+        unsigned int prev = atomicAdd(cnt, 1u);
+        last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(&red[b]);
+    s = block_sum(s);
+    if (threadIdx.x == 0) {
+        out[0] = sqrt(s);
+        *cnt = 0u;
+    }
+}
+
+// ------------------------------------------------------------- assembly
+__global__ void k_check_perm(const double *perm, int64_t count, int *flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        double k = perm[i];
+        if (!(k >= 0.0) || isinf(k)) atomicOr(flag, 1);
+    }
+}
+
+__global__ void k_face_trans(int nf, const int *__restrict__ ga, const int *__restrict__ gb,
+                             const int8_t *__restrict__ axis, const double *__restrict__ mult,
+                             const int *__restrict__ fa, const int *__restrict__ fb, const double *__restrict__ perm,
+                             const double *__restrict__ mob, const double *__restrict__ pprev, double dx, double dy,
+                             double dz, double *__restrict__ T) {
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    const int ax = axis[f];
+    const double h = ax == 0 ? dx : (ax == 1 ? dy : dz);
+    const double area = ax == 0 ? dy * dz : (ax == 1 ? dx * dz : dx * dy);
+    const double ta = perm[3 * (int64_t)ga[f] + ax] * area / (0.5 * h);
+    const double tb = perm[3 * (int64_t)gb[f] + ax] * area / (0.5 * h);
+    const double m = mult[f];
+    double t = (ta > 0.0 && tb > 0.0 && m > 0.0) ? m / (1.0 / ta + 1.0 / tb) : 0.0;
+    if (mob) {
+        const int a = fa[f], b = fb[f];
+        double lf;
+        if (pprev && pprev[a] != pprev[b]) lf = pprev[a] > pprev[b] ? mob[a] : mob[b];
+        else lf = 0.5 * (mob[a] + mob[b]);
+        t *= lf;
+    }
+    T[f] = t;
+}
+
+// A_ii = sum of incident T, A_ij = -T_ij (unpinned); pinned copy drops the
+// off-diagonals of row ref and column ref.
+__global__ void k_row_assemble(int n, int W, int ref, const int *__restrict__ rf_ptr, const int *__restrict__ rf_face,
+                               const uint8_t *__restrict__ rf_slot, const double *__restrict__ T,
+                               const int *__restrict__ col, double *__restrict__ off_u, double *__restrict__ off_p,
+                               double *__restrict__ diag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int w = 0; w < W; ++w) off_u[(int64_t)w * n + i] = 0.0;
+    double d = 0.0;
+    for (int p = rf_ptr[i]; p < rf_ptr[i + 1]; ++p) {
+        const double t = T[rf_face[p]];
+        d += t;
+        off_u[(int64_t)rf_slot[p] * n + i] -= t;
+    }
+    diag[i] = d;
+    for (int w = 0; w < W; ++w) {
+        const int64_t at = (int64_t)w * n + i;
+        const int c = col[at];
+        off_p[at] = (c != i && (i == ref || c == ref)) ? 0.0 : off_u[at];
+    }
+}
+
+// ------------------------------------------------------------- SpMV family
+__global__ void k_spmv(int n, int W, const int *__restrict__ col, const double *__restrict__ off,
+                       const double *__restrict__ diag, const double *__restrict__ x, double *__restrict__ y) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = diag[i] * x[i];
+    for (int w = 0; w < W; ++w) {
+        const int64_t at = (int64_t)w * n + i;
+        s += off[at] * x[col[at]];
+    }
+    y[i] = s;
+}
+
+// r = q - A x and ||r||_2
+__global__ void k_residual(int n, int W, const int *__restrict__ col, const double *__restrict__ off,
+                           const double *__restrict__ diag, const double *__restrict__ q,
+                           const double *__restrict__ x, double *__restrict__ r, double *red, unsigned int *cnt,
+                           double *norm_out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double ri = 0.0;
+    if (i < n) {
+        double s = diag[i] * x[i];
+        for (int w = 0; w < W; ++w) {
+            const int64_t at = (int64_t)w * n + i;
+            s += off[at] * x[col[at]];
+        }
+        ri = q[i] - s;
+        r[i] = ri;
+    }
+    if (norm_out) finish_norm(block_sum(ri * ri), red, cnt, norm_out);
+}
+
+// r -= A z ; x += z   (after a smoother correction z)
+__global__ void k_residual_update(int n, int W, const int *__restrict__ col, const double *__restrict__ off,
+                                  const double *__restrict__ diag, double *__restrict__ r, double *__restrict__ x,
+                                  const double *__restrict__ z) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double zi = z[i];
+    double s = diag[i] * zi;
+    for (int w = 0; w < W; ++w) {
+        const int64_t at = (int64_t)w * n + i;
+        s += off[at] * z[col[at]];
+    }
+    r[i] -= s;
+    x[i] += zi;
+}
+
+// mixed form: r32 = r - A32 z (single precision), x += z
+__global__ void k_residual_update32(int n, int W, const int *__restrict__ col, const float *__restrict__ off,
+                                    const float *__restrict__ diag, const double *__restrict__ r,
+                                    float *__restrict__ r32, double *__restrict__ x, const float *__restrict__ z) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float zi = z[i];
+    float s = diag[i] * zi;
+    for (int w = 0; w < W; ++w) {
+        const int64_t at = (int64_t)w * n + i;
+        s = fmaf(off[at], z[col[at]], s);
+    }
+    r32[i] = (float)r[i] - s;
+    x[i] += (double)zi;
+}
+
+__global__ void k_jacobi(int n, const double *__restrict__ r, const double *__restrict__ diag, double omega,
+                         double *__restrict__ z) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) z[i] = omega * r[i] / diag[i];
+}
+
+__global__ void k_jacobi32(int n, const double *__restrict__ r, const float *__restrict__ diag, float omega,
+                           float *__restrict__ z) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) z[i] = omega * (float)r[i] / diag[i];
+}
+
+__global__ void k_norm2(int n, const double *__restrict__ v, double *red, unsigned int *cnt, double *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double a = i < n ? v[i] : 0.0;
+    finish_norm(block_sum(a * a), red, cnt, out);
+}
+
+__global__ void k_sub(int n, const double *a, const double *b, double *c) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) c[i] = a[i] - b[i];
+}
+
+__global__ void k_set_zero_at(double *v, int idx) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) v[idx] = 0.0;
+}
+
+__global__ void k_widen(const float *a, double *b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i < n; i += (int64_t)gridDim.x * blockDim.x) b[i] = (double)a[i];
+}
+
+__global__ void k_to_float(const double *a, float *b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i < n; i += (int64_t)gridDim.x * blockDim.x) b[i] = (float)a[i];
+}
+
+// ------------------------------------------------------ restrict / prolong
+// d_j = sum over the support of block j of P_ij r_i (one CTA per block).
+template <typename TV, typename TR, typename TD>
+__global__ void k_restrict(const int *__restrict__ cptr, const int *__restrict__ ccell, const TV *__restrict__ cval,
+                           const TR *__restrict__ r, TD *__restrict__ d) {
+    const int j = blockIdx.x;
+    double s = 0.0;
+    for (int e = cptr[j] + threadIdx.x; e < cptr[j + 1]; e += blockDim.x)
+        s += (double)cval[e] * (double)r[ccell[e]];
+    s = block_sum(s);
+    if (threadIdx.x == 0) d[j] = (TD)s;
+}
+
+// single-precision accumulation variant for the mixed form
+__global__ void k_restrict_f32(const int *__restrict__ cptr, const int *__restrict__ ccell,
+                               const float *__restrict__ cval, const float *__restrict__ r, float *__restrict__ d) {
+    __shared__ float part[32];
+    const int j = blockIdx.x;
+    float s = 0.0f;
+    for (int e = cptr[j] + threadIdx.x; e < cptr[j + 1]; e += blockDim.x) s = fmaf(cval[e], r[ccell[e]], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) part[wid] = s;
+    __syncthreads();
+    if (wid == 0) {
+        s = lane < (int)(blockDim.x >> 5) ? part[lane] : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) d[j] = s;
+    }
+}
+
+// x_i += sum_s P_{i,s} x_c[block(s)]
+template <typename TV, typename TC>
+__global__ void k_prolong(int n, int B, const int *__restrict__ pid, const TV *__restrict__ pval,
+                          const TC *__restrict__ xc, double *__restrict__ x) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    TC s = 0;
+    for (int t = 0; t < B; ++t) {
+        const int64_t at = (int64_t)t * n + i;
+        const int j = pid[at];
+        if (j == kSlotPad) break;
+        s += (TC)pval[at] * xc[j];
+    }
+    x[i] += (double)s;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+void launch_check_perm(const double *perm, int64_t count, int *flag, cudaStream_t st) {
+    int blocks = (int)std::min<int64_t>((count + kThreads - 1) / kThreads, 4096);
+    k_check_perm<<<std::max(blocks, 1), kThreads, 0, st>>>(perm, count, flag);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_face_trans(ms_system &s, const double *perm, const double *mob, const double *pprev, cudaStream_t st) {
+    if (s.nf == 0) return;
+    KernelScope ks_(st, "face_trans", (double)s.nf * (4 + 4 + 1 + 8 + 16 + 8) + (mob ? (double)s.nf * 2 * (4 + 8 + (pprev ? 8 : 0)) : 0.0));
+    k_face_trans<<<blocks_for(s.nf), kThreads, 0, st>>>(s.nf, s.f_ga.p, s.f_gb.p, s.f_axis.p, s.f_mult.p, s.f_a.p,
+                                                         s.f_b.p, perm, mob, pprev, s.dx, s.dy, s.dz, s.f_T.p);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_row_assemble(ms_system &s, cudaStream_t st) {
+    KernelScope ks_(st, "row_assemble", (double)s.n * (4 + 8) + (double)s.nf * 2 * (4 + 1 + 8) + (double)s.W * s.n * (4 + 3 * 8));
+    k_row_assemble<<<blocks_for(s.n), kThreads, 0, st>>>(s.n, s.W, s.ref, s.rf_ptr.p, s.rf_face.p, s.rf_slot.p,
+                                                          s.f_T.p, s.col.p, s.off_u.p, s.off_p.p, s.diag.p);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_spmv(const ms_system &s, const double *x, double *y, cudaStream_t st) {
+    KernelScope ks_(st, "spmv", (double)s.n * (8 + 8 + 8) + (double)s.W * s.n * (4 + 8));
+    k_spmv<<<blocks_for(s.n), kThreads, 0, st>>>(s.n, s.W, s.col.p, s.off_p.p, s.diag.p, x, y);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_residual(const ms_system &s, const double *q, const double *x, double *r, double *red,
+                     unsigned int *cnt, double *norm_out, cudaStream_t st) {
+    KernelScope ks_(st, "residual", (double)s.n * (8 + 8 + 8 + 8) + (double)s.W * s.n * (4 + 8));
+    k_residual<<<blocks_for(s.n), kThreads, 0, st>>>(s.n, s.W, s.col.p, s.off_p.p, s.diag.p, q, x, r, red, cnt,
+                                                      norm_out);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_residual_update(const ms_system &s, double *r, double *x, const double *z, cudaStream_t st) {
+    KernelScope ks_(st, "residual_update", (double)s.n * (8 + 8 + 16 + 16) + (double)s.W * s.n * (4 + 8));
+    k_residual_update<<<blocks_for(s.n), kThreads, 0, st>>>(s.n, s.W, s.col.p, s.off_p.p, s.diag.p, r, x, z);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_residual_update32(const ms_system &s, const double *r, float *r32, double *x, const float *z,
+                              cudaStream_t st) {
+    KernelScope ks_(st, "residual_update32", (double)s.n * (4 + 4 + 8 + 4 + 16) + (double)s.W * s.n * (4 + 4));
+    k_residual_update32<<<blocks_for(s.n), kThreads, 0, st>>>(s.n, s.W, s.col.p, s.off_p32.p, s.diag32.p, r, r32,
+                                                               x, z);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_jacobi(const ms_system &s, const double *r, double *z, double omega, cudaStream_t st) {
+    KernelScope ks_(st, "jacobi", (double)s.n * 24);
+    k_jacobi<<<blocks_for(s.n), kThreads, 0, st>>>(s.n, r, s.diag.p, omega, z);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_jacobi32(const ms_system &s, const double *r, float *z, float omega, cudaStream_t st) {
+    KernelScope ks_(st, "jacobi32", (double)s.n * 16);
+    k_jacobi32<<<blocks_for(s.n), kThreads, 0, st>>>(s.n, r, s.diag32.p, omega, z);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_norm2(const double *v, int n, double *red, unsigned int *cnt, double *out, cudaStream_t st) {
+    KernelScope ks_(st, "norm2", (double)n * 8);
+    k_norm2<<<blocks_for(n), kThreads, 0, st>>>(n, v, red, cnt, out);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_sub(const double *a, const double *b, double *c, int n, cudaStream_t st) {
+    k_sub<<<blocks_for(n), kThreads, 0, st>>>(n, a, b, c);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_scatter_zero(double *v, int idx, cudaStream_t st) {
+    k_set_zero_at<<<1, 32, 0, st>>>(v, idx);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_to_float(const double *a, float *b, int64_t n, cudaStream_t st) {
+    if (n <= 0) return;
+    int blocks = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 8192);
+    k_to_float<<<blocks, kThreads, 0, st>>>(a, b, n);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_widen(const float *a, double *b, int64_t n, cudaStream_t st) {
+    if (n <= 0) return;
+    int blocks = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 8192);
+    k_widen<<<blocks, kThreads, 0, st>>>(a, b, n);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_narrow(const double *a, float *b, int64_t n, cudaStream_t st) { launch_to_float(a, b, n, st); }
+
+void launch_restrict(const ms_basis &b, const double *r, double *d, cudaStream_t st) {
+    KernelScope ks_(st, "restrict", (double)b.nnz * (4 + 8) + (double)b.M * (8 + 4));
+    k_restrict<double, double, double><<<b.M, kThreads, 0, st>>>(b.cptr.p, b.ccell.p, b.cval.p, r, d);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_restrict32(const ms_basis &b, const float *r, float *d, cudaStream_t st) {
+    KernelScope ks_(st, "restrict32", (double)b.nnz * (4 + 4) + (double)b.M * (4 + 4));
+    k_restrict_f32<<<b.M, kThreads, 0, st>>>(b.cptr.p, b.ccell.p, b.cval32.p, r, d);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_prolong(const ms_basis &b, int n, const double *xc, double *x, cudaStream_t st) {
+    KernelScope ks_(st, "prolong", (double)b.B * n * (4 + 8) + (double)b.M * 8 + (double)n * 16);
+    k_prolong<double, double><<<blocks_for(n), kThreads, 0, st>>>(n, b.B, b.pid.p, b.pval.p, xc, x);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_prolong32(const ms_basis &b, int n, const float *xc, double *x, cudaStream_t st) {
+    KernelScope ks_(st, "prolong32", (double)b.B * n * (4 + 4) + (double)b.M * 4 + (double)n * 16);
+    k_prolong<float, float><<<blocks_for(n), kThreads, 0, st>>>(n, b.B, b.pid.p, b.pval32.p, xc, x);
+    MS_CHECK_LAUNCH();
+}
+
+}  // namespace msgb

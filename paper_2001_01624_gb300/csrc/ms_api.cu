@@ -1,0 +1,757 @@
+// C ABI (include/ms.h): handle management and host orchestration of the
+// kernels.  Every numeric step of the method runs in this library's CUDA
+// kernels; the host only sequences launches, moves caller arrays, reads
+// convergence scalars and builds integer patterns (ms_analysis.cpp).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+
+#include "ms_internal.h"
+
+using namespace msgb;
+
+namespace {
+
+// Make the context's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) cudaGetLastError();   // later calls report it
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a caller array: the array itself if it is device memory,
+// otherwise a copy in `stage`.
+template <typename T>
+const T *device_in(const T *p, size_t count, DBuf<T> &stage, cudaStream_t st) {
+    if (!p) return nullptr;
+    if (is_device_ptr(p)) return p;
+    stage.alloc(std::max<size_t>(count, 1));
+    MS_CUDA(cudaMemcpyAsync(stage.p, p, count * sizeof(T), cudaMemcpyHostToDevice, st));
+    return stage.p;
+}
+
+template <typename T>
+void copy_out(T *dst, const T *src, size_t count, cudaStream_t st) {
+    MS_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(T), is_device_ptr(dst) ? cudaMemcpyDeviceToDevice
+                                                                           : cudaMemcpyDeviceToHost, st));
+}
+
+void sync(cudaStream_t st) { MS_CUDA(cudaStreamSynchronize(st)); }
+
+int read_error_word(ms_ctx *ctx, const int *dev_word) {
+    int *h = (int *)ctx->pinned.get(64);
+    MS_CUDA(cudaMemcpyAsync(h, dev_word, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    sync(ctx->stream);
+    return *h;
+}
+
+void check_sweep_errors(ms_ctx *ctx, ms_system *s) {
+    const int e = read_error_word(ctx, s->sync.p + 3);
+    if (e) {
+        MS_CUDA(cudaMemsetAsync(s->sync.p + 3, 0, sizeof(int), ctx->stream));
+        if (e & kErrTimeout) throw Error{MS_ERR_TIMEOUT, "a level-ordered sweep wait ran out"};
+        if (e & kErrSingular) throw Error{MS_ERR_INVALID_ARG, "ILU(0) met a zero pivot"};
+        throw Error{MS_ERR_CUDA, "device error word " + std::to_string(e)};
+    }
+}
+
+ms_status fail(ms_ctx *ctx, ms_status st, const std::string &what) {
+    if (ctx) ctx->err = what;
+    return st;
+}
+
+#define API_TRY try {
+#define API_CATCH(ctx)                                                         \
+    }                                                                          \
+    catch (const Error &e) { return fail((ctx), e.status, e.what); }           \
+    catch (const std::bad_alloc &) { return fail((ctx), MS_ERR_OOM, "host allocation failed"); } \
+    catch (...) { return fail((ctx), MS_ERR_CUDA, "unexpected exception"); }
+
+// ------------------------------------------------------------ internals
+void ensure_fp32_matrix(ms_system &s, cudaStream_t st) {
+    const size_t en = std::max<size_t>((size_t)s.W * s.n, 1);
+    s.off_p32.alloc(en);
+    s.off_u32.alloc(en);
+    s.diag32.alloc(s.n);
+    launch_to_float(s.off_p.p, s.off_p32.p, (int64_t)en, st);
+    launch_to_float(s.off_u.p, s.off_u32.p, (int64_t)en, st);
+    launch_to_float(s.diag.p, s.diag32.p, s.n, st);
+}
+
+void ensure_ilu(ms_ctx *ctx, ms_system &s, bool fp32) {
+    if (s.ilu64_valid && (!fp32 || s.ilu32_valid)) return;
+    launch_ilu_factor(s, fp32, ctx->stream);
+    check_sweep_errors(ctx, &s);
+    s.ilu64_valid = true;
+    if (fp32) s.ilu32_valid = true;
+}
+
+// Smooth a basis: reset from the indicator (reset) or continue; returns iterations.
+int smooth_basis(ms_ctx *ctx, ms_system &s, ms_basis &b, bool reset, double tol, int max_iter) {
+    cudaStream_t st = ctx->stream;
+    if (reset) launch_basis_init(b, s.n, st);
+    int it = 0;
+    double inc = 0.0;
+    if (b.rule != MS_SUPPORT_BLOCK) {
+        const bool fp32 = b.precision == MS_PREC_MIXED;
+        s.w_max.alloc(1);
+        unsigned long long *h = (unsigned long long *)ctx->pinned.get(64);
+        while (it < max_iter) {
+            MS_CUDA(cudaMemsetAsync(s.w_max.p, 0, sizeof(unsigned long long), st));
+            launch_msrsb_iter(s, b, fp32, s.w_max.p, st);
+            MS_CUDA(cudaMemcpyAsync(h, s.w_max.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+            sync(st);
+            ++it;
+            std::memcpy(&inc, h, sizeof(double));
+            if (!(inc == inc)) throw Error{MS_ERR_INVALID_ARG, "basis smoothing produced NaN"};
+            if (inc < tol) break;
+        }
+    }
+    b.iters = it;
+    b.last_inc = inc;
+    b.assembly_id = s.assembly_id;
+    launch_basis_columns(b, st);
+    return it;
+}
+
+ms_basis *create_basis(ms_ctx *ctx, ms_system &s, const std::vector<int> &part, int M, int rule, int precision,
+                       int bx, int by, int bz) {
+    std::vector<int> cptr, ccell, pid, csrc;
+    std::vector<unsigned char> home;
+    analyse_supports(s, part, M, rule, bx, by, bz, cptr, ccell);
+    int B = 0;
+    slot_layout(s, part, M, cptr, ccell, B, pid, csrc, home);
+    MS_REQUIRE((int64_t)B * s.n < ((int64_t)1 << 31), MS_ERR_INVALID_ARG, "basis slot layout too large");
+    std::unique_ptr<ms_basis> b(new ms_basis());
+    b->M = M;
+    b->B = B;
+    b->nnz = (int64_t)ccell.size();
+    b->rule = rule;
+    b->precision = precision;
+    b->h_part = part;
+    cudaStream_t st = ctx->stream;
+    b->part.upload(part, st);
+    b->pid.upload(pid, st);
+    b->is_home.upload(home, st);
+    b->cptr.upload(cptr, st);
+    b->ccell.upload(ccell, st);
+    b->csrc.upload(csrc, st);
+    const size_t slots = (size_t)B * s.n;
+    b->pval.alloc(slots);
+    b->cval.alloc(std::max<int64_t>(b->nnz, 1));
+    if (precision == MS_PREC_MIXED) {
+        b->pval32.alloc(slots);
+        b->pval32_tmp.alloc(slots);
+        b->cval32.alloc(std::max<int64_t>(b->nnz, 1));
+        MS_CUDA(cudaMemsetAsync(b->pval32_tmp.p, 0, slots * sizeof(float), st));
+    } else {
+        b->pval_tmp.alloc(slots);
+        MS_CUDA(cudaMemsetAsync(b->pval_tmp.p, 0, slots * sizeof(double), st));
+    }
+    return b.release();
+}
+
+void galerkin_values(ms_ctx *ctx, ms_system &s, const ms_basis &b, ms_coarse &c) {
+    cudaStream_t st = ctx->stream;
+    MS_REQUIRE(s.assembled, MS_ERR_STATE, "system not assembled");
+    s.w_i0.alloc(4);
+    int *h = (int *)ctx->pinned.get(64);
+    const int wap = launch_ap_count(s, b, s.w_i0.p, h, st);
+    c.WAP = std::max(wap, 1);
+    c.apid.alloc((size_t)c.WAP * s.n);
+    c.apval.alloc((size_t)c.WAP * s.n);
+    launch_ap_fill(s, b, c, st);
+    c.Ac.alloc((size_t)c.M * c.M);
+    launch_rap(s, b, c, st);
+    MS_CUDA(cudaMemsetAsync(s.w_i0.p, 0, sizeof(int), st));
+    if (c.precision == MS_PREC_MIXED) dense_factor_inverse32(c, s.w_i0.p, st);
+    else dense_factor_inverse64(c, s.w_i0.p, st);
+    const int err = read_error_word(ctx, s.w_i0.p);
+    if (err) throw Error{MS_ERR_COARSE_SINGULAR, "coarse Cholesky met a non-positive pivot"};
+    // the apid/apval scratch is only needed while forming A_c
+    c.apid.release();
+    c.apval.release();
+}
+
+ms_coarse *create_coarse(ms_ctx *ctx, ms_system &s, const ms_basis &b, int precision) {
+    std::unique_ptr<ms_coarse> c(new ms_coarse());
+    c->M = b.M;
+    c->precision = precision;
+    c->basis = &b;
+    galerkin_values(ctx, s, b, *c);
+    return c.release();
+}
+
+// Dynamic partition of a device dp into device part; returns block count.
+int partition_dynamic_dev(ms_ctx *ctx, ms_system &s, const double *dp, int n_bins, double eps, int *part) {
+    cudaStream_t st = ctx->stream;
+    const int nb = (s.n + 255) / 256;
+    s.w_i1.alloc(s.n);                    // classes, then labels
+    s.w_i2.alloc((size_t)s.n + nb + 2);   // scan scratch
+    s.w_max.alloc(4);
+    launch_dynamic_classes(s, dp, n_bins, eps, s.w_i1.p, s.w_max.p, st);
+    s.w_i0.alloc(std::max(s.n, 4));
+    launch_components(s, s.w_i1.p, s.w_i0.p, st);
+    int *h = (int *)ctx->pinned.get(64);
+    return launch_number_components(s, s.w_i0.p, part, s.w_i2.p, h, st);
+}
+
+ms_basis *adaptive_basis(ms_ctx *ctx, ms_system &s, const double *dp_dev, const ms_adapt_opts &o,
+                         int precision) {
+    MS_REQUIRE(o.n_bins > 0 && o.eps > 0, MS_ERR_INVALID_ARG, "adaptive options: n_bins > 0 and eps > 0 required");
+    DBuf<int> part_d;
+    part_d.alloc(s.n);
+    const int M = partition_dynamic_dev(ctx, s, dp_dev, o.n_bins, o.eps, part_d.p);
+    std::vector<int> part(s.n);
+    MS_CUDA(cudaMemcpyAsync(part.data(), part_d.p, s.n * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    sync(ctx->stream);
+    const int rule = o.smoothed ? MS_SUPPORT_HOP : MS_SUPPORT_BLOCK;
+    std::unique_ptr<ms_basis> b(create_basis(ctx, s, part, M, rule, precision, 0, 0, 0));
+    b->omega = o.omega > 0 ? o.omega : 2.0 / 3.0;
+    b->tol = o.tol > 0 ? o.tol : 1e-3;
+    b->max_iter = o.max_iter > 0 ? o.max_iter : 500;
+    smooth_basis(ctx, s, *b, true, b->tol, b->max_iter);
+    return b.release();
+}
+
+double read_norm(ms_ctx *ctx, const double *dev) {
+    double *h = (double *)ctx->pinned.get(64);
+    MS_CUDA(cudaMemcpyAsync(h, dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    sync(ctx->stream);
+    return *h;
+}
+
+}  // namespace
+
+// =================================================================== ABI
+extern "C" {
+
+int32_t ms_abi_version(void) { return MS_ABI_VERSION; }
+
+const char *ms_status_string(ms_status s) {
+    switch (s) {
+        case MS_OK: return "ok";
+        case MS_ERR_INVALID_ARG: return "invalid argument";
+        case MS_ERR_OOM: return "out of memory";
+        case MS_ERR_CUDA: return "CUDA error";
+        case MS_ERR_NOT_CONVERGED: return "not converged";
+        case MS_ERR_COARSE_SINGULAR: return "coarse system not positive definite";
+        case MS_ERR_TIMEOUT: return "device wait timed out";
+        case MS_ERR_STATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+const char *ms_last_error(const ms_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+ms_status ms_create(ms_ctx **out, int32_t device, void *stream) {
+    if (!out) return MS_ERR_INVALID_ARG;
+    *out = nullptr;
+    API_TRY
+    int ndev = 0;
+    MS_CUDA(cudaGetDeviceCount(&ndev));
+    MS_REQUIRE(device >= 0 && device < ndev, MS_ERR_INVALID_ARG, "no such CUDA device");
+    std::unique_ptr<ms_ctx> c(new ms_ctx());
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    DeviceGuard g(device);
+    MS_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
+    *out = c.release();
+    return MS_OK;
+    API_CATCH(nullptr)
+}
+
+ms_status ms_destroy(ms_ctx *ctx) {
+    delete ctx;
+    return MS_OK;
+}
+
+ms_status ms_set_stream(ms_ctx *ctx, void *stream) {
+    if (!ctx) return MS_ERR_INVALID_ARG;
+    ctx->stream = (cudaStream_t)stream;
+    return MS_OK;
+}
+
+ms_status ms_system_create(ms_ctx *ctx, const ms_grid *grid, int32_t ref_cell, ms_system **out) {
+    if (!ctx || !grid || !out) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    API_TRY
+    DeviceGuard g(ctx->device);
+    std::unique_ptr<ms_system> s(new ms_system());
+    s->device = ctx->device;
+    analyse_grid(*s, *grid);
+    MS_REQUIRE(ref_cell >= 0 && ref_cell < s->n, MS_ERR_INVALID_ARG, "reference cell out of range");
+    s->ref = ref_cell;
+    *out = s.release();
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_system_release(ms_system *sys) {
+    if (sys) {
+        DeviceGuard g(sys->device);
+        delete sys;
+    }
+    return MS_OK;
+}
+
+ms_status ms_system_get_info(const ms_system *s, ms_system_info *info) {
+    if (!s || !info) return MS_ERR_INVALID_ARG;
+    info->n = s->n;
+    info->n_faces = s->nf;
+    info->ell_width = s->W;
+    info->n_levels = s->n_levels;
+    info->ref_cell = s->ref;
+    return MS_OK;
+}
+
+ms_status ms_assemble_tpfa(ms_ctx *ctx, ms_system *s, const double *perm, const double *mobility,
+                           const double *p_prev) {
+    if (!ctx || !s || !perm) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    if (p_prev && !mobility) return fail(ctx, MS_ERR_INVALID_ARG, "p_prev given without mobility");
+    API_TRY
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const int64_t N = (int64_t)s->nx * s->ny * s->nz;
+    DBuf<double> stage_perm, stage_mob, stage_pp;
+    const double *kp = device_in(perm, (size_t)(3 * N), stage_perm, st);
+    const double *mob = device_in(mobility, (size_t)s->n, stage_mob, st);
+    const double *pp = device_in(p_prev, (size_t)s->n, stage_pp, st);
+    s->w_i0.alloc(4);
+    MS_CUDA(cudaMemsetAsync(s->w_i0.p, 0, sizeof(int), st));
+    launch_check_perm(kp, 3 * N, s->w_i0.p, st);
+    if (read_error_word(ctx, s->w_i0.p)) throw Error{MS_ERR_INVALID_ARG, "permeability negative, NaN or infinite"};
+    launch_face_trans(*s, kp, mob, pp, st);
+    launch_row_assemble(*s, st);
+    ensure_fp32_matrix(*s, st);
+    s->ilu64_valid = s->ilu32_valid = false;
+    s->assembled = true;
+    s->assembly_id++;
+    sync(st);
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_system_get_matrix(ms_ctx *ctx, const ms_system *s, int32_t pinned, int32_t *col, double *val,
+                               double *diag) {
+    if (!ctx || !s || !col || !val || !diag) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    API_TRY
+    DeviceGuard g(ctx->device);
+    MS_REQUIRE(s->assembled, MS_ERR_STATE, "system not assembled");
+    const size_t en = (size_t)s->W * s->n;
+    if (en) {
+        copy_out(col, s->col.p, en, ctx->stream);
+        copy_out(val, pinned ? s->off_p.p : s->off_u.p, en, ctx->stream);
+    }
+    copy_out(diag, s->diag.p, s->n, ctx->stream);
+    sync(ctx->stream);
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_spmv(ms_ctx *ctx, const ms_system *s, const double *x, double *y) {
+    if (!ctx || !s || !x || !y) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    API_TRY
+    DeviceGuard g(ctx->device);
+    MS_REQUIRE(s->assembled, MS_ERR_STATE, "system not assembled");
+    ms_system &m = const_cast<ms_system &>(*s);
+    const double *xd = device_in(x, s->n, m.w_q, ctx->stream);
+    m.w_r.alloc(s->n);
+    launch_spmv(*s, xd, m.w_r.p, ctx->stream);
+    copy_out(y, m.w_r.p, s->n, ctx->stream);
+    sync(ctx->stream);
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_ilu_apply(ms_ctx *ctx, ms_system *s, int32_t precision, const double *r, double *z) {
+    if (!ctx || !s || !r || !z) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    API_TRY
+    DeviceGuard g(ctx->device);
+    MS_REQUIRE(s->assembled, MS_ERR_STATE, "system not assembled");
+    cudaStream_t st = ctx->stream;
+    const bool fp32 = precision == MS_PREC_MIXED;
+    ensure_ilu(ctx, *s, fp32);
+    const double *rd = device_in(r, s->n, s->w_q, st);
+    s->w_z.alloc(s->n);
+    if (fp32) {
+        s->w_y32.alloc(s->n);
+        s->w_z32.alloc(s->n);
+        launch_ilu_apply32(*s, rd, s->w_y32.p, s->w_z32.p, st);
+        launch_widen(s->w_z32.p, s->w_z.p, s->n, st);
+    } else {
+        s->w_y.alloc(s->n);
+        launch_ilu_apply64(*s, rd, s->w_y.p, s->w_z.p, st);
+    }
+    check_sweep_errors(ctx, s);
+    copy_out(z, s->w_z.p, s->n, st);
+    sync(st);
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_partition_cartesian(ms_ctx *ctx, const ms_system *s, int32_t bx, int32_t by, int32_t bz,
+                                 int32_t *part, int32_t *n_blocks) {
+    if (!ctx || !s || !part || !n_blocks) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    API_TRY
+    std::vector<int> p;
+    *n_blocks = partition_cartesian(*s, bx, by, bz, p);
+    std::memcpy(part, p.data(), p.size() * sizeof(int));
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_partition_components(ms_ctx *ctx, const ms_system *sc, const int32_t *cls, int32_t *part,
+                                  int32_t *n_blocks) {
+    if (!ctx || !sc || !cls || !part || !n_blocks) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    API_TRY
+    DeviceGuard g(ctx->device);
+    ms_system &s = const_cast<ms_system &>(*sc);
+    cudaStream_t st = ctx->stream;
+    DBuf<int> stage;
+    const int *cd = device_in(cls, s.n, stage, st);
+    const int nb = (s.n + 255) / 256;
+    DBuf<int> label, out, scratch;
+    label.alloc(s.n);
+    out.alloc(s.n);
+    scratch.alloc((size_t)s.n + nb + 2);
+    launch_components(s, cd, label.p, st);
+    int *h = (int *)ctx->pinned.get(64);
+    *n_blocks = launch_number_components(s, label.p, out.p, scratch.p, h, st);
+    copy_out(part, out.p, s.n, st);
+    sync(st);
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_partition_dynamic(ms_ctx *ctx, const ms_system *sc, const double *dp, int32_t n_bins, double eps,
+                               int32_t *part, int32_t *n_blocks) {
+    if (!ctx || !sc || !dp || !part || !n_blocks) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    if (n_bins <= 0 || !(eps > 0)) return fail(ctx, MS_ERR_INVALID_ARG, "n_bins > 0 and eps > 0 required");
+    API_TRY
+    DeviceGuard g(ctx->device);
+    ms_system &s = const_cast<ms_system &>(*sc);
+    cudaStream_t st = ctx->stream;
+    DBuf<double> stage;
+    const double *dd = device_in(dp, s.n, stage, st);
+    DBuf<int> out;
+    out.alloc(s.n);
+    *n_blocks = partition_dynamic_dev(ctx, s, dd, n_bins, eps, out.p);
+    copy_out(part, out.p, s.n, st);
+    sync(st);
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_build_basis(ms_ctx *ctx, ms_system *s, const int32_t *partition, int32_t n_blocks,
+                         const ms_basis_opts *opts, ms_basis **out, int32_t *iters) {
+    if (!ctx || !s || !partition || !opts || !out) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    API_TRY
+    DeviceGuard g(ctx->device);
+    MS_REQUIRE(s->assembled, MS_ERR_STATE, "system not assembled");
+    MS_REQUIRE(n_blocks > 0 && n_blocks <= s->n, MS_ERR_INVALID_ARG, "n_blocks out of range");
+    MS_REQUIRE(opts->precision == MS_PREC_FP64 || opts->precision == MS_PREC_MIXED, MS_ERR_INVALID_ARG,
+               "unknown precision");
+    MS_REQUIRE(opts->support >= 0 && opts->support <= 2, MS_ERR_INVALID_ARG, "unknown support rule");
+    MS_REQUIRE(opts->support == MS_SUPPORT_BLOCK || (opts->omega > 0 && opts->omega < 2 && opts->max_iter >= 0),
+               MS_ERR_INVALID_ARG, "basis options out of range");
+    std::vector<int> part(partition, partition + s->n);
+    for (int v : part) MS_REQUIRE(v >= 0 && v < n_blocks, MS_ERR_INVALID_ARG, "partition id out of range");
+    std::unique_ptr<ms_basis> b(
+        create_basis(ctx, *s, part, n_blocks, opts->support, opts->precision, opts->bx, opts->by, opts->bz));
+    b->omega = opts->omega;
+    b->tol = opts->tol;
+    b->max_iter = opts->max_iter;
+    const int it = smooth_basis(ctx, *s, *b, true, b->tol, b->max_iter);
+    if (iters) *iters = it;
+    sync(ctx->stream);
+    *out = b.release();
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_basis_rebuild(ms_ctx *ctx, ms_system *s, ms_basis *b, int32_t *iters) {
+    if (!ctx || !s || !b) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    API_TRY
+    DeviceGuard g(ctx->device);
+    MS_REQUIRE(s->assembled, MS_ERR_STATE, "system not assembled");
+    const int it = smooth_basis(ctx, *s, *b, true, b->tol, b->max_iter);
+    if (iters) *iters = it;
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_basis_update(ms_ctx *ctx, ms_system *s, ms_basis *b, double tol, int32_t max_iter, int32_t *iters) {
+    if (!ctx || !s || !b || max_iter < 0) return fail(ctx, MS_ERR_INVALID_ARG, "bad argument");
+    API_TRY
+    DeviceGuard g(ctx->device);
+    MS_REQUIRE(s->assembled, MS_ERR_STATE, "system not assembled");
+    const int it = smooth_basis(ctx, *s, *b, false, tol, max_iter);
+    if (iters) *iters = it;
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_basis_release(ms_basis *b) {
+    delete b;
+    return MS_OK;
+}
+
+ms_status ms_basis_get_info(const ms_basis *b, ms_basis_info *info) {
+    if (!b || !info) return MS_ERR_INVALID_ARG;
+    info->M = b->M;
+    info->nnz = b->nnz;
+    info->max_overlap = b->B;
+    info->iters = b->iters;
+    info->last_increment = b->last_inc;
+    return MS_OK;
+}
+
+ms_status ms_basis_get(ms_ctx *ctx, const ms_basis *b, int32_t *cptr, int32_t *cells, double *val) {
+    if (!ctx || !b || !cptr || !cells || !val) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    API_TRY
+    DeviceGuard g(ctx->device);
+    copy_out(cptr, b->cptr.p, (size_t)b->M + 1, ctx->stream);
+    if (b->nnz) {
+        copy_out(cells, b->ccell.p, (size_t)b->nnz, ctx->stream);
+        copy_out(val, b->cval.p, (size_t)b->nnz, ctx->stream);
+    }
+    sync(ctx->stream);
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_add_adaptive_basis(ms_ctx *ctx, ms_system *s, const double *dp, const ms_adapt_opts *opts,
+                                ms_basis **out) {
+    if (!ctx || !s || !dp || !opts || !out) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    API_TRY
+    DeviceGuard g(ctx->device);
+    MS_REQUIRE(s->assembled, MS_ERR_STATE, "system not assembled");
+    DBuf<double> stage;
+    const double *dd = device_in(dp, s->n, stage, ctx->stream);
+    *out = adaptive_basis(ctx, *s, dd, *opts, MS_PREC_FP64);
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_galerkin(ms_ctx *ctx, ms_system *s, const ms_basis *b, int32_t precision, ms_coarse **out) {
+    if (!ctx || !s || !b || !out) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    API_TRY
+    DeviceGuard g(ctx->device);
+    MS_REQUIRE(precision == MS_PREC_FP64 || precision == MS_PREC_MIXED, MS_ERR_INVALID_ARG, "unknown precision");
+    MS_REQUIRE(precision == MS_PREC_FP64 || b->precision == MS_PREC_MIXED, MS_ERR_INVALID_ARG,
+               "a mixed-precision coarse operator needs a mixed-precision basis");
+    *out = create_coarse(ctx, *s, *b, precision);
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_coarse_refresh(ms_ctx *ctx, ms_system *s, ms_coarse *c) {
+    if (!ctx || !s || !c) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    API_TRY
+    DeviceGuard g(ctx->device);
+    galerkin_values(ctx, *s, *c->basis, *c);
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_coarse_release(ms_coarse *c) {
+    delete c;
+    return MS_OK;
+}
+
+ms_status ms_coarse_get(ms_ctx *ctx, const ms_coarse *c, double *Ac, int32_t *M) {
+    if (!ctx || !c) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    API_TRY
+    DeviceGuard g(ctx->device);
+    if (M) *M = c->M;
+    if (Ac) {
+        copy_out(Ac, c->Ac.p, (size_t)c->M * c->M, ctx->stream);
+        sync(ctx->stream);
+    }
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t n_stages, const double *q,
+                   double *p, const ms_solve_opts *opts, ms_solve_info *info) {
+    if (!ctx || !s || !q || !p || !opts) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    if (n_stages < 0 || (n_stages > 0 && !stages)) return fail(ctx, MS_ERR_INVALID_ARG, "bad stage list");
+    const auto t0 = std::chrono::steady_clock::now();
+    API_TRY
+    DeviceGuard g(ctx->device);
+    MS_REQUIRE(s->assembled, MS_ERR_STATE, "system not assembled");
+    MS_REQUIRE(opts->tol >= 0 && opts->max_iter >= 0, MS_ERR_INVALID_ARG, "tol and max_iter must be >= 0");
+    MS_REQUIRE(opts->smoother == MS_SMOOTHER_ILU0 || opts->smoother == MS_SMOOTHER_JACOBI, MS_ERR_INVALID_ARG,
+               "unknown smoother");
+    MS_REQUIRE(opts->precision == MS_PREC_FP64 || opts->precision == MS_PREC_MIXED, MS_ERR_INVALID_ARG,
+               "unknown precision");
+    MS_REQUIRE(opts->adapt_schedule >= 0 && opts->adapt_schedule <= 2, MS_ERR_INVALID_ARG, "unknown schedule");
+    const bool mixed = opts->precision == MS_PREC_MIXED;
+    for (int l = 0; l < n_stages; ++l) {
+        MS_REQUIRE(stages[l] && stages[l]->basis, MS_ERR_INVALID_ARG, "null stage");
+        MS_REQUIRE(!mixed || stages[l]->precision == MS_PREC_MIXED, MS_ERR_INVALID_ARG,
+                   "mixed solve needs mixed-precision coarse operators");
+    }
+    cudaStream_t st = ctx->stream;
+    const int n = s->n;
+    int Mmax = 1;
+    for (int l = 0; l < n_stages; ++l) Mmax = std::max(Mmax, stages[l]->M);
+
+    // workspace
+    s->w_x.alloc(n); s->w_r.alloc(n); s->w_z.alloc(n); s->w_y.alloc(n); s->w_xprev.alloc(n);
+    const int rblocks = (n + 255) / 256;
+    s->w_red.alloc(rblocks + 8);
+    s->w_cnt.alloc(4);
+    s->w_cnt.zero(st);
+    DBuf<double> norms;
+    norms.alloc(4);
+    bool any32 = mixed;
+    for (int l = 0; l < n_stages; ++l) any32 = any32 || stages[l]->precision == MS_PREC_MIXED;
+    if (mixed) { s->w_y32.alloc(n); s->w_z32.alloc(n); }
+    if (any32 || opts->adapt_schedule) s->w_r32.alloc(n);
+
+    // q (pinned: q[ref] = 0) and the initial guess
+    s->w_q.alloc(n);
+    MS_CUDA(cudaMemcpyAsync(s->w_q.p, q, n * sizeof(double),
+                            is_device_ptr(q) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    launch_scatter_zero(s->w_q.p, s->ref, st);
+    if (opts->use_x0) {
+        MS_CUDA(cudaMemcpyAsync(s->w_x.p, p, n * sizeof(double),
+                                is_device_ptr(p) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    } else {
+        s->w_x.zero(st);
+    }
+    if (opts->smoother == MS_SMOOTHER_ILU0) ensure_ilu(ctx, *s, mixed);
+
+    launch_norm2(s->w_q.p, n, s->w_red.p, s->w_cnt.p, norms.p, st);
+    launch_residual(*s, s->w_q.p, s->w_x.p, s->w_r.p, s->w_red.p, s->w_cnt.p, norms.p + 1, st);
+    double hn[2];
+    {
+        double *h = (double *)ctx->pinned.get(64);
+        MS_CUDA(cudaMemcpyAsync(h, norms.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        sync(st);
+        hn[0] = h[0]; hn[1] = h[1];
+    }
+    const double nq = hn[0];
+    double res = nq > 0 ? hn[1] / nq : 0.0;
+    if (info && info->history) info->history[0] = res;
+    if (nq == 0.0) s->w_x.zero(st);
+
+    // dynamic stage (owned by this call)
+    std::unique_ptr<ms_basis> dyn_basis;
+    std::unique_ptr<ms_coarse> dyn_coarse;
+    const double jw = opts->jacobi_omega > 0 ? opts->jacobi_omega : 2.0 / 3.0;
+
+    int it = 0;
+    while (res > opts->tol && it < opts->max_iter) {
+        if (opts->adapt_schedule) MS_CUDA(cudaMemcpyAsync(s->w_xprev.p, s->w_x.p, n * sizeof(double),
+                                                          cudaMemcpyDeviceToDevice, st));
+        const int total = n_stages + (dyn_coarse ? 1 : 0);
+        for (int l = 0; l < total; ++l) {
+            const ms_coarse &c = l < n_stages ? *stages[l] : *dyn_coarse;
+            const ms_basis &b = *c.basis;
+            // r holds q - A x here
+            if (mixed) {
+                if (opts->smoother == MS_SMOOTHER_ILU0) launch_ilu_apply32(*s, s->w_r.p, s->w_y32.p, s->w_z32.p, st);
+                else launch_jacobi32(*s, s->w_r.p, s->w_z32.p, (float)jw, st);
+                launch_residual_update32(*s, s->w_r.p, s->w_r32.p, s->w_x.p, s->w_z32.p, st);
+            } else {
+                if (opts->smoother == MS_SMOOTHER_ILU0) launch_ilu_apply64(*s, s->w_r.p, s->w_y.p, s->w_z.p, st);
+                else launch_jacobi(*s, s->w_r.p, s->w_z.p, jw, st);
+                launch_residual_update(*s, s->w_r.p, s->w_x.p, s->w_z.p, st);
+            }
+            const int M = c.M;
+            if (c.precision == MS_PREC_MIXED) {
+                s->w_d32.alloc(std::max(M, Mmax)); s->w_xc32.alloc(std::max(M, Mmax));
+                s->w_d.alloc(std::max(M, Mmax)); s->w_xc.alloc(std::max(M, Mmax)); s->w_rc.alloc(std::max(M, Mmax));
+                if (!mixed) {   // FP64 residual restricted with the FP32 basis copy
+                    launch_to_float(s->w_r.p, s->w_r32.p, n, st);
+                }
+                launch_restrict32(b, s->w_r32.p, s->w_d32.p, st);
+                // coarse solve: FP32 inverse with FP64 refinement against A_c
+                launch_widen(s->w_d32.p, s->w_d.p, M, st);
+                launch_coarse_refine(c, s->w_d.p, s->w_xc.p, s->w_rc.p, s->w_d32.p, s->w_xc32.p, 2, st);
+                launch_narrow(s->w_xc.p, s->w_xc32.p, M, st);
+                launch_prolong32(b, n, s->w_xc32.p, s->w_x.p, st);
+            } else {
+                s->w_d.alloc(std::max(M, Mmax)); s->w_xc.alloc(std::max(M, Mmax));
+                launch_restrict(b, s->w_r.p, s->w_d.p, st);
+                launch_gemv64(c.inv64.p, M, s->w_d.p, s->w_xc.p, st);
+                launch_prolong(b, n, s->w_xc.p, s->w_x.p, st);
+            }
+            const bool last = (l == total - 1);
+            launch_residual(*s, s->w_q.p, s->w_x.p, s->w_r.p, s->w_red.p, s->w_cnt.p, last ? norms.p + 1 : nullptr,
+                            st);
+        }
+        if (info && info->dyn_blocks) info->dyn_blocks[it] = dyn_coarse ? dyn_coarse->M : 0;
+        ++it;
+        res = read_norm(ctx, norms.p + 1) / nq;
+        if (!(res == res)) throw Error{MS_ERR_CUDA, "residual became NaN"};
+        if (info && info->history) info->history[it] = res;
+        if (opts->smoother == MS_SMOOTHER_ILU0) check_sweep_errors(ctx, s);
+        if (opts->adapt_schedule && res > opts->tol &&
+            (opts->adapt_schedule == 1 || (opts->adapt_schedule == 2 && it <= 2))) {
+            s->w_part.alloc(n);
+            launch_sub(s->w_x.p, s->w_xprev.p, s->w_part.p, n, st);
+            const int dprec = mixed ? MS_PREC_MIXED : MS_PREC_FP64;
+            dyn_coarse.reset();
+            dyn_basis.reset(adaptive_basis(ctx, *s, s->w_part.p, opts->adapt, dprec));
+            dyn_coarse.reset(create_coarse(ctx, *s, *dyn_basis, dprec));
+            Mmax = std::max(Mmax, dyn_basis->M);
+        }
+    }
+    copy_out(p, s->w_x.p, n, st);
+    sync(st);
+    const bool conv = res <= opts->tol;
+    if (info) {
+        info->iters = it;
+        info->converged = conv ? 1 : 0;
+        info->rel_residual = res;
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return conv ? MS_OK : fail(ctx, MS_ERR_NOT_CONVERGED, "iteration cap reached");
+    API_CATCH(ctx)
+}
+
+ms_status ms_profile_enable(int32_t on) {
+    profile_enable(on != 0);
+    return MS_OK;
+}
+
+ms_status ms_profile_reset(void) {
+    profile_reset();
+    return MS_OK;
+}
+
+ms_status ms_profile_read(ms_kernel_stat *out, int32_t capacity, int32_t *count, int64_t *total_launches) {
+    if (capacity < 0 || (capacity > 0 && !out)) return MS_ERR_INVALID_ARG;
+    const int k = profile_read(out, capacity, total_launches);
+    if (count) *count = k;
+    return MS_OK;
+}
+
+}  // extern "C"

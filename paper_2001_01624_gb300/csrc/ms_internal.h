@@ -1,0 +1,286 @@
+// Internal declarations of the GB300 multiscale pressure solver library.
+// Host orchestration (ms_api.cu), host analysis (ms_analysis.cpp) and the
+// kernel translation units share these structures.  Nothing here is part of
+// the public ABI (include/ms.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "ms.h"
+
+namespace msgb {
+
+// ----------------------------------------------------------------- errors
+struct Error {
+    ms_status status;
+    std::string what;
+};
+
+#define MS_CUDA(call)                                                                        \
+    do {                                                                                     \
+        cudaError_t e__ = (call);                                                            \
+        if (e__ != cudaSuccess)                                                              \
+            throw ::msgb::Error{e__ == cudaErrorMemoryAllocation ? MS_ERR_OOM : MS_ERR_CUDA, \
+                                std::string(#call) + ": " + cudaGetErrorString(e__)};        \
+    } while (0)
+
+#define MS_REQUIRE(cond, st, msg)                           \
+    do {                                                    \
+        if (!(cond)) throw ::msgb::Error{(st), (msg)};      \
+    } while (0)
+
+#define MS_CHECK_LAUNCH() MS_CUDA(cudaGetLastError())
+
+// ------------------------------------------------------------ device buffer
+template <typename T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    ~DBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    // Grow-only: keeps the buffer when it already holds `count` elements.
+    void alloc(size_t count) {
+        if (count <= n && p) return;
+        release();
+        if (count == 0) return;
+        MS_CUDA(cudaMalloc(&p, count * sizeof(T)));
+        n = count;
+    }
+    void upload(const std::vector<T> &h, cudaStream_t s) {
+        alloc(h.size());
+        if (!h.empty()) MS_CUDA(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    }
+    void zero(cudaStream_t s) {
+        if (n) MS_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), s));
+    }
+};
+
+// Pinned host scratch for small device->host reads (norms, flags).
+struct HostScratch {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ~HostScratch() {
+        if (p) cudaFreeHost(p);
+    }
+    void *get(size_t b) {
+        if (b > bytes) {
+            if (p) cudaFreeHost(p);
+            p = nullptr;
+            MS_CUDA(cudaMallocHost(&p, b));
+            bytes = b;
+        }
+        return p;
+    }
+};
+
+constexpr int kSlotPad = 0x7fffffff;   // padding block id in basis slot lists (sorts last)
+
+// Device-side synchronisation words of the level-ordered sweeps:
+// [0] sweep counter, [1] CTA ticket, [2] CTAs done, [3] error flags.
+constexpr int kSyncWords = 8;
+constexpr int kErrTimeout = 1;
+constexpr int kErrSingular = 2;
+constexpr int kErrNaN = 4;
+
+// Kernel tracing scope: counts the launch made inside it and, when tracing is
+// enabled, brackets it with CUDA events on its stream.
+class KernelScope {
+  public:
+    KernelScope(cudaStream_t st, const char *name, double bytes);
+    ~KernelScope();
+    KernelScope(const KernelScope &) = delete;
+    KernelScope &operator=(const KernelScope &) = delete;
+
+  private:
+    cudaStream_t st_;
+    const char *name_;
+    double bytes_;
+    cudaEvent_t a_ = nullptr;
+};
+void profile_enable(bool on);
+void profile_reset();
+int profile_read(ms_kernel_stat *out, int cap, int64_t *total);
+
+}  // namespace msgb
+
+// ------------------------------------------------------------------ handles
+struct ms_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    std::string err;
+    msgb::HostScratch pinned;
+};
+
+// Host-side analysis products of a grid (built once per grid).
+struct ms_system {
+    int device = 0;
+    int nx = 0, ny = 0, nz = 0;
+    double dx = 0, dy = 0, dz = 0;
+    int n = 0;       // active cells
+    int ref = 0;     // pinned reference cell
+    std::vector<int> cells;   // grid index of each active cell
+    std::vector<int> g2a;     // active index of each grid cell (-1 inactive)
+
+    // two-point connections
+    int nf = 0;
+    std::vector<int> h_fa, h_fb;          // active indices
+    msgb::DBuf<int> f_ga, f_gb;           // grid indices (permeability lookup)
+    msgb::DBuf<int> f_a, f_b;             // active indices
+    msgb::DBuf<int8_t> f_axis;
+    msgb::DBuf<double> f_mult;
+    msgb::DBuf<double> f_T;               // transmissibility with mobility
+    // row -> incident connections (for deterministic row assembly)
+    msgb::DBuf<int> rf_ptr, rf_face;
+    msgb::DBuf<uint8_t> rf_slot;
+
+    // ELL storage of A: slot w of row i at [w*n + i]; padding col = i, val = 0
+    int W = 0;
+    std::vector<int> h_col;
+    msgb::DBuf<int> col;
+    msgb::DBuf<double> off_u, off_p, diag;    // unpinned / pinned off-diagonals, diagonal
+    msgb::DBuf<float> off_p32, diag32;        // single-precision copies (mixed solve)
+    msgb::DBuf<float> off_u32;                // single-precision unpinned (mixed basis)
+
+    // natural-order wavefront levels, each padded to a multiple of 32 rows
+    int n_levels = 0;
+    int ntot = 0;
+    int64_t nnz_lower = 0;   // structural entries below / above the diagonal
+    msgb::DBuf<int> lperm;
+
+    // ILU(0) factors on A's pattern (L in lower slots, U in upper slots)
+    bool ilu64_valid = false, ilu32_valid = false;
+    msgb::DBuf<double> lu64, dinv64;
+    msgb::DBuf<float> lu32, dinv32;
+
+    // sweep synchronisation
+    msgb::DBuf<int> flags;
+    msgb::DBuf<int> sync;
+
+    bool assembled = false;
+    uint64_t assembly_id = 0;   // bumped by every assembly
+
+    // solve workspace (grown on demand)
+    msgb::DBuf<double> w_q, w_x, w_r, w_z, w_xprev, w_d, w_xc, w_rc, w_part;
+    msgb::DBuf<float> w_y32, w_z32, w_r32, w_d32, w_xc32;
+    msgb::DBuf<double> w_y;
+    msgb::DBuf<double> w_red;                 // reduction partials
+    msgb::DBuf<unsigned int> w_cnt;           // reduction counters
+    msgb::DBuf<unsigned long long> w_max;     // max reductions
+    msgb::DBuf<int> w_i0, w_i1, w_i2;         // integer scratch (partitions)
+};
+
+struct ms_basis {
+    int M = 0;
+    int B = 0;                  // slots per cell (max overlap)
+    int64_t nnz = 0;
+    int rule = 0;
+    int precision = 0;
+    double omega = 2.0 / 3.0, tol = 1e-3;
+    int max_iter = 500;
+    int iters = 0;
+    double last_inc = 0;
+    uint64_t assembly_id = 0;   // assembly the values were smoothed with
+    std::vector<int> h_part;
+    msgb::DBuf<int> part;       // block of each cell
+    // cell-major slots: [s*n + i], block ids ascending, padding kSlotPad
+    msgb::DBuf<int> pid;
+    msgb::DBuf<double> pval, pval_tmp;
+    msgb::DBuf<float> pval32, pval32_tmp;
+    // column view (CSC)
+    msgb::DBuf<int> cptr, ccell, csrc;
+    msgb::DBuf<double> cval;
+    msgb::DBuf<float> cval32;
+    msgb::DBuf<unsigned char> is_home;   // 1 where the slot's block is the cell's own block
+};
+
+struct ms_coarse {
+    int M = 0;
+    int precision = 0;
+    const ms_basis *basis = nullptr;
+    msgb::DBuf<double> Ac;       // M*M row-major, Galerkin operator
+    msgb::DBuf<double> inv64;    // M*M inverse (FP64)
+    msgb::DBuf<float> inv32;     // M*M inverse (FP32, mixed)
+    msgb::DBuf<double> work64;   // factor workspace
+    msgb::DBuf<float> work32;
+    // Galerkin scratch: cell-major (A P) lists
+    int WAP = 0;
+    msgb::DBuf<int> apid;
+    msgb::DBuf<double> apval;
+};
+
+namespace msgb {
+
+// ---------------------------------------------------------------- analysis
+void analyse_grid(ms_system &s, const ms_grid &g);
+int partition_cartesian(const ms_system &s, int bx, int by, int bz, std::vector<int> &part);
+// Support patterns for a partition; fills per-block sorted cell lists.
+void analyse_supports(const ms_system &s, const std::vector<int> &part, int M, int rule, int bx, int by, int bz,
+                      std::vector<int> &cptr, std::vector<int> &ccell);
+// Cell-major slot layout from the column view.
+void slot_layout(const ms_system &s, const std::vector<int> &part, int M, const std::vector<int> &cptr,
+                 const std::vector<int> &ccell, int &B, std::vector<int> &pid, std::vector<int> &csrc,
+                 std::vector<unsigned char> &is_home);
+
+// ------------------------------------------------------------------ kernels
+// assembly
+void launch_face_trans(ms_system &s, const double *perm, const double *mob, const double *pprev, cudaStream_t st);
+void launch_row_assemble(ms_system &s, cudaStream_t st);
+void launch_check_perm(const double *perm, int64_t count, int *flag, cudaStream_t st);
+// sparse
+void launch_spmv(const ms_system &s, const double *x, double *y, cudaStream_t st);
+void launch_residual(const ms_system &s, const double *q, const double *x, double *r, double *red,
+                     unsigned int *cnt, double *norm_out, cudaStream_t st);
+void launch_residual_update(const ms_system &s, double *r, double *x, const double *z, cudaStream_t st);
+void launch_residual_update32(const ms_system &s, const double *r, float *r32, double *x, const float *z,
+                              cudaStream_t st);
+void launch_jacobi(const ms_system &s, const double *r, double *z, double omega, cudaStream_t st);
+void launch_jacobi32(const ms_system &s, const double *r, float *z, float omega, cudaStream_t st);
+void launch_norm2(const double *v, int n, double *red, unsigned int *cnt, double *out, cudaStream_t st);
+void launch_sub(const double *a, const double *b, double *c, int n, cudaStream_t st);
+void launch_scatter_zero(double *v, int idx, cudaStream_t st);
+void launch_restrict(const ms_basis &b, const double *r, double *d, cudaStream_t st);
+void launch_restrict32(const ms_basis &b, const float *r, float *d, cudaStream_t st);
+void launch_prolong(const ms_basis &b, int n, const double *xc, double *x, cudaStream_t st);
+void launch_prolong32(const ms_basis &b, int n, const float *xc, double *x, cudaStream_t st);
+void launch_to_float(const double *a, float *b, int64_t n, cudaStream_t st);
+void launch_widen(const float *a, double *b, int64_t n, cudaStream_t st);
+void launch_narrow(const double *a, float *b, int64_t n, cudaStream_t st);
+// ILU(0)
+void launch_ilu_factor(ms_system &s, bool fp32, cudaStream_t st);
+void launch_ilu_apply64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st);
+void launch_ilu_apply32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st);
+// basis
+void launch_basis_init(ms_basis &b, int n, cudaStream_t st);
+void launch_msrsb_iter(const ms_system &s, ms_basis &b, bool fp32, unsigned long long *maxinc, cudaStream_t st);
+void launch_basis_columns(ms_basis &b, cudaStream_t st);
+// Galerkin
+int launch_ap_count(const ms_system &s, const ms_basis &b, int *cnt_max, int *host_pinned, cudaStream_t st);
+void launch_ap_fill(const ms_system &s, const ms_basis &b, ms_coarse &c, cudaStream_t st);
+void launch_rap(const ms_system &s, const ms_basis &b, ms_coarse &c, cudaStream_t st);
+// dense
+void dense_factor_inverse64(ms_coarse &c, int *err, cudaStream_t st);
+void dense_factor_inverse32(ms_coarse &c, int *err, cudaStream_t st);
+void launch_gemv64(const double *A, int M, const double *x, double *y, cudaStream_t st);
+void launch_gemv32(const float *A, int M, const float *x, float *y, cudaStream_t st);
+void launch_coarse_refine(const ms_coarse &c, const double *d, double *xc, double *rc, float *t32a, float *t32b,
+                          int steps, cudaStream_t st);
+// partitions
+void launch_components(const ms_system &s, const int *cls, int *label, cudaStream_t st);
+void launch_dynamic_classes(const ms_system &s, const double *dp, int n_bins, double eps, int *cls,
+                            unsigned long long *maxbuf, cudaStream_t st);
+int launch_number_components(const ms_system &s, int *label, int *part, int *scratch, int *host_pinned,
+                             cudaStream_t st);
+
+}  // namespace msgb

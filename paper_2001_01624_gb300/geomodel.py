@@ -161,8 +161,11 @@ def corner_sources(grid: Grid) -> np.ndarray:
     prd = np.array([(nx - 1) + nx * ((ny - 1) + ny * k) for k in range(nz)])
     inj = inj[act[inj]]
     prd = prd[act[prd]]
-    if len(inj) == 0 or len(prd) == 0:
-        raise ValueError("corner source columns are fully inactive")
+    if len(inj) == 0 or len(prd) == 0:      # fall back to the columns of the first / last active cell
+        cells = np.flatnonzero(act)
+        c0, c1 = cells[0], cells[-1]
+        inj = np.array([c for c in (c0 % (nx * ny) + nx * ny * k for k in range(nz)) if act[c]])
+        prd = np.array([c for c in (c1 % (nx * ny) + nx * ny * k for k in range(nz)) if act[c]])
     q[inj] = 1.0 / len(inj)
     q[prd] = -1.0 / len(prd)
     return q
@@ -296,6 +299,9 @@ def faulted(nx, ny, nz, seed=0, n_fault_x=3, n_fault_y=3, throw=2, inactive_pct=
     if inactive_pct > 0:
         s = gaussian_field((nz, ny, nx), corr, rng).ravel()
         act = s <= np.percentile(s, 100.0 - inactive_pct)
+        for kk in range(nz):                     # keep the source corner columns active
+            act[0 + nx * ny * kk] = True
+            act[(nx - 1) + nx * ((ny - 1) + ny * kk)] = True
     else:
         act = np.ones(grid.N, bool)
     act = _largest_component(grid, act)

@@ -1,0 +1,90 @@
+"""Full-size parity in the benchmark's launch configuration.
+
+* 2D 60x220 lognormal geomodel (13,200 cells): GPU and oracle solved in full.
+* 3D 60x220x85 geomodel (1,122,000 cells): the GPU pipeline as bench.py runs
+  it, against the stored full FP64 oracle run (tests/golden/oracle_c2_seed0.json,
+  written by tests/golden/make_oracle_c2.py): basis iterations equal,
+  Richardson cycles within +/-1, the first residuals to 1e-6 relative,
+  pressure at 4096 seeded sample cells to 1e-6 (FP64) / 1e-5 (mixed), and
+  the final residual checked independently with the oracle's matrix.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2001_01624_gb300 import geomodel as G
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "oracle_c2_seed0.json")
+
+
+@pytest.fixture(scope="module")
+def ms():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2001_01624_gb300 as pkg
+    return pkg
+
+
+def _pipeline(ms, gm, prec, dev):
+    stream = torch.cuda.Stream(dev)
+    ctx = ms.ms_create(0, stream)
+    s = ms.ms_system_create(ctx, gm.grid, 0)
+    perm = torch.from_numpy(gm.perm.ravel().copy()).to(dev)
+    ms.ms_assemble_tpfa(ctx, s, perm)
+    part, M = ms.ms_partition_cartesian(ctx, s, gm.block)
+    b, bit = ms.ms_build_basis(ctx, s, part, M, block=gm.block, precision=prec)
+    c = ms.ms_galerkin(ctx, s, b, prec)
+    q = torch.from_numpy(gm.q_active()).to(dev)
+    p = torch.zeros_like(q)
+    info = ms.ms_solve(ctx, s, [c], q, p, tol=1e-6, max_iter=5000, precision=prec)
+    torch.cuda.synchronize()
+    x = p.cpu().numpy()
+    ms.ms_coarse_release(c)
+    ms.ms_basis_release(b)
+    ms.ms_system_release(s)
+    ms.ms_destroy(ctx)
+    return x, bit, info
+
+
+def test_config1_full_size(ms):
+    gm = G.config1(0)
+    sysr, Ap, qp, B, Ac, L = O.setup_general(gm)
+    r = O.ms_solve(Ap, [(B, L)], qp, tol=1e-6, max_iter=5000)
+    x, bit, info = _pipeline(ms, gm, ms.MS_PREC_FP64, torch.device("cuda:0"))
+    assert bit == B.iters
+    assert info["converged"] and abs(info["iters"] - r.iters) <= 1
+    assert np.linalg.norm(x - r.x) <= 1e-6 * np.linalg.norm(r.x)
+    xm, _, im = _pipeline(ms, gm, ms.MS_PREC_MIXED, torch.device("cuda:0"))
+    assert im["converged"] and abs(im["iters"] - r.iters) <= 1, (im["iters"], r.iters)
+    assert np.linalg.norm(xm - r.x) <= 1e-5 * np.linalg.norm(r.x)
+
+
+@pytest.mark.skipif(not os.path.exists(GOLD), reason="stored oracle run missing")
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_config2_full_size_against_stored_oracle(ms, prec):
+    g = json.load(open(GOLD))
+    gm = G.config2(0)
+    P = ms.MS_PREC_FP64 if prec == "fp64" else ms.MS_PREC_MIXED
+    x, bit, info = _pipeline(ms, gm, P, torch.device("cuda:0"))
+    assert info["converged"]
+    idx = np.array(g["sample_cells"])
+    ps = np.array(g["p_sample"])
+    tol = 1e-6 if prec == "fp64" else 1e-5
+    assert np.linalg.norm(x[idx] - ps) <= tol * np.linalg.norm(ps)
+    assert abs(info["iters"] - g["cycles"]) <= 1, (info["iters"], g["cycles"])
+    if prec == "fp64":
+        assert bit == g["basis_iters"]
+        k = min(len(g["hist_first"]), len(info["history"]))
+        np.testing.assert_allclose(info["history"][:k], g["hist_first"][:k], rtol=1e-6)
+    # the final residual, recomputed with the oracle's own matrix
+    s = O.assemble_tpfa(gm.grid, gm.perm)
+    Ap, qp = O.pin(s.A, gm.q_active(), 0)
+    res = np.linalg.norm(qp - Ap.to_scipy() @ x) / np.linalg.norm(qp)
+    assert res <= 1e-6 * (1 + 1e-9)

@@ -1,0 +1,353 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Same seeded inputs on both sides.  Integer results (partitions, supports,
+iteration counts of the basis) must match exactly; floating-point results
+within the tolerances stated per test: assembly and SpMV to rounding
+(1e-13), ILU(0) and basis values to 1e-10 / 1e-12, Galerkin operators to
+1e-12 of their largest entry, FP64 solves to relative pressure error 1e-6
+with Richardson cycle counts within +/-1, mixed-precision solves to 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2001_01624_gb300 import geomodel as G
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ms():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2001_01624_gb300 as pkg
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def ctx(ms):
+    c = ms.ms_create(0, torch.cuda.current_stream())
+    yield c
+    ms.ms_destroy(c)
+
+
+CASES = {
+    "2d_12x8": lambda: G.lognormal_box(12, 8, 1, seed=1, block=(4, 4, 1)),
+    "3d_10x10x4": lambda: G.lognormal_box(10, 10, 4, seed=2, block=(5, 5, 2), kz_ratio=0.1),
+    "ragged_13x11x5": lambda: G.lognormal_box(13, 11, 5, seed=21, block=(4, 4, 2), kz_ratio=0.1),
+    "faulted_18x14x7": lambda: G.faulted(18, 14, 7, seed=5, n_fault_x=1, n_fault_y=1, block=(5, 4, 3)),
+}
+
+
+def _dense_ell(col, val, diag):
+    n = len(diag)
+    A = np.diag(diag).astype(float)
+    W = col.shape[0]
+    for w in range(W):
+        for i in range(n):
+            if col[w, i] != i:
+                A[i, col[w, i]] += val[w, i]
+    return A
+
+
+def _system(ms, ctx, gm):
+    s = ms.ms_system_create(ctx, gm.grid, 0)
+    ms.ms_assemble_tpfa(ctx, s, gm.perm.ravel())
+    return s
+
+
+# ------------------------------------------------------------------ assembly
+@pytest.mark.parametrize("case", list(CASES))
+def test_assembly_matches_oracle(ms, ctx, case):
+    gm = CASES[case]()
+    s = _system(ms, ctx, gm)
+    ref = O.assemble_tpfa(gm.grid, gm.perm)
+    Ap, _ = O.pin(ref.A, None, 0)
+    for pinned, R in ((False, ref.A), (True, Ap)):
+        col, val, diag = ms.ms_system_get_matrix(ctx, s, pinned)
+        A = _dense_ell(col, val, diag)
+        D = R.dense()
+        np.testing.assert_allclose(A, D, rtol=1e-13, atol=1e-13 * np.abs(D).max())
+    info = ms.ms_system_get_info(s)
+    assert info["n"] == ref.A.n and info["n_faces"] == len(ref.faces[0])
+    ms.ms_system_release(s)
+
+
+def test_assembly_with_upstream_mobility(ms, ctx):
+    gm = CASES["3d_10x10x4"]()
+    s = ms.ms_system_create(ctx, gm.grid, 0)
+    rng = np.random.default_rng(0)
+    lam = rng.uniform(0.2, 3.0, gm.grid.n_active())
+    pp = rng.standard_normal(gm.grid.n_active())
+    pp[::7] = pp[1::7][: len(pp[::7])] if False else pp[::7]
+    ms.ms_assemble_tpfa(ctx, s, gm.perm.ravel(), lam, pp)
+    ref = O.assemble_tpfa(gm.grid, gm.perm, lam=lam, p_prev=pp)
+    col, val, diag = ms.ms_system_get_matrix(ctx, s, False)
+    np.testing.assert_allclose(_dense_ell(col, val, diag), ref.A.dense(), rtol=1e-13,
+                               atol=1e-13 * np.abs(ref.A.val).max())
+    ms.ms_system_release(s)
+
+
+def test_invalid_permeability_rejected(ms, ctx):
+    gm = CASES["2d_12x8"]()
+    s = ms.ms_system_create(ctx, gm.grid, 0)
+    bad = gm.perm.copy()
+    bad[5, 1] = -1.0
+    with pytest.raises(ms.MsError) as e:
+        ms.ms_assemble_tpfa(ctx, s, bad.ravel())
+    assert e.value.status == ms.MS_ERR_INVALID_ARG
+    bad[5, 1] = np.nan
+    with pytest.raises(ms.MsError):
+        ms.ms_assemble_tpfa(ctx, s, bad.ravel())
+    ms.ms_system_release(s)
+
+
+# -------------------------------------------------------------- SpMV, ILU(0)
+@pytest.mark.parametrize("case", ["2d_12x8", "faulted_18x14x7"])
+def test_spmv_and_ilu_match_oracle(ms, ctx, case):
+    gm = CASES[case]()
+    s = _system(ms, ctx, gm)
+    ref = O.assemble_tpfa(gm.grid, gm.perm)
+    Ap, _ = O.pin(ref.A, None, 0)
+    x = np.random.default_rng(1).standard_normal(Ap.n)
+    y = np.empty(Ap.n)
+    ms.ms_spmv(ctx, s, x, y)
+    yr = Ap.to_scipy() @ x
+    np.testing.assert_allclose(y, yr, rtol=1e-12, atol=1e-13 * np.abs(yr).max())
+    z = np.empty(Ap.n)
+    ms.ms_ilu_apply(ctx, s, x, z)
+    zr = O.ilu0_apply(Ap, O.ilu0(Ap), x)
+    np.testing.assert_allclose(z, zr, rtol=1e-10, atol=1e-12 * np.abs(zr).max())
+    # FP32 factors: single-precision rounding only
+    ms.ms_ilu_apply(ctx, s, x, z, ms.MS_PREC_MIXED)
+    assert np.abs(z - zr).max() <= 1e-4 * np.abs(zr).max()
+    ms.ms_system_release(s)
+
+
+# ---------------------------------------------------------------- partitions
+@pytest.mark.parametrize("case", list(CASES))
+def test_partitions_match_oracle(ms, ctx, case):
+    gm = CASES[case]()
+    s = _system(ms, ctx, gm)
+    ref = O.assemble_tpfa(gm.grid, gm.perm)
+    part, M = ms.ms_partition_cartesian(ctx, s, gm.block)
+    rp, rM = O.partition_cartesian(gm.grid, ref.cells, gm.block)
+    assert M == rM and np.array_equal(part, rp)
+    fac = (np.log(gm.perm[ref.cells, 0]) > np.median(np.log(gm.perm[ref.cells, 0]))).astype(np.int32)
+    cls = part * 2 + fac
+    out = np.empty(ref.A.n, np.int32)
+    Ms = ms.ms_partition_components(ctx, s, cls, out)
+    sp, sM = O.components(ref.A, cls)
+    assert Ms == sM and np.array_equal(out, sp)
+    rng = np.random.default_rng(7)
+    dp = rng.standard_normal(ref.A.n) * 10.0 ** rng.uniform(-9, 0, ref.A.n)
+    dp[::11] = 0.0
+    Md = ms.ms_partition_dynamic(ctx, s, dp, out, 8, 1e-8)
+    dpart, dM = O.partition_dynamic(ref.A, dp, 8, 1e-8)
+    assert Md == dM and np.array_equal(out, dpart)
+    ms.ms_system_release(s)
+
+
+# -------------------------------------------------------------------- basis
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("rule", ["box", "hop"])
+def test_basis_matches_oracle(ms, ctx, case, rule):
+    gm = CASES[case]()
+    s = _system(ms, ctx, gm)
+    ref = O.assemble_tpfa(gm.grid, gm.perm)
+    part, M = ms.ms_partition_cartesian(ctx, s, gm.block)
+    sup = ms.MS_SUPPORT_BOX if rule == "box" else ms.MS_SUPPORT_HOP
+    b, it = ms.ms_build_basis(ctx, s, part, M, support=sup, block=gm.block)
+    if rule == "box":
+        sp, sc = O.support_box(gm.grid, ref.cells, ref.A, part, M, gm.block)
+    else:
+        sp, sc = O.support_hop(gm.grid, ref.cells, ref.A, part, M)
+    B = O.msrsb_basis(ref.A, part, M, sp, sc)
+    cptr, cells, val = ms.ms_basis_get(ctx, b)
+    assert np.array_equal(cptr, sp) and np.array_equal(cells, sc)
+    assert it == B.iters
+    np.testing.assert_allclose(val, B.pval, rtol=0, atol=1e-12)
+    # Galerkin coarse operator with the pinned A (Eq. (10))
+    c = ms.ms_galerkin(ctx, s, b)
+    Ac = ms.ms_coarse_get(ctx, c)
+    Ap, _ = O.pin(ref.A, None, 0)
+    Acr = O.galerkin(Ap, B)
+    np.testing.assert_allclose(Ac, Acr, rtol=0, atol=1e-12 * np.abs(Acr).max())
+    assert np.array_equal(Ac, Ac.T)
+    ms.ms_coarse_release(c)
+    ms.ms_basis_release(b)
+    ms.ms_system_release(s)
+
+
+def test_basis_update_continues_smoothing(ms, ctx):
+    gm = CASES["3d_10x10x4"]()
+    s = _system(ms, ctx, gm)
+    ref = O.assemble_tpfa(gm.grid, gm.perm)
+    part, M = ms.ms_partition_cartesian(ctx, s, gm.block)
+    b, it = ms.ms_build_basis(ctx, s, part, M, block=gm.block, tol=0.0, max_iter=3)
+    assert it == 3
+    assert ms.ms_basis_update(ctx, s, b, 0.0, 4) == 4
+    sp, sc = O.support_box(gm.grid, ref.cells, ref.A, part, M, gm.block)
+    B = O.msrsb_basis(ref.A, part, M, sp, sc, tol=0.0, max_iter=7)
+    _, _, val = ms.ms_basis_get(ctx, b)
+    np.testing.assert_allclose(val, B.pval, rtol=0, atol=1e-12)
+    assert ms.ms_basis_rebuild(ctx, s, b) == 3
+    ms.ms_basis_release(b)
+    ms.ms_system_release(s)
+
+
+# -------------------------------------------------------------------- solve
+def _oracle_general(gm, rule="box"):
+    return O.setup_general(gm, support=rule)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("smoother", ["ilu0", "jacobi"])
+def test_solve_matches_oracle(ms, ctx, case, smoother):
+    gm = CASES[case]()
+    s = _system(ms, ctx, gm)
+    part, M = ms.ms_partition_cartesian(ctx, s, gm.block)
+    b, _ = ms.ms_build_basis(ctx, s, part, M, block=gm.block)
+    c = ms.ms_galerkin(ctx, s, b)
+    q = gm.q_active()
+    p = np.zeros_like(q)
+    sm = ms.MS_SMOOTHER_ILU0 if smoother == "ilu0" else ms.MS_SMOOTHER_JACOBI
+    maxit = 3000 if smoother == "ilu0" else 20000
+    info = ms.ms_solve(ctx, s, [c], q, p, tol=1e-6, max_iter=maxit, smoother=sm)
+    sysr, Ap, qp, B, Ac, L = _oracle_general(gm)
+    r = O.ms_solve(Ap, [(B, L)], qp, tol=1e-6, max_iter=maxit, smoother=smoother)
+    assert info["converged"] == r.converged
+    assert abs(info["iters"] - r.iters) <= 1
+    assert np.linalg.norm(p - r.x) <= 1e-6 * np.linalg.norm(r.x)
+    k = min(len(info["history"]), len(r.hist), 6)
+    np.testing.assert_allclose(info["history"][:k], r.hist[:k], rtol=1e-8)
+    ms.ms_coarse_release(c)
+    ms.ms_basis_release(b)
+    ms.ms_system_release(s)
+
+
+def test_solve_device_pointers_and_initial_guess(ms, ctx):
+    gm = CASES["3d_10x10x4"]()
+    dev = torch.device("cuda:0")
+    s = ms.ms_system_create(ctx, gm.grid, 0)
+    ms.ms_assemble_tpfa(ctx, s, torch.from_numpy(gm.perm.ravel().copy()).to(dev))
+    part, M = ms.ms_partition_cartesian(ctx, s, gm.block)
+    b, _ = ms.ms_build_basis(ctx, s, part, M, block=gm.block)
+    c = ms.ms_galerkin(ctx, s, b)
+    q = torch.from_numpy(gm.q_active()).to(dev)
+    p = torch.zeros_like(q)
+    info = ms.ms_solve(ctx, s, [c], q, p, tol=1e-9, max_iter=3000)
+    torch.cuda.synchronize()
+    assert info["converged"]
+    sysr, Ap, qp, B, Ac, L = _oracle_general(gm)
+    x = np.linalg.solve(Ap.dense(), qp)
+    assert np.linalg.norm(p.cpu().numpy() - x) <= 1e-6 * np.linalg.norm(x)
+    # restarting from the converged iterate takes no cycle
+    info2 = ms.ms_solve(ctx, s, [c], q, p, tol=1e-6, max_iter=10, use_x0=True)
+    assert info2["iters"] == 0 and info2["converged"]
+    ms.ms_coarse_release(c)
+    ms.ms_basis_release(b)
+    ms.ms_system_release(s)
+
+
+def test_not_converged_returns_last_iterate(ms, ctx):
+    gm = CASES["2d_12x8"]()
+    s = _system(ms, ctx, gm)
+    part, M = ms.ms_partition_cartesian(ctx, s, gm.block)
+    b, _ = ms.ms_build_basis(ctx, s, part, M, block=gm.block)
+    c = ms.ms_galerkin(ctx, s, b)
+    q = gm.q_active()
+    p = np.zeros_like(q)
+    info = ms.ms_solve(ctx, s, [c], q, p, tol=1e-12, max_iter=3)
+    assert info["status"] == ms.MS_ERR_NOT_CONVERGED and info["iters"] == 3 and not info["converged"]
+    sysr, Ap, qp, B, Ac, L = _oracle_general(gm)
+    r = O.ms_solve(Ap, [(B, L)], qp, tol=1e-12, max_iter=3)
+    assert np.linalg.norm(p - r.x) <= 1e-9 * np.linalg.norm(r.x)
+    with pytest.raises(ms.MsError):
+        ms.ms_solve(ctx, s, [c], q, p, tol=1e-12, max_iter=3, raise_not_converged=True)
+    ms.ms_coarse_release(c)
+    ms.ms_basis_release(b)
+    ms.ms_system_release(s)
+
+
+def test_multistage_static_and_adaptive_match_oracle(ms, ctx):
+    gm = G.faulted(20, 16, 8, seed=9, n_fault_x=1, n_fault_y=1, block=(5, 4, 4))
+    s = _system(ms, ctx, gm)
+    ref = O.assemble_tpfa(gm.grid, gm.perm)
+    part, M = ms.ms_partition_cartesian(ctx, s, gm.block)
+    fac = gm.facies[ref.cells].astype(np.int32)
+    ps = np.empty(ref.A.n, np.int32)
+    Ms = ms.ms_partition_components(ctx, s, part * 2 + fac, ps)
+    b1, _ = ms.ms_build_basis(ctx, s, part, M, block=gm.block)
+    b2, _ = ms.ms_build_basis(ctx, s, ps, Ms, support=ms.MS_SUPPORT_HOP)
+    c1, c2 = ms.ms_galerkin(ctx, s, b1), ms.ms_galerkin(ctx, s, b2)
+    q = gm.q_active()
+    sysr, Ap, qp, B, Ac, L = _oracle_general(gm)
+    rps, rMs = O.partition_static(ref.A, B.part, gm.facies[ref.cells])
+    assert rMs == Ms and np.array_equal(rps, ps)
+    sp, sc = O.support_hop(gm.grid, ref.cells, ref.A, rps, rMs)
+    B2 = O.msrsb_basis(ref.A, rps, rMs, sp, sc)
+    L2 = O.cholesky(O.galerkin(Ap, B2))
+    for sched, smoothed in ((0, 0), (2, 0), (1, 0), (2, 1)):
+        p = np.zeros_like(q)
+        info = ms.ms_solve(ctx, s, [c1, c2], q, p, tol=1e-6, max_iter=3000, adapt_schedule=sched,
+                           adapt=dict(smoothed=smoothed))
+        ad = None if sched == 0 else dict(schedule=sched, smoothed=smoothed, grid=gm.grid, cells=ref.cells,
+                                          A_unpinned=ref.A)
+        r = O.ms_solve(Ap, [(B, L), (B2, L2)], qp, tol=1e-6, max_iter=3000, adapt=ad)
+        assert info["converged"] and r.converged
+        assert abs(info["iters"] - r.iters) <= 1, (sched, smoothed, info["iters"], r.iters)
+        assert np.linalg.norm(p - r.x) <= 1e-6 * np.linalg.norm(r.x)
+        if sched:
+            k = min(len(info["dyn_blocks"]), len(r.md_hist))
+            assert np.array_equal(info["dyn_blocks"][:k], r.md_hist[:k])
+    for h in (c1, c2):
+        ms.ms_coarse_release(h)
+    for h in (b1, b2):
+        ms.ms_basis_release(h)
+    ms.ms_system_release(s)
+
+
+def test_adaptive_basis_entry_point(ms, ctx):
+    gm = CASES["faulted_18x14x7"]()
+    s = _system(ms, ctx, gm)
+    ref = O.assemble_tpfa(gm.grid, gm.perm)
+    dp = np.random.default_rng(3).standard_normal(ref.A.n) * 10.0 ** np.linspace(-6, 0, ref.A.n)
+    for smoothed in (0, 1):
+        b = ms.ms_add_adaptive_basis(ctx, s, dp, smoothed=smoothed)
+        part, M = O.partition_dynamic(ref.A, dp)
+        if smoothed:
+            sp, sc = O.support_hop(gm.grid, ref.cells, ref.A, part, M)
+            B = O.msrsb_basis(ref.A, part, M, sp, sc)
+        else:
+            B = O.constant_basis(part, M)
+        cptr, cells, val = ms.ms_basis_get(ctx, b)
+        assert np.array_equal(cptr, B.sptr) and np.array_equal(cells, B.scells)
+        np.testing.assert_allclose(val, B.pval, rtol=0, atol=1e-12)
+        ms.ms_basis_release(b)
+    ms.ms_system_release(s)
+
+
+# -------------------------------------------------------------- mixed form
+@pytest.mark.parametrize("case", ["3d_10x10x4", "faulted_18x14x7"])
+def test_mixed_precision_solve(ms, ctx, case):
+    gm = CASES[case]()
+    s = _system(ms, ctx, gm)
+    part, M = ms.ms_partition_cartesian(ctx, s, gm.block)
+    b, _ = ms.ms_build_basis(ctx, s, part, M, block=gm.block, precision=ms.MS_PREC_MIXED)
+    c = ms.ms_galerkin(ctx, s, b, ms.MS_PREC_MIXED)
+    q = gm.q_active()
+    p = np.zeros_like(q)
+    info = ms.ms_solve(ctx, s, [c], q, p, tol=1e-6, max_iter=3000, precision=ms.MS_PREC_MIXED)
+    sysr, Ap, qp, B, Ac, L = _oracle_general(gm)
+    r = O.ms_solve(Ap, [(B, L)], qp, tol=1e-6, max_iter=3000)
+    assert info["converged"]
+    assert abs(info["iters"] - r.iters) <= 1, (info["iters"], r.iters)
+    assert np.linalg.norm(p - r.x) <= 1e-5 * np.linalg.norm(r.x)
+    ms.ms_coarse_release(c)
+    ms.ms_basis_release(b)
+    ms.ms_system_release(s)
