@@ -234,6 +234,31 @@ __global__ void k_axpy_f32(int M, const float *t, double *x, int assign) {
     if (i < M) x[i] = (assign ? 0.0 : x[i]) + (double)t[i];
 }
 
+// Test vector v_i = 1 + 0.5 sin(i) for the FP32 inverse quality check.
+__global__ void k_test_vector(int M, double *v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M) v[i] = 1.0 + 0.5 * sin((double)i);
+}
+
+// out[0] = ||x - v||^2, out[1] = ||v||^2 (one CTA, fixed order)
+__global__ void k_err_norms(int M, const float *x, const double *v, double *out) {
+    __shared__ double a[256], b[256];
+    double e = 0.0, w = 0.0;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const double d = (double)x[i] - v[i];
+        e += d * d;
+        w += v[i] * v[i];
+    }
+    a[threadIdx.x] = e;
+    b[threadIdx.x] = w;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) { a[threadIdx.x] += a[threadIdx.x + o]; b[threadIdx.x] += b[threadIdx.x + o]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { out[0] = a[0]; out[1] = b[0]; }
+}
+
 __global__ void k_d2f(int M, const double *a, float *b) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < M) b[i] = (float)a[i];
@@ -296,6 +321,24 @@ void dense_factor_inverse32(ms_coarse &c, int *err, cudaStream_t st) {
     factor_inverse<float>(c.work32.p, c.work32.p + MM, c.inv32.p, M, err, st);
     k_unscale<<<(int)((MM + 255) / 256), 256, 0, st>>>(c.inv32.p, c.work64.p, M);
     MS_CHECK_LAUNCH();
+}
+
+// Relative error ||inv32 (A_c v) - v|| / ||v||: bounds the contraction of
+// the FP64 refinement that uses the FP32 inverse.
+double coarse_inverse_check32(const ms_coarse &c, double *host2, cudaStream_t st) {
+    const int M = c.M;
+    DBuf<double> v, d, out;
+    DBuf<float> d32, x32;
+    v.alloc(M); d.alloc(M); out.alloc(2); d32.alloc(M); x32.alloc(M);
+    k_test_vector<<<(M + 255) / 256, 256, 0, st>>>(M, v.p);
+    k_gemv<double><<<(M + 7) / 8, 256, 0, st>>>(c.Ac.p, M, v.p, d.p);
+    k_d2f<<<(M + 255) / 256, 256, 0, st>>>(M, d.p, d32.p);
+    k_gemv<float><<<(M + 7) / 8, 256, 0, st>>>(c.inv32.p, M, d32.p, x32.p);
+    k_err_norms<<<1, 256, 0, st>>>(M, x32.p, v.p, out.p);
+    MS_CHECK_LAUNCH();
+    MS_CUDA(cudaMemcpyAsync(host2, out.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MS_CUDA(cudaStreamSynchronize(st));
+    return host2[1] > 0 ? std::sqrt(host2[0] / host2[1]) : 0.0;
 }
 
 void launch_gemv64(const double *A, int M, const double *x, double *y, cudaStream_t st) {

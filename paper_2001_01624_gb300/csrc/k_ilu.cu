@@ -18,7 +18,7 @@ namespace msgb {
 namespace {
 
 constexpr int kSweepThreads = 128;
-constexpr long long kSpinLimit = 1ll << 22;
+constexpr long long kSpinLimit = 1ll << 23;   // x up to 1 us back-off: several seconds at most
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
     int v;
@@ -58,10 +58,18 @@ __device__ __forceinline__ void sweep_end(int *sync) {
 
 // Bounded wait for flags[k] == tgt.  Gives up (and stops all later waits)
 // once the error word is set.
+// Polls back off exponentially (32 ns .. 1 us) so that rows waiting far
+// ahead of the wavefront do not saturate L2 with flag reads.
 __device__ __forceinline__ bool wait_row(const int *flags, int k, int tgt, int *sync) {
     long long spins = 0;
+    unsigned ns = 32;
     while (ld_acquire(&flags[k]) != tgt) {
-        if ((++spins & 1023) == 0) {
+        ++spins;
+        if (spins > 4) {
+            __nanosleep(ns);
+            ns = ns < 1024 ? 2 * ns : 1024;
+        }
+        if ((spins & 63) == 0) {
             if (*((volatile int *)&sync[3]) != 0) return false;
             if (spins > kSpinLimit) {
                 atomicOr(&sync[3], kErrTimeout);

@@ -12,6 +12,8 @@
 //  * slot_layout      -- cell-major slot lists of P (block ids ascending).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <limits>
@@ -166,6 +168,40 @@ void analyse_grid(ms_system &s, const ms_grid &g) {
         for (int i = 0; i < s.n; ++i) lperm[fill[lev[i]]++] = i;
     }
 
+    // structured grids: every cell active and every connection a Cartesian face
+    s.structured = (s.n == N) && (int)(conns.size()) > 0;
+    for (const Conn &c : conns)
+        if (!((c.gb - c.ga == 1 && c.axis == 0) || (c.gb - c.ga == nx && c.axis == 1) ||
+              (c.gb - c.ga == nx * ny && c.axis == 2))) { s.structured = false; break; }
+    std::vector<int8_t> dslot;
+    if (s.structured) {
+        dslot.assign((size_t)6 * s.n, (int8_t)-1);
+        for (const Conn &c : conns) {
+            dslot[(size_t)(3 + c.axis) * s.n + c.a] = (int8_t)slot_of(c.a, c.b);   // +axis neighbour of a
+            dslot[(size_t)c.axis * s.n + c.b] = (int8_t)slot_of(c.b, c.a);         // -axis neighbour of b
+        }
+        // CTA tile of x-pencils: TJ x TK pencils (j, k); tiles visited in
+        // order of increasing J + K (a topological order of the tile DAG)
+        int tk = std::min(nz, 8), tj;
+        if (nz == 1) tj = std::min(512, ((ny + 31) / 32) * 32);
+        else tj = std::min(256 / tk, ((ny + 31) / 32) * 32);
+        if (const char *e = std::getenv("MSGB_ILU_TILE")) {     // tuning override "TJxTK"
+            int a = 0, b = 0;
+            if (std::sscanf(e, "%dx%d", &a, &b) == 2 && a > 0 && b > 0 && a * b <= 512) { tj = a; tk = b; }
+        }
+        s.TJ = tj; s.TK = tk;
+        s.NJ = (ny + tj - 1) / tj; s.NK = (nz + tk - 1) / tk;
+        std::vector<int> order;
+        for (int d = 0; d <= s.NJ + s.NK - 2; ++d)
+            for (int J = 0; J < s.NJ; ++J) {
+                const int K = d - J;
+                if (K >= 0 && K < s.NK) order.push_back(J + s.NJ * K);
+            }
+        s.tile_order.upload(order, nullptr);
+        s.tile_prog.alloc(order.size());
+        s.tile_prog.zero(nullptr);
+    }
+
     // host copies + device upload
     s.h_fa.resize(s.nf);
     s.h_fb.resize(s.nf);
@@ -189,6 +225,7 @@ void analyse_grid(ms_system &s, const ms_grid &g) {
     s.rf_face.upload(rf_face, st);
     s.rf_slot.upload(rf_slot, st);
     s.col.upload(s.h_col, st);
+    if (s.structured) s.dir_slot.upload(dslot, st);
     s.lperm.upload(lperm, st);
     size_t en = std::max<size_t>((size_t)W * s.n, 1);
     s.off_u.alloc(en); s.off_p.alloc(en); s.diag.alloc(s.n);

@@ -100,10 +100,27 @@ void ensure_fp32_matrix(ms_system &s, cudaStream_t st) {
 
 void ensure_ilu(ms_ctx *ctx, ms_system &s, bool fp32) {
     if (s.ilu64_valid && (!fp32 || s.ilu32_valid)) return;
+    const bool had64 = s.ilu64_valid;
     launch_ilu_factor(s, fp32, ctx->stream);
     check_sweep_errors(ctx, &s);
+    if (s.structured) {
+        if (!had64) launch_ilu_extract_dirs(s, false, ctx->stream);
+        if (fp32) launch_ilu_extract_dirs(s, true, ctx->stream);
+    }
     s.ilu64_valid = true;
     if (fp32) s.ilu32_valid = true;
+}
+
+// z = (LU)^{-1} r: tiled wavefront sweeps on structured grids, level-ordered
+// sweeps otherwise.
+void ilu_apply64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st) {
+    if (s.structured) launch_ilu_tiled64(s, r, y, z, st);
+    else launch_ilu_apply64(s, r, y, z, st);
+}
+
+void ilu_apply32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st) {
+    if (s.structured) launch_ilu_tiled32(s, r, y, z, st);
+    else launch_ilu_apply32(s, r, y, z, st);
 }
 
 // Smooth a basis: reset from the indicator (reset) or continue; returns iterations.
@@ -184,8 +201,22 @@ void galerkin_values(ms_ctx *ctx, ms_system &s, const ms_basis &b, ms_coarse &c)
     c.Ac.alloc((size_t)c.M * c.M);
     launch_rap(s, b, c, st);
     MS_CUDA(cudaMemsetAsync(s.w_i0.p, 0, sizeof(int), st));
-    if (c.precision == MS_PREC_MIXED) dense_factor_inverse32(c, s.w_i0.p, st);
-    else dense_factor_inverse64(c, s.w_i0.p, st);
+    c.use64 = false;
+    c.inv32_error = 0.0;
+    if (c.precision == MS_PREC_MIXED) {
+        dense_factor_inverse32(c, s.w_i0.p, st);
+        const int err32 = read_error_word(ctx, s.w_i0.p);
+        c.inv32_error = err32 ? INFINITY : coarse_inverse_check32(c, (double *)ctx->pinned.get(64), st);
+        // the two FP64 refinement steps contract by about this error; fall back
+        // to an FP64 inverse when FP32 cannot resolve this coarse system
+        if (!(c.inv32_error <= 0.25)) {
+            c.use64 = true;
+            MS_CUDA(cudaMemsetAsync(s.w_i0.p, 0, sizeof(int), st));
+            dense_factor_inverse64(c, s.w_i0.p, st);
+        }
+    } else {
+        dense_factor_inverse64(c, s.w_i0.p, st);
+    }
     const int err = read_error_word(ctx, s.w_i0.p);
     if (err) throw Error{MS_ERR_COARSE_SINGULAR, "coarse Cholesky met a non-positive pivot"};
     // the apid/apval scratch is only needed while forming A_c
@@ -397,11 +428,11 @@ ms_status ms_ilu_apply(ms_ctx *ctx, ms_system *s, int32_t precision, const doubl
     if (fp32) {
         s->w_y32.alloc(s->n);
         s->w_z32.alloc(s->n);
-        launch_ilu_apply32(*s, rd, s->w_y32.p, s->w_z32.p, st);
+        ilu_apply32(*s, rd, s->w_y32.p, s->w_z32.p, st);
         launch_widen(s->w_z32.p, s->w_z.p, s->n, st);
     } else {
         s->w_y.alloc(s->n);
-        launch_ilu_apply64(*s, rd, s->w_y.p, s->w_z.p, st);
+        ilu_apply64(*s, rd, s->w_y.p, s->w_z.p, st);
     }
     check_sweep_errors(ctx, s);
     copy_out(z, s->w_z.p, s->n, st);
@@ -676,11 +707,11 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
             const ms_basis &b = *c.basis;
             // r holds q - A x here
             if (mixed) {
-                if (opts->smoother == MS_SMOOTHER_ILU0) launch_ilu_apply32(*s, s->w_r.p, s->w_y32.p, s->w_z32.p, st);
+                if (opts->smoother == MS_SMOOTHER_ILU0) ilu_apply32(*s, s->w_r.p, s->w_y32.p, s->w_z32.p, st);
                 else launch_jacobi32(*s, s->w_r.p, s->w_z32.p, (float)jw, st);
                 launch_residual_update32(*s, s->w_r.p, s->w_r32.p, s->w_x.p, s->w_z32.p, st);
             } else {
-                if (opts->smoother == MS_SMOOTHER_ILU0) launch_ilu_apply64(*s, s->w_r.p, s->w_y.p, s->w_z.p, st);
+                if (opts->smoother == MS_SMOOTHER_ILU0) ilu_apply64(*s, s->w_r.p, s->w_y.p, s->w_z.p, st);
                 else launch_jacobi(*s, s->w_r.p, s->w_z.p, jw, st);
                 launch_residual_update(*s, s->w_r.p, s->w_x.p, s->w_z.p, st);
             }
@@ -693,8 +724,10 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
                 }
                 launch_restrict32(b, s->w_r32.p, s->w_d32.p, st);
                 // coarse solve: FP32 inverse with FP64 refinement against A_c
+                // (or the FP64 inverse when FP32 cannot resolve this coarse system)
                 launch_widen(s->w_d32.p, s->w_d.p, M, st);
-                launch_coarse_refine(c, s->w_d.p, s->w_xc.p, s->w_rc.p, s->w_d32.p, s->w_xc32.p, 2, st);
+                if (c.use64) launch_gemv64(c.inv64.p, M, s->w_d.p, s->w_xc.p, st);
+                else launch_coarse_refine(c, s->w_d.p, s->w_xc.p, s->w_rc.p, s->w_d32.p, s->w_xc32.p, 2, st);
                 launch_narrow(s->w_xc.p, s->w_xc32.p, M, st);
                 launch_prolong32(b, n, s->w_xc32.p, s->w_x.p, st);
             } else {

