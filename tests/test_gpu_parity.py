@@ -83,7 +83,7 @@ def test_assembly_with_upstream_mobility(ms, ctx):
     rng = np.random.default_rng(0)
     lam = rng.uniform(0.2, 3.0, gm.grid.n_active())
     pp = rng.standard_normal(gm.grid.n_active())
-    pp[::7] = pp[1::7][: len(pp[::7])] if False else pp[::7]
+    pp[1::5] = pp[0::5][: len(pp[1::5])]     # equal pressures across some faces: mean mobility
     ms.ms_assemble_tpfa(ctx, s, gm.perm.ravel(), lam, pp)
     ref = O.assemble_tpfa(gm.grid, gm.perm, lam=lam, p_prev=pp)
     col, val, diag = ms.ms_system_get_matrix(ctx, s, False)
