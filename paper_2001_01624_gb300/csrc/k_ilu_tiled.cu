@@ -55,16 +55,41 @@ __device__ __forceinline__ unsigned long long wait_progress(const unsigned long 
     return v;
 }
 
+__device__ __forceinline__ int ld_acquire_cta_s32(const volatile int *p) {
+    int v;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared((const void *)p)) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_cta_s32(volatile int *p, int v) {
+    asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared((const void *)p)), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void compute_barrier(int nthreads) {
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// Warp-specialised tile sweep.  Warps 0..W-1 compute (TJ x TK pencils, one
+// named barrier per step among themselves); the last warp handles all
+// cross-CTA traffic: it publishes this tile's completed step count (release)
+// whenever the compute warps advance, and polls the producer tiles
+// (acquire), handing their progress to the compute warps through shared
+// memory.  Fence and poll latency thus delay the wavefront once per tile hop
+// instead of once per step.
 template <typename T, typename TR, bool BWD, int D>
-__global__ void __launch_bounds__(512) k_tile_sweep(int nx, int ny, int nz, int TJ, int TK, int NJ, int P,
-                                                     const int *__restrict__ order, const T *__restrict__ c0,
-                                                     const T *__restrict__ c1, const T *__restrict__ c2,
-                                                     const T *__restrict__ dinv, const TR *__restrict__ rhs,
-                                                     T *__restrict__ out, unsigned long long *prog, int *sync) {
+__global__ void __launch_bounds__(544, 1) k_tile_sweep(int nx, int ny, int nz, int TJ, int TK, int NJ,
+                                                    const int *__restrict__ order, const T *__restrict__ c0,
+                                                    const T *__restrict__ c1, const T *__restrict__ c2,
+                                                    const T *__restrict__ dinv, const TR *__restrict__ rhs,
+                                                    T *__restrict__ out, unsigned long long *prog, int *sync) {
     extern __shared__ unsigned char smraw[];
     T *sm = reinterpret_cast<T *>(smraw);   // [2][TK][TJ]
     __shared__ int s_vb, s_tgt;
+    __shared__ volatile int s_done, s_availJ, s_availK, s_abort;
     const int tid = threadIdx.x;
+    const int ncomp = TJ * TK;
+    const int ncw = (ncomp + 31) / 32;      // compute warps
+    const int steps = nx + TJ + TK - 2;
     if (tid == 0) {
         s_vb = atomicAdd(&sync[1], 1);
         s_tgt = *((volatile int *)&sync[0]) + 1;
@@ -73,86 +98,123 @@ __global__ void __launch_bounds__(512) k_tile_sweep(int nx, int ny, int nz, int 
     const int tile = order[s_vb];
     const unsigned long long epoch = (unsigned long long)(unsigned)s_tgt << 32;
     const int J = tile % NJ, K = tile / NJ;
-    const int tj = tid % TJ, tk = tid / TJ;
-    const int jm = J * TJ + tj, km = K * TK + tk;   // mirrored pencil coordinates
-    const bool live = jm < ny && km < nz;
-    const int j = BWD ? ny - 1 - jm : jm, k = BWD ? nz - 1 - km : km;
-    const long long plane = (long long)nx * ny;
-    const long long row0 = (long long)nx * j + plane * k;   // real index of x = 0
-    const long long oy = BWD ? -(long long)nx : (long long)nx;   // me - (j-dependency)
-    const long long oz = BWD ? -plane : plane;
-    const int steps = nx + TJ + TK - 2;
     const int prodJ = J > 0 ? (J - 1) + NJ * K : -1;
     const int prodK = K > 0 ? J + NJ * (K - 1) : -1;
-    const int tsz = TJ * TK;
-    const bool needJ = live && tj == 0 && jm > 0;   // reads the neighbouring tile (global)
-    const bool needK = live && tk == 0 && km > 0;
-
-    // register ring: inputs for mirrored x = xcur + d, d = 0..D-1
-    T rr[D], a0[D], a1[D], a2[D], di[D], vj[D], vk[D];
-    auto load = [&](int d, int xm) {
-        rr[d] = T(0); a0[d] = T(0); a1[d] = T(0); a2[d] = T(0); di[d] = T(1); vj[d] = T(0); vk[d] = T(0);
-        if (!live || xm < 0 || xm >= nx) return;
-        const long long c = row0 + (BWD ? nx - 1 - xm : xm);
-        rr[d] = (T)__ldg(&rhs[c]);
-        a0[d] = __ldg(&c0[c]);
-        a1[d] = __ldg(&c1[c]);
-        a2[d] = __ldg(&c2[c]);
-        if (BWD) di[d] = __ldg(&dinv[c]);
-        if (needJ) vj[d] = __ldcg(&out[c - oy]);
-        if (needK) vk[d] = __ldcg(&out[c - oz]);
-    };
-
-    unsigned long long haveJ = 0, haveK = 0;
-    auto ready = [&](int t) {   // producers must have completed the steps feeding loads at step t
-        if (tid == 0) {
-            if (prodJ >= 0) {
-                const unsigned long long need = epoch | (unsigned long long)min(t + D + TJ, steps);
-                if (haveJ < need) haveJ = wait_progress(&prog[prodJ], need, sync);
-            }
-            if (prodK >= 0) {
-                const unsigned long long need = epoch | (unsigned long long)min(t + D + TK, steps);
-                if (haveK < need) haveK = wait_progress(&prog[prodK], need, sync);
-            }
-        }
-    };
-
-    ready(0);
+    if (tid == 0) {
+        s_done = 0;
+        s_availJ = prodJ >= 0 ? 0 : steps;
+        s_availK = prodK >= 0 ? 0 : steps;
+        s_abort = 0;
+    }
     __syncthreads();
-    const int skew = tj + tk;
-#pragma unroll
-    for (int d = 0; d < D; ++d) load(d, d - skew);
-    T prev = T(0);
-    for (int t = 0; t < steps; ++t) {
-        if (t > 0) {
-            ready(t);
-            __syncthreads();   // progress of producers + shared values of step t-1
-        }
-        const int xm = t - skew;
-        if (live && xm >= 0 && xm < nx) {
-            const T *smp = sm + ((t - 1) & 1) * tsz;
-            const T nj = tj > 0 ? smp[tk * TJ + tj - 1] : vj[0];
-            const T nk = tk > 0 ? smp[(tk - 1) * TJ + tj] : vk[0];
-            T s = rr[0] - a0[0] * prev - a1[0] * nj - a2[0] * nk;
-            if (BWD) s *= di[0];
-            out[row0 + (BWD ? nx - 1 - xm : xm)] = s;
-            prev = s;
-            sm[(t & 1) * tsz + tk * TJ + tj] = s;
-        }
-        // shift the ring and fetch inputs D steps ahead
-#pragma unroll
-        for (int d = 0; d < D - 1; ++d) {
-            rr[d] = rr[d + 1]; a0[d] = a0[d + 1]; a1[d] = a1[d + 1]; a2[d] = a2[d + 1];
-            di[d] = di[d + 1]; vj[d] = vj[d + 1]; vk[d] = vk[d + 1];
-        }
-        load(D - 1, xm + D);
-        if ((t % P) == P - 1 || t == steps - 1) {
-            __syncthreads();
-            if (tid == 0) {
-                __threadfence();
-                st_release_u64(&prog[tile], epoch | (unsigned long long)(t + 1));
+
+    if (tid >= ncw * 32) {
+        // ------------------------------------------------ communication warp
+        if (tid == ncw * 32) {
+            int published = 0, aJ = s_availJ, aK = s_availK;
+            long long spins = 0;
+            while (true) {
+                const int d = ld_acquire_cta_s32(&s_done);
+                if (d > published) {
+                    st_release_u64(&prog[tile], epoch | (unsigned long long)d);
+                    published = d;
+                }
+                if (aJ < steps) {
+                    const unsigned long long v = ld_acquire_u64(&prog[prodJ]);
+                    const int a = v >= epoch ? (int)(v - epoch) : 0;
+                    if (a > aJ) { aJ = a; st_release_cta_s32(&s_availJ, aJ); }
+                }
+                if (aK < steps) {
+                    const unsigned long long v = ld_acquire_u64(&prog[prodK]);
+                    const int a = v >= epoch ? (int)(v - epoch) : 0;
+                    if (a > aK) { aK = a; st_release_cta_s32(&s_availK, aK); }
+                }
+                if (published == steps && aJ >= steps && aK >= steps) break;
+                if ((++spins & 1023) == 0) {
+                    if (*((volatile int *)&sync[3]) != 0 || spins > kSpinLimit) {
+                        if (spins > kSpinLimit) atomicOr(&sync[3], kErrTimeout);
+                        s_abort = 1;
+                        break;
+                    }
+                }
             }
         }
+    } else {
+        // ----------------------------------------------------- compute warps
+        const int tj = tid % TJ, tk = tid / TJ;
+        const int jm = J * TJ + tj, km = K * TK + tk;   // mirrored pencil coordinates
+        const bool live = tid < ncomp && jm < ny && km < nz;
+        const int j = BWD ? ny - 1 - jm : jm, k = BWD ? nz - 1 - km : km;
+        const long long plane = (long long)nx * ny;
+        const long long row0 = (long long)nx * j + plane * k;   // real index of x = 0
+        const long long oy = BWD ? -(long long)nx : (long long)nx;
+        const long long oz = BWD ? -plane : plane;
+        const bool needJ = live && tj == 0 && jm > 0;
+        const bool needK = live && tk == 0 && km > 0;
+        const int nct = ncw * 32;
+
+        T rr[D], a0[D], a1[D], a2[D], di[D], vj[D], vk[D];
+        auto load = [&](int d, int xm) {
+            rr[d] = T(0); a0[d] = T(0); a1[d] = T(0); a2[d] = T(0); di[d] = T(1); vj[d] = T(0); vk[d] = T(0);
+            if (!live || xm < 0 || xm >= nx) return;
+            const long long c = row0 + (BWD ? nx - 1 - xm : xm);
+            rr[d] = (T)__ldg(&rhs[c]);
+            a0[d] = __ldg(&c0[c]);
+            a1[d] = __ldg(&c1[c]);
+            a2[d] = __ldg(&c2[c]);
+            if (BWD) di[d] = __ldg(&dinv[c]);
+            if (needJ) vj[d] = __ldcg(&out[c - oy]);
+            if (needK) vk[d] = __ldcg(&out[c - oz]);
+        };
+        // loads at step t need producers to have completed min(t + D + TJ|TK, steps) steps
+        auto ready = [&](int t) {
+            if (tid == 0) {
+                const int nJ = min(t + D + TJ, steps), nK = min(t + D + TK, steps);
+                long long spins = 0;
+                while (s_availJ < nJ || s_availK < nK) {
+                    if (s_abort) break;
+                    if (++spins > (kSpinLimit << 4)) {
+                        atomicOr(&sync[3], kErrTimeout);
+                        s_abort = 1;
+                        break;
+                    }
+                }
+                __threadfence_block();
+            }
+        };
+
+        ready(0);
+        compute_barrier(nct);
+        const int skew = tj + tk;
+#pragma unroll
+        for (int d = 0; d < D; ++d) load(d, d - skew);
+        T prev = T(0);
+        for (int t = 0; t < steps; ++t) {
+            if (t > 0) {
+                ready(t);
+                compute_barrier(nct);   // step t-1 complete: values in shared memory, producers ready
+                if (tid == 0) st_release_cta_s32(&s_done, t);
+            }
+            const int xm = t - skew;
+            if (live && xm >= 0 && xm < nx) {
+                const T *smp = sm + ((t - 1) & 1) * ncomp;
+                const T nj = tj > 0 ? smp[tk * TJ + tj - 1] : vj[0];
+                const T nk = tk > 0 ? smp[(tk - 1) * TJ + tj] : vk[0];
+                T s = rr[0] - a0[0] * prev - a1[0] * nj - a2[0] * nk;
+                if (BWD) s *= di[0];
+                out[row0 + (BWD ? nx - 1 - xm : xm)] = s;
+                prev = s;
+                sm[(t & 1) * ncomp + tk * TJ + tj] = s;
+            }
+#pragma unroll
+            for (int d = 0; d < D - 1; ++d) {
+                rr[d] = rr[d + 1]; a0[d] = a0[d + 1]; a1[d] = a1[d + 1]; a2[d] = a2[d + 1];
+                di[d] = di[d + 1]; vj[d] = vj[d + 1]; vk[d] = vk[d + 1];
+            }
+            load(D - 1, xm + D);
+        }
+        compute_barrier(nct);
+        if (tid == 0) st_release_cta_s32(&s_done, steps);
     }
     __syncthreads();
     if (tid == 0) {
@@ -179,25 +241,26 @@ __global__ void k_extract_dirs(int n, const int8_t *__restrict__ dslot, const do
     }
 }
 
-constexpr int kRing = 4;
-constexpr int kPublish = 4;
+// register-ring depth: steps of load latency hidden (bounded by registers)
+template <typename T> constexpr int ring_depth() { return sizeof(T) == 8 ? 4 : 8; }
 
 template <typename T, typename TR>
 void tiled_apply(ms_system &s, const T *coef, const T *dinv, const TR *r, T *y, T *z, cudaStream_t st) {
     const int nT = s.NJ * s.NK;
-    const int threads = s.TJ * s.TK;
-    const size_t smem = 2 * (size_t)threads * sizeof(T);
+    const int ncomp = s.TJ * s.TK;
+    const int threads = 32 * ((ncomp + 31) / 32) + 32;   // compute warps + one communication warp
+    const size_t smem = 2 * (size_t)ncomp * sizeof(T);
     const int64_t n = s.n;
     const double nl = (double)s.nnz_lower;
     {
         KernelScope ks_(st, sizeof(T) == 8 ? "ilu_fwd" : "ilu_fwd32", nl * sizeof(T) + (double)n * (sizeof(TR) + sizeof(T)));
-        k_tile_sweep<T, TR, false, kRing><<<nT, threads, smem, st>>>(
-            s.nx, s.ny, s.nz, s.TJ, s.TK, s.NJ, kPublish, s.tile_order.p, coef, coef + n, coef + 2 * n, nullptr, r, y,
+        k_tile_sweep<T, TR, false, ring_depth<T>()><<<nT, threads, smem, st>>>(
+            s.nx, s.ny, s.nz, s.TJ, s.TK, s.NJ, s.tile_order.p, coef, coef + n, coef + 2 * n, nullptr, r, y,
             s.tile_prog.p, s.sync.p);
         MS_CHECK_LAUNCH();
     }
     KernelScope ks_(st, sizeof(T) == 8 ? "ilu_bwd" : "ilu_bwd32", nl * sizeof(T) + (double)n * 3 * sizeof(T));
-    k_tile_sweep<T, T, true, kRing><<<nT, threads, smem, st>>>(s.nx, s.ny, s.nz, s.TJ, s.TK, s.NJ, kPublish,
+    k_tile_sweep<T, T, true, ring_depth<T>()><<<nT, threads, smem, st>>>(s.nx, s.ny, s.nz, s.TJ, s.TK, s.NJ,
                                                               s.tile_order.p, coef + 3 * n, coef + 4 * n,
                                                               coef + 5 * n, dinv, y, z, s.tile_prog.p, s.sync.p);
     MS_CHECK_LAUNCH();
