@@ -104,6 +104,102 @@ __global__ void __launch_bounds__(kThreads) k_msrsb(int n, int W, int B, const i
     }
 }
 
+// Neighbour slot maps: one merge of sorted slot lists per (cell, A slot),
+// done once per basis pattern.
+__global__ void k_basis_maps(int n, int W, int B, const int *__restrict__ col, const int *__restrict__ pid,
+                             unsigned *__restrict__ nmap, unsigned char *__restrict__ nslots) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int ids[8];
+    int cnt = 0;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        ids[s] = s < B ? pid[(int64_t)s * n + i] : kSlotPad;
+        cnt += ids[s] != kSlotPad;
+    }
+    nslots[i] = (unsigned char)cnt;
+    for (int w = 0; w < W; ++w) {
+        const int k = col[(int64_t)w * n + i];
+        unsigned m = 0xffffffffu;
+        if (k != i) {
+            int t = 0;
+            int kid = pid[k];
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                if (ids[s] != kSlotPad) {
+                    while (kid < ids[s]) {
+                        ++t;
+                        kid = t < B ? pid[(int64_t)t * n + k] : kSlotPad;
+                    }
+                    if (kid == ids[s]) m = (m & ~(15u << (4 * s))) | ((unsigned)t << (4 * s));
+                }
+            }
+        }
+        nmap[(int64_t)w * n + i] = m;
+    }
+}
+
+// MsRSB iteration with precomputed neighbour slot maps (B <= 8): every
+// neighbour contribution is an independent load.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_msrsb_mapped(int n, int W, const int *__restrict__ col,
+                                                           const T *__restrict__ off, const T *__restrict__ diag,
+                                                           const unsigned *__restrict__ nmap,
+                                                           const unsigned char *__restrict__ nslots,
+                                                           const T *__restrict__ pin, T *__restrict__ pout, T omega,
+                                                           unsigned long long *maxinc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    T inc = 0;
+    if (i < n) {
+        const int cnt = nslots[i];
+        T v[8], acc[8];
+        const T d = diag[i];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            v[s] = s < cnt ? pin[(int64_t)s * n + i] : T(0);
+            acc[s] = d * v[s];
+        }
+        for (int w = 0; w < W; ++w) {
+            const int64_t at = (int64_t)w * n + i;
+            const int k = col[at];
+            if (k == i) continue;
+            const T a = off[at];
+            const unsigned m = nmap[at];
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                const unsigned t = (m >> (4 * s)) & 15u;
+                if (s < cnt && t != 15u) acc[s] += a * pin[(int64_t)t * n + k];
+            }
+        }
+        T sum = 0;
+#pragma unroll
+        for (int s = 0; s < 8; ++s)
+            if (s < cnt) {
+                acc[s] = v[s] - omega * acc[s] / d;
+                sum += acc[s];
+            }
+#pragma unroll
+        for (int s = 0; s < 8; ++s)
+            if (s < cnt) {
+                const T nv = acc[s] / sum;
+                const T dv = nv > v[s] ? nv - v[s] : v[s] - nv;
+                inc = dv > inc ? dv : inc;
+                pout[(int64_t)s * n + i] = nv;
+            }
+    }
+    __shared__ double wmax[kThreads / 32];
+    double m = (double)inc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mm = 0.0;
+        for (int q = 0; q < kThreads / 32; ++q) mm = fmax(mm, wmax[q]);
+        atomic_max_nonneg(maxinc, mm);
+    }
+}
+
 template <typename T>
 __global__ void k_gather_columns(int64_t nnz, const int *__restrict__ csrc, const T *__restrict__ pval,
                                  T *__restrict__ cval) {
@@ -212,6 +308,16 @@ __global__ void k_symmetrise(int M, double *Ac) {
 
 }  // namespace
 
+void launch_basis_maps(const ms_system &s, ms_basis &b, cudaStream_t st) {
+    b.has_map = false;
+    if (b.B > 8 || s.W == 0) return;
+    b.nmap.alloc((size_t)s.W * s.n);
+    b.nslots.alloc(s.n);
+    k_basis_maps<<<blocks_for(s.n), kThreads, 0, st>>>(s.n, s.W, b.B, s.col.p, b.pid.p, b.nmap.p, b.nslots.p);
+    MS_CHECK_LAUNCH();
+    b.has_map = true;
+}
+
 void launch_basis_init(ms_basis &b, int n, cudaStream_t st) {
     const int64_t total = (int64_t)b.B * n;
     const int blocks = (int)std::min<int64_t>((total + kThreads - 1) / kThreads, 8192);
@@ -222,9 +328,20 @@ void launch_basis_init(ms_basis &b, int n, cudaStream_t st) {
 }
 
 template <typename T>
-static void msrsb_dispatch(const ms_system &s, int B, const int *pid, const T *off, const T *diag, const T *pin,
-                           T *pout, T omega, unsigned long long *maxinc, cudaStream_t st) {
+static void msrsb_dispatch(const ms_system &s, const ms_basis &b, const int *pid, const T *off, const T *diag,
+                           const T *pin, T *pout, T omega, unsigned long long *maxinc, cudaStream_t st) {
     const int g = blocks_for(s.n);
+    const int B = b.B;
+    if (b.has_map) {
+        // A (unpinned) and the maps once, old slot values read once, new written
+        KernelScope ks_(st, sizeof(T) == 8 ? "msrsb" : "msrsb32",
+                        (double)s.n * (sizeof(T) + 1) + (double)s.W * s.n * (4 + sizeof(T) + 4) +
+                            (double)b.nnz * 2 * sizeof(T));
+        k_msrsb_mapped<T><<<g, kThreads, 0, st>>>(s.n, s.W, s.col.p, off, diag, b.nmap.p, b.nslots.p, pin, pout,
+                                                  omega, maxinc);
+        MS_CHECK_LAUNCH();
+        return;
+    }
     // A (unpinned) once, slot ids and old values once, new values written
     KernelScope ks_(st, sizeof(T) == 8 ? "msrsb" : "msrsb32",
                     (double)s.n * sizeof(T) + (double)s.W * s.n * (4 + sizeof(T)) +
@@ -240,11 +357,11 @@ static void msrsb_dispatch(const ms_system &s, int B, const int *pid, const T *o
 // One iteration; the new values end up in pval (buffers swapped).
 void launch_msrsb_iter(const ms_system &s, ms_basis &b, bool fp32, unsigned long long *maxinc, cudaStream_t st) {
     if (fp32) {
-        msrsb_dispatch<float>(s, b.B, b.pid.p, s.off_u32.p, s.diag32.p, b.pval32.p, b.pval32_tmp.p, (float)b.omega,
+        msrsb_dispatch<float>(s, b, b.pid.p, s.off_u32.p, s.diag32.p, b.pval32.p, b.pval32_tmp.p, (float)b.omega,
                               maxinc, st);
         std::swap(b.pval32.p, b.pval32_tmp.p);
     } else {
-        msrsb_dispatch<double>(s, b.B, b.pid.p, s.off_u.p, s.diag.p, b.pval.p, b.pval_tmp.p, b.omega, maxinc, st);
+        msrsb_dispatch<double>(s, b, b.pid.p, s.off_u.p, s.diag.p, b.pval.p, b.pval_tmp.p, b.omega, maxinc, st);
         std::swap(b.pval.p, b.pval_tmp.p);
     }
 }

@@ -60,10 +60,19 @@ __device__ __forceinline__ void sweep_end(int *sync) {
 // once the error word is set.
 // Polls back off exponentially (32 ns .. 1 us) so that rows waiting far
 // ahead of the wavefront do not saturate L2 with flag reads.
+__device__ __forceinline__ int ld_relaxed(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Relaxed polls with one acquire fence once the flag is seen (an acquire on
+// every poll would keep invalidating the SM's L1).
 __device__ __forceinline__ bool wait_row(const int *flags, int k, int tgt, int *sync) {
+    if (ld_acquire(&flags[k]) == tgt) return true;
     long long spins = 0;
     unsigned ns = 32;
-    while (ld_acquire(&flags[k]) != tgt) {
+    while (ld_relaxed(&flags[k]) != tgt) {
         ++spins;
         if (spins > 4) {
             __nanosleep(ns);
@@ -77,6 +86,7 @@ __device__ __forceinline__ bool wait_row(const int *flags, int k, int tgt, int *
             }
         }
     }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
     return true;
 }
 

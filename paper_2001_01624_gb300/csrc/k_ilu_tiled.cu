@@ -33,6 +33,14 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     return v;
 }
 
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 __device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -119,15 +127,20 @@ __global__ void __launch_bounds__(544, 1) k_tile_sweep(int nx, int ny, int nz, i
                     st_release_u64(&prog[tile], epoch | (unsigned long long)d);
                     published = d;
                 }
+                // relaxed polls; one acquire fence only when a producer advanced
+                int nJ = aJ, nK = aK;
                 if (aJ < steps) {
-                    const unsigned long long v = ld_acquire_u64(&prog[prodJ]);
-                    const int a = v >= epoch ? (int)(v - epoch) : 0;
-                    if (a > aJ) { aJ = a; st_release_cta_s32(&s_availJ, aJ); }
+                    const unsigned long long v = ld_relaxed_u64(&prog[prodJ]);
+                    nJ = v >= epoch ? (int)(v - epoch) : 0;
                 }
                 if (aK < steps) {
-                    const unsigned long long v = ld_acquire_u64(&prog[prodK]);
-                    const int a = v >= epoch ? (int)(v - epoch) : 0;
-                    if (a > aK) { aK = a; st_release_cta_s32(&s_availK, aK); }
+                    const unsigned long long v = ld_relaxed_u64(&prog[prodK]);
+                    nK = v >= epoch ? (int)(v - epoch) : 0;
+                }
+                if (nJ > aJ || nK > aK) {
+                    fence_acq_rel_gpu();
+                    if (nJ > aJ) { aJ = nJ; st_release_cta_s32(&s_availJ, aJ); }
+                    if (nK > aK) { aK = nK; st_release_cta_s32(&s_availK, aK); }
                 }
                 if (published == steps && aJ >= steps && aK >= steps) break;
                 if ((++spins & 1023) == 0) {

@@ -173,6 +173,7 @@ ms_basis *create_basis(ms_ctx *ctx, ms_system &s, const std::vector<int> &part, 
     b->cptr.upload(cptr, st);
     b->ccell.upload(ccell, st);
     b->csrc.upload(csrc, st);
+    if (rule != MS_SUPPORT_BLOCK) launch_basis_maps(s, *b, st);
     const size_t slots = (size_t)B * s.n;
     b->pval.alloc(slots);
     b->cval.alloc(std::max<int64_t>(b->nnz, 1));

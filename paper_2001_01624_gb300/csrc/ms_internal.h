@@ -214,6 +214,11 @@ struct ms_basis {
     msgb::DBuf<double> cval;
     msgb::DBuf<float> cval32;
     msgb::DBuf<unsigned char> is_home;   // 1 where the slot's block is the cell's own block
+    // neighbour slot maps (B <= 8): for slot w of A's row i, 4 bits per basis
+    // slot s of cell i = slot of the same block in neighbour col[w][i] (15: none)
+    bool has_map = false;
+    msgb::DBuf<unsigned> nmap;
+    msgb::DBuf<unsigned char> nslots;    // number of real slots of each cell
 };
 
 struct ms_coarse {
@@ -279,6 +284,7 @@ void launch_ilu_tiled64(ms_system &s, const double *r, double *y, double *z, cud
 void launch_ilu_tiled32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st);
 // basis
 void launch_basis_init(ms_basis &b, int n, cudaStream_t st);
+void launch_basis_maps(const ms_system &s, ms_basis &b, cudaStream_t st);
 void launch_msrsb_iter(const ms_system &s, ms_basis &b, bool fp32, unsigned long long *maxinc, cudaStream_t st);
 void launch_basis_columns(ms_basis &b, cudaStream_t st);
 // Galerkin
