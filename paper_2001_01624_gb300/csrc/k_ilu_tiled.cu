@@ -63,40 +63,73 @@ __device__ __forceinline__ unsigned long long wait_progress(const unsigned long 
     return v;
 }
 
-__device__ __forceinline__ int ld_acquire_cta_s32(const volatile int *p) {
-    int v;
-    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared((const void *)p)) : "memory");
-    return v;
+// Tagged words: a 32-bit payload with the 32-bit sweep counter in the high
+// half, written and read as single 64-bit accesses.  A consumer accepts a
+// word only when its tag is the current sweep's, so no flag, fence or
+// ordering between words is needed: each word validates itself.
+__device__ __forceinline__ void st_tag(unsigned long long *p, unsigned payload, unsigned tag) {
+    const unsigned long long w = ((unsigned long long)tag << 32) | payload;
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
 }
 
-__device__ __forceinline__ void st_release_cta_s32(volatile int *p, int v) {
-    asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared((const void *)p)), "r"(v) : "memory");
+__device__ __forceinline__ unsigned long long ld_tag(const unsigned long long *p) {
+    unsigned long long w;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+    return w;
 }
 
-__device__ __forceinline__ void compute_barrier(int nthreads) {
-    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
-}
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
-// Warp-specialised tile sweep.  Warps 0..W-1 compute (TJ x TK pencils, one
-// named barrier per step among themselves); the last warp handles all
-// cross-CTA traffic: it publishes this tile's completed step count (release)
-// whenever the compute warps advance, and polls the producer tiles
-// (acquire), handing their progress to the compute warps through shared
-// memory.  Fence and poll latency thus delay the wavefront once per tile hop
-// instead of once per step.
+// Values of type T exchanged as one (float) or two (double) tagged words.
+template <typename T>
+struct Tagged;
+template <>
+struct Tagged<float> {
+    static constexpr int W = 1;
+    __device__ static void put(unsigned long long *p, float v, unsigned tag) { st_tag(p, __float_as_uint(v), tag); }
+    __device__ static void fetch(const unsigned long long *p, unsigned long long *w) { w[0] = ld_tag(p); }
+    __device__ static bool ok(const unsigned long long *w, unsigned tag) { return (unsigned)(w[0] >> 32) == tag; }
+    __device__ static float value(const unsigned long long *w) { return __uint_as_float((unsigned)w[0]); }
+};
+template <>
+struct Tagged<double> {
+    static constexpr int W = 2;
+    __device__ static void put(unsigned long long *p, double v, unsigned tag) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        st_tag(p, (unsigned)b, tag);
+        st_tag(p + 1, (unsigned)(b >> 32), tag);
+    }
+    __device__ static void fetch(const unsigned long long *p, unsigned long long *w) {
+        w[0] = ld_tag(p);
+        w[1] = ld_tag(p + 1);
+    }
+    __device__ static bool ok(const unsigned long long *w, unsigned tag) {
+        return (unsigned)(w[0] >> 32) == tag && (unsigned)(w[1] >> 32) == tag;
+    }
+    __device__ static double value(const unsigned long long *w) {
+        return __longlong_as_double((long long)(((w[1] & 0xffffffffull) << 32) | (w[0] & 0xffffffffull)));
+    }
+};
+
+// Tile sweep.  Tiles exchange the values on their high j and k faces
+// through tagged face buffers: jface[tile][tk][x] feeds tile (J+1, K),
+// kface[tile][tj][x] feeds tile (J, K+1).  A consumer pencil prefetches the
+// face word D steps ahead and validates it when used, re-reading (bounded)
+// while it still carries an older sweep's tag.
 template <typename T, typename TR, bool BWD, int D>
-__global__ void __launch_bounds__(544, 1) k_tile_sweep(int nx, int ny, int nz, int TJ, int TK, int NJ,
+__global__ void __launch_bounds__(512) k_tile_sweep(int nx, int ny, int nz, int TJ, int TK, int NJ, int NK,
                                                     const int *__restrict__ order, const T *__restrict__ c0,
                                                     const T *__restrict__ c1, const T *__restrict__ c2,
                                                     const T *__restrict__ dinv, const TR *__restrict__ rhs,
-                                                    T *__restrict__ out, unsigned long long *prog, int *sync) {
+                                                    T *__restrict__ out, unsigned long long *jface,
+                                                    unsigned long long *kface, int *sync) {
+    using TG = Tagged<T>;
+    constexpr int WW = TG::W;
     extern __shared__ unsigned char smraw[];
     T *sm = reinterpret_cast<T *>(smraw);   // [2][TK][TJ]
     __shared__ int s_vb, s_tgt;
-    __shared__ volatile int s_done, s_availJ, s_availK, s_abort;
     const int tid = threadIdx.x;
     const int ncomp = TJ * TK;
-    const int ncw = (ncomp + 31) / 32;      // compute warps
     const int steps = nx + TJ + TK - 2;
     if (tid == 0) {
         s_vb = atomicAdd(&sync[1], 1);
@@ -104,130 +137,96 @@ __global__ void __launch_bounds__(544, 1) k_tile_sweep(int nx, int ny, int nz, i
     }
     __syncthreads();
     const int tile = order[s_vb];
-    const unsigned long long epoch = (unsigned long long)(unsigned)s_tgt << 32;
+    const unsigned tag = (unsigned)s_tgt;
     const int J = tile % NJ, K = tile / NJ;
-    const int prodJ = J > 0 ? (J - 1) + NJ * K : -1;
-    const int prodK = K > 0 ? J + NJ * (K - 1) : -1;
-    if (tid == 0) {
-        s_done = 0;
-        s_availJ = prodJ >= 0 ? 0 : steps;
-        s_availK = prodK >= 0 ? 0 : steps;
-        s_abort = 0;
+    const int tj = tid % TJ, tk = tid / TJ;
+    const int jm = J * TJ + tj, km = K * TK + tk;   // mirrored pencil coordinates
+    const bool live = tid < ncomp && jm < ny && km < nz;
+    const int j = BWD ? ny - 1 - jm : jm, k = BWD ? nz - 1 - km : km;
+    const long long plane = (long long)nx * ny;
+    const long long row0 = (long long)nx * j + plane * k;   // real index of x = 0
+    const bool needJ = live && tj == 0 && J > 0;
+    const bool needK = live && tk == 0 && K > 0;
+    const bool feedJ = live && tj == TJ - 1 && J + 1 < NJ;
+    const bool feedK = live && tk == TK - 1 && K + 1 < NK;
+    const unsigned long long *inJ = needJ ? jface + (((long long)((J - 1) + NJ * K) * TK + tk) * nx) * WW : nullptr;
+    const unsigned long long *inK = needK ? kface + (((long long)(J + NJ * (K - 1)) * TJ + tj) * nx) * WW : nullptr;
+    unsigned long long *outJ = feedJ ? jface + (((long long)tile * TK + tk) * nx) * WW : nullptr;
+    unsigned long long *outK = feedK ? kface + (((long long)tile * TJ + tj) * nx) * WW : nullptr;
+
+    // stream this pencil's inputs into L2 now; the register ring then hits L2
+    if (live) {
+        const T *arr[4] = {c0, c1, c2, BWD ? dinv : c0};
+        for (int x = 0; x < nx; x += 128 / (int)sizeof(T)) {
+            const long long c = row0 + x;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) prefetch_l2(arr[a] + c);
+            prefetch_l2(rhs + c);
+        }
     }
-    __syncthreads();
 
-    if (tid >= ncw * 32) {
-        // ------------------------------------------------ communication warp
-        if (tid == ncw * 32) {
-            int published = 0, aJ = s_availJ, aK = s_availK;
-            long long spins = 0;
-            while (true) {
-                const int d = ld_acquire_cta_s32(&s_done);
-                if (d > published) {
-                    st_release_u64(&prog[tile], epoch | (unsigned long long)d);
-                    published = d;
+    T rr[D], a0[D], a1[D], a2[D], di[D];
+    unsigned long long wj[D][WW], wk[D][WW];
+    auto load = [&](int d, int xm) {
+        rr[d] = T(0); a0[d] = T(0); a1[d] = T(0); a2[d] = T(0); di[d] = T(1);
+#pragma unroll
+        for (int q = 0; q < WW; ++q) { wj[d][q] = 0ull; wk[d][q] = 0ull; }
+        if (!live || xm < 0 || xm >= nx) return;
+        const long long c = row0 + (BWD ? nx - 1 - xm : xm);
+        rr[d] = (T)__ldg(&rhs[c]);
+        a0[d] = __ldg(&c0[c]);
+        a1[d] = __ldg(&c1[c]);
+        a2[d] = __ldg(&c2[c]);
+        if (BWD) di[d] = __ldg(&dinv[c]);
+        if (needJ) TG::fetch(inJ + (long long)xm * WW, wj[d]);
+        if (needK) TG::fetch(inK + (long long)xm * WW, wk[d]);
+    };
+    // accept a prefetched face word, re-reading while it is stale (bounded)
+    auto accept = [&](unsigned long long *w, const unsigned long long *src) -> T {
+        long long spins = 0;
+        while (!TG::ok(w, tag)) {
+            if ((++spins & 255) == 0) {
+                if (*((volatile int *)&sync[3]) != 0) break;
+                if (spins > kSpinLimit) {
+                    atomicOr(&sync[3], kErrTimeout);
+                    break;
                 }
-                // relaxed polls; one acquire fence only when a producer advanced
-                int nJ = aJ, nK = aK;
-                if (aJ < steps) {
-                    const unsigned long long v = ld_relaxed_u64(&prog[prodJ]);
-                    nJ = v >= epoch ? (int)(v - epoch) : 0;
+            }
+            TG::fetch(src, w);
+        }
+        return TG::value(w);
+    };
+
+    const int skew = tj + tk;
+#pragma unroll
+    for (int d = 0; d < D; ++d) load(d, d - skew);
+    T prev = T(0);
+    // Unrolled by D: ring slot u holds the inputs of steps t = u (mod D), is
+    // consumed at step t and refilled for step t + D (no in-flight register moves).
+    for (int t0 = 0; t0 < steps; t0 += D) {
+#pragma unroll
+        for (int u = 0; u < D; ++u) {
+            const int t = t0 + u;
+            if (t < steps) {
+                if (t > 0) __syncthreads();   // step t-1 values in shared memory
+                const int xm = t - skew;
+                if (live && xm >= 0 && xm < nx) {
+                    const T *smp = sm + ((t - 1) & 1) * ncomp;
+                    const T nj = tj > 0 ? smp[tk * TJ + tj - 1]
+                                        : (needJ ? accept(wj[u], inJ + (long long)xm * WW) : T(0));
+                    const T nk = tk > 0 ? smp[(tk - 1) * TJ + tj]
+                                        : (needK ? accept(wk[u], inK + (long long)xm * WW) : T(0));
+                    T s = rr[u] - a0[u] * prev - a1[u] * nj - a2[u] * nk;
+                    if (BWD) s *= di[u];
+                    out[row0 + (BWD ? nx - 1 - xm : xm)] = s;
+                    if (feedJ) TG::put(outJ + (long long)xm * WW, s, tag);
+                    if (feedK) TG::put(outK + (long long)xm * WW, s, tag);
+                    prev = s;
+                    sm[(t & 1) * ncomp + tk * TJ + tj] = s;
                 }
-                if (aK < steps) {
-                    const unsigned long long v = ld_relaxed_u64(&prog[prodK]);
-                    nK = v >= epoch ? (int)(v - epoch) : 0;
-                }
-                if (nJ > aJ || nK > aK) {
-                    fence_acq_rel_gpu();
-                    if (nJ > aJ) { aJ = nJ; st_release_cta_s32(&s_availJ, aJ); }
-                    if (nK > aK) { aK = nK; st_release_cta_s32(&s_availK, aK); }
-                }
-                if (published == steps && aJ >= steps && aK >= steps) break;
-                if ((++spins & 1023) == 0) {
-                    if (*((volatile int *)&sync[3]) != 0 || spins > kSpinLimit) {
-                        if (spins > kSpinLimit) atomicOr(&sync[3], kErrTimeout);
-                        s_abort = 1;
-                        break;
-                    }
-                }
+                load(u, xm + D);
             }
         }
-    } else {
-        // ----------------------------------------------------- compute warps
-        const int tj = tid % TJ, tk = tid / TJ;
-        const int jm = J * TJ + tj, km = K * TK + tk;   // mirrored pencil coordinates
-        const bool live = tid < ncomp && jm < ny && km < nz;
-        const int j = BWD ? ny - 1 - jm : jm, k = BWD ? nz - 1 - km : km;
-        const long long plane = (long long)nx * ny;
-        const long long row0 = (long long)nx * j + plane * k;   // real index of x = 0
-        const long long oy = BWD ? -(long long)nx : (long long)nx;
-        const long long oz = BWD ? -plane : plane;
-        const bool needJ = live && tj == 0 && jm > 0;
-        const bool needK = live && tk == 0 && km > 0;
-        const int nct = ncw * 32;
-
-        T rr[D], a0[D], a1[D], a2[D], di[D], vj[D], vk[D];
-        auto load = [&](int d, int xm) {
-            rr[d] = T(0); a0[d] = T(0); a1[d] = T(0); a2[d] = T(0); di[d] = T(1); vj[d] = T(0); vk[d] = T(0);
-            if (!live || xm < 0 || xm >= nx) return;
-            const long long c = row0 + (BWD ? nx - 1 - xm : xm);
-            rr[d] = (T)__ldg(&rhs[c]);
-            a0[d] = __ldg(&c0[c]);
-            a1[d] = __ldg(&c1[c]);
-            a2[d] = __ldg(&c2[c]);
-            if (BWD) di[d] = __ldg(&dinv[c]);
-            if (needJ) vj[d] = __ldcg(&out[c - oy]);
-            if (needK) vk[d] = __ldcg(&out[c - oz]);
-        };
-        // loads at step t need producers to have completed min(t + D + TJ|TK, steps) steps
-        auto ready = [&](int t) {
-            if (tid == 0) {
-                const int nJ = min(t + D + TJ, steps), nK = min(t + D + TK, steps);
-                long long spins = 0;
-                while (s_availJ < nJ || s_availK < nK) {
-                    if (s_abort) break;
-                    if (++spins > (kSpinLimit << 4)) {
-                        atomicOr(&sync[3], kErrTimeout);
-                        s_abort = 1;
-                        break;
-                    }
-                }
-                __threadfence_block();
-            }
-        };
-
-        ready(0);
-        compute_barrier(nct);
-        const int skew = tj + tk;
-#pragma unroll
-        for (int d = 0; d < D; ++d) load(d, d - skew);
-        T prev = T(0);
-        for (int t = 0; t < steps; ++t) {
-            if (t > 0) {
-                ready(t);
-                compute_barrier(nct);   // step t-1 complete: values in shared memory, producers ready
-                if (tid == 0) st_release_cta_s32(&s_done, t);
-            }
-            const int xm = t - skew;
-            if (live && xm >= 0 && xm < nx) {
-                const T *smp = sm + ((t - 1) & 1) * ncomp;
-                const T nj = tj > 0 ? smp[tk * TJ + tj - 1] : vj[0];
-                const T nk = tk > 0 ? smp[(tk - 1) * TJ + tj] : vk[0];
-                T s = rr[0] - a0[0] * prev - a1[0] * nj - a2[0] * nk;
-                if (BWD) s *= di[0];
-                out[row0 + (BWD ? nx - 1 - xm : xm)] = s;
-                prev = s;
-                sm[(t & 1) * ncomp + tk * TJ + tj] = s;
-            }
-#pragma unroll
-            for (int d = 0; d < D - 1; ++d) {
-                rr[d] = rr[d + 1]; a0[d] = a0[d + 1]; a1[d] = a1[d + 1]; a2[d] = a2[d + 1];
-                di[d] = di[d + 1]; vj[d] = vj[d + 1]; vk[d] = vk[d + 1];
-            }
-            load(D - 1, xm + D);
-        }
-        compute_barrier(nct);
-        if (tid == 0) st_release_cta_s32(&s_done, steps);
     }
     __syncthreads();
     if (tid == 0) {
@@ -260,22 +259,22 @@ template <typename T> constexpr int ring_depth() { return sizeof(T) == 8 ? 4 : 8
 template <typename T, typename TR>
 void tiled_apply(ms_system &s, const T *coef, const T *dinv, const TR *r, T *y, T *z, cudaStream_t st) {
     const int nT = s.NJ * s.NK;
-    const int ncomp = s.TJ * s.TK;
-    const int threads = 32 * ((ncomp + 31) / 32) + 32;   // compute warps + one communication warp
-    const size_t smem = 2 * (size_t)ncomp * sizeof(T);
+    const int threads = s.TJ * s.TK;
+    const size_t smem = 2 * (size_t)threads * sizeof(T);
     const int64_t n = s.n;
     const double nl = (double)s.nnz_lower;
+    unsigned long long *jf = s.face_j.p, *kf = s.face_k.p;
     {
         KernelScope ks_(st, sizeof(T) == 8 ? "ilu_fwd" : "ilu_fwd32", nl * sizeof(T) + (double)n * (sizeof(TR) + sizeof(T)));
         k_tile_sweep<T, TR, false, ring_depth<T>()><<<nT, threads, smem, st>>>(
-            s.nx, s.ny, s.nz, s.TJ, s.TK, s.NJ, s.tile_order.p, coef, coef + n, coef + 2 * n, nullptr, r, y,
-            s.tile_prog.p, s.sync.p);
+            s.nx, s.ny, s.nz, s.TJ, s.TK, s.NJ, s.NK, s.tile_order.p, coef, coef + n, coef + 2 * n, nullptr, r, y, jf,
+            kf, s.sync.p);
         MS_CHECK_LAUNCH();
     }
     KernelScope ks_(st, sizeof(T) == 8 ? "ilu_bwd" : "ilu_bwd32", nl * sizeof(T) + (double)n * 3 * sizeof(T));
-    k_tile_sweep<T, T, true, ring_depth<T>()><<<nT, threads, smem, st>>>(s.nx, s.ny, s.nz, s.TJ, s.TK, s.NJ,
-                                                              s.tile_order.p, coef + 3 * n, coef + 4 * n,
-                                                              coef + 5 * n, dinv, y, z, s.tile_prog.p, s.sync.p);
+    k_tile_sweep<T, T, true, ring_depth<T>()><<<nT, threads, smem, st>>>(s.nx, s.ny, s.nz, s.TJ, s.TK, s.NJ, s.NK,
+                                                                        s.tile_order.p, coef + 3 * n, coef + 4 * n,
+                                                                        coef + 5 * n, dinv, y, z, jf, kf, s.sync.p);
     MS_CHECK_LAUNCH();
 }
 

@@ -198,8 +198,11 @@ void analyse_grid(ms_system &s, const ms_grid &g) {
                 if (K >= 0 && K < s.NK) order.push_back(J + s.NJ * K);
             }
         s.tile_order.upload(order, nullptr);
-        s.tile_prog.alloc(order.size());
-        s.tile_prog.zero(nullptr);
+        // two tagged words per value (FP64); zero tags never match a sweep
+        s.face_j.alloc(std::max<size_t>((size_t)order.size() * tk * nx * 2, 1));
+        s.face_k.alloc(std::max<size_t>((size_t)order.size() * tj * nx * 2, 1));
+        s.face_j.zero(nullptr);
+        s.face_k.zero(nullptr);
     }
 
     // host copies + device upload

@@ -165,7 +165,7 @@ struct ms_system {
     msgb::DBuf<int8_t> dir_slot;              // [d*n + i]
     int TJ = 0, TK = 0, NJ = 0, NK = 0;
     msgb::DBuf<int> tile_order;
-    msgb::DBuf<unsigned long long> tile_prog;
+    msgb::DBuf<unsigned long long> face_j, face_k;   // tagged tile-face exchange buffers
     msgb::DBuf<double> dcoef64;               // [6*n]: L(-x,-y,-z), U(+x,+y,+z)
     msgb::DBuf<float> dcoef32;
     msgb::DBuf<int> lperm;
