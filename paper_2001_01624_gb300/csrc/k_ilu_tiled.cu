@@ -80,28 +80,23 @@ __device__ __forceinline__ unsigned long long ld_tag(const unsigned long long *p
 
 __device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
-// Values of type T exchanged as one (float) or two (double) tagged words.
+// Tagged face values: 16 bytes per value, one (float) or two (double)
+// tagged 64-bit words, so a consumer can fetch a value with one 16-byte
+// async copy and validate it in shared memory.
 template <typename T>
 struct Tagged;
 template <>
 struct Tagged<float> {
-    static constexpr int W = 1;
     __device__ static void put(unsigned long long *p, float v, unsigned tag) { st_tag(p, __float_as_uint(v), tag); }
-    __device__ static void fetch(const unsigned long long *p, unsigned long long *w) { w[0] = ld_tag(p); }
     __device__ static bool ok(const unsigned long long *w, unsigned tag) { return (unsigned)(w[0] >> 32) == tag; }
     __device__ static float value(const unsigned long long *w) { return __uint_as_float((unsigned)w[0]); }
 };
 template <>
 struct Tagged<double> {
-    static constexpr int W = 2;
     __device__ static void put(unsigned long long *p, double v, unsigned tag) {
         const unsigned long long b = (unsigned long long)__double_as_longlong(v);
         st_tag(p, (unsigned)b, tag);
         st_tag(p + 1, (unsigned)(b >> 32), tag);
-    }
-    __device__ static void fetch(const unsigned long long *p, unsigned long long *w) {
-        w[0] = ld_tag(p);
-        w[1] = ld_tag(p + 1);
     }
     __device__ static bool ok(const unsigned long long *w, unsigned tag) {
         return (unsigned)(w[0] >> 32) == tag && (unsigned)(w[1] >> 32) == tag;
@@ -111,11 +106,30 @@ struct Tagged<double> {
     }
 };
 
-// Tile sweep.  Tiles exchange the values on their high j and k faces
-// through tagged face buffers: jface[tile][tk][x] feeds tile (J+1, K),
-// kface[tile][tj][x] feeds tile (J, K+1).  A consumer pencil prefetches the
-// face word D steps ahead and validates it when used, re-reading (bounded)
-// while it still carries an older sweep's tag.
+// Asynchronous global -> shared copies (per thread).  src_bytes = 0 fills
+// the destination with zeros without reading the source.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem_dst, const void *gsrc, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    const int sb = valid ? BYTES : 0;
+    if (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(sb) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(gsrc), "n"(BYTES), "r"(sb)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Tile sweep.  Per step: one CTA barrier, two shared-memory neighbour reads,
+// one fused multiply-add chain.  Inputs of step t + D are copied
+// asynchronously into a per-thread shared-memory ring at step t (async
+// copies are not waited for by the barrier).  Tiles exchange their high j
+// and k faces through tagged face buffers: jface[tile][tk][x] feeds tile
+// (J+1, K), kface[tile][tj][x] feeds tile (J, K+1); a consumer validates the
+// prefetched face value when it uses it and re-reads it (bounded) while it
+// still carries an older sweep's tag.
 template <typename T, typename TR, bool BWD, int D>
 __global__ void __launch_bounds__(512) k_tile_sweep(int nx, int ny, int nz, int TJ, int TK, int NJ, int NK,
                                                     const int *__restrict__ order, const T *__restrict__ c0,
@@ -124,12 +138,26 @@ __global__ void __launch_bounds__(512) k_tile_sweep(int nx, int ny, int nz, int 
                                                     T *__restrict__ out, unsigned long long *jface,
                                                     unsigned long long *kface, int *sync) {
     using TG = Tagged<T>;
-    constexpr int WW = TG::W;
-    extern __shared__ unsigned char smraw[];
-    T *sm = reinterpret_cast<T *>(smraw);   // [2][TK][TJ]
-    __shared__ int s_vb, s_tgt;
+    constexpr int NA = BWD ? 5 : 4;            // rhs, c0, c1, c2 (, dinv)
+    extern __shared__ __align__(16) unsigned char smraw[];
     const int tid = threadIdx.x;
+    const int nthr = blockDim.x;
     const int ncomp = TJ * TK;
+    // shared layout: [2][ncomp] exchange | ring [D][NA-1][nthr] of T | rhs ring [D][nthr] of TR |
+    // j-face ring [D][TK] and k-face ring [D][TJ] of 16-byte tagged values
+    T *sm = reinterpret_cast<T *>(smraw);
+    size_t off = (((size_t)2 * ncomp * sizeof(T)) + 15) & ~(size_t)15;
+    TR *rrs = nullptr;   // rhs ring kept in its own type
+    T *ring = reinterpret_cast<T *>(smraw + off);
+    off += (size_t)D * (NA - 1) * nthr * sizeof(T);
+    off = (off + 15) & ~(size_t)15;
+    rrs = reinterpret_cast<TR *>(smraw + off);
+    off += (size_t)D * nthr * sizeof(TR);
+    off = (off + 15) & ~(size_t)15;
+    unsigned long long *fringJ = reinterpret_cast<unsigned long long *>(smraw + off);
+    unsigned long long *fringK = fringJ + (size_t)D * TK * 2;
+
+    __shared__ int s_vb, s_tgt;
     const int steps = nx + TJ + TK - 2;
     if (tid == 0) {
         s_vb = atomicAdd(&sync[1], 1);
@@ -144,47 +172,49 @@ __global__ void __launch_bounds__(512) k_tile_sweep(int nx, int ny, int nz, int 
     const bool live = tid < ncomp && jm < ny && km < nz;
     const int j = BWD ? ny - 1 - jm : jm, k = BWD ? nz - 1 - km : km;
     const long long plane = (long long)nx * ny;
-    const long long row0 = (long long)nx * j + plane * k;   // real index of x = 0
+    const long long row0 = live ? (long long)nx * j + plane * k : 0;   // real index of x = 0
     const bool needJ = live && tj == 0 && J > 0;
     const bool needK = live && tk == 0 && K > 0;
     const bool feedJ = live && tj == TJ - 1 && J + 1 < NJ;
     const bool feedK = live && tk == TK - 1 && K + 1 < NK;
-    const unsigned long long *inJ = needJ ? jface + (((long long)((J - 1) + NJ * K) * TK + tk) * nx) * WW : nullptr;
-    const unsigned long long *inK = needK ? kface + (((long long)(J + NJ * (K - 1)) * TJ + tj) * nx) * WW : nullptr;
-    unsigned long long *outJ = feedJ ? jface + (((long long)tile * TK + tk) * nx) * WW : nullptr;
-    unsigned long long *outK = feedK ? kface + (((long long)tile * TJ + tj) * nx) * WW : nullptr;
+    const unsigned long long *inJ = jface + (needJ ? (((long long)((J - 1) + NJ * K) * TK + tk) * nx) * 2 : 0);
+    const unsigned long long *inK = kface + (needK ? (((long long)(J + NJ * (K - 1)) * TJ + tj) * nx) * 2 : 0);
+    unsigned long long *outJ = jface + (feedJ ? (((long long)tile * TK + tk) * nx) * 2 : 0);
+    unsigned long long *outK = kface + (feedK ? (((long long)tile * TJ + tj) * nx) * 2 : 0);
 
-    // stream this pencil's inputs into L2 now; the register ring then hits L2
+    // stream this pencil's inputs into L2 now; the async ring then hits L2
     if (live) {
-        const T *arr[4] = {c0, c1, c2, BWD ? dinv : c0};
         for (int x = 0; x < nx; x += 128 / (int)sizeof(T)) {
             const long long c = row0 + x;
-#pragma unroll
-            for (int a = 0; a < 4; ++a) prefetch_l2(arr[a] + c);
+            prefetch_l2(c0 + c);
+            prefetch_l2(c1 + c);
+            prefetch_l2(c2 + c);
+            if (BWD) prefetch_l2(dinv + c);
             prefetch_l2(rhs + c);
         }
     }
 
-    T rr[D], a0[D], a1[D], a2[D], di[D];
-    unsigned long long wj[D][WW], wk[D][WW];
-    auto load = [&](int d, int xm) {
-        rr[d] = T(0); a0[d] = T(0); a1[d] = T(0); a2[d] = T(0); di[d] = T(1);
-#pragma unroll
-        for (int q = 0; q < WW; ++q) { wj[d][q] = 0ull; wk[d][q] = 0ull; }
-        if (!live || xm < 0 || xm >= nx) return;
-        const long long c = row0 + (BWD ? nx - 1 - xm : xm);
-        rr[d] = (T)__ldg(&rhs[c]);
-        a0[d] = __ldg(&c0[c]);
-        a1[d] = __ldg(&c1[c]);
-        a2[d] = __ldg(&c2[c]);
-        if (BWD) di[d] = __ldg(&dinv[c]);
-        if (needJ) TG::fetch(inJ + (long long)xm * WW, wj[d]);
-        if (needK) TG::fetch(inK + (long long)xm * WW, wk[d]);
+    auto slot = [&](int d, int a) -> T * { return ring + ((size_t)d * (NA - 1) + a) * nthr + tid; };
+    auto fslotJ = [&](int d) -> unsigned long long * { return fringJ + ((size_t)d * TK + tk) * 2; };
+    auto fslotK = [&](int d) -> unsigned long long * { return fringK + ((size_t)d * TJ + tj) * 2; };
+    // issue the copies for mirrored x into ring slot d (one commit group per call)
+    auto issue = [&](int d, int xm) {
+        const bool v = live && xm >= 0 && xm < nx;
+        const long long c = v ? row0 + (BWD ? nx - 1 - xm : xm) : 0;
+        cp_async<sizeof(TR)>(rrs + (size_t)d * nthr + tid, rhs + c, v);
+        cp_async<sizeof(T)>(slot(d, 0), c0 + c, v);
+        cp_async<sizeof(T)>(slot(d, 1), c1 + c, v);
+        cp_async<sizeof(T)>(slot(d, 2), c2 + c, v);
+        if (BWD) cp_async<sizeof(T)>(slot(d, 3), dinv + c, v);
+        if (needJ) cp_async<16>(fslotJ(d), inJ + (long long)(v ? xm : 0) * 2, v);
+        if (needK) cp_async<16>(fslotK(d), inK + (long long)(v ? xm : 0) * 2, v);
+        cp_async_commit();
     };
-    // accept a prefetched face word, re-reading while it is stale (bounded)
+    // value of a face word in shared memory, re-read from global while stale
     auto accept = [&](unsigned long long *w, const unsigned long long *src) -> T {
+        unsigned long long g[2] = {w[0], w[1]};
         long long spins = 0;
-        while (!TG::ok(w, tag)) {
+        while (!TG::ok(g, tag)) {
             if ((++spins & 255) == 0) {
                 if (*((volatile int *)&sync[3]) != 0) break;
                 if (spins > kSpinLimit) {
@@ -192,42 +222,43 @@ __global__ void __launch_bounds__(512) k_tile_sweep(int nx, int ny, int nz, int 
                     break;
                 }
             }
-            TG::fetch(src, w);
+            g[0] = ld_tag(src);
+            g[1] = ld_tag(src + 1);
         }
-        return TG::value(w);
+        return TG::value(g);
     };
 
     const int skew = tj + tk;
 #pragma unroll
-    for (int d = 0; d < D; ++d) load(d, d - skew);
+    for (int d = 0; d < D; ++d) issue(d, d - skew);
     T prev = T(0);
-    // Unrolled by D: ring slot u holds the inputs of steps t = u (mod D), is
-    // consumed at step t and refilled for step t + D (no in-flight register moves).
     for (int t0 = 0; t0 < steps; t0 += D) {
 #pragma unroll
         for (int u = 0; u < D; ++u) {
             const int t = t0 + u;
             if (t < steps) {
-                if (t > 0) __syncthreads();   // step t-1 values in shared memory
+                cp_async_wait<D - 1>();          // this thread's copies for step t have landed
+                if (t > 0) __syncthreads();      // step t-1 values in shared memory
                 const int xm = t - skew;
                 if (live && xm >= 0 && xm < nx) {
                     const T *smp = sm + ((t - 1) & 1) * ncomp;
                     const T nj = tj > 0 ? smp[tk * TJ + tj - 1]
-                                        : (needJ ? accept(wj[u], inJ + (long long)xm * WW) : T(0));
+                                        : (needJ ? accept(fslotJ(u), inJ + (long long)xm * 2) : T(0));
                     const T nk = tk > 0 ? smp[(tk - 1) * TJ + tj]
-                                        : (needK ? accept(wk[u], inK + (long long)xm * WW) : T(0));
-                    T s = rr[u] - a0[u] * prev - a1[u] * nj - a2[u] * nk;
-                    if (BWD) s *= di[u];
+                                        : (needK ? accept(fslotK(u), inK + (long long)xm * 2) : T(0));
+                    T s = (T)rrs[(size_t)u * nthr + tid] - *slot(u, 0) * prev - *slot(u, 1) * nj - *slot(u, 2) * nk;
+                    if (BWD) s *= *slot(u, 3);
                     out[row0 + (BWD ? nx - 1 - xm : xm)] = s;
-                    if (feedJ) TG::put(outJ + (long long)xm * WW, s, tag);
-                    if (feedK) TG::put(outK + (long long)xm * WW, s, tag);
+                    if (feedJ) TG::put(outJ + (long long)xm * 2, s, tag);
+                    if (feedK) TG::put(outK + (long long)xm * 2, s, tag);
                     prev = s;
                     sm[(t & 1) * ncomp + tk * TJ + tj] = s;
                 }
-                load(u, xm + D);
+                issue(u, xm + D);
             }
         }
     }
+    cp_async_wait<0>();
     __syncthreads();
     if (tid == 0) {
         __threadfence();
@@ -239,6 +270,19 @@ __global__ void __launch_bounds__(512) k_tile_sweep(int nx, int ny, int nz, int 
             atomicAdd(&sync[0], 1);
         }
     }
+}
+
+template <typename T, typename TR, bool BWD, int D>
+size_t tile_smem(int TJ, int TK) {
+    constexpr int NA = BWD ? 5 : 4;
+    const int nthr = TJ * TK;
+    size_t off = (((size_t)2 * nthr * sizeof(T)) + 15) & ~(size_t)15;
+    off += (size_t)D * (NA - 1) * nthr * sizeof(T);
+    off = (off + 15) & ~(size_t)15;
+    off += (size_t)D * nthr * sizeof(TR);
+    off = (off + 15) & ~(size_t)15;
+    off += (size_t)D * (TJ + TK) * 16;
+    return off;
 }
 
 // Direction-major factor coefficients from the ELL factor.
@@ -254,28 +298,36 @@ __global__ void k_extract_dirs(int n, const int8_t *__restrict__ dslot, const do
 }
 
 // register-ring depth: steps of load latency hidden (bounded by registers)
-template <typename T> constexpr int ring_depth() { return sizeof(T) == 8 ? 4 : 8; }
+template <typename T> constexpr int ring_depth() { return 8; }
+
+template <typename T, typename TR, bool BWD>
+void launch_sweep(ms_system &s, const T *a0, const T *a1, const T *a2, const T *dinv, const TR *rhs, T *out,
+                  cudaStream_t st) {
+    constexpr int D = ring_depth<T>();
+    const int nT = s.NJ * s.NK;
+    const int threads = s.TJ * s.TK;
+    const size_t smem = tile_smem<T, TR, BWD, D>(s.TJ, s.TK);
+    auto kern = k_tile_sweep<T, TR, BWD, D>;
+    static size_t smem_set = 48 * 1024;   // per instantiation: raise the dynamic shared-memory limit once
+    if (smem > smem_set) {
+        MS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        smem_set = smem;
+    }
+    kern<<<nT, threads, smem, st>>>(s.nx, s.ny, s.nz, s.TJ, s.TK, s.NJ, s.NK, s.tile_order.p, a0, a1, a2, dinv, rhs,
+                                    out, s.face_j.p, s.face_k.p, s.sync.p);
+    MS_CHECK_LAUNCH();
+}
 
 template <typename T, typename TR>
 void tiled_apply(ms_system &s, const T *coef, const T *dinv, const TR *r, T *y, T *z, cudaStream_t st) {
-    const int nT = s.NJ * s.NK;
-    const int threads = s.TJ * s.TK;
-    const size_t smem = 2 * (size_t)threads * sizeof(T);
     const int64_t n = s.n;
     const double nl = (double)s.nnz_lower;
-    unsigned long long *jf = s.face_j.p, *kf = s.face_k.p;
     {
         KernelScope ks_(st, sizeof(T) == 8 ? "ilu_fwd" : "ilu_fwd32", nl * sizeof(T) + (double)n * (sizeof(TR) + sizeof(T)));
-        k_tile_sweep<T, TR, false, ring_depth<T>()><<<nT, threads, smem, st>>>(
-            s.nx, s.ny, s.nz, s.TJ, s.TK, s.NJ, s.NK, s.tile_order.p, coef, coef + n, coef + 2 * n, nullptr, r, y, jf,
-            kf, s.sync.p);
-        MS_CHECK_LAUNCH();
+        launch_sweep<T, TR, false>(s, coef, coef + n, coef + 2 * n, nullptr, r, y, st);
     }
     KernelScope ks_(st, sizeof(T) == 8 ? "ilu_bwd" : "ilu_bwd32", nl * sizeof(T) + (double)n * 3 * sizeof(T));
-    k_tile_sweep<T, T, true, ring_depth<T>()><<<nT, threads, smem, st>>>(s.nx, s.ny, s.nz, s.TJ, s.TK, s.NJ, s.NK,
-                                                                        s.tile_order.p, coef + 3 * n, coef + 4 * n,
-                                                                        coef + 5 * n, dinv, y, z, jf, kf, s.sync.p);
-    MS_CHECK_LAUNCH();
+    launch_sweep<T, T, true>(s, coef + 3 * n, coef + 4 * n, coef + 5 * n, dinv, y, z, st);
 }
 
 }  // namespace
