@@ -136,7 +136,8 @@ __global__ void __launch_bounds__(512) k_tile_sweep(int nx, int ny, int nz, int 
                                                     const T *__restrict__ c1, const T *__restrict__ c2,
                                                     const T *__restrict__ dinv, const TR *__restrict__ rhs,
                                                     T *__restrict__ out, unsigned long long *jface,
-                                                    unsigned long long *kface, int *sync) {
+                                                    unsigned long long *kface, unsigned long long *progress,
+                                                    int *sync) {
     using TG = Tagged<T>;
     constexpr int NA = BWD ? 5 : 4;            // rhs, c0, c1, c2 (, dinv)
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -156,6 +157,7 @@ __global__ void __launch_bounds__(512) k_tile_sweep(int nx, int ny, int nz, int 
     off = (off + 15) & ~(size_t)15;
     unsigned long long *fringJ = reinterpret_cast<unsigned long long *>(smraw + off);
     unsigned long long *fringK = fringJ + (size_t)D * TK * 2;
+    unsigned long long *pring = fringK + (size_t)D * TJ * 2;   // [D][2] producer progress words (x2 for 16 B)
 
     __shared__ int s_vb, s_tgt;
     const int steps = nx + TJ + TK - 2;
@@ -228,9 +230,49 @@ __global__ void __launch_bounds__(512) k_tile_sweep(int nx, int ny, int nz, int 
         return TG::value(g);
     };
 
+    // Pacing: tile progress words are hints only (tags make the data safe).
+    // Thread 0 fetches the producers' progress through the async ring and,
+    // before the barrier of step t, waits until the producers have completed
+    // the steps whose face values this CTA prefetches at step t.  A consumer
+    // thus trails its producer far enough that face prefetches are fresh,
+    // instead of re-polling stale values on every step.
+    const int prodJ = J > 0 ? (J - 1) + NJ * K : -1;
+    const int prodK = K > 0 ? J + NJ * (K - 1) : -1;
+    const bool pacer = tid == 0 && (prodJ >= 0 || prodK >= 0);
+    unsigned seenJ = 0, seenK = 0;   // producer steps known complete (this sweep)
+    auto progress_of = [&](unsigned long long w) -> unsigned {
+        return (unsigned)(w >> 32) == tag ? (unsigned)w : 0u;
+    };
+    auto pace = [&](int t, int u) {
+        if (!pacer) return;
+        const unsigned nJ = (unsigned)min(t + D + TJ, steps), nK = (unsigned)min(t + D + TK, steps);
+        if (prodJ >= 0) seenJ = max(seenJ, progress_of(pring[u * 4 + 0]));
+        if (prodK >= 0) seenK = max(seenK, progress_of(pring[u * 4 + 2]));
+        long long spins = 0;
+        while ((prodJ >= 0 && seenJ < nJ) || (prodK >= 0 && seenK < nK)) {
+            if (prodJ >= 0 && seenJ < nJ) seenJ = max(seenJ, progress_of(ld_tag(progress + 2 * prodJ)));
+            if (prodK >= 0 && seenK < nK) seenK = max(seenK, progress_of(ld_tag(progress + 2 * prodK)));
+            if ((++spins & 255) == 0) {
+                if (*((volatile int *)&sync[3]) != 0) break;
+                if (spins > kSpinLimit) {
+                    atomicOr(&sync[3], kErrTimeout);
+                    break;
+                }
+            }
+        }
+    };
+    auto issue_progress = [&](int u) {
+        if (!pacer) return;
+        if (prodJ >= 0) cp_async<16>(pring + u * 4 + 0, progress + 2 * prodJ, true);   // 16 B: via L2
+        if (prodK >= 0) cp_async<16>(pring + u * 4 + 2, progress + 2 * prodK, true);
+    };
+
     const int skew = tj + tk;
 #pragma unroll
-    for (int d = 0; d < D; ++d) issue(d, d - skew);
+    for (int d = 0; d < D; ++d) {
+        issue_progress(d);
+        issue(d, d - skew);
+    }
     T prev = T(0);
     for (int t0 = 0; t0 < steps; t0 += D) {
 #pragma unroll
@@ -238,7 +280,9 @@ __global__ void __launch_bounds__(512) k_tile_sweep(int nx, int ny, int nz, int 
             const int t = t0 + u;
             if (t < steps) {
                 cp_async_wait<D - 1>();          // this thread's copies for step t have landed
+                pace(t, u);
                 if (t > 0) __syncthreads();      // step t-1 values in shared memory
+                if (tid == 0 && t > 0) st_tag(progress + 2 * tile, (unsigned)t, tag);   // steps 0..t-1 done
                 const int xm = t - skew;
                 if (live && xm >= 0 && xm < nx) {
                     const T *smp = sm + ((t - 1) & 1) * ncomp;
@@ -254,12 +298,14 @@ __global__ void __launch_bounds__(512) k_tile_sweep(int nx, int ny, int nz, int 
                     prev = s;
                     sm[(t & 1) * ncomp + tk * TJ + tj] = s;
                 }
+                issue_progress(u);
                 issue(u, xm + D);
             }
         }
     }
     cp_async_wait<0>();
     __syncthreads();
+    if (tid == 0) st_tag(progress + 2 * tile, (unsigned)steps, tag);
     if (tid == 0) {
         __threadfence();
         const int prev_done = atomicAdd(&sync[2], 1);
@@ -282,6 +328,7 @@ size_t tile_smem(int TJ, int TK) {
     off += (size_t)D * nthr * sizeof(TR);
     off = (off + 15) & ~(size_t)15;
     off += (size_t)D * (TJ + TK) * 16;
+    off += (size_t)D * 32;   // progress ring
     return off;
 }
 
@@ -314,7 +361,7 @@ void launch_sweep(ms_system &s, const T *a0, const T *a1, const T *a2, const T *
         smem_set = smem;
     }
     kern<<<nT, threads, smem, st>>>(s.nx, s.ny, s.nz, s.TJ, s.TK, s.NJ, s.NK, s.tile_order.p, a0, a1, a2, dinv, rhs,
-                                    out, s.face_j.p, s.face_k.p, s.sync.p);
+                                    out, s.face_j.p, s.face_k.p, s.tile_progress.p, s.sync.p);
     MS_CHECK_LAUNCH();
 }
 
@@ -350,6 +397,10 @@ void launch_ilu_tiled64(ms_system &s, const double *r, double *y, double *z, cud
 
 void launch_ilu_tiled32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st) {
     tiled_apply<float, double>(s, s.dcoef32.p, s.dinv32.p, r, y, z, st);
+}
+
+void launch_ilu_tiled32f(ms_system &s, const float *r, float *y, float *z, cudaStream_t st) {
+    tiled_apply<float, float>(s, s.dcoef32.p, s.dinv32.p, r, y, z, st);
 }
 
 }  // namespace msgb

@@ -134,8 +134,8 @@ __global__ void k_spmv(int n, int W, const int *__restrict__ col, const double *
 // r = q - A x and ||r||_2
 __global__ void k_residual(int n, int W, const int *__restrict__ col, const double *__restrict__ off,
                            const double *__restrict__ diag, const double *__restrict__ q,
-                           const double *__restrict__ x, double *__restrict__ r, double *red, unsigned int *cnt,
-                           double *norm_out) {
+                           const double *__restrict__ x, double *__restrict__ r, float *__restrict__ r32,
+                           double *red, unsigned int *cnt, double *norm_out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     double ri = 0.0;
     if (i < n) {
@@ -146,6 +146,7 @@ __global__ void k_residual(int n, int W, const int *__restrict__ col, const doub
         }
         ri = q[i] - s;
         r[i] = ri;
+        if (r32) r32[i] = (float)ri;
     }
     if (norm_out) finish_norm(block_sum(ri * ri), red, cnt, norm_out);
 }
@@ -299,9 +300,9 @@ void launch_spmv(const ms_system &s, const double *x, double *y, cudaStream_t st
 }
 
 void launch_residual(const ms_system &s, const double *q, const double *x, double *r, double *red,
-                     unsigned int *cnt, double *norm_out, cudaStream_t st) {
-    KernelScope ks_(st, "residual", (double)s.n * (8 + 8 + 8 + 8) + (double)s.W * s.n * (4 + 8));
-    k_residual<<<blocks_for(s.n), kThreads, 0, st>>>(s.n, s.W, s.col.p, s.off_p.p, s.diag.p, q, x, r, red, cnt,
+                     unsigned int *cnt, double *norm_out, cudaStream_t st, float *r32) {
+    KernelScope ks_(st, "residual", (double)s.n * (8 + 8 + 8 + 8 + (r32 ? 4 : 0)) + (double)s.W * s.n * (4 + 8));
+    k_residual<<<blocks_for(s.n), kThreads, 0, st>>>(s.n, s.W, s.col.p, s.off_p.p, s.diag.p, q, x, r, r32, red, cnt,
                                                       norm_out);
     MS_CHECK_LAUNCH();
 }

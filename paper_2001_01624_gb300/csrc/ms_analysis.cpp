@@ -203,6 +203,8 @@ void analyse_grid(ms_system &s, const ms_grid &g) {
         s.face_k.alloc(std::max<size_t>((size_t)order.size() * tj * nx * 2, 1));
         s.face_j.zero(nullptr);
         s.face_k.zero(nullptr);
+        s.tile_progress.alloc(2 * order.size());   // 16 bytes per tile (fetched with 16-byte async copies)
+        s.tile_progress.zero(nullptr);
     }
 
     // host copies + device upload

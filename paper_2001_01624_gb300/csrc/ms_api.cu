@@ -679,8 +679,14 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
     }
     if (opts->smoother == MS_SMOOTHER_ILU0) ensure_ilu(ctx, *s, mixed);
 
+    // mixed form: the residual also provides the FP32 right-hand side of the FP32 sweeps
+    float *rin32 = nullptr;
+    if (mixed) {
+        s->w_rin32.alloc(n);
+        rin32 = s->w_rin32.p;
+    }
     launch_norm2(s->w_q.p, n, s->w_red.p, s->w_cnt.p, norms.p, st);
-    launch_residual(*s, s->w_q.p, s->w_x.p, s->w_r.p, s->w_red.p, s->w_cnt.p, norms.p + 1, st);
+    launch_residual(*s, s->w_q.p, s->w_x.p, s->w_r.p, s->w_red.p, s->w_cnt.p, norms.p + 1, st, rin32);
     double hn[2];
     {
         double *h = (double *)ctx->pinned.get(64);
@@ -708,7 +714,10 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
             const ms_basis &b = *c.basis;
             // r holds q - A x here
             if (mixed) {
-                if (opts->smoother == MS_SMOOTHER_ILU0) ilu_apply32(*s, s->w_r.p, s->w_y32.p, s->w_z32.p, st);
+                if (opts->smoother == MS_SMOOTHER_ILU0) {
+                    if (s->structured) launch_ilu_tiled32f(*s, s->w_rin32.p, s->w_y32.p, s->w_z32.p, st);
+                    else ilu_apply32(*s, s->w_r.p, s->w_y32.p, s->w_z32.p, st);
+                }
                 else launch_jacobi32(*s, s->w_r.p, s->w_z32.p, (float)jw, st);
                 launch_residual_update32(*s, s->w_r.p, s->w_r32.p, s->w_x.p, s->w_z32.p, st);
             } else {
@@ -739,7 +748,7 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
             }
             const bool last = (l == total - 1);
             launch_residual(*s, s->w_q.p, s->w_x.p, s->w_r.p, s->w_red.p, s->w_cnt.p, last ? norms.p + 1 : nullptr,
-                            st);
+                            st, rin32);
         }
         if (info && info->dyn_blocks) info->dyn_blocks[it] = dyn_coarse ? dyn_coarse->M : 0;
         ++it;

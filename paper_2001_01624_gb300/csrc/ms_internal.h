@@ -166,6 +166,7 @@ struct ms_system {
     int TJ = 0, TK = 0, NJ = 0, NK = 0;
     msgb::DBuf<int> tile_order;
     msgb::DBuf<unsigned long long> face_j, face_k;   // tagged tile-face exchange buffers
+    msgb::DBuf<unsigned long long> tile_progress;    // tagged per-tile progress hints
     msgb::DBuf<double> dcoef64;               // [6*n]: L(-x,-y,-z), U(+x,+y,+z)
     msgb::DBuf<float> dcoef32;
     msgb::DBuf<int> lperm;
@@ -184,7 +185,7 @@ struct ms_system {
 
     // solve workspace (grown on demand)
     msgb::DBuf<double> w_q, w_x, w_r, w_z, w_xprev, w_d, w_xc, w_rc, w_part;
-    msgb::DBuf<float> w_y32, w_z32, w_r32, w_d32, w_xc32;
+    msgb::DBuf<float> w_y32, w_z32, w_r32, w_d32, w_xc32, w_rin32;
     msgb::DBuf<double> w_y;
     msgb::DBuf<double> w_red;                 // reduction partials
     msgb::DBuf<unsigned int> w_cnt;           // reduction counters
@@ -259,7 +260,7 @@ void launch_check_perm(const double *perm, int64_t count, int *flag, cudaStream_
 // sparse
 void launch_spmv(const ms_system &s, const double *x, double *y, cudaStream_t st);
 void launch_residual(const ms_system &s, const double *q, const double *x, double *r, double *red,
-                     unsigned int *cnt, double *norm_out, cudaStream_t st);
+                     unsigned int *cnt, double *norm_out, cudaStream_t st, float *r32 = nullptr);
 void launch_residual_update(const ms_system &s, double *r, double *x, const double *z, cudaStream_t st);
 void launch_residual_update32(const ms_system &s, const double *r, float *r32, double *x, const float *z,
                               cudaStream_t st);
@@ -282,6 +283,7 @@ void launch_ilu_apply32(ms_system &s, const double *r, float *y, float *z, cudaS
 void launch_ilu_extract_dirs(ms_system &s, bool fp32, cudaStream_t st);
 void launch_ilu_tiled64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st);
 void launch_ilu_tiled32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st);
+void launch_ilu_tiled32f(ms_system &s, const float *r, float *y, float *z, cudaStream_t st);
 // basis
 void launch_basis_init(ms_basis &b, int n, cudaStream_t st);
 void launch_basis_maps(const ms_system &s, ms_basis &b, cudaStream_t st);
