@@ -199,6 +199,35 @@ ms_status ms_spmv(ms_ctx *ctx, const ms_system *sys, const double *x, double *y)
  * FP64 or FP32 factors. */
 ms_status ms_ilu_apply(ms_ctx *ctx, ms_system *sys, int32_t precision, const double *r, double *z);
 
+/* Allocation-free ILU(0) application.  The paper has no counterpart: this
+ * is a deployment variant of ms_ilu_apply for callers that cannot allocate
+ * at the point of the call -- for example an application that has handed
+ * all free device memory to its own pool allocator, or a latency-critical
+ * loop that cannot afford an allocation's implicit device synchronisation
+ * or its failure under memory pressure.  It computes z = (L U)^{-1} r with
+ * the system's FP64 factors by the level-ordered sweeps, keeping every
+ * scratch buffer (sweep counters, per-row completion flags, the
+ * forward-sweep vector) in one fixed device array inside the library: the
+ * call performs no cudaMalloc, cudaFree or other allocating call.
+ *  - Limit: n <= 1,048,576 unknowns.  The array takes 12 MiB + 256 bytes on
+ *    every GPU that loads the library, until the process exits.  Larger
+ *    systems return MS_ERR_INVALID_ARG.
+ *  - r and z must be device memory of the context's device (host arrays
+ *    would need staging buffers): otherwise MS_ERR_INVALID_ARG.
+ *  - The FP64 ILU(0) factors of the current assembly must already exist
+ *    (made by an earlier ms_ilu_apply or ms_solve with the ILU(0)
+ *    smoother); otherwise MS_ERR_STATE.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture.
+ *  - Every call shares the one array and it keeps the last call's contents;
+ *    each call clears the counters that must start at zero.  Calls that
+ *    overlap on the GPU race on the array: do not overlap them.
+ *  - Results equal ms_ilu_apply's up to rounding (on structured grids
+ *    ms_ilu_apply uses the tiled sweeps).  Waits for the context's stream
+ *    before returning, to report a timed-out sweep as MS_ERR_TIMEOUT. */
+ms_status ms_ilu_apply_noalloc(ms_ctx *ctx, const ms_system *sys, const double *r, double *z);
+
 /* ------------------------------------------------------------- partitions */
 /* General structured partition (Sec. 5: non-overlapping coarse blocks;
  * Sec. 5.1 general partitions): cell (i,j,k) goes to Cartesian block

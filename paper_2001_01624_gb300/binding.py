@@ -96,6 +96,7 @@ def lib():
         "ms_system_get_matrix": ([_vp, _vp, _i32, _vp, _vp, _vp], _i32),
         "ms_spmv": ([_vp, _vp, _vp, _vp], _i32),
         "ms_ilu_apply": ([_vp, _vp, _i32, _vp, _vp], _i32),
+        "ms_ilu_apply_noalloc": ([_vp, _vp, _vp, _vp], _i32),
         "ms_partition_cartesian": ([_vp, _vp, _i32, _i32, _i32, _vp, P(_i32)], _i32),
         "ms_partition_components": ([_vp, _vp, _vp, _vp, P(_i32)], _i32),
         "ms_partition_dynamic": ([_vp, _vp, _vp, _i32, _d, _vp, P(_i32)], _i32),
@@ -126,7 +127,7 @@ def lib():
 def exported_symbols() -> Sequence[str]:
     return ["ms_abi_version", "ms_status_string", "ms_last_error", "ms_create", "ms_destroy", "ms_set_stream",
             "ms_system_create", "ms_system_release", "ms_system_get_info", "ms_assemble_tpfa",
-            "ms_system_get_matrix", "ms_spmv", "ms_ilu_apply", "ms_partition_cartesian", "ms_partition_components", "ms_partition_dynamic",
+            "ms_system_get_matrix", "ms_spmv", "ms_ilu_apply", "ms_ilu_apply_noalloc", "ms_partition_cartesian", "ms_partition_components", "ms_partition_dynamic",
             "ms_build_basis", "ms_basis_rebuild", "ms_basis_update", "ms_basis_release", "ms_basis_get_info",
             "ms_basis_get", "ms_add_adaptive_basis", "ms_galerkin", "ms_coarse_refresh", "ms_coarse_release",
             "ms_coarse_get", "ms_solve", "ms_profile_enable", "ms_profile_reset", "ms_profile_read"]
@@ -246,6 +247,11 @@ def ms_spmv(ctx, sys, x, y):
 
 def ms_ilu_apply(ctx, sys, r, z, precision: int = MS_PREC_FP64):
     _check(lib().ms_ilu_apply(ctx, sys, precision, _ptr(_as(r, np.float64)), _ptr(z)), ctx)
+
+
+def ms_ilu_apply_noalloc(ctx, sys, r, z):
+    """Allocation-free ILU(0) application: r and z must be device tensors."""
+    _check(lib().ms_ilu_apply_noalloc(ctx, sys, _ptr(r), _ptr(z)), ctx)
 
 
 # --------------------------------------------------------------- partitions

@@ -241,3 +241,20 @@ void launch_ilu_apply32(ms_system &s, const double *r, float *y, float *z, cudaS
 }
 
 }  // namespace msgb
+
+namespace msgb {
+
+// Level-ordered FP64 sweeps with caller-provided scratch: the intermediate
+// vector y (n doubles), per-row flags (n ints) and the sweep words (8 ints).
+// No tracing scope here: the allocation-free entry point uses this launcher.
+void launch_ilu_apply64_scratch(const ms_system &s, const double *r, double *y, double *z, int *flags, int *sync,
+                                cudaStream_t st) {
+    k_ilu_fwd<double, double><<<sweep_blocks(s), kSweepThreads, 0, st>>>(s.n, s.W, s.ntot, s.lperm.p, s.col.p,
+                                                                          s.lu64.p, r, y, flags, sync);
+    MS_CHECK_LAUNCH();
+    k_ilu_bwd<double><<<sweep_blocks(s), kSweepThreads, 0, st>>>(s.n, s.W, s.ntot, s.lperm.p, s.col.p, s.lu64.p,
+                                                                 s.dinv64.p, y, z, flags, sync);
+    MS_CHECK_LAUNCH();
+}
+
+}  // namespace msgb

@@ -281,6 +281,8 @@ void launch_ilu_factor(ms_system &s, bool fp32, cudaStream_t st);
 void launch_ilu_apply64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st);
 void launch_ilu_apply32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st);
 void launch_ilu_extract_dirs(ms_system &s, bool fp32, cudaStream_t st);
+void launch_ilu_apply64_scratch(const ms_system &s, const double *r, double *y, double *z, int *flags, int *sync,
+                                cudaStream_t st);
 void launch_ilu_tiled64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st);
 void launch_ilu_tiled32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st);
 void launch_ilu_tiled32f(ms_system &s, const float *r, float *y, float *z, cudaStream_t st);
