@@ -205,6 +205,36 @@ void analyse_grid(ms_system &s, const ms_grid &g) {
         s.face_k.zero(nullptr);
         s.tile_progress.alloc(2 * order.size());   // 16 bytes per tile (fetched with 16-byte async copies)
         s.tile_progress.zero(nullptr);
+        // line-scan tiles: LTK warps (one k-row of x-lines each) x LTJ lines in j.
+        // Shared memory per warp (worst case FP64 backward sweep, 4-slot ring):
+        // exchange 2 + ring 4 x 5 lines of 8 bytes, plus the k-face ring.
+        const int E = (nx + 31) / 32, LW = 32 * E;
+        if (E <= 8) {
+            const size_t per_warp = (size_t)LW * 8 * (2 + 4 * 5);
+            int ltk = (int)std::min<size_t>(8, (200 * 1024 - (size_t)4 * LW * 16) / per_warp);
+            ltk = std::max(1, std::min(ltk, nz));
+            int ltj = std::min(ny, 32);
+            if (const char *e = std::getenv("MSGB_LINE_TILE")) {     // tuning override "TJxTK"
+                int a = 0, b = 0;
+                if (std::sscanf(e, "%dx%d", &a, &b) == 2 && a > 0 && b > 0 && b <= 8 &&
+                    (size_t)b * per_warp + (size_t)4 * LW * 16 <= 220 * 1024) { ltj = a; ltk = b; }
+            }
+            s.LTJ = ltj; s.LTK = ltk;
+            s.LNJ = (ny + ltj - 1) / ltj; s.LNK = (nz + ltk - 1) / ltk;
+            std::vector<int> lorder;
+            for (int d = 0; d <= s.LNJ + s.LNK - 2; ++d)
+                for (int J = 0; J < s.LNJ; ++J) {
+                    const int K = d - J;
+                    if (K >= 0 && K < s.LNK) lorder.push_back(J + s.LNJ * K);
+                }
+            s.line_order.upload(lorder, nullptr);
+            s.lface_j.alloc((size_t)lorder.size() * ltk * nx * 2);
+            s.lface_k.alloc((size_t)lorder.size() * ltj * nx * 2);
+            s.line_progress.alloc(2 * lorder.size());
+            s.lface_j.zero(nullptr);
+            s.lface_k.zero(nullptr);
+            s.line_progress.zero(nullptr);
+        }
     }
 
     // host copies + device upload

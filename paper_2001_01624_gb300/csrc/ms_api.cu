@@ -113,14 +113,23 @@ void ensure_ilu(ms_ctx *ctx, ms_system &s, bool fp32) {
 
 // z = (LU)^{-1} r: tiled wavefront sweeps on structured grids, level-ordered
 // sweeps otherwise.
+// (line-scan sweeps when the x-lines fit a warp's registers, pencil tiles for
+// longer lines)
 void ilu_apply64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st) {
-    if (s.structured) launch_ilu_tiled64(s, r, y, z, st);
+    if (lines_supported(s)) launch_ilu_lines64(s, r, y, z, st);
+    else if (s.structured) launch_ilu_tiled64(s, r, y, z, st);
     else launch_ilu_apply64(s, r, y, z, st);
 }
 
 void ilu_apply32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st) {
-    if (s.structured) launch_ilu_tiled32(s, r, y, z, st);
+    if (lines_supported(s)) launch_ilu_lines32(s, r, y, z, st);
+    else if (s.structured) launch_ilu_tiled32(s, r, y, z, st);
     else launch_ilu_apply32(s, r, y, z, st);
+}
+
+void ilu_apply32f(ms_system &s, const float *r, float *y, float *z, cudaStream_t st) {
+    if (lines_supported(s)) launch_ilu_lines32f(s, r, y, z, st);
+    else launch_ilu_tiled32f(s, r, y, z, st);
 }
 
 // Smooth a basis: reset from the indicator (reset) or continue; returns iterations.
@@ -715,7 +724,7 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
             // r holds q - A x here
             if (mixed) {
                 if (opts->smoother == MS_SMOOTHER_ILU0) {
-                    if (s->structured) launch_ilu_tiled32f(*s, s->w_rin32.p, s->w_y32.p, s->w_z32.p, st);
+                    if (s->structured) ilu_apply32f(*s, s->w_rin32.p, s->w_y32.p, s->w_z32.p, st);
                     else ilu_apply32(*s, s->w_r.p, s->w_y32.p, s->w_z32.p, st);
                 }
                 else launch_jacobi32(*s, s->w_r.p, s->w_z32.p, (float)jw, st);

@@ -167,6 +167,10 @@ struct ms_system {
     msgb::DBuf<int> tile_order;
     msgb::DBuf<unsigned long long> face_j, face_k;   // tagged tile-face exchange buffers
     msgb::DBuf<unsigned long long> tile_progress;    // tagged per-tile progress hints
+    // line-scan sweeps: TK warps per CTA walk TJ x TK tiles of x-lines
+    int LTJ = 0, LTK = 0, LNJ = 0, LNK = 0;
+    msgb::DBuf<int> line_order;
+    msgb::DBuf<unsigned long long> lface_j, lface_k, line_progress;
     msgb::DBuf<double> dcoef64;               // [6*n]: L(-x,-y,-z), U(+x,+y,+z)
     msgb::DBuf<float> dcoef32;
     msgb::DBuf<int> lperm;
@@ -286,6 +290,10 @@ void launch_ilu_apply64_scratch(const ms_system &s, const double *r, double *y, 
 void launch_ilu_tiled64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st);
 void launch_ilu_tiled32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st);
 void launch_ilu_tiled32f(ms_system &s, const float *r, float *y, float *z, cudaStream_t st);
+bool lines_supported(const ms_system &s);
+void launch_ilu_lines64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st);
+void launch_ilu_lines32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st);
+void launch_ilu_lines32f(ms_system &s, const float *r, float *y, float *z, cudaStream_t st);
 // basis
 void launch_basis_init(ms_basis &b, int n, cudaStream_t st);
 void launch_basis_maps(const ms_system &s, ms_basis &b, cudaStream_t st);

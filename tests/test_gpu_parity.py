@@ -360,11 +360,13 @@ def test_mixed_precision_solve(ms, ctx, case):
 
 # ------------------------------------------------- tiled wavefront ILU(0)
 @pytest.mark.parametrize("tile", ["4x2", "8x1", "3x3", "32x8", "1x4"])
-@pytest.mark.parametrize("shape", [(9, 13, 7), (6, 40, 1), (17, 5, 11)])
+@pytest.mark.parametrize("shape", [(9, 13, 7), (6, 40, 1), (17, 5, 11), (300, 7, 3)])
 def test_tiled_ilu_sweeps_across_tiles(ms, ctx, monkeypatch, tile, shape):
-    """Structured grids use the tiled wavefront sweeps; small tiles force many
-    CTAs, ragged last tiles and cross-tile waits."""
+    """Structured grids use the tiled wavefront sweeps (x-line scans, or
+    x-pencils for lines longer than 256 cells); small tiles force many CTAs,
+    ragged last tiles and cross-tile hand-overs."""
     monkeypatch.setenv("MSGB_ILU_TILE", tile)
+    monkeypatch.setenv("MSGB_LINE_TILE", tile)
     gm = G.lognormal_box(*shape, seed=31, block=(3, 4, 2), kz_ratio=0.1)
     s = _system(ms, ctx, gm)
     ref = O.assemble_tpfa(gm.grid, gm.perm)
