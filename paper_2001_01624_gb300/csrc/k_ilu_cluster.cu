@@ -1,0 +1,484 @@
+// ILU(0) triangular sweeps on structured grids: line scan pipelined across
+// one thread-block cluster.
+//
+// Natural-order ILU(0) on the 7-point pattern (the smoother of the second
+// stage of the multistage cycle, Sec. 3): the forward sweep is
+//     y(x,j,k) = r - Lx y(x-1,j,k) - Ly y(x,j-1,k) - Lz y(x,j,k-1),
+// the backward sweep the mirror image with U and the reciprocal diagonal.
+// Given the neighbouring x-lines (j-1,k) and (j,k-1), the x-line (j,k) is the
+// first-order recurrence v(x) = A(x) v(x-1) + B(x), which one warp solves with
+// an affine shuffle scan (E consecutive cells per lane).
+//
+// Every k-row of x-lines is owned by one warp, which walks its row along j
+// and keeps the previous line (the j-neighbour) in registers.  Row g needs
+// line j of row g-1 (the k-neighbour): rows hand finished lines to the next
+// row through a small ring of shared-memory buffers guarded by mbarriers
+// (full / empty), so each row waits only for its own neighbour instead of for
+// a block-wide barrier, and rows drift into a natural wavefront.  The rows are
+// split over the CTAs of one cluster (TK rows per CTA).  A line is handed over
+// with asynchronous stores into the next row's buffer (in the next CTA for the
+// last row of a CTA, through distributed shared memory) that count as
+// transaction bytes on the receiver's barrier, so no release fence is needed
+// and a CTA boundary costs the same as a warp boundary; the receiver re-arms
+// its barrier with the expected byte count when it frees the buffer.  A
+// producer warp per CTA streams each row's inputs (the packed coefficient line
+// and the right-hand-side line, one bulk copy each) into a ring of
+// shared-memory slots, independently per row.
+//
+// Coefficients are packed four per cell (x, y, z neighbour and a fourth
+// entry: zero forward, the reciprocal diagonal backward), so a coefficient
+// line starts on a 16-byte boundary and is one bulk copy.  All waits are
+// bounded in device time and report a timeout instead of hanging.
+#include "ms_internal.h"
+
+namespace msgb {
+
+namespace {
+
+constexpr int RF = 4;    // fetch ring: lines in flight per row
+constexpr int NBX = 4;   // row-exchange ring: lines a row may run ahead of the next
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mb_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mb_expect(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mb_try(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mb_test(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned map_cta(unsigned addr, unsigned rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+// relaxed arrivals: no ordering of earlier memory operations is needed (the
+// data they guard travels with transaction bytes, or was consumed already)
+__device__ __forceinline__ void mb_arrive_relaxed(unsigned bar) {
+    asm volatile("mbarrier.arrive.relaxed.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mb_arrive_relaxed_remote(unsigned cbar) {
+    asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(cbar) : "memory");
+}
+__device__ __forceinline__ void mb_expect_relaxed(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.relaxed.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// asynchronous store into the shared memory of a CTA of the cluster (this one
+// included), counted as transaction bytes on that CTA's barrier
+__device__ __forceinline__ void st_async2(unsigned addr, float a, float b, unsigned cbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(addr), "f"(a),
+                 "f"(b), "r"(cbar)
+                 : "memory");
+}
+__device__ __forceinline__ void st_async2(unsigned addr, double a, double b, unsigned cbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];" ::"r"(addr), "d"(a),
+                 "d"(b), "r"(cbar)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_up(T v, int d) {
+    return __shfl_up_sync(0xffffffffu, v, d);
+}
+
+// wait for a barrier phase, bounded; the result is uniform across the warp
+__device__ __forceinline__ bool wait_phase(unsigned bar, unsigned parity, int *err) {
+    unsigned long long t0 = 0;
+    int spins = 0;
+    bool ok = true;
+    while (!mb_try(bar, parity)) {
+        if ((++spins & 63) == 0) {
+            const unsigned long long now = global_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > kWaitNs) {
+                atomicOr(err, kErrTimeout);
+                ok = false;
+                break;
+            }
+        }
+    }
+    return __all_sync(0xffffffffu, ok);
+}
+
+// the four packed coefficients of one cell
+template <typename T>
+struct Coef4 {
+    T a, b, c, d;
+};
+__device__ __forceinline__ Coef4<float> load_coef(const float *p) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Coef4<double> load_coef(const double *p) {
+    const double2 u = reinterpret_cast<const double2 *>(p)[0], v = reinterpret_cast<const double2 *>(p)[1];
+    return {u.x, u.y, v.x, v.y};
+}
+
+// rhs window: the line plus 16 bytes of alignment slack on each side, a multiple of 16 bytes
+__host__ __device__ constexpr int rhs_win(int nx, int esz) {
+    return (nx + 3 * (16 / esz) + 16 / esz - 1) / (16 / esz) * (16 / esz);
+}
+
+template <typename T, typename TR, bool BWD, int E>
+__global__ void __launch_bounds__(544, 1)
+    k_line_cluster(int nx, int ny, int nz, int TK, const T *__restrict__ coef4, const TR *__restrict__ rhs,
+                   T *__restrict__ out, int *err) {
+    constexpr int LW = 32 * E;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const unsigned K = cluster_rank();
+    const int WR = rhs_win(nx, sizeof(TR));
+    const int CLN = nx * 4;   // packed coefficient line (elements of T)
+    // shared: coefficient slots [RF][TK][CLN] T | rhs slots [RF][TK][WR] TR | exchange [TK][NBX][LW] T |
+    //         barriers full_f, empty_f [RF][TK], full_x, empty_x [NBX][TK]
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *cwin = reinterpret_cast<T *>(smraw);
+    size_t off = (size_t)RF * TK * CLN * sizeof(T);
+    TR *rwin = reinterpret_cast<TR *>(smraw + off);
+    off += (size_t)RF * TK * WR * sizeof(TR);
+    T *xin = reinterpret_cast<T *>(smraw + off);
+    off += (size_t)TK * NBX * LW * sizeof(T);
+    const unsigned full_f = smem_u32(smraw + off);
+    const unsigned empty_f = full_f + 8 * RF * TK;
+    const unsigned full_x = empty_f + 8 * RF * TK;
+    const unsigned empty_x = full_x + 8 * NBX * TK;
+
+    if (tid < TK) {
+        for (int q = 0; q < RF; ++q) {
+            mb_init(full_f + 8 * (q * TK + tid), 1);
+            mb_init(empty_f + 8 * (q * TK + tid), 1);
+        }
+        for (int b = 0; b < NBX; ++b) {
+            mb_init(full_x + 8 * (b * TK + tid), 1);
+            mb_init(empty_x + 8 * (b * TK + tid), 1);
+        }
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    cluster_sync_all();
+
+    const long long plane = (long long)nx * ny;
+    const long long dj = BWD ? -(long long)nx : (long long)nx;   // real index step from line j to j+1 (mirrored)
+    if (w == TK) {
+        // producer warp: lane r streams the inputs of row r, each row on its own
+        const int g = (int)K * TK + lane;
+        int tj = (lane < TK && g < nz) ? 0 : ny;
+        const int kr = BWD ? nz - 1 - g : g;
+        const long long base0 = (long long)nx * (BWD ? ny - 1 : 0) + plane * kr;
+        const unsigned lc = (unsigned)nx * 4 * sizeof(T);
+        unsigned long long t0 = 0;
+        int idle = 0;
+        while (__any_sync(0xffffffffu, tj < ny)) {
+            bool issued = false;
+            if (tj < ny) {
+                const int q = tj % RF;
+                const unsigned u = (unsigned)(tj / RF);
+                if (tj < RF || mb_test(empty_f + 8 * (q * TK + lane), (u - 1) & 1u)) {
+                    const long long base = base0 + dj * tj;
+                    const unsigned fb = full_f + 8 * (q * TK + lane);
+                    // the rhs line rounded out to 16-byte granules (never leaving the
+                    // granule of a valid address, so inside the mapped allocation)
+                    const unsigned long long ar = (unsigned long long)(size_t)(rhs + base);
+                    const unsigned long long a0 = ar & ~15ull;
+                    const unsigned lr = (unsigned)(((ar + (unsigned long long)nx * sizeof(TR) + 15ull) & ~15ull) - a0);
+                    mb_expect(fb, lc + lr);
+                    bulk_g2s(smem_u32(cwin + (size_t)(q * TK + lane) * CLN), coef4 + base * 4, lc, fb);
+                    bulk_g2s(smem_u32(rwin + (size_t)(q * TK + lane) * WR), (const void *)(size_t)a0, lr, fb);
+                    ++tj;
+                    issued = true;
+                }
+            }
+            if (__any_sync(0xffffffffu, issued)) {
+                t0 = 0;
+            } else {
+                __nanosleep(32);
+                if ((++idle & 63) == 0) {
+                    const unsigned long long now = __shfl_sync(0xffffffffu, global_ns(), 0);
+                    if (t0 == 0) t0 = now;
+                    else if (now - t0 > kWaitNs) {
+                        if (lane == 0) atomicOr(err, kErrTimeout);
+                        break;
+                    }
+                }
+            }
+        }
+    } else if (w < TK && (int)K * TK + w < nz) {
+        const int g = (int)K * TK + w;
+        const int kr = BWD ? nz - 1 - g : g;
+        const long long base0 = (long long)nx * (BWD ? ny - 1 : 0) + plane * kr;
+        const bool has_src = g > 0, has_dst = g + 1 < nz;
+        const bool src_remote = w == 0, dst_remote = w == TK - 1;
+        // a line handed to the next row: LW values, all lanes' E values (cells past nx are padding)
+        constexpr unsigned XB = LW * sizeof(T);
+        if (has_src && lane == 0)
+            for (int b = 0; b < NBX && b < ny; ++b) mb_expect_relaxed(full_x + 8 * (b * TK + w), XB);
+        // where this row's lines go: the next row's exchange ring, here or in CTA K+1
+        const unsigned dst_rank = dst_remote ? K + 1 : K;
+        const int dst_w = dst_remote ? 0 : w + 1;
+        const unsigned dst_xin = map_cta(smem_u32(xin + (size_t)dst_w * NBX * LW + lane * E), dst_rank);
+        const unsigned dst_full = map_cta(full_x + 8 * dst_w, dst_rank);
+        // where to release the lines this row read: the previous row's empty ring, here or in CTA K-1
+        const unsigned src_empty = has_src ? map_cta(empty_x + 8 * (src_remote ? TK - 1 : w - 1), src_remote ? K - 1 : K) : 0u;
+        T prev[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) prev[e] = T(0);
+        for (int tj = 0; tj < ny; ++tj) {
+            const int q = tj % RF, b = tj % NBX;
+            const unsigned u = (unsigned)(tj / RF), ub = (unsigned)(tj / NBX);
+            if (!wait_phase(full_f + 8 * (q * TK + w), u & 1u, err)) break;
+            T nk[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) nk[e] = T(0);
+            if (has_src) {
+                if (!wait_phase(full_x + 8 * (b * TK + w), ub & 1u, err)) break;
+                const T *xi = xin + ((size_t)w * NBX + b) * LW + lane * E;
+#pragma unroll
+                for (int e = 0; e < E; ++e) nk[e] = xi[e];
+            }
+            const long long base = base0 + dj * tj;
+            const int shr = (int)((((unsigned)(size_t)rhs + (unsigned)base * (unsigned)sizeof(TR)) & 15u) / sizeof(TR));
+            const T *cl = cwin + (size_t)(q * TK + w) * CLN;
+            const TR *rl = rwin + (size_t)(q * TK + w) * WR + shr;
+            T A[E], B[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int at = lane * E + e;
+                A[e] = T(1);
+                B[e] = T(0);
+                if (at < nx) {
+                    const int x = BWD ? nx - 1 - at : at;   // real x of the cell
+                    const Coef4<T> c = load_coef(cl + 4 * x);
+                    T bb = (T)rl[x] - c.b * prev[e] - c.c * nk[e];
+                    T aa = -c.a;
+                    if (BWD) {
+                        bb *= c.d;
+                        aa *= c.d;
+                    }
+                    A[e] = aa;
+                    B[e] = bb;
+                }
+            }
+            T LA = A[0], LB = B[0];
+#pragma unroll
+            for (int e = 1; e < E; ++e) {
+                LB = A[e] * LB + B[e];
+                LA = A[e] * LA;
+            }
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const T pa = shfl_up(LA, d), pb = shfl_up(LB, d);
+                if (lane >= d) {
+                    LB = LA * pb + LB;
+                    LA = LA * pa;
+                }
+            }
+            T v = shfl_up(LB, 1);
+            if (lane == 0) v = T(0);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                v = A[e] * v + B[e];
+                prev[e] = v;
+            }
+            // every lane's reads of slot q and of exchange buffer b fed the scan, so
+            // they are complete: hand both back
+            if (lane == 0) {
+                mb_arrive_relaxed(empty_f + 8 * (q * TK + w));
+                if (has_src) {
+                    if (tj + NBX < ny) mb_expect_relaxed(full_x + 8 * (b * TK + w), XB);
+                    if (src_remote) mb_arrive_relaxed_remote(src_empty + 8 * b * TK);
+                    else mb_arrive_relaxed(src_empty + 8 * b * TK);
+                }
+            }
+            if (has_dst) {
+                if (tj >= NBX && !wait_phase(empty_x + 8 * (b * TK + w), (ub - 1) & 1u, err)) break;
+                const unsigned xo = dst_xin + (unsigned)(b * LW * sizeof(T)), fb = dst_full + 8 * b * TK;
+#pragma unroll
+                for (int e = 0; e < E; e += 2) st_async2(xo + e * (unsigned)sizeof(T), prev[e], prev[e + 1], fb);
+            }
+            T *ob = out + base;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int at = lane * E + e;
+                if (at < nx) ob[BWD ? nx - 1 - at : at] = prev[e];
+            }
+        }
+    }
+    cluster_sync_all();   // no CTA leaves while a neighbour may still touch its shared memory
+}
+
+template <typename T>
+__global__ void k_pack_coef4(int n, const T *__restrict__ dcoef, const T *__restrict__ dinv, T *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T *l = out + (size_t)i * 4, *u = out + ((size_t)n + i) * 4;
+    l[0] = dcoef[i];
+    l[1] = dcoef[(size_t)n + i];
+    l[2] = dcoef[(size_t)2 * n + i];
+    l[3] = T(0);
+    u[0] = dcoef[(size_t)3 * n + i];
+    u[1] = dcoef[(size_t)4 * n + i];
+    u[2] = dcoef[(size_t)5 * n + i];
+    u[3] = dinv[i];
+}
+
+inline int line_cells(int nx) { return nx <= 64 ? 2 : nx <= 128 ? 4 : 8; }
+
+template <typename T, typename TR>
+size_t cluster_smem(int nx, int TK) {
+    const int LW = 32 * line_cells(nx);
+    return (size_t)RF * TK * nx * 4 * sizeof(T) + (size_t)RF * TK * rhs_win(nx, sizeof(TR)) * sizeof(TR) +
+           (size_t)TK * NBX * LW * sizeof(T) + (size_t)8 * 2 * (RF + NBX) * TK;
+}
+
+template <typename T, typename TR, bool BWD, int E>
+cudaError_t launch_cluster_e(const ms_system &s, int TK, int NK, const T *coef4, const TR *rhs, T *out,
+                             cudaStream_t st, bool query_only, int *clusters) {
+    auto kern = k_line_cluster<T, TR, BWD, E>;
+    const size_t smem = cluster_smem<T, TR>(s.nx, TK);
+    static size_t smem_set = 0;       // per instantiation: attributes are raised once
+    static bool nonportable = false;
+    cudaError_t e = cudaSuccess;
+    if (smem > smem_set) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        smem_set = smem;
+    }
+    if (NK > 8 && !nonportable) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        nonportable = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(NK, 1, 1);
+    cfg.blockDim = dim3(32 * (TK + 1), 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = NK;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (query_only) return cudaOccupancyMaxActiveClusters(clusters, kern, &cfg);
+    return cudaLaunchKernelEx(&cfg, kern, s.nx, s.ny, s.nz, TK, coef4, rhs, out, s.sync.p + 3);
+}
+
+template <typename T, typename TR, bool BWD>
+cudaError_t launch_cluster(const ms_system &s, int TK, int NK, const T *coef4, const TR *rhs, T *out,
+                           cudaStream_t st, bool query_only = false, int *clusters = nullptr) {
+    switch (line_cells(s.nx)) {
+        case 2: return launch_cluster_e<T, TR, BWD, 2>(s, TK, NK, coef4, rhs, out, st, query_only, clusters);
+        case 4: return launch_cluster_e<T, TR, BWD, 4>(s, TK, NK, coef4, rhs, out, st, query_only, clusters);
+        default: return launch_cluster_e<T, TR, BWD, 8>(s, TK, NK, coef4, rhs, out, st, query_only, clusters);
+    }
+}
+
+template <typename T, typename TR>
+void cluster_apply(ms_system &s, const T *coef4, const TR *r, T *y, T *z, cudaStream_t st) {
+    const int64_t n = s.n;
+    const int p = sizeof(T) == 8 ? 0 : 1;
+    const double nl = (double)s.nnz_lower;
+    {
+        KernelScope ks_(st, sizeof(T) == 8 ? "ilu_fwd" : "ilu_fwd32", nl * sizeof(T) + (double)n * (sizeof(TR) + sizeof(T)));
+        const cudaError_t e = launch_cluster<T, TR, false>(s, s.cl_TK[p], s.cl_NK[p], coef4, r, y, st);
+        MS_CUDA(e);
+    }
+    KernelScope ks_(st, sizeof(T) == 8 ? "ilu_bwd" : "ilu_bwd32", nl * sizeof(T) + (double)n * 3 * sizeof(T));
+    const cudaError_t e = launch_cluster<T, T, true>(s, s.cl_TK[p], s.cl_NK[p], coef4 + (size_t)4 * n, y, z, st);
+    MS_CUDA(e);
+}
+
+// Rows per CTA and cluster size for one precision: the cluster spans all k-rows,
+// at most 16 CTAs (more than 8 needs the non-portable size) of at most 16 rows,
+// within the shared-memory limit, and the launch must be schedulable.
+template <typename T, typename TR>
+bool plan_precision(ms_system &s, int p) {
+    if (s.nx > 256 || s.ny < 1 || s.nz < 1) return false;
+    for (int C : {16, 8}) {
+        const int TK = (s.nz + C - 1) / C;
+        if (TK > 16) continue;
+        const int NK = (s.nz + TK - 1) / TK;
+        if (cluster_smem<T, TR>(s.nx, TK) > 220 * 1024 || cluster_smem<T, T>(s.nx, TK) > 220 * 1024) continue;
+        int c1 = 0, c2 = 0;
+        if (launch_cluster<T, TR, false>(s, TK, NK, nullptr, nullptr, nullptr, nullptr, true, &c1) != cudaSuccess ||
+            launch_cluster<T, T, true>(s, TK, NK, nullptr, nullptr, nullptr, nullptr, true, &c2) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (c1 >= 1 && c2 >= 1) {
+            s.cl_TK[p] = TK;
+            s.cl_NK[p] = NK;
+            return true;
+        }
+    }
+    return false;
+}
+
+}  // namespace
+
+void plan_ilu_cluster(ms_system &s) {
+    s.cl_ok[0] = plan_precision<double, double>(s, 0);
+    s.cl_ok[1] = plan_precision<float, double>(s, 1) && plan_precision<float, float>(s, 1);
+}
+
+void launch_ilu_pack_coef4(ms_system &s, bool fp32, cudaStream_t st) {
+    const int g = (s.n + 255) / 256;
+    if (fp32) {
+        s.coef4_32.alloc((size_t)8 * s.n);
+        k_pack_coef4<float><<<g, 256, 0, st>>>(s.n, s.dcoef32.p, s.dinv32.p, s.coef4_32.p);
+    } else {
+        s.coef4_64.alloc((size_t)8 * s.n);
+        k_pack_coef4<double><<<g, 256, 0, st>>>(s.n, s.dcoef64.p, s.dinv64.p, s.coef4_64.p);
+    }
+    MS_CHECK_LAUNCH();
+}
+
+void launch_ilu_cluster64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st) {
+    cluster_apply<double, double>(s, s.coef4_64.p, r, y, z, st);
+}
+
+void launch_ilu_cluster32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st) {
+    cluster_apply<float, double>(s, s.coef4_32.p, r, y, z, st);
+}
+
+void launch_ilu_cluster32f(ms_system &s, const float *r, float *y, float *z, cudaStream_t st) {
+    cluster_apply<float, float>(s, s.coef4_32.p, r, y, z, st);
+}
+
+}  // namespace msgb

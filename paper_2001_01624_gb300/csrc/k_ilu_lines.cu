@@ -15,12 +15,18 @@
 // TJ x TK tile of lines; warp w walks the k-row tk = w along j, one line per
 // step (line (tj, w) at step tj + w), keeping its previous line in registers
 // and passing each finished line to warp w + 1 through double-buffered shared
-// memory (one barrier per step).  Line inputs for step s + 1 are fetched with
-// per-lane async copies during step s (barriers do not wait on them).  Tiles
-// hand over their high j / k face lines as tagged words (payload + sweep
-// counter, validated by the consumer) and pace each other with tagged
-// per-tile progress hints; tickets follow a topological order of the tile
-// grid, and every wait is bounded.
+// memory (one barrier per step).  Lane 0 of each warp fetches the inputs of
+// its line RING - 1 steps ahead with bulk copies (one per array and line, the
+// line's span rounded out to 16 bytes) into a shared-memory ring, completing on
+// one mbarrier per warp and slot.  Tiles hand over their high j / k face lines
+// as tagged words (payload + sweep counter, validated by the consumer) and pace
+// each other with tagged per-tile progress hints; tickets follow a topological
+// order of the tile grid, and every wait is bounded.
+//
+// A step is short and its work is a chain of dependent instructions executed
+// by one or two warps per SM sub-partition, so the step time is set by that
+// chain's latency: the cell count per lane is a compile-time constant and all
+// per-line addressing is hoisted out of the step loop.
 #include "ms_internal.h"
 
 namespace msgb {
@@ -28,7 +34,6 @@ namespace msgb {
 namespace {
 
 constexpr long long kSpinLimit = 1ll << 24;
-constexpr int EMAX = 8;   // cells per lane: lines up to 256 cells
 
 __device__ __forceinline__ void st_tag(unsigned long long *p, unsigned payload, unsigned tag) {
     const unsigned long long w = ((unsigned long long)tag << 32) | payload;
@@ -41,20 +46,38 @@ __device__ __forceinline__ unsigned long long ld_tag(const unsigned long long *p
     return w;
 }
 
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void *smem_dst, const void *gsrc, bool valid) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    const int sb = valid ? BYTES : 0;
-    if (BYTES == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(sb) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(gsrc), "n"(BYTES), "r"(sb)
-                     : "memory");
+// Bulk (TMA-class) copies global -> shared completing on an mbarrier.
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(bar)), "r"(count)
+                 : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"((unsigned)__cvta_generic_to_shared(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void *smem_dst, const void *gsrc, unsigned bytes, unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            (unsigned)__cvta_generic_to_shared(smem_dst)),
+        "l"(gsrc), "r"(bytes), "r"((unsigned)__cvta_generic_to_shared(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
 
 template <typename T>
 struct Tag;
@@ -106,103 +129,131 @@ __device__ __forceinline__ T shfl_up(T v, int d) {
 
 constexpr int RING = 4;   // line inputs are fetched RING - 1 steps ahead
 
-template <typename T, typename TR, bool BWD>
-__global__ void __launch_bounds__(256) k_line_sweep(int nx, int ny, int nz, int TJ, int TK, int NJ, int NK, int E,
-                                                     const int *__restrict__ order, const T *__restrict__ c0,
-                                                     const T *__restrict__ c1, const T *__restrict__ c2,
-                                                     const T *__restrict__ dinv, const TR *__restrict__ rhs,
-                                                     T *__restrict__ out, unsigned long long *jface,
-                                                     unsigned long long *kface, unsigned long long *progress,
-                                                     int *sync) {
-    constexpr int NA = BWD ? 5 : 4;   // rhs, c0, c1, c2 (, dinv) ring arrays
+// Shared window per input array, warp and ring slot: the line plus up to 16
+// bytes of alignment slack on each side, a multiple of 16 bytes long.
+__host__ __device__ constexpr int win_elems(int nx, int esz) {
+    return (nx + 3 * (16 / esz) + 16 / esz - 1) / (16 / esz) * (16 / esz);
+}
+
+// One sweep (forward, or backward when BWD) over the tiles of the line grid;
+// E cells per lane (lines of up to 32 E cells).
+template <typename T, typename TR, bool BWD, int E>
+__global__ void __launch_bounds__(256, 1) k_line_sweep(int nx, int ny, int nz, int TJ, int TK, int NJ, int NK,
+                                                    const int *__restrict__ order, const T *__restrict__ c0,
+                                                    const T *__restrict__ c1, const T *__restrict__ c2,
+                                                    const T *__restrict__ dinv, const TR *__restrict__ rhs,
+                                                    T *__restrict__ out, unsigned long long *jface,
+                                                    unsigned long long *kface, unsigned long long *progress,
+                                                    int *sync) {
+    constexpr int NC = BWD ? 4 : 3;   // coefficient windows: c0, c1, c2 (, dinv)
+    constexpr int LW = 32 * E;
+    constexpr int SG = BWD ? -1 : 1;  // direction of x inside a line (cell order along the sweep)
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int LW = 32 * E;            // padded line length held by a warp
-    // shared: exchange [2][TK][LW] T | input ring [RING][NA-1][TK][LW] T | rhs ring [RING][TK][LW] TR |
-    //         k-face ring (warp 0) [RING][LW] x 16 B | progress ring [RING][2] x 16 B
+    const int WT = win_elems(nx, sizeof(T));
+    const int WR = win_elems(nx, sizeof(TR));
+    // shared: exchange [2][TK][LW] T | coefficient windows [RING][NC][TK][WT] T |
+    //         rhs windows [RING][TK][WR] TR | k-face windows (warp 0) [RING][nx] x 16 B | mbarriers [RING][TK]
     extern __shared__ __align__(16) unsigned char smraw[];
     T *xch = reinterpret_cast<T *>(smraw);
     size_t off = ((size_t)2 * TK * LW * sizeof(T) + 15) & ~(size_t)15;
-    T *ring = reinterpret_cast<T *>(smraw + off);
-    off += (size_t)RING * (NA - 1) * TK * LW * sizeof(T);
-    off = (off + 15) & ~(size_t)15;
-    TR *rring = reinterpret_cast<TR *>(smraw + off);
-    off += (size_t)RING * TK * LW * sizeof(TR);
-    off = (off + 15) & ~(size_t)15;
-    unsigned long long *kring = reinterpret_cast<unsigned long long *>(smraw + off);   // [RING][LW][2]
-    off += (size_t)RING * LW * 16;
-    unsigned long long *pring = reinterpret_cast<unsigned long long *>(smraw + off);   // [RING][2][2]
+    T *cwin = reinterpret_cast<T *>(smraw + off);
+    off += (size_t)RING * NC * TK * WT * sizeof(T);
+    TR *rwin = reinterpret_cast<TR *>(smraw + off);
+    off += (size_t)RING * TK * WR * sizeof(TR);
+    unsigned long long *kwin = reinterpret_cast<unsigned long long *>(smraw + off);
+    off += (size_t)RING * nx * 16;
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(smraw + off);
 
     __shared__ int s_vb, s_tgt;
     if (tid == 0) {
         s_vb = atomicAdd(&sync[1], 1);
         s_tgt = *((volatile int *)&sync[0]) + 1;
     }
+    if (lane == 0)
+        for (int q = 0; q < RING; ++q) mbar_init(&mbar[q * TK + w], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncthreads();
     const int tile = order[s_vb];
     const unsigned tag = (unsigned)s_tgt;
     const int J = tile % NJ, K = tile / NJ;
     const int steps = TJ + TK - 1;
-    const int km = K * TK + w;                       // mirrored k of this warp's row
+    const int km = K * TK + w;                           // mirrored k of this warp's row
     const bool rowlive = km < nz;
-    const int kr = BWD ? nz - 1 - km : km;           // real k
-    const long long plane = (long long)nx * ny;
+    const int kr = BWD ? nz - 1 - km : km;               // real k
+    const int nlive = min(TJ, ny - J * TJ);              // lines of this tile in j
     const int prodJ = J > 0 ? (J - 1) + NJ * K : -1;
     const int prodK = K > 0 ? J + NJ * (K - 1) : -1;
     const bool feedJ = J + 1 < NJ;
     const bool feedK = K + 1 < NK && w == TK - 1;
+    // real index of x = 0 of line tj: base0 + dj * tj
+    const long long plane = (long long)nx * ny;
+    const long long base0 = (long long)nx * (BWD ? ny - 1 - J * TJ : J * TJ) + plane * kr;
+    const long long dj = BWD ? -(long long)nx : (long long)nx;
+    // per-warp shared offsets (elements)
+    const int cw_w = w * WT, rw_w = w * WR;
+    const int cslot = NC * TK * WT, carr = TK * WT, rslot = TK * WR;
 
-    // real x of this lane's cell e, and whether it exists
-    auto xreal = [&](int e) { const int xm = lane * E + e; return BWD ? nx - 1 - xm : xm; };
-    auto xok = [&](int e) { return lane * E + e < nx; };
-
-    // line (tj, w) of this tile exists when the row is live and its j is inside the grid
-    auto line_j = [&](int tj) { return J * TJ + tj; };   // mirrored j
-    auto line_live = [&](int tj) { return rowlive && tj >= 0 && tj < TJ && line_j(tj) < ny; };
-    auto row_base = [&](int tj) {                         // real index of x = 0 of line (tj, w)
-        const int jm = line_j(tj);
-        const int jr = BWD ? ny - 1 - jm : jm;
-        return (long long)nx * jr + plane * kr;
+    // span of a line in a global array, rounded out to 16-byte granules (never
+    // leaving the granule of a valid address, so inside the mapped allocation)
+    auto span_len = [&](unsigned long long b0, int esz) {
+        return (unsigned)((((b0 + (unsigned long long)nx * esz) + 15ull) & ~15ull) - (b0 & ~15ull));
+    };
+    // lane 0 of each warp issues the bulk copies of line tj into ring slot q
+    auto fetch = [&](int q, int tj) {
+        if (lane != 0) return;
+        unsigned long long *bar = &mbar[q * TK + w];
+        if (!rowlive || tj < 0 || tj >= nlive) {
+            mbar_arrive_expect(bar, 0);
+            return;
+        }
+        const long long base = base0 + dj * tj;
+        const unsigned long long ar = (unsigned long long)(size_t)(rhs + base),
+                                 a0 = (unsigned long long)(size_t)(c0 + base),
+                                 a1 = (unsigned long long)(size_t)(c1 + base),
+                                 a2 = (unsigned long long)(size_t)(c2 + base),
+                                 a3 = BWD ? (unsigned long long)(size_t)(dinv + base) : 0ull;
+        const unsigned lr = span_len(ar, sizeof(TR)), l0 = span_len(a0, sizeof(T)), l1 = span_len(a1, sizeof(T)),
+                       l2 = span_len(a2, sizeof(T)), l3 = BWD ? span_len(a3, sizeof(T)) : 0u;
+        const bool kf = (w == 0 && prodK >= 0);
+        mbar_arrive_expect(bar, lr + l0 + l1 + l2 + l3 + (kf ? (unsigned)nx * 16 : 0u));
+        T *cq = cwin + q * cslot + cw_w;
+        bulk_g2s(rwin + q * rslot + rw_w, (const void *)(size_t)(ar & ~15ull), lr, bar);
+        bulk_g2s(cq, (const void *)(size_t)(a0 & ~15ull), l0, bar);
+        bulk_g2s(cq + carr, (const void *)(size_t)(a1 & ~15ull), l1, bar);
+        bulk_g2s(cq + 2 * carr, (const void *)(size_t)(a2 & ~15ull), l2, bar);
+        if (BWD) bulk_g2s(cq + 3 * carr, (const void *)(size_t)(a3 & ~15ull), l3, bar);
+        if (kf) bulk_g2s(kwin + (size_t)q * nx * 2, kface + (((long long)prodK * TJ + tj) * nx) * 2, (unsigned)nx * 16, bar);
+    };
+    // the copies read valid memory and always complete; the wait is still
+    // bounded (2 s of device time) and reports a timeout instead of hanging
+    auto wait_slot = [&](int q, unsigned parity) {
+        unsigned long long t0 = 0;
+        int spins = 0;
+        while (!mbar_try_wait(&mbar[q * TK + w], parity)) {
+            if ((++spins & 63) == 0) {
+                const unsigned long long now = global_ns();
+                if (t0 == 0) t0 = now;
+                else if (now - t0 > 2000000000ull) {
+                    atomicOr(&sync[3], kErrTimeout);
+                    break;
+                }
+            }
+        }
     };
 
-    // async fetch of the inputs of line tj into ring slot b (one commit group)
-    auto fetch = [&](int b, int tj) {
-        const bool live = line_live(tj);
-        const long long base = live ? row_base(tj) : 0;
-        for (int e = 0; e < E; ++e) {
-            const bool v = live && xok(e);
-            const long long c = v ? base + xreal(e) : 0;
-            const int at = lane * E + e;
-            cp_async<sizeof(TR)>(rring + ((size_t)b * TK + w) * LW + at, rhs + c, v);
-            cp_async<sizeof(T)>(ring + (((size_t)b * (NA - 1) + 0) * TK + w) * LW + at, c0 + c, v);
-            cp_async<sizeof(T)>(ring + (((size_t)b * (NA - 1) + 1) * TK + w) * LW + at, c1 + c, v);
-            cp_async<sizeof(T)>(ring + (((size_t)b * (NA - 1) + 2) * TK + w) * LW + at, c2 + c, v);
-            if (BWD) cp_async<sizeof(T)>(ring + (((size_t)b * (NA - 1) + 3) * TK + w) * LW + at, dinv + c, v);
-        }
-        // warp 0 also needs the k-face line (tj, TK-1) of tile (J, K-1)
-        if (w == 0 && prodK >= 0 && live) {
-            const unsigned long long *src = kface + (((long long)prodK * TJ + tj) * nx) * 2;
-            for (int e = 0; e < E; ++e)
-                cp_async<16>(kring + (((size_t)b * LW) + lane * E + e) * 2, src + (long long)(xok(e) ? lane * E + e : 0) * 2,
-                             xok(e));
-        }
-        if (tid == 0 && prodK >= 0) cp_async<16>(pring + (size_t)b * 4 + 2, progress + 2 * prodK, true);
-        cp_async_commit();
-    };
-
-    // pacing (thread 0): before the step-s barrier, producer (J, K-1) must have
-    // completed the step that makes the k-face line fetched during step s;
-    // j-face lines are taken (validated) when used, once per warp and tile
+    // pacing (thread 0): producer (J, K-1) must have completed the step that
+    // makes the k-face line fetched during step s; j-face lines are taken
+    // (validated) when used, once per warp and tile
     unsigned seenK = 0;
-    auto prog_of = [&](unsigned long long v) -> unsigned { return (unsigned)(v >> 32) == tag ? (unsigned)v : 0u; };
-    auto pace = [&](int s, int b) {
+    auto pace = [&](int s) {
         if (tid != 0 || prodK < 0) return;
-        const int ahead = s + RING - 1;   // line tj = ahead of warp 0 is fetched during step s
+        const int ahead = s + RING - 1;
         if (ahead >= TJ) return;
-        const unsigned needK = (unsigned)min(ahead + TK, steps);   // produced at producer step ahead + TK - 1
-        seenK = max(seenK, prog_of(pring[b * 4 + 2]));
+        const unsigned needK = (unsigned)min(ahead + TK, steps);
         long long spins = 0;
         while (seenK < needK) {
-            seenK = max(seenK, prog_of(ld_tag(progress + 2 * prodK)));
+            const unsigned long long v = ld_tag(progress + 2 * prodK);
+            if ((unsigned)(v >> 32) == tag) seenK = max(seenK, (unsigned)v);
             if ((++spins & 255) == 0) {
                 if (*((volatile int *)&sync[3]) != 0) break;
                 if (spins > kSpinLimit) {
@@ -213,54 +264,60 @@ __global__ void __launch_bounds__(256) k_line_sweep(int nx, int ny, int nz, int 
         }
     };
 
-    T prevline[EMAX];
+    T prevline[E];
 #pragma unroll
-    for (int e = 0; e < EMAX; ++e) prevline[e] = T(0);
+    for (int e = 0; e < E; ++e) prevline[e] = T(0);
 
-#pragma unroll
-    for (int q = 0; q < RING - 1; ++q) fetch(q, q - w);   // inputs of steps 0 .. RING-2
+    for (int q = 0; q < RING - 1; ++q) {   // the first RING-1 fetches need the producer's progress too
+        pace(q - (RING - 1));
+        __syncwarp();
+        fetch(q, q - w);
+    }
+    int q = 0;
+    unsigned parity = 0;
     for (int s = 0; s < steps; ++s) {
-        const int b = s % RING;
-        cp_async_wait<RING - 2>();              // this thread's copies for step s have landed
-        pace(s, b);
-        __syncthreads();                        // lines of step s-1 visible; ring slot of step s-1 free
+        pace(s);
+        __syncthreads();   // lines of step s-1 visible; slot of step s-1 free; pacing done
         if (tid == 0 && s > 0) st_tag(progress + 2 * tile, (unsigned)s, tag);   // steps 0..s-1 complete
-        fetch((s + RING - 1) % RING, s + RING - 1 - w);   // prefetch while this step is solved
+        fetch(q == 0 ? RING - 1 : q - 1, s + RING - 1 - w);
         const int tj = s - w;
-        if (line_live(tj)) {
-            const long long base = row_base(tj);
-            const T *xin = xch + ((size_t)((s - 1) & 1) * TK + (w - 1)) * LW;   // warp w-1's line of step s-1
-            T A[EMAX], B[EMAX];
-            // neighbour lines: (tj-1) in registers (or the j-face of tile J-1), (w-1) in shared
-            // memory (or the k-face of tile K-1 for warp 0)
-            const bool jin = line_j(tj) > 0, kin = km > 0;
-            const unsigned long long *jsrc =
-                (tj == 0 && prodJ >= 0) ? jface + (((long long)prodJ * TK + w) * nx) * 2 : nullptr;
+        wait_slot(q, parity);
+        if (rowlive && tj >= 0 && tj < nlive) {
+            const long long base = base0 + dj * tj;
+            const unsigned bl = (unsigned)base;
+            // element shift of the line's first cell inside each 16-byte aligned window
+            const int shr = (int)((((unsigned)(size_t)rhs + bl * (unsigned)sizeof(TR)) & 15u) / sizeof(TR));
+            const int sh0 = (int)((((unsigned)(size_t)c0 + bl * (unsigned)sizeof(T)) & 15u) / sizeof(T));
+            const int sh1 = (int)((((unsigned)(size_t)c1 + bl * (unsigned)sizeof(T)) & 15u) / sizeof(T));
+            const int sh2 = (int)((((unsigned)(size_t)c2 + bl * (unsigned)sizeof(T)) & 15u) / sizeof(T));
+            const int sh3 = BWD ? (int)((((unsigned)(size_t)dinv + bl * (unsigned)sizeof(T)) & 15u) / sizeof(T)) : 0;
+            const int x0 = BWD ? nx - 1 : 0;   // window position of the first cell along the sweep
+            const TR *rl = rwin + q * rslot + rw_w + shr + x0;
+            const T *cq = cwin + q * cslot + cw_w + x0;
+            const T *cl0 = cq + sh0, *cl1 = cq + carr + sh1, *cl2 = cq + 2 * carr + sh2;
+            const T *cl3 = cq + 3 * carr + sh3;
+            T A[E], B[E];
 #pragma unroll
-            for (int e = 0; e < EMAX; ++e) {
+            for (int e = 0; e < E; ++e) {
+                const int at = lane * E + e;
                 A[e] = T(1);
                 B[e] = T(0);
-                if (e < E && xok(e)) {
-                    const int at = lane * E + e;
+                if (at < nx) {
                     T nj = T(0), nk = T(0);
-                    if (jin) nj = jsrc ? take_tagged<T>(jsrc + (long long)at * 2, tag, sync) : prevline[e];
-                    if (kin) {
-                        if (w > 0) nk = xin[at];
-                        else {
-                            const unsigned long long *kw = kring + (((size_t)b * LW) + at) * 2;
-                            nk = Tag<T>::ok(kw, tag) ? Tag<T>::value(kw)
-                                                     : take_tagged<T>(kface + (((long long)prodK * TJ + tj) * nx + at) * 2,
-                                                                      tag, sync);
-                        }
+                    if (tj > 0) nj = prevline[e];
+                    else if (J > 0) nj = take_tagged<T>(jface + (((long long)prodJ * TK + w) * nx + at) * 2, tag, sync);
+                    if (w > 0) nk = xch[(((s - 1) & 1) * TK + (w - 1)) * LW + at];
+                    else if (K > 0) {
+                        const unsigned long long *kw = kwin + ((size_t)q * nx + at) * 2;
+                        nk = Tag<T>::ok(kw, tag)
+                                 ? Tag<T>::value(kw)
+                                 : take_tagged<T>(kface + (((long long)prodK * TJ + tj) * nx + at) * 2, tag, sync);
                     }
-                    const T r = (T)rring[((size_t)b * TK + w) * LW + at];
-                    const T a0 = ring[(((size_t)b * (NA - 1) + 0) * TK + w) * LW + at];
-                    const T a1 = ring[(((size_t)b * (NA - 1) + 1) * TK + w) * LW + at];
-                    const T a2 = ring[(((size_t)b * (NA - 1) + 2) * TK + w) * LW + at];
-                    T bb = r - a1 * nj - a2 * nk;
-                    T aa = -a0;
+                    const int xi = SG * at;
+                    T bb = (T)rl[xi] - cl1[xi] * nj - cl2[xi] * nk;
+                    T aa = -cl0[xi];
                     if (BWD) {
-                        const T d = ring[(((size_t)b * (NA - 1) + 3) * TK + w) * LW + at];
+                        const T d = cl3[xi];
                         bb *= d;
                         aa *= d;
                     }
@@ -268,15 +325,12 @@ __global__ void __launch_bounds__(256) k_line_sweep(int nx, int ny, int nz, int 
                     B[e] = bb;
                 }
             }
-            // lane composition: (a, b) applied after (A, B): (a A, a B + b)
-            T LA = T(1), LB = T(0);
+            T LA = A[0], LB = B[0];
 #pragma unroll
-            for (int e = 0; e < EMAX; ++e)
-                if (e < E) {
-                    LB = A[e] * LB + B[e];
-                    LA = A[e] * LA;
-                }
-            // warp inclusive scan of the lane maps (Kogge-Stone)
+            for (int e = 1; e < E; ++e) {
+                LB = A[e] * LB + B[e];
+                LA = A[e] * LA;
+            }
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
                 const T pa = shfl_up(LA, d), pb = shfl_up(LB, d);
@@ -285,28 +339,40 @@ __global__ void __launch_bounds__(256) k_line_sweep(int nx, int ny, int nz, int 
                     LA = LA * pa;
                 }
             }
-            // value entering this lane: the prefix of lanes < lane applied to 0
             T v = shfl_up(LB, 1);
             if (lane == 0) v = T(0);
 #pragma unroll
-            for (int e = 0; e < EMAX; ++e)
-                if (e < E) {
-                    v = A[e] * v + B[e];
-                    prevline[e] = v;
-                }
-            T *xo = xch + ((size_t)(s & 1) * TK + w) * LW;
+            for (int e = 0; e < E; ++e) {
+                v = A[e] * v + B[e];
+                prevline[e] = v;
+            }
+            T *xo = xch + ((s & 1) * TK + w) * LW;
+            T *ob = out + base + x0;
+            const bool putJ = feedJ && tj == TJ - 1;
 #pragma unroll
-            for (int e = 0; e < EMAX; ++e)
-                if (e < E && xok(e)) {
-                    const int at = lane * E + e;
-                    out[base + xreal(e)] = prevline[e];
+            for (int e = 0; e < E; ++e) {
+                const int at = lane * E + e;
+                if (at < nx) {
+                    ob[SG * at] = prevline[e];
                     xo[at] = prevline[e];
-                    if (feedJ && tj == TJ - 1) Tag<T>::put(jface + (((long long)tile * TK + w) * nx + at) * 2, prevline[e], tag);
+                    if (putJ) Tag<T>::put(jface + (((long long)tile * TK + w) * nx + at) * 2, prevline[e], tag);
                     if (feedK) Tag<T>::put(kface + (((long long)tile * TJ + tj) * nx + at) * 2, prevline[e], tag);
                 }
+            }
+        }
+        if (++q == RING) {
+            q = 0;
+            parity ^= 1u;
         }
     }
-    cp_async_wait0();
+    // drain: the last RING-1 fetches were issued for steps beyond the tile
+    for (int s = steps; s < steps + RING - 1; ++s) {
+        wait_slot(q, parity);
+        if (++q == RING) {
+            q = 0;
+            parity ^= 1u;
+        }
+    }
     __syncthreads();
     if (tid == 0) {
         st_tag(progress + 2 * tile, (unsigned)steps, tag);
@@ -321,35 +387,46 @@ __global__ void __launch_bounds__(256) k_line_sweep(int nx, int ny, int nz, int 
     }
 }
 
+// cells per lane: the smallest of 2, 4, 8 covering the line
+inline int line_e(int nx) { return nx <= 64 ? 2 : nx <= 128 ? 4 : 8; }
+
 template <typename T, typename TR, bool BWD>
-size_t line_smem(int TK, int E) {
-    constexpr int NA = BWD ? 5 : 4;
-    const int LW = 32 * E;
+size_t line_smem(int nx, int TK) {
+    constexpr int NC = BWD ? 4 : 3;
+    const int LW = 32 * line_e(nx);
+    const int WT = win_elems(nx, sizeof(T)), WR = win_elems(nx, sizeof(TR));
     size_t off = ((size_t)2 * TK * LW * sizeof(T) + 15) & ~(size_t)15;
-    off += (size_t)RING * (NA - 1) * TK * LW * sizeof(T);
-    off = (off + 15) & ~(size_t)15;
-    off += (size_t)RING * TK * LW * sizeof(TR);
-    off = (off + 15) & ~(size_t)15;
-    off += (size_t)RING * LW * 16;
-    off += (size_t)RING * 32;
+    off += (size_t)RING * NC * TK * WT * sizeof(T);
+    off += (size_t)RING * TK * WR * sizeof(TR);
+    off += (size_t)RING * nx * 16;
+    off += (size_t)RING * TK * 8;
     return off;
 }
 
-template <typename T, typename TR, bool BWD>
-void launch_lines(ms_system &s, const T *a0, const T *a1, const T *a2, const T *dinv, const TR *rhs, T *out,
-                  cudaStream_t st) {
-    const int E = (s.nx + 31) / 32;
+template <typename T, typename TR, bool BWD, int E>
+void launch_lines_e(ms_system &s, const T *a0, const T *a1, const T *a2, const T *dinv, const TR *rhs, T *out,
+                    cudaStream_t st) {
     const int nT = s.LNJ * s.LNK;
-    const size_t smem = line_smem<T, TR, BWD>(s.LTK, E);
-    auto kern = k_line_sweep<T, TR, BWD>;
+    const size_t smem = line_smem<T, TR, BWD>(s.nx, s.LTK);
+    auto kern = k_line_sweep<T, TR, BWD, E>;
     static size_t smem_set = 48 * 1024;
     if (smem > smem_set) {
         MS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         smem_set = smem;
     }
-    kern<<<nT, 32 * s.LTK, smem, st>>>(s.nx, s.ny, s.nz, s.LTJ, s.LTK, s.LNJ, s.LNK, E, s.line_order.p, a0, a1, a2,
-                                       dinv, rhs, out, s.lface_j.p, s.lface_k.p, s.line_progress.p, s.sync.p);
+    kern<<<nT, 32 * s.LTK, smem, st>>>(s.nx, s.ny, s.nz, s.LTJ, s.LTK, s.LNJ, s.LNK, s.line_order.p, a0, a1, a2, dinv,
+                                       rhs, out, s.lface_j.p, s.lface_k.p, s.line_progress.p, s.sync.p);
     MS_CHECK_LAUNCH();
+}
+
+template <typename T, typename TR, bool BWD>
+void launch_lines(ms_system &s, const T *a0, const T *a1, const T *a2, const T *dinv, const TR *rhs, T *out,
+                  cudaStream_t st) {
+    switch (line_e(s.nx)) {
+        case 2: launch_lines_e<T, TR, BWD, 2>(s, a0, a1, a2, dinv, rhs, out, st); break;
+        case 4: launch_lines_e<T, TR, BWD, 4>(s, a0, a1, a2, dinv, rhs, out, st); break;
+        default: launch_lines_e<T, TR, BWD, 8>(s, a0, a1, a2, dinv, rhs, out, st); break;
+    }
 }
 
 template <typename T, typename TR>
@@ -366,7 +443,6 @@ void lines_apply(ms_system &s, const T *coef, const T *dinv, const TR *r, T *y, 
 
 }  // namespace
 
-bool lines_supported(const ms_system &s) { return s.structured && s.nx <= 32 * EMAX && s.LTK > 0; }
 
 void launch_ilu_lines64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st) {
     lines_apply<double, double>(s, s.dcoef64.p, s.dinv64.p, r, y, z, st);

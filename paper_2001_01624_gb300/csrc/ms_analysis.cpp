@@ -17,6 +17,7 @@
 #include <cstring>
 #include <deque>
 #include <limits>
+#include <string>
 
 #include "ms_internal.h"
 
@@ -208,16 +209,16 @@ void analyse_grid(ms_system &s, const ms_grid &g) {
         // line-scan tiles: LTK warps (one k-row of x-lines each) x LTJ lines in j.
         // Shared memory per warp (worst case FP64 backward sweep, 4-slot ring):
         // exchange 2 + ring 4 x 5 lines of 8 bytes, plus the k-face ring.
-        const int E = (nx + 31) / 32, LW = 32 * E;
-        if (E <= 8) {
-            const size_t per_warp = (size_t)LW * 8 * (2 + 4 * 5);
-            int ltk = (int)std::min<size_t>(8, (200 * 1024 - (size_t)4 * LW * 16) / per_warp);
+        const int LW = 32 * (nx <= 64 ? 2 : nx <= 128 ? 4 : 8);
+        if (nx <= 256) {
+            const size_t per_warp = (size_t)LW * 8 * 2 + (size_t)4 * 5 * (nx + 8) * 8;
+            int ltk = (int)std::min<size_t>(8, (200 * 1024 - (size_t)4 * (nx + 2) * 16) / per_warp);
             ltk = std::max(1, std::min(ltk, nz));
             int ltj = std::min(ny, 32);
             if (const char *e = std::getenv("MSGB_LINE_TILE")) {     // tuning override "TJxTK"
                 int a = 0, b = 0;
                 if (std::sscanf(e, "%dx%d", &a, &b) == 2 && a > 0 && b > 0 && b <= 8 &&
-                    (size_t)b * per_warp + (size_t)4 * LW * 16 <= 220 * 1024) { ltj = a; ltk = b; }
+                    (size_t)b * per_warp + (size_t)4 * (nx + 2) * 16 <= 220 * 1024) { ltj = a; ltk = b; }
             }
             s.LTJ = ltj; s.LTK = ltk;
             s.LNJ = (ny + ltj - 1) / ltj; s.LNK = (nz + ltk - 1) / ltk;
@@ -234,6 +235,22 @@ void analyse_grid(ms_system &s, const ms_grid &g) {
             s.lface_j.zero(nullptr);
             s.lface_k.zero(nullptr);
             s.line_progress.zero(nullptr);
+        }
+        // sweep kernels: line scan across one cluster where it can be launched,
+        // else line scan over CTA tiles where the x-lines fit a warp, else pencil
+        // tiles; MSGB_ILU_KERNEL=cluster|lines|pencil|generic overrides (tuning)
+        plan_ilu_cluster(s);
+        for (int p = 0; p < 2; ++p) {
+            const int tiles = s.LTK > 0 ? 2 : 1;
+            int k = s.cl_ok[p] ? 3 : tiles;
+            if (const char *e = std::getenv("MSGB_ILU_KERNEL")) {
+                const std::string v(e);
+                if (v == "cluster") k = s.cl_ok[p] ? 3 : tiles;
+                else if (v == "lines") k = tiles;
+                else if (v == "pencil") k = 1;
+                else if (v == "generic") k = 0;
+            }
+            s.ilu_kind[p] = k;
         }
     }
 

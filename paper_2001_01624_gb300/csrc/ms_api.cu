@@ -104,32 +104,47 @@ void ensure_ilu(ms_ctx *ctx, ms_system &s, bool fp32) {
     launch_ilu_factor(s, fp32, ctx->stream);
     check_sweep_errors(ctx, &s);
     if (s.structured) {
-        if (!had64) launch_ilu_extract_dirs(s, false, ctx->stream);
-        if (fp32) launch_ilu_extract_dirs(s, true, ctx->stream);
+        if (!had64) {
+            launch_ilu_extract_dirs(s, false, ctx->stream);
+            if (s.cl_ok[0]) launch_ilu_pack_coef4(s, false, ctx->stream);
+        }
+        if (fp32) {
+            launch_ilu_extract_dirs(s, true, ctx->stream);
+            if (s.cl_ok[1]) launch_ilu_pack_coef4(s, true, ctx->stream);
+        }
     }
     s.ilu64_valid = true;
     if (fp32) s.ilu32_valid = true;
 }
 
-// z = (LU)^{-1} r: tiled wavefront sweeps on structured grids, level-ordered
-// sweeps otherwise.
-// (line-scan sweeps when the x-lines fit a warp's registers, pencil tiles for
-// longer lines)
+// z = (LU)^{-1} r: wavefront sweeps on structured grids (line scan across a
+// cluster, line scan over CTA tiles, or pencil tiles, chosen per precision when
+// the system is analysed), level-ordered sweeps otherwise.
 void ilu_apply64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st) {
-    if (lines_supported(s)) launch_ilu_lines64(s, r, y, z, st);
-    else if (s.structured) launch_ilu_tiled64(s, r, y, z, st);
-    else launch_ilu_apply64(s, r, y, z, st);
+    switch (s.ilu_kind[0]) {
+        case 3: launch_ilu_cluster64(s, r, y, z, st); break;
+        case 2: launch_ilu_lines64(s, r, y, z, st); break;
+        case 1: launch_ilu_tiled64(s, r, y, z, st); break;
+        default: launch_ilu_apply64(s, r, y, z, st);
+    }
 }
 
 void ilu_apply32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st) {
-    if (lines_supported(s)) launch_ilu_lines32(s, r, y, z, st);
-    else if (s.structured) launch_ilu_tiled32(s, r, y, z, st);
-    else launch_ilu_apply32(s, r, y, z, st);
+    switch (s.ilu_kind[1]) {
+        case 3: launch_ilu_cluster32(s, r, y, z, st); break;
+        case 2: launch_ilu_lines32(s, r, y, z, st); break;
+        case 1: launch_ilu_tiled32(s, r, y, z, st); break;
+        default: launch_ilu_apply32(s, r, y, z, st);
+    }
 }
 
+// FP32 right-hand side: structured systems only
 void ilu_apply32f(ms_system &s, const float *r, float *y, float *z, cudaStream_t st) {
-    if (lines_supported(s)) launch_ilu_lines32f(s, r, y, z, st);
-    else launch_ilu_tiled32f(s, r, y, z, st);
+    switch (s.ilu_kind[1]) {
+        case 3: launch_ilu_cluster32f(s, r, y, z, st); break;
+        case 2: launch_ilu_lines32f(s, r, y, z, st); break;
+        default: launch_ilu_tiled32f(s, r, y, z, st);
+    }
 }
 
 // Smooth a basis: reset from the indicator (reset) or continue; returns iterations.

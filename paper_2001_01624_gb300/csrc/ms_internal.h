@@ -169,6 +169,14 @@ struct ms_system {
     msgb::DBuf<unsigned long long> tile_progress;    // tagged per-tile progress hints
     // line-scan sweeps: TK warps per CTA walk TJ x TK tiles of x-lines
     int LTJ = 0, LTK = 0, LNJ = 0, LNK = 0;
+    // sweep kernel per precision ([0] FP64, [1] FP32): 0 level-ordered, 1 pencil tiles,
+    // 2 line scan over CTA tiles, 3 line scan pipelined across one cluster
+    int ilu_kind[2] = {0, 0};
+    // cluster line scan per precision: feasible, rows per CTA, CTAs (= cluster size)
+    bool cl_ok[2] = {false, false};
+    int cl_TK[2] = {0, 0}, cl_NK[2] = {0, 0};
+    msgb::DBuf<double> coef4_64;              // [2][n][4]: (Lx, Ly, Lz, 0), (Ux, Uy, Uz, 1/d) per cell
+    msgb::DBuf<float> coef4_32;
     msgb::DBuf<int> line_order;
     msgb::DBuf<unsigned long long> lface_j, lface_k, line_progress;
     msgb::DBuf<double> dcoef64;               // [6*n]: L(-x,-y,-z), U(+x,+y,+z)
@@ -290,7 +298,11 @@ void launch_ilu_apply64_scratch(const ms_system &s, const double *r, double *y, 
 void launch_ilu_tiled64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st);
 void launch_ilu_tiled32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st);
 void launch_ilu_tiled32f(ms_system &s, const float *r, float *y, float *z, cudaStream_t st);
-bool lines_supported(const ms_system &s);
+void plan_ilu_cluster(ms_system &s);
+void launch_ilu_pack_coef4(ms_system &s, bool fp32, cudaStream_t st);
+void launch_ilu_cluster64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st);
+void launch_ilu_cluster32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st);
+void launch_ilu_cluster32f(ms_system &s, const float *r, float *y, float *z, cudaStream_t st);
 void launch_ilu_lines64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st);
 void launch_ilu_lines32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st);
 void launch_ilu_lines32f(ms_system &s, const float *r, float *y, float *z, cudaStream_t st);

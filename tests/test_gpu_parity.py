@@ -359,15 +359,7 @@ def test_mixed_precision_solve(ms, ctx, case):
 
 
 # ------------------------------------------------- tiled wavefront ILU(0)
-@pytest.mark.parametrize("tile", ["4x2", "8x1", "3x3", "32x8", "1x4"])
-@pytest.mark.parametrize("shape", [(9, 13, 7), (6, 40, 1), (17, 5, 11), (300, 7, 3)])
-def test_tiled_ilu_sweeps_across_tiles(ms, ctx, monkeypatch, tile, shape):
-    """Structured grids use the tiled wavefront sweeps (x-line scans, or
-    x-pencils for lines longer than 256 cells); small tiles force many CTAs,
-    ragged last tiles and cross-tile hand-overs."""
-    monkeypatch.setenv("MSGB_ILU_TILE", tile)
-    monkeypatch.setenv("MSGB_LINE_TILE", tile)
-    gm = G.lognormal_box(*shape, seed=31, block=(3, 4, 2), kz_ratio=0.1)
+def _check_ilu_sweeps(ms, ctx, gm):
     s = _system(ms, ctx, gm)
     ref = O.assemble_tpfa(gm.grid, gm.perm)
     Ap, _ = O.pin(ref.A, None, 0)
@@ -382,6 +374,29 @@ def test_tiled_ilu_sweeps_across_tiles(ms, ctx, monkeypatch, tile, shape):
         ms.ms_ilu_apply(ctx, s, x, z, ms.MS_PREC_MIXED)
         assert np.abs(z - zr).max() <= 1e-4 * np.abs(zr).max()
     ms.ms_system_release(s)
+
+
+@pytest.mark.parametrize("kernel", ["lines", "pencil"])
+@pytest.mark.parametrize("tile", ["4x2", "8x1", "3x3", "32x8", "1x4"])
+@pytest.mark.parametrize("shape", [(9, 13, 7), (6, 40, 1), (17, 5, 11), (300, 7, 3)])
+def test_tiled_ilu_sweeps_across_tiles(ms, ctx, monkeypatch, kernel, tile, shape):
+    """Tiled wavefront sweeps (x-line scans over CTA tiles, or x-pencils, the
+    only form for lines longer than 256 cells); small tiles force many CTAs,
+    ragged last tiles and cross-tile hand-overs."""
+    monkeypatch.setenv("MSGB_ILU_KERNEL", kernel)
+    monkeypatch.setenv("MSGB_ILU_TILE", tile)
+    monkeypatch.setenv("MSGB_LINE_TILE", tile)
+    _check_ilu_sweeps(ms, ctx, G.lognormal_box(*shape, seed=31, block=(3, 4, 2), kz_ratio=0.1))
+
+
+@pytest.mark.parametrize("shape", [(9, 13, 1), (9, 13, 7), (70, 6, 17), (33, 20, 40), (200, 5, 11),
+                                   (60, 9, 85), (12, 4, 200), (256, 3, 5)])
+def test_cluster_ilu_sweeps(ms, ctx, monkeypatch, shape):
+    """Line scans pipelined across one thread-block cluster: k-rows split over
+    up to 16 CTAs (rows per CTA from 1 to 13, ragged last CTA), 2, 4 and 8
+    cells per lane, one-layer and single-CTA grids."""
+    monkeypatch.setenv("MSGB_ILU_KERNEL", "cluster")
+    _check_ilu_sweeps(ms, ctx, G.lognormal_box(*shape, seed=37, block=(3, 2, 2), kz_ratio=0.1))
 
 
 def test_ilu_apply_full_size_config2(ms, ctx):
