@@ -333,6 +333,28 @@ void launch_jacobi32(const ms_system &s, const double *r, float *z, float omega,
     MS_CHECK_LAUNCH();
 }
 
+namespace {
+// End of a Richardson cycle inside a graph: count the cycle, record the
+// relative residual ||q - A x|| / ||q|| (norms[1] / norms[0]) and keep the
+// loop going while it is above tol, finite, and under the cycle cap.
+__global__ void k_cycle_control(const double *norms, double tol, int max_iter, int *ctl_it, double *ctl_res,
+                                double *hist, cudaGraphConditionalHandle handle) {
+    const int it = *ctl_it + 1;
+    *ctl_it = it;
+    const double res = norms[0] > 0.0 ? norms[1] / norms[0] : 0.0;
+    *ctl_res = res;
+    if (hist) hist[it] = res;
+    cudaGraphSetConditional(handle, (res > tol && it < max_iter && res == res) ? 1u : 0u);
+}
+}  // namespace
+
+void launch_cycle_control(const double *norms, double tol, int max_iter, int *ctl_it, double *ctl_res, double *hist,
+                          cudaGraphConditionalHandle handle, cudaStream_t st) {
+    KernelScope ks_(st, "cycle_control", 0.0);
+    k_cycle_control<<<1, 1, 0, st>>>(norms, tol, max_iter, ctl_it, ctl_res, hist, handle);
+    MS_CHECK_LAUNCH();
+}
+
 void launch_norm2(const double *v, int n, double *red, unsigned int *cnt, double *out, cudaStream_t st) {
     KernelScope ks_(st, "norm2", (double)n * 8);
     k_norm2<<<blocks_for(n), kThreads, 0, st>>>(n, v, red, cnt, out);

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -728,10 +729,9 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
     std::unique_ptr<ms_coarse> dyn_coarse;
     const double jw = opts->jacobi_omega > 0 ? opts->jacobi_omega : 2.0 / 3.0;
 
-    int it = 0;
-    while (res > opts->tol && it < opts->max_iter) {
-        if (opts->adapt_schedule) MS_CUDA(cudaMemcpyAsync(s->w_xprev.p, s->w_x.p, n * sizeof(double),
-                                                          cudaMemcpyDeviceToDevice, st));
+    // one multistage cycle (Sec. 3): per stage, smoother then coarse correction;
+    // the last stage's residual also yields ||q - A x|| in norms[1]
+    auto enqueue_cycle = [&](cudaStream_t st) {
         const int total = n_stages + (dyn_coarse ? 1 : 0);
         for (int l = 0; l < total; ++l) {
             const ms_coarse &c = l < n_stages ? *stages[l] : *dyn_coarse;
@@ -751,8 +751,6 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
             }
             const int M = c.M;
             if (c.precision == MS_PREC_MIXED) {
-                s->w_d32.alloc(std::max(M, Mmax)); s->w_xc32.alloc(std::max(M, Mmax));
-                s->w_d.alloc(std::max(M, Mmax)); s->w_xc.alloc(std::max(M, Mmax)); s->w_rc.alloc(std::max(M, Mmax));
                 if (!mixed) {   // FP64 residual restricted with the FP32 basis copy
                     launch_to_float(s->w_r.p, s->w_r32.p, n, st);
                 }
@@ -765,7 +763,6 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
                 launch_narrow(s->w_xc.p, s->w_xc32.p, M, st);
                 launch_prolong32(b, n, s->w_xc32.p, s->w_x.p, st);
             } else {
-                s->w_d.alloc(std::max(M, Mmax)); s->w_xc.alloc(std::max(M, Mmax));
                 launch_restrict(b, s->w_r.p, s->w_d.p, st);
                 launch_gemv64(c.inv64.p, M, s->w_d.p, s->w_xc.p, st);
                 launch_prolong(b, n, s->w_xc.p, s->w_x.p, st);
@@ -774,6 +771,26 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
             launch_residual(*s, s->w_q.p, s->w_x.p, s->w_r.p, s->w_red.p, s->w_cnt.p, last ? norms.p + 1 : nullptr,
                             st, rin32);
         }
+    };
+    auto grow_coarse_work = [&]() {
+        s->w_d32.alloc(Mmax); s->w_xc32.alloc(Mmax);
+        s->w_d.alloc(Mmax); s->w_xc.alloc(Mmax); s->w_rc.alloc(Mmax);
+    };
+    grow_coarse_work();
+
+    // Cycles that rebuild the dynamic stage (Sec. 5.1 schedules), or run while
+    // kernels are traced, are driven from the host with one residual read per
+    // cycle; all other cycles run as one CUDA graph with a device-side while
+    // loop (MSGB_SOLVE_GRAPH=0 keeps every cycle on the host).
+    const char *genv = std::getenv("MSGB_SOLVE_GRAPH");
+    const bool graphs = !(genv && genv[0] == '0') && !profile_enabled();
+    int it = 0;
+    while (res > opts->tol && it < opts->max_iter) {
+        const bool rebuilds = opts->adapt_schedule == 1 || (opts->adapt_schedule == 2 && it < 2);
+        if (graphs && !rebuilds) break;
+        if (opts->adapt_schedule) MS_CUDA(cudaMemcpyAsync(s->w_xprev.p, s->w_x.p, n * sizeof(double),
+                                                          cudaMemcpyDeviceToDevice, st));
+        enqueue_cycle(st);
         if (info && info->dyn_blocks) info->dyn_blocks[it] = dyn_coarse ? dyn_coarse->M : 0;
         ++it;
         res = read_norm(ctx, norms.p + 1) / nq;
@@ -789,7 +806,77 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
             dyn_basis.reset(adaptive_basis(ctx, *s, s->w_part.p, opts->adapt, dprec));
             dyn_coarse.reset(create_coarse(ctx, *s, *dyn_basis, dprec));
             Mmax = std::max(Mmax, dyn_basis->M);
+            grow_coarse_work();
         }
+    }
+    if (res > opts->tol && it < opts->max_iter) {
+        // remaining cycles: while (res > tol && it < max_iter) { cycle } on the device
+        DBuf<int> ctl_it;
+        DBuf<double> ctl_res, hist;
+        ctl_it.alloc(1);
+        ctl_res.alloc(1);
+        MS_CUDA(cudaMemcpyAsync(ctl_it.p, &it, sizeof(int), cudaMemcpyHostToDevice, st));
+        if (info && info->history) hist.alloc((size_t)opts->max_iter + 1);
+        cudaGraph_t graph = nullptr, body = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        std::vector<std::string> captured;
+        try {
+            MS_CUDA(cudaGraphCreate(&graph, 0));
+            cudaGraphConditionalHandle handle;
+            MS_CUDA(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = handle;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t node;
+            MS_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+            body = cp.conditional.phGraph_out[0];
+            // captured on a private stream (the caller's may be the legacy default
+            // stream, which cannot be captured); the graph is launched on the caller's
+            if (!ctx->capture) MS_CUDA(cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking));
+            cudaStream_t cs = ctx->capture;
+            profile_record_begin();
+            MS_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+            try {
+                enqueue_cycle(cs);
+                launch_cycle_control(norms.p, opts->tol, opts->max_iter, ctl_it.p, ctl_res.p, hist.p, handle, cs);
+            } catch (...) {
+                cudaGraph_t dummy = nullptr;
+                cudaStreamEndCapture(cs, &dummy);
+                throw;
+            }
+            MS_CUDA(cudaStreamEndCapture(cs, &body));
+            captured = profile_record_end();
+            MS_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+            MS_CUDA(cudaGraphLaunch(exec, st));
+            int it_end = it;
+            double res_end = 0;
+            {
+                char *h = (char *)ctx->pinned.get(64);
+                MS_CUDA(cudaMemcpyAsync(h, ctl_it.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+                MS_CUDA(cudaMemcpyAsync(h + 8, ctl_res.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+                sync(st);
+                std::memcpy(&it_end, h, sizeof(int));
+                std::memcpy(&res_end, h + 8, sizeof(double));
+            }
+            if (it_end - it > 1) profile_add_launches(captured, it_end - it - 1);
+            if (info && info->history && it_end > it)
+                copy_out(info->history + it + 1, hist.p + it + 1, (size_t)(it_end - it), st);
+            if (info && info->dyn_blocks)
+                for (int k = it; k < it_end; ++k) info->dyn_blocks[k] = dyn_coarse ? dyn_coarse->M : 0;
+            it = it_end;
+            res = res_end;
+        } catch (...) {
+            profile_record_end();
+            if (exec) cudaGraphExecDestroy(exec);
+            if (graph) cudaGraphDestroy(graph);
+            throw;
+        }
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        if (!(res == res)) throw Error{MS_ERR_CUDA, "residual became NaN"};
+        if (opts->smoother == MS_SMOOTHER_ILU0) check_sweep_errors(ctx, s);
     }
     copy_out(p, s->w_x.p, n, st);
     sync(st);

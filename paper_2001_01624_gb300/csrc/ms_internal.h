@@ -109,6 +109,12 @@ class KernelScope {
     cudaEvent_t a_ = nullptr;
 };
 void profile_enable(bool on);
+bool profile_enabled();
+// graph capture: list the launches captured (counted once at capture), then
+// add them again per extra replay of the graph
+void profile_record_begin();
+std::vector<std::string> profile_record_end();
+void profile_add_launches(const std::vector<std::string> &names, int64_t times);
 void profile_reset();
 int profile_read(ms_kernel_stat *out, int cap, int64_t *total);
 
@@ -118,6 +124,10 @@ int profile_read(ms_kernel_stat *out, int cap, int64_t *total);
 struct ms_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t capture = nullptr;   // private stream that graphs are captured on (never executes)
+    ~ms_ctx() {
+        if (capture) cudaStreamDestroy(capture);
+    }
     int sm_count = 0;
     std::string err;
     msgb::HostScratch pinned;
@@ -279,6 +289,8 @@ void launch_residual_update32(const ms_system &s, const double *r, float *r32, d
 void launch_jacobi(const ms_system &s, const double *r, double *z, double omega, cudaStream_t st);
 void launch_jacobi32(const ms_system &s, const double *r, float *z, float omega, cudaStream_t st);
 void launch_norm2(const double *v, int n, double *red, unsigned int *cnt, double *out, cudaStream_t st);
+void launch_cycle_control(const double *norms, double tol, int max_iter, int *ctl_it, double *ctl_res, double *hist,
+                          cudaGraphConditionalHandle handle, cudaStream_t st);
 void launch_sub(const double *a, const double *b, double *c, int n, cudaStream_t st);
 void launch_scatter_zero(double *v, int idx, cudaStream_t st);
 void launch_restrict(const ms_basis &b, const double *r, double *d, cudaStream_t st);

@@ -28,6 +28,8 @@ struct Stat {
 struct Profiler {
     std::mutex mu;
     bool enabled = false;
+    bool recording = false;                 // launches captured into a graph are listed
+    std::vector<std::string> recorded;
     std::map<std::string, Stat> stats;
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> pool;
@@ -77,6 +79,10 @@ KernelScope::KernelScope(cudaStream_t st, const char *name, double bytes) : st_(
     std::lock_guard<std::mutex> g(p.mu);
     p.total_launches++;
     p.stats[name].launches++;
+    if (p.recording) {   // captured into a graph: counted per replay, never timed with events
+        p.recorded.emplace_back(name);
+        return;
+    }
     if (p.enabled) {
         a_ = p.get_event();
         if (a_) cudaEventRecord(a_, st_);
@@ -90,6 +96,35 @@ KernelScope::~KernelScope() {
     cudaEvent_t b = p.get_event();
     if (b) cudaEventRecord(b, st_);
     p.pending.push_back({name_, a_, b, bytes_});
+}
+
+bool profile_enabled() {
+    Profiler &p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    return p.enabled;
+}
+
+void profile_record_begin() {
+    Profiler &p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    p.recording = true;
+    p.recorded.clear();
+}
+
+std::vector<std::string> profile_record_end() {
+    Profiler &p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    p.recording = false;
+    return std::move(p.recorded);
+}
+
+void profile_add_launches(const std::vector<std::string> &names, int64_t times) {
+    Profiler &p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    for (const std::string &n : names) {
+        p.stats[n].launches += times;
+        p.total_launches += times;
+    }
 }
 
 void profile_enable(bool on) {

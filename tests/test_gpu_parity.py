@@ -230,6 +230,41 @@ def test_solve_matches_oracle(ms, ctx, case, smoother):
     ms.ms_system_release(s)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", ["3d_10x10x4", "faulted_18x14x7"])
+def test_graph_cycles_match_host_cycles(ms, ctx, monkeypatch, precision, case):
+    """Cycles run as one CUDA graph with a device-side while loop give the
+    same iterates, residual history and cycle count as cycles driven from the
+    host (the same kernels in the same order, deterministic reductions)."""
+    gm = CASES[case]()
+    prec = ms.MS_PREC_FP64 if precision == "fp64" else ms.MS_PREC_MIXED
+    s = _system(ms, ctx, gm)
+    part, M = ms.ms_partition_cartesian(ctx, s, gm.block)
+    b, _ = ms.ms_build_basis(ctx, s, part, M, block=gm.block, precision=prec)
+    c = ms.ms_galerkin(ctx, s, b, prec)
+    q = gm.q_active()
+    out = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("MSGB_SOLVE_GRAPH", mode)
+        p = np.zeros_like(q)
+        info = ms.ms_solve(ctx, s, [c], q, p, tol=1e-8, max_iter=3000, precision=prec)
+        out[mode] = (p, info)
+    (p0, i0), (p1, i1) = out["0"], out["1"]
+    assert i0["converged"] and i1["converged"]
+    assert i0["iters"] == i1["iters"]
+    np.testing.assert_array_equal(i0["history"], i1["history"])
+    np.testing.assert_array_equal(p0, p1)
+    # the cycle cap stops the device loop exactly
+    monkeypatch.setenv("MSGB_SOLVE_GRAPH", "1")
+    p = np.zeros_like(q)
+    info = ms.ms_solve(ctx, s, [c], q, p, tol=1e-14, max_iter=7, precision=prec)
+    assert info["iters"] == 7 and not info["converged"]
+    np.testing.assert_array_equal(info["history"], i0["history"][:8])
+    ms.ms_coarse_release(c)
+    ms.ms_basis_release(b)
+    ms.ms_system_release(s)
+
+
 def test_solve_device_pointers_and_initial_guess(ms, ctx):
     gm = CASES["3d_10x10x4"]()
     dev = torch.device("cuda:0")
