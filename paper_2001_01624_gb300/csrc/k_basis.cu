@@ -272,18 +272,27 @@ __global__ void __launch_bounds__(128) k_ap(int n, int W, int B, const int *__re
 }
 
 // Row j of A_c: warp-per-block accumulation over the support of block j.
-__global__ void k_rap(int n, int M, int WAP, const int *__restrict__ cptr, const int *__restrict__ ccell,
-                      const double *__restrict__ cval, const int *__restrict__ apid,
-                      const double *__restrict__ apval, double *__restrict__ Ac) {
+// A_c(j, :) = sum over the support of column j of P_ij (A P)(i, :), one warp
+// per column chunk with a dense shared-memory row accumulator (lanes take the
+// distinct entries of an (A P) row, cells in support order).  A column cut
+// into several chunks writes each chunk's row to its partial slot; the last
+// chunk to finish adds the partial rows in chunk order (deterministic).
+__global__ void k_rap(int n, int M, int WAP, int nch, int C, const int *__restrict__ ch_beg,
+                      const int *__restrict__ ch_col, const int *__restrict__ ch_ptr, const int *__restrict__ ch_slot,
+                      const int *__restrict__ cptr, const int *__restrict__ ccell, const double *__restrict__ cval,
+                      const int *__restrict__ apid, const double *__restrict__ apval, double *part, unsigned *cnt,
+                      double *__restrict__ Ac) {
     extern __shared__ double acc_all[];
     const int warps = blockDim.x >> 5;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = blockIdx.x * warps + wid;
+    const int c = blockIdx.x * warps + wid;
     double *acc = acc_all + (size_t)wid * M;
-    if (j >= M) return;
+    if (c >= nch) return;
     for (int l = lane; l < M; l += 32) acc[l] = 0.0;
     __syncwarp();
-    for (int e = cptr[j]; e < cptr[j + 1]; ++e) {
+    const int j = ch_col[c];
+    const int e0 = ch_beg[c], e1 = min(e0 + C, cptr[j + 1]);
+    for (int e = e0; e < e1; ++e) {
         const int i = ccell[e];
         const double p = cval[e];
         for (int w = lane; w < WAP; w += 32) {
@@ -292,7 +301,26 @@ __global__ void k_rap(int n, int M, int WAP, const int *__restrict__ cptr, const
         }
         __syncwarp();
     }
-    for (int l = lane; l < M; l += 32) Ac[(int64_t)j * M + l] = acc[l];
+    const int q0 = ch_ptr[j], k = ch_ptr[j + 1] - q0;
+    if (k == 1) {
+        for (int l = lane; l < M; l += 32) Ac[(int64_t)j * M + l] = acc[l];
+        return;
+    }
+    double *pp = part + (int64_t)ch_slot[c] * M;
+    for (int l = lane; l < M; l += 32) pp[l] = acc[l];
+    __threadfence();
+    __syncwarp();
+    unsigned t = 0;
+    if (lane == 0) t = atomicAdd(&cnt[j], 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t != (unsigned)(k - 1)) return;
+    __threadfence();
+    for (int l = lane; l < M; l += 32) {
+        double v = 0.0;
+        for (int q = q0; q < q0 + k; ++q) v += __ldcg(part + (int64_t)ch_slot[q] * M + l);
+        Ac[(int64_t)j * M + l] = v;
+    }
+    if (lane == 0) cnt[j] = 0u;
 }
 
 __global__ void k_symmetrise(int M, double *Ac) {
@@ -407,14 +435,36 @@ void launch_rap(const ms_system &s, const ms_basis &b, ms_coarse &c, cudaStream_
     const int M = c.M;
     const size_t per_warp = (size_t)M * sizeof(double);
     MS_REQUIRE(per_warp <= 200 * 1024, MS_ERR_INVALID_ARG, "coarse system too large for the Galerkin kernel");
-    int warps = (int)std::max<size_t>(1, std::min<size_t>(8, (48 * 1024) / per_warp));
+    if (c.gchunk == 0) {
+        // chunk size: the partial rows of split columns stay within 256 MB
+        std::vector<int> cb, cc, cp, sl;
+        int multi = 0;
+        int C = kColChunk;
+        for (;; C *= 2) {
+            build_column_chunks(b.h_cptr, M, C, cb, cc, cp, &sl, &multi);
+            if ((double)multi * M * 8.0 <= 256.0 * 1024 * 1024 || C >= (1 << 30) / 2) break;
+        }
+        c.gchunk = C;
+        c.n_gchunks = (int)cb.size();
+        c.gch_beg.upload(cb, st);
+        c.gch_col.upload(cc, st);
+        c.gch_ptr.upload(cp, st);
+        c.gch_slot.upload(sl, st);
+        c.gpart.alloc(std::max<size_t>((size_t)multi * M, 1));
+        c.gcnt.alloc(std::max(M, 1));
+        c.gcnt.zero(st);
+    }
+    int warps = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / per_warp));
     size_t smem = per_warp * warps;
-    if (smem > 48 * 1024) {
+    static size_t smem_set = 48 * 1024;
+    if (smem > smem_set) {
         MS_CUDA(cudaFuncSetAttribute(k_rap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        smem_set = smem;
     }
     KernelScope ks_(st, "rap", 0.0);
-    k_rap<<<(M + warps - 1) / warps, 32 * warps, smem, st>>>(s.n, M, c.WAP, b.cptr.p, b.ccell.p, b.cval.p, c.apid.p,
-                                                            c.apval.p, c.Ac.p);
+    k_rap<<<(c.n_gchunks + warps - 1) / warps, 32 * warps, smem, st>>>(
+        s.n, M, c.WAP, c.n_gchunks, c.gchunk, c.gch_beg.p, c.gch_col.p, c.gch_ptr.p, c.gch_slot.p, b.cptr.p, b.ccell.p,
+        b.cval.p, c.apid.p, c.apval.p, c.gpart.p, c.gcnt.p, c.Ac.p);
     MS_CHECK_LAUNCH();
     const int64_t MM = (int64_t)M * M;
     k_symmetrise<<<(int)((MM + kThreads - 1) / kThreads), kThreads, 0, st>>>(M, c.Ac.p);

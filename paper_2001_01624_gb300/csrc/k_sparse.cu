@@ -8,6 +8,8 @@
 // depend on scheduling.
 #include <cfloat>
 
+#include <algorithm>
+
 #include "ms_internal.h"
 
 namespace msgb {
@@ -221,35 +223,38 @@ __global__ void k_to_float(const double *a, float *b, int64_t n) {
 }
 
 // ------------------------------------------------------ restrict / prolong
-// d_j = sum over the support of block j of P_ij r_i (one CTA per block).
-template <typename TV, typename TR, typename TD>
-__global__ void k_restrict(const int *__restrict__ cptr, const int *__restrict__ ccell, const TV *__restrict__ cval,
-                           const TR *__restrict__ r, TD *__restrict__ d) {
-    const int j = blockIdx.x;
-    double s = 0.0;
-    for (int e = cptr[j] + threadIdx.x; e < cptr[j + 1]; e += blockDim.x)
-        s += (double)cval[e] * (double)r[ccell[e]];
-    s = block_sum(s);
-    if (threadIdx.x == 0) d[j] = (TD)s;
-}
-
-// single-precision accumulation variant for the mixed form
-__global__ void k_restrict_f32(const int *__restrict__ cptr, const int *__restrict__ ccell,
-                               const float *__restrict__ cval, const float *__restrict__ r, float *__restrict__ d) {
-    __shared__ float part[32];
-    const int j = blockIdx.x;
-    float s = 0.0f;
-    for (int e = cptr[j] + threadIdx.x; e < cptr[j + 1]; e += blockDim.x) s = fmaf(cval[e], r[ccell[e]], s);
+// d_j = sum over the support of block j of P_ij r_i, one warp per column
+// chunk: chunk sums in a fixed lane order, then the last chunk of a column to
+// finish adds the column's chunk sums in chunk order (deterministic; balanced
+// however uneven the supports are).  ACC is the accumulation type.
+template <typename TV, typename TR, typename TD, typename ACC>
+__global__ void k_restrict_ch(int nch, const int *__restrict__ ch_beg, const int *__restrict__ ch_col,
+                              const int *__restrict__ ch_ptr, const int *__restrict__ cptr,
+                              const int *__restrict__ ccell, const TV *__restrict__ cval, const TR *__restrict__ r,
+                              double *part, unsigned *cnt, TD *__restrict__ d) {
+    const int c = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (c >= nch) return;
+    const int j = ch_col[c];
+    const int e0 = ch_beg[c], e1 = min(e0 + kColChunk, cptr[j + 1]);
+    ACC s = ACC(0);
+    for (int e = e0 + lane; e < e1; e += 32) s += (ACC)cval[e] * (ACC)r[ccell[e]];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) part[wid] = s;
-    __syncthreads();
-    if (wid == 0) {
-        s = lane < (int)(blockDim.x >> 5) ? part[lane] : 0.0f;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) d[j] = s;
+    if (lane != 0) return;
+    const int q0 = ch_ptr[j], k = ch_ptr[j + 1] - q0;
+    if (k == 1) {
+        d[j] = (TD)s;
+        return;
+    }
+    part[c] = (double)s;
+    __threadfence();
+    if (atomicAdd(&cnt[j], 1u) == (unsigned)(k - 1)) {   // last chunk of column j
+        __threadfence();
+        ACC t = ACC(0);
+        for (int q = q0; q < q0 + k; ++q) t += (ACC)__ldcg(part + q);
+        d[j] = (TD)t;
+        cnt[j] = 0u;
     }
 }
 
@@ -387,15 +392,40 @@ void launch_widen(const float *a, double *b, int64_t n, cudaStream_t st) {
 
 void launch_narrow(const double *a, float *b, int64_t n, cudaStream_t st) { launch_to_float(a, b, n, st); }
 
+void build_column_chunks(const std::vector<int> &cptr, int M, int C, std::vector<int> &beg, std::vector<int> &col,
+                         std::vector<int> &ptr, std::vector<int> *slot, int *multi) {
+    beg.clear();
+    col.clear();
+    ptr.assign((size_t)M + 1, 0);
+    if (slot) slot->clear();
+    int nm = 0;
+    for (int j = 0; j < M; ++j) {
+        const int len = cptr[j + 1] - cptr[j];
+        const int k = std::max(1, (len + C - 1) / C);
+        ptr[j + 1] = ptr[j] + k;
+        for (int t = 0; t < k; ++t) {
+            beg.push_back(cptr[j] + t * C);
+            col.push_back(j);
+            if (slot) slot->push_back(k > 1 ? nm++ : -1);
+        }
+    }
+    if (multi) *multi = nm;
+}
+
 void launch_restrict(const ms_basis &b, const double *r, double *d, cudaStream_t st) {
     KernelScope ks_(st, "restrict", (double)b.nnz * (4 + 8) + (double)b.M * (8 + 4));
-    k_restrict<double, double, double><<<b.M, kThreads, 0, st>>>(b.cptr.p, b.ccell.p, b.cval.p, r, d);
+    const int g = (int)(((int64_t)b.n_chunks * 32 + kThreads - 1) / kThreads);
+    k_restrict_ch<double, double, double, double><<<g, kThreads, 0, st>>>(
+        b.n_chunks, b.ch_beg.p, b.ch_col.p, b.ch_ptr.p, b.cptr.p, b.ccell.p, b.cval.p, r, b.ch_part.p, b.ch_cnt.p, d);
     MS_CHECK_LAUNCH();
 }
 
 void launch_restrict32(const ms_basis &b, const float *r, float *d, cudaStream_t st) {
     KernelScope ks_(st, "restrict32", (double)b.nnz * (4 + 4) + (double)b.M * (4 + 4));
-    k_restrict_f32<<<b.M, kThreads, 0, st>>>(b.cptr.p, b.ccell.p, b.cval32.p, r, d);
+    const int g = (int)(((int64_t)b.n_chunks * 32 + kThreads - 1) / kThreads);
+    k_restrict_ch<float, float, float, float><<<g, kThreads, 0, st>>>(
+        b.n_chunks, b.ch_beg.p, b.ch_col.p, b.ch_ptr.p, b.cptr.p, b.ccell.p, b.cval32.p, r, b.ch_part.p, b.ch_cnt.p,
+        d);
     MS_CHECK_LAUNCH();
 }
 

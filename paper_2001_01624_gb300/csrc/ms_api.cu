@@ -196,6 +196,18 @@ ms_basis *create_basis(ms_ctx *ctx, ms_system &s, const std::vector<int> &part, 
     b->pid.upload(pid, st);
     b->is_home.upload(home, st);
     b->cptr.upload(cptr, st);
+    {
+        std::vector<int> cb, cc, cp;
+        build_column_chunks(cptr, M, kColChunk, cb, cc, cp, nullptr, nullptr);
+        b->n_chunks = (int)cb.size();
+        b->ch_beg.upload(cb, st);
+        b->ch_col.upload(cc, st);
+        b->ch_ptr.upload(cp, st);
+        b->ch_part.alloc(std::max<size_t>(cb.size(), 1));
+        b->ch_cnt.alloc(std::max(M, 1));
+        b->ch_cnt.zero(st);
+    }
+    b->h_cptr = cptr;
     b->ccell.upload(ccell, st);
     b->csrc.upload(csrc, st);
     if (rule != MS_SUPPORT_BLOCK) launch_basis_maps(s, *b, st);

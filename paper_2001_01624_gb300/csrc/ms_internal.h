@@ -242,7 +242,17 @@ struct ms_basis {
     bool has_map = false;
     msgb::DBuf<unsigned> nmap;
     msgb::DBuf<unsigned char> nslots;    // number of real slots of each cell
+    // column chunks: each support cut into pieces of at most kColChunk entries
+    // (chunk c covers entries [ch_beg[c], min(ch_beg[c] + kColChunk, cptr[j+1]))
+    // of column j = ch_col[c]; column j owns chunks [ch_ptr[j], ch_ptr[j+1]));
+    // column sums are taken over chunks, then over a column's chunks in order
+    std::vector<int> h_cptr;
+    int n_chunks = 0;
+    msgb::DBuf<int> ch_beg, ch_col, ch_ptr;
+    msgb::DBuf<double> ch_part;          // per-chunk partial sums
+    msgb::DBuf<unsigned> ch_cnt;         // per-column arrival counters (back to 0 after each use)
 };
+constexpr int kColChunk = 1024;
 
 struct ms_coarse {
     int M = 0;
@@ -255,6 +265,13 @@ struct ms_coarse {
     double inv32_error = 0.0;    // ||inv32 A_c v - v|| / ||v|| on a test vector
     msgb::DBuf<double> work64;   // factor workspace
     msgb::DBuf<float> work32;
+    // Galerkin column chunks (size gchunk, chosen so the partial rows of split
+    // columns fit in memory): chunk beg / column / slot of its partial row (-1:
+    // the column is a single chunk)
+    int gchunk = 0, n_gchunks = 0;
+    msgb::DBuf<int> gch_beg, gch_col, gch_ptr, gch_slot;
+    msgb::DBuf<double> gpart;
+    msgb::DBuf<unsigned> gcnt;
     // Galerkin scratch: cell-major (A P) lists
     int WAP = 0;
     msgb::DBuf<int> apid;
@@ -293,6 +310,8 @@ void launch_cycle_control(const double *norms, double tol, int max_iter, int *ct
                           cudaGraphConditionalHandle handle, cudaStream_t st);
 void launch_sub(const double *a, const double *b, double *c, int n, cudaStream_t st);
 void launch_scatter_zero(double *v, int idx, cudaStream_t st);
+void build_column_chunks(const std::vector<int> &cptr, int M, int C, std::vector<int> &beg, std::vector<int> &col,
+                         std::vector<int> &ptr, std::vector<int> *slot, int *multi);
 void launch_restrict(const ms_basis &b, const double *r, double *d, cudaStream_t st);
 void launch_restrict32(const ms_basis &b, const float *r, float *d, cudaStream_t st);
 void launch_prolong(const ms_basis &b, int n, const double *xc, double *x, cudaStream_t st);
