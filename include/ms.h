@@ -303,6 +303,40 @@ ms_status ms_coarse_get(ms_ctx *ctx, const ms_coarse *coarse, double *Ac, int32_
 ms_status ms_solve(ms_ctx *ctx, ms_system *sys, ms_coarse *const *stages, int32_t n_stages, const double *q,
                    double *p, const ms_solve_opts *opts, ms_solve_info *info);
 
+/* One member of a batched solve: an independent system with its own stages,
+ * sources and result.  `rebuild` (or NULL): a basis of this system to
+ * re-smooth from its block indicator before the solve (Sec. 3 basis
+ * construction), after which every stage built on it is re-formed (Galerkin
+ * product and coarse factor); `basis_iters` receives its iteration count.
+ * `status` receives the member's result (MS_ERR_NOT_CONVERGED keeps the last
+ * iterate in p, as for ms_solve). */
+typedef struct {
+    ms_system *sys;
+    ms_coarse *const *stages;
+    int32_t n_stages;
+    const double *q;       /* host or device, n doubles */
+    double *p;             /* host or device, n doubles */
+    ms_solve_info *info;   /* or NULL */
+    ms_basis *rebuild;     /* or NULL */
+    int32_t basis_iters;   /* out */
+    ms_status status;      /* out */
+} ms_batch_member;
+
+/* Batched solve of independent members (no counterpart in the paper, which
+ * solves one system at a time): members run concurrently on `n_workers`
+ * worker streams of this context's device (0: min(16, n_members)), each
+ * worker taking the largest remaining member next, so the small kernels of
+ * many members overlap on the GPU.  Each member computes exactly what
+ * ms_solve (after ms_basis_rebuild / ms_coarse_refresh when `rebuild` is set)
+ * computes for it alone.  The batch is ordered after earlier work on the
+ * context's stream and later work on that stream is ordered after it; the
+ * call returns when every member is done.  Returns MS_OK when every member
+ * converged, MS_ERR_NOT_CONVERGED when some did not (and none failed), else
+ * the first failing member's status.  Handles of different members must be
+ * distinct. */
+ms_status ms_solve_batch(ms_ctx *ctx, ms_batch_member *members, int32_t n_members, const ms_solve_opts *opts,
+                         int32_t n_workers);
+
 /* ---------------------------------------------------------------- tracing */
 /* Process-wide kernel tracing.  Launch counts are always kept; when enabled,
  * each launch is also timed with a pair of CUDA events recorded on the

@@ -70,6 +70,11 @@ class ms_solve_info(C.Structure):
                 ("dyn_blocks", _vp), ("seconds", _d)]
 
 
+class ms_batch_member(C.Structure):
+    _fields_ = [("sys", _vp), ("stages", _vp), ("n_stages", _i32), ("q", _vp), ("p", _vp),
+                ("info", C.POINTER(ms_solve_info)), ("rebuild", _vp), ("basis_iters", _i32), ("status", _i32)]
+
+
 _lib = None
 
 
@@ -112,6 +117,7 @@ def lib():
         "ms_coarse_release": ([_vp], _i32),
         "ms_coarse_get": ([_vp, _vp, _vp, P(_i32)], _i32),
         "ms_solve": ([_vp, _vp, P(_vp), _i32, _vp, _vp, P(ms_solve_opts), P(ms_solve_info)], _i32),
+        "ms_solve_batch": ([_vp, P(ms_batch_member), _i32, P(ms_solve_opts), _i32], _i32),
         "ms_profile_enable": ([_i32], _i32),
         "ms_profile_reset": ([], _i32),
         "ms_profile_read": ([_vp, _i32, P(_i32), P(_i64)], _i32),
@@ -130,7 +136,7 @@ def exported_symbols() -> Sequence[str]:
             "ms_system_get_matrix", "ms_spmv", "ms_ilu_apply", "ms_ilu_apply_noalloc", "ms_partition_cartesian", "ms_partition_components", "ms_partition_dynamic",
             "ms_build_basis", "ms_basis_rebuild", "ms_basis_update", "ms_basis_release", "ms_basis_get_info",
             "ms_basis_get", "ms_add_adaptive_basis", "ms_galerkin", "ms_coarse_refresh", "ms_coarse_release",
-            "ms_coarse_get", "ms_solve", "ms_profile_enable", "ms_profile_reset", "ms_profile_read"]
+            "ms_coarse_get", "ms_solve", "ms_solve_batch", "ms_profile_enable", "ms_profile_reset", "ms_profile_read"]
 
 
 def _ptr(a):
@@ -369,6 +375,40 @@ def ms_solve(ctx, sys, stages, q, p, tol=1e-6, max_iter=500, smoother=MS_SMOOTHE
         _check(st, ctx)
     return dict(status=st, iters=info.iters, converged=bool(info.converged), rel_residual=info.rel_residual,
                 history=hist[: info.iters + 1].copy(), dyn_blocks=dyn[: info.iters].copy(), seconds=info.seconds)
+
+
+def ms_solve_batch(ctx, members: Sequence[dict], tol=1e-6, max_iter=500, smoother=MS_SMOOTHER_ILU0,
+                   precision=MS_PREC_FP64, jacobi_omega=2.0 / 3.0, n_workers=0) -> list:
+    """Batched solve of independent members.  Each member is a dict with
+    keys sys, stages, q, p and optionally rebuild (a basis to re-smooth
+    first).  Returns one dict per member: status, iters, converged,
+    rel_residual, history, basis_iters, seconds."""
+    o = ms_solve_opts(tol, max_iter, smoother, precision, jacobi_omega, 0, ms_adapt_opts(8, 1e-8, 0, 2.0 / 3.0, 1e-3, 500), 0)
+    n = len(members)
+    arr = (ms_batch_member * max(n, 1))()
+    keep = []
+    hists = []
+    infos = (ms_solve_info * max(n, 1))()
+    for k, m in enumerate(members):
+        st_arr = (_vp * max(len(m["stages"]), 1))(*[s.value if isinstance(s, _vp) else s for s in m["stages"]])
+        q = _as(m["q"], np.float64)
+        hist = np.zeros(max_iter + 1)
+        infos[k] = ms_solve_info(0, 0, 0.0, hist.ctypes.data, None, 0.0)
+        keep += [st_arr, q]
+        hists.append(hist)
+        rb = m.get("rebuild")
+        arr[k] = ms_batch_member(m["sys"].value if isinstance(m["sys"], _vp) else m["sys"], C.cast(st_arr, _vp),
+                                 len(m["stages"]), _ptr(q), _ptr(m["p"]), C.pointer(infos[k]),
+                                 (rb.value if isinstance(rb, _vp) else rb) if rb is not None else None, 0, -1)
+    st = lib().ms_solve_batch(ctx, arr, n, C.byref(o), n_workers)
+    if st not in (MS_OK, MS_ERR_NOT_CONVERGED):
+        _check(st, ctx)
+    out = []
+    for k in range(n):
+        i = infos[k]
+        out.append(dict(status=arr[k].status, iters=i.iters, converged=bool(i.converged), rel_residual=i.rel_residual,
+                        history=hists[k][: i.iters + 1].copy(), basis_iters=arr[k].basis_iters, seconds=i.seconds))
+    return out
 
 
 # ------------------------------------------------------------------ tracing

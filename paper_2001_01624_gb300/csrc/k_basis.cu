@@ -457,10 +457,7 @@ void launch_rap(const ms_system &s, const ms_basis &b, ms_coarse &c, cudaStream_
     int warps = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / per_warp));
     size_t smem = per_warp * warps;
     static size_t smem_set = 48 * 1024;
-    if (smem > smem_set) {
-        MS_CUDA(cudaFuncSetAttribute(k_rap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        smem_set = smem;
-    }
+    MS_CUDA(raise_smem_limit(k_rap, smem, smem_set));
     KernelScope ks_(st, "rap", 0.0);
     k_rap<<<(c.n_gchunks + warps - 1) / warps, 32 * warps, smem, st>>>(
         s.n, M, c.WAP, c.n_gchunks, c.gchunk, c.gch_beg.p, c.gch_col.p, c.gch_ptr.p, c.gch_slot.p, b.cptr.p, b.ccell.p,

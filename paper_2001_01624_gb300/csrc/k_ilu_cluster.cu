@@ -29,6 +29,8 @@
 // entry: zero forward, the reciprocal diagonal backward), so a coefficient
 // line starts on a 16-byte boundary and is one bulk copy.  All waits are
 // bounded in device time and report a timeout instead of hanging.
+#include <atomic>
+
 #include "ms_internal.h"
 
 namespace msgb {
@@ -370,14 +372,10 @@ cudaError_t launch_cluster_e(const ms_system &s, int TK, int NK, const T *coef4,
                              cudaStream_t st, bool query_only, int *clusters) {
     auto kern = k_line_cluster<T, TR, BWD, E>;
     const size_t smem = cluster_smem<T, TR>(s.nx, TK);
-    static size_t smem_set = 0;       // per instantiation: attributes are raised once
-    static bool nonportable = false;
-    cudaError_t e = cudaSuccess;
-    if (smem > smem_set) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        smem_set = smem;
-    }
+    static size_t smem_set = 0;                      // per instantiation: attributes are raised once
+    static std::atomic<bool> nonportable{false};
+    cudaError_t e = raise_smem_limit(kern, smem, smem_set);
+    if (e != cudaSuccess) return e;
     if (NK > 8 && !nonportable) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;

@@ -410,10 +410,7 @@ void launch_lines_e(ms_system &s, const T *a0, const T *a1, const T *a2, const T
     const size_t smem = line_smem<T, TR, BWD>(s.nx, s.LTK);
     auto kern = k_line_sweep<T, TR, BWD, E>;
     static size_t smem_set = 48 * 1024;
-    if (smem > smem_set) {
-        MS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        smem_set = smem;
-    }
+    MS_CUDA(raise_smem_limit(kern, smem, smem_set));
     kern<<<nT, 32 * s.LTK, smem, st>>>(s.nx, s.ny, s.nz, s.LTJ, s.LTK, s.LNJ, s.LNK, s.line_order.p, a0, a1, a2, dinv,
                                        rhs, out, s.lface_j.p, s.lface_k.p, s.line_progress.p, s.sync.p);
     MS_CHECK_LAUNCH();

@@ -355,11 +355,8 @@ void launch_sweep(ms_system &s, const T *a0, const T *a1, const T *a2, const T *
     const int threads = s.TJ * s.TK;
     const size_t smem = tile_smem<T, TR, BWD, D>(s.TJ, s.TK);
     auto kern = k_tile_sweep<T, TR, BWD, D>;
-    static size_t smem_set = 48 * 1024;   // per instantiation: raise the dynamic shared-memory limit once
-    if (smem > smem_set) {
-        MS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        smem_set = smem;
-    }
+    static size_t smem_set = 48 * 1024;   // per instantiation
+    MS_CUDA(raise_smem_limit(kern, smem, smem_set));
     kern<<<nT, threads, smem, st>>>(s.nx, s.ny, s.nz, s.TJ, s.TK, s.NJ, s.NK, s.tile_order.p, a0, a1, a2, dinv, rhs,
                                     out, s.face_j.p, s.face_k.p, s.tile_progress.p, s.sync.p);
     MS_CHECK_LAUNCH();

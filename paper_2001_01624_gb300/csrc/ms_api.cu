@@ -3,6 +3,8 @@
 // kernels; the host only sequences launches, moves caller arrays, reads
 // convergence scalars and builds integer patterns (ms_analysis.cpp).
 #include <algorithm>
+#include <thread>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
@@ -900,6 +902,74 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     return conv ? MS_OK : fail(ctx, MS_ERR_NOT_CONVERGED, "iteration cap reached");
+    API_CATCH(ctx)
+}
+
+ms_status ms_solve_batch(ms_ctx *ctx, ms_batch_member *members, int32_t n_members, const ms_solve_opts *opts,
+                         int32_t n_workers) {
+    if (!ctx || !opts || n_members < 0 || (n_members > 0 && !members))
+        return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    if (n_members == 0) return MS_OK;
+    API_TRY
+    DeviceGuard g(ctx->device);
+    for (int m = 0; m < n_members; ++m) {
+        MS_REQUIRE(members[m].sys && members[m].q && members[m].p, MS_ERR_INVALID_ARG, "incomplete member");
+        members[m].status = MS_ERR_STATE;
+        members[m].basis_iters = 0;
+    }
+    const int W = std::max(1, std::min(n_members, n_workers > 0 ? n_workers : 16));
+    while ((int)ctx->workers.size() < W) {
+        std::unique_ptr<ms_ctx> w(new ms_ctx());
+        w->device = ctx->device;
+        w->sm_count = ctx->sm_count;
+        MS_CUDA(cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking));
+        w->owns_stream = true;
+        ctx->workers.push_back(std::move(w));
+    }
+    // order: earlier work on the caller's stream -> all workers -> later work on it
+    cudaEvent_t ev;
+    MS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    MS_CUDA(cudaEventRecord(ev, ctx->stream));
+    for (int w = 0; w < W; ++w) MS_CUDA(cudaStreamWaitEvent(ctx->workers[w]->stream, ev, 0));
+    // largest members first
+    std::vector<int> order(n_members);
+    for (int m = 0; m < n_members; ++m) order[m] = m;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return members[a].sys->n > members[b].sys->n; });
+    std::atomic<int> next{0};
+    auto work = [&](ms_ctx *wc) {
+        cudaSetDevice(wc->device);
+        for (int k = next++; k < n_members; k = next++) {
+            ms_batch_member &mb = members[order[k]];
+            ms_status st = MS_OK;
+            if (mb.rebuild) {
+                st = ms_basis_rebuild(wc, mb.sys, mb.rebuild, &mb.basis_iters);
+                for (int l = 0; st == MS_OK && l < mb.n_stages; ++l)
+                    if (mb.stages[l] && mb.stages[l]->basis == mb.rebuild) st = ms_coarse_refresh(wc, mb.sys, mb.stages[l]);
+            }
+            if (st == MS_OK) st = ms_solve(wc, mb.sys, mb.stages, mb.n_stages, mb.q, mb.p, opts, mb.info);
+            mb.status = st;
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int w = 1; w < W; ++w) pool.emplace_back(work, ctx->workers[w].get());
+    work(ctx->workers[0].get());
+    for (auto &t : pool) t.join();
+    for (int w = 0; w < W; ++w) {
+        MS_CUDA(cudaEventRecord(ev, ctx->workers[w]->stream));
+        MS_CUDA(cudaStreamWaitEvent(ctx->stream, ev, 0));
+    }
+    cudaEventDestroy(ev);
+    ms_status worst = MS_OK;
+    for (int m = 0; m < n_members; ++m) {
+        const ms_status st = members[m].status;
+        if (st != MS_OK && st != MS_ERR_NOT_CONVERGED) {
+            ctx->err = "member " + std::to_string(m) + ": " + ms_status_string(st);
+            return st;
+        }
+        if (st == MS_ERR_NOT_CONVERGED) worst = st;
+    }
+    return worst;
     API_CATCH(ctx)
 }
 

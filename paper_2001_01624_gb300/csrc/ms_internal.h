@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -108,6 +110,18 @@ class KernelScope {
     double bytes_;
     cudaEvent_t a_ = nullptr;
 };
+// Raise a kernel's dynamic shared-memory limit to at least `bytes`; `cur`
+// (one per kernel) remembers the limit set.  Thread-safe, never lowers it.
+std::mutex &attr_mutex();
+template <typename K>
+cudaError_t raise_smem_limit(K kern, size_t bytes, size_t &cur) {
+    std::lock_guard<std::mutex> g(attr_mutex());
+    if (bytes <= cur) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
 void profile_enable(bool on);
 bool profile_enabled();
 // graph capture: list the launches captured (counted once at capture), then
@@ -125,8 +139,12 @@ struct ms_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t capture = nullptr;   // private stream that graphs are captured on (never executes)
+    bool owns_stream = false;         // worker contexts of batched solves own their stream
+    std::vector<std::unique_ptr<ms_ctx>> workers;
     ~ms_ctx() {
+        workers.clear();
         if (capture) cudaStreamDestroy(capture);
+        if (owns_stream && stream) cudaStreamDestroy(stream);
     }
     int sm_count = 0;
     std::string err;

@@ -28,8 +28,6 @@ struct Stat {
 struct Profiler {
     std::mutex mu;
     bool enabled = false;
-    bool recording = false;                 // launches captured into a graph are listed
-    std::vector<std::string> recorded;
     std::map<std::string, Stat> stats;
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> pool;
@@ -67,6 +65,10 @@ struct Profiler {
     }
 };
 
+// launches captured into a graph on this thread are listed, not timed
+thread_local bool t_recording = false;
+thread_local std::vector<std::string> t_recorded;
+
 Profiler &prof() {
     static Profiler *p = new Profiler();   // never destroyed: events may outlive the CUDA context at exit
     return *p;
@@ -79,8 +81,8 @@ KernelScope::KernelScope(cudaStream_t st, const char *name, double bytes) : st_(
     std::lock_guard<std::mutex> g(p.mu);
     p.total_launches++;
     p.stats[name].launches++;
-    if (p.recording) {   // captured into a graph: counted per replay, never timed with events
-        p.recorded.emplace_back(name);
+    if (t_recording) {   // captured into a graph: counted per replay, never timed with events
+        t_recorded.emplace_back(name);
         return;
     }
     if (p.enabled) {
@@ -98,6 +100,11 @@ KernelScope::~KernelScope() {
     p.pending.push_back({name_, a_, b, bytes_});
 }
 
+std::mutex &attr_mutex() {
+    static std::mutex m;
+    return m;
+}
+
 bool profile_enabled() {
     Profiler &p = prof();
     std::lock_guard<std::mutex> g(p.mu);
@@ -105,17 +112,13 @@ bool profile_enabled() {
 }
 
 void profile_record_begin() {
-    Profiler &p = prof();
-    std::lock_guard<std::mutex> g(p.mu);
-    p.recording = true;
-    p.recorded.clear();
+    t_recording = true;
+    t_recorded.clear();
 }
 
 std::vector<std::string> profile_record_end() {
-    Profiler &p = prof();
-    std::lock_guard<std::mutex> g(p.mu);
-    p.recording = false;
-    return std::move(p.recorded);
+    t_recording = false;
+    return std::move(t_recorded);
 }
 
 void profile_add_launches(const std::vector<std::string> &names, int64_t times) {

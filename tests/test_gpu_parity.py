@@ -265,6 +265,48 @@ def test_graph_cycles_match_host_cycles(ms, ctx, monkeypatch, precision, case):
     ms.ms_system_release(s)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_batch_matches_individual_solves(ms, ctx, precision):
+    """Members of uneven size (structured and faulted) solved concurrently on
+    worker streams give exactly what each gives alone: basis re-smoothed,
+    Galerkin operator re-formed, then solved."""
+    prec = ms.MS_PREC_FP64 if precision == "fp64" else ms.MS_PREC_MIXED
+    models = [G.lognormal_box(24, 18, 9, seed=41, block=(8, 6, 3), kz_ratio=0.1),
+              G.lognormal_box(10, 30, 4, seed=42, block=(5, 10, 2)),
+              G.faulted(18, 14, 7, seed=5, n_fault_x=1, n_fault_y=1, block=(5, 4, 3)),
+              G.lognormal_box(40, 12, 16, seed=43, block=(8, 4, 4), kz_ratio=0.1),
+              G.lognormal_box(7, 9, 3, seed=44, block=(4, 3, 3))]
+    mem = []
+    for gm in models:
+        s = _system(ms, ctx, gm)
+        part, M = ms.ms_partition_cartesian(ctx, s, gm.block)
+        b, _ = ms.ms_build_basis(ctx, s, part, M, block=gm.block, precision=prec)
+        c = ms.ms_galerkin(ctx, s, b, prec)
+        mem.append(dict(sys=s, basis=b, coarse=c, q=gm.q_active()))
+    ref = []
+    for m in mem:
+        it = ms.ms_basis_rebuild(ctx, m["sys"], m["basis"])
+        ms.ms_coarse_refresh(ctx, m["sys"], m["coarse"])
+        p = np.zeros_like(m["q"])
+        info = ms.ms_solve(ctx, m["sys"], [m["coarse"]], m["q"], p, tol=1e-8, max_iter=3000, precision=prec)
+        ref.append((p, info, it))
+    for workers in (3, 1):
+        ps = [np.zeros_like(m["q"]) for m in mem]
+        out = ms.ms_solve_batch(ctx, [dict(sys=m["sys"], stages=[m["coarse"]], q=m["q"], p=p, rebuild=m["basis"])
+                                      for m, p in zip(mem, ps)], tol=1e-8, max_iter=3000, precision=prec,
+                                n_workers=workers)
+        for (pr, ir, itr), p, o in zip(ref, ps, out):
+            assert o["status"] == ms.MS_OK and o["converged"]
+            assert o["basis_iters"] == itr
+            assert o["iters"] == ir["iters"]
+            np.testing.assert_array_equal(o["history"], ir["history"])
+            np.testing.assert_array_equal(p, pr)
+    for m in mem:
+        ms.ms_coarse_release(m["coarse"])
+        ms.ms_basis_release(m["basis"])
+        ms.ms_system_release(m["sys"])
+
+
 def test_solve_device_pointers_and_initial_guess(ms, ctx):
     gm = CASES["3d_10x10x4"]()
     dev = torch.device("cuda:0")
