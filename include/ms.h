@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define MS_ABI_VERSION 1
+#define MS_ABI_VERSION 2
 
 typedef enum {
     MS_OK = 0,
@@ -60,6 +60,9 @@ typedef enum {
 
 typedef enum { MS_PREC_FP64 = 0, MS_PREC_MIXED = 1 } ms_precision;
 typedef enum { MS_SMOOTHER_ILU0 = 0, MS_SMOOTHER_JACOBI = 1 } ms_smoother;
+/* Outer iteration (Sec. 5.2: "Richardson or GMRES"): Richardson cycles, or
+ * restarted GMRES right-preconditioned with one multistage cycle. */
+typedef enum { MS_OUTER_RICHARDSON = 0, MS_OUTER_GMRES = 1 } ms_outer;
 typedef enum {
     MS_SUPPORT_BOX = 0,   /* Cartesian block box grown by floor(b/2) per side, cells reachable inside it */
     MS_SUPPORT_HOP = 1,   /* general partitions: block + neighbour-block cells nearer (in hops) to the
@@ -135,6 +138,8 @@ typedef struct {
                            /* 2 after cycles 1 and 2 only (Sec. 5.1 schedule)          */
     ms_adapt_opts adapt;   /* dynamic-stage options (used when adapt_schedule != 0)  */
     int32_t use_x0;        /* 1: p holds the initial guess; 0: start from p = 0      */
+    int32_t outer;         /* ms_outer                                                */
+    int32_t restart;       /* GMRES: Arnoldi steps per restart (0: 30)                */
 } ms_solve_opts;
 
 typedef struct {
@@ -296,6 +301,12 @@ ms_status ms_coarse_get(ms_ctx *ctx, const ms_coarse *coarse, double *Ac, int32_
  * (Sec. 5.2).  Per cycle, for each stage l = 0..n_stages-1 (then the
  * dynamic stage, if any):  p += S(q - A p);  p += P_l A_c,l^{-1} P_l^T (q - A p).
  * After each cycle the cycle stops when ||q - A p||_2 <= tol ||q||_2.
+ * With opts->outer = MS_OUTER_GMRES the same cycle, from a zero guess, is
+ * the right preconditioner of restarted flexible GMRES (Arnoldi by classical
+ * Gram-Schmidt applied twice, Givens rotations); iters then counts Arnoldi
+ * steps (one cycle each), history holds the GMRES residual estimate after
+ * each step and the true residual at each restart, and max_iter bounds the
+ * steps.  GMRES takes no adaptive schedule (MS_ERR_INVALID_ARG).
  * q: host or device, n doubles; p: host or device, n doubles (initial guess
  * if opts->use_x0, else overwritten from 0; holds the last iterate on
  * return, also on MS_ERR_NOT_CONVERGED).  stages: coarse operators built on

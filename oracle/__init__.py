@@ -118,6 +118,8 @@ def lib():
         L.or_ilu0_apply.restype = None
         L.or_ms_solve.argtypes = [_i, _vp, _vp, _vp, _i, C.POINTER(_Stage), _i, _vp, _d, _vp, _vp, _d, _i,
                                   C.POINTER(_Adapt), _pi, _vp]
+        L.or_ms_gmres.argtypes = [_i, _vp, _vp, _vp, _i, C.POINTER(_Stage), _i, _vp, _d, _vp, _vp, _d, _i, _i,
+                                  _pi, _vp]
         L.or_cost_model.argtypes = [_d, _d, _d, _d, _d]
         L.or_cost_model.restype = _d
     return _lib
@@ -396,6 +398,35 @@ def ms_solve(A: CSR, stages: Sequence[tuple], q, tol=1e-6, max_iter=500, smoothe
     n_it = it.value
     return SolveResult(x, n_it, hist[: n_it + 1].copy(), st == OK, dyn_part,
                        None if md_hist is None else md_hist[:n_it].copy())
+
+
+def ms_gmres(A: CSR, stages: Sequence[tuple], q, tol=1e-6, max_iter=500, restart=30, smoother="ilu0",
+             jac_omega=2.0 / 3.0, x0=None, lu=None) -> SolveResult:
+    """Restarted right-preconditioned GMRES(restart) with one multistage cycle
+    (Eq. (11), zero initial guess) as the preconditioner; max_iter bounds the
+    Arnoldi steps.  hist[k] is ||q - A x|| / ||q|| after step k (the GMRES
+    estimate inside a restart, the true residual at its end)."""
+    L = lib()
+    q = _f64(q)
+    x = np.zeros(A.n) if x0 is None else _f64(x0).copy()
+    keep = []
+    arr = (_Stage * max(len(stages), 1))()
+    for s, (B, Lc) in enumerate(stages):
+        Lc = _f64(Lc)
+        keep += [B, Lc]
+        arr[s] = _Stage(B.M, _p(B.sptr), _p(B.scells), _p(B.pval), _p(Lc))
+    sm = 0 if smoother == "ilu0" else 1
+    if sm == 0 and lu is None:
+        lu = ilu0(A)
+    hist = np.zeros(max_iter + 1)
+    it = _i()
+    st = L.or_ms_gmres(A.n, _p(A.rowptr), _p(A.col), _p(A.val), len(stages), arr, sm,
+                       _p(lu) if lu is not None else None, jac_omega, _p(q), _p(x), tol, max_iter, restart,
+                       C.byref(it), _p(hist))
+    if st not in (OK, ENOTCONV):
+        raise OracleError(st, "ms_gmres")
+    n_it = it.value
+    return SolveResult(x, n_it, hist[: n_it + 1].copy(), st == OK, None, None)
 
 
 def cost_model(N, Np, d, b, Nc):

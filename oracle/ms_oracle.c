@@ -911,6 +911,130 @@ int or_ms_solve(int n, const int *rowptr, const int *col, const double *val,
     return (res <= tol) ? OR_OK : OR_ENOTCONV;
 }
 
+/* Preconditioner of the outer Krylov solve (Sec. 5.2, "Richardson or GMRES"):
+ * one multistage cycle applied to v from a zero initial guess, z = M^{-1} v. */
+static void ms_cycle_from_zero(int n, const int *rp, const int *ci, const double *val, int n_stages,
+                               const or_stage *stages, int smoother, const double *lu, double jac_omega,
+                               const double *dg, const double *v, double *z, double *r, double *t, double *d,
+                               double *xc) {
+    for (int i = 0; i < n; ++i) z[i] = 0.0;
+    for (int s = 0; s < n_stages; ++s) {
+        residual(n, rp, ci, val, v, z, r);
+        if (smoother == 0) or_ilu0_apply(n, rp, ci, lu, r, t);
+        else for (int i = 0; i < n; ++i) t[i] = jac_omega * r[i] / dg[i];
+        for (int i = 0; i < n; ++i) z[i] += t[i];
+        coarse_correction(n, rp, ci, val, v, stages[s].M, stages[s].sptr, stages[s].scells, stages[s].pval,
+                          stages[s].L, z, r, d, xc);
+    }
+}
+
+/* Restarted GMRES(m), right-preconditioned with the multistage cycle and
+ * flexible (the preconditioned directions z_j are kept), as in Saad's
+ * "Iterative Methods for Sparse Linear Systems", Alg. 9.6.  Arnoldi with
+ * classical Gram-Schmidt applied twice; Givens rotations on the Hessenberg
+ * columns; the rotated right-hand side gives ||q - A x|| after every step,
+ * which is compared with tol ||q|| (hist[k] = that estimate / ||q|| after
+ * step k).  At convergence or after m steps, x += Z y and the true residual
+ * restarts the cycle.  max_iter bounds the Arnoldi steps (one preconditioner
+ * application each). */
+int or_ms_gmres(int n, const int *rowptr, const int *col, const double *val,
+                int n_stages, const or_stage *stages,
+                int smoother, const double *lu, double jac_omega,
+                const double *q, double *x, double tol, int max_iter, int m,
+                int *iters_out, double *hist) {
+    if (m < 1) m = 1;
+    int Mmax = 1;
+    for (int s = 0; s < n_stages; ++s) if (stages[s].M > Mmax) Mmax = stages[s].M;
+    double *V = (double *)xcalloc((size_t)(m + 1) * n, sizeof(double));
+    double *Z = (double *)xcalloc((size_t)m * n, sizeof(double));
+    double *H = (double *)xcalloc((size_t)(m + 1) * m, sizeof(double));   /* H[i*m + j] */
+    double *cs = (double *)xcalloc((size_t)m, sizeof(double));
+    double *sn = (double *)xcalloc((size_t)m, sizeof(double));
+    double *g = (double *)xcalloc((size_t)m + 1, sizeof(double));
+    double *y = (double *)xcalloc((size_t)m, sizeof(double));
+    double *h2 = (double *)xcalloc((size_t)m + 1, sizeof(double));
+    double *w = (double *)xmalloc((size_t)n * sizeof(double));
+    double *r = (double *)xmalloc((size_t)n * sizeof(double));
+    double *t = (double *)xmalloc((size_t)n * sizeof(double));
+    double *dg = (double *)xmalloc((size_t)n * sizeof(double));
+    double *d = (double *)xmalloc((size_t)Mmax * sizeof(double));
+    double *xc = (double *)xmalloc((size_t)Mmax * sizeof(double));
+    for (int i = 0; i < n; ++i) { int p = diag_pos(rowptr, col, i); dg[i] = p >= 0 ? val[p] : 0.0; }
+    const double nq = nrm2(n, q);
+    residual(n, rowptr, col, val, q, x, r);
+    double res = nq > 0 ? nrm2(n, r) / nq : 0.0;
+    if (hist) hist[0] = res;
+    if (nq == 0.0) { for (int i = 0; i < n; ++i) x[i] = 0.0; res = 0.0; }
+    int it = 0;
+    while (res > tol && it < max_iter) {
+        const double beta = nrm2(n, r);
+        for (int i = 0; i < n; ++i) V[i] = r[i] / beta;
+        for (int i = 0; i <= m; ++i) g[i] = 0.0;
+        g[0] = beta;
+        int k = 0;   /* Arnoldi steps in this restart */
+        while (k < m && it < max_iter) {
+            const double *vk = V + (size_t)k * n;
+            double *zk = Z + (size_t)k * n;
+            ms_cycle_from_zero(n, rowptr, col, val, n_stages, stages, smoother, lu, jac_omega, dg, vk, zk, r, t, d, xc);
+            csr_mv(n, rowptr, col, val, zk, w);
+            for (int i = 0; i <= k; ++i) H[i * m + k] = 0.0;
+            for (int pass = 0; pass < 2; ++pass) {       /* h = V^T w; w -= V h (twice) */
+                for (int i = 0; i <= k; ++i) {
+                    const double *vi = V + (size_t)i * n;
+                    double sdot = 0.0;
+                    for (int l = 0; l < n; ++l) sdot += vi[l] * w[l];
+                    h2[i] = sdot;
+                }
+                for (int i = 0; i <= k; ++i) {
+                    const double *vi = V + (size_t)i * n;
+                    for (int l = 0; l < n; ++l) w[l] -= h2[i] * vi[l];
+                    H[i * m + k] += h2[i];
+                }
+            }
+            const double hn = nrm2(n, w);
+            H[(k + 1) * m + k] = hn;
+            if (hn > 0.0) {
+                double *vn = V + (size_t)(k + 1) * n;
+                for (int l = 0; l < n; ++l) vn[l] = w[l] / hn;
+            }
+            for (int i = 0; i < k; ++i) {                 /* previous rotations on column k */
+                const double a = H[i * m + k], b = H[(i + 1) * m + k];
+                H[i * m + k] = cs[i] * a + sn[i] * b;
+                H[(i + 1) * m + k] = -sn[i] * a + cs[i] * b;
+            }
+            const double a = H[k * m + k], b = H[(k + 1) * m + k];
+            const double rho = sqrt(a * a + b * b);
+            cs[k] = rho > 0 ? a / rho : 1.0;
+            sn[k] = rho > 0 ? b / rho : 0.0;
+            H[k * m + k] = rho;
+            H[(k + 1) * m + k] = 0.0;
+            g[k + 1] = -sn[k] * g[k];
+            g[k] = cs[k] * g[k];
+            ++k;
+            ++it;
+            res = fabs(g[k]) / nq;
+            if (hist) hist[it] = res;
+            if (res <= tol || hn == 0.0) break;
+        }
+        for (int i = k - 1; i >= 0; --i) {              /* H(0:k,0:k) y = g(0:k) */
+            double sacc = g[i];
+            for (int l = i + 1; l < k; ++l) sacc -= H[i * m + l] * y[l];
+            y[i] = sacc / H[i * m + i];
+        }
+        for (int i = 0; i < k; ++i) {
+            const double *zi = Z + (size_t)i * n;
+            for (int l = 0; l < n; ++l) x[l] += y[i] * zi[l];
+        }
+        residual(n, rowptr, col, val, q, x, r);
+        res = nrm2(n, r) / nq;
+        if (hist) hist[it] = res;
+    }
+    free(V); free(Z); free(H); free(cs); free(sn); free(g); free(y); free(h2);
+    free(w); free(r); free(t); free(dg); free(d); free(xc);
+    *iters_out = it;
+    return (res <= tol) ? OR_OK : OR_ENOTCONV;
+}
+
 /* Operation count of one linear iteration with N_p partitions (Sec. 6.4,
  * Eq. (12)):  c = N [ N_p (4d + 2b + 4) + N_c (d + 1) + N_c (2 d N_c + 1) ]. */
 double or_cost_model(double N, double Np, double d, double b, double Nc) {

@@ -21,6 +21,7 @@ MS_OK, MS_ERR_INVALID_ARG, MS_ERR_OOM, MS_ERR_CUDA, MS_ERR_NOT_CONVERGED = 0, 1,
 MS_ERR_COARSE_SINGULAR, MS_ERR_TIMEOUT, MS_ERR_STATE = 5, 6, 7
 MS_PREC_FP64, MS_PREC_MIXED = 0, 1
 MS_SMOOTHER_ILU0, MS_SMOOTHER_JACOBI = 0, 1
+MS_OUTER_RICHARDSON, MS_OUTER_GMRES = 0, 1
 MS_SUPPORT_BOX, MS_SUPPORT_HOP, MS_SUPPORT_BLOCK = 0, 1, 2
 
 _vp, _i32, _i64, _d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
@@ -57,7 +58,8 @@ class ms_adapt_opts(C.Structure):
 
 class ms_solve_opts(C.Structure):
     _fields_ = [("tol", _d), ("max_iter", _i32), ("smoother", _i32), ("precision", _i32), ("jacobi_omega", _d),
-                ("adapt_schedule", _i32), ("adapt", ms_adapt_opts), ("use_x0", _i32)]
+                ("adapt_schedule", _i32), ("adapt", ms_adapt_opts), ("use_x0", _i32), ("outer", _i32),
+                ("restart", _i32)]
 
 
 class ms_kernel_stat(C.Structure):
@@ -358,13 +360,13 @@ def ms_coarse_get(ctx, coarse):
 # -------------------------------------------------------------------- solve
 def ms_solve(ctx, sys, stages, q, p, tol=1e-6, max_iter=500, smoother=MS_SMOOTHER_ILU0, precision=MS_PREC_FP64,
              jacobi_omega=2.0 / 3.0, adapt_schedule=0, adapt: Optional[dict] = None, use_x0=False,
-             raise_not_converged=False) -> dict:
+             raise_not_converged=False, outer=0, restart=30) -> dict:
     """Returns dict(status, iters, converged, rel_residual, history, dyn_blocks, seconds)."""
     ad = dict(n_bins=8, eps=1e-8, smoothed=0, omega=2.0 / 3.0, tol=1e-3, max_iter=500)
     ad.update(adapt or {})
     o = ms_solve_opts(tol, max_iter, smoother, precision, jacobi_omega, adapt_schedule,
                       ms_adapt_opts(ad["n_bins"], ad["eps"], ad["smoothed"], ad["omega"], ad["tol"], ad["max_iter"]),
-                      int(use_x0))
+                      int(use_x0), int(outer), int(restart))
     hist = np.zeros(max_iter + 1)
     dyn = np.zeros(max(max_iter, 1), np.int32)
     info = ms_solve_info(0, 0, 0.0, hist.ctypes.data, dyn.ctypes.data, 0.0)
@@ -378,12 +380,13 @@ def ms_solve(ctx, sys, stages, q, p, tol=1e-6, max_iter=500, smoother=MS_SMOOTHE
 
 
 def ms_solve_batch(ctx, members: Sequence[dict], tol=1e-6, max_iter=500, smoother=MS_SMOOTHER_ILU0,
-                   precision=MS_PREC_FP64, jacobi_omega=2.0 / 3.0, n_workers=0) -> list:
+                   precision=MS_PREC_FP64, jacobi_omega=2.0 / 3.0, n_workers=0, outer=0, restart=30) -> list:
     """Batched solve of independent members.  Each member is a dict with
     keys sys, stages, q, p and optionally rebuild (a basis to re-smooth
     first).  Returns one dict per member: status, iters, converged,
     rel_residual, history, basis_iters, seconds."""
-    o = ms_solve_opts(tol, max_iter, smoother, precision, jacobi_omega, 0, ms_adapt_opts(8, 1e-8, 0, 2.0 / 3.0, 1e-3, 500), 0)
+    o = ms_solve_opts(tol, max_iter, smoother, precision, jacobi_omega, 0, ms_adapt_opts(8, 1e-8, 0, 2.0 / 3.0, 1e-3, 500), 0,
+                      int(outer), int(restart))
     n = len(members)
     arr = (ms_batch_member * max(n, 1))()
     keep = []

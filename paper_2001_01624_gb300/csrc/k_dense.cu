@@ -235,9 +235,19 @@ __global__ void k_axpy_f32(int M, const float *t, double *x, int assign) {
 }
 
 // Test vector v_i = 1 + 0.5 sin(i) for the FP32 inverse quality check.
+// test vector with components along every eigenvector: uniform in [-1, 1)
+// from a 32-bit integer hash of the index (a mix of odd-constant multiplies
+// and xor-shifts)
 __global__ void k_test_vector(int M, double *v) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < M) v[i] = 1.0 + 0.5 * sin((double)i);
+    if (i >= M) return;
+    unsigned h = (unsigned)i * 0x9E3779B1u + 0x7F4A7C15u;
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    v[i] = (double)h * (2.0 / 4294967296.0) - 1.0;
 }
 
 // out[0] = ||x - v||^2, out[1] = ||v||^2 (one CTA, fixed order)

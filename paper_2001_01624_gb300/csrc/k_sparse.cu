@@ -360,6 +360,76 @@ void launch_cycle_control(const double *norms, double tol, int max_iter, int *ct
     MS_CHECK_LAUNCH();
 }
 
+namespace {
+// h[i] = sum_l V[i n + l] w[l] for i < k (Krylov basis against one vector):
+// each block forms its partial sums of all k products over a grid-stride
+// slice, then the last block to finish adds each product's partials in block
+// order (deterministic).
+__global__ void k_multidot(int n, int k, const double *__restrict__ V, const double *__restrict__ w, double *red,
+                           unsigned int *cnt, double *h) {
+    for (int i = 0; i < k; ++i) {
+        double a = 0.0;
+        const double *vi = V + (int64_t)i * n;
+        for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) a += vi[l] * w[l];
+        a = block_sum(a);
+        if (threadIdx.x == 0) red[(int64_t)blockIdx.x * k + i] = a;
+    }
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        double t = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(&red[(int64_t)b * k + i]);
+        h[i] = t;
+    }
+    if (threadIdx.x == 0) *cnt = 0u;
+}
+
+// y[l] += sign * sum_{i<k} c[i] V[i n + l]   (c on the device, k <= 128)
+__global__ void k_multiaxpy(int n, int k, const double *__restrict__ V, const double *__restrict__ c, double sign,
+                            double *__restrict__ y) {
+    __shared__ double cs[128];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) cs[i] = sign * c[i];
+    __syncthreads();
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
+        double a = y[l];
+        for (int i = 0; i < k; ++i) a += cs[i] * V[(int64_t)i * n + l];
+        y[l] = a;
+    }
+}
+
+__global__ void k_scale(int n, const double *__restrict__ x, double a, double *__restrict__ y) {
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) y[l] = a * x[l];
+}
+
+int stride_grid(int n) { return std::max(1, std::min((n + kThreads - 1) / kThreads, 4 * 152)); }
+}  // namespace
+
+int multidot_blocks(int n) { return stride_grid(n); }
+
+void launch_multidot(int n, int k, const double *V, const double *w, double *red, unsigned int *cnt, double *h,
+                     cudaStream_t st) {
+    KernelScope ks_(st, "krylov_dot", (double)(k + 1) * n * 8);
+    k_multidot<<<stride_grid(n), kThreads, 0, st>>>(n, k, V, w, red, cnt, h);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_multiaxpy(int n, int k, const double *V, const double *c, double sign, double *y, cudaStream_t st) {
+    KernelScope ks_(st, "krylov_axpy", (double)(k + 2) * n * 8);
+    k_multiaxpy<<<stride_grid(n), kThreads, 0, st>>>(n, k, V, c, sign, y);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_scale(int n, const double *x, double a, double *y, cudaStream_t st) {
+    k_scale<<<stride_grid(n), kThreads, 0, st>>>(n, x, a, y);
+    MS_CHECK_LAUNCH();
+}
+
 void launch_norm2(const double *v, int n, double *red, unsigned int *cnt, double *out, cudaStream_t st) {
     KernelScope ks_(st, "norm2", (double)n * 8);
     k_norm2<<<blocks_for(n), kThreads, 0, st>>>(n, v, red, cnt, out);

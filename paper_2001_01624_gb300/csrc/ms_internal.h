@@ -227,6 +227,9 @@ struct ms_system {
     msgb::DBuf<double> w_q, w_x, w_r, w_z, w_xprev, w_d, w_xc, w_rc, w_part;
     msgb::DBuf<float> w_y32, w_z32, w_r32, w_d32, w_xc32, w_rin32;
     msgb::DBuf<double> w_y;
+    msgb::DBuf<double> w_kry;                 // GMRES: V [(m+1) n], Z [m n], w, q copy; dot scratch
+    msgb::DBuf<double> w_kred, w_kh;
+    msgb::DBuf<unsigned int> w_kcnt;
     msgb::DBuf<double> w_red;                 // reduction partials
     msgb::DBuf<unsigned int> w_cnt;           // reduction counters
     msgb::DBuf<unsigned long long> w_max;     // max reductions
@@ -324,6 +327,11 @@ void launch_residual_update32(const ms_system &s, const double *r, float *r32, d
 void launch_jacobi(const ms_system &s, const double *r, double *z, double omega, cudaStream_t st);
 void launch_jacobi32(const ms_system &s, const double *r, float *z, float omega, cudaStream_t st);
 void launch_norm2(const double *v, int n, double *red, unsigned int *cnt, double *out, cudaStream_t st);
+int multidot_blocks(int n);
+void launch_multidot(int n, int k, const double *V, const double *w, double *red, unsigned int *cnt, double *h,
+                     cudaStream_t st);
+void launch_multiaxpy(int n, int k, const double *V, const double *c, double sign, double *y, cudaStream_t st);
+void launch_scale(int n, const double *x, double a, double *y, cudaStream_t st);
 void launch_cycle_control(const double *norms, double tol, int max_iter, int *ctl_it, double *ctl_res, double *hist,
                           cudaGraphConditionalHandle handle, cudaStream_t st);
 void launch_sub(const double *a, const double *b, double *c, int n, cudaStream_t st);

@@ -232,6 +232,33 @@ def test_solve_matches_oracle(ms, ctx, case, smoother):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("case", ["3d_10x10x4", "faulted_18x14x7"])
+@pytest.mark.parametrize("restart", [30, 5])
+def test_gmres_matches_oracle(ms, ctx, precision, case, restart):
+    gm = CASES[case]()
+    prec = ms.MS_PREC_FP64 if precision == "fp64" else ms.MS_PREC_MIXED
+    s = _system(ms, ctx, gm)
+    part, M = ms.ms_partition_cartesian(ctx, s, gm.block)
+    b, _ = ms.ms_build_basis(ctx, s, part, M, block=gm.block, precision=prec)
+    c = ms.ms_galerkin(ctx, s, b, prec)
+    q = gm.q_active()
+    p = np.zeros_like(q)
+    info = ms.ms_solve(ctx, s, [c], q, p, tol=1e-8, max_iter=500, precision=prec, outer=ms.MS_OUTER_GMRES,
+                       restart=restart)
+    sysr, Ap, qp, B, Ac, L = _oracle_general(gm)
+    r = O.ms_gmres(Ap, [(B, L)], qp, tol=1e-8, max_iter=500, restart=restart)
+    assert info["converged"] and r.converged
+    assert abs(info["iters"] - r.iters) <= 1, (info["iters"], r.iters)
+    tol = 1e-6 if precision == "fp64" else 1e-5
+    assert np.linalg.norm(p - r.x) <= tol * np.linalg.norm(r.x)
+    k = min(len(info["history"]), len(r.hist), 4)
+    np.testing.assert_allclose(info["history"][:k], r.hist[:k], rtol=1e-6 if precision == "fp64" else 1e-2)
+    ms.ms_coarse_release(c)
+    ms.ms_basis_release(b)
+    ms.ms_system_release(s)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", ["3d_10x10x4", "faulted_18x14x7"])
 def test_graph_cycles_match_host_cycles(ms, ctx, monkeypatch, precision, case):
     """Cycles run as one CUDA graph with a device-side while loop give the
     same iterates, residual history and cycle count as cycles driven from the

@@ -166,6 +166,59 @@ def test_identity_partition_converges_in_one_cycle():
     assert r.iters == 1 and r.converged
 
 
+@pytest.mark.parametrize("case", ["3d", "faulted"])
+@pytest.mark.parametrize("restart", [30, 4])
+def test_gmres_matches_direct_solve(case, restart):
+    """Restarted GMRES with the multistage cycle as right preconditioner
+    reaches the pinned system's unique solution (also with restarts every 4
+    steps)."""
+    if case == "3d":
+        gm = G.lognormal_box(10, 10, 4, seed=2, block=(5, 5, 2), kz_ratio=0.1)
+    else:
+        gm = G.faulted(14, 12, 6, seed=5, n_fault_x=1, n_fault_y=1, block=(5, 4, 3))
+    sysm, Ap, qp, B, Ac, L = O.setup_general(gm)
+    r = O.ms_gmres(Ap, [(B, L)], qp, tol=1e-11, max_iter=3000, restart=restart)
+    assert r.converged
+    x = _dense_pinned_solve(Ap, qp)
+    assert np.linalg.norm(r.x - x) <= 1e-8 * np.linalg.norm(x)
+    assert r.hist[-1] <= 1e-11
+    assert abs(np.linalg.norm(qp - Ap.dense() @ r.x) / np.linalg.norm(qp) - r.hist[-1]) <= 1e-12
+
+
+def test_gmres_residual_monotone_within_restart_and_true_at_restart():
+    """Within one restart the GMRES residual (least-squares minimum over a
+    growing Krylov space) cannot increase; with no restart it ends at the true
+    residual of the iterate."""
+    gm = G.lognormal_box(12, 10, 3, seed=8, block=(4, 5, 3), kz_ratio=0.1)
+    sysm, Ap, qp, B, Ac, L = O.setup_general(gm)
+    r = O.ms_gmres(Ap, [(B, L)], qp, tol=1e-10, max_iter=200, restart=200)
+    assert r.converged
+    assert np.all(np.diff(r.hist) <= 1e-14)
+    rr = np.linalg.norm(qp - Ap.dense() @ r.x) / np.linalg.norm(qp)
+    assert abs(rr - r.hist[-1]) <= 1e-12
+
+
+def test_gmres_exact_preconditioner_converges_in_one_step():
+    """With one coarse block per cell the cycle is an exact solve, so the
+    preconditioned operator is the identity and one Arnoldi step suffices."""
+    gm = G.lognormal_box(6, 5, 2, seed=7, block=(1, 1, 1))
+    sysm, Ap, qp, B, Ac, L = O.setup_general(gm)
+    r = O.ms_gmres(Ap, [(B, L)], qp, tol=1e-12, max_iter=10)
+    assert r.iters == 1 and r.converged
+
+
+def test_gmres_needs_no_more_steps_than_richardson_cycles():
+    """Richardson's iterate after k cycles lies in the same preconditioned
+    Krylov space GMRES minimises over (without restarts), so GMRES needs at
+    most as many steps."""
+    gm = G.lognormal_box(14, 12, 4, seed=9, block=(7, 6, 2), kz_ratio=0.1)
+    sysm, Ap, qp, B, Ac, L = O.setup_general(gm)
+    r1 = O.ms_solve(Ap, [(B, L)], qp, tol=1e-8, max_iter=3000)
+    r2 = O.ms_gmres(Ap, [(B, L)], qp, tol=1e-8, max_iter=3000, restart=3000)
+    assert r1.converged and r2.converged
+    assert r2.iters <= r1.iters
+
+
 def test_coarse_stage_does_not_increase_energy_error():
     """x + P A_c^-1 P^T (q - A x) is the A-orthogonal projection: ||e||_A
     never grows (Eq. (10), Galerkin restriction)."""
