@@ -51,8 +51,12 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run N extra untimed steps only (for ncu launch lists)")
-    ap.add_argument("--workload", choices=["c2", "ensemble"], default="c2",
-                    help="c2: the 60x220x85 geomodel (headline); ensemble: the batched uneven ensemble")
+    ap.add_argument("--workload", choices=["c2", "ensemble", "serving"], default="c2",
+                    help="c2: the 60x220x85 geomodel (headline); ensemble: the batched uneven ensemble; "
+                         "serving: Poisson stream of two-phase time steps on resident geomodels")
+    ap.add_argument("--models", type=int, default=32, help="serving: resident geomodels")
+    ap.add_argument("--requests", type=int, default=400, help="serving: requests in the stream")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrival rate (requests/s)")
     ap.add_argument("--members", type=int, default=256, help="ensemble members")
     ap.add_argument("--workers", type=int, default=16, help="ensemble worker streams")
     return ap.parse_args()
@@ -402,6 +406,93 @@ def run_ensemble(args):
     return 0
 
 
+SERVING = ("serving: Poisson arrivals (mean {rate:g} req/s, {req} requests, seed 7) of sequential-implicit two-phase "
+           "time steps (Corey n = 2, mu_w = 1, mu_o = 3 cP, porosity 0.2; 0.2 % of the pore volume injected per step) on "
+           "{m} resident geomodels of N log-uniform in [50k, 2M] cells (lognormal, sigma 2, correlation 8 cells, "
+           "Kz = 0.1 Kx; 10x10x5 coarse blocks); per request: total mobility, TPFA assembly with upstream face "
+           "mobility, Galerkin re-formed on the resident basis, dynamic stage from the last pressure change, "
+           "mixed-precision solve from the previous pressure to 1e-6, CFL-limited upstream transport; "
+           "{w} worker slots (continuous batching)")
+
+
+def serving_models(m_count, torch, dev, seed=0):
+    from paper_2001_01624_gb300 import geomodel as G, serve
+    rng = np.random.default_rng(seed)
+    models = []
+    for k in range(m_count):
+        N = float(np.exp(rng.uniform(np.log(5e4), np.log(2e6))))
+        nz = int(rng.integers(20, 61))
+        nxy = max(10, int(round(np.sqrt(N / nz))))
+        nx = max(10, int(round(nxy * rng.uniform(0.6, 1.4))))
+        ny = max(10, int(round(N / nz / nx)))
+        gm = G.lognormal_box(nx, ny, nz, seed=2000 + k, sigma=2.0, corr=8.0, block=(10, 10, 5), kz_ratio=0.1)
+        gm.q[:] *= 1e-4
+        models.append(serve.Model(k, gm, torch, dev))
+    return models
+
+
+def run_serving(args):
+    rank, world, local = dist_env()
+    import torch
+    global np
+    import numpy as np
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2001_01624_gb300 as ms
+    from paper_2001_01624_gb300 import serve
+    models = serving_models(args.models, torch, dev, seed=rank)
+
+    def dt_of(mid):
+        m = models[mid]
+        vol = m.gm.grid.dx * m.gm.grid.dy * m.gm.grid.dz
+        return 0.002 * 0.2 * vol * m.n / 1e-4
+    srv = serve.Server(torch, dev, models, workers=args.workers)
+    srv.warm(0.0)
+    ms.ms_profile_reset()
+    reqs = serve.poisson_stream(args.requests, args.rate, len(models), dt_of, seed=7 + rank)
+    sampler = ClockSampler(local)
+    sampler.start()
+    srv.run(reqs)
+    clocks = sampler.stop()
+    launches = ms.ms_profile_read()["_total_launches"]
+    st = serve.latency_stats(reqs)
+    if world > 1:
+        t = torch.tensor([st["p99_ms"], st["p50_ms"]], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        st["p99_ms"], st["p50_ms"] = float(t[0]), float(t[1])
+    cells = sum(models[r.model].n for r in reqs)
+    span = max(r.done for r in reqs) - min(r.arrival for r in reqs)
+    line = {"metric": "p99 request latency (serving: arrival to result on the host)", "value": st["p99_ms"],
+            "unit": "ms", "n_gpus": world, "steps": args.requests, "warmup": 1, "ms_per_step": st["mean_ms"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 bulk + f64 residual/refinement", "data": "synthetic",
+            "config": {"workload": SERVING.format(rate=args.rate, req=args.requests, m=args.models, w=args.workers),
+                       "models": args.models, "cells_resident": sum(m.n for m in models),
+                       "parallelism": "replicas (one stream of requests per GPU)"},
+            "latency": st,
+            "requests": {"cycles_mean": float(np.mean([r.cycles for r in reqs])),
+                         "cycles_max": int(max(r.cycles for r in reqs)),
+                         "substeps_mean": float(np.mean([r.substeps for r in reqs])),
+                         "max_rel_residual": float(max(r.rel_residual for r in reqs)),
+                         "unknowns_per_s": cells * world / span},
+            "gpu_launches": int(launches), "clocks": clocks}
+    srv.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def ensemble_oracle_sample(mem, out):
     """CPU oracle on the two smallest members: setup in full, 10 basis
     iterations and 10 cycles timed and scaled to each member's measured counts;
@@ -441,6 +532,8 @@ def main():
         return run_reference(args)
     if args.workload == "ensemble":
         return run_ensemble(args)
+    if args.workload == "serving":
+        return run_serving(args)
     import torch
     import numpy as np
     rank, world, local = dist_env()

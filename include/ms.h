@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define MS_ABI_VERSION 2
+#define MS_ABI_VERSION 3
 
 typedef enum {
     MS_OK = 0,
@@ -126,6 +126,7 @@ typedef struct {
     int32_t smoothed;   /* 0: constant basis (the paper's); 1: MsRSB on hop supports */
     double omega, tol;  /* smoothing parameters when smoothed                     */
     int32_t max_iter;
+    int32_t precision;  /* ms_precision of the basis made by ms_add_adaptive_basis   */
 } ms_adapt_opts;
 
 typedef struct {
@@ -347,6 +348,38 @@ typedef struct {
  * distinct. */
 ms_status ms_solve_batch(ms_ctx *ctx, ms_batch_member *members, int32_t n_members, const ms_solve_opts *opts,
                          int32_t n_workers);
+
+/* ------------------------------------------------------------- two-phase */
+/* Water / oil fluid for sequential-implicit time steps (Sec. 2): Corey
+ * relative permeabilities krw = Se^n_w, kro = (1 - Se)^n_o with
+ * Se = (S - s_wc) / (1 - s_wc - s_or) clipped to [0, 1], viscosities in
+ * consistent units, porosity, and the CFL number of the transport substeps. */
+typedef struct {
+    double mu_w, mu_o;
+    double n_w, n_o;
+    double s_wc, s_or;
+    double porosity;
+    double cfl;
+} ms_fluid;
+
+/* Total mobility lambda_t = krw/mu_w + kro/mu_o per active cell (the
+ * `mobility` argument of ms_assemble_tpfa).  S, lambda: host or device, n
+ * doubles. */
+ms_status ms_total_mobility(ms_ctx *ctx, const ms_system *sys, const ms_fluid *fluid, const double *S,
+                            double *lambda);
+
+/* Advance the water saturation S over dt with explicit single-point
+ * upstream transport: total fluxes u = T (p_a - p_b) from the transmissibilities
+ * of the last assembly (with its face mobilities) and the pressure p; water
+ * flux u f_w(S_upstream), f_w = (krw/mu_w) / lambda_t; sources q (total
+ * rate, + injection of water, - production at the cell's f_w); substeps of
+ * equal length h <= cfl * min_i (phi V_i / outflow_i) / max f_w', where
+ * outflow_i sums the fluxes leaving cell i and its production and max f_w'
+ * is the largest slope of f_w from central differences on 2000 intervals.
+ * p, q: host or device, n doubles; S: host or device, n doubles, updated in
+ * place; substeps (or NULL) receives the substep count. */
+ms_status ms_transport_step(ms_ctx *ctx, ms_system *sys, const ms_fluid *fluid, const double *p, const double *q,
+                            double dt, double *S, int32_t *substeps);
 
 /* ---------------------------------------------------------------- tracing */
 /* Process-wide kernel tracing.  Launch counts are always kept; when enabled,

@@ -120,6 +120,11 @@ def lib():
                                   C.POINTER(_Adapt), _pi, _vp]
         L.or_ms_gmres.argtypes = [_i, _vp, _vp, _vp, _i, C.POINTER(_Stage), _i, _vp, _d, _vp, _vp, _d, _i, _i,
                                   _pi, _vp]
+        L.or_total_mobility.argtypes = [_i, _vp, _vp, _vp]
+        L.or_total_mobility.restype = None
+        L.or_fw_max_slope.argtypes = [_vp]
+        L.or_fw_max_slope.restype = _d
+        L.or_transport_step.argtypes = [_i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d, _d, _d, _d, _pi]
         L.or_cost_model.argtypes = [_d, _d, _d, _d, _d]
         L.or_cost_model.restype = _d
     return _lib
@@ -427,6 +432,42 @@ def ms_gmres(A: CSR, stages: Sequence[tuple], q, tol=1e-6, max_iter=500, restart
         raise OracleError(st, "ms_gmres")
     n_it = it.value
     return SolveResult(x, n_it, hist[: n_it + 1].copy(), st == OK, None, None)
+
+
+def _fluid(fl):
+    d = dict(mu_w=1.0, mu_o=3.0, n_w=2.0, n_o=2.0, s_wc=0.0, s_or=0.0)
+    d.update(fl or {})
+    return np.array([d["mu_w"], d["mu_o"], d["n_w"], d["n_o"], d["s_wc"], d["s_or"]])
+
+
+def total_mobility(S, fluid=None):
+    """lambda_t = krw/mu_w + kro/mu_o (Corey) per cell."""
+    S = _f64(S)
+    fl = _fluid(fluid)
+    lam = np.empty(len(S))
+    lib().or_total_mobility(len(S), _p(S), _p(fl), _p(lam))
+    return lam
+
+
+def fw_max_slope(fluid=None):
+    fl = _fluid(fluid)
+    return lib().or_fw_max_slope(_p(fl))
+
+
+def transport_step(A_unpinned: CSR, p, q, S, dt, fluid=None, porosity=0.2, volume=1.0, cfl=0.9):
+    """Explicit upstream water transport over dt with the transmissibilities of
+    A_unpinned (assembled with the step's face mobilities).  Returns (S_new,
+    substeps)."""
+    fl = _fluid(fluid)
+    S = _f64(S).copy()
+    p = _f64(p)
+    q = _f64(q)
+    k = _i()
+    st = lib().or_transport_step(A_unpinned.n, _p(A_unpinned.rowptr), _p(A_unpinned.col), _p(A_unpinned.val),
+                                 _p(p), _p(q), _p(S), _p(fl), porosity, volume, cfl, dt, C.byref(k))
+    if st != OK:
+        raise OracleError(st, "transport_step")
+    return S, k.value
 
 
 def cost_model(N, Np, d, b, Nc):

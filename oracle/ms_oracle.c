@@ -1035,6 +1035,94 @@ int or_ms_gmres(int n, const int *rowptr, const int *col, const double *val,
     return (res <= tol) ? OR_OK : OR_ENOTCONV;
 }
 
+/* ------------------------------------------------------------ two-phase
+ * Water / oil with Corey relative permeabilities (Sec. 2 two-phase model):
+ * fl = (mu_w, mu_o, n_w, n_o, s_wc, s_or); Se = (S - s_wc)/(1 - s_wc - s_or)
+ * clipped to [0, 1], krw = Se^n_w, kro = (1 - Se)^n_o. */
+static void mobilities(const double *fl, double S, double *lw, double *lo) {
+    double se = (S - fl[4]) / (1.0 - fl[4] - fl[5]);
+    if (se < 0.0) se = 0.0;
+    if (se > 1.0) se = 1.0;
+    *lw = pow(se, fl[2]) / fl[0];
+    *lo = pow(1.0 - se, fl[3]) / fl[1];
+}
+
+static double fw_of(const double *fl, double S) {
+    double lw, lo;
+    mobilities(fl, S, &lw, &lo);
+    return (lw + lo) > 0.0 ? lw / (lw + lo) : 0.0;
+}
+
+void or_total_mobility(int n, const double *S, const double *fl, double *lam) {
+    for (int i = 0; i < n; ++i) {
+        double lw, lo;
+        mobilities(fl, S[i], &lw, &lo);
+        lam[i] = lw + lo;
+    }
+}
+
+/* Largest slope of f_w: central differences on 2000 equal intervals of [0, 1]. */
+double or_fw_max_slope(const double *fl) {
+    double m = 0.0;
+    for (int k = 1; k < 2000; ++k) {
+        const double s0 = (double)(k - 1) / 2000.0, s1 = (double)(k + 1) / 2000.0;
+        const double d = (fw_of(fl, s1) - fw_of(fl, s0)) / (s1 - s0);
+        if (d > m) m = d;
+    }
+    return m;
+}
+
+/* Explicit single-point upstream transport over dt.  The connection
+ * transmissibilities (with their face mobilities) are the negated
+ * off-diagonals of the unpinned pressure matrix A; u_ij = T_ij (p_i - p_j)
+ * leaves cell i.  Per substep of length h:
+ *   S_i += h / (phi V) [ q_w,i - sum_j u_ij f_w(S_upstream(i,j)) ],
+ * q_w,i = q_i (injection, q_i > 0) or q_i f_w(S_i) (production).  h = dt / k
+ * with k the smallest count such that h <= cfl * min_i (phi V / outflow_i) /
+ * max f_w', outflow_i = max(-q_i, 0) + sum of positive u_ij. */
+int or_transport_step(int n, const int *rowptr, const int *col, const double *val, const double *p,
+                      const double *q, double *S, const double *fl, double porosity, double volume, double cfl,
+                      double dt, int *nsub_out) {
+    const double pv = porosity * volume;
+    double tmin = INFINITY;
+    for (int i = 0; i < n; ++i) {
+        double out = q[i] < 0.0 ? -q[i] : 0.0;
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            const int j = col[e];
+            if (j == i) continue;
+            const double u = -val[e] * (p[i] - p[j]);
+            if (u > 0.0) out += u;
+        }
+        if (out > 0.0 && pv / out < tmin) tmin = pv / out;
+    }
+    const double slope = or_fw_max_slope(fl);
+    const double hmax = slope > 0.0 ? cfl * tmin / slope : INFINITY;
+    int k = 1;
+    if (dt > 0.0 && isfinite(hmax)) {
+        const double c = ceil(dt / hmax);
+        if (c >= 1e7) return OR_EINVAL;
+        k = c < 1.0 ? 1 : (int)c;
+    }
+    const double h = dt / k;
+    double *Sn = (double *)xmalloc((size_t)n * sizeof(double));
+    for (int step = 0; step < k; ++step) {
+        for (int i = 0; i < n; ++i) {
+            double acc = q[i] > 0.0 ? q[i] : q[i] * fw_of(fl, S[i]);
+            for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+                const int j = col[e];
+                if (j == i) continue;
+                const double u = -val[e] * (p[i] - p[j]);
+                acc -= u * fw_of(fl, u >= 0.0 ? S[i] : S[j]);
+            }
+            Sn[i] = S[i] + h / pv * acc;
+        }
+        memcpy(S, Sn, (size_t)n * sizeof(double));
+    }
+    free(Sn);
+    *nsub_out = k;
+    return OR_OK;
+}
+
 /* Operation count of one linear iteration with N_p partitions (Sec. 6.4,
  * Eq. (12)):  c = N [ N_p (4d + 2b + 4) + N_c (d + 1) + N_c (2 d N_c + 1) ]. */
 double or_cost_model(double N, double Np, double d, double b, double Nc) {

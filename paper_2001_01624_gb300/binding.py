@@ -53,7 +53,8 @@ class ms_basis_info(C.Structure):
 
 
 class ms_adapt_opts(C.Structure):
-    _fields_ = [("n_bins", _i32), ("eps", _d), ("smoothed", _i32), ("omega", _d), ("tol", _d), ("max_iter", _i32)]
+    _fields_ = [("n_bins", _i32), ("eps", _d), ("smoothed", _i32), ("omega", _d), ("tol", _d), ("max_iter", _i32),
+                ("precision", _i32)]
 
 
 class ms_solve_opts(C.Structure):
@@ -70,6 +71,15 @@ class ms_kernel_stat(C.Structure):
 class ms_solve_info(C.Structure):
     _fields_ = [("iters", _i32), ("converged", _i32), ("rel_residual", _d), ("history", _vp),
                 ("dyn_blocks", _vp), ("seconds", _d)]
+
+
+class ms_fluid(C.Structure):
+    _fields_ = [("mu_w", _d), ("mu_o", _d), ("n_w", _d), ("n_o", _d), ("s_wc", _d), ("s_or", _d),
+                ("porosity", _d), ("cfl", _d)]
+
+
+def fluid(mu_w=1.0, mu_o=3.0, n_w=2.0, n_o=2.0, s_wc=0.0, s_or=0.0, porosity=0.2, cfl=0.9) -> ms_fluid:
+    return ms_fluid(mu_w, mu_o, n_w, n_o, s_wc, s_or, porosity, cfl)
 
 
 class ms_batch_member(C.Structure):
@@ -120,6 +130,8 @@ def lib():
         "ms_coarse_get": ([_vp, _vp, _vp, P(_i32)], _i32),
         "ms_solve": ([_vp, _vp, P(_vp), _i32, _vp, _vp, P(ms_solve_opts), P(ms_solve_info)], _i32),
         "ms_solve_batch": ([_vp, P(ms_batch_member), _i32, P(ms_solve_opts), _i32], _i32),
+        "ms_total_mobility": ([_vp, _vp, P(ms_fluid), _vp, _vp], _i32),
+        "ms_transport_step": ([_vp, _vp, P(ms_fluid), _vp, _vp, _d, _vp, P(_i32)], _i32),
         "ms_profile_enable": ([_i32], _i32),
         "ms_profile_reset": ([], _i32),
         "ms_profile_read": ([_vp, _i32, P(_i32), P(_i64)], _i32),
@@ -138,7 +150,7 @@ def exported_symbols() -> Sequence[str]:
             "ms_system_get_matrix", "ms_spmv", "ms_ilu_apply", "ms_ilu_apply_noalloc", "ms_partition_cartesian", "ms_partition_components", "ms_partition_dynamic",
             "ms_build_basis", "ms_basis_rebuild", "ms_basis_update", "ms_basis_release", "ms_basis_get_info",
             "ms_basis_get", "ms_add_adaptive_basis", "ms_galerkin", "ms_coarse_refresh", "ms_coarse_release",
-            "ms_coarse_get", "ms_solve", "ms_solve_batch", "ms_profile_enable", "ms_profile_reset", "ms_profile_read"]
+            "ms_coarse_get", "ms_solve", "ms_solve_batch", "ms_total_mobility", "ms_transport_step", "ms_profile_enable", "ms_profile_reset", "ms_profile_read"]
 
 
 def _ptr(a):
@@ -327,8 +339,9 @@ def ms_basis_get(ctx, basis):
     return cptr, cells[: info["nnz"]], val[: info["nnz"]]
 
 
-def ms_add_adaptive_basis(ctx, sys, dp, n_bins=8, eps=1e-8, smoothed=0, omega=2.0 / 3.0, tol=1e-3, max_iter=500):
-    o = ms_adapt_opts(n_bins, eps, smoothed, omega, tol, max_iter)
+def ms_add_adaptive_basis(ctx, sys, dp, n_bins=8, eps=1e-8, smoothed=0, omega=2.0 / 3.0, tol=1e-3, max_iter=500,
+                          precision=MS_PREC_FP64):
+    o = ms_adapt_opts(n_bins, eps, smoothed, omega, tol, max_iter, precision)
     h = _vp()
     _check(lib().ms_add_adaptive_basis(ctx, sys, _ptr(_as(dp, np.float64)), C.byref(o), C.byref(h)), ctx)
     return h
@@ -365,7 +378,8 @@ def ms_solve(ctx, sys, stages, q, p, tol=1e-6, max_iter=500, smoother=MS_SMOOTHE
     ad = dict(n_bins=8, eps=1e-8, smoothed=0, omega=2.0 / 3.0, tol=1e-3, max_iter=500)
     ad.update(adapt or {})
     o = ms_solve_opts(tol, max_iter, smoother, precision, jacobi_omega, adapt_schedule,
-                      ms_adapt_opts(ad["n_bins"], ad["eps"], ad["smoothed"], ad["omega"], ad["tol"], ad["max_iter"]),
+                      ms_adapt_opts(ad["n_bins"], ad["eps"], ad["smoothed"], ad["omega"], ad["tol"], ad["max_iter"],
+                                    precision),
                       int(use_x0), int(outer), int(restart))
     hist = np.zeros(max_iter + 1)
     dyn = np.zeros(max(max_iter, 1), np.int32)
@@ -385,7 +399,7 @@ def ms_solve_batch(ctx, members: Sequence[dict], tol=1e-6, max_iter=500, smoothe
     keys sys, stages, q, p and optionally rebuild (a basis to re-smooth
     first).  Returns one dict per member: status, iters, converged,
     rel_residual, history, basis_iters, seconds."""
-    o = ms_solve_opts(tol, max_iter, smoother, precision, jacobi_omega, 0, ms_adapt_opts(8, 1e-8, 0, 2.0 / 3.0, 1e-3, 500), 0,
+    o = ms_solve_opts(tol, max_iter, smoother, precision, jacobi_omega, 0, ms_adapt_opts(8, 1e-8, 0, 2.0 / 3.0, 1e-3, 500, precision), 0,
                       int(outer), int(restart))
     n = len(members)
     arr = (ms_batch_member * max(n, 1))()
@@ -412,6 +426,25 @@ def ms_solve_batch(ctx, members: Sequence[dict], tol=1e-6, max_iter=500, smoothe
         out.append(dict(status=arr[k].status, iters=i.iters, converged=bool(i.converged), rel_residual=i.rel_residual,
                         history=hists[k][: i.iters + 1].copy(), basis_iters=arr[k].basis_iters, seconds=i.seconds))
     return out
+
+
+# ---------------------------------------------------------------- two-phase
+def ms_total_mobility(ctx, sys, fl: ms_fluid, S, lam=None):
+    """lambda_t per active cell; S, lam: numpy arrays or device tensors."""
+    S = _as(S, np.float64)
+    if lam is None:
+        lam = np.empty(len(S))
+    _check(lib().ms_total_mobility(ctx, sys, C.byref(fl), _ptr(S), _ptr(lam)), ctx)
+    return lam
+
+
+def ms_transport_step(ctx, sys, fl: ms_fluid, p, q, dt, S) -> int:
+    """Advance S (updated in place) over dt; returns the substep count."""
+    p = _as(p, np.float64)
+    q = _as(q, np.float64)
+    k = _i32()
+    _check(lib().ms_transport_step(ctx, sys, C.byref(fl), _ptr(p), _ptr(q), float(dt), _ptr(S), C.byref(k)), ctx)
+    return k.value
 
 
 # ------------------------------------------------------------------ tracing

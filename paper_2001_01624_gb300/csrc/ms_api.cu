@@ -623,7 +623,9 @@ ms_status ms_add_adaptive_basis(ms_ctx *ctx, ms_system *s, const double *dp, con
     MS_REQUIRE(s->assembled, MS_ERR_STATE, "system not assembled");
     DBuf<double> stage;
     const double *dd = device_in(dp, s->n, stage, ctx->stream);
-    *out = adaptive_basis(ctx, *s, dd, *opts, MS_PREC_FP64);
+    MS_REQUIRE(opts->precision == MS_PREC_FP64 || opts->precision == MS_PREC_MIXED, MS_ERR_INVALID_ARG,
+               "unknown precision");
+    *out = adaptive_basis(ctx, *s, dd, *opts, opts->precision);
     return MS_OK;
     API_CATCH(ctx)
 }
@@ -1065,6 +1067,79 @@ ms_status ms_solve_batch(ms_ctx *ctx, ms_batch_member *members, int32_t n_member
         if (st == MS_ERR_NOT_CONVERGED) worst = st;
     }
     return worst;
+    API_CATCH(ctx)
+}
+
+ms_status ms_total_mobility(ms_ctx *ctx, const ms_system *s, const ms_fluid *fl, const double *S, double *lam) {
+    if (!ctx || !s || !fl || !S || !lam) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    API_TRY
+    DeviceGuard g(ctx->device);
+    MS_REQUIRE(fl->mu_w > 0 && fl->mu_o > 0 && fl->s_wc + fl->s_or < 1.0, MS_ERR_INVALID_ARG, "bad fluid");
+    cudaStream_t st = ctx->stream;
+    const double par[6] = {fl->mu_w, fl->mu_o, fl->n_w, fl->n_o, fl->s_wc, fl->s_or};
+    DBuf<double> stage, out;
+    const double *Sd = device_in(S, s->n, stage, st);
+    double *ld = lam;
+    if (!is_device_ptr(lam)) {
+        out.alloc(s->n);
+        ld = out.p;
+    }
+    launch_total_mobility(s->n, par, Sd, ld, st);
+    if (ld != lam) copy_out(lam, ld, s->n, st);
+    sync(st);
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_transport_step(ms_ctx *ctx, ms_system *s, const ms_fluid *fl, const double *p, const double *q,
+                            double dt, double *S, int32_t *substeps) {
+    if (!ctx || !s || !fl || !p || !q || !S) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    API_TRY
+    DeviceGuard g(ctx->device);
+    MS_REQUIRE(s->assembled, MS_ERR_STATE, "system not assembled");
+    MS_REQUIRE(fl->mu_w > 0 && fl->mu_o > 0 && fl->s_wc + fl->s_or < 1.0 && fl->porosity > 0 && fl->cfl > 0 &&
+                   dt >= 0,
+               MS_ERR_INVALID_ARG, "bad fluid or time step");
+    cudaStream_t st = ctx->stream;
+    const int n = s->n;
+    const double par[6] = {fl->mu_w, fl->mu_o, fl->n_w, fl->n_o, fl->s_wc, fl->s_or};
+    DBuf<double> sp, sq;
+    const double *pd = device_in(p, n, sp, st);
+    const double *qd = device_in(q, n, sq, st);
+    s->w_tu.alloc(std::max(s->nf, 1));
+    s->w_ts.alloc((size_t)3 * n);
+    double *S0 = s->w_ts.p, *S1 = S0 + n, *fw = S1 + n;
+    MS_CUDA(cudaMemcpyAsync(S0, S, n * sizeof(double), is_device_ptr(S) ? cudaMemcpyDeviceToDevice
+                                                                         : cudaMemcpyHostToDevice, st));
+    launch_face_flux(*s, pd, s->w_tu.p, st);
+    const double pv = fl->porosity * s->dx * s->dy * s->dz;
+    s->w_max.alloc(1);
+    const unsigned long long inf_bits = 0x7FF0000000000000ull;   // +infinity
+    MS_CUDA(cudaMemcpyAsync(s->w_max.p, &inf_bits, sizeof(inf_bits), cudaMemcpyHostToDevice, st));
+    launch_outflow_limit(*s, s->w_tu.p, qd, pv, s->w_max.p, st);
+    unsigned long long *h = (unsigned long long *)ctx->pinned.get(64);
+    MS_CUDA(cudaMemcpyAsync(h, s->w_max.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    sync(st);
+    double tmin;
+    std::memcpy(&tmin, h, sizeof(double));
+    const double slope = frac_flow_max_slope(fl->mu_w, fl->mu_o, fl->n_w, fl->n_o, fl->s_wc, fl->s_or);
+    const double hmax = slope > 0 ? fl->cfl * tmin / slope : INFINITY;
+    int nsub = 1;
+    if (dt > 0 && std::isfinite(hmax)) {
+        const double k = std::ceil(dt / hmax);
+        MS_REQUIRE(k < 1e7, MS_ERR_INVALID_ARG, "time step needs more than 1e7 transport substeps");
+        nsub = std::max(1, (int)k);
+    }
+    const double hs = dt / nsub;
+    for (int k = 0; k < nsub; ++k) {
+        launch_transport_substep(*s, par, s->w_tu.p, qd, S0, fw, S1, hs / pv, st);
+        std::swap(S0, S1);
+    }
+    MS_CUDA(cudaMemcpyAsync(S, S0, n * sizeof(double), is_device_ptr(S) ? cudaMemcpyDeviceToDevice
+                                                                         : cudaMemcpyDeviceToHost, st));
+    sync(st);
+    if (substeps) *substeps = nsub;
+    return MS_OK;
     API_CATCH(ctx)
 }
 

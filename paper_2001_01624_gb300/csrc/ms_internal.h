@@ -230,6 +230,7 @@ struct ms_system {
     msgb::DBuf<double> w_kry;                 // GMRES: V [(m+1) n], Z [m n], w, q copy; dot scratch
     msgb::DBuf<double> w_kred, w_kh;
     msgb::DBuf<unsigned int> w_kcnt;
+    msgb::DBuf<double> w_tu, w_ts, w_tq;      // transport: face fluxes, saturation buffer, sources
     msgb::DBuf<double> w_red;                 // reduction partials
     msgb::DBuf<unsigned int> w_cnt;           // reduction counters
     msgb::DBuf<unsigned long long> w_max;     // max reductions
@@ -328,6 +329,14 @@ void launch_jacobi(const ms_system &s, const double *r, double *z, double omega,
 void launch_jacobi32(const ms_system &s, const double *r, float *z, float omega, cudaStream_t st);
 void launch_norm2(const double *v, int n, double *red, unsigned int *cnt, double *out, cudaStream_t st);
 int multidot_blocks(int n);
+// two-phase transport; fl = (mu_w, mu_o, n_w, n_o, s_wc, s_or)
+double frac_flow_max_slope(double mu_w, double mu_o, double n_w, double n_o, double s_wc, double s_or);
+void launch_total_mobility(int n, const double fl[6], const double *S, double *lam, cudaStream_t st);
+void launch_face_flux(const ms_system &s, const double *p, double *u, cudaStream_t st);
+void launch_outflow_limit(const ms_system &s, const double *u, const double *q, double pore_volume,
+                          unsigned long long *min_bits, cudaStream_t st);
+void launch_transport_substep(const ms_system &s, const double fl[6], const double *u, const double *q,
+                              const double *S, double *fw, double *Snew, double h_over_pv, cudaStream_t st);
 void launch_multidot(int n, int k, const double *V, const double *w, double *red, unsigned int *cnt, double *h,
                      cudaStream_t st);
 void launch_multiaxpy(int n, int k, const double *V, const double *c, double sign, double *y, cudaStream_t st);

@@ -513,3 +513,29 @@ def test_ilu_apply_full_size_config2(ms, ctx):
     ms.ms_ilu_apply(ctx, s, qp, z)
     np.testing.assert_allclose(z, zr, rtol=1e-9, atol=1e-11 * np.abs(zr).max())
     ms.ms_system_release(s)
+
+
+# ---------------------------------------------------------------- two-phase
+@pytest.mark.parametrize("case", ["3d_10x10x4", "faulted_18x14x7"])
+def test_mobility_and_transport_match_oracle(ms, ctx, case):
+    gm = CASES[case]()
+    n = gm.grid.n_active()
+    rng = np.random.default_rng(11)
+    S = rng.uniform(0, 1, n)
+    fl = ms.fluid(mu_w=1.0, mu_o=3.0, porosity=0.2, cfl=0.9)
+    s = ms.ms_system_create(ctx, gm.grid, 0)
+    lam = ms.ms_total_mobility(ctx, s, fl, S)
+    np.testing.assert_allclose(lam, O.total_mobility(S), rtol=1e-14)
+    p_prev = rng.standard_normal(n)
+    ms.ms_assemble_tpfa(ctx, s, gm.perm.ravel(), mobility=lam, p_prev=p_prev)
+    ref = O.assemble_tpfa(gm.grid, gm.perm, lam=lam, p_prev=p_prev)
+    p = rng.standard_normal(n) * 1e6
+    q = gm.q_active() * 1e-3
+    vol = gm.grid.dx * gm.grid.dy * gm.grid.dz
+    dt = 30.0 * vol / np.abs(q).sum()
+    S_gpu = S.copy()
+    k = ms.ms_transport_step(ctx, s, fl, p, q, dt, S_gpu)
+    S_ref, k_ref = O.transport_step(ref.A, p, q, S, dt, porosity=0.2, volume=vol, cfl=0.9)
+    assert k == k_ref and k > 1
+    np.testing.assert_allclose(S_gpu, S_ref, rtol=1e-11, atol=1e-12)
+    ms.ms_system_release(s)

@@ -456,3 +456,69 @@ def test_cost_model_is_sum_of_itemised_counts(N, Np, d, b, Nc):
     residual_update = Nc * N * d + Nc * N
     corrector = 2 * d * Nc ** 2 * N + Nc * N
     assert O.cost_model(N, Np, d, b, Nc) == pytest.approx(predictor + residual_update + corrector, rel=1e-14)
+
+
+# ------------------------------------------------------------- two-phase
+def test_total_mobility_closed_forms():
+    lam = O.total_mobility([0.0, 1.0, 0.5], dict(mu_w=1.0, mu_o=3.0))
+    np.testing.assert_allclose(lam, [1.0 / 3.0, 1.0, 0.25 + 0.25 / 3.0], rtol=1e-15)
+    # residual saturations: Se clipped, so S <= s_wc is immobile water
+    lam = O.total_mobility([0.1, 0.95], dict(mu_w=2.0, mu_o=4.0, s_wc=0.2, s_or=0.1))
+    np.testing.assert_allclose(lam, [0.25, 0.5], rtol=1e-15)
+
+
+def _pressure(gm, lam, p_prev=None):
+    sysm = O.assemble_tpfa(gm.grid, gm.perm, lam=lam, p_prev=p_prev)
+    Ap, qp = O.pin(sysm.A, gm.q_active(), 0)
+    return sysm, np.linalg.solve(Ap.dense(), qp)
+
+
+def test_transport_keeps_pure_water_and_bounds():
+    """A divergence-free total flux carries S = 1 unchanged (f_w = 1 and the
+    pressure solution balances every cell); from any S in [0, 1] the monotone
+    upstream scheme under the CFL limit stays in [0, 1]."""
+    gm = G.lognormal_box(9, 7, 3, seed=4, block=(3, 7, 3), kz_ratio=0.1)
+    n = gm.grid.n_active()
+    q = gm.q_active() * 1e-3
+    gm.q[:] = 0
+    gm.q[gm.grid.active_cells()] = q
+    S = np.ones(n)
+    sysm, p = _pressure(gm, O.total_mobility(S))
+    vol = gm.grid.dx * gm.grid.dy * gm.grid.dz
+    S1, k = O.transport_step(sysm.A, p, q, S, dt=50.0 * vol / np.abs(q).sum(), volume=vol)
+    assert k > 1
+    np.testing.assert_allclose(S1, 1.0, atol=1e-9)
+    S = np.random.default_rng(3).uniform(0, 1, n)
+    sysm, p = _pressure(gm, O.total_mobility(S), p_prev=np.random.default_rng(4).standard_normal(n))
+    S1, k = O.transport_step(sysm.A, p, q, S, dt=20.0 * vol / np.abs(q).sum(), volume=vol)
+    assert S1.min() >= -1e-12 and S1.max() <= 1 + 1e-12
+
+
+def test_transport_buckley_leverett_front():
+    """1D water flood (mu_w = 1, mu_o = 3, Corey n = 2, no residuals): the
+    saturation front moves at f_w'(S_f) times the injected pore volumes, S_f
+    the Welge tangent point f_w(S_f) / S_f = f_w'(S_f) (Buckley-Leverett).
+    The upstream scheme's smeared front brackets that position."""
+    n = 800
+    gm = G.homogeneous(n, 1, 1, block=(10, 1, 1))
+    gm.q[:] = 0
+    gm.q[0], gm.q[n - 1] = 1e-3, -1e-3
+    q = gm.q_active()
+    vol = gm.grid.dx * gm.grid.dy * gm.grid.dz
+    phi = 0.2
+    S = np.zeros(n)
+    pvi = 0.3
+    dt_total = pvi * phi * vol * n / 1e-3
+    for _ in range(6):                       # sequential steps (the 1D total flux is q whatever lambda is)
+        sysm, p = _pressure(gm, O.total_mobility(S))
+        S, _ = O.transport_step(sysm.A, p, q, S, dt=dt_total / 6, porosity=phi, volume=vol)
+    fw = lambda s: s * s / (s * s + (1 - s) ** 2 / 3.0)
+    ss = np.linspace(0.3, 0.9, 600001)
+    d = (fw(ss + 1e-7) - fw(ss - 1e-7)) / 2e-7
+    sf = ss[np.argmin(np.abs(fw(ss) / ss - d))]
+    dfs = (fw(sf + 1e-7) - fw(sf - 1e-7)) / 2e-7
+    x_front = dfs * pvi                      # fraction of the column
+    cross = np.argmax(S < 0.5 * sf) / n
+    assert abs(cross - x_front) < 0.03, (cross, x_front, sf)
+    # mass balance: water in place = water injected (nothing produced yet)
+    assert abs(S.sum() * phi * vol - 1e-3 * dt_total) <= 1e-9 * 1e-3 * dt_total
