@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run N extra untimed steps only (for ncu launch lists)")
+    ap.add_argument("--profile-ilu", type=int, default=0,
+                    help="only assemble the c2 system and apply ILU(0) N times in each precision (for ncu captures)")
+    ap.add_argument("--nz", type=int, default=85, help="--profile-ilu: layers of the 60x220 grid")
     ap.add_argument("--workload", choices=["c2", "ensemble", "serving"], default="c2",
                     help="c2: the 60x220x85 geomodel (headline); ensemble: the batched uneven ensemble; "
                          "serving: Poisson stream of two-phase time steps on resident geomodels")
@@ -526,10 +529,38 @@ def ensemble_oracle_sample(mem, out):
                       f"full, 10 basis iterations and 10 cycles timed, scaled to each member's GPU iteration counts"}
 
 
+def run_profile_ilu(args):
+    """ILU(0) applications alone on the 60x220xNZ geomodel (untimed)."""
+    import torch
+    import numpy as np
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2001_01624_gb300 as ms
+    from paper_2001_01624_gb300 import geomodel as G
+    dev = torch.device("cuda:0")
+    gm = G.config2(0) if args.nz == 85 else G.lognormal_box(60, 220, args.nz, seed=0, block=(10, 20, 5), kz_ratio=0.1)
+    stream = torch.cuda.Stream(dev)
+    ctx = ms.ms_create(0, stream)
+    s = ms.ms_system_create(ctx, gm.grid, 0)
+    with torch.cuda.stream(stream):
+        ms.ms_assemble_tpfa(ctx, s, torch.from_numpy(gm.perm.ravel().copy()).to(dev))
+        r = torch.from_numpy(gm.q_active()).to(dev)
+        z = torch.zeros_like(r)
+        for prec in (ms.MS_PREC_FP64, ms.MS_PREC_MIXED):
+            for _ in range(args.profile_ilu):
+                ms.ms_ilu_apply(ctx, s, r, z, prec)
+    torch.cuda.synchronize()
+    ms.ms_system_release(s)
+    ms.ms_destroy(ctx)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_ilu:
+        return run_profile_ilu(args)
     if args.workload == "ensemble":
         return run_ensemble(args)
     if args.workload == "serving":
