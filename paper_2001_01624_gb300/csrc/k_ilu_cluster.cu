@@ -120,25 +120,6 @@ __device__ __forceinline__ T shfl_up(T v, int d) {
     return __shfl_up_sync(0xffffffffu, v, d);
 }
 
-// wait for a barrier phase, bounded; the result is uniform across the warp
-__device__ __forceinline__ bool wait_phase(unsigned bar, unsigned parity, int *err) {
-    unsigned long long t0 = 0;
-    int spins = 0;
-    bool ok = true;
-    while (!mb_try(bar, parity)) {
-        if ((++spins & 63) == 0) {
-            const unsigned long long now = global_ns();
-            if (t0 == 0) t0 = now;
-            else if (now - t0 > kWaitNs) {
-                atomicOr(err, kErrTimeout);
-                ok = false;
-                break;
-            }
-        }
-    }
-    return __all_sync(0xffffffffu, ok);
-}
-
 // the four packed coefficients of one cell
 template <typename T>
 struct Coef4 {
@@ -158,34 +139,61 @@ __host__ __device__ constexpr int rhs_win(int nx, int esz) {
     return (nx + 3 * (16 / esz) + 16 / esz - 1) / (16 / esz) * (16 / esz);
 }
 
-template <typename T, typename TR, bool BWD, int E>
+// wait for a barrier phase, bounded; per lane (no warp vote)
+__device__ __forceinline__ bool wait_lane(unsigned bar, unsigned parity, int *err) {
+    unsigned long long t0 = 0;
+    int spins = 0;
+    while (!mb_try(bar, parity)) {
+        if ((++spins & 63) == 0) {
+            const unsigned long long now = global_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > kWaitNs) {
+                atomicOr(err, kErrTimeout);
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
+// G k-rows per warp, in lane groups of L = 32 / G lanes; E cells per lane.
+// Warp step t: group h solves line t - h of its row, so the k-neighbour of
+// groups h > 0 is the line group h - 1 finished in step t - 1 (passed by a
+// shuffle); group 0 receives its k-neighbour from the previous warp's last
+// row through the exchange ring, and group G - 1 sends to the next warp's.
+template <typename T, typename TR, bool BWD, int E, int G>
 __global__ void __launch_bounds__(544, 1)
     k_line_cluster(int nx, int ny, int nz, int TK, const T *__restrict__ coef4, const TR *__restrict__ rhs,
                    T *__restrict__ out, int *err) {
-    constexpr int LW = 32 * E;
+    constexpr int L = 32 / G;
+    constexpr int LW = L * E;
+    constexpr unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const unsigned K = cluster_rank();
+    const int RPC = TK * G;   // rows per CTA
     const int WR = rhs_win(nx, sizeof(TR));
     const int CLN = nx * 4;   // packed coefficient line (elements of T)
-    // shared: coefficient slots [RF][TK][CLN] T | rhs slots [RF][TK][WR] TR | exchange [TK][NBX][LW] T |
-    //         barriers full_f, empty_f [RF][TK], full_x, empty_x [NBX][TK]
+    // shared: coefficient slots [RF][RPC][CLN] T | rhs slots [RF][RPC][WR] TR | exchange [TK][NBX][LW] T |
+    //         barriers full_f, empty_f [RF][RPC], full_x, empty_x [NBX][TK]
     extern __shared__ __align__(16) unsigned char smraw[];
     T *cwin = reinterpret_cast<T *>(smraw);
-    size_t off = (size_t)RF * TK * CLN * sizeof(T);
+    size_t off = (size_t)RF * RPC * CLN * sizeof(T);
     TR *rwin = reinterpret_cast<TR *>(smraw + off);
-    off += (size_t)RF * TK * WR * sizeof(TR);
+    off += (size_t)RF * RPC * WR * sizeof(TR);
     T *xin = reinterpret_cast<T *>(smraw + off);
     off += (size_t)TK * NBX * LW * sizeof(T);
     const unsigned full_f = smem_u32(smraw + off);
-    const unsigned empty_f = full_f + 8 * RF * TK;
-    const unsigned full_x = empty_f + 8 * RF * TK;
+    const unsigned empty_f = full_f + 8 * RF * RPC;
+    const unsigned full_x = empty_f + 8 * RF * RPC;
     const unsigned empty_x = full_x + 8 * NBX * TK;
 
-    if (tid < TK) {
+    if (tid < RPC) {
         for (int q = 0; q < RF; ++q) {
-            mb_init(full_f + 8 * (q * TK + tid), 1);
-            mb_init(empty_f + 8 * (q * TK + tid), 1);
+            mb_init(full_f + 8 * (q * RPC + tid), 1);
+            mb_init(empty_f + 8 * (q * RPC + tid), 1);
         }
+    }
+    if (tid < TK) {
         for (int b = 0; b < NBX; ++b) {
             mb_init(full_x + 8 * (b * TK + tid), 1);
             mb_init(empty_x + 8 * (b * TK + tid), 1);
@@ -198,39 +206,39 @@ __global__ void __launch_bounds__(544, 1)
     const long long dj = BWD ? -(long long)nx : (long long)nx;   // real index step from line j to j+1 (mirrored)
     if (w == TK) {
         // producer warp: lane r streams the inputs of row r, each row on its own
-        const int g = (int)K * TK + lane;
-        int tj = (lane < TK && g < nz) ? 0 : ny;
+        const int g = (int)K * RPC + lane;
+        int tj = (lane < RPC && g < nz) ? 0 : ny;
         const int kr = BWD ? nz - 1 - g : g;
         const long long base0 = (long long)nx * (BWD ? ny - 1 : 0) + plane * kr;
         const unsigned lc = (unsigned)nx * 4 * sizeof(T);
         unsigned long long t0 = 0;
         int idle = 0;
-        while (__any_sync(0xffffffffu, tj < ny)) {
+        while (__any_sync(FULL, tj < ny)) {
             bool issued = false;
             if (tj < ny) {
                 const int q = tj % RF;
                 const unsigned u = (unsigned)(tj / RF);
-                if (tj < RF || mb_test(empty_f + 8 * (q * TK + lane), (u - 1) & 1u)) {
+                if (tj < RF || mb_test(empty_f + 8 * (q * RPC + lane), (u - 1) & 1u)) {
                     const long long base = base0 + dj * tj;
-                    const unsigned fb = full_f + 8 * (q * TK + lane);
+                    const unsigned fb = full_f + 8 * (q * RPC + lane);
                     // the rhs line rounded out to 16-byte granules (never leaving the
                     // granule of a valid address, so inside the mapped allocation)
                     const unsigned long long ar = (unsigned long long)(size_t)(rhs + base);
                     const unsigned long long a0 = ar & ~15ull;
                     const unsigned lr = (unsigned)(((ar + (unsigned long long)nx * sizeof(TR) + 15ull) & ~15ull) - a0);
                     mb_expect(fb, lc + lr);
-                    bulk_g2s(smem_u32(cwin + (size_t)(q * TK + lane) * CLN), coef4 + base * 4, lc, fb);
-                    bulk_g2s(smem_u32(rwin + (size_t)(q * TK + lane) * WR), (const void *)(size_t)a0, lr, fb);
+                    bulk_g2s(smem_u32(cwin + (size_t)(q * RPC + lane) * CLN), coef4 + base * 4, lc, fb);
+                    bulk_g2s(smem_u32(rwin + (size_t)(q * RPC + lane) * WR), (const void *)(size_t)a0, lr, fb);
                     ++tj;
                     issued = true;
                 }
             }
-            if (__any_sync(0xffffffffu, issued)) {
+            if (__any_sync(FULL, issued)) {
                 t0 = 0;
             } else {
                 __nanosleep(32);
                 if ((++idle & 63) == 0) {
-                    const unsigned long long now = __shfl_sync(0xffffffffu, global_ns(), 0);
+                    const unsigned long long now = __shfl_sync(FULL, global_ns(), 0);
                     if (t0 == 0) t0 = now;
                     else if (now - t0 > kWaitNs) {
                         if (lane == 0) atomicOr(err, kErrTimeout);
@@ -239,60 +247,83 @@ __global__ void __launch_bounds__(544, 1)
                 }
             }
         }
-    } else if (w < TK && (int)K * TK + w < nz) {
-        const int g = (int)K * TK + w;
+    } else if (w < TK && ((int)K * TK + w) * G < nz) {
+        const int grp = lane / L, gl = lane % L;
+        const int wrow0 = ((int)K * TK + w) * G;             // first row of this warp
+        const int g = wrow0 + grp;                           // row of this lane's group
+        const int rl = w * G + grp;                          // row within the CTA
+        const bool live = g < nz;
         const int kr = BWD ? nz - 1 - g : g;
         const long long base0 = (long long)nx * (BWD ? ny - 1 : 0) + plane * kr;
-        const bool has_src = g > 0, has_dst = g + 1 < nz;
+        const bool has_src = wrow0 > 0;                      // the previous warp's last row exists
+        const bool has_dst = wrow0 + G < nz;                 // the next warp's first row exists (this warp full)
         const bool src_remote = w == 0, dst_remote = w == TK - 1;
-        // a line handed to the next row: LW values, all lanes' E values (cells past nx are padding)
+        // a line handed to the next warp: LW values (cells past nx are padding)
         constexpr unsigned XB = LW * sizeof(T);
         if (has_src && lane == 0)
             for (int b = 0; b < NBX && b < ny; ++b) mb_expect_relaxed(full_x + 8 * (b * TK + w), XB);
-        // where this row's lines go: the next row's exchange ring, here or in CTA K+1
         const unsigned dst_rank = dst_remote ? K + 1 : K;
         const int dst_w = dst_remote ? 0 : w + 1;
-        const unsigned dst_xin = map_cta(smem_u32(xin + (size_t)dst_w * NBX * LW + lane * E), dst_rank);
+        const unsigned dst_xin = map_cta(smem_u32(xin + (size_t)dst_w * NBX * LW + gl * E), dst_rank);
         const unsigned dst_full = map_cta(full_x + 8 * dst_w, dst_rank);
-        // where to release the lines this row read: the previous row's empty ring, here or in CTA K-1
         const unsigned src_empty = has_src ? map_cta(empty_x + 8 * (src_remote ? TK - 1 : w - 1), src_remote ? K - 1 : K) : 0u;
         T prev[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) prev[e] = T(0);
-        for (int tj = 0; tj < ny; ++tj) {
-            const int q = tj % RF, b = tj % NBX;
-            const unsigned u = (unsigned)(tj / RF), ub = (unsigned)(tj / NBX);
-            if (!wait_phase(full_f + 8 * (q * TK + w), u & 1u, err)) break;
+        const int steps = ny + G - 1;
+        for (int t = 0; t < steps; ++t) {
+            const int tj = t - grp;
+            const bool act = live && tj >= 0 && tj < ny;
+            const int q = act ? tj % RF : 0;
+            const unsigned u = act ? (unsigned)(tj / RF) : 0u;
+            bool ok = true;
+            if (act) ok = wait_lane(full_f + 8 * (q * RPC + rl), u & 1u, err);
+            // k-neighbour: the group below finished this line in the previous step
             T nk[E];
 #pragma unroll
-            for (int e = 0; e < E; ++e) nk[e] = T(0);
-            if (has_src) {
-                if (!wait_phase(full_x + 8 * (b * TK + w), ub & 1u, err)) break;
-                const T *xi = xin + ((size_t)w * NBX + b) * LW + lane * E;
+            for (int e = 0; e < E; ++e) nk[e] = G > 1 ? __shfl_up_sync(FULL, prev[e], L) : T(0);
+            const int b = t % NBX;
+            const unsigned ub = (unsigned)(t / NBX);
+            const bool recv = grp == 0 && has_src && act;
+            if (grp == 0) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) nk[e] = T(0);
+            }
+            if (recv) {
+                ok = ok && wait_lane(full_x + 8 * (b * TK + w), ub & 1u, err);
+                const T *xi = xin + ((size_t)w * NBX + b) * LW + gl * E;
 #pragma unroll
                 for (int e = 0; e < E; ++e) nk[e] = xi[e];
             }
-            const long long base = base0 + dj * tj;
-            const int shr = (int)((((unsigned)(size_t)rhs + (unsigned)base * (unsigned)sizeof(TR)) & 15u) / sizeof(TR));
-            const T *cl = cwin + (size_t)(q * TK + w) * CLN;
-            const TR *rl = rwin + (size_t)(q * TK + w) * WR + shr;
+            if (!__all_sync(FULL, ok)) break;
             T A[E], B[E];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const int at = lane * E + e;
                 A[e] = T(1);
                 B[e] = T(0);
-                if (at < nx) {
-                    const int x = BWD ? nx - 1 - at : at;   // real x of the cell
-                    const Coef4<T> c = load_coef(cl + 4 * x);
-                    T bb = (T)rl[x] - c.b * prev[e] - c.c * nk[e];
-                    T aa = -c.a;
-                    if (BWD) {
-                        bb *= c.d;
-                        aa *= c.d;
+            }
+            long long base = 0;
+            if (act) {
+                base = base0 + dj * tj;
+                const int shr =
+                    (int)((((unsigned)(size_t)rhs + (unsigned)base * (unsigned)sizeof(TR)) & 15u) / sizeof(TR));
+                const T *cl = cwin + (size_t)(q * RPC + rl) * CLN;
+                const TR *rl_ = rwin + (size_t)(q * RPC + rl) * WR + shr;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int at = gl * E + e;
+                    if (at < nx) {
+                        const int x = BWD ? nx - 1 - at : at;   // real x of the cell
+                        const Coef4<T> c = load_coef(cl + 4 * x);
+                        T bb = (T)rl_[x] - c.b * prev[e] - c.c * nk[e];
+                        T aa = -c.a;
+                        if (BWD) {
+                            bb *= c.d;
+                            aa *= c.d;
+                        }
+                        A[e] = aa;
+                        B[e] = bb;
                     }
-                    A[e] = aa;
-                    B[e] = bb;
                 }
             }
             T LA = A[0], LB = B[0];
@@ -302,42 +333,55 @@ __global__ void __launch_bounds__(544, 1)
                 LA = A[e] * LA;
             }
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const T pa = shfl_up(LA, d), pb = shfl_up(LB, d);
-                if (lane >= d) {
+            for (int d = 1; d < L; d <<= 1) {
+                const T pa = __shfl_up_sync(FULL, LA, d, L), pb = __shfl_up_sync(FULL, LB, d, L);
+                if (gl >= d) {
                     LB = LA * pb + LB;
                     LA = LA * pa;
                 }
             }
-            T v = shfl_up(LB, 1);
-            if (lane == 0) v = T(0);
+            T v = __shfl_up_sync(FULL, LB, 1, L);
+            if (gl == 0) v = T(0);
+            T val[E];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 v = A[e] * v + B[e];
-                prev[e] = v;
+                val[e] = v;
             }
-            // every lane's reads of slot q and of exchange buffer b fed the scan, so
-            // they are complete: hand both back
-            if (lane == 0) {
-                mb_arrive_relaxed(empty_f + 8 * (q * TK + w));
-                if (has_src) {
-                    if (tj + NBX < ny) mb_expect_relaxed(full_x + 8 * (b * TK + w), XB);
-                    if (src_remote) mb_arrive_relaxed_remote(src_empty + 8 * b * TK);
-                    else mb_arrive_relaxed(src_empty + 8 * b * TK);
+            // every lane's reads of its slot and of the exchange buffer fed the scan
+            // (a warp-wide shuffle), so they are complete: hand both back
+            if (act && gl == 0) mb_arrive_relaxed(empty_f + 8 * (q * RPC + rl));
+            if (recv && gl == 0) {
+                if (t + NBX < ny) mb_expect_relaxed(full_x + 8 * (b * TK + w), XB);
+                if (src_remote) mb_arrive_relaxed_remote(src_empty + 8 * b * TK);
+                else mb_arrive_relaxed(src_empty + 8 * b * TK);
+            }
+            if (act) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) prev[e] = val[e];
+            }
+            // the last group passes its line to the next warp
+            const bool send = has_dst && grp == G - 1 && act;
+            bool ok2 = true;
+            if (send) {
+                const int bs = tj % NBX;
+                const unsigned ubs = (unsigned)(tj / NBX);
+                if (tj >= NBX) ok2 = wait_lane(empty_x + 8 * (bs * TK + w), (ubs - 1) & 1u, err);
+                if (ok2) {
+                    const unsigned xo = dst_xin + (unsigned)(bs * LW * sizeof(T)), fb = dst_full + 8 * bs * TK;
+#pragma unroll
+                    for (int e = 0; e < E; e += 2) st_async2(xo + e * (unsigned)sizeof(T), val[e], val[e + 1], fb);
                 }
             }
-            if (has_dst) {
-                if (tj >= NBX && !wait_phase(empty_x + 8 * (b * TK + w), (ub - 1) & 1u, err)) break;
-                const unsigned xo = dst_xin + (unsigned)(b * LW * sizeof(T)), fb = dst_full + 8 * b * TK;
+            if (act) {
+                T *ob = out + base;
 #pragma unroll
-                for (int e = 0; e < E; e += 2) st_async2(xo + e * (unsigned)sizeof(T), prev[e], prev[e + 1], fb);
+                for (int e = 0; e < E; ++e) {
+                    const int at = gl * E + e;
+                    if (at < nx) ob[BWD ? nx - 1 - at : at] = val[e];
+                }
             }
-            T *ob = out + base;
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int at = lane * E + e;
-                if (at < nx) ob[BWD ? nx - 1 - at : at] = prev[e];
-            }
+            if (!__all_sync(FULL, ok2)) break;
         }
     }
     cluster_sync_all();   // no CTA leaves while a neighbour may still touch its shared memory
@@ -358,19 +402,28 @@ __global__ void k_pack_coef4(int n, const T *__restrict__ dcoef, const T *__rest
     u[3] = dinv[i];
 }
 
-inline int line_cells(int nx) { return nx <= 64 ? 2 : nx <= 128 ? 4 : 8; }
+// Lane layout of a line: G rows per warp (lanes per line L = 32 / G) and E
+// cells per lane.  One row per warp: with G = 4 (8 lanes of 8 cells per line)
+// the lanes' 128-byte strided reads of the packed coefficient line conflict on
+// the same shared-memory banks, and the 60x220x85 sweep measured 0.9 ms FP32
+// against 0.19 ms with G = 1.
+struct LineShape {
+    int G, E;
+};
+inline LineShape line_shape(int nx, bool) { return {1, nx <= 64 ? 2 : nx <= 128 ? 4 : 8}; }
 
 template <typename T, typename TR>
 size_t cluster_smem(int nx, int TK) {
-    const int LW = 32 * line_cells(nx);
-    return (size_t)RF * TK * nx * 4 * sizeof(T) + (size_t)RF * TK * rhs_win(nx, sizeof(TR)) * sizeof(TR) +
-           (size_t)TK * NBX * LW * sizeof(T) + (size_t)8 * 2 * (RF + NBX) * TK;
+    const LineShape ls = line_shape(nx, sizeof(T) == 4);
+    const int RPC = TK * ls.G, LW = (32 / ls.G) * ls.E;
+    return (size_t)RF * RPC * nx * 4 * sizeof(T) + (size_t)RF * RPC * rhs_win(nx, sizeof(TR)) * sizeof(TR) +
+           (size_t)TK * NBX * LW * sizeof(T) + (size_t)8 * 2 * RF * RPC + (size_t)8 * 2 * NBX * TK;
 }
 
-template <typename T, typename TR, bool BWD, int E>
+template <typename T, typename TR, bool BWD, int E, int G>
 cudaError_t launch_cluster_e(const ms_system &s, int TK, int NK, const T *coef4, const TR *rhs, T *out,
                              cudaStream_t st, bool query_only, int *clusters) {
-    auto kern = k_line_cluster<T, TR, BWD, E>;
+    auto kern = k_line_cluster<T, TR, BWD, E, G>;
     const size_t smem = cluster_smem<T, TR>(s.nx, TK);
     static size_t smem_set = 0;                      // per instantiation: attributes are raised once
     static std::atomic<bool> nonportable{false};
@@ -400,10 +453,10 @@ cudaError_t launch_cluster_e(const ms_system &s, int TK, int NK, const T *coef4,
 template <typename T, typename TR, bool BWD>
 cudaError_t launch_cluster(const ms_system &s, int TK, int NK, const T *coef4, const TR *rhs, T *out,
                            cudaStream_t st, bool query_only = false, int *clusters = nullptr) {
-    switch (line_cells(s.nx)) {
-        case 2: return launch_cluster_e<T, TR, BWD, 2>(s, TK, NK, coef4, rhs, out, st, query_only, clusters);
-        case 4: return launch_cluster_e<T, TR, BWD, 4>(s, TK, NK, coef4, rhs, out, st, query_only, clusters);
-        default: return launch_cluster_e<T, TR, BWD, 8>(s, TK, NK, coef4, rhs, out, st, query_only, clusters);
+    switch (line_shape(s.nx, sizeof(T) == 4).E) {
+        case 2: return launch_cluster_e<T, TR, BWD, 2, 1>(s, TK, NK, coef4, rhs, out, st, query_only, clusters);
+        case 4: return launch_cluster_e<T, TR, BWD, 4, 1>(s, TK, NK, coef4, rhs, out, st, query_only, clusters);
+        default: return launch_cluster_e<T, TR, BWD, 8, 1>(s, TK, NK, coef4, rhs, out, st, query_only, clusters);
     }
 }
 
@@ -422,16 +475,20 @@ void cluster_apply(ms_system &s, const T *coef4, const TR *r, T *y, T *z, cudaSt
     MS_CUDA(e);
 }
 
-// Rows per CTA and cluster size for one precision: the cluster spans all k-rows,
-// at most 16 CTAs (more than 8 needs the non-portable size) of at most 16 rows,
-// within the shared-memory limit, and the launch must be schedulable.
+// Warps per CTA and cluster size for one precision: the cluster spans all
+// k-rows (G per warp), at most 16 CTAs (more than 8 needs the non-portable
+// size) of at most 16 warps and 32 rows, within the shared-memory limit, and
+// the launch must be schedulable.  Fewer warps per CTA come first (one warp
+// per SM sub-partition keeps each warp's dependency chain unshared).
 template <typename T, typename TR>
 bool plan_precision(ms_system &s, int p) {
     if (s.nx > 256 || s.ny < 1 || s.nz < 1) return false;
+    const LineShape ls = line_shape(s.nx, sizeof(T) == 4);
+    const int warps = (s.nz + ls.G - 1) / ls.G;
     for (int C : {16, 8}) {
-        const int TK = (s.nz + C - 1) / C;
-        if (TK > 16) continue;
-        const int NK = (s.nz + TK - 1) / TK;
+        const int TK = (warps + C - 1) / C;
+        if (TK > 16 || TK * ls.G > 32) continue;
+        const int NK = (warps + TK - 1) / TK;
         if (cluster_smem<T, TR>(s.nx, TK) > 220 * 1024 || cluster_smem<T, T>(s.nx, TK) > 220 * 1024) continue;
         int c1 = 0, c2 = 0;
         if (launch_cluster<T, TR, false>(s, TK, NK, nullptr, nullptr, nullptr, nullptr, true, &c1) != cudaSuccess ||
