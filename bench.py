@@ -8,7 +8,9 @@ pass of the whole hot path per step on the 3D 60x220x85 geomodel
 
     TPFA assembly -> MsRSB basis smoothing from the block indicator to
     increment 1e-3 -> Galerkin A_c = P^T A P -> dense coarse factor/inverse ->
-    multiscale + ILU(0) Richardson solve from p = 0 to ||q - A p|| <= 1e-6 ||q||
+    multiscale + ILU(0) solve from p = 0 to ||q - A p|| <= 1e-6 ||q||, with
+    GMRES(30) right-preconditioned by the multistage cycle (Sec. 5.2 gives
+    Richardson or GMRES as the outer iteration); Richardson is timed beside it
 
 Inputs (permeability, sources) are resident in HBM when the timed region
 starts; the integer analysis (connection list, wavefront levels, support
@@ -34,7 +36,10 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = ("3D 60x220x85 Cartesian (1,122,000 cells), TPFA 7-point, top 35 layers lognormal "
             "(ln K ~ N(ln 100 mD, 2^2), corr 8 cells, Kz=0.1Kx), bottom 50 layers binary channels 1000:1 "
-            "(Kz=0.1Kx); 6x11x17 coarse blocks of 10x20x5; MsRSB omega 2/3 to 1e-3; MS+ILU(0) Richardson to 1e-6")
+            "(Kz=0.1Kx); 6x11x17 coarse blocks of 10x20x5; MsRSB omega 2/3 to 1e-3; MS+ILU(0) cycle as "
+            "preconditioner of GMRES(30) to 1e-6")
+OUTER = {"gmres": (1, 30), "richardson": (0, 30)}
+ORACLE_GOLD_GMRES = os.path.join(ROOT, "tests", "golden", "oracle_c2_seed0_gmres.json")
 METRIC = "fine-cell unknowns/sec to 1e-6 rel residual (full hot path per step)"
 UNIT = "unknowns/s"
 ORACLE_GOLD = os.path.join(ROOT, "tests", "golden", "oracle_c2_seed0.json")
@@ -153,7 +158,7 @@ def dist_env():
 
 
 # ---------------------------------------------------------------- oracle leg
-def oracle_sample(gm, basis_iters, cycles, full_basis, full_cycles):
+def oracle_sample(gm, basis_iters, cycles, full_basis, full_cycles, outer="gmres"):
     """Time the CPU oracle on a bounded sample of the step and scale the
     iteration phases to the full iteration counts.  Returns (seconds for a
     full step, description)."""
@@ -173,20 +178,25 @@ def oracle_sample(gm, basis_iters, cycles, full_basis, full_cycles):
     lu = O.ilu0(Ap)
     t["fixed"] += time.perf_counter() - t0
     t0 = time.perf_counter()
-    O.ms_solve(Ap, [(B, L)], qp, tol=0.0, max_iter=cycles, lu=lu)
+    if outer == "gmres":
+        O.ms_gmres(Ap, [(B, L)], qp, tol=0.0, max_iter=cycles, restart=OUTER["gmres"][1], lu=lu)
+    else:
+        O.ms_solve(Ap, [(B, L)], qp, tol=0.0, max_iter=cycles, lu=lu)
     t["solve"] = time.perf_counter() - t0
     full = t["fixed"] + t["basis"] * full_basis / basis_iters + t["solve"] * full_cycles / cycles
+    what = "GMRES(30) steps (one full restart)" if outer == "gmres" else "Richardson cycles"
     desc = (f"oracle (plain C, FP64, 1 thread) on the same workload: assembly, pin, partition, supports, "
             f"Galerkin, Cholesky, ILU(0) factor in full; {basis_iters} of {full_basis} basis iterations and "
-            f"{cycles} of {full_cycles} Richardson cycles timed, scaled to the full counts "
+            f"{cycles} of {full_cycles} {what} timed, scaled to the full counts "
             f"(measured {t['fixed'] + t['basis'] + t['solve']:.1f} s)")
     return full, desc
 
 
 def full_counts():
+    """(basis iterations, GMRES steps) of the stored full oracle run."""
     try:
-        g = json.load(open(ORACLE_GOLD))
-        return int(g["basis_iters"]), int(g["cycles"])
+        g = json.load(open(ORACLE_GOLD_GMRES))
+        return int(g["basis_iters"]), int(g["steps"])
     except (OSError, KeyError, ValueError):
         return None
 
@@ -206,11 +216,11 @@ def run_reference(args):
     fb, fc = counts
     n = gm.grid.n_active()
     for _ in range(args.warmup):
-        oracle_sample(gm, 8, 12, fb, fc)
+        oracle_sample(gm, 8, 10, fb, fc)
     secs = []
     desc = ""
     for _ in range(args.steps):
-        s, desc = oracle_sample(gm, 8, 12, fb, fc)
+        s, desc = oracle_sample(gm, 8, 10, fb, fc)
         secs.append(s)
     tot = sum(secs)
     v = n * len(secs) / tot
@@ -241,13 +251,14 @@ class Plan:
         self.n = ms.ms_system_get_info(self.sys)["n"]
         self.M = M
 
-    def step(self, perm=None, q=None, p=None):
+    def step(self, perm=None, q=None, p=None, outer="gmres"):
         ms, ctx = self.ms, self.ctx
         ms.ms_assemble_tpfa(ctx, self.sys, self.perm if perm is None else perm)
         bit = ms.ms_basis_rebuild(ctx, self.sys, self.basis)
         ms.ms_coarse_refresh(ctx, self.sys, self.coarse)
+        o, m = OUTER[outer]
         info = ms.ms_solve(ctx, self.sys, [self.coarse], self.q if q is None else q, self.p if p is None else p,
-                           tol=1e-6, max_iter=5000, precision=self.prec)
+                           tol=1e-6, max_iter=5000, precision=self.prec, outer=o, restart=m)
         info["basis_iters"] = bit
         return info
 
@@ -257,13 +268,13 @@ class Plan:
         self.ms.ms_system_release(self.sys)
 
 
-def timed_steps(torch, plan, stream, K, dist, world):
+def timed_steps(torch, plan, stream, K, dist, world, outer="gmres"):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    infos = [plan.step() for _ in range(K)]
+    infos = [plan.step(outer=outer) for _ in range(K)]
     e1.record(stream)
     torch.cuda.synchronize()
     ms_tot = e0.elapsed_time(e1)
@@ -596,13 +607,13 @@ def main():
         return 0
 
     results = {}
+    rich = {}
     clocks = None
     for prec, plan in plans.items():
         with torch.cuda.stream(stream):
             for _ in range(args.warmup):
                 plan.step()
-        # timed region: tracing off, so the Richardson cycles run as one CUDA graph
-        # per solve (launch counts are still kept, per graph replay)
+        # timed region (tracing off; launch counts are still kept)
         ms.ms_profile_reset()
         sampler = ClockSampler(local) if prec == ms.MS_PREC_FP64 else None
         if sampler:
@@ -611,8 +622,8 @@ def main():
         if sampler:
             clocks = sampler.stop()
         counts = ms.ms_profile_read()
-        # traced step: every launch timed with a pair of CUDA events on its stream
-        # (cycles driven from the host), for the per-kernel durations
+        # traced step: every launch timed with a pair of CUDA events on its stream,
+        # for the per-kernel durations
         ms.ms_profile_reset()
         ms.ms_profile_enable(True)
         plan.step()
@@ -620,6 +631,11 @@ def main():
         ms.ms_profile_enable(False)
         prof = ms.ms_profile_read()
         results[prec] = dict(ms=ms_tot, infos=infos, prof=prof, launches=counts["_total_launches"])
+        # the same step with Richardson cycles (run as one CUDA graph per solve)
+        with torch.cuda.stream(stream):
+            plan.step(outer="richardson")
+        r_ms, r_infos = timed_steps(torch, plan, stream, max(1, args.steps // 2), dist, world, outer="richardson")
+        rich[prec] = dict(ms=r_ms, infos=r_infos, steps=max(1, args.steps // 2))
 
     r64 = results[ms.MS_PREC_FP64]
     K = args.steps
@@ -646,8 +662,8 @@ def main():
                    "precision": "fp64", "parallelism": "replicas (one independent seeded geomodel per GPU)",
                    "l2": "no flush: working set of each step (A, ILU factors, 8-slot basis, vectors) exceeds the "
                          "129 MB L2"},
-        "solve": {"cycles": info0["iters"], "basis_iters": info0["basis_iters"],
-                  "rel_residual": info0["rel_residual"], "solve_ms": solve_ms,
+        "solve": {"outer": "GMRES(30), multistage cycle as right preconditioner", "steps": info0["iters"],
+                  "basis_iters": info0["basis_iters"], "rel_residual": info0["rel_residual"], "solve_ms": solve_ms,
                   "solve_unknowns_per_s": n / (solve_ms * 1e-3)},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs",
@@ -661,13 +677,21 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    line["richardson"] = {}
+    for prec, nm in ((ms.MS_PREC_FP64, "fp64"), (ms.MS_PREC_MIXED, "mixed")):
+        if prec in rich:
+            rr = rich[prec]
+            ir = rr["infos"][-1]
+            line["richardson"][nm] = {"value": n * rr["steps"] * world / (rr["ms"] * 1e-3), "unit": UNIT,
+                                      "ms_per_step": rr["ms"] / rr["steps"], "cycles": ir["iters"],
+                                      "solve_ms": ir["seconds"] * 1e3, "rel_residual": ir["rel_residual"]}
     if ms.MS_PREC_MIXED in results:
         rm = results[ms.MS_PREC_MIXED]
         im = rm["infos"][-1]
         pk = {k: v for k, v in rm["prof"].items() if k != "_total_launches" and v["timed_launches"] > 0}
         tot = sum(v["total_ms"] for v in pk.values())
         line["mixed"] = {"value": n * K * world / (rm["ms"] * 1e-3), "unit": UNIT, "ms_per_step": rm["ms"] / K,
-                         "dtype": "f32 bulk + f64 residual/refinement", "cycles": im["iters"],
+                         "dtype": "f32 bulk + f64 residual/refinement", "steps": im["iters"],
                          "basis_iters": im["basis_iters"], "solve_ms": im["seconds"] * 1e3,
                          "rel_residual": im["rel_residual"],
                          "kernels": {k: {"launches": v["timed_launches"], "ms": round(v["total_ms"], 3),
@@ -703,7 +727,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         counts = full_counts()
         if counts:
-            secs, desc = oracle_sample(gm, 40, 60, counts[0], counts[1])
+            secs, desc = oracle_sample(gm, 40, 30, counts[0], counts[1])
             line["cpu_baseline"] = {"value": n / secs, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
         else:
             line["cpu_baseline"] = None

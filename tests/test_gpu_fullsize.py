@@ -32,7 +32,10 @@ def ms():
     return pkg
 
 
-def _pipeline(ms, gm, prec, dev):
+GOLD_GMRES = os.path.join(os.path.dirname(__file__), "golden", "oracle_c2_seed0_gmres.json")
+
+
+def _pipeline(ms, gm, prec, dev, outer=0, restart=30):
     stream = torch.cuda.Stream(dev)
     ctx = ms.ms_create(0, stream)
     s = ms.ms_system_create(ctx, gm.grid, 0)
@@ -43,7 +46,7 @@ def _pipeline(ms, gm, prec, dev):
     c = ms.ms_galerkin(ctx, s, b, prec)
     q = torch.from_numpy(gm.q_active()).to(dev)
     p = torch.zeros_like(q)
-    info = ms.ms_solve(ctx, s, [c], q, p, tol=1e-6, max_iter=5000, precision=prec)
+    info = ms.ms_solve(ctx, s, [c], q, p, tol=1e-6, max_iter=5000, precision=prec, outer=outer, restart=restart)
     torch.cuda.synchronize()
     x = p.cpu().numpy()
     ms.ms_coarse_release(c)
@@ -84,6 +87,33 @@ def test_config2_full_size_against_stored_oracle(ms, prec):
         k = min(len(g["hist_first"]), len(info["history"]))
         np.testing.assert_allclose(info["history"][:k], g["hist_first"][:k], rtol=1e-6)
     # the final residual, recomputed with the oracle's own matrix
+    s = O.assemble_tpfa(gm.grid, gm.perm)
+    Ap, qp = O.pin(s.A, gm.q_active(), 0)
+    res = np.linalg.norm(qp - Ap.to_scipy() @ x) / np.linalg.norm(qp)
+    assert res <= 1e-6 * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_config2_gmres_full_size_against_stored_oracle(ms, prec):
+    """The bench's headline solve: GMRES(30) preconditioned by the multistage
+    cycle, against the stored full FP64 oracle GMRES run
+    (tests/golden/oracle_c2_seed0_gmres.json): steps within +/-1, the residual
+    history of the first restart, sampled pressures, the final residual with
+    the oracle's matrix."""
+    g = json.load(open(GOLD_GMRES))
+    gm = G.config2(0)
+    P = ms.MS_PREC_FP64 if prec == "fp64" else ms.MS_PREC_MIXED
+    x, bit, info = _pipeline(ms, gm, P, torch.device("cuda:0"), outer=ms.MS_OUTER_GMRES, restart=g["restart"])
+    assert info["converged"]
+    assert abs(info["iters"] - g["steps"]) <= 1, (info["iters"], g["steps"])
+    idx = np.array(g["sample_cells"])
+    ps = np.array(g["p_sample"])
+    tol = 1e-6 if prec == "fp64" else 1e-5
+    assert np.linalg.norm(x[idx] - ps) <= tol * np.linalg.norm(ps)
+    if prec == "fp64":
+        assert bit == g["basis_iters"]
+        k = min(25, len(g["hist"]), len(info["history"]))
+        np.testing.assert_allclose(info["history"][:k], g["hist"][:k], rtol=1e-5)
     s = O.assemble_tpfa(gm.grid, gm.perm)
     Ap, qp = O.pin(s.A, gm.q_active(), 0)
     res = np.linalg.norm(qp - Ap.to_scipy() @ x) / np.linalg.norm(qp)
