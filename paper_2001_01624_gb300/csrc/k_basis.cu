@@ -72,18 +72,21 @@ __global__ void __launch_bounds__(kThreads) k_msrsb(int n, int W, int B, const i
                 }
             }
         }
+        // one division each for omega / A_ii and for the partition-of-unity scale
+        const T od = omega / d;
         T sum = 0;
 #pragma unroll
         for (int s = 0; s < BM; ++s) {
             if (ids[s] != kSlotPad) {
-                acc[s] = v[s] - omega * acc[s] / d;
+                acc[s] = v[s] - od * acc[s];
                 sum += acc[s];
             }
         }
+        const T rs = T(1) / sum;
 #pragma unroll
         for (int s = 0; s < BM; ++s) {
             if (ids[s] != kSlotPad) {
-                const T nv = acc[s] / sum;
+                const T nv = acc[s] * rs;
                 const T dv = nv > v[s] ? nv - v[s] : v[s] - nv;
                 inc = dv > inc ? dv : inc;
                 pout[(int64_t)s * n + i] = nv;
@@ -171,17 +174,20 @@ __global__ void __launch_bounds__(kThreads) k_msrsb_mapped(int n, int W, const i
                 if (s < cnt && t != 15u) acc[s] += a * pin[(int64_t)t * n + k];
             }
         }
+        // one division each for omega / A_ii and for the partition-of-unity scale
+        const T od = omega / d;
         T sum = 0;
 #pragma unroll
         for (int s = 0; s < 8; ++s)
             if (s < cnt) {
-                acc[s] = v[s] - omega * acc[s] / d;
+                acc[s] = v[s] - od * acc[s];
                 sum += acc[s];
             }
+        const T rs = T(1) / sum;
 #pragma unroll
         for (int s = 0; s < 8; ++s)
             if (s < cnt) {
-                const T nv = acc[s] / sum;
+                const T nv = acc[s] * rs;
                 const T dv = nv > v[s] ? nv - v[s] : v[s] - nv;
                 inc = dv > inc ? dv : inc;
                 pout[(int64_t)s * n + i] = nv;

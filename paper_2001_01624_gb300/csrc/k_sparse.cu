@@ -382,10 +382,66 @@ __global__ void k_multidot(int n, int k, const double *__restrict__ V, const dou
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = wid; i < k; i += (int)(blockDim.x >> 5)) {
         double t = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(&red[(int64_t)b * k + i]);
-        h[i] = t;
+        for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(&red[(int64_t)b * k + i]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) h[i] = t;
+    }
+    if (threadIdx.x == 0) *cnt = 0u;
+}
+
+// The same products in one pass over V for k <= 32: each thread keeps all k
+// partial sums; warp trees, then the block's warps in order, then the last
+// block adds the blocks' partials in block order (deterministic).
+__global__ void __launch_bounds__(256) k_multidot32(int n, int k, const double *__restrict__ V,
+                                                    const double *__restrict__ w, double *red, unsigned int *cnt,
+                                                    double *h) {
+    double acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = 0.0;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
+        const double wl = w[l];
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            if (i < k) acc[i] += V[(int64_t)i * n + l] * wl;
+    }
+    __shared__ double part[8][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        if (i < k) {
+            double a = acc[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (lane == 0) part[wid][i] = a;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < k) {
+        double a = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += part[q][threadIdx.x];
+        red[(int64_t)blockIdx.x * k + threadIdx.x] = a;
+    }
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // warp q adds the block partials of products q, q + 8, ...: lanes stride the
+    // blocks, then a fixed shuffle tree
+    for (int i = wid; i < k; i += (int)(blockDim.x >> 5)) {
+        double t = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(&red[(int64_t)b * k + i]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) h[i] = t;
     }
     if (threadIdx.x == 0) *cnt = 0u;
 }
@@ -415,7 +471,8 @@ int multidot_blocks(int n) { return stride_grid(n); }
 void launch_multidot(int n, int k, const double *V, const double *w, double *red, unsigned int *cnt, double *h,
                      cudaStream_t st) {
     KernelScope ks_(st, "krylov_dot", (double)(k + 1) * n * 8);
-    k_multidot<<<stride_grid(n), kThreads, 0, st>>>(n, k, V, w, red, cnt, h);
+    if (k <= 32) k_multidot32<<<stride_grid(n), kThreads, 0, st>>>(n, k, V, w, red, cnt, h);
+    else k_multidot<<<stride_grid(n), kThreads, 0, st>>>(n, k, V, w, red, cnt, h);
     MS_CHECK_LAUNCH();
 }
 
