@@ -6,7 +6,8 @@ Sec. 5 multiscale solver):
     lambda_t(S)  ->  TPFA assembly with upstream face mobility (previous p)
     ->  Galerkin operator of the resident basis re-formed  (basis kept)
     ->  dynamic stage from the previous pressure change dp (adaptive refresh)
-    ->  multiscale solve from the previous pressure to 1e-6
+    ->  GMRES preconditioned by the multiscale cycle, from the previous
+        pressure to 1e-6
     ->  explicit upstream saturation transport with CFL substeps.
 
 Continuous batching: a pool of worker slots (one library context and CUDA
@@ -118,7 +119,7 @@ class Model:
             stages.append(dyn_c)
         p_old = self.p.clone()
         info = ms.ms_solve(ctx, self.sys, stages, self.qd, self.p, tol=tol, max_iter=max_iter, precision=precision,
-                           use_x0=self.steps > 0)
+                           use_x0=self.steps > 0, outer=ms.MS_OUTER_GMRES, restart=30)
         if dyn_c is not None:
             ms.ms_coarse_release(dyn_c)
             ms.ms_basis_release(dyn_b)
