@@ -31,6 +31,8 @@
 // bounded in device time and report a timeout instead of hanging.
 #include <atomic>
 
+#include <cstdlib>
+
 #include "ms_internal.h"
 
 namespace msgb {
@@ -387,19 +389,61 @@ __global__ void __launch_bounds__(544, 1)
     cluster_sync_all();   // no CTA leaves while a neighbour may still touch its shared memory
 }
 
+// Packed sweep coefficients.  x-lines: cell i keeps (Lx, Ly, Lz, 0) and
+// (Ux, Uy, Uz, 1/U_ii).  y-lines (transposed = 1): the cell moves to
+// t = y + ny (x + nx z) and keeps (Ly, Lx, Lz, 0) and (Uy, Ux, Uz, 1/U_ii), so
+// that the in-line neighbour comes first, then the previous line's.
 template <typename T>
-__global__ void k_pack_coef4(int n, const T *__restrict__ dcoef, const T *__restrict__ dinv, T *__restrict__ out) {
+__global__ void k_pack_coef4(int n, int nx, int ny, int transposed, const T *__restrict__ dcoef,
+                             const T *__restrict__ dinv, T *__restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    T *l = out + (size_t)i * 4, *u = out + ((size_t)n + i) * 4;
-    l[0] = dcoef[i];
-    l[1] = dcoef[(size_t)n + i];
+    int t = i, a = 0, b = 1;
+    if (transposed) {
+        const int x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
+        t = y + ny * (x + nx * z);
+        a = 1;
+        b = 0;
+    }
+    T *l = out + (size_t)t * 4, *u = out + ((size_t)n + t) * 4;
+    l[0] = dcoef[(size_t)a * n + i];
+    l[1] = dcoef[(size_t)b * n + i];
     l[2] = dcoef[(size_t)2 * n + i];
     l[3] = T(0);
-    u[0] = dcoef[(size_t)3 * n + i];
-    u[1] = dcoef[(size_t)4 * n + i];
+    u[0] = dcoef[(size_t)(3 + a) * n + i];
+    u[1] = dcoef[(size_t)(3 + b) * n + i];
     u[2] = dcoef[(size_t)5 * n + i];
     u[3] = dinv[i];
+}
+
+// out[y + ny (x + nx z)] = in[x + nx (y + ny z)] (inverse = 1: the other way),
+// 32 x 32 tiles of each z plane through shared memory
+template <typename TI, typename TO>
+__global__ void k_transpose_xy(int nx, int ny, int inverse, const TI *__restrict__ in, TO *__restrict__ out) {
+    __shared__ TO tile[32][33];
+    const int z = blockIdx.z;
+    // tile of the source plane: rows r (slow index), columns c (fast index)
+    const int R = inverse ? nx : ny, Cn = inverse ? ny : nx;
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const size_t plane = (size_t)nx * ny * z;
+    for (int dr = threadIdx.y; dr < 32; dr += blockDim.y) {
+        const int r = r0 + dr, c = c0 + threadIdx.x;
+        if (r < R && c < Cn) tile[dr][threadIdx.x] = (TO)in[plane + (size_t)r * Cn + c];
+    }
+    __syncthreads();
+    for (int dc = threadIdx.y; dc < 32; dc += blockDim.y) {
+        const int c = c0 + dc, r = r0 + threadIdx.x;
+        if (r < R && c < Cn) out[plane + (size_t)c * R + r] = tile[threadIdx.x][dc];
+    }
+}
+
+template <typename TI, typename TO>
+void transpose_xy(const ms_system &s, bool inverse, const TI *in, TO *out, cudaStream_t st) {
+    const int R = inverse ? s.nx : s.ny, Cn = inverse ? s.ny : s.nx;
+    const dim3 grid((Cn + 31) / 32, (R + 31) / 32, s.nz), block(32, 8);
+    KernelScope ks_(st, "transpose", (double)s.n * (sizeof(TI) + sizeof(TO)));
+    k_transpose_xy<TI, TO><<<grid, block, 0, st>>>(s.nx, s.ny, inverse ? 1 : 0, in, out);
+    MS_CHECK_LAUNCH();
 }
 
 // Lane layout of a line: G rows per warp (lanes per line L = 32 / G) and E
@@ -421,10 +465,10 @@ size_t cluster_smem(int nx, int TK) {
 }
 
 template <typename T, typename TR, bool BWD, int E, int G>
-cudaError_t launch_cluster_e(const ms_system &s, int TK, int NK, const T *coef4, const TR *rhs, T *out,
-                             cudaStream_t st, bool query_only, int *clusters) {
+cudaError_t launch_cluster_e(const ms_system &s, const int dims[3], int TK, int NK, const T *coef4, const TR *rhs,
+                             T *out, cudaStream_t st, bool query_only, int *clusters) {
     auto kern = k_line_cluster<T, TR, BWD, E, G>;
-    const size_t smem = cluster_smem<T, TR>(s.nx, TK);
+    const size_t smem = cluster_smem<T, TR>(dims[0], TK);
     static size_t smem_set = 0;                      // per instantiation: attributes are raised once
     static std::atomic<bool> nonportable{false};
     cudaError_t e = raise_smem_limit(kern, smem, smem_set);
@@ -447,17 +491,24 @@ cudaError_t launch_cluster_e(const ms_system &s, int TK, int NK, const T *coef4,
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (query_only) return cudaOccupancyMaxActiveClusters(clusters, kern, &cfg);
-    return cudaLaunchKernelEx(&cfg, kern, s.nx, s.ny, s.nz, TK, coef4, rhs, out, s.sync.p + 3);
+    return cudaLaunchKernelEx(&cfg, kern, dims[0], dims[1], dims[2], TK, coef4, rhs, out, s.sync.p + 3);
 }
 
+// dims: (line length, lines walked per row, rows) of the sweep's layout
 template <typename T, typename TR, bool BWD>
-cudaError_t launch_cluster(const ms_system &s, int TK, int NK, const T *coef4, const TR *rhs, T *out,
-                           cudaStream_t st, bool query_only = false, int *clusters = nullptr) {
-    switch (line_shape(s.nx, sizeof(T) == 4).E) {
-        case 2: return launch_cluster_e<T, TR, BWD, 2, 1>(s, TK, NK, coef4, rhs, out, st, query_only, clusters);
-        case 4: return launch_cluster_e<T, TR, BWD, 4, 1>(s, TK, NK, coef4, rhs, out, st, query_only, clusters);
-        default: return launch_cluster_e<T, TR, BWD, 8, 1>(s, TK, NK, coef4, rhs, out, st, query_only, clusters);
+cudaError_t launch_cluster(const ms_system &s, const int dims[3], int TK, int NK, const T *coef4, const TR *rhs,
+                           T *out, cudaStream_t st, bool query_only = false, int *clusters = nullptr) {
+    switch (line_shape(dims[0], sizeof(T) == 4).E) {
+        case 2: return launch_cluster_e<T, TR, BWD, 2, 1>(s, dims, TK, NK, coef4, rhs, out, st, query_only, clusters);
+        case 4: return launch_cluster_e<T, TR, BWD, 4, 1>(s, dims, TK, NK, coef4, rhs, out, st, query_only, clusters);
+        default: return launch_cluster_e<T, TR, BWD, 8, 1>(s, dims, TK, NK, coef4, rhs, out, st, query_only, clusters);
     }
+}
+
+inline void sweep_dims(const ms_system &s, int p, int dims[3]) {
+    dims[0] = s.cl_T[p] ? s.ny : s.nx;
+    dims[1] = s.cl_T[p] ? s.nx : s.ny;
+    dims[2] = s.nz;
 }
 
 template <typename T, typename TR>
@@ -465,34 +516,47 @@ void cluster_apply(ms_system &s, const T *coef4, const TR *r, T *y, T *z, cudaSt
     const int64_t n = s.n;
     const int p = sizeof(T) == 8 ? 0 : 1;
     const double nl = (double)s.nnz_lower;
+    int dims[3];
+    sweep_dims(s, p, dims);
+    const TR *rin = r;
+    T *zout = z;
+    if (s.cl_T[p]) {   // y-lines: sweeps on transposed copies of the vectors
+        TR *rt = reinterpret_cast<TR *>(sizeof(TR) == 8 ? (void *)s.w_T64.p : (void *)s.w_T32.p);
+        transpose_xy<TR, TR>(s, false, r, rt, st);
+        rin = rt;
+        zout = reinterpret_cast<T *>(sizeof(T) == 8 ? (void *)s.w_T64b.p : (void *)s.w_T32b.p);
+    }
     {
         KernelScope ks_(st, sizeof(T) == 8 ? "ilu_fwd" : "ilu_fwd32", nl * sizeof(T) + (double)n * (sizeof(TR) + sizeof(T)));
-        const cudaError_t e = launch_cluster<T, TR, false>(s, s.cl_TK[p], s.cl_NK[p], coef4, r, y, st);
+        const cudaError_t e = launch_cluster<T, TR, false>(s, dims, s.cl_TK[p], s.cl_NK[p], coef4, rin, y, st);
         MS_CUDA(e);
     }
-    KernelScope ks_(st, sizeof(T) == 8 ? "ilu_bwd" : "ilu_bwd32", nl * sizeof(T) + (double)n * 3 * sizeof(T));
-    const cudaError_t e = launch_cluster<T, T, true>(s, s.cl_TK[p], s.cl_NK[p], coef4 + (size_t)4 * n, y, z, st);
-    MS_CUDA(e);
+    {
+        KernelScope ks_(st, sizeof(T) == 8 ? "ilu_bwd" : "ilu_bwd32", nl * sizeof(T) + (double)n * 3 * sizeof(T));
+        const cudaError_t e = launch_cluster<T, T, true>(s, dims, s.cl_TK[p], s.cl_NK[p], coef4 + (size_t)4 * n, y, zout, st);
+        MS_CUDA(e);
+    }
+    if (s.cl_T[p]) transpose_xy<T, T>(s, true, zout, z, st);
 }
 
-// Warps per CTA and cluster size for one precision: the cluster spans all
-// k-rows (G per warp), at most 16 CTAs (more than 8 needs the non-portable
-// size) of at most 16 warps and 32 rows, within the shared-memory limit, and
-// the launch must be schedulable.  Fewer warps per CTA come first (one warp
-// per SM sub-partition keeps each warp's dependency chain unshared).
+// Warps per CTA and cluster size for one precision and sweep layout dims: the
+// cluster spans all k-rows (G per warp), at most 16 CTAs (more than 8 needs the
+// non-portable size) of at most 16 warps and 32 rows, within the shared-memory
+// limit, and the launch must be schedulable.  Fewer warps per CTA come first
+// (one warp per SM sub-partition keeps each warp's dependency chain unshared).
 template <typename T, typename TR>
-bool plan_precision(ms_system &s, int p) {
-    if (s.nx > 256 || s.ny < 1 || s.nz < 1) return false;
-    const LineShape ls = line_shape(s.nx, sizeof(T) == 4);
-    const int warps = (s.nz + ls.G - 1) / ls.G;
+bool plan_precision(ms_system &s, int p, const int dims[3]) {
+    if (dims[0] > 256 || dims[1] < 1 || dims[2] < 1) return false;
+    const LineShape ls = line_shape(dims[0], sizeof(T) == 4);
+    const int warps = (dims[2] + ls.G - 1) / ls.G;
     for (int C : {16, 8}) {
         const int TK = (warps + C - 1) / C;
         if (TK > 16 || TK * ls.G > 32) continue;
         const int NK = (warps + TK - 1) / TK;
-        if (cluster_smem<T, TR>(s.nx, TK) > 220 * 1024 || cluster_smem<T, T>(s.nx, TK) > 220 * 1024) continue;
+        if (cluster_smem<T, TR>(dims[0], TK) > 220 * 1024 || cluster_smem<T, T>(dims[0], TK) > 220 * 1024) continue;
         int c1 = 0, c2 = 0;
-        if (launch_cluster<T, TR, false>(s, TK, NK, nullptr, nullptr, nullptr, nullptr, true, &c1) != cudaSuccess ||
-            launch_cluster<T, T, true>(s, TK, NK, nullptr, nullptr, nullptr, nullptr, true, &c2) != cudaSuccess) {
+        if (launch_cluster<T, TR, false>(s, dims, TK, NK, nullptr, nullptr, nullptr, nullptr, true, &c1) != cudaSuccess ||
+            launch_cluster<T, T, true>(s, dims, TK, NK, nullptr, nullptr, nullptr, nullptr, true, &c2) != cudaSuccess) {
             cudaGetLastError();
             continue;
         }
@@ -507,19 +571,43 @@ bool plan_precision(ms_system &s, int p) {
 
 }  // namespace
 
+// Sweep layouts: x-lines (critical path ny + nz - 1 line steps), or, for FP32
+// with MSGB_ILU_LINES=y, y-lines on transposed vectors when ny > nx (critical
+// path nx + nz - 1).  x-lines are the default: with 8 cells per lane the
+// lanes' 128-byte strided reads of a y-line's packed coefficients serialise on
+// one shared-memory bank group, and the 60x220x85 FP32 sweep measured
+// 0.23 ms on y-lines against 0.19 ms on x-lines (2 cells per lane).
 void plan_ilu_cluster(ms_system &s) {
-    s.cl_ok[0] = plan_precision<double, double>(s, 0);
-    s.cl_ok[1] = plan_precision<float, double>(s, 1) && plan_precision<float, float>(s, 1);
+    const char *e = std::getenv("MSGB_ILU_LINES");
+    const bool want_y = e && e[0] == 'y';
+    int d[3] = {s.nx, s.ny, s.nz};
+    s.cl_T[0] = false;
+    s.cl_ok[0] = plan_precision<double, double>(s, 0, d);
+    s.cl_T[1] = want_y && s.ny > s.nx && s.ny <= 256;
+    if (s.cl_T[1]) {
+        int dt[3] = {s.ny, s.nx, s.nz};
+        s.cl_ok[1] = plan_precision<float, double>(s, 1, dt) && plan_precision<float, float>(s, 1, dt);
+        if (!s.cl_ok[1]) s.cl_T[1] = false;
+    }
+    if (!s.cl_T[1]) s.cl_ok[1] = plan_precision<float, double>(s, 1, d) && plan_precision<float, float>(s, 1, d);
+    if (s.cl_T[1] && s.cl_ok[1]) {
+        s.w_T64.alloc(s.n);
+        s.w_T32.alloc(s.n);
+        s.w_T64b.alloc(s.n);
+        s.w_T32b.alloc(s.n);
+    }
 }
 
 void launch_ilu_pack_coef4(ms_system &s, bool fp32, cudaStream_t st) {
     const int g = (s.n + 255) / 256;
     if (fp32) {
         s.coef4_32.alloc((size_t)8 * s.n);
-        k_pack_coef4<float><<<g, 256, 0, st>>>(s.n, s.dcoef32.p, s.dinv32.p, s.coef4_32.p);
+        k_pack_coef4<float><<<g, 256, 0, st>>>(s.n, s.nx, s.ny, s.cl_T[1] ? 1 : 0, s.dcoef32.p, s.dinv32.p,
+                                               s.coef4_32.p);
     } else {
         s.coef4_64.alloc((size_t)8 * s.n);
-        k_pack_coef4<double><<<g, 256, 0, st>>>(s.n, s.dcoef64.p, s.dinv64.p, s.coef4_64.p);
+        k_pack_coef4<double><<<g, 256, 0, st>>>(s.n, s.nx, s.ny, s.cl_T[0] ? 1 : 0, s.dcoef64.p, s.dinv64.p,
+                                                s.coef4_64.p);
     }
     MS_CHECK_LAUNCH();
 }

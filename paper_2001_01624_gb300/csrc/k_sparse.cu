@@ -393,57 +393,59 @@ __global__ void k_multidot(int n, int k, const double *__restrict__ V, const dou
     if (threadIdx.x == 0) *cnt = 0u;
 }
 
-// The same products in one pass over V for k <= 32: each thread keeps all k
-// partial sums; warp trees, then the block's warps in order, then the last
-// block adds the blocks' partials in block order (deterministic).
-__global__ void __launch_bounds__(256) k_multidot32(int n, int k, const double *__restrict__ V,
-                                                    const double *__restrict__ w, double *red, unsigned int *cnt,
-                                                    double *h) {
-    double acc[32];
+// The same products with the vectors taken 8 at a time (blockIdx.y = group of
+// 8): each thread keeps 8 partial sums over a grid-stride slice, warp trees and
+// the block's warps in order give the block partials, and the last block of
+// each group adds its group's partials in block order (deterministic).
+__global__ void __launch_bounds__(256) k_multidot8(int n, int k, const double *__restrict__ V,
+                                                   const double *__restrict__ w, double *red, unsigned int *cnt,
+                                                   double *h) {
+    const int i0 = blockIdx.y * 8;
+    const int kk = min(8, k - i0);
+    double acc[8];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) acc[i] = 0.0;
+    for (int i = 0; i < 8; ++i) acc[i] = 0.0;
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
-        const double wl = w[l];
+        const double wl = __ldg(w + l);
+        double vv[8];
 #pragma unroll
-        for (int i = 0; i < 32; ++i)
-            if (i < k) acc[i] += V[(int64_t)i * n + l] * wl;
+        for (int i = 0; i < 8; ++i) vv[i] = i < kk ? __ldcs(V + (int64_t)(i0 + i) * n + l) : 0.0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] += vv[i] * wl;
     }
-    __shared__ double part[8][32];
+    __shared__ double part[8][8];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < 32; ++i) {
-        if (i < k) {
-            double a = acc[i];
+    for (int i = 0; i < 8; ++i) {
+        double a = acc[i];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-            if (lane == 0) part[wid][i] = a;
-        }
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) part[wid][i] = a;
     }
     __syncthreads();
-    if (threadIdx.x < k) {
+    double *rg = red + (int64_t)blockIdx.y * gridDim.x * 8;
+    if (threadIdx.x < 8) {
         double a = 0.0;
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += part[q][threadIdx.x];
-        red[(int64_t)blockIdx.x * k + threadIdx.x] = a;
+        rg[(int64_t)blockIdx.x * 8 + threadIdx.x] = a;
     }
     __shared__ bool last;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+        last = atomicAdd(cnt + blockIdx.y, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // warp q adds the block partials of products q, q + 8, ...: lanes stride the
-    // blocks, then a fixed shuffle tree
-    for (int i = wid; i < k; i += (int)(blockDim.x >> 5)) {
+    if (wid < kk) {
         double t = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(&red[(int64_t)b * k + i]);
+        for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(&rg[(int64_t)b * 8 + wid]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-        if (lane == 0) h[i] = t;
+        if (lane == 0) h[i0 + wid] = t;
     }
-    if (threadIdx.x == 0) *cnt = 0u;
+    if (threadIdx.x == 0) cnt[blockIdx.y] = 0u;
 }
 
 // y[l] += sign * sum_{i<k} c[i] V[i n + l]   (c on the device, k <= 128)
@@ -464,6 +466,7 @@ __global__ void k_scale(int n, const double *__restrict__ x, double a, double *_
 }
 
 int stride_grid(int n) { return std::max(1, std::min((n + kThreads - 1) / kThreads, 4 * 152)); }
+constexpr int kDotGroups = 16;   // up to 128 vectors in groups of 8
 }  // namespace
 
 int multidot_blocks(int n) { return stride_grid(n); }
@@ -471,7 +474,7 @@ int multidot_blocks(int n) { return stride_grid(n); }
 void launch_multidot(int n, int k, const double *V, const double *w, double *red, unsigned int *cnt, double *h,
                      cudaStream_t st) {
     KernelScope ks_(st, "krylov_dot", (double)(k + 1) * n * 8);
-    if (k <= 32) k_multidot32<<<stride_grid(n), kThreads, 0, st>>>(n, k, V, w, red, cnt, h);
+    if (k <= 8 * kDotGroups) k_multidot8<<<dim3(stride_grid(n), (k + 7) / 8), kThreads, 0, st>>>(n, k, V, w, red, cnt, h);
     else k_multidot<<<stride_grid(n), kThreads, 0, st>>>(n, k, V, w, red, cnt, h);
     MS_CHECK_LAUNCH();
 }

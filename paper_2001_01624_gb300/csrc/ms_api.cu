@@ -808,9 +808,9 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
         const int m = opts->restart > 0 ? std::min(opts->restart, 120) : 30;
         s->w_kry.alloc((size_t)(2 * m + 3) * n);
         double *V = s->w_kry.p, *Z = V + (size_t)(m + 1) * n, *w = Z + (size_t)m * n, *qk = w + n;
-        s->w_kred.alloc((size_t)multidot_blocks(n) * (m + 1));
+        s->w_kred.alloc((size_t)multidot_blocks(n) * (m + 8));   // block partials, vectors in groups of 8
         s->w_kh.alloc((size_t)3 * (m + 1) + 2);
-        s->w_kcnt.alloc(1);
+        s->w_kcnt.alloc(16);                                     // one arrival counter per group of 8
         s->w_kcnt.zero(st);
         double *h1 = s->w_kh.p, *h2 = h1 + (m + 1), *hn_dev = h2 + (m + 1), *ydev = hn_dev + 1;
         double *xg = s->w_xprev.p;

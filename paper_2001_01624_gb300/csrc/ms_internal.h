@@ -202,6 +202,9 @@ struct ms_system {
     int ilu_kind[2] = {0, 0};
     // cluster line scan per precision: feasible, rows per CTA, CTAs (= cluster size)
     bool cl_ok[2] = {false, false};
+    bool cl_T[2] = {false, false};            // y-lines on transposed vectors (x fastest -> y fastest)
+    msgb::DBuf<double> w_T64, w_T64b;         // transposed right-hand side / result
+    msgb::DBuf<float> w_T32, w_T32b;
     int cl_TK[2] = {0, 0}, cl_NK[2] = {0, 0};
     msgb::DBuf<double> coef4_64;              // [2][n][4]: (Lx, Ly, Lz, 0), (Ux, Uy, Uz, 1/d) per cell
     msgb::DBuf<float> coef4_32;
