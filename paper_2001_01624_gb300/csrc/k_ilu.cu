@@ -196,7 +196,7 @@ void launch_ilu_factor(ms_system &s, bool fp32, cudaStream_t st) {
     s.lu64.alloc(en);
     s.dinv64.alloc(s.n);
     s.w_y.alloc(s.n);   // U diagonal scratch
-    if (!s.ilu64_valid) {
+    if (!s.ilu64_valid && !launch_ilu_factor_cluster(s, st)) {
         KernelScope ks_(st, "ilu_factor", (double)s.n * (8 + 8 + 8 + 4) + (double)s.W * s.n * (4 + 8 + 8));
         k_ilu_factor<<<sweep_blocks(s), kSweepThreads, 0, st>>>(s.n, s.W, s.ntot, s.lperm.p, s.col.p, s.off_p.p,
                                                                  s.diag.p, s.lu64.p, s.w_y.p, s.dinv64.p, s.flags.p,

@@ -393,6 +393,260 @@ __global__ void __launch_bounds__(544, 1)
 // (Ux, Uy, Uz, 1/U_ii).  y-lines (transposed = 1): the cell moves to
 // t = y + ny (x + nx z) and keeps (Ly, Lx, Lz, 0) and (Uy, Ux, Uz, 1/U_ii), so
 // that the in-line neighbour comes first, then the previous line's.
+// ILU(0) factorisation of the 7-point pattern in natural order: no fill, so
+// U keeps A's upper entries, L_ik = A_ik / u_k, and only the pivots follow a
+// recurrence, u_i = A_ii - sum over the lower neighbours k of A_ik A_ki / u_k.
+// Its dependencies are those of the forward sweep, so the same cluster line
+// pipeline computes it: a warp per k-row, lines walked along j, the j- and
+// k-neighbour pivots (as 1/u) from registers and the exchange ring; within a
+// line the x-recurrence is a composition of projective maps, scanned across
+// the lanes.
+// Input per cell (c_x, c_y, c_z, A_ii) with c_d = A_ik A_ki; output 1/u.
+template <int E>
+__global__ void __launch_bounds__(544, 1)
+    k_factor_cluster(int nx, int ny, int nz, int TK, const double *__restrict__ fac4, double *__restrict__ dinv,
+                     int *err) {
+    constexpr int LW = 32 * E;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const unsigned K = cluster_rank();
+    const int CLN = nx * 4;
+    // shared: coefficient slots [RF][TK][CLN] | exchange [TK][NBX][LW] |
+    //         barriers full_f, empty_f [RF][TK], full_x, empty_x [NBX][TK]
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double *cwin = reinterpret_cast<double *>(smraw);
+    size_t off = (size_t)RF * TK * CLN * sizeof(double);
+    double *xin = reinterpret_cast<double *>(smraw + off);
+    off += (size_t)TK * NBX * LW * sizeof(double);
+    const unsigned full_f = smem_u32(smraw + off);
+    const unsigned empty_f = full_f + 8 * RF * TK;
+    const unsigned full_x = empty_f + 8 * RF * TK;
+    const unsigned empty_x = full_x + 8 * NBX * TK;
+    if (tid < TK) {
+        for (int q = 0; q < RF; ++q) {
+            mb_init(full_f + 8 * (q * TK + tid), 1);
+            mb_init(empty_f + 8 * (q * TK + tid), 1);
+        }
+        for (int b = 0; b < NBX; ++b) {
+            mb_init(full_x + 8 * (b * TK + tid), 1);
+            mb_init(empty_x + 8 * (b * TK + tid), 1);
+        }
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    cluster_sync_all();
+    const long long plane = (long long)nx * ny;
+    if (w == TK) {
+        // producer warp: lane r streams the packed lines of row r
+        const int g = (int)K * TK + lane;
+        int tj = (lane < TK && g < nz) ? 0 : ny;
+        const unsigned lc = (unsigned)nx * 32;
+        unsigned long long t0 = 0;
+        int idle = 0;
+        while (__any_sync(FULL, tj < ny)) {
+            bool issued = false;
+            if (tj < ny) {
+                const int q = tj % RF;
+                const unsigned u = (unsigned)(tj / RF);
+                if (tj < RF || mb_test(empty_f + 8 * (q * TK + lane), (u - 1) & 1u)) {
+                    const long long base = (long long)nx * tj + plane * g;
+                    const unsigned fb = full_f + 8 * (q * TK + lane);
+                    mb_expect(fb, lc);
+                    bulk_g2s(smem_u32(cwin + (size_t)(q * TK + lane) * CLN), fac4 + base * 4, lc, fb);
+                    ++tj;
+                    issued = true;
+                }
+            }
+            if (__any_sync(FULL, issued)) {
+                t0 = 0;
+            } else {
+                __nanosleep(32);
+                if ((++idle & 63) == 0) {
+                    const unsigned long long now = __shfl_sync(FULL, global_ns(), 0);
+                    if (t0 == 0) t0 = now;
+                    else if (now - t0 > kWaitNs) {
+                        if (lane == 0) atomicOr(err, kErrTimeout);
+                        break;
+                    }
+                }
+            }
+        }
+    } else if (w < TK && (int)K * TK + w < nz) {
+        const int g = (int)K * TK + w;
+        const bool has_src = g > 0, has_dst = g + 1 < nz;
+        const bool src_remote = w == 0, dst_remote = w == TK - 1;
+        constexpr unsigned XB = LW * sizeof(double);
+        if (has_src && lane == 0)
+            for (int b = 0; b < NBX && b < ny; ++b) mb_expect_relaxed(full_x + 8 * (b * TK + w), XB);
+        const unsigned dst_rank = dst_remote ? K + 1 : K;
+        const int dst_w = dst_remote ? 0 : w + 1;
+        const unsigned dst_xin = map_cta(smem_u32(xin + (size_t)dst_w * NBX * LW + lane * E), dst_rank);
+        const unsigned dst_full = map_cta(full_x + 8 * dst_w, dst_rank);
+        const unsigned src_empty = has_src ? map_cta(empty_x + 8 * (src_remote ? TK - 1 : w - 1), src_remote ? K - 1 : K) : 0u;
+        double prev[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) prev[e] = 0.0;
+        for (int tj = 0; tj < ny; ++tj) {
+            const int q = tj % RF, b = tj % NBX;
+            const unsigned u = (unsigned)(tj / RF), ub = (unsigned)(tj / NBX);
+            bool ok = wait_lane(full_f + 8 * (q * TK + w), u & 1u, err);
+            double nk[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) nk[e] = 0.0;
+            if (has_src) {
+                ok = ok && wait_lane(full_x + 8 * (b * TK + w), ub & 1u, err);
+                const double *xi = xin + ((size_t)w * NBX + b) * LW + lane * E;
+#pragma unroll
+                for (int e = 0; e < E; ++e) nk[e] = xi[e];
+            }
+            if (!__all_sync(FULL, ok)) break;
+            // u_x = a'_x - c_x / u_{x-1} is the projective map v -> M_x v on
+            // v = (u, 1), M_x = [[a'_x, -c_x], [1, 0]]: lanes compose their cells'
+            // maps, a shuffle scan composes the lanes (each product rescaled by a
+            // power of two, exact, so the entries stay near 1), and each lane
+            // applies the maps to the vector coming from the cells before it.
+            const double *cl = cwin + (size_t)(q * TK + w) * CLN;
+            double ma[E], mc[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int x = lane * E + e;
+                ma[e] = 1.0;   // padding cells are skipped below
+                mc[e] = 0.0;
+                if (x < nx) {
+                    const double4 c = reinterpret_cast<const double4 *>(cl)[x];
+                    ma[e] = c.w - c.y * prev[e] - c.z * nk[e];   // A_ii minus the j- and k-neighbour terms
+                    mc[e] = c.x;
+                }
+            }
+            // lane product P = M_{E-1} ... M_0 (padding cells contribute the identity)
+            double p00 = 1.0, p01 = 0.0, p10 = 0.0, p11 = 1.0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                if (lane * E + e < nx) {
+                    const double n00 = ma[e] * p00 - mc[e] * p10, n01 = ma[e] * p01 - mc[e] * p11;
+                    p10 = p00;
+                    p11 = p01;
+                    p00 = n00;
+                    p01 = n01;
+                }
+            }
+            auto rescale = [](double &a, double &b, double &c, double &d) {
+                const double m = fmax(fmax(fabs(a), fabs(b)), fmax(fabs(c), fabs(d)));
+                if (m > 0.0 && m < INFINITY) {
+                    const int k = ilogb(m);
+                    a = scalbn(a, -k);
+                    b = scalbn(b, -k);
+                    c = scalbn(c, -k);
+                    d = scalbn(d, -k);
+                }
+            };
+            rescale(p00, p01, p10, p11);
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const double q00 = __shfl_up_sync(FULL, p00, d), q01 = __shfl_up_sync(FULL, p01, d);
+                const double q10 = __shfl_up_sync(FULL, p10, d), q11 = __shfl_up_sync(FULL, p11, d);
+                if (lane >= d) {   // P <- P Q (the earlier lanes' maps act first)
+                    const double n00 = p00 * q00 + p01 * q10, n01 = p00 * q01 + p01 * q11;
+                    const double n10 = p10 * q00 + p11 * q10, n11 = p10 * q01 + p11 * q11;
+                    p00 = n00;
+                    p01 = n01;
+                    p10 = n10;
+                    p11 = n11;
+                    rescale(p00, p01, p10, p11);
+                }
+            }
+            // vector entering this lane: earlier lanes' product applied to (1, 0) (u_{-1} infinite)
+            double v0 = __shfl_up_sync(FULL, p00, 1), v1 = __shfl_up_sync(FULL, p10, 1);
+            if (lane == 0) {
+                v0 = 1.0;
+                v1 = 0.0;
+            }
+            double val[E];
+            bool bad = false;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                val[e] = 0.0;
+                if (lane * E + e < nx) {
+                    const double n0 = ma[e] * v0 - mc[e] * v1;
+                    v1 = v0;
+                    v0 = n0;
+                    const double m = fmax(fabs(v0), fabs(v1));
+                    if (m > 0.0 && m < INFINITY) {
+                        const int k = ilogb(m);
+                        v0 = scalbn(v0, -k);
+                        v1 = scalbn(v1, -k);
+                    }
+                    val[e] = v1 / v0;   // 1 / u_x
+                    bad |= !(val[e] > 0.0);
+                }
+            }
+            if (bad) atomicOr(err, kErrSingular);
+            if (lane == 0) {
+                mb_arrive_relaxed(empty_f + 8 * (q * TK + w));
+                if (has_src) {
+                    if (tj + NBX < ny) mb_expect_relaxed(full_x + 8 * (b * TK + w), XB);
+                    if (src_remote) mb_arrive_relaxed_remote(src_empty + 8 * b * TK);
+                    else mb_arrive_relaxed(src_empty + 8 * b * TK);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < E; ++e) prev[e] = val[e];
+            bool ok2 = true;
+            if (has_dst) {
+                if (tj >= NBX) ok2 = wait_lane(empty_x + 8 * (b * TK + w), (ub - 1) & 1u, err);
+                if (ok2) {
+                    const unsigned xo = dst_xin + (unsigned)(b * LW * sizeof(double)), fb = dst_full + 8 * b * TK;
+#pragma unroll
+                    for (int e = 0; e < E; e += 2) st_async2(xo + e * (unsigned)sizeof(double), val[e], val[e + 1], fb);
+                }
+            }
+            double *ob = dinv + (long long)nx * tj + plane * g;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int x = lane * E + e;
+                if (x < nx) ob[x] = val[e];
+            }
+            if (!__all_sync(FULL, ok2)) break;
+        }
+    }
+    cluster_sync_all();
+}
+
+// (c_x, c_y, c_z, A_ii) per cell from the pinned ELL matrix: c_d = A_ik A_ki for
+// the lower neighbour k in direction d (0 where there is none)
+__global__ void k_pack_factor(int n, const int8_t *__restrict__ dslot, const int *__restrict__ col,
+                              const double *__restrict__ off, const double *__restrict__ diag, double *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double c[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        c[d] = 0.0;
+        const int wl = dslot[(int64_t)d * n + i];
+        if (wl >= 0) {
+            const int k = col[(int64_t)wl * n + i];
+            const int wu = dslot[(int64_t)(d + 3) * n + k];   // k's slot pointing back to i
+            if (wu >= 0) c[d] = off[(int64_t)wl * n + i] * off[(int64_t)wu * n + k];
+        }
+    }
+    double *o = out + (size_t)i * 4;
+    o[0] = c[0];
+    o[1] = c[1];
+    o[2] = c[2];
+    o[3] = diag[i];
+}
+
+// L_ik = A_ik / u_k in the lower slots, A's entries in the upper slots
+__global__ void k_factor_finish(int n, int W, const int *__restrict__ col, const double *__restrict__ off,
+                                const double *__restrict__ dinv, double *__restrict__ lu) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int w = 0; w < W; ++w) {
+        const int64_t at = (int64_t)w * n + i;
+        const int k = col[at];
+        lu[at] = k < i ? off[at] * dinv[k] : off[at];
+    }
+}
+
 template <typename T>
 __global__ void k_pack_coef4(int n, int nx, int ny, int transposed, const T *__restrict__ dcoef,
                              const T *__restrict__ dinv, T *__restrict__ out) {
@@ -596,6 +850,53 @@ void plan_ilu_cluster(ms_system &s) {
         s.w_T64b.alloc(s.n);
         s.w_T32b.alloc(s.n);
     }
+}
+
+// Structured ILU(0) factors (FP64) with the cluster line pipeline; false when
+// the layout cannot be launched (the caller uses the level-ordered kernel).
+bool launch_ilu_factor_cluster(ms_system &s, cudaStream_t st) {
+    if (!s.structured || !s.cl_ok[0] || s.nx > 256) return false;
+    const int E = s.nx <= 64 ? 2 : s.nx <= 128 ? 4 : 8;
+    const int TK = s.cl_TK[0], NK = s.cl_NK[0];
+    const int LW = 32 * E;
+    const size_t smem = (size_t)RF * TK * s.nx * 32 + (size_t)TK * NBX * LW * 8 + (size_t)8 * 2 * (RF + NBX) * TK;
+    if (smem > 220 * 1024) return false;
+    s.w_fac4.alloc((size_t)4 * s.n);
+    const int g = (s.n + 255) / 256;
+    KernelScope ks_(st, "ilu_factor", (double)s.n * (8 + 8 + 8) + (double)s.W * s.n * (4 + 8 + 8));
+    k_pack_factor<<<g, 256, 0, st>>>(s.n, s.dir_slot.p, s.col.p, s.off_p.p, s.diag.p, s.w_fac4.p);
+    MS_CHECK_LAUNCH();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(NK, 1, 1);
+    cfg.blockDim = dim3(32 * (TK + 1), 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = NK;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaSuccess;
+    auto go = [&](auto kern) {
+        static size_t smem_set = 0;
+        e = raise_smem_limit(kern, smem, smem_set);
+        if (e == cudaSuccess && NK > 8) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e == cudaSuccess)
+            e = cudaLaunchKernelEx(&cfg, kern, s.nx, s.ny, s.nz, TK, (const double *)s.w_fac4.p, s.dinv64.p,
+                                   s.sync.p + 3);
+    };
+    if (E == 2) go(k_factor_cluster<2>);
+    else if (E == 4) go(k_factor_cluster<4>);
+    else go(k_factor_cluster<8>);
+    if (e != cudaSuccess) {   // not launchable here: the level-ordered factorisation runs instead
+        cudaGetLastError();
+        return false;
+    }
+    k_factor_finish<<<g, 256, 0, st>>>(s.n, s.W, s.col.p, s.off_p.p, s.dinv64.p, s.lu64.p);
+    MS_CHECK_LAUNCH();
+    return true;
 }
 
 void launch_ilu_pack_coef4(ms_system &s, bool fp32, cudaStream_t st) {

@@ -205,6 +205,7 @@ struct ms_system {
     bool cl_T[2] = {false, false};            // y-lines on transposed vectors (x fastest -> y fastest)
     msgb::DBuf<double> w_T64, w_T64b;         // transposed right-hand side / result
     msgb::DBuf<float> w_T32, w_T32b;
+    msgb::DBuf<double> w_fac4;                // structured factorisation input (c_x, c_y, c_z, A_ii) per cell
     int cl_TK[2] = {0, 0}, cl_NK[2] = {0, 0};
     msgb::DBuf<double> coef4_64;              // [2][n][4]: (Lx, Ly, Lz, 0), (Ux, Uy, Uz, 1/d) per cell
     msgb::DBuf<float> coef4_32;
@@ -368,6 +369,7 @@ void launch_ilu_tiled64(ms_system &s, const double *r, double *y, double *z, cud
 void launch_ilu_tiled32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st);
 void launch_ilu_tiled32f(ms_system &s, const float *r, float *y, float *z, cudaStream_t st);
 void plan_ilu_cluster(ms_system &s);
+bool launch_ilu_factor_cluster(ms_system &s, cudaStream_t st);
 void launch_ilu_pack_coef4(ms_system &s, bool fp32, cudaStream_t st);
 void launch_ilu_cluster64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st);
 void launch_ilu_cluster32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st);
