@@ -182,6 +182,135 @@ __global__ void __launch_bounds__(kSweepThreads) k_ilu_bwd(int n, int W, int nto
     sweep_end(sync);
 }
 
+// Level-synchronous sweeps for any grid.  One cooperative launch walks the
+// wavefront levels of the natural order (rows of one level are independent):
+// the whole grid takes a level's rows, then meets at a grid barrier before the
+// next level.  Forward L y = r, or backward (BWD) U z = y in reverse level order.
+//
+// Barrier: a 64-bit arrival counter bar[0] that only grows (one fire-and-forget
+// add per block per barrier; a block passes barrier j of this launch when the
+// counter reaches base + j * blocks), and bar[1] = the counter's value when a
+// launch starts, advanced by block 0 once every block has read it.  Waits are
+// bounded: after 2 s of device time a block records a timeout and the launch
+// ends early.  A row's slots, right-hand side and pivot do not depend on the
+// sweep's results, so each thread loads its next row before the barrier; after
+// it only the neighbours' results are read.
+constexpr int kLevelThreads = 512;
+constexpr int kLevelSlots = 8;      // slots held in registers (wider rows take the flag-ordered sweeps)
+
+__device__ __forceinline__ unsigned long long grid_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool level_barrier(unsigned long long *cnt, unsigned long long target, int *err) {
+    __shared__ int s_fail;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        __threadfence();
+        atomicAdd(cnt, 1ull);
+        volatile unsigned long long *c = cnt;
+        unsigned long long t0 = 0;
+        int spins = 0;
+        while (*c < target) {
+            if ((++spins & 63) == 0) {
+                const unsigned long long now = grid_ns();
+                if (t0 == 0) t0 = now;
+                else if (now - t0 > 2000000000ull) {
+                    atomicOr(err, kErrTimeout);
+                    s_fail = 1;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return s_fail == 0;
+}
+
+template <typename T>
+struct LevelRow {
+    int i;
+    int k[kLevelSlots];
+    T v[kLevelSlots];
+    T r, d;
+};
+
+// Row t of lperm (or none) with its slots of the triangle the sweep uses.
+template <typename T, typename TR, bool BWD>
+__device__ __forceinline__ void level_row_load(LevelRow<T> &row, int t, int e1, int n, int W,
+                                               const int *__restrict__ lperm, const int *__restrict__ col,
+                                               const T *__restrict__ lu, const T *__restrict__ dinv,
+                                               const TR *__restrict__ rhs) {
+    row.i = t < e1 ? lperm[t] : -1;
+    if (row.i < 0) return;
+    const int i = row.i;
+    row.r = (T)rhs[i];
+    row.d = BWD ? dinv[i] : T(1);
+#pragma unroll
+    for (int w = 0; w < kLevelSlots; ++w) {
+        int k = i;
+        T v = T(0);
+        if (w < W) {
+            k = col[(int64_t)w * n + i];
+            v = lu[(int64_t)w * n + i];
+        }
+        const bool use = BWD ? k > i : k < i;
+        row.k[w] = use ? k : -1;
+        row.v[w] = v;
+    }
+}
+
+template <typename T, typename TR, bool BWD>
+__global__ void __launch_bounds__(kLevelThreads) k_level_sweep(int n, int W, int nlev, const int *__restrict__ lev_off,
+                                                               const int *__restrict__ lperm,
+                                                               const int *__restrict__ col, const T *__restrict__ lu,
+                                                               const T *__restrict__ dinv,
+                                                               const TR *__restrict__ rhs, T *out,
+                                                               unsigned long long *bar, int *err) {
+    const int G = gridDim.x;
+    const int gsize = G * blockDim.x;
+    const int j0 = threadIdx.x * G + blockIdx.x;     // rows of a level spread over all blocks first
+    const unsigned long long base = __ldcg(&bar[1]);
+    LevelRow<T> row;
+    {
+        const int L = BWD ? nlev - 1 : 0;
+        level_row_load<T, TR, BWD>(row, lev_off[L] + j0, lev_off[L + 1], n, W, lperm, col, lu, dinv, rhs);
+    }
+    for (int li = 0; li < nlev; ++li) {
+        const int L = BWD ? nlev - 1 - li : li;
+        if (row.i >= 0) {
+            T x[kLevelSlots];
+#pragma unroll
+            for (int w = 0; w < kLevelSlots; ++w) x[w] = row.k[w] >= 0 ? __ldcg(&out[row.k[w]]) : T(0);
+            T s = row.r;
+#pragma unroll
+            for (int w = 0; w < kLevelSlots; ++w) s -= row.v[w] * x[w];
+            out[row.i] = BWD ? s * row.d : s;
+        }
+        const int e0 = lev_off[L], e1 = lev_off[L + 1];
+        for (int t = e0 + j0 + gsize; t < e1; t += gsize) {      // levels wider than the grid
+            LevelRow<T> extra;
+            level_row_load<T, TR, BWD>(extra, t, e1, n, W, lperm, col, lu, dinv, rhs);
+            if (extra.i < 0) continue;
+            T s = extra.r;
+#pragma unroll
+            for (int w = 0; w < kLevelSlots; ++w)
+                if (extra.k[w] >= 0) s -= extra.v[w] * __ldcg(&out[extra.k[w]]);
+            out[extra.i] = BWD ? s * extra.d : s;
+        }
+        if (li + 1 == nlev) break;
+        const int Ln = BWD ? L - 1 : L + 1;
+        level_row_load<T, TR, BWD>(row, lev_off[Ln] + j0, lev_off[Ln + 1], n, W, lperm, col, lu, dinv, rhs);
+        if (!level_barrier(bar, base + (unsigned long long)(li + 1) * G, err)) return;
+        if (li == 0 && blockIdx.x == 0 && threadIdx.x == 0)      // every block has read bar[1]
+            bar[1] = base + (unsigned long long)(nlev - 1) * G;
+    }
+}
+
 __global__ void k_copy_f32(const double *a, float *b, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (; i < n; i += (int64_t)gridDim.x * blockDim.x) b[i] = (float)a[i];
@@ -240,9 +369,66 @@ void launch_ilu_apply32(ms_system &s, const double *r, float *y, float *z, cudaS
     MS_CHECK_LAUNCH();
 }
 
+template <typename T, typename TR, bool BWD>
+bool launch_level(ms_system &s, const T *lu, const T *dinv, const TR *rhs, T *out, cudaStream_t st) {
+    if (s.W > kLevelSlots) return false;
+    auto kern = k_level_sweep<T, TR, BWD>;
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kLevelThreads, 0) != cudaSuccess) {
+            cudaGetLastError();
+            b = 0;
+        }
+        per_sm = b;
+    }
+    if (per_sm < 1) return false;
+    int sms = 0;
+    MS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s.device));
+    // one block per SM (fewer arrivals per barrier); small systems fewer
+    const int grid = std::max(1, std::min(sms, (s.ntot + kLevelThreads - 1) / kLevelThreads));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kLevelThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;   // all blocks co-resident (the grid barrier relies on it)
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, s.n, s.W, s.n_levels, (const int *)s.lev_off.p,
+                                             (const int *)s.lperm.p, (const int *)s.col.p, lu, dinv, rhs, out,
+                                             s.lev_bar.p, s.sync.p + 3);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+template <typename T, typename TR>
+bool level_apply(ms_system &s, const T *lu, const T *dinv, const TR *r, T *y, T *z, cudaStream_t st) {
+    if (s.lev_off.n == 0 || s.W > kLevelSlots) return false;
+    const double nl = (double)s.nnz_lower;
+    {
+        KernelScope ks_(st, sizeof(T) == 8 ? "ilu_level_fwd" : "ilu_level_fwd32", nl * (4 + sizeof(T)) + (double)s.n * (sizeof(TR) + sizeof(T)));
+        if (!launch_level<T, TR, false>(s, lu, dinv, r, y, st)) return false;
+    }
+    KernelScope ks_(st, sizeof(T) == 8 ? "ilu_level_bwd" : "ilu_level_bwd32", nl * (4 + sizeof(T)) + (double)s.n * 3 * sizeof(T));
+    return launch_level<T, T, true>(s, lu, dinv, y, z, st);
+}
+
 }  // namespace msgb
 
 namespace msgb {
+
+bool launch_ilu_level64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st) {
+    return level_apply<double, double>(s, s.lu64.p, s.dinv64.p, r, y, z, st);
+}
+
+bool launch_ilu_level32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st) {
+    return level_apply<float, double>(s, s.lu32.p, s.dinv32.p, r, y, z, st);
+}
 
 // Level-ordered FP64 sweeps with caller-provided scratch: the intermediate
 // vector y (n doubles), per-row flags (n ints) and the sweep words (8 ints).

@@ -249,9 +249,16 @@ void analyse_grid(ms_system &s, const ms_grid &g) {
                 else if (v == "lines") k = tiles;
                 else if (v == "pencil") k = 1;
                 else if (v == "generic") k = 0;
+                else if (v == "level") k = 4;
             }
             s.ilu_kind[p] = k;
         }
+    } else {
+        // any grid: level-synchronous sweeps in one cooperative launch;
+        // MSGB_ILU_KERNEL=generic selects the flag-ordered sweeps instead
+        const char *e = std::getenv("MSGB_ILU_KERNEL");
+        const int k = (e && std::string(e) == "generic") ? 0 : 4;
+        s.ilu_kind[0] = s.ilu_kind[1] = k;
     }
 
     // host copies + device upload
@@ -279,6 +286,13 @@ void analyse_grid(ms_system &s, const ms_grid &g) {
     s.col.upload(s.h_col, st);
     if (s.structured) s.dir_slot.upload(dslot, st);
     s.lperm.upload(lperm, st);
+    {
+        std::vector<int> lo(off.size());
+        for (size_t l = 0; l < off.size(); ++l) lo[l] = (int)off[l];
+        s.lev_off.upload(lo, st);
+        s.lev_bar.alloc(2);
+        s.lev_bar.zero(st);
+    }
     size_t en = std::max<size_t>((size_t)W * s.n, 1);
     s.off_u.alloc(en); s.off_p.alloc(en); s.diag.alloc(s.n);
     s.flags.alloc(s.n);

@@ -72,6 +72,8 @@ void check_sweep_errors(ms_ctx *ctx, ms_system *s) {
     const int e = read_error_word(ctx, s->sync.p + 3);
     if (e) {
         MS_CUDA(cudaMemsetAsync(s->sync.p + 3, 0, sizeof(int), ctx->stream));
+        // a sweep that gave up left its barrier counter short: start it afresh
+        if (s->lev_bar.n) MS_CUDA(cudaMemsetAsync(s->lev_bar.p, 0, 2 * sizeof(unsigned long long), ctx->stream));
         if (e & kErrTimeout) throw Error{MS_ERR_TIMEOUT, "a level-ordered sweep wait ran out"};
         if (e & kErrSingular) throw Error{MS_ERR_INVALID_ARG, "ILU(0) met a zero pivot"};
         throw Error{MS_ERR_CUDA, "device error word " + std::to_string(e)};
@@ -122,12 +124,14 @@ void ensure_ilu(ms_ctx *ctx, ms_system &s, bool fp32) {
 
 // z = (LU)^{-1} r: wavefront sweeps on structured grids (line scan across a
 // cluster, line scan over CTA tiles, or pencil tiles, chosen per precision when
-// the system is analysed), level-ordered sweeps otherwise.
+// the system is analysed), level-synchronous sweeps in one cooperative launch
+// otherwise (flag-ordered sweeps where that launch is refused).
 void ilu_apply64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st) {
     switch (s.ilu_kind[0]) {
         case 3: launch_ilu_cluster64(s, r, y, z, st); break;
         case 2: launch_ilu_lines64(s, r, y, z, st); break;
         case 1: launch_ilu_tiled64(s, r, y, z, st); break;
+        case 4: if (launch_ilu_level64(s, r, y, z, st)) break; [[fallthrough]];
         default: launch_ilu_apply64(s, r, y, z, st);
     }
 }
@@ -137,6 +141,7 @@ void ilu_apply32(ms_system &s, const double *r, float *y, float *z, cudaStream_t
         case 3: launch_ilu_cluster32(s, r, y, z, st); break;
         case 2: launch_ilu_lines32(s, r, y, z, st); break;
         case 1: launch_ilu_tiled32(s, r, y, z, st); break;
+        case 4: if (launch_ilu_level32(s, r, y, z, st)) break; [[fallthrough]];
         default: launch_ilu_apply32(s, r, y, z, st);
     }
 }

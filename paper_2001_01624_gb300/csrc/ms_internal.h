@@ -214,6 +214,8 @@ struct ms_system {
     msgb::DBuf<double> dcoef64;               // [6*n]: L(-x,-y,-z), U(+x,+y,+z)
     msgb::DBuf<float> dcoef32;
     msgb::DBuf<int> lperm;
+    msgb::DBuf<int> lev_off;                  // [n_levels + 1] level offsets into lperm
+    msgb::DBuf<unsigned long long> lev_bar;   // grid barrier of the level-synchronous sweeps (counter, base)
 
     // ILU(0) factors on A's pattern (L in lower slots, U in upper slots)
     bool ilu64_valid = false, ilu32_valid = false;
@@ -375,6 +377,8 @@ void launch_ilu_cluster64(ms_system &s, const double *r, double *y, double *z, c
 void launch_ilu_cluster32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st);
 void launch_ilu_cluster32f(ms_system &s, const float *r, float *y, float *z, cudaStream_t st);
 void launch_ilu_lines64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st);
+bool launch_ilu_level64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st);
+bool launch_ilu_level32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st);
 void launch_ilu_lines32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st);
 void launch_ilu_lines32f(ms_system &s, const float *r, float *y, float *z, cudaStream_t st);
 // basis
