@@ -28,6 +28,15 @@ msrsb_basis            Sec. 5.1 (MsRSB, localized iterations)      partition of 
 galerkin               Eq. (10), R = P^T                           symmetry; positive definiteness; P^T A 1 = 0
                                                                    for the unpinned A; dense P^T A P by numpy
 cholesky(_solve)       coarse solve (A_c)^-1                       numpy.linalg.solve
+galerkin_fv            Sec. 5, finite-volume restriction R         A_c 1 = 0 and 1^T A_c = 0 (unpinned A);
+                                                                   constant basis: equals the Galerkin operator
+                                                                   and -sum of the face transmissibilities
+                                                                   between blocks (closed form)
+lu(_solve)             coarse solve, Gaussian elimination          P A = L U; a zero leading pivot; numpy solve
+partition_wells        Sec. 6.2 well bases                         hand-worked blocks; repeated cell rejected
+ms_solve (FV stage)    Eq. (11) with R = block indicator           after a cycle ending in an FV coarse
+                                                                   correction every block's residual sums to
+                                                                   zero (local conservation); dense direct solve
 ilu0 / ilu0_apply      Sec. 5.1 / 6.4 ILU(0)                       (L U)_ij = A_ij on the pattern (defining
                                                                    property); exact on tridiagonal A
 ms_solve               Eq. (11) in Richardson (Sec. 5.2)           dense direct solve; identity partition
@@ -82,7 +91,8 @@ _vp = C.c_void_p
 
 
 class _Stage(C.Structure):
-    _fields_ = [("M", _i), ("sptr", _vp), ("scells", _vp), ("pval", _vp), ("L", _vp)]
+    _fields_ = [("M", _i), ("sptr", _vp), ("scells", _vp), ("pval", _vp), ("L", _vp), ("part", _vp),
+                ("piv", _vp)]
 
 
 class _Adapt(C.Structure):
@@ -113,6 +123,11 @@ def lib():
         L.or_cholesky.argtypes = [_i, _vp]
         L.or_cholesky_solve.argtypes = [_i, _vp, _vp, _vp]
         L.or_cholesky_solve.restype = None
+        L.or_galerkin_fv.argtypes = [_i, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp]
+        L.or_lu.argtypes = [_i, _vp, _vp]
+        L.or_lu_solve.argtypes = [_i, _vp, _vp, _vp, _vp]
+        L.or_lu_solve.restype = None
+        L.or_partition_wells.argtypes = [_i, _i, _vp, _vp, _vp, _pi]
         L.or_ilu0.argtypes = [_i, _vp, _vp, _vp, _vp]
         L.or_ilu0_apply.argtypes = [_i, _vp, _vp, _vp, _vp, _vp]
         L.or_ilu0_apply.restype = None
@@ -338,6 +353,67 @@ def cholesky_solve(L, b):
     return x
 
 
+@dataclass
+class FVFactor:
+    """Finite-volume coarse stage: LU factors (with interchanges) of
+    A_c = R A P, R the block indicator of ``part``."""
+    LU: np.ndarray
+    piv: np.ndarray
+    part: np.ndarray
+
+
+def galerkin_fv(A: CSR, B: Basis, part=None) -> np.ndarray:
+    """A_c = R A P with R_ji = 1 for the cells i of block j (Sec. 5,
+    finite-volume restriction); ``part`` defaults to the basis's partition."""
+    part = _i32(B.part if part is None else part)
+    Ac = np.empty((B.M, B.M))
+    _check(lib().or_galerkin_fv(A.n, _p(A.rowptr), _p(A.col), _p(A.val), B.M, _p(B.sptr), _p(B.scells),
+                                _p(B.pval), _p(part), _p(Ac)), "galerkin_fv")
+    return Ac
+
+
+def lu(Ac):
+    """Dense LU with partial pivoting: returns (LU, piv)."""
+    LU = _f64(Ac).copy()
+    piv = np.zeros(LU.shape[0], np.int32)
+    _check(lib().or_lu(LU.shape[0], _p(LU), _p(piv)), "lu")
+    return LU, piv
+
+
+def lu_solve(LU, piv, b):
+    b = _f64(b); x = np.empty_like(b)
+    lib().or_lu_solve(LU.shape[0], _p(_f64(LU)), _p(_i32(piv)), _p(b), _p(x))
+    return x
+
+
+def coarse_fv(A: CSR, B: Basis) -> FVFactor:
+    """The finite-volume stage of basis B on the pinned A: factors of R A P."""
+    LU, piv = lu(galerkin_fv(A, B))
+    return FVFactor(LU, piv, _i32(B.part))
+
+
+def partition_wells(n: int, wells: Sequence[Sequence[int]]):
+    """Block w = the cells of well w; every other cell in block len(wells)."""
+    wptr = np.zeros(len(wells) + 1, np.int32)
+    for w, c in enumerate(wells):
+        wptr[w + 1] = wptr[w] + len(c)
+    wcells = _i32(np.concatenate([np.asarray(c, np.int32) for c in wells]) if wells else np.zeros(0, np.int32))
+    part = np.empty(n, np.int32)
+    M = _i()
+    _check(lib().or_partition_wells(n, len(wells), _p(wptr), _p(wcells), _p(part), C.byref(M)), "partition_wells")
+    return part, M.value
+
+
+def _stage_struct(B, Lc, keep):
+    if isinstance(Lc, FVFactor):
+        LU, piv, part = _f64(Lc.LU), _i32(Lc.piv), _i32(Lc.part)
+        keep += [B, LU, piv, part]
+        return _Stage(B.M, _p(B.sptr), _p(B.scells), _p(B.pval), _p(LU), _p(part), _p(piv))
+    Lc = _f64(Lc)
+    keep += [B, Lc]
+    return _Stage(B.M, _p(B.sptr), _p(B.scells), _p(B.pval), _p(Lc), None, None)
+
+
 def ilu0(A: CSR) -> np.ndarray:
     lu = np.empty_like(A.val)
     _check(lib().or_ilu0(A.n, _p(A.rowptr), _p(A.col), _p(A.val), _p(lu)), "ilu0")
@@ -363,7 +439,8 @@ class SolveResult:
 def ms_solve(A: CSR, stages: Sequence[tuple], q, tol=1e-6, max_iter=500, smoother="ilu0", jac_omega=2.0 / 3.0,
              x0=None, adapt: Optional[dict] = None, lu=None) -> SolveResult:
     """Multistage Richardson solve (Eq. (11)).  ``stages`` holds (Basis, L)
-    pairs with L the Cholesky factor of the stage's A_c.  ``adapt`` (optional):
+    pairs with L the Cholesky factor of the stage's Galerkin A_c, or an
+    FVFactor for a finite-volume stage.  ``adapt`` (optional):
     dict(schedule=1|2, n_bins, eps, smoothed, omega, tol, max_iter,
     A_unpinned, grid, cells)."""
     L = lib()
@@ -372,9 +449,7 @@ def ms_solve(A: CSR, stages: Sequence[tuple], q, tol=1e-6, max_iter=500, smoothe
     keep = []
     arr = (_Stage * max(len(stages), 1))()
     for s, (B, Lc) in enumerate(stages):
-        Lc = _f64(Lc)
-        keep += [B, Lc]
-        arr[s] = _Stage(B.M, _p(B.sptr), _p(B.scells), _p(B.pval), _p(Lc))
+        arr[s] = _stage_struct(B, Lc, keep)
     sm = 0 if smoother == "ilu0" else 1
     if sm == 0 and lu is None:
         lu = ilu0(A)
@@ -417,9 +492,7 @@ def ms_gmres(A: CSR, stages: Sequence[tuple], q, tol=1e-6, max_iter=500, restart
     keep = []
     arr = (_Stage * max(len(stages), 1))()
     for s, (B, Lc) in enumerate(stages):
-        Lc = _f64(Lc)
-        keep += [B, Lc]
-        arr[s] = _Stage(B.M, _p(B.sptr), _p(B.scells), _p(B.pval), _p(Lc))
+        arr[s] = _stage_struct(B, Lc, keep)
     sm = 0 if smoother == "ilu0" else 1
     if sm == 0 and lu is None:
         lu = ilu0(A)

@@ -699,6 +699,105 @@ void or_cholesky_solve(int M, const double *L, const double *b, double *x) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Finite-volume coarse operator (Sec. 5, choice of the restriction: R sums  */
+/* the fine cells of each block, R_ji = 1 for i in block j, 0 otherwise;     */
+/* Sec. 6.4 b = 1): A_c = R A P, dense row-major M x M, in general not       */
+/* symmetric.  part[i] is the block of cell i.                               */
+/* ------------------------------------------------------------------------ */
+int or_galerkin_fv(int n, const int *rowptr, const int *col, const double *val,
+                   int M, const int *sptr, const int *scells, const double *pval, const int *part, double *Ac) {
+    memset(Ac, 0, (size_t)M * M * sizeof(double));
+    double *w = (double *)xcalloc((size_t)n, sizeof(double));
+    int *mark = (int *)xmalloc((size_t)n * sizeof(int));
+    for (int i = 0; i < n; ++i) mark[i] = -1;
+    int *lst = (int *)xmalloc((size_t)n * sizeof(int));
+    for (int l = 0; l < M; ++l) {
+        int nl = 0;
+        for (int e = sptr[l]; e < sptr[l + 1]; ++e) w[scells[e]] = pval[e];
+        for (int e = sptr[l]; e < sptr[l + 1]; ++e) {
+            int i = scells[e];
+            for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+                int k = col[p];
+                if (mark[k] != l) { mark[k] = l; lst[nl++] = k; }
+            }
+        }
+        for (int t = 0; t < nl; ++t) {      /* (A P_l)_i lands in row part[i] */
+            int i = lst[t];
+            double u = 0.0;
+            for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) u += val[p] * w[col[p]];
+            Ac[(size_t)part[i] * M + l] += u;
+        }
+        for (int e = sptr[l]; e < sptr[l + 1]; ++e) w[scells[e]] = 0.0;
+    }
+    free(w); free(mark); free(lst);
+    return OR_OK;
+}
+
+/* Dense LU with partial pivoting, P A = L U (Gaussian elimination, row     */
+/* interchanges choosing the largest |entry| of the column, first such row  */
+/* on ties).  In place: U on and above the diagonal, the multipliers of L   */
+/* below it; piv[k] = the row exchanged with row k at step k.               */
+int or_lu(int M, double *A, int *piv) {
+    for (int k = 0; k < M; ++k) {
+        int p = k;
+        double best = fabs(A[(size_t)k * M + k]);
+        for (int i = k + 1; i < M; ++i) {
+            double v = fabs(A[(size_t)i * M + k]);
+            if (v > best) { best = v; p = i; }
+        }
+        piv[k] = p;
+        if (!(best > 0.0)) return OR_ESINGULAR;
+        if (p != k)
+            for (int j = 0; j < M; ++j) {
+                double t = A[(size_t)k * M + j];
+                A[(size_t)k * M + j] = A[(size_t)p * M + j];
+                A[(size_t)p * M + j] = t;
+            }
+        for (int i = k + 1; i < M; ++i) {
+            double l = A[(size_t)i * M + k] / A[(size_t)k * M + k];
+            A[(size_t)i * M + k] = l;
+            for (int j = k + 1; j < M; ++j) A[(size_t)i * M + j] -= l * A[(size_t)k * M + j];
+        }
+    }
+    return OR_OK;
+}
+
+/* x = A^{-1} b from or_lu's factors: apply the interchanges to b, then     */
+/* L y = P b (unit lower) and U x = y.                                        */
+void or_lu_solve(int M, const double *LU, const int *piv, const double *b, double *x) {
+    for (int i = 0; i < M; ++i) x[i] = b[i];
+    for (int k = 0; k < M; ++k)
+        if (piv[k] != k) { double t = x[k]; x[k] = x[piv[k]]; x[piv[k]] = t; }
+    for (int i = 0; i < M; ++i) {
+        double s = x[i];
+        for (int p = 0; p < i; ++p) s -= LU[(size_t)i * M + p] * x[p];
+        x[i] = s;
+    }
+    for (int i = M - 1; i >= 0; --i) {
+        double s = x[i];
+        for (int p = i + 1; p < M; ++p) s -= LU[(size_t)i * M + p] * x[p];
+        x[i] = s / LU[(size_t)i * M + i];
+    }
+}
+
+/* Well partition (Sec. 6.2, well bases): the perforated cells of well w form */
+/* block w, every other cell the one remaining block (index n_wells), which   */
+/* keeps the partition of unity.  Returns OR_EINVAL when a cell is listed    */
+/* twice or is out of range.                                                 */
+int or_partition_wells(int n, int n_wells, const int *wptr, const int *wcells, int *part, int *M_out) {
+    for (int i = 0; i < n; ++i) part[i] = -1;
+    for (int w = 0; w < n_wells; ++w)
+        for (int e = wptr[w]; e < wptr[w + 1]; ++e) {
+            int i = wcells[e];
+            if (i < 0 || i >= n || part[i] != -1) return OR_EINVAL;
+            part[i] = w;
+        }
+    for (int i = 0; i < n; ++i) if (part[i] == -1) part[i] = n_wells;
+    *M_out = n_wells + 1;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* ILU(0) smoother (Sec. 5.1 smoother S; Sec. 6.4 "Smooth").  Incomplete LU */
 /* with zero fill-in on A's pattern, natural row order, IKJ form:           */
 /* for each row i, for each k < i in row i: a_ik /= a_kk, then              */
@@ -768,7 +867,9 @@ typedef struct {
     const int *sptr;
     const int *scells;
     const double *pval;
-    const double *L;     /* Cholesky factor of A_c, M x M row-major */
+    const double *L;     /* Galerkin: Cholesky factor of A_c; finite volume: or_lu factors (M x M row-major) */
+    const int *part;     /* finite volume: block of each cell (restriction R = block indicator); NULL: R = P^T */
+    const int *piv;      /* finite volume: or_lu interchanges */
 } or_stage;
 
 typedef struct {
@@ -839,14 +940,20 @@ static void residual(int n, const int *rp, const int *ci, const double *v, const
 
 static void coarse_correction(int n, const int *rp, const int *ci, const double *v, const double *q,
                               int M, const int *sptr, const int *scells, const double *pval, const double *L,
-                              double *x, double *r, double *d, double *xc) {
+                              const int *part, const int *piv, double *x, double *r, double *d, double *xc) {
     residual(n, rp, ci, v, q, x, r);
-    for (int j = 0; j < M; ++j) {                       /* d = P^T r */
-        double s = 0.0;
-        for (int e = sptr[j]; e < sptr[j + 1]; ++e) s += pval[e] * r[scells[e]];
-        d[j] = s;
+    if (part) {                                          /* d = R r, R sums each block's cells */
+        for (int j = 0; j < M; ++j) d[j] = 0.0;
+        for (int i = 0; i < n; ++i) d[part[i]] += r[i];
+        or_lu_solve(M, L, piv, d, xc);
+    } else {
+        for (int j = 0; j < M; ++j) {                   /* d = P^T r */
+            double s = 0.0;
+            for (int e = sptr[j]; e < sptr[j + 1]; ++e) s += pval[e] * r[scells[e]];
+            d[j] = s;
+        }
+        or_cholesky_solve(M, L, d, xc);
     }
-    or_cholesky_solve(M, L, d, xc);
     for (int j = 0; j < M; ++j)                          /* x += P xc */
         for (int e = sptr[j]; e < sptr[j + 1]; ++e) x[scells[e]] += pval[e] * xc[j];
 }
@@ -887,10 +994,10 @@ int or_ms_solve(int n, const int *rowptr, const int *col, const double *val,
             for (int i = 0; i < n; ++i) x[i] += z[i];
             if (s < n_stages)
                 coarse_correction(n, rowptr, col, val, q, stages[s].M, stages[s].sptr, stages[s].scells,
-                                  stages[s].pval, stages[s].L, x, r, d, xc);
+                                  stages[s].pval, stages[s].L, stages[s].part, stages[s].piv, x, r, d, xc);
             else
                 coarse_correction(n, rowptr, col, val, q, dyn.M, dyn.sptr, dyn.scells, dyn.pval, dyn.L,
-                                  x, r, d, xc);
+                                  NULL, NULL, x, r, d, xc);
         }
         if (adapt && adapt->md_hist) adapt->md_hist[it] = dyn.M;
         ++it;
@@ -924,7 +1031,7 @@ static void ms_cycle_from_zero(int n, const int *rp, const int *ci, const double
         else for (int i = 0; i < n; ++i) t[i] = jac_omega * r[i] / dg[i];
         for (int i = 0; i < n; ++i) z[i] += t[i];
         coarse_correction(n, rp, ci, val, v, stages[s].M, stages[s].sptr, stages[s].scells, stages[s].pval,
-                          stages[s].L, z, r, d, xc);
+                          stages[s].L, stages[s].part, stages[s].piv, z, r, d, xc);
     }
 }
 

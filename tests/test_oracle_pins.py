@@ -522,3 +522,133 @@ def test_transport_buckley_leverett_front():
     assert abs(cross - x_front) < 0.03, (cross, x_front, sf)
     # mass balance: water in place = water injected (nothing produced yet)
     assert abs(S.sum() * phi * vol - 1e-3 * dt_total) <= 1e-9 * 1e-3 * dt_total
+
+
+# ----------------------------------------------------------------------------- finite-volume restriction (Sec. 5)
+def test_fv_operator_annihilates_constants():
+    """A_c = R A P with R the block indicator: A_c 1 = R A P 1 = R A 1 = 0 and,
+    A being symmetric, 1^T A_c = 1^T A P = (A 1)^T P = 0 (unpinned A)."""
+    gm = G.lognormal_box(16, 12, 3, seed=12, block=(4, 4, 3))
+    s, B = _setup_basis(gm)
+    Ac = O.galerkin_fv(s.A, B)
+    scale = np.abs(Ac).max()
+    assert np.abs(Ac @ np.ones(B.M)).max() <= 1e-12 * scale
+    assert np.abs(np.ones(B.M) @ Ac).max() <= 1e-12 * scale
+    assert np.abs(Ac - Ac.T).max() > 1e-6 * scale          # not the Galerkin operator: not symmetric
+
+
+def test_fv_operator_constant_basis_closed_form():
+    """With the indicator basis P = R^T, R A P = P^T A P, and off the
+    diagonal -A_c(j, l) is the sum of the transmissibilities of the faces
+    between blocks j and l, the diagonal the sum over the faces leaving j."""
+    gm = G.faulted(12, 10, 4, seed=3, n_fault_x=1, n_fault_y=1, block=(4, 5, 2))
+    s = O.assemble_tpfa(gm.grid, gm.perm)
+    part, M = O.partition_cartesian(gm.grid, s.cells, gm.block)
+    B = O.constant_basis(part, M)
+    Ac = O.galerkin_fv(s.A, B)
+    fa, fb, ft = s.faces
+    ref = np.zeros((M, M))
+    for a, b, t in zip(fa, fb, ft):
+        ja, jb = part[a], part[b]
+        if ja != jb:
+            ref[ja, jb] -= t
+            ref[jb, ja] -= t
+            ref[ja, ja] += t
+            ref[jb, jb] += t
+    np.testing.assert_allclose(Ac, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    np.testing.assert_allclose(Ac, O.galerkin(s.A, B), rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_lu_factors_and_solve():
+    rng = np.random.default_rng(5)
+    for M in (1, 2, 7, 40):
+        A = rng.standard_normal((M, M))
+        if M > 1:
+            A[0, 0] = 0.0                          # forces an interchange at the first step
+        LU, piv = O.lu(A)
+        L = np.tril(LU, -1) + np.eye(M)
+        U = np.triu(LU)
+        PA = A.copy()
+        for k in range(M):
+            PA[[k, piv[k]]] = PA[[piv[k], k]]
+        np.testing.assert_allclose(L @ U, PA, rtol=1e-12, atol=1e-12 * np.abs(A).max())
+        assert np.abs(L).max() <= 1.0 + 1e-15     # partial pivoting bounds the multipliers
+        b = rng.standard_normal(M)
+        np.testing.assert_allclose(O.lu_solve(LU, piv, b), np.linalg.solve(A, b), rtol=1e-9, atol=1e-11)
+    P = np.array([[0.0, 2.0], [3.0, 0.0]])        # needs the interchange; inverse by hand
+    LU, piv = O.lu(P)
+    assert list(piv) == [1, 1]
+    np.testing.assert_allclose(O.lu_solve(LU, piv, np.array([4.0, 9.0])), [3.0, 2.0], rtol=1e-15)
+    with pytest.raises(O.OracleError):
+        O.lu(np.zeros((3, 3)))
+
+
+def test_partition_wells_hand_worked():
+    part, M = O.partition_wells(10, [[2, 3], [7], [9, 0]])
+    assert M == 4
+    assert list(part) == [2, 3, 0, 0, 3, 3, 3, 1, 3, 2]
+    with pytest.raises(O.OracleError):
+        O.partition_wells(10, [[1, 2], [2]])
+    with pytest.raises(O.OracleError):
+        O.partition_wells(10, [[10]])
+
+
+@pytest.mark.parametrize("case", ["3d", "faulted"])
+def test_fv_cycle_conserves_mass_per_block(case):
+    """A cycle that ends with a finite-volume coarse correction leaves a
+    residual whose sum over every block is zero: R (q - A x) = R q - A_c x_c
+    - R A (x - P x_c) = 0 by construction of x_c (local conservation)."""
+    if case == "3d":
+        gm = G.lognormal_box(10, 10, 4, seed=2, block=(5, 5, 2), kz_ratio=0.1)
+    else:
+        gm = G.faulted(14, 12, 6, seed=5, n_fault_x=1, n_fault_y=1, block=(5, 4, 3))
+    sysm, Ap, qp, B, Ac, L = O.setup_general(gm)
+    F = O.coarse_fv(Ap, B)
+    for cycles in (1, 3):
+        r = O.ms_solve(Ap, [(B, F)], qp, tol=1e-30, max_iter=cycles)
+        assert r.iters == cycles
+        res = qp - Ap.to_scipy() @ r.x
+        sums = np.bincount(B.part, weights=res, minlength=B.M)
+        assert np.abs(sums).max() <= 1e-10 * np.abs(res).sum()
+        # the Galerkin stage does not conserve: its block sums stay of the residual's size
+    rg = O.ms_solve(Ap, [(B, L)], qp, tol=1e-30, max_iter=1)
+    resg = qp - Ap.to_scipy() @ rg.x
+    assert np.abs(np.bincount(B.part, weights=resg, minlength=B.M)).max() > 1e-6 * np.abs(resg).sum()
+
+
+@pytest.mark.parametrize("outer", ["richardson", "gmres"])
+def test_fv_solve_matches_direct(outer):
+    """Richardson with a finite-volume stage is not an energy-norm projection
+    and may diverge (it does on the faulted case, spectral radius above one),
+    so it is pinned on a lognormal box; GMRES on the faulted grid."""
+    if outer == "richardson":
+        gm = G.lognormal_box(10, 10, 4, seed=2, block=(5, 5, 2), kz_ratio=0.1)
+    else:
+        gm = G.faulted(14, 12, 6, seed=5, n_fault_x=1, n_fault_y=1, block=(5, 4, 3))
+    sysm, Ap, qp, B, Ac, L = O.setup_general(gm)
+    F = O.coarse_fv(Ap, B)
+    if outer == "richardson":
+        r = O.ms_solve(Ap, [(B, F)], qp, tol=1e-11, max_iter=5000)
+    else:
+        r = O.ms_gmres(Ap, [(B, F)], qp, tol=1e-11, max_iter=5000, restart=30)
+    assert r.converged
+    x = _dense_pinned_solve(Ap, qp)
+    assert np.linalg.norm(r.x - x) <= 1e-8 * np.linalg.norm(x)
+
+
+def test_well_basis_stage_converges_to_direct():
+    """Well bases (Sec. 6.2): MsRSB on the partition {cells of each well,
+    the rest}, hop supports, as an extra stage beside the general one."""
+    gm = G.lognormal_box(14, 12, 3, seed=8, block=(7, 6, 3), kz_ratio=0.1)
+    sysm, Ap, qp, B, Ac, L = O.setup_general(gm)
+    wells = [np.flatnonzero(qp > 0), np.flatnonzero(qp < 0)]
+    part, M = O.partition_wells(Ap.n, [w for w in wells if len(w)])
+    sp, sc = O.support_hop(gm.grid, sysm.cells, sysm.A, part, M)
+    Bw = O.msrsb_basis(sysm.A, part, M, sp, sc)
+    P = Bw.dense(Ap.n)
+    assert np.abs(P.sum(1) - 1).max() <= 1e-12
+    Lw = O.cholesky(O.galerkin(Ap, Bw))
+    r = O.ms_solve(Ap, [(B, L), (Bw, Lw)], qp, tol=1e-11, max_iter=3000)
+    assert r.converged
+    x = _dense_pinned_solve(Ap, qp)
+    assert np.linalg.norm(r.x - x) <= 1e-8 * np.linalg.norm(x)
