@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define MS_ABI_VERSION 3
+#define MS_ABI_VERSION 4
 
 typedef enum {
     MS_OK = 0,
@@ -53,7 +53,7 @@ typedef enum {
     MS_ERR_OOM = 2,             /* device or host allocation failed              */
     MS_ERR_CUDA = 3,            /* a CUDA runtime call failed                    */
     MS_ERR_NOT_CONVERGED = 4,   /* iteration cap reached; outputs hold last iterate */
-    MS_ERR_COARSE_SINGULAR = 5, /* coarse Cholesky met a non-positive pivot      */
+    MS_ERR_COARSE_SINGULAR = 5, /* coarse factorisation met a zero / non-positive pivot */
     MS_ERR_TIMEOUT = 6,         /* a bounded device-side wait ran out            */
     MS_ERR_STATE = 7            /* call made on a handle in the wrong state      */
 } ms_status;
@@ -63,6 +63,10 @@ typedef enum { MS_SMOOTHER_ILU0 = 0, MS_SMOOTHER_JACOBI = 1 } ms_smoother;
 /* Outer iteration (Sec. 5.2: "Richardson or GMRES"): Richardson cycles, or
  * restarted GMRES right-preconditioned with one multistage cycle. */
 typedef enum { MS_OUTER_RICHARDSON = 0, MS_OUTER_GMRES = 1 } ms_outer;
+/* Restriction of a coarse stage (Sec. 5, choice of R): the Galerkin R = P^T,
+ * or the finite-volume R that sums the fine cells of each block (Sec. 6.4:
+ * b = 1, one entry per cell). */
+typedef enum { MS_RESTRICT_GALERKIN = 0, MS_RESTRICT_FV = 1 } ms_restriction;
 typedef enum {
     MS_SUPPORT_BOX = 0,   /* Cartesian block box grown by floor(b/2) per side, cells reachable inside it */
     MS_SUPPORT_HOP = 1,   /* general partitions: block + neighbour-block cells nearer (in hops) to the
@@ -243,6 +247,15 @@ ms_status ms_ilu_apply_noalloc(ms_ctx *ctx, const ms_system *sys, const double *
 ms_status ms_partition_cartesian(ms_ctx *ctx, const ms_system *sys, int32_t bx, int32_t by, int32_t bz,
                                  int32_t *part, int32_t *n_blocks);
 
+/* Well partition (Sec. 6.2, well bases): the cells of well w (active
+ * indices well_cells[well_ptr[w] .. well_ptr[w+1]), host arrays) form block
+ * w and every other cell block n_wells, which keeps the partition of unity;
+ * MsRSB on hop supports over it gives the well basis functions.  A cell
+ * listed twice or out of range is MS_ERR_INVALID_ARG.  part: host, n int32;
+ * *n_blocks = n_wells + 1. */
+ms_status ms_partition_wells(ms_ctx *ctx, const ms_system *sys, int32_t n_wells, const int32_t *well_ptr,
+                             const int32_t *well_cells, int32_t *part, int32_t *n_blocks);
+
 /* Face-connected components of cells with equal class (host or device cls,
  * n int32), numbered by their lowest active index (Sec. 5.1 static
  * partitions: class = general block x facies).  part: host or device, n
@@ -291,6 +304,19 @@ ms_status ms_add_adaptive_basis(ms_ctx *ctx, ms_system *sys, const double *dp, c
  * R = P^T) and its dense Cholesky factorisation and inverse for the coarse
  * solve.  precision MS_PREC_MIXED factors in FP32 and refines in FP64. */
 ms_status ms_galerkin(ms_ctx *ctx, ms_system *sys, const ms_basis *basis, int32_t precision, ms_coarse **out);
+/* Coarse stage with the chosen restriction (ms_restriction): A_c = R A P with
+ * the pinned A.  MS_RESTRICT_GALERKIN is ms_galerkin.  MS_RESTRICT_FV takes
+ * R_ji = 1 for the cells i of block j of the basis's partition; A_c is then
+ * not symmetric and is inverted by Gauss-Jordan elimination with partial
+ * pivoting (MS_ERR_COARSE_SINGULAR on a zero pivot column).  A cycle whose
+ * last stage is a finite-volume stage leaves a residual that sums to zero
+ * over every block (local conservation).  Richardson iteration with a
+ * finite-volume stage is not guaranteed to converge (the correction is not
+ * an energy-norm projection); GMRES is the outer iteration to use with it.
+ * MS_PREC_MIXED: FP32 inverse of the equilibrated A_c (positive diagonal
+ * required, else FP64) with FP64 refinement, as for the Galerkin stage. */
+ms_status ms_coarse_create(ms_ctx *ctx, ms_system *sys, const ms_basis *basis, int32_t precision,
+                           int32_t restriction, ms_coarse **out);
 /* Recompute A_c and its factors in place from the basis and the current A. */
 ms_status ms_coarse_refresh(ms_ctx *ctx, ms_system *sys, ms_coarse *coarse);
 ms_status ms_coarse_release(ms_coarse *coarse);

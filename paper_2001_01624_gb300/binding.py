@@ -22,6 +22,7 @@ MS_ERR_COARSE_SINGULAR, MS_ERR_TIMEOUT, MS_ERR_STATE = 5, 6, 7
 MS_PREC_FP64, MS_PREC_MIXED = 0, 1
 MS_SMOOTHER_ILU0, MS_SMOOTHER_JACOBI = 0, 1
 MS_OUTER_RICHARDSON, MS_OUTER_GMRES = 0, 1
+MS_RESTRICT_GALERKIN, MS_RESTRICT_FV = 0, 1
 MS_SUPPORT_BOX, MS_SUPPORT_HOP, MS_SUPPORT_BLOCK = 0, 1, 2
 
 _vp, _i32, _i64, _d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
@@ -125,6 +126,8 @@ def lib():
         "ms_basis_get": ([_vp, _vp, _vp, _vp, _vp], _i32),
         "ms_add_adaptive_basis": ([_vp, _vp, _vp, P(ms_adapt_opts), P(_vp)], _i32),
         "ms_galerkin": ([_vp, _vp, _vp, _i32, P(_vp)], _i32),
+        "ms_coarse_create": ([_vp, _vp, _vp, _i32, _i32, P(_vp)], _i32),
+        "ms_partition_wells": ([_vp, _vp, _i32, _vp, _vp, _vp, P(_i32)], _i32),
         "ms_coarse_refresh": ([_vp, _vp, _vp], _i32),
         "ms_coarse_release": ([_vp], _i32),
         "ms_coarse_get": ([_vp, _vp, _vp, P(_i32)], _i32),
@@ -148,6 +151,7 @@ def exported_symbols() -> Sequence[str]:
     return ["ms_abi_version", "ms_status_string", "ms_last_error", "ms_create", "ms_destroy", "ms_set_stream",
             "ms_system_create", "ms_system_release", "ms_system_get_info", "ms_assemble_tpfa",
             "ms_system_get_matrix", "ms_spmv", "ms_ilu_apply", "ms_ilu_apply_noalloc", "ms_partition_cartesian", "ms_partition_components", "ms_partition_dynamic",
+            "ms_partition_wells", "ms_coarse_create",
             "ms_build_basis", "ms_basis_rebuild", "ms_basis_update", "ms_basis_release", "ms_basis_get_info",
             "ms_basis_get", "ms_add_adaptive_basis", "ms_galerkin", "ms_coarse_refresh", "ms_coarse_release",
             "ms_coarse_get", "ms_solve", "ms_solve_batch", "ms_total_mobility", "ms_transport_step", "ms_profile_enable", "ms_profile_reset", "ms_profile_read"]
@@ -284,6 +288,20 @@ def ms_partition_cartesian(ctx, sys, block):
     return part, m.value
 
 
+def ms_partition_wells(ctx, sys, wells):
+    """wells: sequence of active-cell index lists; returns (part, n_blocks)."""
+    n = ms_system_get_info(sys)["n"]
+    ptr = np.zeros(len(wells) + 1, np.int32)
+    for w, c in enumerate(wells):
+        ptr[w + 1] = ptr[w] + len(c)
+    cells = (np.concatenate([np.asarray(c, np.int32) for c in wells]) if len(wells) else np.zeros(1, np.int32))
+    cells = np.ascontiguousarray(cells, np.int32)
+    part = np.empty(n, np.int32)
+    m = _i32()
+    _check(lib().ms_partition_wells(ctx, sys, len(wells), _ptr(ptr), _ptr(cells), _ptr(part), C.byref(m)), ctx)
+    return part, m.value
+
+
 def ms_partition_components(ctx, sys, cls, part) -> int:
     m = _i32()
     _check(lib().ms_partition_components(ctx, sys, _ptr(_as(cls, np.int32)), _ptr(part), C.byref(m)), ctx)
@@ -351,6 +369,12 @@ def ms_add_adaptive_basis(ctx, sys, dp, n_bins=8, eps=1e-8, smoothed=0, omega=2.
 def ms_galerkin(ctx, sys, basis, precision=MS_PREC_FP64):
     h = _vp()
     _check(lib().ms_galerkin(ctx, sys, basis, precision, C.byref(h)), ctx)
+    return h
+
+
+def ms_coarse_create(ctx, sys, basis, precision=MS_PREC_FP64, restriction=MS_RESTRICT_GALERKIN):
+    h = _vp()
+    _check(lib().ms_coarse_create(ctx, sys, basis, precision, restriction, C.byref(h)), ctx)
     return h
 
 

@@ -277,8 +277,10 @@ __global__ void __launch_bounds__(128) k_ap(int n, int W, int B, const int *__re
     }
 }
 
-// Row j of A_c: warp-per-block accumulation over the support of block j.
-// A_c(j, :) = sum over the support of column j of P_ij (A P)(i, :), one warp
+// Row j of A_c: warp-per-block accumulation over row j of R.
+// A_c(j, :) = sum over row j of R of R_ji (A P)(i, :) (R = P^T: the support
+// of block j with weights P_ij; finite volume: block j's cells, unit
+// weights when cval is null), one warp
 // per column chunk with a dense shared-memory row accumulator (lanes take the
 // distinct entries of an (A P) row, cells in support order).  A column cut
 // into several chunks writes each chunk's row to its partial slot; the last
@@ -300,7 +302,7 @@ __global__ void k_rap(int n, int M, int WAP, int nch, int C, const int *__restri
     const int e0 = ch_beg[c], e1 = min(e0 + C, cptr[j + 1]);
     for (int e = e0; e < e1; ++e) {
         const int i = ccell[e];
-        const double p = cval[e];
+        const double p = cval ? cval[e] : 1.0;
         for (int w = lane; w < WAP; w += 32) {
             const int l = apid[(int64_t)w * n + i];
             if (l != kSlotPad) acc[l] += p * apval[(int64_t)w * n + i];
@@ -437,7 +439,8 @@ void launch_ap_fill(const ms_system &s, const ms_basis &b, ms_coarse &c, cudaStr
     MS_CHECK_LAUNCH();
 }
 
-void launch_rap(const ms_system &s, const ms_basis &b, ms_coarse &c, cudaStream_t st) {
+void launch_rap(const ms_system &s, const std::vector<int> &h_cptr, const int *cptr, const int *ccell,
+                const double *cval, bool symmetrise, ms_coarse &c, cudaStream_t st) {
     const int M = c.M;
     const size_t per_warp = (size_t)M * sizeof(double);
     MS_REQUIRE(per_warp <= 200 * 1024, MS_ERR_INVALID_ARG, "coarse system too large for the Galerkin kernel");
@@ -447,7 +450,7 @@ void launch_rap(const ms_system &s, const ms_basis &b, ms_coarse &c, cudaStream_
         int multi = 0;
         int C = kColChunk;
         for (;; C *= 2) {
-            build_column_chunks(b.h_cptr, M, C, cb, cc, cp, &sl, &multi);
+            build_column_chunks(h_cptr, M, C, cb, cc, cp, &sl, &multi);
             if ((double)multi * M * 8.0 <= 256.0 * 1024 * 1024 || C >= (1 << 30) / 2) break;
         }
         c.gchunk = C;
@@ -466,12 +469,14 @@ void launch_rap(const ms_system &s, const ms_basis &b, ms_coarse &c, cudaStream_
     MS_CUDA(raise_smem_limit(k_rap, smem, smem_set));
     KernelScope ks_(st, "rap", 0.0);
     k_rap<<<(c.n_gchunks + warps - 1) / warps, 32 * warps, smem, st>>>(
-        s.n, M, c.WAP, c.n_gchunks, c.gchunk, c.gch_beg.p, c.gch_col.p, c.gch_ptr.p, c.gch_slot.p, b.cptr.p, b.ccell.p,
-        b.cval.p, c.apid.p, c.apval.p, c.gpart.p, c.gcnt.p, c.Ac.p);
+        s.n, M, c.WAP, c.n_gchunks, c.gchunk, c.gch_beg.p, c.gch_col.p, c.gch_ptr.p, c.gch_slot.p, cptr, ccell,
+        cval, c.apid.p, c.apval.p, c.gpart.p, c.gcnt.p, c.Ac.p);
     MS_CHECK_LAUNCH();
-    const int64_t MM = (int64_t)M * M;
-    k_symmetrise<<<(int)((MM + kThreads - 1) / kThreads), kThreads, 0, st>>>(M, c.Ac.p);
-    MS_CHECK_LAUNCH();
+    if (symmetrise) {
+        const int64_t MM = (int64_t)M * M;
+        k_symmetrise<<<(int)((MM + kThreads - 1) / kThreads), kThreads, 0, st>>>(M, c.Ac.p);
+        MS_CHECK_LAUNCH();
+    }
 }
 
 }  // namespace msgb

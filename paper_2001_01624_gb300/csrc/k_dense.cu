@@ -10,8 +10,13 @@
 // FP32 path (mixed precision): A_c is symmetrically equilibrated,
 // s_i = 1/sqrt(A_ii), factored and inverted in FP32, and the inverse is
 // scaled back; the solve refines x_c in FP64 against the FP64 A_c.
+//
+// Finite-volume stages (A_c = R A P with R the block indicator, not
+// symmetric) are inverted by Gauss-Jordan elimination with partial pivoting
+// in one cooperative launch (k_gauss_jordan).
 #include <cmath>
 
+#include "grid_sync.cuh"
 #include "ms_internal.h"
 
 namespace msgb {
@@ -274,6 +279,185 @@ __global__ void k_d2f(int M, const double *a, float *b) {
     if (i < M) b[i] = (float)a[i];
 }
 
+// ------------------------------------------------- Gauss-Jordan inversion
+// In-place Gauss-Jordan elimination with row interchanges, A <- (Pi A)^{-1}
+// up to a column permutation.  Step k (all blocks, grid barrier between
+// phases):
+//   (a) reduce the per-block pivot candidates of column k to the pivot row p
+//       (largest |a_ik| over i >= k, lowest index on ties); copy row p to rowk
+//       and column k, with rows k and p exchanged, to colk;
+//   (b) scale the pivot row into row k, eliminate column k from every other
+//       row (row p receives the old row k), store the inverse's column k in
+//       place, and gather the per-block candidates of column k + 1.
+// The interchanges are undone on the columns afterwards (k_gj_order,
+// k_gj_gather).  A zero pivot column records kErrSingular and continues
+// with a zero reciprocal, so every block passes the same barriers.
+constexpr int kGJThreads = 512;
+
+__device__ __forceinline__ void gj_better(double &bv, int &bi, double v, int i) {
+    if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+}
+
+// Block-wide best candidate; every thread returns it.
+__device__ __forceinline__ void gj_block_best(double &bv, int &bi) {
+    __shared__ double s_v[kGJThreads / 32];
+    __shared__ int s_i[kGJThreads / 32];
+    __shared__ double s_bv;
+    __shared__ int s_bi;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v = __shfl_down_sync(0xffffffffu, bv, o);
+        const int i = __shfl_down_sync(0xffffffffu, bi, o);
+        gj_better(bv, bi, v, i);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s_v[w] = bv; s_i[w] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = s_v[0];
+        int i = s_i[0];
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) gj_better(v, i, s_v[q], s_i[q]);
+        s_bv = v;
+        s_bi = i;
+    }
+    __syncthreads();
+    bv = s_bv;
+    bi = s_bi;
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kGJThreads) k_gauss_jordan(int M, T *A, T *rowk, T *colk, double *cand_v,
+                                                             int *cand_i, int *piv, unsigned long long *bar,
+                                                             int *err) {
+    const int G = gridDim.x;
+    const int total = 2 * M;          // barriers in this launch
+    GridSync gs;
+    gs.begin(bar, err);
+    // candidates of column 0
+    {
+        double bv = -1.0;
+        int bi = M;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += G * blockDim.x)
+            gj_better(bv, bi, fabs((double)A[(int64_t)i * M]), i);
+        gj_block_best(bv, bi);
+        if (threadIdx.x == 0) { cand_v[blockIdx.x] = bv; cand_i[blockIdx.x] = bi; }
+    }
+    if (!gs.sync(total)) return;
+    for (int k = 0; k < M; ++k) {
+        // (a) pivot row, copies of the pivot row and of column k
+        double bv = -1.0;
+        int bi = M;
+        for (int t = threadIdx.x; t < G; t += blockDim.x) gj_better(bv, bi, __ldcg(&cand_v[t]), __ldcg(&cand_i[t]));
+        gj_block_best(bv, bi);
+        const bool ok = bv > 0.0 && bi < M;
+        const int p = ok ? bi : k;
+        if (!ok && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, kErrSingular);
+        if (blockIdx.x == 0 && threadIdx.x == 0) piv[k] = p;
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 2 * M; t += G * blockDim.x) {
+            if (t < M) {
+                const int src = t == k ? p : (t == p ? k : t);
+                colk[t] = A[(int64_t)src * M + k];
+            } else {
+                rowk[t - M] = A[(int64_t)p * M + (t - M)];
+            }
+        }
+        if (!gs.sync(total)) return;
+        // (b) elimination
+        const T pv = __ldcg(&rowk[k]);
+        const T inv = ok ? T(1) / pv : T(0);
+        bv = -1.0;
+        bi = M;
+        for (int i = blockIdx.x; i < M; i += G) {
+            if (i == p && p != k) continue;           // written with row k
+            T *a = A + (int64_t)i * M;
+            if (i == k) {
+                T *ap = A + (int64_t)p * M;
+                const T f = __ldcg(&colk[p]);         // old a_kk, for the row moved to p
+                for (int j = threadIdx.x; j < M; j += blockDim.x) {
+                    const T sc = j == k ? inv : __ldcg(&rowk[j]) * inv;
+                    if (p != k) {
+                        const T old = a[j];
+                        const T v = j == k ? -f * inv : old - f * sc;
+                        ap[j] = v;
+                        if (j == k + 1) gj_better(bv, bi, fabs((double)v), p);
+                    }
+                    a[j] = sc;
+                }
+            } else {
+                const T f = __ldcg(&colk[i]);
+                for (int j = threadIdx.x; j < M; j += blockDim.x) {
+                    const T v = j == k ? -f * inv : a[j] - f * (__ldcg(&rowk[j]) * inv);
+                    a[j] = v;
+                    if (j == k + 1 && i > k) gj_better(bv, bi, fabs((double)v), i);
+                }
+            }
+        }
+        if (k + 1 == M) break;
+        gj_block_best(bv, bi);
+        if (threadIdx.x == 0) { cand_v[blockIdx.x] = bv; cand_i[blockIdx.x] = bi; }
+        if (!gs.sync(total)) return;
+    }
+}
+
+// Column order after the interchanges: undoing them in reverse order on the
+// columns of the in-place result gives the inverse.
+__global__ void k_gj_order(int M, const int *piv, int *idx) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int j = 0; j < M; ++j) idx[j] = j;
+    for (int k = M - 1; k >= 0; --k) {
+        const int p = piv[k];
+        const int t = idx[k];
+        idx[k] = idx[p];
+        idx[p] = t;
+    }
+}
+
+template <typename T>
+__global__ void k_gj_gather(int M, const T *__restrict__ A, const int *__restrict__ idx, T *__restrict__ X) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)M * M) return;
+    const int r = (int)(e / M), c = (int)(e % M);
+    X[e] = A[(int64_t)r * M + idx[c]];
+}
+
+template <typename T>
+void gauss_jordan_inverse(ms_coarse &c, T *A, T *X, T *vec, int *err, cudaStream_t st) {
+    const int M = c.M;
+    auto kern = k_gauss_jordan<T>;
+    int per_sm = 0, sms = 0, dev = 0;
+    MS_CUDA(cudaGetDevice(&dev));
+    MS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGJThreads, 0));
+    MS_REQUIRE(per_sm >= 1, MS_ERR_CUDA, "Gauss-Jordan kernel cannot be resident");
+    const int G = std::max(1, std::min(sms, M));
+    c.gj_cand_v.alloc(G);
+    c.gj_cand_i.alloc(G);
+    c.gj_piv.alloc(M);
+    c.gj_idx.alloc(M);
+    if (c.gj_bar.n == 0) {
+        c.gj_bar.alloc(2);
+        c.gj_bar.zero(st);
+    }
+    KernelScope ks_(st, sizeof(T) == 8 ? "coarse_gauss_jordan" : "coarse_gauss_jordan32", 0.0);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(kGJThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;   // the grid barrier needs every block resident
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, M, A, vec, vec + M, c.gj_cand_v.p, c.gj_cand_i.p,
+                                             c.gj_piv.p, c.gj_bar.p, err);
+    MS_CUDA(e);
+    k_gj_order<<<1, 32, 0, st>>>(M, c.gj_piv.p, c.gj_idx.p);
+    const int64_t MM = (int64_t)M * M;
+    k_gj_gather<T><<<(int)((MM + 255) / 256), 256, 0, st>>>(M, A, c.gj_idx.p, X);
+    MS_CHECK_LAUNCH();
+}
+
 template <typename T>
 void factor_inverse(T *A, T *Y, T *X, int M, int *err, cudaStream_t st) {
     KernelScope ks_(st, sizeof(T) == 8 ? "coarse_factor_inverse" : "coarse_factor_inverse32", 0.0);
@@ -330,6 +514,37 @@ void dense_factor_inverse32(ms_coarse &c, int *err, cudaStream_t st) {
     MS_CHECK_LAUNCH();
     factor_inverse<float>(c.work32.p, c.work32.p + MM, c.inv32.p, M, err, st);
     k_unscale<<<(int)((MM + 255) / 256), 256, 0, st>>>(c.inv32.p, c.work64.p, M);
+    MS_CHECK_LAUNCH();
+}
+
+// Finite-volume stages: Gauss-Jordan with partial pivoting.  FP64: work64
+// holds the matrix being reduced and the pivot row / column copies.
+void dense_gj_inverse64(ms_coarse &c, int *err, cudaStream_t st) {
+    const int M = c.M;
+    const int64_t MM = (int64_t)M * M;
+    c.work64.alloc(MM + 2 * (int64_t)M);
+    c.inv64.alloc(MM);
+    MS_CUDA(cudaMemcpyAsync(c.work64.p, c.Ac.p, MM * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    gauss_jordan_inverse<double>(c, c.work64.p, c.inv64.p, c.work64.p + MM, err, st);
+}
+
+// FP32: equilibrated as the Cholesky path (positive diagonal required; the
+// caller checks it first), reduced in FP32, scaled back.
+void dense_gj_inverse32(ms_coarse &c, int *err, cudaStream_t st) {
+    const int M = c.M;
+    const int64_t MM = (int64_t)M * M;
+    c.work32.alloc(MM + 2 * (int64_t)M);
+    c.inv32.alloc(MM);
+    c.work64.alloc(M);   // scale vector
+    k_equilibrate<<<(int)((MM + 255) / 256), 256, 0, st>>>(c.Ac.p, c.work32.p, c.work64.p, M);
+    MS_CHECK_LAUNCH();
+    gauss_jordan_inverse<float>(c, c.work32.p, c.inv32.p, c.work32.p + MM, err, st);
+    k_unscale<<<(int)((MM + 255) / 256), 256, 0, st>>>(c.inv32.p, c.work64.p, M);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_check_diag(const ms_coarse &c, int *err, cudaStream_t st) {
+    k_check_diag<<<(c.M + 255) / 256, 256, 0, st>>>(c.Ac.p, c.M, err);
     MS_CHECK_LAUNCH();
 }
 

@@ -11,6 +11,7 @@
 // started before it: the sweep cannot deadlock.  Every wait is bounded; a
 // wait that runs out raises an error bit and the sweep drains without
 // further waiting.  Flags hold a sweep counter, so no reset pass is needed.
+#include "grid_sync.cuh"
 #include "ms_internal.h"
 
 namespace msgb {
@@ -187,49 +188,12 @@ __global__ void __launch_bounds__(kSweepThreads) k_ilu_bwd(int n, int W, int nto
 // the whole grid takes a level's rows, then meets at a grid barrier before the
 // next level.  Forward L y = r, or backward (BWD) U z = y in reverse level order.
 //
-// Barrier: a 64-bit arrival counter bar[0] that only grows (one fire-and-forget
-// add per block per barrier; a block passes barrier j of this launch when the
-// counter reaches base + j * blocks), and bar[1] = the counter's value when a
-// launch starts, advanced by block 0 once every block has read it.  Waits are
-// bounded: after 2 s of device time a block records a timeout and the launch
-// ends early.  A row's slots, right-hand side and pivot do not depend on the
+// Barrier: GridSync (bounded; a block that gives up records a timeout and the
+// launch ends early).  A row's slots, right-hand side and pivot do not depend on the
 // sweep's results, so each thread loads its next row before the barrier; after
 // it only the neighbours' results are read.
 constexpr int kLevelThreads = 512;
 constexpr int kLevelSlots = 8;      // slots held in registers (wider rows take the flag-ordered sweeps)
-
-__device__ __forceinline__ unsigned long long grid_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ bool level_barrier(unsigned long long *cnt, unsigned long long target, int *err) {
-    __shared__ int s_fail;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        s_fail = 0;
-        __threadfence();
-        atomicAdd(cnt, 1ull);
-        volatile unsigned long long *c = cnt;
-        unsigned long long t0 = 0;
-        int spins = 0;
-        while (*c < target) {
-            if ((++spins & 63) == 0) {
-                const unsigned long long now = grid_ns();
-                if (t0 == 0) t0 = now;
-                else if (now - t0 > 2000000000ull) {
-                    atomicOr(err, kErrTimeout);
-                    s_fail = 1;
-                    break;
-                }
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return s_fail == 0;
-}
 
 template <typename T>
 struct LevelRow {
@@ -274,7 +238,8 @@ __global__ void __launch_bounds__(kLevelThreads) k_level_sweep(int n, int W, int
     const int G = gridDim.x;
     const int gsize = G * blockDim.x;
     const int j0 = threadIdx.x * G + blockIdx.x;     // rows of a level spread over all blocks first
-    const unsigned long long base = __ldcg(&bar[1]);
+    GridSync gs;
+    gs.begin(bar, err);
     LevelRow<T> row;
     {
         const int L = BWD ? nlev - 1 : 0;
@@ -305,9 +270,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level_sweep(int n, int W, int
         if (li + 1 == nlev) break;
         const int Ln = BWD ? L - 1 : L + 1;
         level_row_load<T, TR, BWD>(row, lev_off[Ln] + j0, lev_off[Ln + 1], n, W, lperm, col, lu, dinv, rhs);
-        if (!level_barrier(bar, base + (unsigned long long)(li + 1) * G, err)) return;
-        if (li == 0 && blockIdx.x == 0 && threadIdx.x == 0)      // every block has read bar[1]
-            bar[1] = base + (unsigned long long)(nlev - 1) * G;
+        if (!gs.sync(nlev - 1)) return;
     }
 }
 

@@ -223,7 +223,8 @@ __global__ void k_to_float(const double *a, float *b, int64_t n) {
 }
 
 // ------------------------------------------------------ restrict / prolong
-// d_j = sum over the support of block j of P_ij r_i, one warp per column
+// d_j = sum over row j of R (the support of block j with weights P_ij, or the
+// cells of block j with unit weights) of R_ji r_i, one warp per column
 // chunk: chunk sums in a fixed lane order, then the last chunk of a column to
 // finish adds the column's chunk sums in chunk order (deterministic; balanced
 // however uneven the supports are).  ACC is the accumulation type.
@@ -238,7 +239,10 @@ __global__ void k_restrict_ch(int nch, const int *__restrict__ ch_beg, const int
     const int j = ch_col[c];
     const int e0 = ch_beg[c], e1 = min(e0 + kColChunk, cptr[j + 1]);
     ACC s = ACC(0);
-    for (int e = e0 + lane; e < e1; e += 32) s += (ACC)cval[e] * (ACC)r[ccell[e]];
+    if (cval)
+        for (int e = e0 + lane; e < e1; e += 32) s += (ACC)cval[e] * (ACC)r[ccell[e]];
+    else   // unit weights: the finite-volume restriction sums the block's cells
+        for (int e = e0 + lane; e < e1; e += 32) s += (ACC)r[ccell[e]];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane != 0) return;
@@ -542,21 +546,41 @@ void build_column_chunks(const std::vector<int> &cptr, int M, int C, std::vector
     if (multi) *multi = nm;
 }
 
-void launch_restrict(const ms_basis &b, const double *r, double *d, cudaStream_t st) {
-    KernelScope ks_(st, "restrict", (double)b.nnz * (4 + 8) + (double)b.M * (8 + 4));
-    const int g = (int)(((int64_t)b.n_chunks * 32 + kThreads - 1) / kThreads);
+void launch_restrict(const RestrictView &v, const double *r, double *d, cudaStream_t st) {
+    KernelScope ks_(st, "restrict", (double)v.nnz * (4 + (v.cval ? 8 : 0) + 8) + (double)v.M * (8 + 4));
+    const int g = (int)(((int64_t)v.n_chunks * 32 + kThreads - 1) / kThreads);
     k_restrict_ch<double, double, double, double><<<g, kThreads, 0, st>>>(
-        b.n_chunks, b.ch_beg.p, b.ch_col.p, b.ch_ptr.p, b.cptr.p, b.ccell.p, b.cval.p, r, b.ch_part.p, b.ch_cnt.p, d);
+        v.n_chunks, v.ch_beg, v.ch_col, v.ch_ptr, v.cptr, v.ccell, v.cval, r, v.ch_part, v.ch_cnt, d);
     MS_CHECK_LAUNCH();
 }
 
-void launch_restrict32(const ms_basis &b, const float *r, float *d, cudaStream_t st) {
-    KernelScope ks_(st, "restrict32", (double)b.nnz * (4 + 4) + (double)b.M * (4 + 4));
-    const int g = (int)(((int64_t)b.n_chunks * 32 + kThreads - 1) / kThreads);
+void launch_restrict32(const RestrictView &v, const float *r, float *d, cudaStream_t st) {
+    KernelScope ks_(st, "restrict32", (double)v.nnz * (4 + (v.cval32 ? 4 : 0) + 4) + (double)v.M * (4 + 4));
+    const int g = (int)(((int64_t)v.n_chunks * 32 + kThreads - 1) / kThreads);
     k_restrict_ch<float, float, float, float><<<g, kThreads, 0, st>>>(
-        b.n_chunks, b.ch_beg.p, b.ch_col.p, b.ch_ptr.p, b.cptr.p, b.ccell.p, b.cval32.p, r, b.ch_part.p, b.ch_cnt.p,
-        d);
+        v.n_chunks, v.ch_beg, v.ch_col, v.ch_ptr, v.cptr, v.ccell, v.cval32, r, v.ch_part, v.ch_cnt, d);
     MS_CHECK_LAUNCH();
+}
+
+RestrictView restrict_view(const ms_coarse &c) {
+    RestrictView v;
+    v.M = c.M;
+    if (c.restriction == MS_RESTRICT_FV) {
+        v.nnz = c.fv_h_cptr.empty() ? 0 : c.fv_h_cptr.back();
+        v.n_chunks = c.fv_n_chunks;
+        v.ch_beg = c.fv_ch_beg.p; v.ch_col = c.fv_ch_col.p; v.ch_ptr = c.fv_ch_ptr.p;
+        v.cptr = c.fv_cptr.p; v.ccell = c.fv_ccell.p;
+        v.ch_part = c.fv_ch_part.p; v.ch_cnt = c.fv_ch_cnt.p;
+        return v;
+    }
+    const ms_basis &b = *c.basis;
+    v.nnz = b.nnz;
+    v.n_chunks = b.n_chunks;
+    v.ch_beg = b.ch_beg.p; v.ch_col = b.ch_col.p; v.ch_ptr = b.ch_ptr.p;
+    v.cptr = b.cptr.p; v.ccell = b.ccell.p;
+    v.cval = b.cval.p; v.cval32 = b.cval32.p;
+    v.ch_part = b.ch_part.p; v.ch_cnt = b.ch_cnt.p;
+    return v;
 }
 
 void launch_prolong(const ms_basis &b, int n, const double *xc, double *x, cudaStream_t st) {

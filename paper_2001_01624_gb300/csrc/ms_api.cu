@@ -233,9 +233,23 @@ ms_basis *create_basis(ms_ctx *ctx, ms_system &s, const std::vector<int> &part, 
     return b.release();
 }
 
+// Error word of a coarse factorisation: a timeout of the Gauss-Jordan grid
+// barrier resets its counter before the error is raised.
+void coarse_error(ms_ctx *ctx, ms_coarse &c, int err) {
+    if (!err) return;
+    if (err & kErrTimeout) {
+        if (c.gj_bar.n) MS_CUDA(cudaMemsetAsync(c.gj_bar.p, 0, 2 * sizeof(unsigned long long), ctx->stream));
+        throw Error{MS_ERR_TIMEOUT, "a coarse factorisation wait ran out"};
+    }
+    throw Error{MS_ERR_COARSE_SINGULAR, c.restriction == MS_RESTRICT_FV
+                                            ? "coarse Gauss-Jordan elimination met a zero pivot column"
+                                            : "coarse Cholesky met a non-positive pivot"};
+}
+
 void galerkin_values(ms_ctx *ctx, ms_system &s, const ms_basis &b, ms_coarse &c) {
     cudaStream_t st = ctx->stream;
     MS_REQUIRE(s.assembled, MS_ERR_STATE, "system not assembled");
+    const bool fv = c.restriction == MS_RESTRICT_FV;
     s.w_i0.alloc(4);
     int *h = (int *)ctx->pinned.get(64);
     const int wap = launch_ap_count(s, b, s.w_i0.p, h, st);
@@ -244,37 +258,80 @@ void galerkin_values(ms_ctx *ctx, ms_system &s, const ms_basis &b, ms_coarse &c)
     c.apval.alloc((size_t)c.WAP * s.n);
     launch_ap_fill(s, b, c, st);
     c.Ac.alloc((size_t)c.M * c.M);
-    launch_rap(s, b, c, st);
+    if (fv) launch_rap(s, c.fv_h_cptr, c.fv_cptr.p, c.fv_ccell.p, nullptr, false, c, st);
+    else launch_rap(s, b.h_cptr, b.cptr.p, b.ccell.p, b.cval.p, true, c, st);
     MS_CUDA(cudaMemsetAsync(s.w_i0.p, 0, sizeof(int), st));
     c.use64 = false;
     c.inv32_error = 0.0;
+    auto inverse64 = [&]() { fv ? dense_gj_inverse64(c, s.w_i0.p, st) : dense_factor_inverse64(c, s.w_i0.p, st); };
     if (c.precision == MS_PREC_MIXED) {
-        dense_factor_inverse32(c, s.w_i0.p, st);
-        const int err32 = read_error_word(ctx, s.w_i0.p);
-        c.inv32_error = err32 ? INFINITY : coarse_inverse_check32(c, (double *)ctx->pinned.get(64), st);
+        bool try32 = true;
+        if (fv) {   // the FP32 path equilibrates with 1/sqrt(a_jj)
+            launch_check_diag(c, s.w_i0.p, st);
+            try32 = read_error_word(ctx, s.w_i0.p) == 0;
+            MS_CUDA(cudaMemsetAsync(s.w_i0.p, 0, sizeof(int), st));
+        }
+        if (try32) {
+            if (fv) dense_gj_inverse32(c, s.w_i0.p, st);
+            else dense_factor_inverse32(c, s.w_i0.p, st);
+            const int err32 = read_error_word(ctx, s.w_i0.p);
+            if (err32 & kErrTimeout) coarse_error(ctx, c, err32);
+            c.inv32_error = err32 ? INFINITY : coarse_inverse_check32(c, (double *)ctx->pinned.get(64), st);
+        } else {
+            c.inv32_error = INFINITY;
+        }
         // each FP64 refinement step contracts the coarse error by about this
         // factor (two steps: its square); fall back to an FP64 inverse when
         // FP32 cannot resolve this coarse system to about 1e-3
         if (!(c.inv32_error <= 0.03)) {
             c.use64 = true;
             MS_CUDA(cudaMemsetAsync(s.w_i0.p, 0, sizeof(int), st));
-            dense_factor_inverse64(c, s.w_i0.p, st);
+            inverse64();
         }
     } else {
-        dense_factor_inverse64(c, s.w_i0.p, st);
+        inverse64();
     }
-    const int err = read_error_word(ctx, s.w_i0.p);
-    if (err) throw Error{MS_ERR_COARSE_SINGULAR, "coarse Cholesky met a non-positive pivot"};
+    coarse_error(ctx, c, read_error_word(ctx, s.w_i0.p));
     // the apid/apval scratch is only needed while forming A_c
     c.apid.release();
     c.apval.release();
 }
 
-ms_coarse *create_coarse(ms_ctx *ctx, ms_system &s, const ms_basis &b, int precision) {
+// Block member lists of the finite-volume restriction (cells ascending) and
+// their column chunks.
+void fv_view(ms_ctx *ctx, const ms_basis &b, ms_coarse &c) {
+    const int M = b.M;
+    const int n = (int)b.h_part.size();
+    std::vector<int> cptr(M + 1, 0), cell(n);
+    for (int i = 0; i < n; ++i) {
+        MS_REQUIRE(b.h_part[i] >= 0 && b.h_part[i] < M, MS_ERR_INVALID_ARG, "partition entry out of range");
+        cptr[b.h_part[i] + 1]++;
+    }
+    for (int j = 0; j < M; ++j) cptr[j + 1] += cptr[j];
+    std::vector<int> fill(cptr.begin(), cptr.end() - 1);
+    for (int i = 0; i < n; ++i) cell[fill[b.h_part[i]]++] = i;
+    cudaStream_t st = ctx->stream;
+    std::vector<int> cb, cc, cp;
+    build_column_chunks(cptr, M, kColChunk, cb, cc, cp, nullptr, nullptr);
+    c.fv_n_chunks = (int)cb.size();
+    c.fv_ch_beg.upload(cb, st);
+    c.fv_ch_col.upload(cc, st);
+    c.fv_ch_ptr.upload(cp, st);
+    c.fv_ch_part.alloc(std::max<size_t>(cb.size(), 1));
+    c.fv_ch_cnt.alloc(std::max(M, 1));
+    c.fv_ch_cnt.zero(st);
+    c.fv_cptr.upload(cptr, st);
+    c.fv_ccell.upload(cell, st);
+    c.fv_h_cptr = std::move(cptr);
+}
+
+ms_coarse *create_coarse(ms_ctx *ctx, ms_system &s, const ms_basis &b, int precision, int restriction) {
     std::unique_ptr<ms_coarse> c(new ms_coarse());
     c->M = b.M;
     c->precision = precision;
     c->basis = &b;
+    c->restriction = restriction;
+    if (restriction == MS_RESTRICT_FV) fv_view(ctx, b, *c);
     galerkin_values(ctx, s, b, *c);
     return c.release();
 }
@@ -498,6 +555,31 @@ ms_status ms_partition_cartesian(ms_ctx *ctx, const ms_system *s, int32_t bx, in
     API_CATCH(ctx)
 }
 
+ms_status ms_partition_wells(ms_ctx *ctx, const ms_system *s, int32_t n_wells, const int32_t *well_ptr,
+                             const int32_t *well_cells, int32_t *part, int32_t *n_blocks) {
+    if (!ctx || !s || !part || !n_blocks || n_wells < 0 || (n_wells > 0 && (!well_ptr || !well_cells)))
+        return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    API_TRY
+    const int n = s->n;
+    MS_REQUIRE(well_ptr == nullptr || well_ptr[0] == 0, MS_ERR_INVALID_ARG, "well_ptr[0] must be 0");
+    std::vector<int> p(n, -1);
+    for (int w = 0; w < n_wells; ++w) {
+        MS_REQUIRE(well_ptr[w + 1] >= well_ptr[w], MS_ERR_INVALID_ARG, "well_ptr must not decrease");
+        for (int e = well_ptr[w]; e < well_ptr[w + 1]; ++e) {
+            const int i = well_cells[e];
+            MS_REQUIRE(i >= 0 && i < n, MS_ERR_INVALID_ARG, "well cell out of range");
+            MS_REQUIRE(p[i] == -1, MS_ERR_INVALID_ARG, "cell listed in two wells (or twice)");
+            p[i] = w;
+        }
+    }
+    for (int &v : p)
+        if (v == -1) v = n_wells;
+    std::memcpy(part, p.data(), (size_t)n * sizeof(int));
+    *n_blocks = n_wells + 1;
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
 ms_status ms_partition_components(ms_ctx *ctx, const ms_system *sc, const int32_t *cls, int32_t *part,
                                   int32_t *n_blocks) {
     if (!ctx || !sc || !cls || !part || !n_blocks) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
@@ -643,7 +725,23 @@ ms_status ms_galerkin(ms_ctx *ctx, ms_system *s, const ms_basis *b, int32_t prec
     MS_REQUIRE(precision == MS_PREC_FP64 || precision == MS_PREC_MIXED, MS_ERR_INVALID_ARG, "unknown precision");
     MS_REQUIRE(precision == MS_PREC_FP64 || b->precision == MS_PREC_MIXED, MS_ERR_INVALID_ARG,
                "a mixed-precision coarse operator needs a mixed-precision basis");
-    *out = create_coarse(ctx, *s, *b, precision);
+    *out = create_coarse(ctx, *s, *b, precision, MS_RESTRICT_GALERKIN);
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_coarse_create(ms_ctx *ctx, ms_system *s, const ms_basis *b, int32_t precision, int32_t restriction,
+                           ms_coarse **out) {
+    if (!ctx || !s || !b || !out) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    API_TRY
+    DeviceGuard g(ctx->device);
+    MS_REQUIRE(precision == MS_PREC_FP64 || precision == MS_PREC_MIXED, MS_ERR_INVALID_ARG, "unknown precision");
+    MS_REQUIRE(precision == MS_PREC_FP64 || b->precision == MS_PREC_MIXED, MS_ERR_INVALID_ARG,
+               "a mixed-precision coarse operator needs a mixed-precision basis");
+    MS_REQUIRE(restriction == MS_RESTRICT_GALERKIN || restriction == MS_RESTRICT_FV, MS_ERR_INVALID_ARG,
+               "unknown restriction");
+    *out = create_coarse(ctx, *s, *b, precision, restriction);
     return MS_OK;
     API_CATCH(ctx)
 }
@@ -780,7 +878,7 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
                 if (!mixed) {   // FP64 residual restricted with the FP32 basis copy
                     launch_to_float(s->w_r.p, s->w_r32.p, n, st);
                 }
-                launch_restrict32(b, s->w_r32.p, s->w_d32.p, st);
+                launch_restrict32(restrict_view(c), s->w_r32.p, s->w_d32.p, st);
                 // coarse solve: FP32 inverse with FP64 refinement against A_c
                 // (or the FP64 inverse when FP32 cannot resolve this coarse system)
                 launch_widen(s->w_d32.p, s->w_d.p, M, st);
@@ -789,7 +887,7 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
                 launch_narrow(s->w_xc.p, s->w_xc32.p, M, st);
                 launch_prolong32(b, n, s->w_xc32.p, s->w_x.p, st);
             } else {
-                launch_restrict(b, s->w_r.p, s->w_d.p, st);
+                launch_restrict(restrict_view(c), s->w_r.p, s->w_d.p, st);
                 launch_gemv64(c.inv64.p, M, s->w_d.p, s->w_xc.p, st);
                 launch_prolong(b, n, s->w_xc.p, s->w_x.p, st);
             }
@@ -920,7 +1018,7 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
             const int dprec = mixed ? MS_PREC_MIXED : MS_PREC_FP64;
             dyn_coarse.reset();
             dyn_basis.reset(adaptive_basis(ctx, *s, s->w_part.p, opts->adapt, dprec));
-            dyn_coarse.reset(create_coarse(ctx, *s, *dyn_basis, dprec));
+            dyn_coarse.reset(create_coarse(ctx, *s, *dyn_basis, dprec, MS_RESTRICT_GALERKIN));
             Mmax = std::max(Mmax, dyn_basis->M);
             grow_coarse_work();
         }

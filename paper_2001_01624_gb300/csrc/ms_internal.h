@@ -304,7 +304,37 @@ struct ms_coarse {
     int WAP = 0;
     msgb::DBuf<int> apid;
     msgb::DBuf<double> apval;
+    // restriction: MS_RESTRICT_GALERKIN (R = P^T) or MS_RESTRICT_FV (R sums
+    // each block's cells: block member lists, ascending cells, with their
+    // column chunks; unit weights)
+    int restriction = 0;
+    std::vector<int> fv_h_cptr;
+    msgb::DBuf<int> fv_cptr, fv_ccell, fv_ch_beg, fv_ch_col, fv_ch_ptr;
+    msgb::DBuf<double> fv_ch_part;
+    msgb::DBuf<unsigned> fv_ch_cnt;
+    int fv_n_chunks = 0;
+    // Gauss-Jordan scratch (finite-volume stages)
+    msgb::DBuf<double> gj_cand_v;
+    msgb::DBuf<int> gj_cand_i, gj_piv, gj_idx;
+    msgb::DBuf<unsigned long long> gj_bar;
 };
+
+namespace msgb {
+// Column view of a restriction operator (row j of R = entries [cptr[j],
+// cptr[j+1]) over cells ccell with weights cval / cval32, or unit weights
+// when they are null), cut into column chunks for deterministic sums.
+struct RestrictView {
+    int M = 0;
+    int64_t nnz = 0;
+    int n_chunks = 0;
+    const int *ch_beg = nullptr, *ch_col = nullptr, *ch_ptr = nullptr, *cptr = nullptr, *ccell = nullptr;
+    const double *cval = nullptr;
+    const float *cval32 = nullptr;
+    double *ch_part = nullptr;
+    unsigned *ch_cnt = nullptr;
+};
+RestrictView restrict_view(const ms_coarse &c);
+}  // namespace msgb
 
 namespace msgb {
 
@@ -353,8 +383,8 @@ void launch_sub(const double *a, const double *b, double *c, int n, cudaStream_t
 void launch_scatter_zero(double *v, int idx, cudaStream_t st);
 void build_column_chunks(const std::vector<int> &cptr, int M, int C, std::vector<int> &beg, std::vector<int> &col,
                          std::vector<int> &ptr, std::vector<int> *slot, int *multi);
-void launch_restrict(const ms_basis &b, const double *r, double *d, cudaStream_t st);
-void launch_restrict32(const ms_basis &b, const float *r, float *d, cudaStream_t st);
+void launch_restrict(const RestrictView &v, const double *r, double *d, cudaStream_t st);
+void launch_restrict32(const RestrictView &v, const float *r, float *d, cudaStream_t st);
 void launch_prolong(const ms_basis &b, int n, const double *xc, double *x, cudaStream_t st);
 void launch_prolong32(const ms_basis &b, int n, const float *xc, double *x, cudaStream_t st);
 void launch_to_float(const double *a, float *b, int64_t n, cudaStream_t st);
@@ -389,10 +419,16 @@ void launch_basis_columns(ms_basis &b, cudaStream_t st);
 // Galerkin
 int launch_ap_count(const ms_system &s, const ms_basis &b, int *cnt_max, int *host_pinned, cudaStream_t st);
 void launch_ap_fill(const ms_system &s, const ms_basis &b, ms_coarse &c, cudaStream_t st);
-void launch_rap(const ms_system &s, const ms_basis &b, ms_coarse &c, cudaStream_t st);
+// A_c = R (A P) from the (A P) lists of c, R given by its column view
+// (cval null: unit weights); symmetrise for the Galerkin operator.
+void launch_rap(const ms_system &s, const std::vector<int> &h_cptr, const int *cptr, const int *ccell,
+                const double *cval, bool symmetrise, ms_coarse &c, cudaStream_t st);
 // dense
 void dense_factor_inverse64(ms_coarse &c, int *err, cudaStream_t st);
 void dense_factor_inverse32(ms_coarse &c, int *err, cudaStream_t st);
+void dense_gj_inverse64(ms_coarse &c, int *err, cudaStream_t st);
+void dense_gj_inverse32(ms_coarse &c, int *err, cudaStream_t st);
+void launch_check_diag(const ms_coarse &c, int *err, cudaStream_t st);
 double coarse_inverse_check32(const ms_coarse &c, double *host2, cudaStream_t st);
 void launch_gemv64(const double *A, int M, const double *x, double *y, cudaStream_t st);
 void launch_gemv32(const float *A, int M, const float *x, float *y, cudaStream_t st);

@@ -577,3 +577,127 @@ def test_mobility_and_transport_match_oracle(ms, ctx, case):
     assert k == k_ref and k > 1
     np.testing.assert_allclose(S_gpu, S_ref, rtol=1e-11, atol=1e-12)
     ms.ms_system_release(s)
+
+
+# ------------------------------------------------- finite-volume restriction, well bases
+def _fv_setup(ms, ctx, gm, prec):
+    s = _system(ms, ctx, gm)
+    part, M = ms.ms_partition_cartesian(ctx, s, gm.block)
+    b, _ = ms.ms_build_basis(ctx, s, part, M, block=gm.block, precision=prec)
+    c = ms.ms_coarse_create(ctx, s, b, prec, ms.MS_RESTRICT_FV)
+    return s, b, c
+
+
+@pytest.mark.parametrize("case", ["3d_10x10x4", "faulted_18x14x7", "ragged_13x11x5", "2d_12x8"])
+def test_fv_coarse_operator_matches_oracle(ms, ctx, case):
+    """A_c = R A P, R the block indicator (Sec. 5): same entries as the
+    oracle's; not symmetric."""
+    gm = CASES[case]()
+    s, b, c = _fv_setup(ms, ctx, gm, ms.MS_PREC_FP64)
+    Ac = ms.ms_coarse_get(ctx, c)
+    sysr, Ap, qp, B, _, _ = _oracle_general(gm)
+    Acr = O.galerkin_fv(Ap, B)
+    np.testing.assert_allclose(Ac, Acr, rtol=0, atol=1e-12 * np.abs(Acr).max())
+    ms.ms_coarse_refresh(ctx, s, c)
+    assert np.array_equal(ms.ms_coarse_get(ctx, c), Ac)
+    ms.ms_coarse_release(c)
+    ms.ms_basis_release(b)
+    ms.ms_system_release(s)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", ["3d_10x10x4", "faulted_18x14x7"])
+def test_fv_cycle_matches_oracle_and_conserves(ms, ctx, precision, case):
+    """Cycles with a finite-volume stage (Gauss-Jordan inverse of the
+    non-symmetric A_c): the iterate after one and three cycles matches the
+    oracle's (LU solves), and the residual sums to zero over every block."""
+    gm = CASES[case]()
+    prec = ms.MS_PREC_FP64 if precision == "fp64" else ms.MS_PREC_MIXED
+    s, b, c = _fv_setup(ms, ctx, gm, prec)
+    sysr, Ap, qp, B, _, _ = _oracle_general(gm)
+    F = O.coarse_fv(Ap, B)
+    q = gm.q_active()
+    for cycles in (1, 3):
+        p = np.zeros_like(q)
+        info = ms.ms_solve(ctx, s, [c], q, p, tol=1e-30, max_iter=cycles, precision=prec)
+        assert info["iters"] == cycles
+        r = O.ms_solve(Ap, [(B, F)], qp, tol=1e-30, max_iter=cycles)
+        tol = 1e-10 if precision == "fp64" else 1e-5
+        assert np.linalg.norm(p - r.x) <= tol * np.linalg.norm(r.x)
+        res = qp - Ap.to_scipy() @ p
+        sums = np.bincount(B.part, weights=res, minlength=B.M)
+        assert np.abs(sums).max() <= (1e-9 if precision == "fp64" else 1e-4) * np.abs(res).sum()
+    ms.ms_coarse_release(c)
+    ms.ms_basis_release(b)
+    ms.ms_system_release(s)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fv_gmres_matches_oracle(ms, ctx, precision):
+    gm = CASES["faulted_18x14x7"]()
+    prec = ms.MS_PREC_FP64 if precision == "fp64" else ms.MS_PREC_MIXED
+    s, b, c = _fv_setup(ms, ctx, gm, prec)
+    q = gm.q_active()
+    p = np.zeros_like(q)
+    info = ms.ms_solve(ctx, s, [c], q, p, tol=1e-8, max_iter=500, precision=prec, outer=ms.MS_OUTER_GMRES)
+    sysr, Ap, qp, B, _, _ = _oracle_general(gm)
+    r = O.ms_gmres(Ap, [(B, O.coarse_fv(Ap, B))], qp, tol=1e-8, max_iter=500, restart=30)
+    assert info["converged"] and r.converged
+    assert abs(info["iters"] - r.iters) <= 1, (info["iters"], r.iters)
+    tol = 1e-6 if precision == "fp64" else 1e-5
+    assert np.linalg.norm(p - r.x) <= tol * np.linalg.norm(r.x)
+    ms.ms_coarse_release(c)
+    ms.ms_basis_release(b)
+    ms.ms_system_release(s)
+
+
+def test_fv_gauss_jordan_larger_coarse_system(ms, ctx):
+    """Several hundred coarse blocks (many rows per block of the cooperative
+    grid): FP64 cycle equals the oracle's LU-based cycle."""
+    gm = G.lognormal_box(60, 44, 10, seed=23, block=(4, 4, 2), kz_ratio=0.1)
+    s, b, c = _fv_setup(ms, ctx, gm, ms.MS_PREC_FP64)
+    sysr, Ap, qp, B, _, _ = _oracle_general(gm)
+    assert B.M > 700
+    q = gm.q_active()
+    p = np.zeros_like(q)
+    ms.ms_solve(ctx, s, [c], q, p, tol=1e-30, max_iter=1)
+    r = O.ms_solve(Ap, [(B, O.coarse_fv(Ap, B))], qp, tol=1e-30, max_iter=1)
+    assert np.linalg.norm(p - r.x) <= 1e-10 * np.linalg.norm(r.x)
+    ms.ms_coarse_release(c)
+    ms.ms_basis_release(b)
+    ms.ms_system_release(s)
+
+
+def test_well_partition_and_basis_match_oracle(ms, ctx):
+    """Well bases (Sec. 6.2): partition {each well's cells, the rest}, MsRSB on
+    hop supports, as a second stage beside the general one."""
+    gm = CASES["3d_10x10x4"]()
+    s = _system(ms, ctx, gm)
+    sysr, Ap, qp, B, Ac, L = _oracle_general(gm)
+    wells = [np.flatnonzero(qp > 0), np.flatnonzero(qp < 0)]
+    wells = [w for w in wells if len(w)]
+    part, M = ms.ms_partition_wells(ctx, s, wells)
+    rp, rM = O.partition_wells(Ap.n, wells)
+    assert M == rM and np.array_equal(part, rp)
+    with pytest.raises(ms.MsError):
+        ms.ms_partition_wells(ctx, s, [wells[0], wells[0][:1]])
+    bw, it = ms.ms_build_basis(ctx, s, part, M, support=ms.MS_SUPPORT_HOP)
+    sp, sc = O.support_hop(gm.grid, sysr.cells, sysr.A, part, M)
+    Bw = O.msrsb_basis(sysr.A, part, M, sp, sc)
+    cptr, cells, val = ms.ms_basis_get(ctx, bw)
+    assert np.array_equal(cptr, sp) and np.array_equal(cells, sc) and it == Bw.iters
+    np.testing.assert_allclose(val, Bw.pval, rtol=0, atol=1e-12)
+    pg, Mg = ms.ms_partition_cartesian(ctx, s, gm.block)
+    bg, _ = ms.ms_build_basis(ctx, s, pg, Mg, block=gm.block)
+    cg, cw = ms.ms_galerkin(ctx, s, bg), ms.ms_galerkin(ctx, s, bw)
+    q = gm.q_active()
+    p = np.zeros_like(q)
+    info = ms.ms_solve(ctx, s, [cg, cw], q, p, tol=1e-8, max_iter=3000)
+    r = O.ms_solve(Ap, [(B, L), (Bw, O.cholesky(O.galerkin(Ap, Bw)))], qp, tol=1e-8, max_iter=3000)
+    assert info["converged"] and r.converged and abs(info["iters"] - r.iters) <= 1
+    assert np.linalg.norm(p - r.x) <= 1e-6 * np.linalg.norm(r.x)
+    for h in (cg, cw):
+        ms.ms_coarse_release(h)
+    for h in (bg, bw):
+        ms.ms_basis_release(h)
+    ms.ms_system_release(s)
