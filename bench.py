@@ -55,14 +55,16 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-fv", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run N extra untimed steps only (for ncu launch lists)")
     ap.add_argument("--profile-ilu", type=int, default=0,
                     help="only assemble the c2 system and apply ILU(0) N times in each precision (for ncu captures)")
     ap.add_argument("--nz", type=int, default=85, help="--profile-ilu: layers of the 60x220 grid")
-    ap.add_argument("--workload", choices=["c2", "ensemble", "serving"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "ensemble", "serving", "coupling"], default="c2",
                     help="c2: the 60x220x85 geomodel (headline); ensemble: the batched uneven ensemble; "
-                         "serving: Poisson stream of two-phase time steps on resident geomodels")
+                         "serving: Poisson stream of two-phase time steps on resident geomodels; coupling: "
+                         "viscosity-ratio study of dynamic bases on a 42x22 field")
     ap.add_argument("--models", type=int, default=32, help="serving: resident geomodels")
     ap.add_argument("--requests", type=int, default=400, help="serving: requests in the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrival rate (requests/s)")
@@ -252,13 +254,14 @@ class Plan:
         self.n = ms.ms_system_get_info(self.sys)["n"]
         self.M = M
 
-    def step(self, perm=None, q=None, p=None, outer="gmres"):
+    def step(self, perm=None, q=None, p=None, outer="gmres", coarse=None):
         ms, ctx = self.ms, self.ctx
+        coarse = self.coarse if coarse is None else coarse
         ms.ms_assemble_tpfa(ctx, self.sys, self.perm if perm is None else perm)
         bit = ms.ms_basis_rebuild(ctx, self.sys, self.basis)
-        ms.ms_coarse_refresh(ctx, self.sys, self.coarse)
+        ms.ms_coarse_refresh(ctx, self.sys, coarse)
         o, m = OUTER[outer]
-        info = ms.ms_solve(ctx, self.sys, [self.coarse], self.q if q is None else q, self.p if p is None else p,
+        info = ms.ms_solve(ctx, self.sys, [coarse], self.q if q is None else q, self.p if p is None else p,
                            tol=1e-6, max_iter=5000, precision=self.prec, outer=o, restart=m)
         info["basis_iters"] = bit
         return info
@@ -269,13 +272,13 @@ class Plan:
         self.ms.ms_system_release(self.sys)
 
 
-def timed_steps(torch, plan, stream, K, dist, world, outer="gmres"):
+def timed_steps(torch, plan, stream, K, dist, world, outer="gmres", coarse=None):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    infos = [plan.step(outer=outer) for _ in range(K)]
+    infos = [plan.step(outer=outer, coarse=coarse) for _ in range(K)]
     e1.record(stream)
     torch.cuda.synchronize()
     ms_tot = e0.elapsed_time(e1)
@@ -573,6 +576,42 @@ def run_profile_ilu(args):
     return 0
 
 
+def run_coupling(args):
+    """Coupling-strength study (dynamic bases against the viscosity ratio):
+    average Richardson cycles per pressure solve for the general stage alone,
+    Dp(1) and Dp(Inf), 40 sequential two-phase steps per run."""
+    import torch
+    rank, world, local = dist_env()
+    if world > 1 and rank != 0:
+        return 0
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2001_01624_gb300 as ms
+    from paper_2001_01624_gb300 import coupling as CP
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    ctx = ms.ms_create(local, stream)
+    steps = 40
+    CP.study(ctx, ratios=(2.0,), steps=3)                      # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rows = CP.study(ctx, steps=steps)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    ms.ms_destroy(ctx)
+    solves = len(rows) * len(CP.SCHEDULES) * steps
+    line = {"metric": "pressure solves per second (coupling study, 42x22, Richardson to 1e-6)",
+            "value": solves / secs, "unit": "solves/s", "n_gpus": 1, "steps": steps, "warmup": 1,
+            "higher_is_better": True, "scaling": "replicas", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "coupling study: 42x22 lognormal (sigma 2, correlation 8 cells), 6x2 general "
+                                   "blocks, injector / producer columns, linear relative permeabilities, "
+                                   "1 PV in 40 steps; mu_w/mu_o in 1/50..50"},
+            "avg_cycles_per_solve": rows, "seconds": secs}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -583,6 +622,8 @@ def main():
         return run_ensemble(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "coupling":
+        return run_coupling(args)
     import torch
     import numpy as np
     rank, world, local = dist_env()
@@ -719,6 +760,34 @@ def main():
         pm = plans[ms.MS_PREC_MIXED].p.cpu().numpy()
         p64 = plans[ms.MS_PREC_FP64].p.cpu().numpy()
         line["mixed"]["rel_err_vs_fp64"] = float(np.linalg.norm(pm - p64) / np.linalg.norm(p64))
+
+    # finite-volume restriction (R sums each block's cells, Sec. 5) on the same
+    # basis: A_c = R A P inverted by Gauss-Jordan, GMRES(30), FP64
+    if not args.no_fv:
+        plan = plans[ms.MS_PREC_FP64]
+        cfv = ms.ms_coarse_create(ctx, plan.sys, plan.basis, ms.MS_PREC_FP64, ms.MS_RESTRICT_FV)
+        with torch.cuda.stream(stream):
+            plan.step(coarse=cfv)
+        kf = max(1, args.steps // 2)
+        f_ms, f_infos = timed_steps(torch, plan, stream, kf, dist, world, coarse=cfv)
+        ms.ms_profile_reset()
+        ms.ms_profile_enable(True)
+        plan.step(coarse=cfv)
+        torch.cuda.synchronize()
+        ms.ms_profile_enable(False)
+        pf = ms.ms_profile_read()
+        fi = f_infos[-1]
+
+        def per_launch(d, k):
+            v = d.get(k)
+            return None if not v or not v["timed_launches"] else v["total_ms"] / v["timed_launches"]
+        line["fv"] = {"value": n * kf * world / (f_ms * 1e-3), "unit": UNIT, "ms_per_step": f_ms / kf,
+                      "restriction": "finite volume (block sums)", "steps": fi["iters"],
+                      "solve_ms": fi["seconds"] * 1e3, "rel_residual": fi["rel_residual"],
+                      "gauss_jordan_ms": per_launch(pf, "coarse_gauss_jordan"),
+                      "cholesky_inverse_ms": per_launch(prof, "coarse_factor_inverse"),
+                      "restrict_ms": per_launch(pf, "restrict"), "restrict_galerkin_ms": per_launch(prof, "restrict")}
+        ms.ms_coarse_release(cfv)
 
     # end to end through the C ABI with pinned host buffers
     if not args.no_e2e:

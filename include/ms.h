@@ -317,6 +317,12 @@ ms_status ms_galerkin(ms_ctx *ctx, ms_system *sys, const ms_basis *basis, int32_
  * required, else FP64) with FP64 refinement, as for the Galerkin stage. */
 ms_status ms_coarse_create(ms_ctx *ctx, ms_system *sys, const ms_basis *basis, int32_t precision,
                            int32_t restriction, ms_coarse **out);
+/* Dense inverse X = A^{-1} by the Gauss-Jordan elimination with partial
+ * pivoting that inverts finite-volume coarse operators (FP64; A and X host
+ * arrays of M*M row-major doubles).  MS_ERR_COARSE_SINGULAR when a pivot
+ * column is zero.  For checking that kernel on arbitrary matrices; stages
+ * reach it through ms_coarse_create. */
+ms_status ms_dense_inverse(ms_ctx *ctx, int32_t M, const double *A, double *X);
 /* Recompute A_c and its factors in place from the basis and the current A. */
 ms_status ms_coarse_refresh(ms_ctx *ctx, ms_system *sys, ms_coarse *coarse);
 ms_status ms_coarse_release(ms_coarse *coarse);

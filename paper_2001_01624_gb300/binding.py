@@ -128,6 +128,7 @@ def lib():
         "ms_galerkin": ([_vp, _vp, _vp, _i32, P(_vp)], _i32),
         "ms_coarse_create": ([_vp, _vp, _vp, _i32, _i32, P(_vp)], _i32),
         "ms_partition_wells": ([_vp, _vp, _i32, _vp, _vp, _vp, P(_i32)], _i32),
+        "ms_dense_inverse": ([_vp, _i32, _vp, _vp], _i32),
         "ms_coarse_refresh": ([_vp, _vp, _vp], _i32),
         "ms_coarse_release": ([_vp], _i32),
         "ms_coarse_get": ([_vp, _vp, _vp, P(_i32)], _i32),
@@ -151,7 +152,7 @@ def exported_symbols() -> Sequence[str]:
     return ["ms_abi_version", "ms_status_string", "ms_last_error", "ms_create", "ms_destroy", "ms_set_stream",
             "ms_system_create", "ms_system_release", "ms_system_get_info", "ms_assemble_tpfa",
             "ms_system_get_matrix", "ms_spmv", "ms_ilu_apply", "ms_ilu_apply_noalloc", "ms_partition_cartesian", "ms_partition_components", "ms_partition_dynamic",
-            "ms_partition_wells", "ms_coarse_create",
+            "ms_partition_wells", "ms_coarse_create", "ms_dense_inverse",
             "ms_build_basis", "ms_basis_rebuild", "ms_basis_update", "ms_basis_release", "ms_basis_get_info",
             "ms_basis_get", "ms_add_adaptive_basis", "ms_galerkin", "ms_coarse_refresh", "ms_coarse_release",
             "ms_coarse_get", "ms_solve", "ms_solve_batch", "ms_total_mobility", "ms_transport_step", "ms_profile_enable", "ms_profile_reset", "ms_profile_read"]
@@ -376,6 +377,14 @@ def ms_coarse_create(ctx, sys, basis, precision=MS_PREC_FP64, restriction=MS_RES
     h = _vp()
     _check(lib().ms_coarse_create(ctx, sys, basis, precision, restriction, C.byref(h)), ctx)
     return h
+
+
+def ms_dense_inverse(ctx, A):
+    """A^{-1} by the finite-volume stages' Gauss-Jordan kernel (FP64)."""
+    A = np.ascontiguousarray(A, np.float64)
+    X = np.empty_like(A)
+    _check(lib().ms_dense_inverse(ctx, A.shape[0], _ptr(A), _ptr(X)), ctx)
+    return X
 
 
 def ms_coarse_refresh(ctx, sys, coarse):

@@ -42,7 +42,8 @@ template <typename T, int BM>
 __global__ void __launch_bounds__(kThreads) k_msrsb(int n, int W, int B, const int *__restrict__ col,
                                                     const T *__restrict__ off, const T *__restrict__ diag,
                                                     const int *__restrict__ pid, const T *__restrict__ pin,
-                                                    T *__restrict__ pout, T omega, unsigned long long *maxinc) {
+                                                    T *__restrict__ pout, const T *__restrict__ odiag,
+                                                    unsigned long long *maxinc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     T inc = 0;
     if (i < n) {
@@ -72,8 +73,9 @@ __global__ void __launch_bounds__(kThreads) k_msrsb(int n, int W, int B, const i
                 }
             }
         }
-        // one division each for omega / A_ii and for the partition-of-unity scale
-        const T od = omega / d;
+        // omega / A_ii precomputed per smoothing run; one division for the
+        // partition-of-unity scale
+        const T od = odiag[i];
         T sum = 0;
 #pragma unroll
         for (int s = 0; s < BM; ++s) {
@@ -87,8 +89,7 @@ __global__ void __launch_bounds__(kThreads) k_msrsb(int n, int W, int B, const i
         for (int s = 0; s < BM; ++s) {
             if (ids[s] != kSlotPad) {
                 const T nv = acc[s] * rs;
-                const T dv = nv > v[s] ? nv - v[s] : v[s] - nv;
-                inc = dv > inc ? dv : inc;
+                inc = fmax(inc, fabs(nv - v[s]));
                 pout[(int64_t)s * n + i] = nv;
             }
         }
@@ -149,8 +150,8 @@ __global__ void __launch_bounds__(kThreads) k_msrsb_mapped(int n, int W, const i
                                                            const T *__restrict__ off, const T *__restrict__ diag,
                                                            const unsigned *__restrict__ nmap,
                                                            const unsigned char *__restrict__ nslots,
-                                                           const T *__restrict__ pin, T *__restrict__ pout, T omega,
-                                                           unsigned long long *maxinc) {
+                                                           const T *__restrict__ pin, T *__restrict__ pout,
+                                                           const T *__restrict__ odiag, unsigned long long *maxinc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     T inc = 0;
     if (i < n) {
@@ -174,8 +175,9 @@ __global__ void __launch_bounds__(kThreads) k_msrsb_mapped(int n, int W, const i
                 if (s < cnt && t != 15u) acc[s] += a * pin[(int64_t)t * n + k];
             }
         }
-        // one division each for omega / A_ii and for the partition-of-unity scale
-        const T od = omega / d;
+        // omega / A_ii precomputed per smoothing run; one division for the
+        // partition-of-unity scale
+        const T od = odiag[i];
         T sum = 0;
 #pragma unroll
         for (int s = 0; s < 8; ++s)
@@ -188,8 +190,7 @@ __global__ void __launch_bounds__(kThreads) k_msrsb_mapped(int n, int W, const i
         for (int s = 0; s < 8; ++s)
             if (s < cnt) {
                 const T nv = acc[s] * rs;
-                const T dv = nv > v[s] ? nv - v[s] : v[s] - nv;
-                inc = dv > inc ? dv : inc;
+                inc = fmax(inc, fabs(nv - v[s]));
                 pout[(int64_t)s * n + i] = nv;
             }
     }
@@ -204,6 +205,12 @@ __global__ void __launch_bounds__(kThreads) k_msrsb_mapped(int n, int W, const i
         for (int q = 0; q < kThreads / 32; ++q) mm = fmax(mm, wmax[q]);
         atomic_max_nonneg(maxinc, mm);
     }
+}
+
+template <typename T>
+__global__ void k_omega_over_diag(int n, const T *__restrict__ diag, T omega, T *__restrict__ od) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) od[i] = omega / diag[i];
 }
 
 template <typename T>
@@ -325,6 +332,7 @@ __global__ void k_rap(int n, int M, int WAP, int nch, int C, const int *__restri
     __threadfence();
     for (int l = lane; l < M; l += 32) {
         double v = 0.0;
+#pragma unroll 4
         for (int q = q0; q < q0 + k; ++q) v += __ldcg(part + (int64_t)ch_slot[q] * M + l);
         Ac[(int64_t)j * M + l] = v;
     }
@@ -365,22 +373,22 @@ void launch_basis_init(ms_basis &b, int n, cudaStream_t st) {
 
 template <typename T>
 static void msrsb_dispatch(const ms_system &s, const ms_basis &b, const int *pid, const T *off, const T *diag,
-                           const T *pin, T *pout, T omega, unsigned long long *maxinc, cudaStream_t st) {
+                           const T *pin, T *pout, const T *omega, unsigned long long *maxinc, cudaStream_t st) {
     const int g = blocks_for(s.n);
     const int B = b.B;
     if (b.has_map) {
-        // A (unpinned) and the maps once, old slot values read once, new written
+        // A (unpinned), omega / A_ii and the maps once, old slot values read once, new written
         KernelScope ks_(st, sizeof(T) == 8 ? "msrsb" : "msrsb32",
-                        (double)s.n * (sizeof(T) + 1) + (double)s.W * s.n * (4 + sizeof(T) + 4) +
+                        (double)s.n * (2 * sizeof(T) + 1) + (double)s.W * s.n * (4 + sizeof(T) + 4) +
                             (double)b.nnz * 2 * sizeof(T));
         k_msrsb_mapped<T><<<g, kThreads, 0, st>>>(s.n, s.W, s.col.p, off, diag, b.nmap.p, b.nslots.p, pin, pout,
                                                   omega, maxinc);
         MS_CHECK_LAUNCH();
         return;
     }
-    // A (unpinned) once, slot ids and old values once, new values written
+    // A (unpinned) and omega / A_ii once, slot ids and old values once, new values written
     KernelScope ks_(st, sizeof(T) == 8 ? "msrsb" : "msrsb32",
-                    (double)s.n * sizeof(T) + (double)s.W * s.n * (4 + sizeof(T)) +
+                    (double)s.n * 2 * sizeof(T) + (double)s.W * s.n * (4 + sizeof(T)) +
                         (double)B * s.n * (4 + 2 * sizeof(T)));
     if (B <= 4) k_msrsb<T, 4><<<g, kThreads, 0, st>>>(s.n, s.W, B, s.col.p, off, diag, pid, pin, pout, omega, maxinc);
     else if (B <= 8) k_msrsb<T, 8><<<g, kThreads, 0, st>>>(s.n, s.W, B, s.col.p, off, diag, pid, pin, pout, omega, maxinc);
@@ -390,14 +398,28 @@ static void msrsb_dispatch(const ms_system &s, const ms_basis &b, const int *pid
     MS_CHECK_LAUNCH();
 }
 
+// omega / A_ii of the unpinned A for one smoothing run (A fixed during it).
+void launch_basis_scale(const ms_system &s, ms_basis &b, bool fp32, cudaStream_t st) {
+    const int g = blocks_for(s.n);
+    KernelScope ks_(st, "basis_scale", (double)s.n * (fp32 ? 8 : 16));
+    if (fp32) {
+        b.od32.alloc(s.n);
+        k_omega_over_diag<float><<<g, kThreads, 0, st>>>(s.n, s.diag32.p, (float)b.omega, b.od32.p);
+    } else {
+        b.od64.alloc(s.n);
+        k_omega_over_diag<double><<<g, kThreads, 0, st>>>(s.n, s.diag.p, b.omega, b.od64.p);
+    }
+    MS_CHECK_LAUNCH();
+}
+
 // One iteration; the new values end up in pval (buffers swapped).
 void launch_msrsb_iter(const ms_system &s, ms_basis &b, bool fp32, unsigned long long *maxinc, cudaStream_t st) {
     if (fp32) {
-        msrsb_dispatch<float>(s, b, b.pid.p, s.off_u32.p, s.diag32.p, b.pval32.p, b.pval32_tmp.p, (float)b.omega,
-                              maxinc, st);
+        msrsb_dispatch<float>(s, b, b.pid.p, s.off_u32.p, s.diag32.p, b.pval32.p, b.pval32_tmp.p, b.od32.p, maxinc,
+                              st);
         std::swap(b.pval32.p, b.pval32_tmp.p);
     } else {
-        msrsb_dispatch<double>(s, b, b.pid.p, s.off_u.p, s.diag.p, b.pval.p, b.pval_tmp.p, b.omega, maxinc, st);
+        msrsb_dispatch<double>(s, b, b.pid.p, s.off_u.p, s.diag.p, b.pval.p, b.pval_tmp.p, b.od64.p, maxinc, st);
         std::swap(b.pval.p, b.pval_tmp.p);
     }
 }

@@ -280,19 +280,24 @@ __global__ void k_d2f(int M, const double *a, float *b) {
 }
 
 // ------------------------------------------------- Gauss-Jordan inversion
-// In-place Gauss-Jordan elimination with row interchanges, A <- (Pi A)^{-1}
-// up to a column permutation.  Step k (all blocks, grid barrier between
-// phases):
-//   (a) reduce the per-block pivot candidates of column k to the pivot row p
-//       (largest |a_ik| over i >= k, lowest index on ties); copy row p to rowk
-//       and column k, with rows k and p exchanged, to colk;
-//   (b) scale the pivot row into row k, eliminate column k from every other
-//       row (row p receives the old row k), store the inverse's column k in
-//       place, and gather the per-block candidates of column k + 1.
+// Gauss-Jordan elimination with row interchanges (partial pivoting), one
+// cooperative launch, the matrix double-buffered: step k reads `cur` and
+// writes `nxt`, so no block overwrites what another still reads and one grid
+// barrier per step suffices.  Step k, every block:
+//   - reduces the per-block candidates of column k to the pivot row p (largest
+//     |a_ik| over i >= k, lowest index on ties);
+//   - for each of its rows i (block-cyclic), with src = the row that moves to
+//     i (rows k and p exchanged): the pivot row scaled by 1 / a_pk into row k;
+//     a_src,j - a_src,k a_pj / a_pk elsewhere; column k replaced by the
+//     inverse's column (1 / a_pk at row k, -a_src,k / a_pk elsewhere);
+//   - gathers its candidates of column k + 1 (double-buffered by parity).
+// Every read of data another block wrote goes through L2 (ld.global.cg).
 // The interchanges are undone on the columns afterwards (k_gj_order,
 // k_gj_gather).  A zero pivot column records kErrSingular and continues
 // with a zero reciprocal, so every block passes the same barriers.
 constexpr int kGJThreads = 512;
+constexpr int kGJRows = 8;     // rows of a block updated together (loads first)
+constexpr int kGJCols = 2;     // columns per thread and row in one pass
 
 __device__ __forceinline__ void gj_better(double &bv, int &bi, double v, int i) {
     if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
@@ -327,76 +332,86 @@ __device__ __forceinline__ void gj_block_best(double &bv, int &bi) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kGJThreads) k_gauss_jordan(int M, T *A, T *rowk, T *colk, double *cand_v,
-                                                             int *cand_i, int *piv, unsigned long long *bar,
-                                                             int *err) {
+__global__ void __launch_bounds__(kGJThreads, 1) k_gauss_jordan(int M, T *A0, T *A1, double *cand_v, int *cand_i,
+                                                                int *piv, unsigned long long *bar, int *err) {
     const int G = gridDim.x;
-    const int total = 2 * M;          // barriers in this launch
     GridSync gs;
     gs.begin(bar, err);
-    // candidates of column 0
+    // candidates of column 0 (parity 0)
     {
         double bv = -1.0;
         int bi = M;
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += G * blockDim.x)
-            gj_better(bv, bi, fabs((double)A[(int64_t)i * M]), i);
+            gj_better(bv, bi, fabs((double)__ldcg(&A0[(int64_t)i * M])), i);
         gj_block_best(bv, bi);
         if (threadIdx.x == 0) { cand_v[blockIdx.x] = bv; cand_i[blockIdx.x] = bi; }
     }
-    if (!gs.sync(total)) return;
+    if (!gs.sync(M)) return;
+    T *cur = A0, *nxt = A1;
     for (int k = 0; k < M; ++k) {
-        // (a) pivot row, copies of the pivot row and of column k
+        const int par = k & 1;
         double bv = -1.0;
         int bi = M;
-        for (int t = threadIdx.x; t < G; t += blockDim.x) gj_better(bv, bi, __ldcg(&cand_v[t]), __ldcg(&cand_i[t]));
+        for (int t = threadIdx.x; t < G; t += blockDim.x)
+            gj_better(bv, bi, __ldcg(&cand_v[par * G + t]), __ldcg(&cand_i[par * G + t]));
         gj_block_best(bv, bi);
         const bool ok = bv > 0.0 && bi < M;
         const int p = ok ? bi : k;
-        if (!ok && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, kErrSingular);
-        if (blockIdx.x == 0 && threadIdx.x == 0) piv[k] = p;
-        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 2 * M; t += G * blockDim.x) {
-            if (t < M) {
-                const int src = t == k ? p : (t == p ? k : t);
-                colk[t] = A[(int64_t)src * M + k];
-            } else {
-                rowk[t - M] = A[(int64_t)p * M + (t - M)];
-            }
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            piv[k] = p;
+            if (!ok) atomicOr(err, kErrSingular);
         }
-        if (!gs.sync(total)) return;
-        // (b) elimination
-        const T pv = __ldcg(&rowk[k]);
-        const T inv = ok ? T(1) / pv : T(0);
+        const T *prow = cur + (int64_t)p * M;
+        const T inv = ok ? T(1) / __ldcg(&prow[k]) : T(0);
         bv = -1.0;
         bi = M;
-        for (int i = blockIdx.x; i < M; i += G) {
-            if (i == p && p != k) continue;           // written with row k
-            T *a = A + (int64_t)i * M;
-            if (i == k) {
-                T *ap = A + (int64_t)p * M;
-                const T f = __ldcg(&colk[p]);         // old a_kk, for the row moved to p
-                for (int j = threadIdx.x; j < M; j += blockDim.x) {
-                    const T sc = j == k ? inv : __ldcg(&rowk[j]) * inv;
-                    if (p != k) {
-                        const T old = a[j];
-                        const T v = j == k ? -f * inv : old - f * sc;
-                        ap[j] = v;
-                        if (j == k + 1) gj_better(bv, bi, fabs((double)v), p);
-                    }
-                    a[j] = sc;
+        for (int i0 = blockIdx.x; i0 < M; i0 += kGJRows * G) {
+            int src[kGJRows];
+            T f[kGJRows];
+#pragma unroll
+            for (int r = 0; r < kGJRows; ++r) {
+                const int i = i0 + r * G;
+                src[r] = i < M ? (i == k ? p : (i == p ? k : i)) : -1;
+                f[r] = src[r] >= 0 ? __ldcg(&cur[(int64_t)src[r] * M + k]) : T(0);
+            }
+            for (int j0 = threadIdx.x; j0 < M; j0 += kGJCols * blockDim.x) {
+                T pr[kGJCols];
+                T v[kGJRows][kGJCols];
+#pragma unroll
+                for (int c = 0; c < kGJCols; ++c) {
+                    const int j = j0 + c * blockDim.x;
+                    pr[c] = j < M ? __ldcg(&prow[j]) : T(0);
+#pragma unroll
+                    for (int r = 0; r < kGJRows; ++r)
+                        v[r][c] = (j < M && src[r] >= 0) ? __ldcg(&cur[(int64_t)src[r] * M + j]) : T(0);
                 }
-            } else {
-                const T f = __ldcg(&colk[i]);
-                for (int j = threadIdx.x; j < M; j += blockDim.x) {
-                    const T v = j == k ? -f * inv : a[j] - f * (__ldcg(&rowk[j]) * inv);
-                    a[j] = v;
-                    if (j == k + 1 && i > k) gj_better(bv, bi, fabs((double)v), i);
+#pragma unroll
+                for (int c = 0; c < kGJCols; ++c) {
+                    const int j = j0 + c * blockDim.x;
+                    if (j >= M) continue;
+#pragma unroll
+                    for (int r = 0; r < kGJRows; ++r) {
+                        if (src[r] < 0) continue;
+                        const int i = i0 + r * G;
+                        T x;
+                        if (i == k) x = j == k ? inv : pr[c] * inv;
+                        else x = j == k ? -f[r] * inv : v[r][c] - f[r] * (pr[c] * inv);
+                        nxt[(int64_t)i * M + j] = x;
+                        if (j == k + 1 && i > k) gj_better(bv, bi, fabs((double)x), i);
+                    }
                 }
             }
         }
         if (k + 1 == M) break;
         gj_block_best(bv, bi);
-        if (threadIdx.x == 0) { cand_v[blockIdx.x] = bv; cand_i[blockIdx.x] = bi; }
-        if (!gs.sync(total)) return;
+        if (threadIdx.x == 0) {
+            cand_v[(par ^ 1) * G + blockIdx.x] = bv;
+            cand_i[(par ^ 1) * G + blockIdx.x] = bi;
+        }
+        if (!gs.sync(M)) return;
+        T *t = cur;
+        cur = nxt;
+        nxt = t;
     }
 }
 
@@ -421,8 +436,10 @@ __global__ void k_gj_gather(int M, const T *__restrict__ A, const int *__restric
     X[e] = A[(int64_t)r * M + idx[c]];
 }
 
+// X = A^{-1}; A0 holds A on entry and A1 is scratch of the same size (both
+// overwritten).
 template <typename T>
-void gauss_jordan_inverse(ms_coarse &c, T *A, T *X, T *vec, int *err, cudaStream_t st) {
+void gauss_jordan_inverse(ms_coarse &c, T *A0, T *A1, T *X, int *err, cudaStream_t st) {
     const int M = c.M;
     auto kern = k_gauss_jordan<T>;
     int per_sm = 0, sms = 0, dev = 0;
@@ -431,8 +448,8 @@ void gauss_jordan_inverse(ms_coarse &c, T *A, T *X, T *vec, int *err, cudaStream
     MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGJThreads, 0));
     MS_REQUIRE(per_sm >= 1, MS_ERR_CUDA, "Gauss-Jordan kernel cannot be resident");
     const int G = std::max(1, std::min(sms, M));
-    c.gj_cand_v.alloc(G);
-    c.gj_cand_i.alloc(G);
+    c.gj_cand_v.alloc(2 * G);
+    c.gj_cand_i.alloc(2 * G);
     c.gj_piv.alloc(M);
     c.gj_idx.alloc(M);
     if (c.gj_bar.n == 0) {
@@ -449,12 +466,11 @@ void gauss_jordan_inverse(ms_coarse &c, T *A, T *X, T *vec, int *err, cudaStream
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, M, A, vec, vec + M, c.gj_cand_v.p, c.gj_cand_i.p,
-                                             c.gj_piv.p, c.gj_bar.p, err);
-    MS_CUDA(e);
+    MS_CUDA(cudaLaunchKernelEx(&cfg, kern, M, A0, A1, c.gj_cand_v.p, c.gj_cand_i.p, c.gj_piv.p, c.gj_bar.p, err));
     k_gj_order<<<1, 32, 0, st>>>(M, c.gj_piv.p, c.gj_idx.p);
     const int64_t MM = (int64_t)M * M;
-    k_gj_gather<T><<<(int)((MM + 255) / 256), 256, 0, st>>>(M, A, c.gj_idx.p, X);
+    // step k writes A1 when k is even: the last step (k = M - 1) wrote A1 for odd M
+    k_gj_gather<T><<<(int)((MM + 255) / 256), 256, 0, st>>>(M, (M & 1) ? A1 : A0, c.gj_idx.p, X);
     MS_CHECK_LAUNCH();
 }
 
@@ -518,14 +534,14 @@ void dense_factor_inverse32(ms_coarse &c, int *err, cudaStream_t st) {
 }
 
 // Finite-volume stages: Gauss-Jordan with partial pivoting.  FP64: work64
-// holds the matrix being reduced and the pivot row / column copies.
+// holds the two buffers of the matrix being reduced.
 void dense_gj_inverse64(ms_coarse &c, int *err, cudaStream_t st) {
     const int M = c.M;
     const int64_t MM = (int64_t)M * M;
-    c.work64.alloc(MM + 2 * (int64_t)M);
+    c.work64.alloc(2 * MM);
     c.inv64.alloc(MM);
     MS_CUDA(cudaMemcpyAsync(c.work64.p, c.Ac.p, MM * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    gauss_jordan_inverse<double>(c, c.work64.p, c.inv64.p, c.work64.p + MM, err, st);
+    gauss_jordan_inverse<double>(c, c.work64.p, c.work64.p + MM, c.inv64.p, err, st);
 }
 
 // FP32: equilibrated as the Cholesky path (positive diagonal required; the
@@ -533,12 +549,12 @@ void dense_gj_inverse64(ms_coarse &c, int *err, cudaStream_t st) {
 void dense_gj_inverse32(ms_coarse &c, int *err, cudaStream_t st) {
     const int M = c.M;
     const int64_t MM = (int64_t)M * M;
-    c.work32.alloc(MM + 2 * (int64_t)M);
+    c.work32.alloc(2 * MM);
     c.inv32.alloc(MM);
     c.work64.alloc(M);   // scale vector
     k_equilibrate<<<(int)((MM + 255) / 256), 256, 0, st>>>(c.Ac.p, c.work32.p, c.work64.p, M);
     MS_CHECK_LAUNCH();
-    gauss_jordan_inverse<float>(c, c.work32.p, c.inv32.p, c.work32.p + MM, err, st);
+    gauss_jordan_inverse<float>(c, c.work32.p, c.work32.p + MM, c.inv32.p, err, st);
     k_unscale<<<(int)((MM + 255) / 256), 256, 0, st>>>(c.inv32.p, c.work64.p, M);
     MS_CHECK_LAUNCH();
 }

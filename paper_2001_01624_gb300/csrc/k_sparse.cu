@@ -56,6 +56,7 @@ __device__ __forceinline__ void finish_norm(double blk, double *red, unsigned in
     if (!last) return;
     __threadfence();
     double s = 0.0;
+#pragma unroll 8   // independent loads in flight; the sum order is unchanged
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(&red[b]);
     s = block_sum(s);
     if (threadIdx.x == 0) {
@@ -256,6 +257,7 @@ __global__ void k_restrict_ch(int nch, const int *__restrict__ ch_beg, const int
     if (atomicAdd(&cnt[j], 1u) == (unsigned)(k - 1)) {   // last chunk of column j
         __threadfence();
         ACC t = ACC(0);
+#pragma unroll 4
         for (int q = q0; q < q0 + k; ++q) t += (ACC)__ldcg(part + q);
         d[j] = (TD)t;
         cnt[j] = 0u;
@@ -389,6 +391,7 @@ __global__ void k_multidot(int n, int k, const double *__restrict__ V, const dou
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int i = wid; i < k; i += (int)(blockDim.x >> 5)) {
         double t = 0.0;
+#pragma unroll 8
         for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(&red[(int64_t)b * k + i]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
@@ -444,6 +447,7 @@ __global__ void __launch_bounds__(256) k_multidot8(int n, int k, const double *_
     __threadfence();
     if (wid < kk) {
         double t = 0.0;
+#pragma unroll 8   // independent loads in flight; the sum order is unchanged
         for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(&rg[(int64_t)b * 8 + wid]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
@@ -460,7 +464,15 @@ __global__ void k_multiaxpy(int n, int k, const double *__restrict__ V, const do
     __syncthreads();
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
         double a = y[l];
-        for (int i = 0; i < k; ++i) a += cs[i] * V[(int64_t)i * n + l];
+        int i = 0;
+        for (; i + 8 <= k; i += 8) {   // eight vectors' loads in flight, summed in order
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldcs(V + (int64_t)(i + u) * n + l);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a += cs[i + u] * v[u];
+        }
+        for (; i < k; ++i) a += cs[i] * V[(int64_t)i * n + l];
         y[l] = a;
     }
 }
@@ -485,7 +497,7 @@ void launch_multidot(int n, int k, const double *V, const double *w, double *red
 
 void launch_multiaxpy(int n, int k, const double *V, const double *c, double sign, double *y, cudaStream_t st) {
     KernelScope ks_(st, "krylov_axpy", (double)(k + 2) * n * 8);
-    k_multiaxpy<<<stride_grid(n), kThreads, 0, st>>>(n, k, V, c, sign, y);
+    k_multiaxpy<<<2 * stride_grid(n), kThreads, 0, st>>>(n, k, V, c, sign, y);
     MS_CHECK_LAUNCH();
 }
 

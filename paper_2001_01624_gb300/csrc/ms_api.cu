@@ -165,6 +165,7 @@ int smooth_basis(ms_ctx *ctx, ms_system &s, ms_basis &b, bool reset, double tol,
         const bool fp32 = b.precision == MS_PREC_MIXED;
         s.w_max.alloc(1);
         unsigned long long *h = (unsigned long long *)ctx->pinned.get(64);
+        if (max_iter > 0) launch_basis_scale(s, b, fp32, st);
         while (it < max_iter) {
             MS_CUDA(cudaMemsetAsync(s.w_max.p, 0, sizeof(unsigned long long), st));
             launch_msrsb_iter(s, b, fp32, s.w_max.p, st);
@@ -742,6 +743,28 @@ ms_status ms_coarse_create(ms_ctx *ctx, ms_system *s, const ms_basis *b, int32_t
     MS_REQUIRE(restriction == MS_RESTRICT_GALERKIN || restriction == MS_RESTRICT_FV, MS_ERR_INVALID_ARG,
                "unknown restriction");
     *out = create_coarse(ctx, *s, *b, precision, restriction);
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_dense_inverse(ms_ctx *ctx, int32_t M, const double *A, double *X) {
+    if (!ctx || !A || !X || M <= 0) return fail(ctx, MS_ERR_INVALID_ARG, "null argument or M <= 0");
+    API_TRY
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const size_t MM = (size_t)M * M;
+    ms_coarse c;
+    c.M = M;
+    c.restriction = MS_RESTRICT_FV;
+    c.Ac.alloc(MM);
+    MS_CUDA(cudaMemcpyAsync(c.Ac.p, A, MM * sizeof(double), cudaMemcpyHostToDevice, st));
+    DBuf<int> err;
+    err.alloc(1);
+    err.zero(st);
+    dense_gj_inverse64(c, err.p, st);
+    coarse_error(ctx, c, read_error_word(ctx, err.p));
+    MS_CUDA(cudaMemcpyAsync(X, c.inv64.p, MM * sizeof(double), cudaMemcpyDeviceToHost, st));
+    sync(st);
     return MS_OK;
     API_CATCH(ctx)
 }

@@ -260,6 +260,8 @@ struct ms_basis {
     msgb::DBuf<int> pid;
     msgb::DBuf<double> pval, pval_tmp;
     msgb::DBuf<float> pval32, pval32_tmp;
+    msgb::DBuf<double> od64;             // omega / A_ii for the current smoothing run
+    msgb::DBuf<float> od32;
     // column view (CSC)
     msgb::DBuf<int> cptr, ccell, csrc;
     msgb::DBuf<double> cval;
@@ -414,6 +416,7 @@ void launch_ilu_lines32f(ms_system &s, const float *r, float *y, float *z, cudaS
 // basis
 void launch_basis_init(ms_basis &b, int n, cudaStream_t st);
 void launch_basis_maps(const ms_system &s, ms_basis &b, cudaStream_t st);
+void launch_basis_scale(const ms_system &s, ms_basis &b, bool fp32, cudaStream_t st);
 void launch_msrsb_iter(const ms_system &s, ms_basis &b, bool fp32, unsigned long long *maxinc, cudaStream_t st);
 void launch_basis_columns(ms_basis &b, cudaStream_t st);
 // Galerkin

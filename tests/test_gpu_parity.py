@@ -701,3 +701,41 @@ def test_well_partition_and_basis_match_oracle(ms, ctx):
     for h in (bg, bw):
         ms.ms_basis_release(h)
     ms.ms_system_release(s)
+
+
+@pytest.mark.parametrize("M", [1, 2, 5, 37, 152, 153, 700, 1300])
+def test_gauss_jordan_inverse_with_pivoting(ms, ctx, M):
+    """The Gauss-Jordan kernel on matrices that need row interchanges: a zero
+    leading entry and a scaled permutation matrix (an interchange at nearly
+    every step), against the oracle's LU solves and X A = I; sizes below,
+    at and above one row per block of the cooperative grid, several rows per
+    block and a ragged last batch."""
+    rng = np.random.default_rng(M)
+    A = rng.standard_normal((M, M))
+    A[0, 0] = 0.0 if M > 1 else A[0, 0]
+    X = ms.ms_dense_inverse(ctx, A)
+    LU, piv = O.lu(A)
+    E = np.eye(M)
+    ks = range(M) if M <= 160 else rng.choice(M, 40, replace=False)
+    cond = np.linalg.cond(A)
+    for j in ks:
+        xr = O.lu_solve(LU, piv, E[:, j])
+        assert np.linalg.norm(X[:, j] - xr) <= 1e-13 * cond * np.linalg.norm(xr)
+    assert np.abs(X @ A - E).max() <= 1e-13 * cond
+    perm = rng.permutation(M)
+    d = rng.uniform(1.0, 4.0, M)
+    Pm = np.zeros((M, M))
+    Pm[np.arange(M), perm] = d
+    Xp = ms.ms_dense_inverse(ctx, Pm)
+    ref = np.zeros((M, M))
+    ref[perm, np.arange(M)] = 1.0 / d
+    np.testing.assert_allclose(Xp, ref, rtol=1e-15, atol=0)
+
+
+def test_gauss_jordan_singular_is_reported(ms, ctx):
+    A = np.ones((6, 6))
+    with pytest.raises(ms.MsError) as e:
+        ms.ms_dense_inverse(ctx, A)
+    assert e.value.status == ms.MS_ERR_COARSE_SINGULAR
+    X = ms.ms_dense_inverse(ctx, np.eye(6) * 2.0)      # the context and barrier stay usable
+    np.testing.assert_array_equal(X, np.eye(6) * 0.5)
