@@ -34,6 +34,12 @@ galerkin_fv            Sec. 5, finite-volume restriction R         A_c 1 = 0 and
                                                                    between blocks (closed form)
 lu(_solve)             coarse solve, Gaussian elimination          P A = L U; a zero leading pivot; numpy solve
 partition_wells        Sec. 6.2 well bases                         hand-worked blocks; repeated cell rejected
+cpr_residual /         Sec. 4 quasi-IMPES decoupling of a          Jacobian blocks against central finite
+cpr_pressure           compressible two-phase step                 differences of cpr_residual; fluxes cancel in
+                                                                   the sums over cells; weights cancel the
+                                                                   saturation diagonal and sum to one;
+                                                                   incompressible, equal densities, uniform
+                                                                   state: J* = lambda_t A_tpfa / 2 (closed form)
 ms_solve (FV stage)    Eq. (11) with R = block indicator           after a cycle ending in an FV coarse
                                                                    correction every block's residual sums to
                                                                    zero (local conservation); dense direct solve
@@ -128,6 +134,10 @@ def lib():
         L.or_lu_solve.argtypes = [_i, _vp, _vp, _vp, _vp]
         L.or_lu_solve.restype = None
         L.or_partition_wells.argtypes = [_i, _i, _vp, _vp, _vp, _pi]
+        L.or_cpr_residual.argtypes = [_i, _i, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp]
+        L.or_cpr_residual.restype = None
+        L.or_cpr_pressure.argtypes = [_i, _vp, _vp, _i, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d,
+                                      _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.or_ilu0.argtypes = [_i, _vp, _vp, _vp, _vp]
         L.or_ilu0_apply.argtypes = [_i, _vp, _vp, _vp, _vp, _vp]
         L.or_ilu0_apply.restype = None
@@ -404,7 +414,23 @@ def partition_wells(n: int, wells: Sequence[Sequence[int]]):
     return part, M.value
 
 
+@dataclass
+class LUFactor:
+    """Galerkin stage of a non-symmetric A: LU factors of P^T A P."""
+    LU: np.ndarray
+    piv: np.ndarray
+
+
+def coarse_lu(A: CSR, B: Basis) -> LUFactor:
+    LU, piv = lu(galerkin(A, B))
+    return LUFactor(LU, piv)
+
+
 def _stage_struct(B, Lc, keep):
+    if isinstance(Lc, LUFactor):
+        LU, piv = _f64(Lc.LU), _i32(Lc.piv)
+        keep += [B, LU, piv]
+        return _Stage(B.M, _p(B.sptr), _p(B.scells), _p(B.pval), _p(LU), None, _p(piv))
     if isinstance(Lc, FVFactor):
         LU, piv, part = _f64(Lc.LU), _i32(Lc.piv), _i32(Lc.part)
         keep += [B, LU, piv, part]
@@ -541,6 +567,49 @@ def transport_step(A_unpinned: CSR, p, q, S, dt, fluid=None, porosity=0.2, volum
     if st != OK:
         raise OracleError(st, "transport_step")
     return S, k.value
+
+
+CPR_DEFAULT = dict(mu_w=1e-3, mu_o=3e-3, n_w=2.0, n_o=2.0, s_wc=0.0, s_or=0.0, phi0=0.2, rho_w0=1000.0,
+                   rho_o0=800.0, c_w=4.5e-10, c_o=1.5e-9, c_r=5e-10, p_ref=2e7)
+
+
+def _cpr_params(params):
+    d = dict(CPR_DEFAULT)
+    d.update(params or {})
+    return np.array([d[k] for k in ("mu_w", "mu_o", "n_w", "n_o", "s_wc", "s_or", "phi0", "rho_w0", "rho_o0",
+                                    "c_w", "c_o", "c_r", "p_ref")])
+
+
+def cpr_residual(sysm: System, vol, p, s, p0, s0, qw, qo, dt, params=None):
+    """(R_w, R_o) of the compressible two-phase step (Sec. 4 reading)."""
+    fa, fb, T = sysm.faces
+    cp = _cpr_params(params)
+    n = sysm.A.n
+    Rw, Ro = np.empty(n), np.empty(n)
+    args = [_f64(x) for x in (p, s, p0, s0, qw, qo)]
+    lib().or_cpr_residual(n, len(fa), _p(_i32(fa)), _p(_i32(fb)), _p(_f64(T)), float(vol), _p(cp),
+                          *[_p(a) for a in args], float(dt), _p(Rw), _p(Ro))
+    return Rw, Ro
+
+
+def cpr_pressure(sysm: System, vol, p, s, p0, s0, qw, qo, dt, params=None) -> dict:
+    """Jacobian blocks, quasi-IMPES weights and the CPR pressure system
+    (Sec. 4): dict(Jwp, Jop, Jstar as CSR on A's pattern; Dws, Dos, Rw, Ro,
+    ww, wo, rstar as vectors)."""
+    A = sysm.A
+    fa, fb, T = sysm.faces
+    cp = _cpr_params(params)
+    n, nnz = A.n, len(A.val)
+    out = {k: np.empty(nnz) for k in ("Jwp", "Jop", "Jstar")}
+    out.update({k: np.empty(n) for k in ("Dws", "Dos", "Rw", "Ro", "ww", "wo", "rstar")})
+    args = [_f64(x) for x in (p, s, p0, s0, qw, qo)]
+    _check(lib().or_cpr_pressure(n, _p(A.rowptr), _p(A.col), len(fa), _p(_i32(fa)), _p(_i32(fb)), _p(_f64(T)),
+                                 float(vol), _p(cp), *[_p(a) for a in args], float(dt),
+                                 *[_p(out[k]) for k in ("Jwp", "Jop", "Dws", "Dos", "Rw", "Ro", "ww", "wo",
+                                                        "Jstar", "rstar")]), "cpr_pressure")
+    for k in ("Jwp", "Jop", "Jstar"):
+        out[k] = CSR(n, A.rowptr, A.col, out[k])
+    return out
 
 
 def cost_model(N, Np, d, b, Nc):

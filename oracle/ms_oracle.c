@@ -867,9 +867,9 @@ typedef struct {
     const int *sptr;
     const int *scells;
     const double *pval;
-    const double *L;     /* Galerkin: Cholesky factor of A_c; finite volume: or_lu factors (M x M row-major) */
+    const double *L;     /* Cholesky factor of A_c, or or_lu factors when piv is set (M x M row-major) */
     const int *part;     /* finite volume: block of each cell (restriction R = block indicator); NULL: R = P^T */
-    const int *piv;      /* finite volume: or_lu interchanges */
+    const int *piv;      /* or_lu interchanges (finite volume, or a non-symmetric Galerkin A_c); NULL: Cholesky */
 } or_stage;
 
 typedef struct {
@@ -952,7 +952,8 @@ static void coarse_correction(int n, const int *rp, const int *ci, const double 
             for (int e = sptr[j]; e < sptr[j + 1]; ++e) s += pval[e] * r[scells[e]];
             d[j] = s;
         }
-        or_cholesky_solve(M, L, d, xc);
+        if (piv) or_lu_solve(M, L, piv, d, xc);        /* non-symmetric A (Galerkin, LU factors) */
+        else or_cholesky_solve(M, L, d, xc);
     }
     for (int j = 0; j < M; ++j)                          /* x += P xc */
         for (int e = sptr[j]; e < sptr[j + 1]; ++e) x[scells[e]] += pval[e] * xc[j];
@@ -1227,6 +1228,116 @@ int or_transport_step(int n, const int *rowptr, const int *col, const double *va
     }
     free(Sn);
     *nsub_out = k;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* CPR pressure stage (Sec. 4, quasi-IMPES decoupling; Fig. 3 predictor)    */
+/* for a compressible two-phase (water / oil) system, one fully implicit     */
+/* time step with primary variables p (Pa) and s = s_w per cell.  Readings:  */
+/*   rho_a(p) = rho_a0 exp(c_a (p - p_ref)), phi(p) = phi0 exp(c_r (p - p_ref)); */
+/*   lambda_a = kr_a(s) / mu_a with the Corey curves above;                   */
+/*   R_a,i = V/dt [phi rho_a s_a - (phi rho_a s_a)^0] + sum_j F_a,ij - q_a,i,  */
+/*   F_a,ij = T_ij (lambda_a rho_a)(up) (p_i - p_j), up = the cell with the   */
+/*   higher pressure (the lower index on a tie); q_a fixed mass rates.        */
+/* cp = (mu_w, mu_o, n_w, n_o, s_wc, s_or, phi0, rho_w0, rho_o0, c_w, c_o,    */
+/*       c_r, p_ref).                                                         */
+/* ------------------------------------------------------------------------ */
+static void cpr_mob(const double *cp, double s, double *lw, double *lo, double *dlw, double *dlo) {
+    const double d = 1.0 - cp[4] - cp[5];
+    const double x = (s - cp[4]) / d;
+    double se = x, dse = 1.0 / d;
+    if (x < 0.0) { se = 0.0; dse = 0.0; }          /* clipped: constant mobility */
+    else if (x > 1.0) { se = 1.0; dse = 0.0; }
+    *lw = pow(se, cp[2]) / cp[0];
+    *lo = pow(1.0 - se, cp[3]) / cp[1];
+    *dlw = cp[2] * pow(se, cp[2] - 1.0) * dse / cp[0];
+    *dlo = -cp[3] * pow(1.0 - se, cp[3] - 1.0) * dse / cp[1];
+}
+
+static int cpr_upstream(int a, int b, const double *p) {
+    if (p[a] > p[b]) return a;
+    if (p[b] > p[a]) return b;
+    return a < b ? a : b;
+}
+
+/* Residuals R_w, R_o (mass per time). */
+void or_cpr_residual(int n, int nf, const int *fa, const int *fb, const double *T, double vol, const double *cp,
+                     const double *p, const double *s, const double *p0, const double *s0, const double *qw,
+                     const double *qo, double dt, double *Rw, double *Ro) {
+    const double phi0 = cp[6], rw0 = cp[7], ro0 = cp[8], cw = cp[9], co = cp[10], cr = cp[11], pr = cp[12];
+    for (int i = 0; i < n; ++i) {
+        const double ph = phi0 * exp(cr * (p[i] - pr)), ph0 = phi0 * exp(cr * (p0[i] - pr));
+        const double rw = rw0 * exp(cw * (p[i] - pr)), rwo = rw0 * exp(cw * (p0[i] - pr));
+        const double ro = ro0 * exp(co * (p[i] - pr)), roo = ro0 * exp(co * (p0[i] - pr));
+        Rw[i] = vol / dt * (ph * rw * s[i] - ph0 * rwo * s0[i]) - qw[i];
+        Ro[i] = vol / dt * (ph * ro * (1.0 - s[i]) - ph0 * roo * (1.0 - s0[i])) - qo[i];
+    }
+    for (int f = 0; f < nf; ++f) {
+        const int a = fa[f], b = fb[f], u = cpr_upstream(a, b, p);
+        double lw, lo, dlw, dlo;
+        cpr_mob(cp, s[u], &lw, &lo, &dlw, &dlo);
+        const double dp = p[a] - p[b];
+        const double Fw = T[f] * lw * rw0 * exp(cw * (p[u] - pr)) * dp;
+        const double Fo = T[f] * lo * ro0 * exp(co * (p[u] - pr)) * dp;
+        Rw[a] += Fw; Rw[b] -= Fw;
+        Ro[a] += Fo; Ro[b] -= Fo;
+    }
+}
+
+/* Jacobian blocks on A's CSR pattern: Jwp = dR_w/dp, Jop = dR_o/dp (full),  */
+/* Dws, Dos = the diagonals of dR_w/ds, dR_o/ds; quasi-IMPES weights          */
+/* w_w D_ws + w_o D_os = 0, w_w + w_o = 1 per cell; pressure system          */
+/* Jstar = W_w Jwp + W_o Jop and rstar = W_w R_w + W_o R_o.                   */
+int or_cpr_pressure(int n, const int *rowptr, const int *col, int nf, const int *fa, const int *fb,
+                    const double *T, double vol, const double *cp, const double *p, const double *s,
+                    const double *p0, const double *s0, const double *qw, const double *qo, double dt,
+                    double *Jwp, double *Jop, double *Dws, double *Dos, double *Rw, double *Ro, double *ww,
+                    double *wo, double *Jstar, double *rstar) {
+    const double phi0 = cp[6], rw0 = cp[7], ro0 = cp[8], cw = cp[9], co = cp[10], cr = cp[11], pr = cp[12];
+    const int nnz = rowptr[n];
+    for (int e = 0; e < nnz; ++e) { Jwp[e] = 0.0; Jop[e] = 0.0; }
+    or_cpr_residual(n, nf, fa, fb, T, vol, cp, p, s, p0, s0, qw, qo, dt, Rw, Ro);
+    for (int i = 0; i < n; ++i) {                       /* accumulation */
+        const double ph = phi0 * exp(cr * (p[i] - pr));
+        const double rw = rw0 * exp(cw * (p[i] - pr)), ro = ro0 * exp(co * (p[i] - pr));
+        const int d = diag_pos(rowptr, col, i);
+        if (d < 0) return OR_EINVAL;
+        Jwp[d] += vol / dt * ph * rw * (cr + cw) * s[i];
+        Jop[d] += vol / dt * ph * ro * (cr + co) * (1.0 - s[i]);
+        Dws[i] = vol / dt * ph * rw;
+        Dos[i] = -vol / dt * ph * ro;
+    }
+    for (int f = 0; f < nf; ++f) {                      /* fluxes: +F in row a, -F in row b */
+        const int a = fa[f], b = fb[f], u = cpr_upstream(a, b, p);
+        double lw, lo, dlw, dlo;
+        cpr_mob(cp, s[u], &lw, &lo, &dlw, &dlo);
+        const double dp = p[a] - p[b];
+        const double rwu = rw0 * exp(cw * (p[u] - pr)), rou = ro0 * exp(co * (p[u] - pr));
+        const double gw = T[f] * lw * rwu, go = T[f] * lo * rou;
+        /* dF/dp_a, dF/dp_b (the density of the upstream cell moves with its pressure) */
+        const double wa = gw + (u == a ? dp * T[f] * lw * cw * rwu : 0.0);
+        const double wb = -gw + (u == b ? dp * T[f] * lw * cw * rwu : 0.0);
+        const double oa = go + (u == a ? dp * T[f] * lo * co * rou : 0.0);
+        const double ob = -go + (u == b ? dp * T[f] * lo * co * rou : 0.0);
+        const int aa = find_col(col, rowptr[a], rowptr[a + 1], a), ab = find_col(col, rowptr[a], rowptr[a + 1], b);
+        const int bb = find_col(col, rowptr[b], rowptr[b + 1], b), ba = find_col(col, rowptr[b], rowptr[b + 1], a);
+        if (aa < 0 || ab < 0 || bb < 0 || ba < 0) return OR_EINVAL;
+        Jwp[aa] += wa; Jwp[ab] += wb; Jwp[ba] -= wa; Jwp[bb] -= wb;
+        Jop[aa] += oa; Jop[ab] += ob; Jop[ba] -= oa; Jop[bb] -= ob;
+        /* dF/ds of the upstream cell, on its own row only */
+        const double sw = dp * T[f] * dlw * rwu, so = dp * T[f] * dlo * rou;
+        if (u == a) { Dws[a] += sw; Dos[a] += so; }
+        else { Dws[b] -= sw; Dos[b] -= so; }
+    }
+    for (int i = 0; i < n; ++i) {
+        const double den = Dos[i] - Dws[i];
+        if (!(den != 0.0)) return OR_ESINGULAR;
+        ww[i] = Dos[i] / den;
+        wo[i] = -Dws[i] / den;
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) Jstar[e] = ww[i] * Jwp[e] + wo[i] * Jop[e];
+        rstar[i] = ww[i] * Rw[i] + wo[i] * Ro[i];
+    }
     return OR_OK;
 }
 

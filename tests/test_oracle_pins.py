@@ -652,3 +652,103 @@ def test_well_basis_stage_converges_to_direct():
     assert r.converged
     x = _dense_pinned_solve(Ap, qp)
     assert np.linalg.norm(r.x - x) <= 1e-8 * np.linalg.norm(x)
+
+
+# ----------------------------------------------------------------------------- CPR pressure stage (Sec. 4)
+def _cpr_case(seed=0, faulted=True):
+    gm = (G.faulted(12, 10, 4, seed=seed, n_fault_x=1, n_fault_y=1, block=(4, 5, 2)) if faulted
+          else G.lognormal_box(9, 7, 3, seed=seed, block=(3, 7, 3), kz_ratio=0.1))
+    sysm = O.assemble_tpfa(gm.grid, gm.perm)
+    n = sysm.A.n
+    rng = np.random.default_rng(seed + 100)
+    p = 2e7 + 1e6 * rng.standard_normal(n)
+    s = rng.uniform(0.15, 0.85, n)
+    p0 = p - 1e5 * rng.uniform(0.0, 1.0, n)
+    s0 = np.clip(s - 0.05 * rng.uniform(0, 1, n), 0.0, 1.0)
+    qw = np.zeros(n); qo = np.zeros(n)
+    qw[0], qo[n - 1], qw[n - 1] = 0.5, -0.4, -0.1
+    g = gm.grid
+    return gm, sysm, g.dx * g.dy * g.dz, p, s, p0, s0, qw, qo, 86400.0
+
+
+def test_cpr_jacobian_matches_finite_differences():
+    gm, sysm, vol, p, s, p0, s0, qw, qo, dt = _cpr_case()
+    fa, fb, _ = sysm.faces
+    gap = np.abs(p[fa] - p[fb]).min()
+    hp = 1e-3 * gap
+    assert hp > 1e-4                                # no upstream direction changes under the perturbation
+    out = O.cpr_pressure(sysm, vol, p, s, p0, s0, qw, qo, dt)
+    Jw, Jo = out["Jwp"].dense(), out["Jop"].dense()
+    n = sysm.A.n
+    fdw, fdo = np.zeros((n, n)), np.zeros((n, n))
+    for k in range(n):
+        e = np.zeros(n); e[k] = hp
+        rwp, rop = O.cpr_residual(sysm, vol, p + e, s, p0, s0, qw, qo, dt)
+        rwm, rom = O.cpr_residual(sysm, vol, p - e, s, p0, s0, qw, qo, dt)
+        fdw[:, k] = (rwp - rwm) / (2 * hp)
+        fdo[:, k] = (rop - rom) / (2 * hp)
+    np.testing.assert_allclose(Jw, fdw, rtol=0, atol=1e-6 * np.abs(Jw).max())
+    np.testing.assert_allclose(Jo, fdo, rtol=0, atol=1e-6 * np.abs(Jo).max())
+    hs = 1e-6
+    dsw, dso = np.zeros(n), np.zeros(n)
+    for k in range(n):
+        e = np.zeros(n); e[k] = hs
+        rwp, rop = O.cpr_residual(sysm, vol, p, s + e, p0, s0, qw, qo, dt)
+        rwm, rom = O.cpr_residual(sysm, vol, p, s - e, p0, s0, qw, qo, dt)
+        dsw[k] = (rwp[k] - rwm[k]) / (2 * hs)
+        dso[k] = (rop[k] - rom[k]) / (2 * hs)
+    np.testing.assert_allclose(out["Dws"], dsw, rtol=1e-6, atol=1e-9 * np.abs(dsw).max())
+    np.testing.assert_allclose(out["Dos"], dso, rtol=1e-6, atol=1e-9 * np.abs(dso).max())
+
+
+def test_cpr_fluxes_cancel_and_weights_decouple():
+    gm, sysm, vol, p, s, p0, s0, qw, qo, dt = _cpr_case(seed=4)
+    out = O.cpr_pressure(sysm, vol, p, s, p0, s0, qw, qo, dt)
+    # fluxes cancel over the whole grid: sum_i R_a,i = accumulation - sources
+    cp = O.CPR_DEFAULT
+    e = lambda x: np.exp(x)
+    ph, ph0 = cp["phi0"] * e(cp["c_r"] * (p - cp["p_ref"])), cp["phi0"] * e(cp["c_r"] * (p0 - cp["p_ref"]))
+    rw, rw0 = cp["rho_w0"] * e(cp["c_w"] * (p - cp["p_ref"])), cp["rho_w0"] * e(cp["c_w"] * (p0 - cp["p_ref"]))
+    accw = vol / dt * (ph * rw * s - ph0 * rw0 * s0)
+    assert abs(out["Rw"].sum() - (accw.sum() - qw.sum())) <= 1e-9 * np.abs(out["Rw"]).sum()
+    # and so do their pressure derivatives: column sums of J_wp are the accumulation derivatives
+    Jw = out["Jwp"].dense()
+    np.testing.assert_allclose(Jw.sum(0), vol / dt * ph * rw * (cp["c_r"] + cp["c_w"]) * s,
+                               rtol=0, atol=1e-9 * np.abs(Jw).max())
+    # quasi-IMPES: the weighted saturation diagonal vanishes and the weights sum to one
+    np.testing.assert_allclose(out["ww"] + out["wo"], 1.0, rtol=1e-14)
+    assert np.abs(out["ww"] * out["Dws"] + out["wo"] * out["Dos"]).max() <= 1e-12 * np.abs(out["Dws"]).max()
+    np.testing.assert_allclose(out["rstar"], out["ww"] * out["Rw"] + out["wo"] * out["Ro"], rtol=1e-14)
+
+
+def test_cpr_incompressible_limit_is_half_total_mobility_tpfa():
+    """No compressibility, unit densities, uniform pressure and saturation:
+    the saturation diagonals are +-V phi / dt, the weights 1/2, and J* is
+    half the TPFA matrix with the total mobility."""
+    gm, sysm, vol, p, s, p0, s0, qw, qo, dt = _cpr_case(seed=2)
+    n = sysm.A.n
+    params = dict(c_w=0.0, c_o=0.0, c_r=0.0, rho_w0=1.0, rho_o0=1.0)
+    pu, su = np.full(n, 2e7), np.full(n, 0.4)
+    out = O.cpr_pressure(sysm, vol, pu, su, pu, su, np.zeros(n), np.zeros(n), dt, params)
+    np.testing.assert_allclose(out["ww"], 0.5, rtol=1e-14)
+    lam_t = O.total_mobility(np.array([0.4]), dict(mu_w=1e-3, mu_o=3e-3))[0]
+    A = sysm.A.dense()
+    np.testing.assert_allclose(out["Jstar"].dense(), 0.5 * lam_t * A, rtol=0, atol=1e-13 * lam_t * np.abs(A).max())
+    assert np.abs(out["rstar"]).max() == 0.0
+
+
+def test_cpr_predictor_solve_matches_direct():
+    """The pressure stage of CPR: J* dp = -r* by GMRES with the multistage
+    cycle (Galerkin stage of the non-symmetric J*, LU coarse solve)."""
+    gm, sysm, vol, p, s, p0, s0, qw, qo, dt = _cpr_case(seed=6)
+    out = O.cpr_pressure(sysm, vol, p, s, p0, s0, qw, qo, dt)
+    J = out["Jstar"]
+    part, M = O.partition_cartesian(gm.grid, sysm.cells, gm.block)
+    sp, sc = O.support_box(gm.grid, sysm.cells, sysm.A, part, M, gm.block)
+    B = O.msrsb_basis(sysm.A, part, M, sp, sc)
+    F = O.coarse_lu(J, B)
+    rhs = -out["rstar"]
+    r = O.ms_gmres(J, [(B, F)], rhs, tol=1e-11, max_iter=500, restart=30)
+    assert r.converged
+    x = np.linalg.solve(J.dense(), rhs)
+    assert np.linalg.norm(r.x - x) <= 1e-8 * np.linalg.norm(x)
