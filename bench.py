@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-fv", action="store_true")
+    ap.add_argument("--no-cpr", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run N extra untimed steps only (for ncu launch lists)")
     ap.add_argument("--profile-ilu", type=int, default=0,
@@ -788,6 +789,61 @@ def main():
                       "cholesky_inverse_ms": per_launch(prof, "coarse_factor_inverse"),
                       "restrict_ms": per_launch(pf, "restrict"), "restrict_galerkin_ms": per_launch(prof, "restrict")}
         ms.ms_coarse_release(cfv)
+
+    # CPR pressure stage (Sec. 4 quasi-IMPES) of a compressible two-phase step on the same grid and basis:
+    # J* and r* from the per-cell state, Galerkin stage of the non-symmetric J* (Gauss-Jordan inverse),
+    # GMRES(30) predictor solve to 1e-6
+    if not args.no_cpr:
+        plan = plans[ms.MS_PREC_FP64]
+        pn = plan.p / torch.clamp(plan.p.abs().max(), min=1e-300)
+        p_c = 2e7 + 1e6 * pn
+        s_c = torch.clamp(0.5 * (1.0 + pn), 0.0, 1.0)
+        p0_c = p_c - 1e4
+        s0_c = 0.99 * s_c
+        qw_c = torch.clamp(plan.q, min=0.0) * 10.0
+        qo_c = torch.clamp(plan.q, max=0.0) * 8.0
+        rhs_c = torch.empty_like(p_c)
+        dp_c = torch.zeros_like(p_c)
+        fl = ms.cpr_fluid()
+        with torch.cuda.stream(stream):
+            ms.ms_cpr_pressure_system(ctx, plan.sys, plan.perm, fl, p_c, s_c, p0_c, s0_c, qw_c, qo_c, 86400.0, rhs_c)
+            ccpr = ms.ms_galerkin(ctx, plan.sys, plan.basis, ms.MS_PREC_FP64)
+
+            def cpr_step():
+                ms.ms_cpr_pressure_system(ctx, plan.sys, plan.perm, fl, p_c, s_c, p0_c, s0_c, qw_c, qo_c, 86400.0,
+                                          rhs_c)
+                ms.ms_coarse_refresh(ctx, plan.sys, ccpr)
+                dp_c.zero_()
+                return ms.ms_solve(ctx, plan.sys, [ccpr], rhs_c, dp_c, tol=1e-6, max_iter=5000,
+                                   precision=ms.MS_PREC_FP64, outer=ms.MS_OUTER_GMRES, restart=30)
+            cpr_step()
+            kc = max(1, args.steps // 2)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            cinfo = [cpr_step() for _ in range(kc)]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            c_ms = e0.elapsed_time(e1)
+            ms.ms_profile_reset()
+            ms.ms_profile_enable(True)
+            cpr_step()
+            torch.cuda.synchronize()
+            ms.ms_profile_enable(False)
+            pc = ms.ms_profile_read()
+        ms.ms_coarse_release(ccpr)
+
+        def stat(k):
+            v = pc.get(k)
+            if not v or not v["timed_launches"]:
+                return None
+            t = v["total_ms"] / v["timed_launches"]
+            return {"ms": t, "GBps": (v["bytes"] / v["timed_launches"]) / (t * 1e-3) / 1e9 if v["bytes"] else None}
+        line["cpr"] = {"value": n * kc * world / (c_ms * 1e-3), "unit": UNIT, "ms_per_step": c_ms / kc,
+                       "stage": "CPR pressure system (quasi-IMPES) + Galerkin + GJ inverse + GMRES(30) to 1e-6",
+                       "steps": cinfo[-1]["iters"], "rel_residual": cinfo[-1]["rel_residual"],
+                       "cpr_cell": stat("cpr_cell"), "cpr_rows": stat("cpr_rows"),
+                       "gauss_jordan_ms": (stat("coarse_gauss_jordan") or {}).get("ms")}
 
     # end to end through the C ABI with pinned host buffers
     if not args.no_e2e:

@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define MS_ABI_VERSION 4
+#define MS_ABI_VERSION 5
 
 typedef enum {
     MS_OK = 0,
@@ -328,6 +328,42 @@ ms_status ms_coarse_refresh(ms_ctx *ctx, ms_system *sys, ms_coarse *coarse);
 ms_status ms_coarse_release(ms_coarse *coarse);
 /* Copy A_c out (host, M*M doubles, row-major). */
 ms_status ms_coarse_get(ms_ctx *ctx, const ms_coarse *coarse, double *Ac, int32_t *M);
+
+/* ----------------------------------------------------- CPR pressure stage */
+/* Compressible two-phase (water / oil) properties for the CPR pressure stage:
+ * rho_a(p) = rho_a0 exp(c_a (p - p_ref)), phi(p) = phi0 exp(c_r (p - p_ref)),
+ * Corey mobilities kr_a(s) / mu_a as in ms_fluid.  SI units. */
+typedef struct {
+    double mu_w, mu_o;        /* viscosities (Pa s)                    */
+    double n_w, n_o;          /* Corey exponents (>= 1)                */
+    double s_wc, s_or;        /* residual saturations                  */
+    double phi0;              /* porosity at p_ref                     */
+    double rho_w0, rho_o0;    /* densities at p_ref (kg/m^3)           */
+    double c_w, c_o, c_r;     /* water, oil and rock compressibility (1/Pa) */
+    double p_ref;             /* reference pressure (Pa)               */
+} ms_cpr_fluid;
+
+/* Pressure stage of CPR (Sec. 4, quasi-IMPES decoupling; the predictor of
+ * the paper's Fig. 3) for one fully implicit step of the compressible
+ * two-phase system with primary variables p and s = s_w per cell:
+ *   R_a,i = V/dt [phi rho_a s_a - (phi rho_a s_a)^0] + sum_j T_ij (lambda_a
+ *   rho_a)(up) (p_i - p_j) - q_a,i,   up = the higher-pressure cell (lower
+ *   index on a tie), T_ij the geometric TPFA transmissibilities of perm.
+ * Quasi-IMPES weights w_w + w_o = 1 cancel the diagonal saturation
+ * derivatives, w_w dR_w/ds_i + w_o dR_o/ds_i = 0, and the system's matrix is
+ * replaced by J* = W_w dR_w/dp + W_o dR_o/dp (not symmetric, no reference-cell
+ * pinning: compressibility makes it nonsingular); rhs = -(W_w R_w + W_o R_o),
+ * so ms_solve(q = rhs) returns the pressure update of the predictor.  Galerkin
+ * stages formed afterwards are not symmetrised and are inverted by
+ * Gauss-Jordan elimination.  The basis is not touched (smooth it on the TPFA
+ * matrix first, or on J* with ms_basis_rebuild).  ms_assemble_tpfa restores
+ * a symmetric pinned TPFA matrix.
+ * perm: 3N; p, s, p0, s0 (state at the start of the step), q_w, q_o (fixed
+ * mass rates, kg/s): n doubles each; rhs: n doubles out; weights: 2n out
+ * (w_w then w_o) or NULL; host or device arrays; dt > 0. */
+ms_status ms_cpr_pressure_system(ms_ctx *ctx, ms_system *sys, const double *perm, const ms_cpr_fluid *fluid,
+                                 const double *p, const double *s, const double *p0, const double *s0,
+                                 const double *q_w, const double *q_o, double dt, double *rhs, double *weights);
 
 /* ------------------------------------------------------------------ solve */
 /* Multiscale multibasis iteration (Eq. (11)) in a Richardson loop

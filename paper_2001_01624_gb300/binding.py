@@ -83,6 +83,16 @@ def fluid(mu_w=1.0, mu_o=3.0, n_w=2.0, n_o=2.0, s_wc=0.0, s_or=0.0, porosity=0.2
     return ms_fluid(mu_w, mu_o, n_w, n_o, s_wc, s_or, porosity, cfl)
 
 
+class ms_cpr_fluid(C.Structure):
+    _fields_ = [("mu_w", _d), ("mu_o", _d), ("n_w", _d), ("n_o", _d), ("s_wc", _d), ("s_or", _d), ("phi0", _d),
+                ("rho_w0", _d), ("rho_o0", _d), ("c_w", _d), ("c_o", _d), ("c_r", _d), ("p_ref", _d)]
+
+
+def cpr_fluid(mu_w=1e-3, mu_o=3e-3, n_w=2.0, n_o=2.0, s_wc=0.0, s_or=0.0, phi0=0.2, rho_w0=1000.0, rho_o0=800.0,
+              c_w=4.5e-10, c_o=1.5e-9, c_r=5e-10, p_ref=2e7) -> ms_cpr_fluid:
+    return ms_cpr_fluid(mu_w, mu_o, n_w, n_o, s_wc, s_or, phi0, rho_w0, rho_o0, c_w, c_o, c_r, p_ref)
+
+
 class ms_batch_member(C.Structure):
     _fields_ = [("sys", _vp), ("stages", _vp), ("n_stages", _i32), ("q", _vp), ("p", _vp),
                 ("info", C.POINTER(ms_solve_info)), ("rebuild", _vp), ("basis_iters", _i32), ("status", _i32)]
@@ -129,6 +139,8 @@ def lib():
         "ms_coarse_create": ([_vp, _vp, _vp, _i32, _i32, P(_vp)], _i32),
         "ms_partition_wells": ([_vp, _vp, _i32, _vp, _vp, _vp, P(_i32)], _i32),
         "ms_dense_inverse": ([_vp, _i32, _vp, _vp], _i32),
+        "ms_cpr_pressure_system": ([_vp, _vp, _vp, P(ms_cpr_fluid), _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp],
+                                   _i32),
         "ms_coarse_refresh": ([_vp, _vp, _vp], _i32),
         "ms_coarse_release": ([_vp], _i32),
         "ms_coarse_get": ([_vp, _vp, _vp, P(_i32)], _i32),
@@ -152,7 +164,7 @@ def exported_symbols() -> Sequence[str]:
     return ["ms_abi_version", "ms_status_string", "ms_last_error", "ms_create", "ms_destroy", "ms_set_stream",
             "ms_system_create", "ms_system_release", "ms_system_get_info", "ms_assemble_tpfa",
             "ms_system_get_matrix", "ms_spmv", "ms_ilu_apply", "ms_ilu_apply_noalloc", "ms_partition_cartesian", "ms_partition_components", "ms_partition_dynamic",
-            "ms_partition_wells", "ms_coarse_create", "ms_dense_inverse",
+            "ms_partition_wells", "ms_coarse_create", "ms_dense_inverse", "ms_cpr_pressure_system",
             "ms_build_basis", "ms_basis_rebuild", "ms_basis_update", "ms_basis_release", "ms_basis_get_info",
             "ms_basis_get", "ms_add_adaptive_basis", "ms_galerkin", "ms_coarse_refresh", "ms_coarse_release",
             "ms_coarse_get", "ms_solve", "ms_solve_batch", "ms_total_mobility", "ms_transport_step", "ms_profile_enable", "ms_profile_reset", "ms_profile_read"]
@@ -385,6 +397,19 @@ def ms_dense_inverse(ctx, A):
     X = np.empty_like(A)
     _check(lib().ms_dense_inverse(ctx, A.shape[0], _ptr(A), _ptr(X)), ctx)
     return X
+
+
+def ms_cpr_pressure_system(ctx, sys, perm, fluid, p, s, p0, s0, q_w, q_o, dt, rhs=None, weights=None):
+    """Replace the system's matrix by the CPR pressure matrix J* (quasi-IMPES)
+    of the compressible two-phase step; returns rhs = -(W_w R_w + W_o R_o)
+    (numpy unless an output tensor is given).  weights: optional 2n output."""
+    n = ms_system_get_info(sys)["n"]
+    out = np.empty(n) if rhs is None else rhs
+    _check(lib().ms_cpr_pressure_system(ctx, sys, _ptr(_as(perm, np.float64)), C.byref(fluid), _ptr(_as(p, np.float64)),
+                                        _ptr(_as(s, np.float64)), _ptr(_as(p0, np.float64)), _ptr(_as(s0, np.float64)),
+                                        _ptr(_as(q_w, np.float64)), _ptr(_as(q_o, np.float64)), float(dt), _ptr(out),
+                                        _ptr(weights)), ctx)
+    return out
 
 
 def ms_coarse_refresh(ctx, sys, coarse):

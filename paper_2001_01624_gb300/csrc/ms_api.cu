@@ -242,7 +242,7 @@ void coarse_error(ms_ctx *ctx, ms_coarse &c, int err) {
         if (c.gj_bar.n) MS_CUDA(cudaMemsetAsync(c.gj_bar.p, 0, 2 * sizeof(unsigned long long), ctx->stream));
         throw Error{MS_ERR_TIMEOUT, "a coarse factorisation wait ran out"};
     }
-    throw Error{MS_ERR_COARSE_SINGULAR, c.restriction == MS_RESTRICT_FV
+    throw Error{MS_ERR_COARSE_SINGULAR, c.nonsym
                                             ? "coarse Gauss-Jordan elimination met a zero pivot column"
                                             : "coarse Cholesky met a non-positive pivot"};
 }
@@ -251,6 +251,7 @@ void galerkin_values(ms_ctx *ctx, ms_system &s, const ms_basis &b, ms_coarse &c)
     cudaStream_t st = ctx->stream;
     MS_REQUIRE(s.assembled, MS_ERR_STATE, "system not assembled");
     const bool fv = c.restriction == MS_RESTRICT_FV;
+    c.nonsym = fv || !s.symmetric;   // Gauss-Jordan inverse instead of Cholesky
     s.w_i0.alloc(4);
     int *h = (int *)ctx->pinned.get(64);
     const int wap = launch_ap_count(s, b, s.w_i0.p, h, st);
@@ -260,20 +261,21 @@ void galerkin_values(ms_ctx *ctx, ms_system &s, const ms_basis &b, ms_coarse &c)
     launch_ap_fill(s, b, c, st);
     c.Ac.alloc((size_t)c.M * c.M);
     if (fv) launch_rap(s, c.fv_h_cptr, c.fv_cptr.p, c.fv_ccell.p, nullptr, false, c, st);
-    else launch_rap(s, b.h_cptr, b.cptr.p, b.ccell.p, b.cval.p, true, c, st);
+    else launch_rap(s, b.h_cptr, b.cptr.p, b.ccell.p, b.cval.p, s.symmetric, c, st);
     MS_CUDA(cudaMemsetAsync(s.w_i0.p, 0, sizeof(int), st));
     c.use64 = false;
     c.inv32_error = 0.0;
-    auto inverse64 = [&]() { fv ? dense_gj_inverse64(c, s.w_i0.p, st) : dense_factor_inverse64(c, s.w_i0.p, st); };
+    const bool gj = c.nonsym;
+    auto inverse64 = [&]() { gj ? dense_gj_inverse64(c, s.w_i0.p, st) : dense_factor_inverse64(c, s.w_i0.p, st); };
     if (c.precision == MS_PREC_MIXED) {
         bool try32 = true;
-        if (fv) {   // the FP32 path equilibrates with 1/sqrt(a_jj)
+        if (gj) {   // the FP32 path equilibrates with 1/sqrt(a_jj)
             launch_check_diag(c, s.w_i0.p, st);
             try32 = read_error_word(ctx, s.w_i0.p) == 0;
             MS_CUDA(cudaMemsetAsync(s.w_i0.p, 0, sizeof(int), st));
         }
         if (try32) {
-            if (fv) dense_gj_inverse32(c, s.w_i0.p, st);
+            if (gj) dense_gj_inverse32(c, s.w_i0.p, st);
             else dense_factor_inverse32(c, s.w_i0.p, st);
             const int err32 = read_error_word(ctx, s.w_i0.p);
             if (err32 & kErrTimeout) coarse_error(ctx, c, err32);
@@ -481,7 +483,47 @@ ms_status ms_assemble_tpfa(ms_ctx *ctx, ms_system *s, const double *perm, const 
     ensure_fp32_matrix(*s, st);
     s->ilu64_valid = s->ilu32_valid = false;
     s->assembled = true;
+    s->pinned = s->symmetric = true;
     s->assembly_id++;
+    sync(st);
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_cpr_pressure_system(ms_ctx *ctx, ms_system *s, const double *perm, const ms_cpr_fluid *f,
+                                 const double *p, const double *sw, const double *p0, const double *s0,
+                                 const double *q_w, const double *q_o, double dt, double *rhs, double *weights) {
+    if (!ctx || !s || !perm || !f || !p || !sw || !p0 || !s0 || !q_w || !q_o || !rhs)
+        return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    API_TRY
+    DeviceGuard g(ctx->device);
+    MS_REQUIRE(dt > 0 && f->mu_w > 0 && f->mu_o > 0 && f->n_w >= 1 && f->n_o >= 1 && f->s_wc >= 0 && f->s_or >= 0 &&
+                   f->s_wc + f->s_or < 1.0 && f->phi0 > 0 && f->rho_w0 > 0 && f->rho_o0 > 0,
+               MS_ERR_INVALID_ARG, "bad CPR fluid or time step");
+    cudaStream_t st = ctx->stream;
+    const int64_t N = (int64_t)s->nx * s->ny * s->nz;
+    const size_t n = (size_t)s->n;
+    DBuf<double> stage_perm, sp, ss, sp0, ss0, sqw, sqo, out_r, out_w;
+    const double *kp = device_in(perm, (size_t)(3 * N), stage_perm, st);
+    s->w_i0.alloc(4);
+    MS_CUDA(cudaMemsetAsync(s->w_i0.p, 0, sizeof(int), st));
+    launch_check_perm(kp, 3 * N, s->w_i0.p, st);
+    if (read_error_word(ctx, s->w_i0.p)) throw Error{MS_ERR_INVALID_ARG, "permeability negative, NaN or infinite"};
+    launch_face_trans(*s, kp, nullptr, nullptr, st);   // geometric transmissibilities
+    const double *pd = device_in(p, n, sp, st), *sd = device_in(sw, n, ss, st);
+    const double *p0d = device_in(p0, n, sp0, st), *s0d = device_in(s0, n, ss0, st);
+    const double *qwd = device_in(q_w, n, sqw, st), *qod = device_in(q_o, n, sqo, st);
+    double *rd = rhs, *wd = weights;
+    if (!is_device_ptr(rhs)) { out_r.alloc(n); rd = out_r.p; }
+    if (weights && !is_device_ptr(weights)) { out_w.alloc(2 * n); wd = out_w.p; }
+    launch_cpr_pressure(*s, *f, dt, pd, sd, p0d, s0d, qwd, qod, rd, wd, st);
+    ensure_fp32_matrix(*s, st);
+    s->ilu64_valid = s->ilu32_valid = false;
+    s->assembled = true;
+    s->pinned = s->symmetric = false;
+    s->assembly_id++;
+    if (rd != rhs) copy_out(rhs, rd, n, st);
+    if (weights && wd != weights) copy_out(weights, wd, 2 * n, st);
     sync(st);
     return MS_OK;
     API_CATCH(ctx)
@@ -842,7 +884,7 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
     s->w_q.alloc(n);
     MS_CUDA(cudaMemcpyAsync(s->w_q.p, q, n * sizeof(double),
                             is_device_ptr(q) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-    launch_scatter_zero(s->w_q.p, s->ref, st);
+    if (s->pinned) launch_scatter_zero(s->w_q.p, s->ref, st);
     if (opts->use_x0) {
         MS_CUDA(cudaMemcpyAsync(s->w_x.p, p, n * sizeof(double),
                                 is_device_ptr(p) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));

@@ -227,6 +227,9 @@ struct ms_system {
     msgb::DBuf<int> sync;
 
     bool assembled = false;
+    bool pinned = true;         // reference cell pinned (TPFA); false for a CPR pressure system
+    bool symmetric = true;      // TPFA matrices are; CPR pressure systems are not
+    msgb::DBuf<double> w_cpr;   // CPR per-cell state functions and accumulation terms
     uint64_t assembly_id = 0;   // bumped by every assembly
 
     // solve workspace (grown on demand)
@@ -310,6 +313,7 @@ struct ms_coarse {
     // each block's cells: block member lists, ascending cells, with their
     // column chunks; unit weights)
     int restriction = 0;
+    bool nonsym = false;        // A_c not symmetric (finite volume, or a non-symmetric A): Gauss-Jordan inverse
     std::vector<int> fv_h_cptr;
     msgb::DBuf<int> fv_cptr, fv_ccell, fv_ch_beg, fv_ch_col, fv_ch_ptr;
     msgb::DBuf<double> fv_ch_part;
@@ -432,6 +436,9 @@ void dense_factor_inverse32(ms_coarse &c, int *err, cudaStream_t st);
 void dense_gj_inverse64(ms_coarse &c, int *err, cudaStream_t st);
 void dense_gj_inverse32(ms_coarse &c, int *err, cudaStream_t st);
 void launch_check_diag(const ms_coarse &c, int *err, cudaStream_t st);
+void launch_cpr_pressure(ms_system &s, const ms_cpr_fluid &f, double dt, const double *p, const double *sw,
+                         const double *p0, const double *s0, const double *qw, const double *qo, double *rhs,
+                         double *wout, cudaStream_t st);
 double coarse_inverse_check32(const ms_coarse &c, double *host2, cudaStream_t st);
 void launch_gemv64(const double *A, int M, const double *x, double *y, cudaStream_t st);
 void launch_gemv32(const float *A, int M, const float *x, float *y, cudaStream_t st);
