@@ -40,6 +40,10 @@ namespace msgb {
 namespace {
 
 constexpr int RF = 4;    // fetch ring: lines in flight per row
+// levels of the shuffle scan over L lanes, and the per-line table of the
+// scan's multipliers (one per level and lane)
+__host__ __device__ constexpr int scan_levels(int L) { return L >= 32 ? 5 : L >= 16 ? 4 : L >= 8 ? 3 : L >= 4 ? 2 : 1; }
+__host__ __device__ constexpr int scan_table(int L) { return L * scan_levels(L); }
 constexpr int NBX = 4;   // row-exchange ring: lines a row may run ahead of the next
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
@@ -165,21 +169,26 @@ __device__ __forceinline__ bool wait_lane(unsigned bar, unsigned parity, int *er
 // row through the exchange ring, and group G - 1 sends to the next warp's.
 template <typename T, typename TR, bool BWD, int E, int G>
 __global__ void __launch_bounds__(544, 1)
-    k_line_cluster(int nx, int ny, int nz, int TK, const T *__restrict__ coef4, const TR *__restrict__ rhs,
-                   T *__restrict__ out, int *err) {
+    k_line_cluster(int nx, int ny, int nz, int TK, const T *__restrict__ coef4, const T *__restrict__ scanm,
+                   const TR *__restrict__ rhs, T *__restrict__ out, int *err) {
     constexpr int L = 32 / G;
     constexpr int LW = L * E;
+    // FP64 only: the FP64 pipe bounds those sweeps; FP32 multiplies are cheap and
+    // table loads would only add shared-memory latency to the scan
+    constexpr bool TAB = sizeof(T) == 8;
+    constexpr int SCN = TAB ? scan_table(L) : 0;
     constexpr unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const unsigned K = cluster_rank();
     const int RPC = TK * G;   // rows per CTA
     const int WR = rhs_win(nx, sizeof(TR));
     const int CLN = nx * 4;   // packed coefficient line (elements of T)
-    // shared: coefficient slots [RF][RPC][CLN] T | rhs slots [RF][RPC][WR] TR | exchange [TK][NBX][LW] T |
+    const int CLS = CLN + SCN;   // a coefficient slot: the line's coefficients, then its scan multipliers
+    // shared: coefficient slots [RF][RPC][CLS] T | rhs slots [RF][RPC][WR] TR | exchange [TK][NBX][LW] T |
     //         barriers full_f, empty_f [RF][RPC], full_x, empty_x [NBX][TK]
     extern __shared__ __align__(16) unsigned char smraw[];
     T *cwin = reinterpret_cast<T *>(smraw);
-    size_t off = (size_t)RF * RPC * CLN * sizeof(T);
+    size_t off = (size_t)RF * RPC * CLS * sizeof(T);
     TR *rwin = reinterpret_cast<TR *>(smraw + off);
     off += (size_t)RF * RPC * WR * sizeof(TR);
     T *xin = reinterpret_cast<T *>(smraw + off);
@@ -213,6 +222,7 @@ __global__ void __launch_bounds__(544, 1)
         const int kr = BWD ? nz - 1 - g : g;
         const long long base0 = (long long)nx * (BWD ? ny - 1 : 0) + plane * kr;
         const unsigned lc = (unsigned)nx * 4 * sizeof(T);
+        constexpr unsigned ls = (unsigned)SCN * sizeof(T);
         unsigned long long t0 = 0;
         int idle = 0;
         while (__any_sync(FULL, tj < ny)) {
@@ -228,8 +238,11 @@ __global__ void __launch_bounds__(544, 1)
                     const unsigned long long ar = (unsigned long long)(size_t)(rhs + base);
                     const unsigned long long a0 = ar & ~15ull;
                     const unsigned lr = (unsigned)(((ar + (unsigned long long)nx * sizeof(TR) + 15ull) & ~15ull) - a0);
-                    mb_expect(fb, lc + lr);
-                    bulk_g2s(smem_u32(cwin + (size_t)(q * RPC + lane) * CLN), coef4 + base * 4, lc, fb);
+                    mb_expect(fb, lc + ls + lr);
+                    bulk_g2s(smem_u32(cwin + (size_t)(q * RPC + lane) * CLS), coef4 + base * 4, lc, fb);
+                    if (TAB)
+                        bulk_g2s(smem_u32(cwin + (size_t)(q * RPC + lane) * CLS + CLN), scanm + (base / nx) * SCN, ls,
+                                 fb);
                     bulk_g2s(smem_u32(rwin + (size_t)(q * RPC + lane) * WR), (const void *)(size_t)a0, lr, fb);
                     ++tj;
                     issued = true;
@@ -304,12 +317,19 @@ __global__ void __launch_bounds__(544, 1)
                 A[e] = T(1);
                 B[e] = T(0);
             }
+            constexpr int NLV = scan_levels(L);
+            T sv[NLV];                      // this lane's scan multipliers from the line's table (FP64)
+            if (TAB) {
+                const T *sm = cwin + (size_t)(q * RPC + rl) * CLS + CLN + gl;
+#pragma unroll
+                for (int lv = 0; lv < NLV; ++lv) sv[lv] = act ? sm[lv * L] : T(0);
+            }
             long long base = 0;
             if (act) {
                 base = base0 + dj * tj;
                 const int shr =
                     (int)((((unsigned)(size_t)rhs + (unsigned)base * (unsigned)sizeof(TR)) & 15u) / sizeof(TR));
-                const T *cl = cwin + (size_t)(q * RPC + rl) * CLN;
+                const T *cl = cwin + (size_t)(q * RPC + rl) * CLS;
                 const TR *rl_ = rwin + (size_t)(q * RPC + rl) * WR + shr;
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
@@ -328,18 +348,33 @@ __global__ void __launch_bounds__(544, 1)
                     }
                 }
             }
-            T LA = A[0], LB = B[0];
+            // lanes compose their cells' maps, then a shuffle scan composes the
+            // lanes.  The products of the multipliers the scan needs at each level
+            // do not depend on the right-hand side: in FP64 they come precomputed
+            // with the line, so only the offsets are scanned.
+            T LB = B[0];
+            if (TAB) {
 #pragma unroll
-            for (int e = 1; e < E; ++e) {
-                LB = A[e] * LB + B[e];
-                LA = A[e] * LA;
-            }
+                for (int e = 1; e < E; ++e) LB = A[e] * LB + B[e];
 #pragma unroll
-            for (int d = 1; d < L; d <<= 1) {
-                const T pa = __shfl_up_sync(FULL, LA, d, L), pb = __shfl_up_sync(FULL, LB, d, L);
-                if (gl >= d) {
-                    LB = LA * pb + LB;
-                    LA = LA * pa;
+                for (int d = 1, lv = 0; d < L; d <<= 1, ++lv) {
+                    const T pb = __shfl_up_sync(FULL, LB, d, L);
+                    if (gl >= d) LB = sv[lv] * pb + LB;
+                }
+            } else {
+                T LA = A[0];
+#pragma unroll
+                for (int e = 1; e < E; ++e) {
+                    LB = A[e] * LB + B[e];
+                    LA = A[e] * LA;
+                }
+#pragma unroll
+                for (int d = 1; d < L; d <<= 1) {
+                    const T pa = __shfl_up_sync(FULL, LA, d, L), pb = __shfl_up_sync(FULL, LB, d, L);
+                    if (gl >= d) {
+                        LB = LA * pb + LB;
+                        LA = LA * pa;
+                    }
                 }
             }
             T v = __shfl_up_sync(FULL, LB, 1, L);
@@ -670,6 +705,42 @@ __global__ void k_pack_coef4(int n, int nx, int ny, int transposed, const T *__r
     u[3] = dinv[i];
 }
 
+// Scan multipliers of every line of one sweep direction: lane gl's product of
+// its E cells' multipliers A (A = -L_x forward, -U_x / U_ii backward, 1 past
+// the line's end) and the running products the sweep's shuffle scan forms
+// before each level, in the sweep's order of operations (so the sweep's
+// results do not change).  One warp per line; table [line][level][lane].
+template <typename T, bool BWD, int E>
+__global__ void k_pack_scan(int nx, long long lines, const T *__restrict__ coef4, T *__restrict__ table) {
+    constexpr int L = 32;
+    const long long line = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int gl = threadIdx.x & 31;
+    if (line >= lines) return;                // whole warps
+    const T *cl = coef4 + line * nx * 4;
+    T A[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int at = gl * E + e;
+        A[e] = T(1);
+        if (at < nx) {
+            const int x = BWD ? nx - 1 - at : at;
+            T aa = -cl[4 * x];
+            if (BWD) aa *= cl[4 * x + 3];
+            A[e] = aa;
+        }
+    }
+    T LA = A[0];
+#pragma unroll
+    for (int e = 1; e < E; ++e) LA = A[e] * LA;
+    T *o = table + line * scan_table(L) + gl;
+#pragma unroll
+    for (int d = 1, lv = 0; d < L; d <<= 1, ++lv) {
+        o[lv * L] = LA;
+        const T pa = __shfl_up_sync(0xffffffffu, LA, d);
+        if (gl >= d) LA = LA * pa;
+    }
+}
+
 // out[y + ny (x + nx z)] = in[x + nx (y + ny z)] (inverse = 1: the other way),
 // 32 x 32 tiles of each z plane through shared memory
 template <typename TI, typename TO>
@@ -714,13 +785,14 @@ template <typename T, typename TR>
 size_t cluster_smem(int nx, int TK) {
     const LineShape ls = line_shape(nx, sizeof(T) == 4);
     const int RPC = TK * ls.G, LW = (32 / ls.G) * ls.E;
-    return (size_t)RF * RPC * nx * 4 * sizeof(T) + (size_t)RF * RPC * rhs_win(nx, sizeof(TR)) * sizeof(TR) +
+    return (size_t)RF * RPC * (nx * 4 + (sizeof(T) == 8 ? scan_table(32 / ls.G) : 0)) * sizeof(T) +
+           (size_t)RF * RPC * rhs_win(nx, sizeof(TR)) * sizeof(TR) +
            (size_t)TK * NBX * LW * sizeof(T) + (size_t)8 * 2 * RF * RPC + (size_t)8 * 2 * NBX * TK;
 }
 
 template <typename T, typename TR, bool BWD, int E, int G>
-cudaError_t launch_cluster_e(const ms_system &s, const int dims[3], int TK, int NK, const T *coef4, const TR *rhs,
-                             T *out, cudaStream_t st, bool query_only, int *clusters) {
+cudaError_t launch_cluster_e(const ms_system &s, const int dims[3], int TK, int NK, const T *coef4, const T *scanm,
+                             const TR *rhs, T *out, cudaStream_t st, bool query_only, int *clusters) {
     auto kern = k_line_cluster<T, TR, BWD, E, G>;
     const size_t smem = cluster_smem<T, TR>(dims[0], TK);
     static size_t smem_set = 0;                      // per instantiation: attributes are raised once
@@ -745,17 +817,21 @@ cudaError_t launch_cluster_e(const ms_system &s, const int dims[3], int TK, int 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (query_only) return cudaOccupancyMaxActiveClusters(clusters, kern, &cfg);
-    return cudaLaunchKernelEx(&cfg, kern, dims[0], dims[1], dims[2], TK, coef4, rhs, out, s.sync.p + 3);
+    return cudaLaunchKernelEx(&cfg, kern, dims[0], dims[1], dims[2], TK, coef4, scanm, rhs, out, s.sync.p + 3);
 }
 
 // dims: (line length, lines walked per row, rows) of the sweep's layout
 template <typename T, typename TR, bool BWD>
-cudaError_t launch_cluster(const ms_system &s, const int dims[3], int TK, int NK, const T *coef4, const TR *rhs,
-                           T *out, cudaStream_t st, bool query_only = false, int *clusters = nullptr) {
+cudaError_t launch_cluster(const ms_system &s, const int dims[3], int TK, int NK, const T *coef4, const T *scanm,
+                           const TR *rhs, T *out, cudaStream_t st, bool query_only = false,
+                           int *clusters = nullptr) {
     switch (line_shape(dims[0], sizeof(T) == 4).E) {
-        case 2: return launch_cluster_e<T, TR, BWD, 2, 1>(s, dims, TK, NK, coef4, rhs, out, st, query_only, clusters);
-        case 4: return launch_cluster_e<T, TR, BWD, 4, 1>(s, dims, TK, NK, coef4, rhs, out, st, query_only, clusters);
-        default: return launch_cluster_e<T, TR, BWD, 8, 1>(s, dims, TK, NK, coef4, rhs, out, st, query_only, clusters);
+        case 2:
+            return launch_cluster_e<T, TR, BWD, 2, 1>(s, dims, TK, NK, coef4, scanm, rhs, out, st, query_only, clusters);
+        case 4:
+            return launch_cluster_e<T, TR, BWD, 4, 1>(s, dims, TK, NK, coef4, scanm, rhs, out, st, query_only, clusters);
+        default:
+            return launch_cluster_e<T, TR, BWD, 8, 1>(s, dims, TK, NK, coef4, scanm, rhs, out, st, query_only, clusters);
     }
 }
 
@@ -766,7 +842,7 @@ inline void sweep_dims(const ms_system &s, int p, int dims[3]) {
 }
 
 template <typename T, typename TR>
-void cluster_apply(ms_system &s, const T *coef4, const TR *r, T *y, T *z, cudaStream_t st) {
+void cluster_apply(ms_system &s, const T *coef4, const T *scanm, const TR *r, T *y, T *z, cudaStream_t st) {
     const int64_t n = s.n;
     const int p = sizeof(T) == 8 ? 0 : 1;
     const double nl = (double)s.nnz_lower;
@@ -782,12 +858,14 @@ void cluster_apply(ms_system &s, const T *coef4, const TR *r, T *y, T *z, cudaSt
     }
     {
         KernelScope ks_(st, sizeof(T) == 8 ? "ilu_fwd" : "ilu_fwd32", nl * sizeof(T) + (double)n * (sizeof(TR) + sizeof(T)));
-        const cudaError_t e = launch_cluster<T, TR, false>(s, dims, s.cl_TK[p], s.cl_NK[p], coef4, rin, y, st);
+        const cudaError_t e = launch_cluster<T, TR, false>(s, dims, s.cl_TK[p], s.cl_NK[p], coef4, scanm, rin, y, st);
         MS_CUDA(e);
     }
     {
         KernelScope ks_(st, sizeof(T) == 8 ? "ilu_bwd" : "ilu_bwd32", nl * sizeof(T) + (double)n * 3 * sizeof(T));
-        const cudaError_t e = launch_cluster<T, T, true>(s, dims, s.cl_TK[p], s.cl_NK[p], coef4 + (size_t)4 * n, y, zout, st);
+        const long long lines = (long long)dims[1] * dims[2];
+        const cudaError_t e = launch_cluster<T, T, true>(s, dims, s.cl_TK[p], s.cl_NK[p], coef4 + (size_t)4 * n,
+                                                         scanm ? scanm + lines * scan_table(32) : nullptr, y, zout, st);
         MS_CUDA(e);
     }
     if (s.cl_T[p]) transpose_xy<T, T>(s, true, zout, z, st);
@@ -809,8 +887,10 @@ bool plan_precision(ms_system &s, int p, const int dims[3]) {
         const int NK = (warps + TK - 1) / TK;
         if (cluster_smem<T, TR>(dims[0], TK) > 220 * 1024 || cluster_smem<T, T>(dims[0], TK) > 220 * 1024) continue;
         int c1 = 0, c2 = 0;
-        if (launch_cluster<T, TR, false>(s, dims, TK, NK, nullptr, nullptr, nullptr, nullptr, true, &c1) != cudaSuccess ||
-            launch_cluster<T, T, true>(s, dims, TK, NK, nullptr, nullptr, nullptr, nullptr, true, &c2) != cudaSuccess) {
+        if (launch_cluster<T, TR, false>(s, dims, TK, NK, nullptr, nullptr, nullptr, nullptr, nullptr, true, &c1) !=
+                cudaSuccess ||
+            launch_cluster<T, T, true>(s, dims, TK, NK, nullptr, nullptr, nullptr, nullptr, nullptr, true, &c2) !=
+                cudaSuccess) {
             cudaGetLastError();
             continue;
         }
@@ -899,30 +979,57 @@ bool launch_ilu_factor_cluster(ms_system &s, cudaStream_t st) {
     return true;
 }
 
+template <typename T>
+void pack_scan_tables(ms_system &s, int p, const T *coef4, T *table, cudaStream_t st) {
+    int dims[3];
+    sweep_dims(s, p, dims);
+    const long long lines = (long long)dims[1] * dims[2];
+    const int g = (int)((lines + 7) / 8);
+    const int E = line_shape(dims[0], sizeof(T) == 4).E;
+    for (int dir = 0; dir < 2; ++dir) {
+        const T *c = coef4 + (size_t)dir * 4 * s.n;
+        T *o = table + (size_t)dir * lines * scan_table(32);
+        if (dir == 0) {
+            if (E == 2) k_pack_scan<T, false, 2><<<g, 256, 0, st>>>(dims[0], lines, c, o);
+            else if (E == 4) k_pack_scan<T, false, 4><<<g, 256, 0, st>>>(dims[0], lines, c, o);
+            else k_pack_scan<T, false, 8><<<g, 256, 0, st>>>(dims[0], lines, c, o);
+        } else {
+            if (E == 2) k_pack_scan<T, true, 2><<<g, 256, 0, st>>>(dims[0], lines, c, o);
+            else if (E == 4) k_pack_scan<T, true, 4><<<g, 256, 0, st>>>(dims[0], lines, c, o);
+            else k_pack_scan<T, true, 8><<<g, 256, 0, st>>>(dims[0], lines, c, o);
+        }
+    }
+}
+
 void launch_ilu_pack_coef4(ms_system &s, bool fp32, cudaStream_t st) {
     const int g = (s.n + 255) / 256;
+    const size_t tab = (size_t)2 * s.n / (size_t)std::max(1, fp32 ? (s.cl_T[1] ? s.ny : s.nx) : (s.cl_T[0] ? s.ny : s.nx)) *
+                       scan_table(32);
     if (fp32) {
         s.coef4_32.alloc((size_t)8 * s.n);
         k_pack_coef4<float><<<g, 256, 0, st>>>(s.n, s.nx, s.ny, s.cl_T[1] ? 1 : 0, s.dcoef32.p, s.dinv32.p,
                                                s.coef4_32.p);
+
     } else {
         s.coef4_64.alloc((size_t)8 * s.n);
         k_pack_coef4<double><<<g, 256, 0, st>>>(s.n, s.nx, s.ny, s.cl_T[0] ? 1 : 0, s.dcoef64.p, s.dinv64.p,
                                                 s.coef4_64.p);
+        s.scan_64.alloc(tab);
+        pack_scan_tables<double>(s, 0, s.coef4_64.p, s.scan_64.p, st);
     }
     MS_CHECK_LAUNCH();
 }
 
 void launch_ilu_cluster64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st) {
-    cluster_apply<double, double>(s, s.coef4_64.p, r, y, z, st);
+    cluster_apply<double, double>(s, s.coef4_64.p, s.scan_64.p, r, y, z, st);
 }
 
 void launch_ilu_cluster32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st) {
-    cluster_apply<float, double>(s, s.coef4_32.p, r, y, z, st);
+    cluster_apply<float, double>(s, s.coef4_32.p, nullptr, r, y, z, st);
 }
 
 void launch_ilu_cluster32f(ms_system &s, const float *r, float *y, float *z, cudaStream_t st) {
-    cluster_apply<float, float>(s, s.coef4_32.p, r, y, z, st);
+    cluster_apply<float, float>(s, s.coef4_32.p, nullptr, r, y, z, st);
 }
 
 }  // namespace msgb

@@ -209,6 +209,7 @@ struct ms_system {
     int cl_TK[2] = {0, 0}, cl_NK[2] = {0, 0};
     msgb::DBuf<double> coef4_64;              // [2][n][4]: (Lx, Ly, Lz, 0), (Ux, Uy, Uz, 1/d) per cell
     msgb::DBuf<float> coef4_32;
+    msgb::DBuf<double> scan_64;               // [2][lines][levels][32]: scan multipliers of each FP64 sweep line
     msgb::DBuf<int> line_order;
     msgb::DBuf<unsigned long long> lface_j, lface_k, line_progress;
     msgb::DBuf<double> dcoef64;               // [6*n]: L(-x,-y,-z), U(+x,+y,+z)
