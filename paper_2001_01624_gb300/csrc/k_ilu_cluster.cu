@@ -337,12 +337,9 @@ __global__ void __launch_bounds__(544, 1)
                     if (at < nx) {
                         const int x = BWD ? nx - 1 - at : at;   // real x of the cell
                         const Coef4<T> c = load_coef(cl + 4 * x);
-                        T bb = (T)rl_[x] - c.b * prev[e] - c.c * nk[e];
-                        T aa = -c.a;
-                        if (BWD) {
-                            bb *= c.d;
-                            aa *= c.d;
-                        }
+                        // backward coefficients come scaled by 1 / U_ii (d = 1 / U_ii)
+                        const T bb = (BWD ? c.d * (T)rl_[x] : (T)rl_[x]) - c.b * prev[e] - c.c * nk[e];
+                        const T aa = -c.a;
                         A[e] = aa;
                         B[e] = bb;
                     }
@@ -699,14 +696,15 @@ __global__ void k_pack_coef4(int n, int nx, int ny, int transposed, const T *__r
     l[1] = dcoef[(size_t)b * n + i];
     l[2] = dcoef[(size_t)2 * n + i];
     l[3] = T(0);
-    u[0] = dcoef[(size_t)(3 + a) * n + i];
-    u[1] = dcoef[(size_t)(3 + b) * n + i];
-    u[2] = dcoef[(size_t)5 * n + i];
-    u[3] = dinv[i];
+    const T di = dinv[i];   // backward sweep: x_i = d (y_i - sum U_ij x_j), the U_ij stored times d
+    u[0] = dcoef[(size_t)(3 + a) * n + i] * di;
+    u[1] = dcoef[(size_t)(3 + b) * n + i] * di;
+    u[2] = dcoef[(size_t)5 * n + i] * di;
+    u[3] = di;
 }
 
 // Scan multipliers of every line of one sweep direction: lane gl's product of
-// its E cells' multipliers A (A = -L_x forward, -U_x / U_ii backward, 1 past
+// its E cells' multipliers A (A = -L_x forward, -U_x / U_ii backward as stored, 1 past
 // the line's end) and the running products the sweep's shuffle scan forms
 // before each level, in the sweep's order of operations (so the sweep's
 // results do not change).  One warp per line; table [line][level][lane].
@@ -724,9 +722,7 @@ __global__ void k_pack_scan(int nx, long long lines, const T *__restrict__ coef4
         A[e] = T(1);
         if (at < nx) {
             const int x = BWD ? nx - 1 - at : at;
-            T aa = -cl[4 * x];
-            if (BWD) aa *= cl[4 * x + 3];
-            A[e] = aa;
+            A[e] = -cl[4 * x];    // backward coefficients are stored scaled by 1 / U_ii
         }
     }
     T LA = A[0];
