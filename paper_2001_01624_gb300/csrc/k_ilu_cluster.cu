@@ -40,6 +40,13 @@ namespace msgb {
 namespace {
 
 constexpr int RF = 4;    // fetch ring: lines in flight per row
+// warps per CTA when the rows span several clusters, for grids deep enough
+// that one cluster would hold at least kClusterSplitFrom warps per CTA (the
+// 60x220x85 sweeps: 340 / 357 us FP64 with 6 warps per CTA in one cluster,
+// 312 / 329 us with 2 per CTA over three)
+constexpr int kClusterTK64 = 2;
+constexpr int kClusterTK32 = 2;
+constexpr int kClusterSplitFrom = 4;
 // levels of the shuffle scan over L lanes, and the per-line table of the
 // scan's multipliers (one per level and lane)
 __host__ __device__ constexpr int scan_levels(int L) { return L >= 32 ? 5 : L >= 16 ? 4 : L >= 8 ? 3 : L >= 4 ? 2 : 1; }
@@ -107,6 +114,36 @@ __device__ __forceinline__ void st_async2(unsigned addr, double a, double b, uns
                  "d"(b), "r"(cbar)
                  : "memory");
 }
+// Rows handed across a cluster boundary go through global memory: each value
+// as 8-byte words that carry the launch's tag in their upper half (FP32: the
+// value's bits; FP64: its low and high halves), one slot per line, written once
+// per launch, so no slot is reused within a launch and a reader knows a value
+// is there when its tag is.
+__device__ __forceinline__ void ring_put(unsigned long long *w, float v, unsigned tag) {
+    *(volatile unsigned long long *)w = (unsigned long long)__float_as_uint(v) | ((unsigned long long)tag << 32);
+}
+__device__ __forceinline__ void ring_put(unsigned long long *w, double v, unsigned tag) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    *(volatile unsigned long long *)w = (b & 0xffffffffull) | ((unsigned long long)tag << 32);
+    *(volatile unsigned long long *)(w + 1) = (b >> 32) | ((unsigned long long)tag << 32);
+}
+// the word once it carries tag (bounded: false after the wait limit)
+__device__ __forceinline__ bool ring_word(const unsigned long long *w, unsigned tag, unsigned &out, int *err);
+__device__ __forceinline__ bool ring_get(const unsigned long long *w, unsigned tag, float &v, int *err) {
+    unsigned a;
+    if (!ring_word(w, tag, a, err)) return false;
+    v = __uint_as_float(a);
+    return true;
+}
+__device__ __forceinline__ bool ring_get(const unsigned long long *w, unsigned tag, double &v, int *err) {
+    unsigned lo, hi;
+    if (!ring_word(w, tag, lo, err) || !ring_word(w + 1, tag, hi, err)) return false;
+    v = __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+    return true;
+}
+template <typename T>
+__host__ __device__ constexpr int ring_words() { return sizeof(T) == 8 ? 2 : 1; }
+
 __device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                  "l"(src), "r"(bytes), "r"(bar)
@@ -162,15 +199,40 @@ __device__ __forceinline__ bool wait_lane(unsigned bar, unsigned parity, int *er
     return true;
 }
 
+__device__ __forceinline__ bool ring_word(const unsigned long long *w, unsigned tag, unsigned &out, int *err) {
+    unsigned long long v = *(const volatile unsigned long long *)w;
+    unsigned long long t0 = 0;
+    int spins = 0;
+    while ((unsigned)(v >> 32) != tag) {
+        if ((++spins & 63) == 0) {
+            const unsigned long long now = global_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > kWaitNs) {
+                atomicOr(err, kErrTimeout);
+                return false;
+            }
+        }
+        v = *(const volatile unsigned long long *)w;
+    }
+    out = (unsigned)(v & 0xffffffffull);
+    return true;
+}
+
 // G k-rows per warp, in lane groups of L = 32 / G lanes; E cells per lane.
+// The rows may span several clusters (NC of them, gridDim.x / NC CTAs each):
+// each cluster takes a ticket when it starts, and the ticket, not the launch
+// position, decides which block of rows it owns, so a cluster only ever waits
+// for one that started before it; at a cluster boundary the line goes through
+// a global ring (one tagged slot per line), so the sender never waits.
 // Warp step t: group h solves line t - h of its row, so the k-neighbour of
 // groups h > 0 is the line group h - 1 finished in step t - 1 (passed by a
 // shuffle); group 0 receives its k-neighbour from the previous warp's last
 // row through the exchange ring, and group G - 1 sends to the next warp's.
 template <typename T, typename TR, bool BWD, int E, int G>
 __global__ void __launch_bounds__(544, 1)
-    k_line_cluster(int nx, int ny, int nz, int TK, const T *__restrict__ coef4, const T *__restrict__ scanm,
-                   const TR *__restrict__ rhs, T *__restrict__ out, int *err) {
+    k_line_cluster(int nx, int ny, int nz, int TK, int NC, const T *__restrict__ coef4, const T *__restrict__ scanm,
+                   const TR *__restrict__ rhs, T *__restrict__ out, unsigned long long *tick,
+                   unsigned long long *ring, int *err) {
     constexpr int L = 32 / G;
     constexpr int LW = L * E;
     // FP64 only: the FP64 pipe bounds those sweeps; FP32 multiplies are cheap and
@@ -197,7 +259,10 @@ __global__ void __launch_bounds__(544, 1)
     const unsigned empty_f = full_f + 8 * RF * RPC;
     const unsigned full_x = empty_f + 8 * RF * RPC;
     const unsigned empty_x = full_x + 8 * NBX * TK;
+    const unsigned empty_r = empty_x + 8 * NBX * TK;     // [NBX]: warp 0 frees a slot the relay warp filled
 
+    __shared__ unsigned long long s_tick;
+    if (NC > 1 && K == 0 && tid == 0) s_tick = atomicAdd(tick, 1ull);
     if (tid < RPC) {
         for (int q = 0; q < RF; ++q) {
             mb_init(full_f + 8 * (q * RPC + tid), 1);
@@ -210,14 +275,25 @@ __global__ void __launch_bounds__(544, 1)
             mb_init(empty_x + 8 * (b * TK + tid), 1);
         }
     }
+    if (tid < NBX) mb_init(empty_r + 8 * tid, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     cluster_sync_all();
+    // this cluster's block of rows (v) and the launch's tag, from rank 0's ticket
+    unsigned long long tk = 0;
+    if (NC > 1) {
+        const unsigned a = map_cta(smem_u32(&s_tick), 0);
+        asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(tk) : "r"(a) : "memory");
+    }
+    const int NKC = (int)gridDim.x / NC;                 // CTAs per cluster
+    const int v = (int)(tk % (unsigned long long)NC);
+    const unsigned tag = (unsigned)(tk / (unsigned long long)NC) + 1u;
+    const int KG = v * NKC + (int)K;                     // CTA position in the row order
 
     const long long plane = (long long)nx * ny;
     const long long dj = BWD ? -(long long)nx : (long long)nx;   // real index step from line j to j+1 (mirrored)
     if (w == TK) {
         // producer warp: lane r streams the inputs of row r, each row on its own
-        const int g = (int)K * RPC + lane;
+        const int g = KG * RPC + lane;
         int tj = (lane < RPC && g < nz) ? 0 : ny;
         const int kr = BWD ? nz - 1 - g : g;
         const long long base0 = (long long)nx * (BWD ? ny - 1 : 0) + plane * kr;
@@ -262,9 +338,83 @@ __global__ void __launch_bounds__(544, 1)
                 }
             }
         }
-    } else if (w < TK && ((int)K * TK + w) * G < nz) {
+    } else if (w == TK + 1) {
+        // relay warp (rows spanning several clusters): the first CTA of a cluster
+        // other than the first takes the previous cluster's last row from the
+        // global ring and hands each line to its warp 0 through the exchange
+        // ring, so the ring's polling stays off warp 0's steps.  Loads for the
+        // next D lines stay in flight; the lines that have arrived, in order,
+        // are forwarded after each round trip.
+        if constexpr (G == 1) {
+            constexpr int RW = ring_words<T>();
+            constexpr int D = 8 / E > 0 ? 8 / E : 1;
+            constexpr int NWD = E * RW;                   // words of one lane's values of a line
+            if (K == 0 && v > 0 && KG * TK < nz) {
+                const unsigned long long *rin = ring + ((size_t)(v - 1) * ny * LW + lane * E) * RW;
+                const unsigned xo0 = map_cta(smem_u32(xin + (size_t)lane * E), K);   // warp 0's slots
+                const unsigned fb0 = map_cta(full_x, K);
+                int tj = 0;
+                unsigned long long t0 = 0;
+                bool ok = true;
+                while (tj < ny && ok) {
+                    unsigned long long wv[D][NWD];
+#pragma unroll
+                    for (int d = 0; d < D; ++d)
+#pragma unroll
+                        for (int k = 0; k < NWD; ++k)
+                            wv[d][k] = tj + d < ny ? *(const volatile unsigned long long *)(rin + (size_t)(tj + d) * LW * RW + k)
+                                                   : 0ull;
+                    int ready = 0;
+#pragma unroll
+                    for (int d = 0; d < D; ++d) {
+                        bool here = tj + d < ny;
+#pragma unroll
+                        for (int k = 0; k < NWD; ++k) here = here && (unsigned)(wv[d][k] >> 32) == tag;
+                        if (here && ready == d) ready = d + 1;
+                    }
+                    ready = (int)__reduce_min_sync(0xffffffffu, (unsigned)ready);
+                    if (ready == 0) {
+                        const unsigned long long now = __shfl_sync(0xffffffffu, global_ns(), 0);
+                        if (t0 == 0) t0 = now;
+                        else if (now - t0 > kWaitNs) {
+                            if (lane == 0) atomicOr(err, kErrTimeout);
+                            ok = false;
+                        }
+                        continue;
+                    }
+                    t0 = 0;
+#pragma unroll
+                    for (int d = 0; d < D; ++d) {
+                        if (d >= ready) break;
+                        const int line = tj + d;
+                        const int bs = line % NBX;
+                        const unsigned ubs = (unsigned)(line / NBX);
+                        if (line >= NBX) ok = wait_lane(empty_r + 8 * bs, (ubs - 1) & 1u, err);
+                        if (!__all_sync(0xffffffffu, ok)) {
+                            ok = false;
+                            break;
+                        }
+                        T val[E];
+#pragma unroll
+                        for (int e = 0; e < E; ++e) {
+                            if (RW == 2) {
+                                const unsigned long long bits = (wv[d][2 * e] & 0xffffffffull) | (wv[d][2 * e + 1] << 32);
+                                val[e] = (T)__longlong_as_double((long long)bits);
+                            } else {
+                                val[e] = (T)__uint_as_float((unsigned)(wv[d][e] & 0xffffffffull));
+                            }
+                        }
+                        const unsigned xo = xo0 + (unsigned)(bs * LW * sizeof(T)), fb = fb0 + 8 * bs * TK;
+#pragma unroll
+                        for (int e = 0; e < E; e += 2) st_async2(xo + e * (unsigned)sizeof(T), val[e], val[e + 1], fb);
+                    }
+                    tj += ready;
+                }
+            }
+        }
+    } else if (w < TK && (KG * TK + w) * G < nz) {
         const int grp = lane / L, gl = lane % L;
-        const int wrow0 = ((int)K * TK + w) * G;             // first row of this warp
+        const int wrow0 = (KG * TK + w) * G;                 // first row of this warp
         const int g = wrow0 + grp;                           // row of this lane's group
         const int rl = w * G + grp;                          // row within the CTA
         const bool live = g < nz;
@@ -273,15 +423,24 @@ __global__ void __launch_bounds__(544, 1)
         const bool has_src = wrow0 > 0;                      // the previous warp's last row exists
         const bool has_dst = wrow0 + G < nz;                 // the next warp's first row exists (this warp full)
         const bool src_remote = w == 0, dst_remote = w == TK - 1;
+        // across a cluster boundary: through the global ring (received by the
+        // relay warp of this CTA, which fills warp 0's exchange ring)
+        const bool src_relay = has_src && src_remote && K == 0;
+        const bool dst_global = has_dst && dst_remote && (int)K == NKC - 1;
         // a line handed to the next warp: LW values (cells past nx are padding)
         constexpr unsigned XB = LW * sizeof(T);
+        constexpr int RW = ring_words<T>();
         if (has_src && lane == 0)
             for (int b = 0; b < NBX && b < ny; ++b) mb_expect_relaxed(full_x + 8 * (b * TK + w), XB);
-        const unsigned dst_rank = dst_remote ? K + 1 : K;
+        const unsigned dst_rank = dst_remote && !dst_global ? K + 1 : K;
         const int dst_w = dst_remote ? 0 : w + 1;
-        const unsigned dst_xin = map_cta(smem_u32(xin + (size_t)dst_w * NBX * LW + gl * E), dst_rank);
-        const unsigned dst_full = map_cta(full_x + 8 * dst_w, dst_rank);
-        const unsigned src_empty = has_src ? map_cta(empty_x + 8 * (src_remote ? TK - 1 : w - 1), src_remote ? K - 1 : K) : 0u;
+        const unsigned dst_xin = dst_global ? 0u : map_cta(smem_u32(xin + (size_t)dst_w * NBX * LW + gl * E), dst_rank);
+        const unsigned dst_full = dst_global ? 0u : map_cta(full_x + 8 * dst_w, dst_rank);
+        const unsigned src_empty =
+            !has_src ? 0u
+                     : (src_relay ? empty_r : map_cta(empty_x + 8 * (src_remote ? TK - 1 : w - 1), src_remote ? K - 1 : K));
+        // ring slots: [boundary][line][LW values][RW words]; the last row of a cluster writes boundary v
+        unsigned long long *ring_out = dst_global ? ring + ((size_t)v * ny * LW + gl * E) * RW : nullptr;
         T prev[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) prev[e] = T(0);
@@ -293,29 +452,14 @@ __global__ void __launch_bounds__(544, 1)
             const unsigned u = act ? (unsigned)(tj / RF) : 0u;
             bool ok = true;
             if (act) ok = wait_lane(full_f + 8 * (q * RPC + rl), u & 1u, err);
-            // k-neighbour: the group below finished this line in the previous step
-            T nk[E];
-#pragma unroll
-            for (int e = 0; e < E; ++e) nk[e] = G > 1 ? __shfl_up_sync(FULL, prev[e], L) : T(0);
-            const int b = t % NBX;
-            const unsigned ub = (unsigned)(t / NBX);
-            const bool recv = grp == 0 && has_src && act;
-            if (grp == 0) {
-#pragma unroll
-                for (int e = 0; e < E; ++e) nk[e] = T(0);
-            }
-            if (recv) {
-                ok = ok && wait_lane(full_x + 8 * (b * TK + w), ub & 1u, err);
-                const T *xi = xin + ((size_t)w * NBX + b) * LW + gl * E;
-#pragma unroll
-                for (int e = 0; e < E; ++e) nk[e] = xi[e];
-            }
-            if (!__all_sync(FULL, ok)) break;
-            T A[E], B[E];
+            // everything that does not depend on the k-neighbour first: the
+            // multipliers, the scan table and the offsets' in-row terms
+            T A[E], B[E], CK[E];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 A[e] = T(1);
                 B[e] = T(0);
+                CK[e] = T(0);
             }
             constexpr int NLV = scan_levels(L);
             T sv[NLV];                      // this lane's scan multipliers from the line's table (FP64)
@@ -338,12 +482,34 @@ __global__ void __launch_bounds__(544, 1)
                         const int x = BWD ? nx - 1 - at : at;   // real x of the cell
                         const Coef4<T> c = load_coef(cl + 4 * x);
                         // backward coefficients come scaled by 1 / U_ii (d = 1 / U_ii)
-                        const T bb = (BWD ? c.d * (T)rl_[x] : (T)rl_[x]) - c.b * prev[e] - c.c * nk[e];
-                        const T aa = -c.a;
-                        A[e] = aa;
-                        B[e] = bb;
+                        B[e] = (BWD ? c.d * (T)rl_[x] : (T)rl_[x]) - c.b * prev[e];
+                        A[e] = -c.a;
+                        CK[e] = c.c;
                     }
                 }
+            }
+            // k-neighbour: the group below finished this line in the previous step
+            T nk[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) nk[e] = G > 1 ? __shfl_up_sync(FULL, prev[e], L) : T(0);
+            const int b = t % NBX;
+            const unsigned ub = (unsigned)(t / NBX);
+            const bool recv = grp == 0 && has_src && act;
+            if (grp == 0) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) nk[e] = T(0);
+            }
+            if (recv) {
+                ok = ok && wait_lane(full_x + 8 * (b * TK + w), ub & 1u, err);
+                const T *xi = xin + ((size_t)w * NBX + b) * LW + gl * E;
+#pragma unroll
+                for (int e = 0; e < E; ++e) nk[e] = xi[e];
+            }
+            if (!__all_sync(FULL, ok)) break;
+            if (act) {
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (gl * E + e < nx) B[e] = B[e] - CK[e] * nk[e];
             }
             // lanes compose their cells' maps, then a shuffle scan composes the
             // lanes.  The products of the multipliers the scan needs at each level
@@ -387,7 +553,8 @@ __global__ void __launch_bounds__(544, 1)
             if (act && gl == 0) mb_arrive_relaxed(empty_f + 8 * (q * RPC + rl));
             if (recv && gl == 0) {
                 if (t + NBX < ny) mb_expect_relaxed(full_x + 8 * (b * TK + w), XB);
-                if (src_remote) mb_arrive_relaxed_remote(src_empty + 8 * b * TK);
+                if (src_relay) mb_arrive_relaxed(src_empty + 8 * b);
+                else if (src_remote) mb_arrive_relaxed_remote(src_empty + 8 * b * TK);
                 else mb_arrive_relaxed(src_empty + 8 * b * TK);
             }
             if (act) {
@@ -397,7 +564,11 @@ __global__ void __launch_bounds__(544, 1)
             // the last group passes its line to the next warp
             const bool send = has_dst && grp == G - 1 && act;
             bool ok2 = true;
-            if (send) {
+            if (send && dst_global) {
+                unsigned long long *ro = ring_out + (size_t)tj * LW * RW;
+#pragma unroll
+                for (int e = 0; e < E; ++e) ring_put(ro + e * RW, val[e], tag);
+            } else if (send) {
                 const int bs = tj % NBX;
                 const unsigned ubs = (unsigned)(tj / NBX);
                 if (tj >= NBX) ok2 = wait_lane(empty_x + 8 * (bs * TK + w), (ubs - 1) & 1u, err);
@@ -782,13 +953,14 @@ size_t cluster_smem(int nx, int TK) {
     const LineShape ls = line_shape(nx, sizeof(T) == 4);
     const int RPC = TK * ls.G, LW = (32 / ls.G) * ls.E;
     return (size_t)RF * RPC * (nx * 4 + (sizeof(T) == 8 ? scan_table(32 / ls.G) : 0)) * sizeof(T) +
-           (size_t)RF * RPC * rhs_win(nx, sizeof(TR)) * sizeof(TR) +
+           (size_t)RF * RPC * rhs_win(nx, sizeof(TR)) * sizeof(TR) + (size_t)8 * NBX +
            (size_t)TK * NBX * LW * sizeof(T) + (size_t)8 * 2 * RF * RPC + (size_t)8 * 2 * NBX * TK;
 }
 
 template <typename T, typename TR, bool BWD, int E, int G>
-cudaError_t launch_cluster_e(const ms_system &s, const int dims[3], int TK, int NK, const T *coef4, const T *scanm,
-                             const TR *rhs, T *out, cudaStream_t st, bool query_only, int *clusters) {
+cudaError_t launch_cluster_e(const ms_system &s, const int dims[3], int TK, int NK, int NC, const T *coef4,
+                             const T *scanm, const TR *rhs, T *out, unsigned long long *tick,
+                             unsigned long long *ring, cudaStream_t st, bool query_only, int *clusters) {
     auto kern = k_line_cluster<T, TR, BWD, E, G>;
     const size_t smem = cluster_smem<T, TR>(dims[0], TK);
     static size_t smem_set = 0;                      // per instantiation: attributes are raised once
@@ -801,8 +973,8 @@ cudaError_t launch_cluster_e(const ms_system &s, const int dims[3], int TK, int 
         nonportable = true;
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(NK, 1, 1);
-    cfg.blockDim = dim3(32 * (TK + 1), 1, 1);
+    cfg.gridDim = dim3(NK * NC, 1, 1);
+    cfg.blockDim = dim3(32 * (TK + 1 + (NC > 1 ? 1 : 0)), 1, 1);   // + producer warp (+ relay warp)
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -813,21 +985,25 @@ cudaError_t launch_cluster_e(const ms_system &s, const int dims[3], int TK, int 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (query_only) return cudaOccupancyMaxActiveClusters(clusters, kern, &cfg);
-    return cudaLaunchKernelEx(&cfg, kern, dims[0], dims[1], dims[2], TK, coef4, scanm, rhs, out, s.sync.p + 3);
+    return cudaLaunchKernelEx(&cfg, kern, dims[0], dims[1], dims[2], TK, NC, coef4, scanm, rhs, out, tick, ring,
+                              s.sync.p + 3);
 }
 
 // dims: (line length, lines walked per row, rows) of the sweep's layout
 template <typename T, typename TR, bool BWD>
-cudaError_t launch_cluster(const ms_system &s, const int dims[3], int TK, int NK, const T *coef4, const T *scanm,
-                           const TR *rhs, T *out, cudaStream_t st, bool query_only = false,
-                           int *clusters = nullptr) {
+cudaError_t launch_cluster(const ms_system &s, const int dims[3], int TK, int NK, int NC, const T *coef4,
+                           const T *scanm, const TR *rhs, T *out, unsigned long long *tick, unsigned long long *ring,
+                           cudaStream_t st, bool query_only = false, int *clusters = nullptr) {
     switch (line_shape(dims[0], sizeof(T) == 4).E) {
         case 2:
-            return launch_cluster_e<T, TR, BWD, 2, 1>(s, dims, TK, NK, coef4, scanm, rhs, out, st, query_only, clusters);
+            return launch_cluster_e<T, TR, BWD, 2, 1>(s, dims, TK, NK, NC, coef4, scanm, rhs, out, tick, ring, st,
+                                                      query_only, clusters);
         case 4:
-            return launch_cluster_e<T, TR, BWD, 4, 1>(s, dims, TK, NK, coef4, scanm, rhs, out, st, query_only, clusters);
+            return launch_cluster_e<T, TR, BWD, 4, 1>(s, dims, TK, NK, NC, coef4, scanm, rhs, out, tick, ring, st,
+                                                      query_only, clusters);
         default:
-            return launch_cluster_e<T, TR, BWD, 8, 1>(s, dims, TK, NK, coef4, scanm, rhs, out, st, query_only, clusters);
+            return launch_cluster_e<T, TR, BWD, 8, 1>(s, dims, TK, NK, NC, coef4, scanm, rhs, out, tick, ring, st,
+                                                      query_only, clusters);
     }
 }
 
@@ -854,14 +1030,17 @@ void cluster_apply(ms_system &s, const T *coef4, const T *scanm, const TR *r, T 
     }
     {
         KernelScope ks_(st, sizeof(T) == 8 ? "ilu_fwd" : "ilu_fwd32", nl * sizeof(T) + (double)n * (sizeof(TR) + sizeof(T)));
-        const cudaError_t e = launch_cluster<T, TR, false>(s, dims, s.cl_TK[p], s.cl_NK[p], coef4, scanm, rin, y, st);
+        const cudaError_t e = launch_cluster<T, TR, false>(s, dims, s.cl_TK[p], s.cl_NK[p], s.cl_NC[p], coef4, scanm,
+                                                           rin, y, s.cl_tick.p + p, s.cl_ring[p].p, st);
         MS_CUDA(e);
     }
     {
         KernelScope ks_(st, sizeof(T) == 8 ? "ilu_bwd" : "ilu_bwd32", nl * sizeof(T) + (double)n * 3 * sizeof(T));
         const long long lines = (long long)dims[1] * dims[2];
-        const cudaError_t e = launch_cluster<T, T, true>(s, dims, s.cl_TK[p], s.cl_NK[p], coef4 + (size_t)4 * n,
-                                                         scanm ? scanm + lines * scan_table(32) : nullptr, y, zout, st);
+        const cudaError_t e = launch_cluster<T, T, true>(s, dims, s.cl_TK[p], s.cl_NK[p], s.cl_NC[p],
+                                                         coef4 + (size_t)4 * n,
+                                                         scanm ? scanm + lines * scan_table(32) : nullptr, y, zout,
+                                                         s.cl_tick.p + p, s.cl_ring[p].p, st);
         MS_CUDA(e);
     }
     if (s.cl_T[p]) transpose_xy<T, T>(s, true, zout, z, st);
@@ -873,30 +1052,59 @@ void cluster_apply(ms_system &s, const T *coef4, const T *scanm, const TR *r, T 
 // limit, and the launch must be schedulable.  Fewer warps per CTA come first
 // (one warp per SM sub-partition keeps each warp's dependency chain unshared).
 template <typename T, typename TR>
+bool plan_fits(ms_system &s, const int dims[3], int TK, int NK, int NC) {
+    if (cluster_smem<T, TR>(dims[0], TK) > 220 * 1024 || cluster_smem<T, T>(dims[0], TK) > 220 * 1024) return false;
+    int c1 = 0, c2 = 0;
+    if (launch_cluster<T, TR, false>(s, dims, TK, NK, NC, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                     true, &c1) != cudaSuccess ||
+        launch_cluster<T, T, true>(s, dims, TK, NK, NC, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                   true, &c2) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return c1 >= NC && c2 >= NC;
+}
+
+template <typename T, typename TR>
 bool plan_precision(ms_system &s, int p, const int dims[3]) {
     if (dims[0] > 256 || dims[1] < 1 || dims[2] < 1) return false;
     const LineShape ls = line_shape(dims[0], sizeof(T) == 4);
     const int warps = (dims[2] + ls.G - 1) / ls.G;
+    // one cluster over all rows (also the factorisation's layout)
+    bool one = false;
     for (int C : {16, 8}) {
         const int TK = (warps + C - 1) / C;
         if (TK > 16 || TK * ls.G > 32) continue;
         const int NK = (warps + TK - 1) / TK;
-        if (cluster_smem<T, TR>(dims[0], TK) > 220 * 1024 || cluster_smem<T, T>(dims[0], TK) > 220 * 1024) continue;
-        int c1 = 0, c2 = 0;
-        if (launch_cluster<T, TR, false>(s, dims, TK, NK, nullptr, nullptr, nullptr, nullptr, nullptr, true, &c1) !=
-                cudaSuccess ||
-            launch_cluster<T, T, true>(s, dims, TK, NK, nullptr, nullptr, nullptr, nullptr, nullptr, true, &c2) !=
-                cudaSuccess) {
-            cudaGetLastError();
-            continue;
-        }
-        if (c1 >= 1 && c2 >= 1) {
-            s.cl_TK[p] = TK;
-            s.cl_NK[p] = NK;
-            return true;
+        if (plan_fits<T, TR>(s, dims, TK, NK, 1)) {
+            s.cl_TK[p] = s.cl_fTK[p] = TK;
+            s.cl_NK[p] = s.cl_fNK[p] = NK;
+            s.cl_NC[p] = 1;
+            one = true;
+            break;
         }
     }
-    return false;
+    if (!one) return false;
+    // rows over several clusters, so that fewer warps share an SM: TK warps per
+    // CTA (MSGB_ILU_TK overrides the default for this precision)
+    int tk = s.cl_TK[p] >= kClusterSplitFrom ? (sizeof(T) == 8 ? kClusterTK64 : kClusterTK32) : 0;
+    if (const char *e = std::getenv("MSGB_ILU_TK")) tk = std::atoi(e);
+    if (tk >= 1 && tk < s.cl_TK[p] && tk <= 15) {
+        const int NKtot = (warps + tk - 1) / tk;
+        const int NC = (NKtot + 15) / 16;
+        const int NK = (NKtot + NC - 1) / NC;
+        const int TK = (warps + NK * NC - 1) / (NK * NC);
+        if (NC > 1 && plan_fits<T, TR>(s, dims, TK, NK, NC)) {
+            s.cl_TK[p] = TK;
+            s.cl_NK[p] = NK;
+            s.cl_NC[p] = NC;
+            s.cl_ring[p].alloc((size_t)(NC - 1) * dims[1] * (32 / ls.G) * ls.E * (sizeof(T) == 8 ? 2 : 1));
+            s.cl_ring[p].zero(nullptr);
+        }
+    }
+    s.cl_tick.alloc(2);
+    s.cl_tick.zero(nullptr);
+    return true;
 }
 
 }  // namespace
@@ -933,7 +1141,7 @@ void plan_ilu_cluster(ms_system &s) {
 bool launch_ilu_factor_cluster(ms_system &s, cudaStream_t st) {
     if (!s.structured || !s.cl_ok[0] || s.nx > 256) return false;
     const int E = s.nx <= 64 ? 2 : s.nx <= 128 ? 4 : 8;
-    const int TK = s.cl_TK[0], NK = s.cl_NK[0];
+    const int TK = s.cl_fTK[0], NK = s.cl_fNK[0];   // one cluster over all rows
     const int LW = 32 * E;
     const size_t smem = (size_t)RF * TK * s.nx * 32 + (size_t)TK * NBX * LW * 8 + (size_t)8 * 2 * (RF + NBX) * TK;
     if (smem > 220 * 1024) return false;

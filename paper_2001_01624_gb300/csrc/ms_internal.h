@@ -207,6 +207,10 @@ struct ms_system {
     msgb::DBuf<float> w_T32, w_T32b;
     msgb::DBuf<double> w_fac4;                // structured factorisation input (c_x, c_y, c_z, A_ii) per cell
     int cl_TK[2] = {0, 0}, cl_NK[2] = {0, 0};
+    int cl_NC[2] = {1, 1};                    // clusters the sweep's rows span
+    int cl_fTK[2] = {0, 0}, cl_fNK[2] = {0, 0};   // single-cluster layout (factorisation)
+    msgb::DBuf<unsigned long long> cl_tick;   // cluster tickets per precision
+    msgb::DBuf<unsigned long long> cl_ring[2];  // lines crossing cluster boundaries (tagged words)
     msgb::DBuf<double> coef4_64;              // [2][n][4]: (Lx, Ly, Lz, 0), (Ux/d, Uy/d, Uz/d, 1/d) per cell, d = U_ii
     msgb::DBuf<float> coef4_32;
     msgb::DBuf<double> scan_64;               // [2][lines][levels][32]: scan multipliers of each FP64 sweep line
