@@ -33,9 +33,21 @@ __global__ void k_basis_init32(int64_t total, const unsigned char *__restrict__ 
     for (; e < total; e += (int64_t)gridDim.x * blockDim.x) pv[e] = is_home[e] ? 1.0f : 0.0f;
 }
 
-__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, double v) {
-    atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+// |x| as an integer key that orders like the value (IEEE bit patterns of
+// non-negative numbers; NaN above infinity), so the running maximum of the
+// basis increments stays off the FP64 pipe; key_value turns the key back.
+__device__ __forceinline__ unsigned long long abs_key(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
+__device__ __forceinline__ unsigned long long abs_key(float x) {
+    return (unsigned long long)(__float_as_uint(x) & 0x7fffffffu);
+}
+template <typename T>
+__device__ __forceinline__ double key_value(unsigned long long k);
+template <>
+__device__ __forceinline__ double key_value<double>(unsigned long long k) { return __longlong_as_double((long long)k); }
+template <>
+__device__ __forceinline__ double key_value<float>(unsigned long long k) { return (double)__uint_as_float((unsigned)k); }
 
 // One MsRSB iteration for all bases, fused with the partition-of-unity pass.
 template <typename T, int BM>
@@ -45,7 +57,7 @@ __global__ void __launch_bounds__(kThreads) k_msrsb(int n, int W, int B, const i
                                                     T *__restrict__ pout, const T *__restrict__ odiag,
                                                     unsigned long long *maxinc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    T inc = 0;
+    unsigned long long inck = 0ull;   // key of the largest |increment|
     if (i < n) {
         int ids[BM];
         T v[BM], acc[BM];
@@ -89,22 +101,22 @@ __global__ void __launch_bounds__(kThreads) k_msrsb(int n, int W, int B, const i
         for (int s = 0; s < BM; ++s) {
             if (ids[s] != kSlotPad) {
                 const T nv = acc[s] * rs;
-                inc = fmax(inc, fabs(nv - v[s]));
+                inck = max(inck, abs_key(nv - v[s]));
                 pout[(int64_t)s * n + i] = nv;
             }
         }
     }
-    // CTA max then one atomic per CTA
-    __shared__ double wmax[kThreads / 32];
-    double m = (double)inc;
+    // CTA max then one atomic per CTA (integer keys)
+    __shared__ unsigned long long wmax[kThreads / 32];
+    unsigned long long m = abs_key(key_value<T>(inck));   // key of the value as a double
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double mm = 0.0;
-        for (int q = 0; q < kThreads / 32; ++q) mm = fmax(mm, wmax[q]);
-        atomic_max_nonneg(maxinc, mm);
+        unsigned long long mm = 0ull;
+        for (int q = 0; q < kThreads / 32; ++q) mm = max(mm, wmax[q]);
+        atomicMax(maxinc, mm);
     }
 }
 
@@ -153,7 +165,7 @@ __global__ void __launch_bounds__(kThreads) k_msrsb_mapped(int n, int W, const i
                                                            const T *__restrict__ pin, T *__restrict__ pout,
                                                            const T *__restrict__ odiag, unsigned long long *maxinc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    T inc = 0;
+    unsigned long long inck = 0ull;   // key of the largest |increment|
     if (i < n) {
         const int cnt = nslots[i];
         T v[8], acc[8];
@@ -190,20 +202,20 @@ __global__ void __launch_bounds__(kThreads) k_msrsb_mapped(int n, int W, const i
         for (int s = 0; s < 8; ++s)
             if (s < cnt) {
                 const T nv = acc[s] * rs;
-                inc = fmax(inc, fabs(nv - v[s]));
+                inck = max(inck, abs_key(nv - v[s]));
                 pout[(int64_t)s * n + i] = nv;
             }
     }
-    __shared__ double wmax[kThreads / 32];
-    double m = (double)inc;
+    __shared__ unsigned long long wmax[kThreads / 32];
+    unsigned long long m = abs_key(key_value<T>(inck));   // key of the value as a double
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double mm = 0.0;
-        for (int q = 0; q < kThreads / 32; ++q) mm = fmax(mm, wmax[q]);
-        atomic_max_nonneg(maxinc, mm);
+        unsigned long long mm = 0ull;
+        for (int q = 0; q < kThreads / 32; ++q) mm = max(mm, wmax[q]);
+        atomicMax(maxinc, mm);
     }
 }
 

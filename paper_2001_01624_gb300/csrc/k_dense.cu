@@ -299,19 +299,31 @@ constexpr int kGJThreads = 512;
 constexpr int kGJRows = 8;     // rows of a block updated together (loads first)
 constexpr int kGJCols = 2;     // columns per thread and row in one pass
 
-__device__ __forceinline__ void gj_better(double &bv, int &bi, double v, int i) {
+// Pivot candidates compare |a_ik| through integer keys: the bit pattern of a
+// non-negative double (or float) orders like its value, so the search keeps
+// off the FP64 pipe, which is narrow on this part.  NaN counts as zero.
+__device__ __forceinline__ unsigned long long gj_key(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+    return b > 0x7ff0000000000000ull ? 0ull : b;
+}
+__device__ __forceinline__ unsigned long long gj_key(float x) {
+    const unsigned b = __float_as_uint(x) & 0x7fffffffu;
+    return b > 0x7f800000u ? 0ull : (unsigned long long)b;
+}
+
+__device__ __forceinline__ void gj_better(unsigned long long &bv, int &bi, unsigned long long v, int i) {
     if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
 }
 
 // Block-wide best candidate; every thread returns it.
-__device__ __forceinline__ void gj_block_best(double &bv, int &bi) {
-    __shared__ double s_v[kGJThreads / 32];
+__device__ __forceinline__ void gj_block_best(unsigned long long &bv, int &bi) {
+    __shared__ unsigned long long s_v[kGJThreads / 32];
     __shared__ int s_i[kGJThreads / 32];
-    __shared__ double s_bv;
+    __shared__ unsigned long long s_bv;
     __shared__ int s_bi;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const double v = __shfl_down_sync(0xffffffffu, bv, o);
+        const unsigned long long v = __shfl_down_sync(0xffffffffu, bv, o);
         const int i = __shfl_down_sync(0xffffffffu, bi, o);
         gj_better(bv, bi, v, i);
     }
@@ -319,7 +331,7 @@ __device__ __forceinline__ void gj_block_best(double &bv, int &bi) {
     if ((threadIdx.x & 31) == 0) { s_v[w] = bv; s_i[w] = bi; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double v = s_v[0];
+        unsigned long long v = s_v[0];
         int i = s_i[0];
         for (int q = 1; q < (int)(blockDim.x >> 5); ++q) gj_better(v, i, s_v[q], s_i[q]);
         s_bv = v;
@@ -332,17 +344,17 @@ __device__ __forceinline__ void gj_block_best(double &bv, int &bi) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kGJThreads, 1) k_gauss_jordan(int M, T *A0, T *A1, double *cand_v, int *cand_i,
+__global__ void __launch_bounds__(kGJThreads, 1) k_gauss_jordan(int M, T *A0, T *A1, unsigned long long *cand_v, int *cand_i,
                                                                 int *piv, unsigned long long *bar, int *err) {
     const int G = gridDim.x;
     GridSync gs;
     gs.begin(bar, err);
     // candidates of column 0 (parity 0)
     {
-        double bv = -1.0;
+        unsigned long long bv = 0ull;
         int bi = M;
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += G * blockDim.x)
-            gj_better(bv, bi, fabs((double)__ldcg(&A0[(int64_t)i * M])), i);
+            gj_better(bv, bi, gj_key(__ldcg(&A0[(int64_t)i * M])), i);
         gj_block_best(bv, bi);
         if (threadIdx.x == 0) { cand_v[blockIdx.x] = bv; cand_i[blockIdx.x] = bi; }
     }
@@ -350,12 +362,12 @@ __global__ void __launch_bounds__(kGJThreads, 1) k_gauss_jordan(int M, T *A0, T 
     T *cur = A0, *nxt = A1;
     for (int k = 0; k < M; ++k) {
         const int par = k & 1;
-        double bv = -1.0;
+        unsigned long long bv = 0ull;
         int bi = M;
         for (int t = threadIdx.x; t < G; t += blockDim.x)
             gj_better(bv, bi, __ldcg(&cand_v[par * G + t]), __ldcg(&cand_i[par * G + t]));
         gj_block_best(bv, bi);
-        const bool ok = bv > 0.0 && bi < M;
+        const bool ok = bv > 0ull && bi < M;
         const int p = ok ? bi : k;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             piv[k] = p;
@@ -363,7 +375,7 @@ __global__ void __launch_bounds__(kGJThreads, 1) k_gauss_jordan(int M, T *A0, T 
         }
         const T *prow = cur + (int64_t)p * M;
         const T inv = ok ? T(1) / __ldcg(&prow[k]) : T(0);
-        bv = -1.0;
+        bv = 0ull;
         bi = M;
         for (int i0 = blockIdx.x; i0 < M; i0 += kGJRows * G) {
             int src[kGJRows];
@@ -389,15 +401,15 @@ __global__ void __launch_bounds__(kGJThreads, 1) k_gauss_jordan(int M, T *A0, T 
                 for (int c = 0; c < kGJCols; ++c) {
                     const int j = j0 + c * blockDim.x;
                     if (j >= M) continue;
+                    const T sc = pr[c] * inv;           // the scaled pivot row, once per column
 #pragma unroll
                     for (int r = 0; r < kGJRows; ++r) {
                         if (src[r] < 0) continue;
                         const int i = i0 + r * G;
-                        T x;
-                        if (i == k) x = j == k ? inv : pr[c] * inv;
-                        else x = j == k ? -f[r] * inv : v[r][c] - f[r] * (pr[c] * inv);
+                        T x = i == k ? sc : v[r][c] - f[r] * sc;
+                        if (j == k) x = i == k ? inv : -f[r] * inv;   // the inverse's column k (one thread)
                         nxt[(int64_t)i * M + j] = x;
-                        if (j == k + 1 && i > k) gj_better(bv, bi, fabs((double)x), i);
+                        if (j == k + 1 && i > k) gj_better(bv, bi, gj_key(x), i);
                     }
                 }
             }

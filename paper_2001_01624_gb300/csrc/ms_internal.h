@@ -325,7 +325,7 @@ struct ms_coarse {
     msgb::DBuf<unsigned> fv_ch_cnt;
     int fv_n_chunks = 0;
     // Gauss-Jordan scratch (finite-volume stages)
-    msgb::DBuf<double> gj_cand_v;
+    msgb::DBuf<unsigned long long> gj_cand_v;   // pivot candidates as integer keys of |a_ik|
     msgb::DBuf<int> gj_cand_i, gj_piv, gj_idx;
     msgb::DBuf<unsigned long long> gj_bar;
 };
