@@ -53,9 +53,13 @@ __device__ __forceinline__ double key_value<float>(unsigned long long k) { retur
 template <typename T, int BM>
 __global__ void __launch_bounds__(kThreads) k_msrsb(int n, int W, int B, const int *__restrict__ col,
                                                     const T *__restrict__ off, const T *__restrict__ diag,
-                                                    const int *__restrict__ pid, const T *__restrict__ pin,
-                                                    T *__restrict__ pout, const T *__restrict__ odiag,
-                                                    unsigned long long *maxinc) {
+                                                    const int *__restrict__ pid, T *bufA, T *bufB,
+                                                    const T *__restrict__ odiag, unsigned long long *ctl) {
+    if (*(volatile const unsigned long long *)ctl) return;   // smoothing finished: no-op
+    const bool odd = ctl[1] & 1ull;                            // iterations done so far
+    const T *__restrict__ pin = odd ? bufB : bufA;
+    T *__restrict__ pout = odd ? bufA : bufB;
+    unsigned long long *maxinc = ctl + 2;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long inck = 0ull;   // key of the largest |increment|
     if (i < n) {
@@ -161,9 +165,14 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_msrsb_mapped(int n, int W, const int *__restrict__ col,
                                                            const T *__restrict__ off, const T *__restrict__ diag,
                                                            const unsigned *__restrict__ nmap,
-                                                           const unsigned char *__restrict__ nslots,
-                                                           const T *__restrict__ pin, T *__restrict__ pout,
-                                                           const T *__restrict__ odiag, unsigned long long *maxinc) {
+                                                           const unsigned char *__restrict__ nslots, T *bufA,
+                                                           T *bufB, const T *__restrict__ odiag,
+                                                           unsigned long long *ctl) {
+    if (*(volatile const unsigned long long *)ctl) return;   // smoothing finished: no-op
+    const bool odd = ctl[1] & 1ull;                            // iterations done so far
+    const T *__restrict__ pin = odd ? bufB : bufA;
+    T *__restrict__ pout = odd ? bufA : bufB;
+    unsigned long long *maxinc = ctl + 2;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long inck = 0ull;   // key of the largest |increment|
     if (i < n) {
@@ -217,6 +226,19 @@ __global__ void __launch_bounds__(kThreads) k_msrsb_mapped(int n, int W, const i
         for (int q = 0; q < kThreads / 32; ++q) mm = max(mm, wmax[q]);
         atomicMax(maxinc, mm);
     }
+}
+
+// After each smoothing iteration: count it, keep its largest increment
+// (ctl[3]) and stop once that is below tol, not a number, or the cap is
+// reached.  ctl = {stopped, iterations, running max key, last max key}.
+__global__ void k_smooth_control(unsigned long long *ctl, double tol, int max_iter) {
+    if (ctl[0]) return;
+    const unsigned long long it = ++ctl[1];
+    const unsigned long long key = ctl[2];
+    ctl[3] = key;
+    ctl[2] = 0ull;
+    const double inc = __longlong_as_double((long long)key);
+    if (inc < tol || inc != inc || it >= (unsigned long long)max_iter) ctl[0] = 1ull;   // converged, NaN or capped
 }
 
 template <typename T>
@@ -385,7 +407,7 @@ void launch_basis_init(ms_basis &b, int n, cudaStream_t st) {
 
 template <typename T>
 static void msrsb_dispatch(const ms_system &s, const ms_basis &b, const int *pid, const T *off, const T *diag,
-                           const T *pin, T *pout, const T *omega, unsigned long long *maxinc, cudaStream_t st) {
+                           T *pin, T *pout, const T *omega, unsigned long long *maxinc, cudaStream_t st) {
     const int g = blocks_for(s.n);
     const int B = b.B;
     if (b.has_map) {
@@ -394,7 +416,7 @@ static void msrsb_dispatch(const ms_system &s, const ms_basis &b, const int *pid
                         (double)s.n * (2 * sizeof(T) + 1) + (double)s.W * s.n * (4 + sizeof(T) + 4) +
                             (double)b.nnz * 2 * sizeof(T));
         k_msrsb_mapped<T><<<g, kThreads, 0, st>>>(s.n, s.W, s.col.p, off, diag, b.nmap.p, b.nslots.p, pin, pout,
-                                                  omega, maxinc);
+                                                  omega, maxinc);   // maxinc: the control block
         MS_CHECK_LAUNCH();
         return;
     }
@@ -424,16 +446,16 @@ void launch_basis_scale(const ms_system &s, ms_basis &b, bool fp32, cudaStream_t
     MS_CHECK_LAUNCH();
 }
 
-// One iteration; the new values end up in pval (buffers swapped).
-void launch_msrsb_iter(const ms_system &s, ms_basis &b, bool fp32, unsigned long long *maxinc, cudaStream_t st) {
-    if (fp32) {
-        msrsb_dispatch<float>(s, b, b.pid.p, s.off_u32.p, s.diag32.p, b.pval32.p, b.pval32_tmp.p, b.od32.p, maxinc,
-                              st);
-        std::swap(b.pval32.p, b.pval32_tmp.p);
-    } else {
-        msrsb_dispatch<double>(s, b, b.pid.p, s.off_u.p, s.diag.p, b.pval.p, b.pval_tmp.p, b.od64.p, maxinc, st);
-        std::swap(b.pval.p, b.pval_tmp.p);
-    }
+// One iteration under the device control block ctl (k_smooth_control after
+// it): reads pval / pval_tmp by the parity of the iterations done, and does
+// nothing once the smoothing has stopped.  The caller swaps the buffers when
+// an odd number of iterations ran.
+void launch_msrsb_iter(const ms_system &s, ms_basis &b, bool fp32, unsigned long long *ctl, double tol, int max_iter,
+                       cudaStream_t st) {
+    if (fp32) msrsb_dispatch<float>(s, b, b.pid.p, s.off_u32.p, s.diag32.p, b.pval32.p, b.pval32_tmp.p, b.od32.p, ctl, st);
+    else msrsb_dispatch<double>(s, b, b.pid.p, s.off_u.p, s.diag.p, b.pval.p, b.pval_tmp.p, b.od64.p, ctl, st);
+    k_smooth_control<<<1, 1, 0, st>>>(ctl, tol, max_iter);
+    MS_CHECK_LAUNCH();
 }
 
 // Column view values from the cell-major slots (and an FP64 copy of FP32

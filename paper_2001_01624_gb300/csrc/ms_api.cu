@@ -163,18 +163,30 @@ int smooth_basis(ms_ctx *ctx, ms_system &s, ms_basis &b, bool reset, double tol,
     double inc = 0.0;
     if (b.rule != MS_SUPPORT_BLOCK) {
         const bool fp32 = b.precision == MS_PREC_MIXED;
-        s.w_max.alloc(1);
+        // iterations are enqueued in batches; a control kernel after each one
+        // counts it and stops the rest on the device once converged, so the host
+        // reads the state once per batch instead of once per iteration
+        s.w_max.alloc(4);
         unsigned long long *h = (unsigned long long *)ctx->pinned.get(64);
-        if (max_iter > 0) launch_basis_scale(s, b, fp32, st);
-        while (it < max_iter) {
-            MS_CUDA(cudaMemsetAsync(s.w_max.p, 0, sizeof(unsigned long long), st));
-            launch_msrsb_iter(s, b, fp32, s.w_max.p, st);
-            MS_CUDA(cudaMemcpyAsync(h, s.w_max.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-            sync(st);
-            ++it;
-            std::memcpy(&inc, h, sizeof(double));
+        if (max_iter > 0) {
+            launch_basis_scale(s, b, fp32, st);
+            MS_CUDA(cudaMemsetAsync(s.w_max.p, 0, 4 * sizeof(unsigned long long), st));
+            constexpr int kBatch = 16;
+            for (int queued = 0; queued < max_iter;) {
+                const int k = std::min(kBatch, max_iter - queued);
+                for (int q = 0; q < k; ++q) launch_msrsb_iter(s, b, fp32, s.w_max.p, tol, max_iter, st);
+                queued += k;
+                MS_CUDA(cudaMemcpyAsync(h, s.w_max.p, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+                sync(st);
+                if (h[0]) break;
+            }
+            it = (int)h[1];
+            std::memcpy(&inc, &h[3], sizeof(double));
+            if (it & 1) {   // the result is in the other buffer
+                if (fp32) std::swap(b.pval32.p, b.pval32_tmp.p);
+                else std::swap(b.pval.p, b.pval_tmp.p);
+            }
             if (!(inc == inc)) throw Error{MS_ERR_INVALID_ARG, "basis smoothing produced NaN"};
-            if (inc < tol) break;
         }
     }
     b.iters = it;

@@ -426,7 +426,8 @@ void launch_ilu_lines32f(ms_system &s, const float *r, float *y, float *z, cudaS
 void launch_basis_init(ms_basis &b, int n, cudaStream_t st);
 void launch_basis_maps(const ms_system &s, ms_basis &b, cudaStream_t st);
 void launch_basis_scale(const ms_system &s, ms_basis &b, bool fp32, cudaStream_t st);
-void launch_msrsb_iter(const ms_system &s, ms_basis &b, bool fp32, unsigned long long *maxinc, cudaStream_t st);
+void launch_msrsb_iter(const ms_system &s, ms_basis &b, bool fp32, unsigned long long *ctl, double tol, int max_iter,
+                       cudaStream_t st);
 void launch_basis_columns(ms_basis &b, cudaStream_t st);
 // Galerkin
 int launch_ap_count(const ms_system &s, const ms_basis &b, int *cnt_max, int *host_pinned, cudaStream_t st);
