@@ -19,6 +19,10 @@ namespace {
 constexpr int kThreads = 256;
 
 inline int blocks_for(int64_t n, int t = kThreads) { return (int)((n + t - 1) / t); }
+// grid of the kernels that end in a deterministic block reduction: few enough
+// blocks that the last-block hand-off (one counter increment per block) stays
+// short, enough to keep every SM busy (4 per SM)
+inline int reduce_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(blocks_for(n), 4 * 152)); }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -139,19 +143,19 @@ __global__ void k_residual(int n, int W, const int *__restrict__ col, const doub
                            const double *__restrict__ diag, const double *__restrict__ q,
                            const double *__restrict__ x, double *__restrict__ r, float *__restrict__ r32,
                            double *red, unsigned int *cnt, double *norm_out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double ri = 0.0;
-    if (i < n) {
+    double ss = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double s = diag[i] * x[i];
         for (int w = 0; w < W; ++w) {
             const int64_t at = (int64_t)w * n + i;
             s += off[at] * x[col[at]];
         }
-        ri = q[i] - s;
+        const double ri = q[i] - s;
         r[i] = ri;
         if (r32) r32[i] = (float)ri;
+        ss += ri * ri;
     }
-    if (norm_out) finish_norm(block_sum(ri * ri), red, cnt, norm_out);
+    if (norm_out) finish_norm(block_sum(ss), red, cnt, norm_out);
 }
 
 // r -= A z ; x += z   (after a smoother correction z)
@@ -199,9 +203,12 @@ __global__ void k_jacobi32(int n, const double *__restrict__ r, const float *__r
 }
 
 __global__ void k_norm2(int n, const double *__restrict__ v, double *red, unsigned int *cnt, double *out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double a = i < n ? v[i] : 0.0;
-    finish_norm(block_sum(a * a), red, cnt, out);
+    double a = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double x = v[i];
+        a += x * x;
+    }
+    finish_norm(block_sum(a), red, cnt, out);
 }
 
 __global__ void k_sub(int n, const double *a, const double *b, double *c) {
@@ -313,8 +320,8 @@ void launch_spmv(const ms_system &s, const double *x, double *y, cudaStream_t st
 void launch_residual(const ms_system &s, const double *q, const double *x, double *r, double *red,
                      unsigned int *cnt, double *norm_out, cudaStream_t st, float *r32) {
     KernelScope ks_(st, "residual", (double)s.n * (8 + 8 + 8 + 8 + (r32 ? 4 : 0)) + (double)s.W * s.n * (4 + 8));
-    k_residual<<<blocks_for(s.n), kThreads, 0, st>>>(s.n, s.W, s.col.p, s.off_p.p, s.diag.p, q, x, r, r32, red, cnt,
-                                                      norm_out);
+    k_residual<<<reduce_grid(s.n), kThreads, 0, st>>>(s.n, s.W, s.col.p, s.off_p.p, s.diag.p, q, x, r, r32, red, cnt,
+                                                       norm_out);
     MS_CHECK_LAUNCH();
 }
 
@@ -508,7 +515,7 @@ void launch_scale(int n, const double *x, double a, double *y, cudaStream_t st) 
 
 void launch_norm2(const double *v, int n, double *red, unsigned int *cnt, double *out, cudaStream_t st) {
     KernelScope ks_(st, "norm2", (double)n * 8);
-    k_norm2<<<blocks_for(n), kThreads, 0, st>>>(n, v, red, cnt, out);
+    k_norm2<<<reduce_grid(n), kThreads, 0, st>>>(n, v, red, cnt, out);
     MS_CHECK_LAUNCH();
 }
 
