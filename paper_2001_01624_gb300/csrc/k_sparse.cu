@@ -419,13 +419,22 @@ __global__ void __launch_bounds__(256) k_multidot8(int n, int k, const double *_
     double acc[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) acc[i] = 0.0;
-    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
-        const double wl = __ldg(w + l);
-        double vv[8];
+    if (kk == 8) {
+        for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
+            const double wl = __ldg(w + l);
+            double vv[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) vv[i] = i < kk ? __ldcs(V + (int64_t)(i0 + i) * n + l) : 0.0;
+            for (int i = 0; i < 8; ++i) vv[i] = __ldcs(V + (int64_t)(i0 + i) * n + l);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) acc[i] += vv[i] * wl;
+            for (int i = 0; i < 8; ++i) acc[i] += vv[i] * wl;
+        }
+    } else {   // the last group: no multiply-adds for absent vectors (FP64 is the scarce pipe)
+        for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
+            const double wl = __ldg(w + l);
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (i < kk) acc[i] += __ldcs(V + (int64_t)(i0 + i) * n + l) * wl;
+        }
     }
     __shared__ double part[8][8];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
