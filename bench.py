@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--profile-ilu", type=int, default=0,
                     help="only assemble the c2 system and apply ILU(0) N times in each precision (for ncu captures)")
     ap.add_argument("--nz", type=int, default=85, help="--profile-ilu: layers of the 60x220 grid")
+    ap.add_argument("--profile-coarse", action="store_true",
+                    help="only form the finite-volume coarse operator of the 60x220x85 geomodel (Gauss-Jordan "
+                         "inverse; for ncu captures)")
     ap.add_argument("--workload", choices=["c2", "ensemble", "serving", "coupling"], default="c2",
                     help="c2: the 60x220x85 geomodel (headline); ensemble: the batched uneven ensemble; "
                          "serving: Poisson stream of two-phase time steps on resident geomodels; coupling: "
@@ -577,6 +580,31 @@ def run_profile_ilu(args):
     return 0
 
 
+def run_profile_coarse(args):
+    """The finite-volume coarse stage of the 60x220x85 geomodel alone (untimed)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2001_01624_gb300 as ms
+    from paper_2001_01624_gb300 import geomodel as G
+    dev = torch.device("cuda:0")
+    gm = G.config2(0)
+    stream = torch.cuda.Stream(dev)
+    ctx = ms.ms_create(0, stream)
+    s = ms.ms_system_create(ctx, gm.grid, 0)
+    with torch.cuda.stream(stream):
+        ms.ms_assemble_tpfa(ctx, s, torch.from_numpy(gm.perm.ravel().copy()).to(dev))
+        part, M = ms.ms_partition_cartesian(ctx, s, gm.block)
+        b, _ = ms.ms_build_basis(ctx, s, part, M, block=gm.block)
+        c = ms.ms_coarse_create(ctx, s, b, ms.MS_PREC_FP64, ms.MS_RESTRICT_FV)
+    torch.cuda.synchronize()
+    ms.ms_coarse_release(c)
+    ms.ms_basis_release(b)
+    ms.ms_system_release(s)
+    ms.ms_destroy(ctx)
+    return 0
+
+
 def run_coupling(args):
     """Coupling-strength study (dynamic bases against the viscosity ratio):
     average Richardson cycles per pressure solve for the general stage alone,
@@ -619,6 +647,8 @@ def main():
         return run_reference(args)
     if args.profile_ilu:
         return run_profile_ilu(args)
+    if args.profile_coarse:
+        return run_profile_coarse(args)
     if args.workload == "ensemble":
         return run_ensemble(args)
     if args.workload == "serving":
