@@ -31,6 +31,8 @@ import sys
 import threading
 import time
 
+from paper_2001_01624_gb300 import replicas as R
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -287,9 +289,7 @@ def timed_steps(torch, plan, stream, K, dist, world, outer="gmres", coarse=None)
     torch.cuda.synchronize()
     ms_tot = e0.elapsed_time(e1)
     if world > 1:
-        t = torch.tensor([ms_tot], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_tot = float(t.item())
+        ms_tot = R.max_over_ranks(dist, [ms_tot], "cuda")[0]
         dist.barrier()
     return ms_tot, infos
 
@@ -325,8 +325,8 @@ def run_ensemble(args):
     ctx = ms.ms_create(local, stream)
     prec = ms.MS_PREC_MIXED
     mem = []
-    for k in range(args.members):
-        gm = G.ensemble_member(rank * args.members + k)
+    for m in R.member_indices(rank, args.members):
+        gm = G.ensemble_member(m)
         s = ms.ms_system_create(ctx, gm.grid, 0)
         ms.ms_assemble_tpfa(ctx, s, torch.from_numpy(gm.perm.ravel().copy()).to(dev))
         part, M = ms.ms_partition_cartesian(ctx, s, gm.block)
@@ -352,9 +352,7 @@ def run_ensemble(args):
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1)
         if world > 1:
-            tt = torch.tensor([t], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
+            t = R.max_over_ranks(dist, [t], dev)[0]
         return t, outs[-1]
 
     for _ in range(args.warmup):
@@ -476,7 +474,7 @@ def run_serving(args):
         dist.barrier()
     import paper_2001_01624_gb300 as ms
     from paper_2001_01624_gb300 import serve
-    models = serving_models(args.models, torch, dev, seed=rank)
+    models = serving_models(args.models, torch, dev, seed=R.serving_seed(rank))
 
     def dt_of(mid):
         m = models[mid]
@@ -493,9 +491,7 @@ def run_serving(args):
     launches = ms.ms_profile_read()["_total_launches"]
     st = serve.latency_stats(reqs)
     if world > 1:
-        t = torch.tensor([st["p99_ms"], st["p50_ms"]], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        st["p99_ms"], st["p50_ms"] = float(t[0]), float(t[1])
+        st["p99_ms"], st["p50_ms"] = R.max_over_ranks(dist, [st["p99_ms"], st["p50_ms"]], dev)
     cells = sum(models[r.model].n for r in reqs)
     span = max(r.done for r in reqs) - min(r.arrival for r in reqs)
     line = {"metric": "p99 request latency (serving: arrival to result on the host)", "value": st["p99_ms"],
@@ -672,7 +668,7 @@ def main():
     import paper_2001_01624_gb300 as ms
     from paper_2001_01624_gb300 import geomodel as G
 
-    gm = G.config2(rank)
+    gm = G.config2(R.geomodel_seed(rank))
     stream = torch.cuda.Stream(dev)
     ctx = ms.ms_create(local, stream)
     precs = [ms.MS_PREC_FP64] + ([] if args.no_mixed else [ms.MS_PREC_MIXED])
@@ -897,9 +893,7 @@ def main():
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         if world > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+            e2e_s = R.max_over_ranks(dist, [e2e_s], dev)[0]
         line["e2e"] = {"value": n * K * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(perm_h.nbytes + q_h.nbytes),
                        "d2h_bytes_per_step": int(p_h.nbytes), "ms_per_step": 1e3 * e2e_s / K}
 
