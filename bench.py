@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-cpr", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run N extra untimed steps only (for ncu launch lists)")
+    ap.add_argument("--profile-mixed", action="store_true",
+                    help="with --profile-steps: the mixed-precision plan only")
     ap.add_argument("--profile-ilu", type=int, default=0,
                     help="only assemble the c2 system and apply ILU(0) N times in each precision (for ncu captures)")
     ap.add_argument("--nz", type=int, default=85, help="--profile-ilu: layers of the 60x220 grid")
@@ -671,6 +673,12 @@ def main():
     gm = G.config2(R.geomodel_seed(rank))
     stream = torch.cuda.Stream(dev)
     ctx = ms.ms_create(local, stream)
+    if args.profile_steps and args.profile_mixed:
+        plan = Plan(ms, ctx, gm, ms.MS_PREC_MIXED, dev, torch)
+        for _ in range(args.profile_steps):
+            plan.step()
+        torch.cuda.synchronize()
+        return 0
     precs = [ms.MS_PREC_FP64] + ([] if args.no_mixed else [ms.MS_PREC_MIXED])
     plans = {p: Plan(ms, ctx, gm, p, dev, torch) for p in precs}
     n = plans[ms.MS_PREC_FP64].n

@@ -161,7 +161,7 @@ __global__ void k_basis_maps(int n, int W, int B, const int *__restrict__ col, c
 
 // MsRSB iteration with precomputed neighbour slot maps (B <= 8): every
 // neighbour contribution is an independent load.
-template <typename T>
+template <typename T, int WM>
 __global__ void __launch_bounds__(kThreads) k_msrsb_mapped(int n, int W, const int *__restrict__ col,
                                                            const T *__restrict__ off, const T *__restrict__ diag,
                                                            const unsigned *__restrict__ nmap,
@@ -184,16 +184,41 @@ __global__ void __launch_bounds__(kThreads) k_msrsb_mapped(int n, int W, const i
             v[s] = s < cnt ? pin[(int64_t)s * n + i] : T(0);
             acc[s] = d * v[s];
         }
-        for (int w = 0; w < W; ++w) {
-            const int64_t at = (int64_t)w * n + i;
-            const int k = col[at];
-            if (k == i) continue;
-            const T a = off[at];
-            const unsigned m = nmap[at];
+        if (WM > 0) {
+            // at most WM connections: every connection's column, coefficient and
+            // slot map are loaded first, then all the gathers, so the loads of
+            // different neighbours overlap (same order of the sums as below)
+            int kk[WM > 0 ? WM : 1];
+            T aw[WM > 0 ? WM : 1];
+            unsigned mw[WM > 0 ? WM : 1];
 #pragma unroll
-            for (int s = 0; s < 8; ++s) {
-                const unsigned t = (m >> (4 * s)) & 15u;
-                if (s < cnt && t != 15u) acc[s] += a * pin[(int64_t)t * n + k];
+            for (int w = 0; w < WM; ++w) {
+                const int64_t at = (int64_t)w * n + i;
+                kk[w] = w < W ? col[at] : i;
+                aw[w] = w < W ? off[at] : T(0);
+                mw[w] = w < W ? nmap[at] : 0xffffffffu;
+            }
+#pragma unroll
+            for (int w = 0; w < WM; ++w) {
+                if (kk[w] == i) continue;
+#pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    const unsigned t = (mw[w] >> (4 * s)) & 15u;
+                    if (s < cnt && t != 15u) acc[s] += aw[w] * pin[(int64_t)t * n + kk[w]];
+                }
+            }
+        } else {
+            for (int w = 0; w < W; ++w) {
+                const int64_t at = (int64_t)w * n + i;
+                const int k = col[at];
+                if (k == i) continue;
+                const T a = off[at];
+                const unsigned m = nmap[at];
+#pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    const unsigned t = (m >> (4 * s)) & 15u;
+                    if (s < cnt && t != 15u) acc[s] += a * pin[(int64_t)t * n + k];
+                }
             }
         }
         // omega / A_ii precomputed per smoothing run; one division for the
@@ -415,8 +440,19 @@ static void msrsb_dispatch(const ms_system &s, const ms_basis &b, const int *pid
         KernelScope ks_(st, sizeof(T) == 8 ? "msrsb" : "msrsb32",
                         (double)s.n * (2 * sizeof(T) + 1) + (double)s.W * s.n * (4 + sizeof(T) + 4) +
                             (double)b.nnz * 2 * sizeof(T));
-        k_msrsb_mapped<T><<<g, kThreads, 0, st>>>(s.n, s.W, s.col.p, off, diag, b.nmap.p, b.nslots.p, pin, pout,
-                                                  omega, maxinc);   // maxinc: the control block
+        // maxinc: the control block
+        if (s.W <= 4)
+            k_msrsb_mapped<T, 4><<<g, kThreads, 0, st>>>(s.n, s.W, s.col.p, off, diag, b.nmap.p, b.nslots.p, pin,
+                                                         pout, omega, maxinc);
+        else if (s.W <= 6)
+            k_msrsb_mapped<T, 6><<<g, kThreads, 0, st>>>(s.n, s.W, s.col.p, off, diag, b.nmap.p, b.nslots.p, pin,
+                                                         pout, omega, maxinc);
+        else if (s.W <= 8)
+            k_msrsb_mapped<T, 8><<<g, kThreads, 0, st>>>(s.n, s.W, s.col.p, off, diag, b.nmap.p, b.nslots.p, pin,
+                                                         pout, omega, maxinc);
+        else
+            k_msrsb_mapped<T, 0><<<g, kThreads, 0, st>>>(s.n, s.W, s.col.p, off, diag, b.nmap.p, b.nslots.p, pin,
+                                                         pout, omega, maxinc);
         MS_CHECK_LAUNCH();
         return;
     }
