@@ -271,18 +271,33 @@ __global__ void k_restrict_ch(int nch, const int *__restrict__ ch_beg, const int
     }
 }
 
-// x_i += sum_s P_{i,s} x_c[block(s)]
-template <typename TV, typename TC>
+// x_i += sum_s P_{i,s} x_c[block(s)]; BM bounds the slots so that every
+// slot's block id and value load before the gathers (padding slots come last)
+template <typename TV, typename TC, int BM>
 __global__ void k_prolong(int n, int B, const int *__restrict__ pid, const TV *__restrict__ pval,
                           const TC *__restrict__ xc, double *__restrict__ x) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     TC s = 0;
-    for (int t = 0; t < B; ++t) {
-        const int64_t at = (int64_t)t * n + i;
-        const int j = pid[at];
-        if (j == kSlotPad) break;
-        s += (TC)pval[at] * xc[j];
+    if (BM > 0) {
+        int j[BM > 0 ? BM : 1];
+        TV pv[BM > 0 ? BM : 1];
+#pragma unroll
+        for (int t = 0; t < BM; ++t) {
+            const int64_t at = (int64_t)t * n + i;
+            j[t] = t < B ? pid[at] : kSlotPad;
+            pv[t] = t < B ? pval[at] : TV(0);
+        }
+#pragma unroll
+        for (int t = 0; t < BM; ++t)
+            if (j[t] != kSlotPad) s += (TC)pv[t] * xc[j[t]];
+    } else {
+        for (int t = 0; t < B; ++t) {
+            const int64_t at = (int64_t)t * n + i;
+            const int jj = pid[at];
+            if (jj == kSlotPad) break;
+            s += (TC)pval[at] * xc[jj];
+        }
     }
     x[i] += (double)s;
 }
@@ -613,13 +628,15 @@ RestrictView restrict_view(const ms_coarse &c) {
 
 void launch_prolong(const ms_basis &b, int n, const double *xc, double *x, cudaStream_t st) {
     KernelScope ks_(st, "prolong", (double)b.B * n * (4 + 8) + (double)b.M * 8 + (double)n * 16);
-    k_prolong<double, double><<<blocks_for(n), kThreads, 0, st>>>(n, b.B, b.pid.p, b.pval.p, xc, x);
+    if (b.B <= 8) k_prolong<double, double, 8><<<blocks_for(n), kThreads, 0, st>>>(n, b.B, b.pid.p, b.pval.p, xc, x);
+    else k_prolong<double, double, 0><<<blocks_for(n), kThreads, 0, st>>>(n, b.B, b.pid.p, b.pval.p, xc, x);
     MS_CHECK_LAUNCH();
 }
 
 void launch_prolong32(const ms_basis &b, int n, const float *xc, double *x, cudaStream_t st) {
     KernelScope ks_(st, "prolong32", (double)b.B * n * (4 + 4) + (double)b.M * 4 + (double)n * 16);
-    k_prolong<float, float><<<blocks_for(n), kThreads, 0, st>>>(n, b.B, b.pid.p, b.pval32.p, xc, x);
+    if (b.B <= 8) k_prolong<float, float, 8><<<blocks_for(n), kThreads, 0, st>>>(n, b.B, b.pid.p, b.pval32.p, xc, x);
+    else k_prolong<float, float, 0><<<blocks_for(n), kThreads, 0, st>>>(n, b.B, b.pid.p, b.pval32.p, xc, x);
     MS_CHECK_LAUNCH();
 }
 
