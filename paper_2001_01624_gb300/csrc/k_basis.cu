@@ -162,7 +162,7 @@ __global__ void k_basis_maps(int n, int W, int B, const int *__restrict__ col, c
 // MsRSB iteration with precomputed neighbour slot maps (B <= 8): every
 // neighbour contribution is an independent load.
 template <typename T, int WM>
-__global__ void __launch_bounds__(kThreads) k_msrsb_mapped(int n, int W, const int *__restrict__ col,
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 3) k_msrsb_mapped(int n, int W, const int *__restrict__ col,
                                                            const T *__restrict__ off, const T *__restrict__ diag,
                                                            const unsigned *__restrict__ nmap,
                                                            const unsigned char *__restrict__ nslots, T *bufA,
