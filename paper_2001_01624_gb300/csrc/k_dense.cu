@@ -33,9 +33,13 @@ template <>
 __device__ __forceinline__ float dsqrt<float>(float v) { return sqrtf(v); }
 
 // Factor the diagonal block A[k0:k0+nb, k0:k0+nb] in place (lower).
+// FP64 latency and throughput are scarce on this part: the kernels below
+// divide once per pivot (its reciprocal, kept in shared memory) and multiply
+// elsewhere.
 template <typename T>
 __global__ void k_potrf_diag(T *A, int M, int k0, int nb, int *err) {
     __shared__ T a[NB][NB + 1];
+    __shared__ T rp;
     const int r = threadIdx.y, c = threadIdx.x;
     if (r < nb && c <= r) a[r][c] = A[(int64_t)(k0 + r) * M + k0 + c];
     for (int p = 0; p < nb; ++p) {
@@ -46,10 +50,12 @@ __global__ void k_potrf_diag(T *A, int M, int k0, int nb, int *err) {
                 atomicOr(err, kErrSingular);
                 d = T(1);
             }
-            a[p][p] = dsqrt<T>(d);
+            const T sd = dsqrt<T>(d);
+            a[p][p] = sd;
+            rp = T(1) / sd;
         }
         __syncthreads();
-        if (c == p && r > p && r < nb) a[r][p] /= a[p][p];
+        if (c == p && r > p && r < nb) a[r][p] *= rp;
         __syncthreads();
         if (r > p && r < nb && c > p && c <= r) a[r][c] -= a[r][p] * a[c][p];
     }
@@ -57,28 +63,37 @@ __global__ void k_potrf_diag(T *A, int M, int k0, int nb, int *err) {
     if (r < nb && c <= r) A[(int64_t)(k0 + r) * M + k0 + c] = a[r][c];
 }
 
-// Rows below the diagonal block: L_rk = A_rk L_kk^{-T}.  One warp per row
-// (lanes hold the 32 panel entries), 8 rows per CTA.
+// Rows below the diagonal block: L_rk = A_rk L_kk^{-T}, one thread per row by
+// forward substitution (x_c = (a_c - sum_{p<c} x_p L_cp) / L_cc).
 template <typename T>
 __global__ void k_trsm_panel(T *A, int M, int k0, int nb) {
     __shared__ T L[NB][NB + 1];
+    __shared__ T rd[NB];
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
         const int r = e / NB, c = e % NB;
         L[r][c] = (r < nb && c <= r) ? A[(int64_t)(k0 + r) * M + k0 + c] : T(0);
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int row = k0 + nb + blockIdx.x * (blockDim.x >> 5) + w;
+    if (threadIdx.x < NB) rd[threadIdx.x] = threadIdx.x < nb ? T(1) / L[threadIdx.x][threadIdx.x] : T(0);
+    __syncthreads();
+    const int row = k0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= M) return;
-    T x = lane < nb ? A[(int64_t)row * M + k0 + lane] : T(0);
-    for (int c = 0; c < nb; ++c) {
-        // x_c = (a_c - sum_{p<c} x_p L_cp) / L_cc   (x_p already final for p < c)
-        T s = lane < c ? x * L[c][lane] : T(0);
+    T *a = A + (int64_t)row * M + k0;
+    T x[NB];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == c) x = (x - s) / L[c][c];
+    for (int c = 0; c < NB; ++c) x[c] = c < nb ? a[c] : T(0);
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+        if (c < nb) {
+            T s = x[c];
+#pragma unroll
+            for (int p = 0; p < c; ++p) s -= x[p] * L[c][p];
+            x[c] = s * rd[c];
+        }
     }
-    if (lane < nb) A[(int64_t)row * M + k0 + lane] = x;
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+        if (c < nb) a[c] = x[c];
 }
 
 // Trailing update of the lower triangle: A_ij -= sum_p L_ip L_jp over the panel.
@@ -111,10 +126,13 @@ __global__ void k_syrk(T *A, int M, int k0, int nb) {
 template <typename T>
 __global__ void k_trsm_rows(const T *L, T *Y, int M, int k0, int nb) {
     __shared__ T Lk[NB][NB + 1];
+    __shared__ T rd[NB];
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
         const int r = e / NB, c = e % NB;
         Lk[r][c] = (r < nb && c <= r) ? L[(int64_t)(k0 + r) * M + k0 + c] : T(0);
     }
+    __syncthreads();
+    if (threadIdx.x < NB) rd[threadIdx.x] = threadIdx.x < nb ? T(1) / Lk[threadIdx.x][threadIdx.x] : T(0);
     __syncthreads();
     const int cidx = blockIdx.x * blockDim.x + threadIdx.x;
     if (cidx >= k0 + nb) return;
@@ -127,7 +145,7 @@ __global__ void k_trsm_rows(const T *L, T *Y, int M, int k0, int nb) {
             T s = x[r];
 #pragma unroll
             for (int p = 0; p < r; ++p) s -= Lk[r][p] * x[p];
-            x[r] = s / Lk[r][r];
+            x[r] = s * rd[r];
         }
     }
 #pragma unroll
@@ -495,7 +513,7 @@ void factor_inverse(T *A, T *Y, T *X, int M, int *err, cudaStream_t st) {
         k_potrf_diag<T><<<1, tile, 0, st>>>(A, M, k0, nb, err);
         const int rest = M - k0 - nb;
         if (rest > 0) {
-            k_trsm_panel<T><<<(rest + 7) / 8, 256, 0, st>>>(A, M, k0, nb);
+            k_trsm_panel<T><<<(rest + 127) / 128, 128, 0, st>>>(A, M, k0, nb);
             const int t = (rest + NB - 1) / NB;
             k_syrk<T><<<t * (t + 1) / 2, tile, 0, st>>>(A, M, k0, nb);
         }
