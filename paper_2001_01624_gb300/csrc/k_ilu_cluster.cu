@@ -117,8 +117,8 @@ __device__ __forceinline__ void st_async2(unsigned addr, double a, double b, uns
 // Rows handed across a cluster boundary go through global memory: each value
 // as 8-byte words that carry the launch's tag in their upper half (FP32: the
 // value's bits; FP64: its low and high halves), one slot per line, written once
-// per launch, so no slot is reused within a launch and a reader knows a value
-// is there when its tag is.
+// per launch, so no slot is reused within a launch and a reader (the relay
+// warp) knows a value is there when its tag is.
 __device__ __forceinline__ void ring_put(unsigned long long *w, float v, unsigned tag) {
     *(volatile unsigned long long *)w = (unsigned long long)__float_as_uint(v) | ((unsigned long long)tag << 32);
 }
@@ -126,20 +126,6 @@ __device__ __forceinline__ void ring_put(unsigned long long *w, double v, unsign
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     *(volatile unsigned long long *)w = (b & 0xffffffffull) | ((unsigned long long)tag << 32);
     *(volatile unsigned long long *)(w + 1) = (b >> 32) | ((unsigned long long)tag << 32);
-}
-// the word once it carries tag (bounded: false after the wait limit)
-__device__ __forceinline__ bool ring_word(const unsigned long long *w, unsigned tag, unsigned &out, int *err);
-__device__ __forceinline__ bool ring_get(const unsigned long long *w, unsigned tag, float &v, int *err) {
-    unsigned a;
-    if (!ring_word(w, tag, a, err)) return false;
-    v = __uint_as_float(a);
-    return true;
-}
-__device__ __forceinline__ bool ring_get(const unsigned long long *w, unsigned tag, double &v, int *err) {
-    unsigned lo, hi;
-    if (!ring_word(w, tag, lo, err) || !ring_word(w + 1, tag, hi, err)) return false;
-    v = __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
-    return true;
 }
 template <typename T>
 __host__ __device__ constexpr int ring_words() { return sizeof(T) == 8 ? 2 : 1; }
@@ -196,25 +182,6 @@ __device__ __forceinline__ bool wait_lane(unsigned bar, unsigned parity, int *er
             }
         }
     }
-    return true;
-}
-
-__device__ __forceinline__ bool ring_word(const unsigned long long *w, unsigned tag, unsigned &out, int *err) {
-    unsigned long long v = *(const volatile unsigned long long *)w;
-    unsigned long long t0 = 0;
-    int spins = 0;
-    while ((unsigned)(v >> 32) != tag) {
-        if ((++spins & 63) == 0) {
-            const unsigned long long now = global_ns();
-            if (t0 == 0) t0 = now;
-            else if (now - t0 > kWaitNs) {
-                atomicOr(err, kErrTimeout);
-                return false;
-            }
-        }
-        v = *(const volatile unsigned long long *)w;
-    }
-    out = (unsigned)(v & 0xffffffffull);
     return true;
 }
 
