@@ -274,6 +274,313 @@ __global__ void __launch_bounds__(kLevelThreads) k_level_sweep(int n, int W, int
     }
 }
 
+// Segment dataflow sweeps for any grid.  The rows are cut into segments: runs
+// of consecutive rows whose only coupling inside the run is the chain (i-1, i)
+// (the x-lines of the natural order, cut at inactive cells, at faults that
+// couple rows of one line, and every kSegMax rows).  One warp solves one
+// segment.  It forms B_i = r_i minus the couplings that leave the segment, then
+// solves the chain y_i = B_i + a_i y_{i-1} (a_i = -l_{i,i-1}; backward
+// z_i = d_i (y_i - sum_j u_ij z_j) + a_i z_{i+1}, a_i = -d_i u_{i,i+1}, d_i = 1/u_ii)
+// by composing the affine maps of each lane's run of rows and scanning the
+// compositions across the warp.  Warps take segments one ticket at a time in
+// the order of their wavefront levels and stage what does not depend on the
+// sweep (right-hand side, chain and coupling values) in shared memory.  Every
+// result is also published as tagged 64-bit words (the sweep counter sync[0]
+// in the high half, the value's bits in the low half: one word per FP32 value,
+// two per FP64 value), so a warp polls the very values it gathers, without
+// flags or fences.  A segment only gathers from segments handed out before
+// it, so the sweep cannot deadlock and needs no grid-wide barrier; every wait
+// is bounded.  Tickets come from sync[1]; sweep_end resets it and advances the
+// sweep counter.
+constexpr int kSegThreads = 64;          // two warps, one segment each at a time
+constexpr int kSegPer = kSegMax / 32;    // rows per lane
+
+__device__ __forceinline__ void ld_relaxed_v2(const unsigned long long *p, unsigned long long &a,
+                                              unsigned long long &b) {
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_v2(unsigned long long *p, unsigned long long a, unsigned long long b) {
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Tagged words of row j (FP64: two words, low and high halves of the value).
+template <typename T>
+struct SegWord {
+    unsigned long long lo, hi;
+};
+
+template <typename T>
+__device__ __forceinline__ SegWord<T> seg_load(const unsigned long long *tw, int j) {
+    SegWord<T> w;
+    if constexpr (sizeof(T) == 8) {
+        w.lo = ld_relaxed_u64(tw + 2 * (size_t)j);
+        w.hi = ld_relaxed_u64(tw + 2 * (size_t)j + 1);
+    } else {
+        w.lo = ld_relaxed_u64(tw + j);
+        w.hi = 0;
+    }
+    return w;
+}
+
+// True, with the value, once the words carry tag tg.
+template <typename T>
+__device__ __forceinline__ bool seg_check(const SegWord<T> &w, unsigned tg, T &x) {
+    if constexpr (sizeof(T) == 8) {
+        if ((unsigned)(w.lo >> 32) != tg || (unsigned)(w.hi >> 32) != tg) return false;
+        x = __hiloint2double((int)(unsigned)w.hi, (int)(unsigned)w.lo);
+    } else {
+        if ((unsigned)(w.lo >> 32) != tg) return false;
+        x = __uint_as_float((unsigned)w.lo);
+    }
+    return true;
+}
+
+template <typename T>
+__device__ __forceinline__ void seg_publish(unsigned long long *tw, int i, unsigned tg, T v) {
+    const unsigned long long hi = (unsigned long long)tg << 32;
+    if constexpr (sizeof(T) == 8) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        st_relaxed_u64(tw + 2 * (size_t)i, hi | (b & 0xffffffffull));
+        st_relaxed_u64(tw + 2 * (size_t)i + 1, hi | (b >> 32));
+    } else {
+        st_relaxed_u64(tw + i, hi | __float_as_uint(v));
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T seg_fma(T a, T b, T c) {
+    if constexpr (sizeof(T) == 4) return fmaf(a, b, c);
+    else return fma(a, b, c);
+}
+
+// Shared memory of one warp: B, a, d, then KG coupling values and KG columns.
+template <typename T, int KG>
+__host__ __device__ constexpr size_t seg_smem_warp() {
+    return (size_t)kSegMax * ((3 + KG) * sizeof(T) + KG * sizeof(int));
+}
+
+template <typename T, typename TR, bool BWD, int KG>
+__global__ void __launch_bounds__(kSegThreads) k_seg_sweep(int n, int nseg, int kg, const int *__restrict__ seg_off,
+                                                           const int *__restrict__ order, const T *__restrict__ ca,
+                                                           const int *__restrict__ gcol,
+                                                           const T *__restrict__ gval,
+                                                           const T *__restrict__ dinv,
+                                                           const TR *__restrict__ rhs, T *__restrict__ out,
+                                                           unsigned long long *tw, int *sync) {
+    extern __shared__ __align__(16) unsigned char seg_smem[];
+    const int lane = threadIdx.x & 31;
+    T *sb = (T *)(seg_smem + (threadIdx.x >> 5) * seg_smem_warp<T, KG>());
+    T *sa = sb + kSegMax;
+    T *sd = sa + kSegMax;
+    T *sv = sd + kSegMax;                       // [KG][kSegMax]
+    int *sc = (int *)(sv + KG * kSegMax);       // [KG][kSegMax]
+    __shared__ int s_tgt;
+    if (threadIdx.x == 0) s_tgt = *((volatile int *)&sync[0]) + 1;
+    __syncthreads();
+    const unsigned tg = (unsigned)s_tgt;
+    bool failed = false;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(&sync[1], 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= nseg) break;
+        const int S = order[t];
+        const int s0 = seg_off[S], len = seg_off[S + 1] - s0;
+        // stage what does not depend on the sweep
+#pragma unroll
+        for (int c = 0; c < kSegPer; ++c) {
+            const int p = c * 32 + lane;
+            if (p < len) {
+                const int i = s0 + p;
+                sb[p] = (T)rhs[i];
+                sa[p] = ca[i];
+                if (BWD) sd[p] = dinv[i];
+#pragma unroll
+                for (int q = 0; q < KG; ++q)
+                    if (q < kg) {
+                        sc[q * kSegMax + p] = gcol[(int64_t)q * n + i];
+                        sv[q * kSegMax + p] = gval[(int64_t)q * n + i];
+                    }
+            }
+        }
+        // couplings leaving the segment, in slot order, by groups of four: poll
+        // the tagged words of every coupling of the group until all carry this
+        // sweep's tag, then subtract the products
+#pragma unroll
+        for (int q0 = 0; q0 < KG; q0 += 4) {
+            T xv[kSegPer][4];
+            int jv[kSegPer][4];
+            unsigned pend = 0u;
+#pragma unroll
+            for (int c = 0; c < kSegPer; ++c)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = q0 + u, p = c * 32 + lane;
+                    jv[c][u] = (q < KG && q < kg && p < len) ? sc[q * kSegMax + p] : -1;
+                    xv[c][u] = T(0);
+                    if (jv[c][u] >= 0) pend |= 1u << (c * 4 + u);
+                }
+            unsigned long long t0 = 0;
+            for (int spins = 0; pend && !failed; ++spins) {
+                // all loads of the round first, then the tag checks
+                SegWord<T> wv[kSegPer][4];
+#pragma unroll
+                for (int c = 0; c < kSegPer; ++c)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if ((pend >> (c * 4 + u)) & 1u) wv[c][u] = seg_load<T>(tw, jv[c][u]);
+                const unsigned was = pend;
+#pragma unroll
+                for (int c = 0; c < kSegPer; ++c)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if ((was >> (c * 4 + u)) & 1u)
+                            if (seg_check<T>(wv[c][u], tg, xv[c][u])) pend &= ~(1u << (c * 4 + u));
+                if (!pend) break;
+                if (spins > 8) __nanosleep(32);
+                if ((spins & 31) == 31) {
+                    if (*((volatile int *)&sync[3]) != 0) failed = true;
+                    const unsigned long long now = gs_now_ns();
+                    if (t0 == 0) t0 = now;
+                    else if (now - t0 > 2000000000ull) {
+                        atomicOr(&sync[3], kErrTimeout);
+                        failed = true;
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < kSegPer; ++c) {
+                const int p = c * 32 + lane;
+                if (p < len) {
+                    T s = sb[p];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (q0 + u < KG && q0 + u < kg) s -= sv[(q0 + u) * kSegMax + p] * xv[c][u];
+                    sb[p] = s;
+                }
+            }
+        }
+        if (BWD) {
+#pragma unroll
+            for (int c = 0; c < kSegPer; ++c) {
+                const int p = c * 32 + lane;
+                if (p < len) sb[p] *= sd[p];
+            }
+        }
+        __syncwarp();
+        // each lane's run of rows: compose its maps, scan the compositions
+        // across the warp, apply
+        const int C = (len + 31) >> 5;
+        const int lo = lane * C, cnt = max(0, min(C, len - lo));
+        T A = T(1), Bc = T(0);
+        T av[kSegPer], bv[kSegPer];
+        if constexpr (sizeof(T) == 4) {   // rows held in registers
+#pragma unroll
+            for (int c = 0; c < kSegPer; ++c) {
+                av[c] = c < cnt ? sa[lo + c] : T(0);
+                bv[c] = c < cnt ? sb[lo + c] : T(0);
+            }
+#pragma unroll
+            for (int k = 0; k < kSegPer; ++k) {
+                const int c = BWD ? kSegPer - 1 - k : k;
+                if (c < cnt) {
+                    Bc = seg_fma(av[c], Bc, bv[c]);
+                    A *= av[c];
+                }
+            }
+        } else {                          // rows read from shared memory
+            if (!BWD) {
+                for (int c = 0; c < cnt; ++c) { Bc = seg_fma(sa[lo + c], Bc, sb[lo + c]); A *= sa[lo + c]; }
+            } else {
+                for (int c = cnt - 1; c >= 0; --c) { Bc = seg_fma(sa[lo + c], Bc, sb[lo + c]); A *= sa[lo + c]; }
+            }
+        }
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const T Ap = BWD ? __shfl_down_sync(0xffffffffu, A, d) : __shfl_up_sync(0xffffffffu, A, d);
+            const T Bp = BWD ? __shfl_down_sync(0xffffffffu, Bc, d) : __shfl_up_sync(0xffffffffu, Bc, d);
+            if (BWD ? lane + d < 32 : lane >= d) {
+                Bc = seg_fma(A, Bp, Bc);
+                A *= Ap;
+            }
+        }
+        T x = BWD ? __shfl_down_sync(0xffffffffu, Bc, 1) : __shfl_up_sync(0xffffffffu, Bc, 1);
+        if (BWD ? lane == 31 : lane == 0) x = T(0);
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+            for (int k = 0; k < kSegPer; ++k) {
+                const int c = BWD ? kSegPer - 1 - k : k;
+                if (c < cnt) {
+                    x = seg_fma(av[c], x, bv[c]);
+                    sb[lo + c] = x;
+                }
+            }
+        } else {
+            if (!BWD) {
+                for (int c = 0; c < cnt; ++c) { x = seg_fma(sa[lo + c], x, sb[lo + c]); sb[lo + c] = x; }
+            } else {
+                for (int c = cnt - 1; c >= 0; --c) { x = seg_fma(sa[lo + c], x, sb[lo + c]); sb[lo + c] = x; }
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < kSegPer; ++c) {
+            const int p = c * 32 + lane;
+            if (p < len) {
+                const T v = sb[p];
+                out[s0 + p] = v;
+                seg_publish<T>(tw, s0 + p, tg, v);
+            }
+        }
+        __syncwarp();
+    }
+    sweep_end(sync);
+}
+
+// Chain coefficients and leaving couplings of every row, in the layout the
+// segment sweeps read: v = [a fwd (n)][a bwd (n)][lower values (kgf n)]
+// [upper values (kgb n)], gc = [lower columns (kgf n)][upper columns (kgb n)],
+// couplings in slot order, padding column -1 with value 0.
+template <typename T>
+__global__ void k_seg_pack(int n, int W, int kgf, int kgb, const int *__restrict__ seg_id,
+                           const int *__restrict__ seg_off, const int *__restrict__ col, const T *__restrict__ lu,
+                           const T *__restrict__ dinv, int *__restrict__ gc, T *__restrict__ v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int S = seg_id[i], s0 = seg_off[S], e0 = seg_off[S + 1];
+    int *gcf = gc, *gcb = gc + (size_t)kgf * n;
+    T *gvf = v + 2 * (size_t)n, *gvb = gvf + (size_t)kgf * n;
+    T af = T(0), ab = T(0);
+    int qf = 0, qb = 0;
+    for (int w = 0; w < W; ++w) {
+        const int k = col[(int64_t)w * n + i];
+        if (k == i) continue;
+        const T a = lu[(int64_t)w * n + i];
+        if (k < i) {
+            if (k == i - 1 && i > s0) af = -a;
+            else if (qf < kgf) { gcf[(int64_t)qf * n + i] = k; gvf[(int64_t)qf * n + i] = a; ++qf; }
+        } else {
+            if (k == i + 1 && i + 1 < e0) ab = -dinv[i] * a;
+            else if (qb < kgb) { gcb[(int64_t)qb * n + i] = k; gvb[(int64_t)qb * n + i] = a; ++qb; }
+        }
+    }
+    for (; qf < kgf; ++qf) { gcf[(int64_t)qf * n + i] = -1; gvf[(int64_t)qf * n + i] = T(0); }
+    for (; qb < kgb; ++qb) { gcb[(int64_t)qb * n + i] = -1; gvb[(int64_t)qb * n + i] = T(0); }
+    v[i] = af;
+    v[(size_t)n + i] = ab;
+}
+
 __global__ void k_copy_f32(const double *a, float *b, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (; i < n; i += (int64_t)gridDim.x * blockDim.x) b[i] = (float)a[i];
@@ -381,9 +688,78 @@ bool level_apply(ms_system &s, const T *lu, const T *dinv, const TR *r, T *y, T 
     return launch_level<T, T, true>(s, lu, dinv, y, z, st);
 }
 
+template <typename T, typename TR, bool BWD, int KG>
+bool launch_seg_kg(ms_system &s, const T *vals, const T *dinv, const TR *rhs, T *out, cudaStream_t st) {
+    auto kern = k_seg_sweep<T, TR, BWD, KG>;
+    const size_t smem = (kSegThreads / 32) * seg_smem_warp<T, KG>();
+    static size_t cur = 0;
+    if (raise_smem_limit(kern, smem, cur) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const int n = s.n, ns = s.n_seg, kgf = s.seg_kg[0];
+    // enough warps for about three levels of segments in flight
+    const int warps = std::max(1, std::min(ns, std::max(32, 3 * s.seg_width)));
+    const int grid = (warps + kSegThreads / 32 - 1) / (kSegThreads / 32);
+    const size_t goff = BWD ? (size_t)kgf * n : 0;
+    kern<<<grid, kSegThreads, smem, st>>>(n, ns, s.seg_kg[BWD ? 1 : 0], s.seg_off.p, s.seg_ord.p + (BWD ? ns : 0),
+                                          vals + (BWD ? (size_t)n : 0), s.seg_gc.p + goff,
+                                          vals + 2 * (size_t)n + goff, dinv, rhs, out, s.seg_tag.p, s.sync.p);
+    MS_CHECK_LAUNCH();
+    return true;
+}
+
+template <typename T, typename TR, bool BWD>
+bool launch_seg(ms_system &s, const T *vals, const T *dinv, const TR *rhs, T *out, cudaStream_t st) {
+    const int kg = s.seg_kg[BWD ? 1 : 0];
+    if (kg <= 2) return launch_seg_kg<T, TR, BWD, 2>(s, vals, dinv, rhs, out, st);
+    if (kg <= 4) return launch_seg_kg<T, TR, BWD, 4>(s, vals, dinv, rhs, out, st);
+    if (kg <= 8) return launch_seg_kg<T, TR, BWD, 8>(s, vals, dinv, rhs, out, st);
+    return false;
+}
+
+template <typename T, typename TR>
+bool seg_apply(ms_system &s, const T *vals, const T *dinv, const TR *r, T *y, T *z, cudaStream_t st) {
+    if (s.n_seg == 0 || vals == nullptr) return false;
+    const double nl = (double)s.nnz_lower;
+    {
+        KernelScope ks_(st, sizeof(T) == 8 ? "ilu_seg_fwd" : "ilu_seg_fwd32",
+                        nl * (4 + sizeof(T)) + (double)s.n * (sizeof(TR) + sizeof(T)));
+        if (!launch_seg<T, TR, false>(s, vals, dinv, r, y, st)) return false;
+    }
+    KernelScope ks_(st, sizeof(T) == 8 ? "ilu_seg_bwd" : "ilu_seg_bwd32", nl * (4 + sizeof(T)) + (double)s.n * 3 * sizeof(T));
+    return launch_seg<T, T, true>(s, vals, dinv, y, z, st);
+}
+
 }  // namespace msgb
 
 namespace msgb {
+
+void launch_ilu_seg_pack(ms_system &s, bool fp32, cudaStream_t st) {
+    if (s.n_seg == 0) return;
+    const size_t kg = (size_t)s.seg_kg[0] + s.seg_kg[1];
+    s.seg_gc.alloc(std::max<size_t>(kg * s.n, 1));
+    const int g = (s.n + 255) / 256;
+    KernelScope ks_(st, "ilu_seg_pack", (double)s.W * s.n * (4 + (fp32 ? 4 : 8)) + (double)kg * s.n * (4 + (fp32 ? 4 : 8)));
+    if (fp32) {
+        s.seg_v32.alloc((2 + kg) * s.n);
+        k_seg_pack<float><<<g, 256, 0, st>>>(s.n, s.W, s.seg_kg[0], s.seg_kg[1], s.seg_id.p, s.seg_off.p, s.col.p,
+                                             s.lu32.p, s.dinv32.p, s.seg_gc.p, s.seg_v32.p);
+    } else {
+        s.seg_v64.alloc((2 + kg) * s.n);
+        k_seg_pack<double><<<g, 256, 0, st>>>(s.n, s.W, s.seg_kg[0], s.seg_kg[1], s.seg_id.p, s.seg_off.p, s.col.p,
+                                              s.lu64.p, s.dinv64.p, s.seg_gc.p, s.seg_v64.p);
+    }
+    MS_CHECK_LAUNCH();
+}
+
+bool launch_ilu_seg64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st) {
+    return seg_apply<double, double>(s, s.seg_v64.p, s.dinv64.p, r, y, z, st);
+}
+
+bool launch_ilu_seg32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st) {
+    return seg_apply<float, double>(s, s.seg_v32.p, s.dinv32.p, r, y, z, st);
+}
 
 bool launch_ilu_level64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st) {
     return level_apply<double, double>(s, s.lu64.p, s.dinv64.p, r, y, z, st);

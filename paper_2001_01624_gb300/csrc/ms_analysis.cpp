@@ -17,6 +17,7 @@
 #include <cstring>
 #include <deque>
 #include <limits>
+#include <numeric>
 #include <string>
 
 #include "ms_internal.h"
@@ -33,6 +34,95 @@ struct Conn {
 };
 
 inline int64_t gidx(int nx, int ny, int i, int j, int k) { return i + (int64_t)nx * (j + (int64_t)ny * k); }
+
+// Segments for the ILU(0) sweeps of any grid: maximal runs of consecutive rows
+// i-1, i coupled both ways, at most kSegMax rows, in which no row has any
+// other coupling to a row of the same run.  A sweep solves the chain of a
+// segment by a scan; every other coupling leaves the segment and becomes a
+// dependency on the segment holding that row.  Per direction the segments are
+// handed out by wavefront level of that dependency graph (forward: couplings
+// to lower rows, backward: to higher rows), so a segment's dependencies are
+// always handed out before it.  Rows sorted ascending per row (nb, deg, rowlen).
+void plan_segments(ms_system &s, const std::vector<int> &nb, const std::vector<int> &deg,
+                   const std::vector<int> &rowlen) {
+    const int n = s.n;
+    auto has = [&](int i, int k) {
+        auto b0 = nb.begin() + deg[i], b1 = b0 + rowlen[i];
+        return std::binary_search(b0, b1, k);
+    };
+    std::vector<int> off{0};
+    std::vector<int> stamp(n, -1);   // rows reached from the current segment by an upper coupling (k >= r + 2)
+    int start = 0;
+    auto mark = [&](int i) {
+        for (int w = 0; w < rowlen[i]; ++w) {
+            const int k = nb[deg[i] + w];
+            if (k >= i + 2) stamp[k] = start;
+        }
+    };
+    mark(0);
+    for (int i = 1; i < n; ++i) {
+        bool join = i - start < kSegMax && has(i, i - 1) && has(i - 1, i) && stamp[i] != start;
+        for (int w = 0; join && w < rowlen[i]; ++w) {
+            const int k = nb[deg[i] + w];
+            if (k >= start && k < i - 1) join = false;
+        }
+        if (!join) {
+            off.push_back(i);
+            start = i;
+        }
+        mark(i);
+    }
+    off.push_back(n);
+    const int ns = (int)off.size() - 1;
+    std::vector<int> sid(n);
+    for (int S = 0; S < ns; ++S)
+        for (int i = off[S]; i < off[S + 1]; ++i) sid[i] = S;
+
+    // couplings leaving each row's segment, and wavefront levels of the segment
+    // graph: forward over couplings to lower segments (ascending order),
+    // backward over couplings to higher segments (descending order)
+    std::vector<int> lf(ns, 0), lb(ns, 0);
+    std::vector<std::vector<int>> up(ns);
+    int kgf = 0, kgb = 0;
+    for (int S = 0; S < ns; ++S) {
+        for (int i = off[S]; i < off[S + 1]; ++i) {
+            int cf = 0, cb = 0;
+            for (int w = 0; w < rowlen[i]; ++w) {
+                const int k = nb[deg[i] + w];
+                if (k < off[S]) { lf[S] = std::max(lf[S], lf[sid[k]] + 1); ++cf; }
+                else if (k >= off[S + 1]) { up[S].push_back(sid[k]); ++cb; }
+            }
+            kgf = std::max(kgf, cf);
+            kgb = std::max(kgb, cb);
+        }
+    }
+    s.seg_kg[0] = kgf;
+    s.seg_kg[1] = kgb;
+    if (kgf > kSegMaxKG || kgb > kSegMaxKG) {   // too many couplings per row: not planned
+        s.n_seg = 0;
+        return;
+    }
+    for (int S = ns - 1; S >= 0; --S)
+        for (int d : up[S]) lb[S] = std::max(lb[S], lb[d] + 1);
+    std::vector<int> ord(2 * (size_t)ns);
+    std::iota(ord.begin(), ord.begin() + ns, 0);
+    std::stable_sort(ord.begin(), ord.begin() + ns, [&](int a, int b) { return lf[a] < lf[b]; });
+    for (int S = 0; S < ns; ++S) ord[(size_t)ns + S] = ns - 1 - S;
+    std::stable_sort(ord.begin() + ns, ord.end(), [&](int a, int b) { return lb[a] < lb[b]; });
+    int width = 0;
+    for (const std::vector<int> *lv : {&lf, &lb}) {
+        std::vector<int> cnt(ns + 1, 0);
+        for (int v : *lv) width = std::max(width, ++cnt[v]);
+    }
+    s.n_seg = ns;
+    s.seg_width = width;
+    cudaStream_t st = nullptr;
+    s.seg_off.upload(off, st);
+    s.seg_id.upload(sid, st);
+    s.seg_ord.upload(ord, st);
+    s.seg_tag.alloc(2 * (size_t)n);
+    s.seg_tag.zero(st);   // tag 0 never matches a sweep (the sweep counter starts at 1)
+}
 
 }  // namespace
 
@@ -254,10 +344,13 @@ void analyse_grid(ms_system &s, const ms_grid &g) {
             s.ilu_kind[p] = k;
         }
     } else {
-        // any grid: level-synchronous sweeps in one cooperative launch;
-        // MSGB_ILU_KERNEL=generic selects the flag-ordered sweeps instead
+        // any grid: segment dataflow sweeps; MSGB_ILU_KERNEL=level selects the
+        // level-synchronous sweeps (one cooperative launch), =generic the
+        // flag-ordered sweeps
+        plan_segments(s, nb, deg, rowlen);
         const char *e = std::getenv("MSGB_ILU_KERNEL");
-        const int k = (e && std::string(e) == "generic") ? 0 : 4;
+        const std::string v = e ? std::string(e) : std::string();
+        const int k = v == "generic" ? 0 : v == "level" ? 4 : (s.n_seg > 0 ? 5 : 4);
         s.ilu_kind[0] = s.ilu_kind[1] = k;
     }
 

@@ -117,6 +117,9 @@ void ensure_ilu(ms_ctx *ctx, ms_system &s, bool fp32) {
             launch_ilu_extract_dirs(s, true, ctx->stream);
             if (s.cl_ok[1]) launch_ilu_pack_coef4(s, true, ctx->stream);
         }
+    } else if (s.n_seg > 0) {
+        if (!had64) launch_ilu_seg_pack(s, false, ctx->stream);
+        if (fp32) launch_ilu_seg_pack(s, true, ctx->stream);
     }
     s.ilu64_valid = true;
     if (fp32) s.ilu32_valid = true;
@@ -124,13 +127,14 @@ void ensure_ilu(ms_ctx *ctx, ms_system &s, bool fp32) {
 
 // z = (LU)^{-1} r: wavefront sweeps on structured grids (line scan across a
 // cluster, line scan over CTA tiles, or pencil tiles, chosen per precision when
-// the system is analysed), level-synchronous sweeps in one cooperative launch
-// otherwise (flag-ordered sweeps where that launch is refused).
+// the system is analysed), segment dataflow sweeps otherwise (level-synchronous
+// sweeps in one cooperative launch, or flag-ordered sweeps, where those cannot run).
 void ilu_apply64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st) {
     switch (s.ilu_kind[0]) {
         case 3: launch_ilu_cluster64(s, r, y, z, st); break;
         case 2: launch_ilu_lines64(s, r, y, z, st); break;
         case 1: launch_ilu_tiled64(s, r, y, z, st); break;
+        case 5: if (launch_ilu_seg64(s, r, y, z, st)) break; [[fallthrough]];
         case 4: if (launch_ilu_level64(s, r, y, z, st)) break; [[fallthrough]];
         default: launch_ilu_apply64(s, r, y, z, st);
     }
@@ -141,6 +145,7 @@ void ilu_apply32(ms_system &s, const double *r, float *y, float *z, cudaStream_t
         case 3: launch_ilu_cluster32(s, r, y, z, st); break;
         case 2: launch_ilu_lines32(s, r, y, z, st); break;
         case 1: launch_ilu_tiled32(s, r, y, z, st); break;
+        case 5: if (launch_ilu_seg32(s, r, y, z, st)) break; [[fallthrough]];
         case 4: if (launch_ilu_level32(s, r, y, z, st)) break; [[fallthrough]];
         default: launch_ilu_apply32(s, r, y, z, st);
     }

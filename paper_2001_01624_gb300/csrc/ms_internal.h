@@ -91,6 +91,8 @@ constexpr int kSlotPad = 0x7fffffff;   // padding block id in basis slot lists (
 // Device-side synchronisation words of the level-ordered sweeps:
 // [0] sweep counter, [1] CTA ticket, [2] CTAs done, [3] error flags.
 constexpr int kSyncWords = 8;
+constexpr int kSegMax = 256;       // rows per segment of the segment sweeps (8 per lane)
+constexpr int kSegMaxKG = 8;       // couplings per row leaving its segment, per direction
 constexpr int kErrTimeout = 1;
 constexpr int kErrSingular = 2;
 constexpr int kErrNaN = 4;
@@ -198,7 +200,8 @@ struct ms_system {
     // line-scan sweeps: TK warps per CTA walk TJ x TK tiles of x-lines
     int LTJ = 0, LTK = 0, LNJ = 0, LNK = 0;
     // sweep kernel per precision ([0] FP64, [1] FP32): 0 level-ordered, 1 pencil tiles,
-    // 2 line scan over CTA tiles, 3 line scan pipelined across one cluster
+    // 2 line scan over CTA tiles, 3 line scan pipelined across one cluster,
+    // 4 level-synchronous (cooperative), 5 segment dataflow
     int ilu_kind[2] = {0, 0};
     // cluster line scan per precision: feasible, rows per CTA, CTAs (= cluster size)
     bool cl_ok[2] = {false, false};
@@ -221,6 +224,18 @@ struct ms_system {
     msgb::DBuf<int> lperm;
     msgb::DBuf<int> lev_off;                  // [n_levels + 1] level offsets into lperm
     msgb::DBuf<unsigned long long> lev_bar;   // grid barrier of the level-synchronous sweeps (counter, base)
+    // segment sweeps (any grid): runs of consecutive rows chained by their (i-1, i)
+    // couplings; per direction a hand-out order by wavefront level
+    int n_seg = 0;
+    int seg_width = 0;                        // most segments on one level (either direction)
+    int seg_kg[2] = {0, 0};                   // couplings per row leaving its segment: lower, upper
+    msgb::DBuf<int> seg_off;                  // [n_seg + 1] first row of each segment
+    msgb::DBuf<int> seg_id;                   // [n] segment of each row
+    msgb::DBuf<int> seg_ord;                  // [2 n_seg] forward order, backward order
+    msgb::DBuf<unsigned long long> seg_tag;   // [2 n] results as tagged words (sweep counter | value bits)
+    msgb::DBuf<int> seg_gc;                   // [(kg0 + kg1) n] columns of the leaving couplings, -1 padding
+    msgb::DBuf<double> seg_v64;               // [(2 + kg0 + kg1) n] chain a (fwd, bwd), coupling values
+    msgb::DBuf<float> seg_v32;
 
     // ILU(0) factors on A's pattern (L in lower slots, U in upper slots)
     bool ilu64_valid = false, ilu32_valid = false;
@@ -420,6 +435,9 @@ void launch_ilu_cluster32f(ms_system &s, const float *r, float *y, float *z, cud
 void launch_ilu_lines64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st);
 bool launch_ilu_level64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st);
 bool launch_ilu_level32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st);
+void launch_ilu_seg_pack(ms_system &s, bool fp32, cudaStream_t st);
+bool launch_ilu_seg64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st);
+bool launch_ilu_seg32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st);
 void launch_ilu_lines32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st);
 void launch_ilu_lines32f(ms_system &s, const float *r, float *y, float *z, cudaStream_t st);
 // basis

@@ -546,6 +546,61 @@ def test_level_sweeps_match_flag_sweeps(ms, ctx, monkeypatch, shape):
         assert np.array_equal(a, b)
 
 
+def _long_line_model():
+    """700 x 3 x 2 box with one inactive cell: x-lines longer than a segment."""
+    gm = G.lognormal_box(700, 3, 2, seed=4, block=(50, 3, 2))
+    act = np.ones(gm.grid.N, np.uint8)
+    act[5] = 0
+    gm.grid.active = act
+    return gm
+
+
+SEG_CASES = {
+    "faulted_18x14x7": lambda: G.faulted(18, 14, 7, seed=9, n_fault_x=1, n_fault_y=1, block=(4, 3, 2)),
+    "faulted_41x23x9": lambda: G.faulted(41, 23, 9, seed=9, n_fault_x=1, n_fault_y=1, block=(4, 3, 2)),
+    "faulted_5x3x2": lambda: G.faulted(5, 3, 2, seed=9, n_fault_x=1, n_fault_y=1, block=(4, 3, 2)),
+    "long_lines_700x3x2": _long_line_model,
+}
+
+
+@pytest.mark.parametrize("case", list(SEG_CASES))
+def test_segment_sweeps_match_oracle(ms, ctx, monkeypatch, case):
+    """Unstructured grids take the segment dataflow sweeps by default: chained
+    runs of rows solved by a warp scan, segments handed out by wavefront level.
+    They match the oracle's ILU(0) apply and the level-synchronous sweeps
+    (same factors; the scan rounds in another order), in FP64 and mixed
+    precision, over repeated applications that reuse the flags and tickets."""
+    gm = SEG_CASES[case]()
+    ref = O.assemble_tpfa(gm.grid, gm.perm)
+    Ap, _ = O.pin(ref.A, None, 0)
+    lu = O.ilu0(Ap)
+    xs = [np.random.default_rng(k).standard_normal(Ap.n) for k in range(3)]
+    out = {}
+    for kernel in ("", "level"):
+        if kernel:
+            monkeypatch.setenv("MSGB_ILU_KERNEL", kernel)
+        else:
+            monkeypatch.delenv("MSGB_ILU_KERNEL", raising=False)
+        s = _system(ms, ctx, gm)
+        ms.ms_profile_reset()
+        zs = []
+        for x in xs:
+            z = np.empty(Ap.n)
+            ms.ms_ilu_apply(ctx, s, x, z)
+            zr = O.ilu0_apply(Ap, lu, x)
+            np.testing.assert_allclose(z, zr, rtol=1e-10, atol=1e-12 * np.abs(zr).max())
+            z32 = np.empty(Ap.n)
+            ms.ms_ilu_apply(ctx, s, x, z32, ms.MS_PREC_MIXED)
+            assert np.abs(z32 - zr).max() <= 1e-4 * np.abs(zr).max()
+            zs.append(z)
+        launched = ms.ms_profile_read()
+        assert ("ilu_seg_fwd" in launched and "ilu_seg_bwd32" in launched) == (kernel == "")
+        out[kernel or "seg"] = zs
+        ms.ms_system_release(s)
+    for a, b in zip(out["seg"], out["level"]):
+        assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
+
+
 def test_ilu_apply_full_size_config2(ms, ctx):
     gm = G.config2(0)
     s = _system(ms, ctx, gm)
