@@ -159,8 +159,85 @@ __global__ void k_basis_maps(int n, int W, int B, const int *__restrict__ col, c
     }
 }
 
+// One cell of the MsRSB iteration with precomputed neighbour slot maps,
+// slots below SB (at least the cell's count); returns the key of its largest
+// |increment|.
+template <typename T, int WM, int SB>
+__device__ __forceinline__ unsigned long long msrsb_cell(int i, int cnt, int n, int W, const int *__restrict__ col,
+                                                         const T *__restrict__ off, const T *__restrict__ diag,
+                                                         const unsigned *__restrict__ nmap,
+                                                         const T *__restrict__ pin, T *__restrict__ pout,
+                                                         const T *__restrict__ odiag) {
+    unsigned long long inck = 0ull;
+    T v[SB], acc[SB];
+    const T d = diag[i];
+#pragma unroll
+    for (int s = 0; s < SB; ++s) {
+        v[s] = s < cnt ? pin[(int64_t)s * n + i] : T(0);
+        acc[s] = d * v[s];
+    }
+    if (WM > 0) {
+        // at most WM connections: every connection's column, coefficient and
+        // slot map are loaded first, then all the gathers, so the loads of
+        // different neighbours overlap (same order of the sums as below)
+        int kk[WM > 0 ? WM : 1];
+        T aw[WM > 0 ? WM : 1];
+        unsigned mw[WM > 0 ? WM : 1];
+#pragma unroll
+        for (int w = 0; w < WM; ++w) {
+            const int64_t at = (int64_t)w * n + i;
+            kk[w] = w < W ? col[at] : i;
+            aw[w] = w < W ? off[at] : T(0);
+            mw[w] = w < W ? nmap[at] : 0xffffffffu;
+        }
+#pragma unroll
+        for (int w = 0; w < WM; ++w) {
+            if (kk[w] == i) continue;
+#pragma unroll
+            for (int s = 0; s < SB; ++s) {
+                const unsigned t = (mw[w] >> (4 * s)) & 15u;
+                if (s < cnt && t != 15u) acc[s] += aw[w] * pin[(int64_t)t * n + kk[w]];
+            }
+        }
+    } else {
+        for (int w = 0; w < W; ++w) {
+            const int64_t at = (int64_t)w * n + i;
+            const int k = col[at];
+            if (k == i) continue;
+            const T a = off[at];
+            const unsigned m = nmap[at];
+#pragma unroll
+            for (int s = 0; s < SB; ++s) {
+                const unsigned t = (m >> (4 * s)) & 15u;
+                if (s < cnt && t != 15u) acc[s] += a * pin[(int64_t)t * n + k];
+            }
+        }
+    }
+    // omega / A_ii precomputed per smoothing run; one division for the
+    // partition-of-unity scale
+    const T od = odiag[i];
+    T sum = 0;
+#pragma unroll
+    for (int s = 0; s < SB; ++s)
+        if (s < cnt) {
+            acc[s] = v[s] - od * acc[s];
+            sum += acc[s];
+        }
+    const T rs = T(1) / sum;
+#pragma unroll
+    for (int s = 0; s < SB; ++s)
+        if (s < cnt) {
+            const T nv = acc[s] * rs;
+            inck = max(inck, abs_key(nv - v[s]));
+            pout[(int64_t)s * n + i] = nv;
+        }
+    return inck;
+}
+
 // MsRSB iteration with precomputed neighbour slot maps (B <= 8): every
-// neighbour contribution is an independent load.
+// neighbour contribution is an independent load.  FP64: the slot loops of a
+// warp stop at the largest slot count among its cells (2, 4 or 8), since a
+// multiply-add that only some lanes need still takes the FP64 pipe for all.
 template <typename T, int WM>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 3) k_msrsb_mapped(int n, int W, const int *__restrict__ col,
                                                            const T *__restrict__ off, const T *__restrict__ diag,
@@ -174,71 +251,17 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 3) k_msrsb_mapp
     T *__restrict__ pout = odd ? bufA : bufB;
     unsigned long long *maxinc = ctl + 2;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cnt = i < n ? (int)nslots[i] : 0;
     unsigned long long inck = 0ull;   // key of the largest |increment|
-    if (i < n) {
-        const int cnt = nslots[i];
-        T v[8], acc[8];
-        const T d = diag[i];
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            v[s] = s < cnt ? pin[(int64_t)s * n + i] : T(0);
-            acc[s] = d * v[s];
+    if constexpr (sizeof(T) == 8) {
+        const int cmax = __reduce_max_sync(0xffffffffu, cnt);
+        if (i < n) {
+            if (cmax <= 2) inck = msrsb_cell<T, WM, 2>(i, cnt, n, W, col, off, diag, nmap, pin, pout, odiag);
+            else if (cmax <= 4) inck = msrsb_cell<T, WM, 4>(i, cnt, n, W, col, off, diag, nmap, pin, pout, odiag);
+            else inck = msrsb_cell<T, WM, 8>(i, cnt, n, W, col, off, diag, nmap, pin, pout, odiag);
         }
-        if (WM > 0) {
-            // at most WM connections: every connection's column, coefficient and
-            // slot map are loaded first, then all the gathers, so the loads of
-            // different neighbours overlap (same order of the sums as below)
-            int kk[WM > 0 ? WM : 1];
-            T aw[WM > 0 ? WM : 1];
-            unsigned mw[WM > 0 ? WM : 1];
-#pragma unroll
-            for (int w = 0; w < WM; ++w) {
-                const int64_t at = (int64_t)w * n + i;
-                kk[w] = w < W ? col[at] : i;
-                aw[w] = w < W ? off[at] : T(0);
-                mw[w] = w < W ? nmap[at] : 0xffffffffu;
-            }
-#pragma unroll
-            for (int w = 0; w < WM; ++w) {
-                if (kk[w] == i) continue;
-#pragma unroll
-                for (int s = 0; s < 8; ++s) {
-                    const unsigned t = (mw[w] >> (4 * s)) & 15u;
-                    if (s < cnt && t != 15u) acc[s] += aw[w] * pin[(int64_t)t * n + kk[w]];
-                }
-            }
-        } else {
-            for (int w = 0; w < W; ++w) {
-                const int64_t at = (int64_t)w * n + i;
-                const int k = col[at];
-                if (k == i) continue;
-                const T a = off[at];
-                const unsigned m = nmap[at];
-#pragma unroll
-                for (int s = 0; s < 8; ++s) {
-                    const unsigned t = (m >> (4 * s)) & 15u;
-                    if (s < cnt && t != 15u) acc[s] += a * pin[(int64_t)t * n + k];
-                }
-            }
-        }
-        // omega / A_ii precomputed per smoothing run; one division for the
-        // partition-of-unity scale
-        const T od = odiag[i];
-        T sum = 0;
-#pragma unroll
-        for (int s = 0; s < 8; ++s)
-            if (s < cnt) {
-                acc[s] = v[s] - od * acc[s];
-                sum += acc[s];
-            }
-        const T rs = T(1) / sum;
-#pragma unroll
-        for (int s = 0; s < 8; ++s)
-            if (s < cnt) {
-                const T nv = acc[s] * rs;
-                inck = max(inck, abs_key(nv - v[s]));
-                pout[(int64_t)s * n + i] = nv;
-            }
+    } else {
+        if (i < n) inck = msrsb_cell<T, WM, 8>(i, cnt, n, W, col, off, diag, nmap, pin, pout, odiag);
     }
     __shared__ unsigned long long wmax[kThreads / 32];
     unsigned long long m = abs_key(key_value<T>(inck));   // key of the value as a double
