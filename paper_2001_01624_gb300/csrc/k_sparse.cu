@@ -426,6 +426,34 @@ __global__ void k_multidot(int n, int k, const double *__restrict__ V, const dou
 // 8): each thread keeps 8 partial sums over a grid-stride slice, warp trees and
 // the block's warps in order give the block partials, and the last block of
 // each group adds its group's partials in block order (deterministic).
+// Warp sums of eight accumulators with nine additions per lane instead of
+// forty: halves of the set are exchanged at lane distances 16, 8 and 4 (a
+// transposing butterfly), then the one accumulator left is summed over
+// distances 2 and 1.  Lanes pair exactly as in a shuffle-down tree (the
+// partner's value is added second on one side, first on the other, and a + b
+// equals b + a), so every sum is the same bit for bit.  Accumulator i ends in
+// lanes 4i .. 4i+3.
+__device__ __forceinline__ double warp_sum8(const double (&acc)[8], int lane) {
+    double a4[4], a2[2];
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const double keep = h16 ? acc[4 + j] : acc[j];
+        const double send = h16 ? acc[j] : acc[4 + j];
+        a4[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const double keep = h8 ? a4[2 + j] : a4[j];
+        const double send = h8 ? a4[j] : a4[2 + j];
+        a2[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    double a = (h4 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, h4 ? a2[0] : a2[1], 4);
+    a += __shfl_xor_sync(0xffffffffu, a, 2);
+    a += __shfl_xor_sync(0xffffffffu, a, 1);
+    return a;
+}
+
 __global__ void __launch_bounds__(256) k_multidot8(int n, int k, const double *__restrict__ V,
                                                    const double *__restrict__ w, double *red, unsigned int *cnt,
                                                    double *h) {
@@ -453,12 +481,9 @@ __global__ void __launch_bounds__(256) k_multidot8(int n, int k, const double *_
     }
     __shared__ double part[8][8];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        double a = acc[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-        if (lane == 0) part[wid][i] = a;
+    {
+        const double a = warp_sum8(acc, lane);
+        if ((lane & 3) == 0) part[wid][lane >> 2] = a;
     }
     __syncthreads();
     double *rg = red + (int64_t)blockIdx.y * gridDim.x * 8;
