@@ -757,12 +757,13 @@ def main():
             "iterations": units,
             "timing": "CUDA events around every launch of one traced step of the same workload"}
     if dom == "msrsb":
-        # FP64 basis smoothing is bound by the FP64 pipe (ncu: 86 % busy, DRAM 13 %): per basis entry
-        # (W + 1) FMAs for A P, the scaled update and the renormalisation = 2 W + 6 flops
+        # FP64 basis smoothing is bound by the FP64 pipe (ncu: 88 % busy, DRAM 16 %).  Per basis entry,
+        # with the rows prescaled by omega / A_ii once per smoothing run: one multiply for the diagonal,
+        # W multiply-adds for the neighbours, the renormalisation's sum and scale = 2 W + 3 flops
         plan = plans[ms.MS_PREC_FP64]
         W = ms.ms_system_get_info(plan.sys)["ell_width"]
         nnz = ms.ms_basis_get_info(plan.basis)["nnz"]
-        flops = nnz * (2 * W + 6)
+        flops = nnz * (2 * W + 3)
         tf = flops / (avg_ms * 1e-3) / 1e12
         roof.update({"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": tf / FP64_PEAK_TFLOPS, "peak_source": "nominal FP64 of the GB300 (1.25 TFLOP/s)",

@@ -162,7 +162,9 @@ __global__ void k_basis_maps(int n, int W, int B, const int *__restrict__ col, c
 // One cell of the MsRSB iteration with precomputed neighbour slot maps,
 // slots below SB (at least the cell's count); returns the key of its largest
 // |increment|.
-template <typename T, int WM, int SB>
+// PRE: the rows come prescaled (diag = 1 - (omega / A_ii) A_ii, off = -(omega / A_ii) A_ij), so the
+// Jacobi update is already in the accumulated sum.
+template <typename T, int WM, int SB, bool PRE>
 __device__ __forceinline__ unsigned long long msrsb_cell(int i, int cnt, int n, int W, const int *__restrict__ col,
                                                          const T *__restrict__ off, const T *__restrict__ diag,
                                                          const unsigned *__restrict__ nmap,
@@ -215,14 +217,20 @@ __device__ __forceinline__ unsigned long long msrsb_cell(int i, int cnt, int n, 
     }
     // omega / A_ii precomputed per smoothing run; one division for the
     // partition-of-unity scale
-    const T od = odiag[i];
     T sum = 0;
+    if (PRE) {
 #pragma unroll
-    for (int s = 0; s < SB; ++s)
-        if (s < cnt) {
-            acc[s] = v[s] - od * acc[s];
-            sum += acc[s];
-        }
+        for (int s = 0; s < SB; ++s)
+            if (s < cnt) sum += acc[s];
+    } else {
+        const T od = odiag[i];
+#pragma unroll
+        for (int s = 0; s < SB; ++s)
+            if (s < cnt) {
+                acc[s] = v[s] - od * acc[s];
+                sum += acc[s];
+            }
+    }
     const T rs = T(1) / sum;
 #pragma unroll
     for (int s = 0; s < SB; ++s)
@@ -235,9 +243,11 @@ __device__ __forceinline__ unsigned long long msrsb_cell(int i, int cnt, int n, 
 }
 
 // MsRSB iteration with precomputed neighbour slot maps (B <= 8): every
-// neighbour contribution is an independent load.  FP64: the slot loops of a
-// warp stop at the largest slot count among its cells (2, 4 or 8), since a
-// multiply-add that only some lanes need still takes the FP64 pipe for all.
+// neighbour contribution is an independent load.  FP64: the rows come
+// prescaled by omega / A_ii (diag and off hold 1 - omega-scaled diagonal and
+// the negated scaled off-diagonals), and the slot loops of a warp stop at the
+// largest slot count among its cells (2, 4 or 8), since a multiply-add that
+// only some lanes need still takes the FP64 pipe for all.
 template <typename T, int WM>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 3) k_msrsb_mapped(int n, int W, const int *__restrict__ col,
                                                            const T *__restrict__ off, const T *__restrict__ diag,
@@ -253,15 +263,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 3) k_msrsb_mapp
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int cnt = i < n ? (int)nslots[i] : 0;
     unsigned long long inck = 0ull;   // key of the largest |increment|
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (sizeof(T) == 8) {   // prescaled rows (one multiply-add less per entry)
         const int cmax = __reduce_max_sync(0xffffffffu, cnt);
         if (i < n) {
-            if (cmax <= 2) inck = msrsb_cell<T, WM, 2>(i, cnt, n, W, col, off, diag, nmap, pin, pout, odiag);
-            else if (cmax <= 4) inck = msrsb_cell<T, WM, 4>(i, cnt, n, W, col, off, diag, nmap, pin, pout, odiag);
-            else inck = msrsb_cell<T, WM, 8>(i, cnt, n, W, col, off, diag, nmap, pin, pout, odiag);
+            if (cmax <= 2) inck = msrsb_cell<T, WM, 2, true>(i, cnt, n, W, col, off, diag, nmap, pin, pout, odiag);
+            else if (cmax <= 4) inck = msrsb_cell<T, WM, 4, true>(i, cnt, n, W, col, off, diag, nmap, pin, pout, odiag);
+            else inck = msrsb_cell<T, WM, 8, true>(i, cnt, n, W, col, off, diag, nmap, pin, pout, odiag);
         }
     } else {
-        if (i < n) inck = msrsb_cell<T, WM, 8>(i, cnt, n, W, col, off, diag, nmap, pin, pout, odiag);
+        if (i < n) inck = msrsb_cell<T, WM, 8, false>(i, cnt, n, W, col, off, diag, nmap, pin, pout, odiag);
     }
     __shared__ unsigned long long wmax[kThreads / 32];
     unsigned long long m = abs_key(key_value<T>(inck));   // key of the value as a double
@@ -293,6 +303,17 @@ template <typename T>
 __global__ void k_omega_over_diag(int n, const T *__restrict__ diag, T omega, T *__restrict__ od) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) od[i] = omega / diag[i];
+}
+
+// Rows of the Jacobi update P - (omega / A_ii) A P prescaled per smoothing run:
+// c_i = 1 - (omega / A_ii) A_ii and b_ij = -(omega / A_ii) A_ij (slot layout of A).
+__global__ void k_prescale_rows(int n, int W, const double *__restrict__ off, const double *__restrict__ diag,
+                                double omega, double *__restrict__ c, double *__restrict__ bw) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double od = omega / diag[i];
+    c[i] = 1.0 - od * diag[i];
+    for (int w = 0; w < W; ++w) bw[(int64_t)w * n + i] = -(od * off[(int64_t)w * n + i]);
 }
 
 template <typename T>
@@ -463,7 +484,11 @@ static void msrsb_dispatch(const ms_system &s, const ms_basis &b, const int *pid
         KernelScope ks_(st, sizeof(T) == 8 ? "msrsb" : "msrsb32",
                         (double)s.n * (2 * sizeof(T) + 1) + (double)s.W * s.n * (4 + sizeof(T) + 4) +
                             (double)b.nnz * 2 * sizeof(T));
-        // maxinc: the control block
+        // maxinc: the control block.  FP64 takes the prescaled rows.
+        if constexpr (sizeof(T) == 8) {
+            off = b.pre_w64.p;
+            diag = b.pre_c64.p;
+        }
         if (s.W <= 4)
             k_msrsb_mapped<T, 4><<<g, kThreads, 0, st>>>(s.n, s.W, s.col.p, off, diag, b.nmap.p, b.nslots.p, pin,
                                                          pout, omega, maxinc);
@@ -501,6 +526,9 @@ void launch_basis_scale(const ms_system &s, ms_basis &b, bool fp32, cudaStream_t
     } else {
         b.od64.alloc(s.n);
         k_omega_over_diag<double><<<g, kThreads, 0, st>>>(s.n, s.diag.p, b.omega, b.od64.p);
+        b.pre_c64.alloc(s.n);
+        b.pre_w64.alloc(std::max<size_t>((size_t)s.W * s.n, 1));
+        k_prescale_rows<<<g, kThreads, 0, st>>>(s.n, s.W, s.off_u.p, s.diag.p, b.omega, b.pre_c64.p, b.pre_w64.p);
     }
     MS_CHECK_LAUNCH();
 }

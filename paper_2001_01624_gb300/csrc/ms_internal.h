@@ -284,6 +284,7 @@ struct ms_basis {
     msgb::DBuf<double> pval, pval_tmp;
     msgb::DBuf<float> pval32, pval32_tmp;
     msgb::DBuf<double> od64;             // omega / A_ii for the current smoothing run
+    msgb::DBuf<double> pre_c64, pre_w64; // prescaled rows of that run: 1 - omega, -(omega / A_ii) A_ij (FP64)
     msgb::DBuf<float> od32;
     // column view (CSC)
     msgb::DBuf<int> cptr, ccell, csrc;
