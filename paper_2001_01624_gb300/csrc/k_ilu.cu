@@ -3,7 +3,12 @@
 // order, IKJ form:  for each row i and each k < i in row i (ascending):
 // a_ik /= u_kk, then a_ij -= a_ik u_kj for every j > k in both rows.
 //
-// GPU scheme: rows are visited in wavefront-level order (levels padded to
+// Three sweep schemes for grids without the structured line sweeps: segment
+// dataflow sweeps (the default; chained row runs, one warp scan each),
+// level-synchronous sweeps (one cooperative launch, a grid barrier per
+// level), and the flag-ordered sweeps below, which also factorise.
+//
+// Flag-ordered scheme: rows are visited in wavefront-level order (levels padded to
 // whole warps so a warp never holds two levels).  Each thread owns one row,
 // waits for the rows it depends on through per-row completion flags
 // (acquire/release), computes, and publishes its own flag.  CTAs take their

@@ -89,7 +89,8 @@ struct HostScratch {
 constexpr int kSlotPad = 0x7fffffff;   // padding block id in basis slot lists (sorts last)
 
 // Device-side synchronisation words of the level-ordered sweeps:
-// [0] sweep counter, [1] CTA ticket, [2] CTAs done, [3] error flags.
+// [0] sweep counter, [1] ticket (a CTA's, or a warp's in the segment sweeps), [2] CTAs done,
+// [3] error flags.
 constexpr int kSyncWords = 8;
 constexpr int kSegMax = 256;       // rows per segment of the segment sweeps (8 per lane)
 constexpr int kSegMaxKG = 8;       // couplings per row leaving its segment, per direction
