@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define MS_ABI_VERSION 5
+#define MS_ABI_VERSION 6
 
 typedef enum {
     MS_OK = 0,
@@ -237,6 +237,27 @@ ms_status ms_ilu_apply(ms_ctx *ctx, ms_system *sys, int32_t precision, const dou
  *    ms_ilu_apply uses the tiled sweeps).  Waits for the context's stream
  *    before returning, to report a timed-out sweep as MS_ERR_TIMEOUT. */
 ms_status ms_ilu_apply_noalloc(ms_ctx *ctx, const ms_system *sys, const double *r, double *z);
+
+/* Segments of the ILU(0) segment sweeps for a sparsity pattern (Sec. 5.1
+ * smoother S, Sec. 6.4 "Smooth": the two triangular solves of natural-order
+ * ILU(0)); the analysis ms_system_create runs on grids without the
+ * structured line sweeps.  Host only, no device work; ctx may be NULL.
+ * rowptr (n+1) and col (rowptr[n]) list row i's columns, host int32, in any
+ * order (the diagonal and repeats are ignored).  A segment is a maximal run
+ * of consecutive rows in which rows i-1 and i are coupled both ways, no row
+ * has another coupling to a row of the run, and at most max_len (1..256)
+ * rows.  Outputs, host and caller-allocated: seg_off (n+1 int32): first row
+ * of each segment, then n; *n_seg; order (2n int32): the forward hand-out
+ * order in [0, n_seg) and the backward one in [n_seg, 2 n_seg), segments by
+ * wavefront level of the segment graph (forward over couplings to lower
+ * rows, ties by ascending segment; backward over couplings to higher rows,
+ * ties by descending segment); kg (2 int32): the most couplings of one row
+ * that leave its segment towards lower / higher rows (the sweeps take at
+ * most 8); *width: the most segments on one level, either direction.
+ * Errors: MS_ERR_INVALID_ARG for a null array, n < 1, max_len outside
+ * 1..256, a decreasing rowptr or a column outside [0, n). */
+ms_status ms_plan_segments(ms_ctx *ctx, int32_t n, const int32_t *rowptr, const int32_t *col, int32_t max_len,
+                           int32_t *seg_off, int32_t *n_seg, int32_t *order, int32_t *kg, int32_t *width);
 
 /* ------------------------------------------------------------- partitions */
 /* General structured partition (Sec. 5: non-overlapping coarse blocks;

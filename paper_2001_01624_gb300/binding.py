@@ -125,6 +125,7 @@ def lib():
         "ms_spmv": ([_vp, _vp, _vp, _vp], _i32),
         "ms_ilu_apply": ([_vp, _vp, _i32, _vp, _vp], _i32),
         "ms_ilu_apply_noalloc": ([_vp, _vp, _vp, _vp], _i32),
+        "ms_plan_segments": ([_vp, _i32, _vp, _vp, _i32, _vp, P(_i32), _vp, _vp, P(_i32)], _i32),
         "ms_partition_cartesian": ([_vp, _vp, _i32, _i32, _i32, _vp, P(_i32)], _i32),
         "ms_partition_components": ([_vp, _vp, _vp, _vp, P(_i32)], _i32),
         "ms_partition_dynamic": ([_vp, _vp, _vp, _i32, _d, _vp, P(_i32)], _i32),
@@ -163,7 +164,7 @@ def lib():
 def exported_symbols() -> Sequence[str]:
     return ["ms_abi_version", "ms_status_string", "ms_last_error", "ms_create", "ms_destroy", "ms_set_stream",
             "ms_system_create", "ms_system_release", "ms_system_get_info", "ms_assemble_tpfa",
-            "ms_system_get_matrix", "ms_spmv", "ms_ilu_apply", "ms_ilu_apply_noalloc", "ms_partition_cartesian", "ms_partition_components", "ms_partition_dynamic",
+            "ms_system_get_matrix", "ms_spmv", "ms_ilu_apply", "ms_ilu_apply_noalloc", "ms_plan_segments", "ms_partition_cartesian", "ms_partition_components", "ms_partition_dynamic",
             "ms_partition_wells", "ms_coarse_create", "ms_dense_inverse", "ms_cpr_pressure_system",
             "ms_build_basis", "ms_basis_rebuild", "ms_basis_update", "ms_basis_release", "ms_basis_get_info",
             "ms_basis_get", "ms_add_adaptive_basis", "ms_galerkin", "ms_coarse_refresh", "ms_coarse_release",
@@ -299,6 +300,25 @@ def ms_partition_cartesian(ctx, sys, block):
     _check(lib().ms_partition_cartesian(ctx, sys, int(block[0]), int(block[1]), int(block[2]), _ptr(part),
                                         C.byref(m)), ctx)
     return part, m.value
+
+
+def ms_plan_segments(rowptr, col, max_len: int = 256, ctx=None) -> dict:
+    """Segments of the ILU(0) segment sweeps for a CSR row pattern (host only,
+    no GPU needed): seg_off (starts, then n), the forward and backward
+    hand-out orders, kg (most couplings of a row leaving its segment, towards
+    lower / higher rows) and the widest level."""
+    rp = np.ascontiguousarray(rowptr, np.int32)
+    cl = np.ascontiguousarray(col, np.int32) if len(col) else np.zeros(1, np.int32)
+    n = len(rp) - 1
+    off = np.empty(max(n, 0) + 1, np.int32)
+    order = np.empty(max(2 * n, 1), np.int32)
+    kg = np.empty(2, np.int32)
+    ns, width = _i32(), _i32()
+    _check(lib().ms_plan_segments(ctx, n, _ptr(rp), _ptr(cl), max_len, _ptr(off), C.byref(ns), _ptr(order), _ptr(kg),
+                                  C.byref(width)), ctx)
+    k = ns.value
+    return dict(seg_off=off[:k + 1].copy(), order_fwd=order[:k].copy(), order_bwd=order[k:2 * k].copy(),
+                kg=(int(kg[0]), int(kg[1])), width=width.value)
 
 
 def ms_partition_wells(ctx, sys, wells):

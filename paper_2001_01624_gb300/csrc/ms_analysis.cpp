@@ -24,33 +24,24 @@
 
 namespace msgb {
 
-namespace {
-
-struct Conn {
-    int a, b;        // active indices, a < b not required
-    int ga, gb;      // grid indices
-    int8_t axis;
-    double mult;
-};
-
-inline int64_t gidx(int nx, int ny, int i, int j, int k) { return i + (int64_t)nx * (j + (int64_t)ny * k); }
-
 // Segments for the ILU(0) sweeps of any grid: maximal runs of consecutive rows
-// i-1, i coupled both ways, at most kSegMax rows, in which no row has any
+// i-1, i coupled both ways, at most max_len rows, in which no row has any
 // other coupling to a row of the same run.  A sweep solves the chain of a
 // segment by a scan; every other coupling leaves the segment and becomes a
 // dependency on the segment holding that row.  Per direction the segments are
 // handed out by wavefront level of that dependency graph (forward: couplings
-// to lower rows, backward: to higher rows), so a segment's dependencies are
-// always handed out before it.  Rows sorted ascending per row (nb, deg, rowlen).
-void plan_segments(ms_system &s, const std::vector<int> &nb, const std::vector<int> &deg,
-                   const std::vector<int> &rowlen) {
-    const int n = s.n;
+// to lower rows, in ascending segment order within a level; backward:
+// couplings to higher rows, descending order), so a segment's dependencies
+// are always handed out before it.  Row i's neighbours (self excluded) are
+// nb[deg[i] .. deg[i] + rowlen[i]), ascending.
+void segment_plan(int n, const std::vector<int> &nb, const std::vector<int> &deg, const std::vector<int> &rowlen,
+                  int max_len, SegmentPlan &sp) {
     auto has = [&](int i, int k) {
         auto b0 = nb.begin() + deg[i], b1 = b0 + rowlen[i];
         return std::binary_search(b0, b1, k);
     };
-    std::vector<int> off{0};
+    std::vector<int> &off = sp.off;
+    off.assign(1, 0);
     std::vector<int> stamp(n, -1);   // rows reached from the current segment by an upper coupling (k >= r + 2)
     int start = 0;
     auto mark = [&](int i) {
@@ -61,7 +52,7 @@ void plan_segments(ms_system &s, const std::vector<int> &nb, const std::vector<i
     };
     mark(0);
     for (int i = 1; i < n; ++i) {
-        bool join = i - start < kSegMax && has(i, i - 1) && has(i - 1, i) && stamp[i] != start;
+        bool join = i - start < max_len && has(i, i - 1) && has(i - 1, i) && stamp[i] != start;
         for (int w = 0; join && w < rowlen[i]; ++w) {
             const int k = nb[deg[i] + w];
             if (k >= start && k < i - 1) join = false;
@@ -74,7 +65,8 @@ void plan_segments(ms_system &s, const std::vector<int> &nb, const std::vector<i
     }
     off.push_back(n);
     const int ns = (int)off.size() - 1;
-    std::vector<int> sid(n);
+    std::vector<int> &sid = sp.sid;
+    sid.assign(n, 0);
     for (int S = 0; S < ns; ++S)
         for (int i = off[S]; i < off[S + 1]; ++i) sid[i] = S;
 
@@ -96,31 +88,52 @@ void plan_segments(ms_system &s, const std::vector<int> &nb, const std::vector<i
             kgb = std::max(kgb, cb);
         }
     }
-    s.seg_kg[0] = kgf;
-    s.seg_kg[1] = kgb;
-    if (kgf > kSegMaxKG || kgb > kSegMaxKG) {   // too many couplings per row: not planned
-        s.n_seg = 0;
-        return;
-    }
+    sp.kg[0] = kgf;
+    sp.kg[1] = kgb;
+    sp.fits = kgf <= kSegMaxKG && kgb <= kSegMaxKG;
     for (int S = ns - 1; S >= 0; --S)
         for (int d : up[S]) lb[S] = std::max(lb[S], lb[d] + 1);
-    std::vector<int> ord(2 * (size_t)ns);
+    std::vector<int> &ord = sp.ord;
+    ord.assign(2 * (size_t)ns, 0);
     std::iota(ord.begin(), ord.begin() + ns, 0);
     std::stable_sort(ord.begin(), ord.begin() + ns, [&](int a, int b) { return lf[a] < lf[b]; });
     for (int S = 0; S < ns; ++S) ord[(size_t)ns + S] = ns - 1 - S;
     std::stable_sort(ord.begin() + ns, ord.end(), [&](int a, int b) { return lb[a] < lb[b]; });
-    int width = 0;
+    sp.width = 0;
     for (const std::vector<int> *lv : {&lf, &lb}) {
         std::vector<int> cnt(ns + 1, 0);
-        for (int v : *lv) width = std::max(width, ++cnt[v]);
+        for (int v : *lv) sp.width = std::max(sp.width, ++cnt[v]);
     }
-    s.n_seg = ns;
-    s.seg_width = width;
+}
+
+namespace {
+
+struct Conn {
+    int a, b;        // active indices, a < b not required
+    int ga, gb;      // grid indices
+    int8_t axis;
+    double mult;
+};
+
+inline int64_t gidx(int nx, int ny, int i, int j, int k) { return i + (int64_t)nx * (j + (int64_t)ny * k); }
+
+void plan_segments(ms_system &s, const std::vector<int> &nb, const std::vector<int> &deg,
+                   const std::vector<int> &rowlen) {
+    SegmentPlan sp;
+    segment_plan(s.n, nb, deg, rowlen, kSegMax, sp);
+    s.seg_kg[0] = sp.kg[0];
+    s.seg_kg[1] = sp.kg[1];
+    if (!sp.fits) {   // too many couplings per row leave a segment: not planned
+        s.n_seg = 0;
+        return;
+    }
+    s.n_seg = (int)sp.off.size() - 1;
+    s.seg_width = sp.width;
     cudaStream_t st = nullptr;
-    s.seg_off.upload(off, st);
-    s.seg_id.upload(sid, st);
-    s.seg_ord.upload(ord, st);
-    s.seg_tag.alloc(2 * (size_t)n);
+    s.seg_off.upload(sp.off, st);
+    s.seg_id.upload(sp.sid, st);
+    s.seg_ord.upload(sp.ord, st);
+    s.seg_tag.alloc(2 * (size_t)s.n);
     s.seg_tag.zero(st);   // tag 0 never matches a sweep (the sweep counter starts at 1)
 }
 

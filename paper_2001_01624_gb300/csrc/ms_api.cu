@@ -604,6 +604,41 @@ ms_status ms_ilu_apply(ms_ctx *ctx, ms_system *s, int32_t precision, const doubl
     API_CATCH(ctx)
 }
 
+ms_status ms_plan_segments(ms_ctx *ctx, int32_t n, const int32_t *rowptr, const int32_t *col, int32_t max_len,
+                           int32_t *seg_off, int32_t *n_seg, int32_t *order, int32_t *kg, int32_t *width) {
+    if (!rowptr || !col || !seg_off || !n_seg || !order || !kg || !width)
+        return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    if (n < 1) return fail(ctx, MS_ERR_INVALID_ARG, "n must be >= 1");
+    if (max_len < 1 || max_len > kSegMax) return fail(ctx, MS_ERR_INVALID_ARG, "max_len must be in 1..256");
+    API_TRY
+    MS_REQUIRE(rowptr[0] == 0, MS_ERR_INVALID_ARG, "rowptr[0] must be 0");
+    std::vector<int> deg(n + 1, 0), nb, rowlen(n);
+    for (int i = 0; i < n; ++i) {
+        MS_REQUIRE(rowptr[i + 1] >= rowptr[i], MS_ERR_INVALID_ARG, "rowptr must not decrease");
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            const int k = col[e];
+            MS_REQUIRE(k >= 0 && k < n, MS_ERR_INVALID_ARG, "column out of range");
+            if (k != i) nb.push_back(k);
+        }
+        auto b0 = nb.begin() + deg[i];
+        std::sort(b0, nb.end());
+        nb.erase(std::unique(b0, nb.end()), nb.end());
+        rowlen[i] = (int)(nb.end() - b0);
+        deg[i + 1] = (int)nb.size();
+    }
+    SegmentPlan sp;
+    segment_plan(n, nb, deg, rowlen, max_len, sp);
+    const int ns = (int)sp.off.size() - 1;
+    std::memcpy(seg_off, sp.off.data(), sp.off.size() * sizeof(int));
+    std::memcpy(order, sp.ord.data(), sp.ord.size() * sizeof(int));
+    *n_seg = ns;
+    kg[0] = sp.kg[0];
+    kg[1] = sp.kg[1];
+    *width = sp.width;
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
 ms_status ms_partition_cartesian(ms_ctx *ctx, const ms_system *s, int32_t bx, int32_t by, int32_t bz,
                                  int32_t *part, int32_t *n_blocks) {
     if (!ctx || !s || !part || !n_blocks) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");

@@ -368,6 +368,15 @@ namespace msgb {
 
 // ---------------------------------------------------------------- analysis
 void analyse_grid(ms_system &s, const ms_grid &g);
+// segments of the segment ILU(0) sweeps (host analysis of a row pattern)
+struct SegmentPlan {
+    std::vector<int> off, sid, ord;   // segment starts (+ n), segment of each row, hand-out orders (fwd, bwd)
+    int kg[2] = {0, 0};               // most couplings of one row leaving its segment: lower, higher rows
+    int width = 0;                    // most segments on one level
+    bool fits = false;                // kg within what the sweeps take
+};
+void segment_plan(int n, const std::vector<int> &nb, const std::vector<int> &deg, const std::vector<int> &rowlen,
+                  int max_len, SegmentPlan &sp);
 int partition_cartesian(const ms_system &s, int bx, int by, int bz, std::vector<int> &part);
 // Support patterns for a partition; fills per-block sorted cell lists.
 void analyse_supports(const ms_system &s, const std::vector<int> &part, int M, int rule, int bx, int by, int bz,
