@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--profile-ilu", type=int, default=0,
                     help="only assemble the c2 system and apply ILU(0) N times in each precision (for ncu captures)")
     ap.add_argument("--nz", type=int, default=85, help="--profile-ilu: layers of the 60x220 grid")
+    ap.add_argument("--faulted", action="store_true",
+                    help="--profile-ilu: the faulted 200x200x50 geomodel instead (segment sweeps)")
     ap.add_argument("--profile-coarse", action="store_true",
                     help="only form the finite-volume coarse operator of the 60x220x85 geomodel (Gauss-Jordan "
                          "inverse; for ncu captures)")
@@ -564,7 +566,8 @@ def ensemble_oracle_sample(mem, out):
 
 
 def run_profile_ilu(args):
-    """ILU(0) applications alone on the 60x220xNZ geomodel (untimed)."""
+    """ILU(0) applications alone on the 60x220xNZ geomodel, or the faulted
+    200x200x50 one (untimed)."""
     import torch
     import numpy as np
     import __graft_entry__
@@ -572,7 +575,11 @@ def run_profile_ilu(args):
     import paper_2001_01624_gb300 as ms
     from paper_2001_01624_gb300 import geomodel as G
     dev = torch.device("cuda:0")
-    gm = G.config2(0) if args.nz == 85 else G.lognormal_box(60, 220, args.nz, seed=0, block=(10, 20, 5), kz_ratio=0.1)
+    if args.faulted:
+        gm = G.config3(0)
+    else:
+        gm = G.config2(0) if args.nz == 85 else G.lognormal_box(60, 220, args.nz, seed=0, block=(10, 20, 5),
+                                                                 kz_ratio=0.1)
     stream = torch.cuda.Stream(dev)
     ctx = ms.ms_create(0, stream)
     s = ms.ms_system_create(ctx, gm.grid, 0)
