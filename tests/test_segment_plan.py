@@ -1,8 +1,10 @@
 """Host analysis of the ILU(0) segment sweeps (CPU, no GPU needed): the
 segments, hand-out orders and coupling counts that ms_plan_segments returns
-against a plain restatement of their definition, plus the invariants the
-sweeps rely on (chains inside a segment, no other coupling inside it,
-dependencies handed out first)."""
+against a plain restatement of their definition, the invariants the sweeps
+rely on (chains inside a segment, no other coupling inside it, dependencies
+handed out first), and the algebra of the sweeps: segments in the plan's
+orders, each chain solved by a 32-lane scan of affine maps, reproduce the
+oracle's ILU(0) application."""
 import numpy as np
 import pytest
 
@@ -151,3 +153,89 @@ def test_single_row_and_errors(b):
         b.ms_plan_segments(rp, np.array([0, 1, 0, 2]))                 # column out of range
     with pytest.raises(b.MsError):
         b.ms_plan_segments(np.array([0, 2, 1]), cl)                    # decreasing rowptr
+
+
+def _lane_scan(a, B, bwd):
+    """One warp's solve of the chain x_p = B_p + a_p x_(p-1) (bwd: x_(p+1)):
+    each of 32 lanes composes the affine maps of its run of rows, the
+    compositions are scanned across the lanes (distances 1, 2, 4, 8, 16), and
+    each lane applies its scanned input."""
+    L = len(a)
+    C = (L + 31) // 32
+    A, Bc = np.ones(32), np.zeros(32)
+    runs = [range(l * C, min(l * C + C, L)) for l in range(32)]
+    for l in range(32):
+        for p in (reversed(runs[l]) if bwd else runs[l]):
+            Bc[l] = a[p] * Bc[l] + B[p]
+            A[l] = a[p] * A[l]
+    d = 1
+    while d < 32:
+        An, Bn = A.copy(), Bc.copy()
+        for l in range(32):
+            src = l + d if bwd else l - d
+            if 0 <= src < 32:
+                Bn[l] = A[l] * Bc[src] + Bc[l]
+                An[l] = A[l] * A[src]
+        A, Bc, d = An, Bn, 2 * d
+    x = np.zeros(L)
+    for l in range(32):
+        src = l + 1 if bwd else l - 1
+        v = Bc[src] if 0 <= src < 32 else 0.0
+        for p in (reversed(runs[l]) if bwd else runs[l]):
+            v = a[p] * v + B[p]
+            x[p] = v
+    return x
+
+
+@pytest.mark.parametrize("case", ["faulted", "long_lines"])
+def test_segment_scans_solve_the_ilu_triangles(b, case):
+    """The segment plan and the chain scans reproduce the oracle's ILU(0)
+    application (Sec. 6.4 "Smooth": L y = r, then U z = y): segments taken
+    in the plan's hand-out orders, couplings leaving a segment gathered from
+    segments already solved, each chain solved by the lane scan."""
+    if case == "faulted":
+        gm = G.faulted(41, 23, 9, seed=9, n_fault_x=1, n_fault_y=1, block=(4, 3, 2))
+        max_len = 256
+    else:
+        gm = G.lognormal_box(700, 3, 2, seed=4, block=(50, 3, 2))
+        act = np.ones(gm.grid.N, np.uint8)
+        act[5] = 0
+        gm.grid.active = act
+        max_len = 64
+    Ap, _ = O.pin(O.assemble_tpfa(gm.grid, gm.perm).A, None, 0)
+    lu = O.ilu0(Ap)
+    r = np.random.default_rng(3).standard_normal(Ap.n)
+    plan = b.ms_plan_segments(Ap.rowptr, Ap.col, max_len)
+    off = plan["seg_off"]
+    row = [(Ap.col[Ap.rowptr[i]:Ap.rowptr[i + 1]], lu[Ap.rowptr[i]:Ap.rowptr[i + 1]]) for i in range(Ap.n)]
+    d = np.array([v[c == i][0] for i, (c, v) in enumerate(row)])
+    y = np.full(Ap.n, np.nan)
+    for S in plan["order_fwd"]:
+        a0, e0 = off[S], off[S + 1]
+        a, B = np.zeros(e0 - a0), np.zeros(e0 - a0)
+        for p, i in enumerate(range(a0, e0)):
+            s = r[i]
+            for k, v in zip(*row[i]):
+                if k == i - 1 and i > a0:
+                    a[p] = -v
+                elif k < a0:
+                    assert not np.isnan(y[k])          # handed out before
+                    s -= v * y[k]
+            B[p] = s
+        y[a0:e0] = _lane_scan(a, B, bwd=False)
+    z = np.full(Ap.n, np.nan)
+    for S in plan["order_bwd"]:
+        a0, e0 = off[S], off[S + 1]
+        a, B = np.zeros(e0 - a0), np.zeros(e0 - a0)
+        for p, i in enumerate(range(a0, e0)):
+            s = y[i]
+            for k, v in zip(*row[i]):
+                if k == i + 1 and i + 1 < e0:
+                    a[p] = -v / d[i]
+                elif k >= e0:
+                    assert not np.isnan(z[k])
+                    s -= v * z[k]
+            B[p] = s / d[i]
+        z[a0:e0] = _lane_scan(a, B, bwd=True)
+    zr = O.ilu0_apply(Ap, lu, r)
+    assert np.abs(z - zr).max() <= 1e-12 * np.abs(zr).max()
