@@ -30,6 +30,11 @@
  * Errors.  Every call returns an ms_status.  On error no output handle is
  *          created and ms_last_error() describes the failure.  Device-side
  *          waits are bounded; a wait that runs out returns MS_ERR_TIMEOUT.
+ *          Null handles or arrays, sizes out of range and non-finite inputs
+ *          are MS_ERR_INVALID_ARG; calls that need matrix values (SpMV,
+ *          matrix copies, ILU(0), bases, coarse operators, solves) on a
+ *          system never assembled are MS_ERR_STATE; failed allocations are
+ *          MS_ERR_OOM and failed CUDA runtime calls MS_ERR_CUDA.
  * Precision. MS_PREC_FP64 computes everything in double precision.
  *          MS_PREC_MIXED stores and applies the basis, the smoother and the
  *          coarse inverse in single precision (single-precision accumulation)
@@ -160,7 +165,10 @@ typedef struct {
 
 /* ---------------------------------------------------------------- context */
 /* Create a context on CUDA device `device` that launches on `stream`
- * (a cudaStream_t, or NULL for the default stream). */
+ * (a cudaStream_t, or NULL for the default stream).  A device index outside
+ * [0, device count) is MS_ERR_INVALID_ARG.  ms_destroy releases the context
+ * (handles made with it must be released first); ms_set_stream changes the
+ * stream later calls launch on. */
 ms_status ms_create(ms_ctx **ctx, int32_t device, void *stream);
 ms_status ms_destroy(ms_ctx *ctx);
 ms_status ms_set_stream(ms_ctx *ctx, void *stream);
@@ -175,7 +183,10 @@ int32_t ms_abi_version(void);
  * the natural-order ILU(0).  `ref_cell` is the active index of the cell whose
  * pressure is fixed at 0 (the problem statement's reference cell; row and
  * column ref_cell lose their off-diagonal entries and q[ref_cell] is taken as
- * 0).  No values are computed until ms_assemble_tpfa. */
+ * 0).  No values are computed until ms_assemble_tpfa.  Non-positive sizes,
+ * a grid of more than 2^30 cells or without active cells, invalid
+ * non-neighbour connections and a ref_cell outside the active cells are
+ * MS_ERR_INVALID_ARG. */
 ms_status ms_system_create(ms_ctx *ctx, const ms_grid *grid, int32_t ref_cell, ms_system **out);
 ms_status ms_system_release(ms_system *sys);
 ms_status ms_system_get_info(const ms_system *sys, ms_system_info *info);
@@ -323,7 +334,9 @@ ms_status ms_add_adaptive_basis(ms_ctx *ctx, ms_system *sys, const double *dp, c
 /* --------------------------------------------------------- coarse operator */
 /* Galerkin coarse operator A_c = P^T A P with the pinned A (Eq. (10),
  * R = P^T) and its dense Cholesky factorisation and inverse for the coarse
- * solve.  precision MS_PREC_MIXED factors in FP32 and refines in FP64. */
+ * solve.  precision MS_PREC_MIXED factors in FP32 and refines in FP64 (an
+ * FP32 factor that fails falls back to FP64).  A non-positive pivot in FP64
+ * is MS_ERR_COARSE_SINGULAR. */
 ms_status ms_galerkin(ms_ctx *ctx, ms_system *sys, const ms_basis *basis, int32_t precision, ms_coarse **out);
 /* Coarse stage with the chosen restriction (ms_restriction): A_c = R A P with
  * the pinned A.  MS_RESTRICT_GALERKIN is ms_galerkin.  MS_RESTRICT_FV takes
