@@ -1,0 +1,58 @@
+"""Host-side pieces of the benchmark (CPU): the ncu traffic figures it reports
+are taken only while the kernel's source is unchanged since the capture, the
+roofline peak falls back when the measured peaks file is absent, and the
+reference arm's iteration counts come from the stored oracle run."""
+import json
+import os
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _tree(tmp_path, src_text, line):
+    (tmp_path / "profiles").mkdir()
+    csrc = tmp_path / "paper_2001_01624_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "k_demo.cu").write_text(src_text)
+    (tmp_path / "profiles" / "ncu_traffic.txt").write_text("# header\n" + line + "\n")
+
+
+def test_traffic_taken_only_for_the_captured_source(tmp_path, monkeypatch):
+    import hashlib
+    src = "__global__ void k() {}\n"
+    sha = hashlib.sha256(src.encode()).hexdigest()[:16]
+    _tree(tmp_path, src, f"demo 123456 k_demo.cu {sha}")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.ncu_traffic("demo") == 123456.0
+    assert bench.ncu_traffic("other") is None
+    (tmp_path / "paper_2001_01624_gb300" / "csrc" / "k_demo.cu").write_text(src + "// changed\n")
+    assert bench.ncu_traffic("demo") is None                   # source changed since the capture
+
+
+def test_committed_traffic_lines_parse():
+    for ln in open(os.path.join(ROOT, "profiles", "ncu_traffic.txt")):
+        f = ln.split()
+        if ln.startswith("#") or not f:
+            continue
+        assert len(f) == 4 and float(f[1]) > 0 and len(f[3]) == 16
+        assert os.path.exists(os.path.join(ROOT, "paper_2001_01624_gb300", "csrc", f[2]))
+
+
+def test_peak_fallback_without_measured_file(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_peak() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6700.5}))
+    assert bench.measured_peak() == (6700.5, "measured")
+
+
+def test_reference_counts_from_the_stored_oracle_run():
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_c2_seed0_gmres.json")))
+    assert bench.full_counts() == (int(gold["basis_iters"]), int(gold["steps"]))
+    rich = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_c2_seed0.json")))
+    assert rich["basis_iters"] == gold["basis_iters"] == 338        # one basis, two outer iterations
+
+
+def test_reference_counts_absent(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ORACLE_GOLD_GMRES", str(tmp_path / "missing.json"))
+    assert bench.full_counts() is None
