@@ -300,19 +300,10 @@ __global__ void __launch_bounds__(kLevelThreads) k_level_sweep(int n, int W, int
 constexpr int kSegThreads = 64;          // two warps, one segment each at a time
 constexpr int kSegPer = kSegMax / 32;    // rows per lane
 
-__device__ __forceinline__ void ld_relaxed_v2(const unsigned long long *p, unsigned long long &a,
-                                              unsigned long long &b) {
-    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
-}
-
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
     unsigned long long v;
     asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
-}
-
-__device__ __forceinline__ void st_relaxed_v2(unsigned long long *p, unsigned long long a, unsigned long long b) {
-    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
 }
 
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {

@@ -27,42 +27,6 @@ namespace {
 
 constexpr long long kSpinLimit = 1ll << 24;
 
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
-
-__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-// Bounded wait until *p >= need (thread 0 only).
-__device__ __forceinline__ unsigned long long wait_progress(const unsigned long long *p, unsigned long long need,
-                                                            int *sync) {
-    unsigned long long v = ld_acquire_u64(p);
-    long long spins = 0;
-    while (v < need) {
-        if ((++spins & 255) == 0) {
-            if (*((volatile int *)&sync[3]) != 0) return need;
-            if (spins > kSpinLimit) {
-                atomicOr(&sync[3], kErrTimeout);
-                return need;
-            }
-        }
-        v = ld_acquire_u64(p);
-    }
-    return v;
-}
-
 // Tagged words: a 32-bit payload with the 32-bit sweep counter in the high
 // half, written and read as single 64-bit accesses.  A consumer accepts a
 // word only when its tag is the current sweep's, so no flag, fence or
