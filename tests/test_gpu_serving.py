@@ -37,7 +37,6 @@ def _stream(models, steps, rate):
 
 
 def _run(workers, budget=None, steps=4):
-    import paper_2001_01624_gb300 as ms
     from paper_2001_01624_gb300 import geomodel as G, serve
     models = _models(G, serve)
     srv = serve.Server(torch, torch.device("cuda:0"), models, workers=workers, hbm_budget=budget)
