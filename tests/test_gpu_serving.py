@@ -8,6 +8,14 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
 def _models(G, serve):
     shapes = [(14, 12, 6), (20, 9, 5), (11, 16, 7), (18, 18, 4)]
     gms = [G.lognormal_box(*sh, seed=50 + k, sigma=1.5, block=(5, 4, 3), kz_ratio=0.1) for k, sh in enumerate(shapes)]
