@@ -24,7 +24,10 @@ support_box            Sec. 5 requirement 2                        hand-worked b
 support_hop            Sec. 5 requirement 2                        hand-worked 1D example (tests/golden)
 msrsb_basis            Sec. 5.1 (MsRSB, localized iterations)      partition of unity; confinement; P >= 0;
                                                                    closed-form converged hat for two blocks in
-                                                                   1D (and its 2D / 3D tensor products)
+                                                                   1D (and its 2D / 3D tensor products); values
+                                                                   and increments of iterations 1 and 2 worked
+                                                                   by hand on a 4-cell chain (omega, update from
+                                                                   old values, renormalisation, stop test)
 galerkin               Eq. (10), R = P^T                           symmetry; positive definiteness; P^T A 1 = 0
                                                                    for the unpinned A; dense P^T A P by numpy
 cholesky(_solve)       coarse solve (A_c)^-1                       numpy.linalg.solve
@@ -47,7 +50,9 @@ ilu0 / ilu0_apply      Sec. 5.1 / 6.4 ILU(0)                       (L U)_ij = A_
                                                                    property); exact on tridiagonal A
 ms_solve               Eq. (11) in Richardson (Sec. 5.2)           dense direct solve; identity partition
                                                                    converges in one cycle; A-norm error does not
-                                                                   grow per coarse stage
+                                                                   grow per coarse stage; first cycle with one
+                                                                   and two stages worked by hand on a 4-cell
+                                                                   ring (smoother before each coarse stage)
 cost_model             Eq. (12)                                    sum of the itemised Sec. 6.4 counts
 =====================  ==========================================  ============================================
 """

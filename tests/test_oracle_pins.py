@@ -318,6 +318,82 @@ def test_basis_constant_reproduction_and_galerkin():
     np.testing.assert_allclose(Ac, P.T @ Ap.dense() @ P, rtol=1e-12, atol=1e-12 * np.abs(Ac).max())
 
 
+def _csr_from_rows(rows):
+    A = np.array(rows, dtype=np.float64)
+    n = A.shape[0]
+    rp, ci, v = [0], [], []
+    for i in range(n):
+        for j in range(n):
+            if A[i, j] != 0.0 or i == j:
+                ci.append(j)
+                v.append(A[i, j])
+        rp.append(len(ci))
+    return O.CSR(n, np.array(rp, np.int32), np.array(ci, np.int32), np.array(v))
+
+
+def _frac(pairs):
+    return np.array([a / b for a, b in pairs])
+
+
+def _basis_from_support(part, supports):
+    sptr = np.cumsum([0] + [len(s) for s in supports]).astype(np.int32)
+    return sptr, np.concatenate([np.asarray(s, np.int32) for s in supports])
+
+
+def test_msrsb_iterations_hand_worked():
+    """One and two MsRSB iterations against the hand derivation
+    (tests/golden/hand_worked.json: omega = 2/3, update from the old values,
+    then renormalisation of every cell); a wrong omega, a Gauss-Seidel update
+    or a missing renormalisation each changes these values."""
+    gd = GOLD["msrsb_two_iterations_1d"]
+    A = _csr_from_rows(gd["A_rows"])
+    sptr, sc = _basis_from_support(gd["part"], gd["supports"])
+    omega = gd["omega"][0] / gd["omega"][1]
+    for k, key in ((1, "expected_iter1"), (2, "expected_iter2")):
+        B = O.msrsb_basis(A, gd["part"], 2, sptr, sc, omega=omega, tol=0.0, max_iter=k)
+        assert B.iters == k
+        for j in range(2):
+            ev = gd[key][j]
+            want = _frac(list(zip(ev[0::2], ev[1::2])))
+            np.testing.assert_allclose(B.pval[sptr[j]:sptr[j + 1]], want, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(B.inc_hist, _frac(gd["expected_increments"][:k]), rtol=0, atol=1e-15)
+    # the stopping test: the increment of iteration 2 (4/81 = 0.0494) is below 0.05, not below 0.04
+    assert O.msrsb_basis(A, gd["part"], 2, sptr, sc, omega=omega, tol=0.05, max_iter=50).iters == 2
+    assert O.msrsb_basis(A, gd["part"], 2, sptr, sc, omega=omega, tol=0.04, max_iter=50).iters > 2
+
+
+def test_ms_cycle_stage_order_hand_worked():
+    """First Richardson cycle of the multistage iteration (Eq. (11)) against
+    the hand derivation on a four-cell ring whose ILU(0) drops fill: the
+    ILU(0) step comes before each stage's coarse correction.  Post-smoothing
+    or the coarse correction first gives other iterates."""
+    gd = GOLD["ms_cycle_ring4"]
+    A = _csr_from_rows(gd["A_rows"])
+    q = np.array(gd["q"], np.float64)
+    lu = O.ilu0(A)
+    np.testing.assert_allclose(O.ilu0_apply(A, lu, q), _frac(gd["expected_smoothed_x_stage1"]), rtol=0,
+                               atol=1e-15)
+    stages = []
+    for part in gd["stage_parts"]:
+        B = O.constant_basis(part, 2)
+        Ac = O.galerkin(A, B)
+        np.testing.assert_array_equal(Ac, np.array(gd["expected_Ac"], np.float64))
+        stages.append((B, O.cholesky(Ac)))
+    for ns, xk, rk in ((1, "expected_x_one_stage", "expected_res_one_stage"),
+                       (2, "expected_x_two_stages", "expected_res_two_stages")):
+        r = O.ms_solve(A, stages[:ns], q, tol=0.0, max_iter=1, lu=lu)
+        assert r.iters == 1 and not r.converged
+        np.testing.assert_allclose(r.x, _frac(gd[xk]), rtol=0, atol=1e-15)
+        assert r.hist[1] == pytest.approx(gd[rk][0] / gd[rk][1], rel=1e-13)
+    # the same cycle as the preconditioner of GMRES: its first step from
+    # x = 0 is the minimal-residual multiple of the one-stage cycle applied to q
+    z = _frac(gd["expected_x_one_stage"])
+    Az = A.dense() @ z
+    alpha = (Az @ q) / (Az @ Az)
+    g = O.ms_gmres(A, stages[:1], q, tol=0.0, max_iter=1, restart=30, lu=lu)
+    np.testing.assert_allclose(g.x, alpha * z, rtol=1e-13)
+
+
 # ----------------------------------------------------------------------------- partitions & supports
 def _chain(nx, ny=1, nz=1):
     g = _grid(nx, ny, nz)
