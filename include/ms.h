@@ -50,7 +50,7 @@
 extern "C" {
 #endif
 
-#define MS_ABI_VERSION 6
+#define MS_ABI_VERSION 7
 
 typedef enum {
     MS_OK = 0,
@@ -248,6 +248,27 @@ ms_status ms_ilu_apply(ms_ctx *ctx, ms_system *sys, int32_t precision, const dou
  *    ms_ilu_apply uses the tiled sweeps).  Waits for the context's stream
  *    before returning, to report a timed-out sweep as MS_ERR_TIMEOUT. */
 ms_status ms_ilu_apply_noalloc(ms_ctx *ctx, const ms_system *sys, const double *r, double *z);
+
+/* Bound of one device-side wait in this system's ILU(0) sweeps and its
+ * structured ILU(0) factorisation (the paper runs on one CPU and has no
+ * counterpart; the library bounds every wait so that a stalled dataflow
+ * sweep returns an error instead of hanging the GPU).  A sweep whose wait
+ * exceeds the bound stops waiting, the call returns MS_ERR_TIMEOUT, and the
+ * system stays usable.  seconds in (0, 60]; 0 restores the default of 2 s;
+ * anything else is MS_ERR_INVALID_ARG.  Ordered on the context's stream. */
+ms_status ms_set_wait_limit(ms_ctx *ctx, ms_system *sys, double seconds);
+
+/* Failure-path testing of the bounded waits (no counterpart in the paper):
+ * the next forward ILU(0) segment sweep of this system (the sweeps of grids
+ * with inactive cells or non-neighbour connections) starts handing out
+ * segments at position `count` of its hand-out order, so the first `count`
+ * segments are never solved and every segment that needs their results
+ * waits until the bound of ms_set_wait_limit runs out; that call then
+ * returns MS_ERR_TIMEOUT.  Nothing is written out of bounds and later sweeps
+ * run normally.  Requires the ILU(0) factors of `precision` (MS_ERR_STATE
+ * if missing, or if the system's sweeps are not the segment sweeps);
+ * count in [1, number of segments), else MS_ERR_INVALID_ARG. */
+ms_status ms_debug_withhold_segments(ms_ctx *ctx, ms_system *sys, int32_t precision, int32_t count);
 
 /* Segments of the ILU(0) segment sweeps for a sparsity pattern (Sec. 5.1
  * smoother S, Sec. 6.4 "Smooth": the two triangular solves of natural-order

@@ -125,6 +125,8 @@ def lib():
         "ms_spmv": ([_vp, _vp, _vp, _vp], _i32),
         "ms_ilu_apply": ([_vp, _vp, _i32, _vp, _vp], _i32),
         "ms_ilu_apply_noalloc": ([_vp, _vp, _vp, _vp], _i32),
+        "ms_set_wait_limit": ([_vp, _vp, _d], _i32),
+        "ms_debug_withhold_segments": ([_vp, _vp, _i32, _i32], _i32),
         "ms_plan_segments": ([_vp, _i32, _vp, _vp, _i32, _vp, P(_i32), _vp, _vp, P(_i32)], _i32),
         "ms_partition_cartesian": ([_vp, _vp, _i32, _i32, _i32, _vp, P(_i32)], _i32),
         "ms_partition_components": ([_vp, _vp, _vp, _vp, P(_i32)], _i32),
@@ -164,7 +166,8 @@ def lib():
 def exported_symbols() -> Sequence[str]:
     return ["ms_abi_version", "ms_status_string", "ms_last_error", "ms_create", "ms_destroy", "ms_set_stream",
             "ms_system_create", "ms_system_release", "ms_system_get_info", "ms_assemble_tpfa",
-            "ms_system_get_matrix", "ms_spmv", "ms_ilu_apply", "ms_ilu_apply_noalloc", "ms_plan_segments", "ms_partition_cartesian", "ms_partition_components", "ms_partition_dynamic",
+            "ms_system_get_matrix", "ms_spmv", "ms_ilu_apply", "ms_ilu_apply_noalloc", "ms_set_wait_limit",
+            "ms_debug_withhold_segments", "ms_plan_segments", "ms_partition_cartesian", "ms_partition_components", "ms_partition_dynamic",
             "ms_partition_wells", "ms_coarse_create", "ms_dense_inverse", "ms_cpr_pressure_system",
             "ms_build_basis", "ms_basis_rebuild", "ms_basis_update", "ms_basis_release", "ms_basis_get_info",
             "ms_basis_get", "ms_add_adaptive_basis", "ms_galerkin", "ms_coarse_refresh", "ms_coarse_release",
@@ -290,6 +293,14 @@ def ms_ilu_apply(ctx, sys, r, z, precision: int = MS_PREC_FP64):
 def ms_ilu_apply_noalloc(ctx, sys, r, z):
     """Allocation-free ILU(0) application: r and z must be device tensors."""
     _check(lib().ms_ilu_apply_noalloc(ctx, sys, _ptr(r), _ptr(z)), ctx)
+
+
+def ms_set_wait_limit(ctx, sys, seconds: float):
+    _check(lib().ms_set_wait_limit(ctx, sys, float(seconds)), ctx)
+
+
+def ms_debug_withhold_segments(ctx, sys, count: int, precision: int = MS_PREC_FP64):
+    _check(lib().ms_debug_withhold_segments(ctx, sys, precision, int(count)), ctx)
 
 
 # --------------------------------------------------------------- partitions

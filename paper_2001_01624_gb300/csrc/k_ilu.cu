@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level_sweep(int n, int W, int
     const int gsize = G * blockDim.x;
     const int j0 = threadIdx.x * G + blockIdx.x;     // rows of a level spread over all blocks first
     GridSync gs;
-    gs.begin(bar, err);
+    gs.begin(bar, err, wait_limit_ns(err));   // err = sync word 3 of the system
     LevelRow<T> row;
     {
         const int L = BWD ? nlev - 1 : 0;
@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_sweep(int n, int nseg, int 
                     if (*((volatile int *)&sync[3]) != 0) failed = true;
                     const unsigned long long now = gs_now_ns();
                     if (t0 == 0) t0 = now;
-                    else if (now - t0 > 2000000000ull) {
+                    else if (now - t0 > wait_limit_ns(sync + 3)) {
                         atomicOr(&sync[3], kErrTimeout);
                         failed = true;
                     }

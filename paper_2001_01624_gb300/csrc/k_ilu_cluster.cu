@@ -52,7 +52,6 @@ constexpr int kClusterSplitFrom = 4;
 __host__ __device__ constexpr int scan_levels(int L) { return L >= 32 ? 5 : L >= 16 ? 4 : L >= 8 ? 3 : L >= 4 ? 2 : 1; }
 __host__ __device__ constexpr int scan_table(int L) { return L * scan_levels(L); }
 constexpr int NBX = 4;   // row-exchange ring: lines a row may run ahead of the next
-constexpr unsigned long long kWaitNs = 2000000000ull;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -176,7 +175,7 @@ __device__ __forceinline__ bool wait_lane(unsigned bar, unsigned parity, int *er
         if ((++spins & 63) == 0) {
             const unsigned long long now = global_ns();
             if (t0 == 0) t0 = now;
-            else if (now - t0 > kWaitNs) {
+            else if (now - t0 > wait_limit_ns(err)) {
                 atomicOr(err, kErrTimeout);
                 return false;
             }
@@ -298,7 +297,7 @@ __global__ void __launch_bounds__(544, 1)
                 if ((++idle & 63) == 0) {
                     const unsigned long long now = __shfl_sync(FULL, global_ns(), 0);
                     if (t0 == 0) t0 = now;
-                    else if (now - t0 > kWaitNs) {
+                    else if (now - t0 > wait_limit_ns(err)) {
                         if (lane == 0) atomicOr(err, kErrTimeout);
                         break;
                     }
@@ -343,7 +342,7 @@ __global__ void __launch_bounds__(544, 1)
                     if (ready == 0) {
                         const unsigned long long now = __shfl_sync(0xffffffffu, global_ns(), 0);
                         if (t0 == 0) t0 = now;
-                        else if (now - t0 > kWaitNs) {
+                        else if (now - t0 > wait_limit_ns(err)) {
                             if (lane == 0) atomicOr(err, kErrTimeout);
                             ok = false;
                         }
@@ -633,7 +632,7 @@ __global__ void __launch_bounds__(544, 1)
                 if ((++idle & 63) == 0) {
                     const unsigned long long now = __shfl_sync(FULL, global_ns(), 0);
                     if (t0 == 0) t0 = now;
-                    else if (now - t0 > kWaitNs) {
+                    else if (now - t0 > wait_limit_ns(err)) {
                         if (lane == 0) atomicOr(err, kErrTimeout);
                         break;
                     }

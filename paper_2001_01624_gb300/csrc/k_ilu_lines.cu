@@ -225,7 +225,8 @@ __global__ void __launch_bounds__(256, 1) k_line_sweep(int nx, int ny, int nz, i
         if (kf) bulk_g2s(kwin + (size_t)q * nx * 2, kface + (((long long)prodK * TJ + tj) * nx) * 2, (unsigned)nx * 16, bar);
     };
     // the copies read valid memory and always complete; the wait is still
-    // bounded (2 s of device time) and reports a timeout instead of hanging
+    // bounded (2 s of device time unless the system sets another bound) and
+    // reports a timeout instead of hanging
     auto wait_slot = [&](int q, unsigned parity) {
         unsigned long long t0 = 0;
         int spins = 0;
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(256, 1) k_line_sweep(int nx, int ny, int nz, i
             if ((++spins & 63) == 0) {
                 const unsigned long long now = global_ns();
                 if (t0 == 0) t0 = now;
-                else if (now - t0 > 2000000000ull) {
+                else if (now - t0 > wait_limit_ns(sync + 3)) {
                     atomicOr(&sync[3], kErrTimeout);
                     break;
                 }

@@ -604,6 +604,38 @@ ms_status ms_ilu_apply(ms_ctx *ctx, ms_system *s, int32_t precision, const doubl
     API_CATCH(ctx)
 }
 
+ms_status ms_set_wait_limit(ms_ctx *ctx, ms_system *s, double seconds) {
+    if (!ctx || !s) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    if (!(seconds >= 0.0 && seconds <= 60.0)) return fail(ctx, MS_ERR_INVALID_ARG, "wait limit must be in [0, 60] s");
+    API_TRY
+    DeviceGuard g(ctx->device);
+    int us = seconds == 0.0 ? 0 : std::max(1, (int)std::lround(seconds * 1e6));
+    MS_CUDA(cudaMemcpyAsync(s->sync.p + 4, &us, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    sync(ctx->stream);
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_debug_withhold_segments(ms_ctx *ctx, ms_system *s, int32_t precision, int32_t count) {
+    if (!ctx || !s) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    API_TRY
+    DeviceGuard g(ctx->device);
+    const int p = precision == MS_PREC_MIXED ? 1 : 0;
+    MS_REQUIRE(s->assembled && (p ? s->ilu32_valid : s->ilu64_valid), MS_ERR_STATE,
+               "needs the ILU(0) factors of that precision (run ms_ilu_apply first)");
+    MS_REQUIRE(!s->structured && s->ilu_kind[p] == 5 && s->n_seg > 0 && s->seg_kg[0] <= kSegMaxKG &&
+                   s->seg_kg[1] <= kSegMaxKG && (p ? (const void *)s->seg_v32.p : (const void *)s->seg_v64.p),
+               MS_ERR_STATE, "the system's ILU(0) sweeps are not the segment sweeps");
+    MS_REQUIRE(count >= 1 && count < s->n_seg, MS_ERR_INVALID_ARG, "count must be in [1, number of segments)");
+    // the next segment sweep hands out tickets from `count` on; sweep_end
+    // resets the ticket for every later sweep
+    int v = count;
+    MS_CUDA(cudaMemcpyAsync(s->sync.p + 1, &v, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    sync(ctx->stream);
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
 ms_status ms_plan_segments(ms_ctx *ctx, int32_t n, const int32_t *rowptr, const int32_t *col, int32_t max_len,
                            int32_t *seg_off, int32_t *n_seg, int32_t *order, int32_t *kg, int32_t *width) {
     if (!rowptr || !col || !seg_off || !n_seg || !order || !kg || !width)

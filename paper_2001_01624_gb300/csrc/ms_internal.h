@@ -90,8 +90,19 @@ constexpr int kSlotPad = 0x7fffffff;   // padding block id in basis slot lists (
 
 // Device-side synchronisation words of the level-ordered sweeps:
 // [0] sweep counter, [1] ticket (a CTA's, or a warp's in the segment sweeps), [2] CTAs done,
-// [3] error flags.
+// [3] error flags, [4] bound of one device-side wait of this system's sweeps in
+// microseconds (0: kDefaultWaitNs).
 constexpr int kSyncWords = 8;
+constexpr unsigned long long kDefaultWaitNs = 2000000000ull;
+
+#ifdef __CUDACC__
+// Bound of a device-side wait, read (only once a wait is already long) from
+// the word after a system's error word `errw` (sync word 3).
+__device__ __forceinline__ unsigned long long wait_limit_ns(const int *errw) {
+    const int us = *((volatile const int *)(errw + 1));
+    return us > 0 ? (unsigned long long)us * 1000ull : kDefaultWaitNs;
+}
+#endif
 constexpr int kSegMax = 256;       // rows per segment of the segment sweeps (8 per lane)
 constexpr int kSegMaxKG = 8;       // couplings per row leaving its segment, per direction
 constexpr int kErrTimeout = 1;
