@@ -42,10 +42,8 @@ WORKLOAD = ("3D 60x220x85 Cartesian (1,122,000 cells), TPFA 7-point, top 35 laye
             "preconditioner of GMRES(30) to 1e-6")
 OUTER = {"gmres": (1, 30), "richardson": (0, 30)}
 FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 rate of the GB300
-ORACLE_GOLD_GMRES = os.path.join(ROOT, "tests", "golden", "oracle_c2_seed0_gmres.json")
 METRIC = "fine-cell unknowns/sec to 1e-6 rel residual (full hot path per step)"
 UNIT = "unknowns/s"
-ORACLE_GOLD = os.path.join(ROOT, "tests", "golden", "oracle_c2_seed0.json")
 
 
 def parse():
@@ -56,6 +54,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-single", action="store_true",
+                    help="also time one full step of the single-threaded oracle (about a minute)")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-fv", action="store_true")
     ap.add_argument("--no-cpr", action="store_true")
@@ -171,47 +171,73 @@ def dist_env():
 
 
 # ---------------------------------------------------------------- oracle leg
-def oracle_sample(gm, basis_iters, cycles, full_basis, full_cycles, outer="gmres"):
-    """Time the CPU oracle on a bounded sample of the step and scale the
-    iteration phases to the full iteration counts.  Returns (seconds for a
-    full step, description)."""
-    import oracle as O
-    t = {}
-    t0 = time.perf_counter()
-    s = O.assemble_tpfa(gm.grid, gm.perm)
-    Ap, qp = O.pin(s.A, gm.q_active(), 0)
-    part, M = O.partition_cartesian(gm.grid, s.cells, gm.block)
-    sp, sc = O.support_box(gm.grid, s.cells, s.A, part, M, gm.block)
-    t["fixed"] = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    B = O.msrsb_basis(s.A, part, M, sp, sc, 2.0 / 3.0, 0.0, basis_iters)
-    t["basis"] = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    L = O.cholesky(O.galerkin(Ap, B))
-    lu = O.ilu0(Ap)
-    t["fixed"] += time.perf_counter() - t0
-    t0 = time.perf_counter()
-    if outer == "gmres":
-        O.ms_gmres(Ap, [(B, L)], qp, tol=0.0, max_iter=cycles, restart=OUTER["gmres"][1], lu=lu)
-    else:
-        O.ms_solve(Ap, [(B, L)], qp, tol=0.0, max_iter=cycles, lu=lu)
-    t["solve"] = time.perf_counter() - t0
-    full = t["fixed"] + t["basis"] * full_basis / basis_iters + t["solve"] * full_cycles / cycles
-    what = "GMRES(30) steps (one full restart)" if outer == "gmres" else "Richardson cycles"
-    desc = (f"oracle (plain C, FP64, 1 thread) on the same workload: assembly, pin, partition, supports, "
-            f"Galerkin, Cholesky, ILU(0) factor in full; {basis_iters} of {full_basis} basis iterations and "
-            f"{cycles} of {full_cycles} {what} timed, scaled to the full counts "
-            f"(measured {t['fixed'] + t['basis'] + t['solve']:.1f} s)")
-    return full, desc
-
-
-def full_counts():
-    """(basis iterations, GMRES steps) of the stored full oracle run."""
+def host_cpu():
+    """(logical CPUs, CPU model) of this host."""
+    model = ""
     try:
-        g = json.load(open(ORACLE_GOLD_GMRES))
-        return int(g["basis_iters"]), int(g["steps"])
-    except (OSError, KeyError, ValueError):
-        return None
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                k = ln.split(":", 1)
+                if len(k) == 2 and k[0].strip() in ("model name", "Model name"):
+                    model = k[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for ln in out.splitlines():
+                if ln.startswith("Model name:"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return os.cpu_count() or 1, model or "unknown"
+
+
+def oracle_full_step(gm, openmp=True, outer="gmres"):
+    """One complete step of the workload by the CPU oracle, nothing sampled or
+    extrapolated: assembly, pin, partition, supports, MsRSB basis to increment
+    1e-3, Galerkin, Cholesky, ILU(0) factors, and the solve from p = 0 to
+    1e-6.  openmp selects the OpenMP build (all host cores) or the
+    single-threaded correctness build.  Returns dict(seconds, phases, counts,
+    threads)."""
+    import oracle as O
+    O.use_openmp(openmp)
+    try:
+        threads = O.openmp_threads() if openmp else 1
+        ph = {}
+        t0 = time.perf_counter()
+        s = O.assemble_tpfa(gm.grid, gm.perm)
+        Ap, qp = O.pin(s.A, gm.q_active(), 0)
+        part, M = O.partition_cartesian(gm.grid, s.cells, gm.block)
+        sp, sc = O.support_box(gm.grid, s.cells, s.A, part, M, gm.block)
+        t1 = time.perf_counter()
+        B = O.msrsb_basis(s.A, part, M, sp, sc, 2.0 / 3.0, 1e-3, 500)
+        t2 = time.perf_counter()
+        L = O.cholesky(O.galerkin(Ap, B))
+        lu = O.ilu0(Ap)
+        t3 = time.perf_counter()
+        if outer == "gmres":
+            r = O.ms_gmres(Ap, [(B, L)], qp, tol=1e-6, max_iter=5000, restart=OUTER["gmres"][1], lu=lu)
+        else:
+            r = O.ms_solve(Ap, [(B, L)], qp, tol=1e-6, max_iter=5000, lu=lu)
+        t4 = time.perf_counter()
+    finally:
+        O.use_openmp(False)
+    ph = {"setup": t1 - t0, "basis": t2 - t1, "coarse_ilu": t3 - t2, "solve": t4 - t3}
+    return {"seconds": t4 - t0, "phases": {k: round(v, 3) for k, v in ph.items()}, "basis_iters": int(B.iters),
+            "steps": int(r.iters), "converged": bool(r.converged), "threads": threads}
+
+
+def cpu_baseline_line(n, res, what="one full step of the same workload"):
+    nproc, model = host_cpu()
+    build = (f"OpenMP build on {res['threads']} threads" if res["threads"] > 1
+             else "single-threaded build")
+    return {"value": n / res["seconds"], "unit": UNIT, "cores": res["threads"], "kind": "oracle",
+            "sample": f"{what} (basis {res['basis_iters']} iterations, GMRES(30) {res['steps']} steps) by the "
+                      f"oracle (plain C, FP64), {build}; timed in full, nothing extrapolated",
+            "seconds": res["seconds"], "phases": res["phases"], "nproc": nproc, "cpu_model": model}
 
 
 def run_reference(args):
@@ -221,27 +247,22 @@ def run_reference(args):
     from paper_2001_01624_gb300 import geomodel as G
     import oracle as O
     O.build()
+    O.build(openmp=True)
     gm = G.config2(0)
-    counts = full_counts()
-    if counts is None:
-        print(json.dumps({"impl": "reference", "unavailable": "oracle iteration counts file missing"}))
-        return 0
-    fb, fc = counts
     n = gm.grid.n_active()
     for _ in range(args.warmup):
-        oracle_sample(gm, 8, 10, fb, fc)
-    secs = []
-    desc = ""
-    for _ in range(args.steps):
-        s, desc = oracle_sample(gm, 8, 10, fb, fc)
-        secs.append(s)
-    tot = sum(secs)
-    v = n * len(secs) / tot
+        oracle_full_step(gm)
+    runs = [oracle_full_step(gm) for _ in range(args.steps)]
+    tot = sum(r["seconds"] for r in runs)
+    v = n * len(runs) / tot
+    cb = cpu_baseline_line(n, runs[-1], what=f"{len(runs)} full steps of the same workload, each")
+    cb["value"] = v
+    cb["seconds"] = tot / len(runs)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(secs),
+            "steps": len(runs), "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(runs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "cells": n, "precision": "fp64", "parallelism": "replicas"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -926,12 +947,11 @@ def main():
 
     # CPU oracle baseline (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        counts = full_counts()
-        if counts:
-            secs, desc = oracle_sample(gm, 40, 30, counts[0], counts[1])
-            line["cpu_baseline"] = {"value": n / secs, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
-        else:
-            line["cpu_baseline"] = None
+        import oracle as O
+        O.build(openmp=True)
+        line["cpu_baseline"] = cpu_baseline_line(n, oracle_full_step(gm))
+        if args.oracle_single:
+            line["cpu_baseline"]["single_thread"] = cpu_baseline_line(n, oracle_full_step(gm, openmp=False))
 
     for p in plans.values():
         p.release()

@@ -1,6 +1,9 @@
 """CPU oracle for the multiscale multibasis pressure solver -- TEST INFRASTRUCTURE.
 
-Plain FP64, single-threaded C (``ms_oracle.c``) behind a ctypes shim.  Only
+Plain FP64 C (``ms_oracle.c``) behind a ctypes shim, built single-threaded
+(the correctness oracle) and, for timing the method on all host cores only,
+with OpenMP (``use_openmp``; bitwise the same results except the rounding of
+dot products and norms).  Only
 ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
 ``--impl reference`` legs of ``bench.py`` may import this package.  It shares
 no code with the CUDA library: the two are compared on the same seeded
@@ -70,6 +73,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ms_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libms_oracle.so")
+_LIB_OMP = os.path.join(_BUILD, "libms_oracle_omp.so")
 
 OK, EINVAL, ENOMEM, ENOTCONV, ESINGULAR = 0, 1, 2, 4, 5
 
@@ -80,17 +84,36 @@ class OracleError(RuntimeError):
         self.code = code
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C11, -O2, no architecture flags)."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with gcc (plain C11, -O2, no architecture flags);
+    openmp=True builds the OpenMP variant used for timing."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+    path = _LIB_OMP if openmp else _LIB
+    if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+        tmp = path + f".tmp{os.getpid()}"
+        extra = ["-fopenmp"] if openmp else []
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared"] + extra + ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, path)
+    return path
 
 
 _lib = None
+_lib_omp = None
+_use_omp = False
+
+
+def use_openmp(on: bool = True) -> None:
+    """Route later calls to the OpenMP build (timing on all host cores; its
+    thread count follows OMP_NUM_THREADS) or back to the single-threaded one."""
+    global _use_omp
+    _use_omp = bool(on)
+
+
+def openmp_threads() -> int:
+    """Threads the OpenMP build runs with (builds it if needed)."""
+    L = _load(True)
+    L.or_threads.restype = _i
+    return int(L.or_threads())
 
 _i = C.c_int
 _d = C.c_double
@@ -113,10 +136,19 @@ class _Adapt(C.Structure):
 
 
 def lib():
-    global _lib
-    if _lib is None:
-        _lib = C.CDLL(build())
-        L = _lib
+    return _load(_use_omp)
+
+
+def _load(omp: bool):
+    global _lib, _lib_omp
+    cur = _lib_omp if omp else _lib
+    if cur is None:
+        cur = C.CDLL(build(openmp=omp))
+        if omp:
+            _lib_omp = cur
+        else:
+            _lib = cur
+        L = cur
         L.or_free.argtypes = [_vp]
         L.or_tpfa_assemble.argtypes = [_i, _i, _i, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _i, _vp, _vp, _vp,
                                        _vp, _vp, _pi, _ppi, _pi, _ppi, _ppi, _ppd, _ppi, _ppi, _ppd]
@@ -157,7 +189,7 @@ def lib():
         L.or_transport_step.argtypes = [_i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d, _d, _d, _d, _pi]
         L.or_cost_model.argtypes = [_d, _d, _d, _d, _d]
         L.or_cost_model.restype = _d
-    return _lib
+    return cur
 
 
 def _p(a):

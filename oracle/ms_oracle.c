@@ -9,9 +9,15 @@
  * test suite, the smoke check and the CPU-baseline leg of the benchmark load
  * it.  It shares no code, header, table or helper with the CUDA library.
  *
- * Every routine is single-threaded, double precision, and follows the paper's
- * steps in the paper's order.  Where the paper is silent the routine follows
- * one stated reading (each is named in its comment).
+ * Every routine is double precision and follows the paper's steps in the
+ * paper's order.  Where the paper is silent the routine follows one stated
+ * reading (each is named in its comment).  The library is built twice: once
+ * single-threaded (the correctness oracle the tests compare against) and
+ * once with -fopenmp, only to time the method on all host cores.  The
+ * OpenMP build splits loops whose iterations each write their own outputs
+ * (rows of a product, basis columns, cells, coarse columns), which gives
+ * bitwise the single-threaded results, and sums dot products and norms in
+ * per-thread partial sums, which changes only their rounding.
  *
  * Memory: routines that produce variable-size results return malloc'd arrays
  * through out-pointers; release them with or_free().
@@ -24,6 +30,23 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#define OR_PAR_FOR _Pragma("omp parallel for schedule(static)")
+#define OR_PAR_FOR_DYN _Pragma("omp parallel for schedule(dynamic, 8)")
+#define OR_PRAGMA(x) _Pragma(#x)
+#define OR_PAR_SUM(v) OR_PRAGMA(omp parallel for schedule(static) reduction(+ : v))
+#define OR_PAR_MAX(v) OR_PRAGMA(omp parallel for schedule(static) reduction(max : v))
+#define OR_THREADS() omp_get_max_threads()
+#define OR_TID() omp_get_thread_num()
+#else
+#define OR_PAR_FOR
+#define OR_PAR_FOR_DYN
+#define OR_PAR_SUM(v)
+#define OR_PAR_MAX(v)
+#define OR_THREADS() 1
+#define OR_TID() 0
+#endif
 
 #define OR_OK 0
 #define OR_EINVAL 1
@@ -32,6 +55,9 @@
 #define OR_ESINGULAR 5
 
 void or_free(void *p) { free(p); }
+
+/* Threads the loops below run on (1 in the single-threaded build). */
+int or_threads(void) { return OR_THREADS(); }
 
 static void *xmalloc(size_t n) { return malloc(n ? n : 1); }
 static void *xcalloc(size_t n, size_t s) { return calloc(n ? n : 1, s ? s : 1); }
@@ -230,6 +256,7 @@ int or_pin(int n, const int *rowptr, const int *col, double *val, double *q, int
 
 /* y = A x  (CSR) */
 static void csr_mv(int n, const int *rp, const int *ci, const double *v, const double *x, double *y) {
+    OR_PAR_FOR
     for (int i = 0; i < n; ++i) {
         double s = 0.0;
         for (int p = rp[i]; p < rp[i + 1]; ++p) s += v[p] * x[ci[p]];
@@ -581,24 +608,42 @@ int or_msrsb_basis(int n, const int *rowptr, const int *col, const double *val,
     }
     for (int j = 0; j < M; ++j)
         for (int e = sptr[j]; e < sptr[j + 1]; ++e) pval[e] = (part[scells[e]] == j) ? 1.0 : 0.0;
-    double *w = (double *)xcalloc((size_t)n, sizeof(double));
+    /* entries of each cell in increasing entry order (block order), for the
+       per-cell sums of the renormalisation */
+    int *cp = (int *)xcalloc((size_t)n + 1, sizeof(int));
+    for (int e = 0; e < nnzp; ++e) cp[scells[e] + 1]++;
+    for (int i = 0; i < n; ++i) cp[i + 1] += cp[i];
+    int *ce = (int *)xmalloc((size_t)nnzp * sizeof(int));
+    int *f = (int *)xmalloc((size_t)n * sizeof(int));
+    memcpy(f, cp, (size_t)n * sizeof(int));
+    for (int e = 0; e < nnzp; ++e) ce[f[scells[e]]++] = e;
+    free(f);
+    const int nt = OR_THREADS();
+    double *w = (double *)xcalloc((size_t)n * nt, sizeof(double));   /* one dense work vector per thread */
     double *pn = (double *)xmalloc((size_t)nnzp * sizeof(double));
     double *rs = (double *)xmalloc((size_t)n * sizeof(double));
     int it = 0;
     while (it < max_iter) {
+        OR_PAR_FOR_DYN
         for (int j = 0; j < M; ++j) {
-            for (int e = sptr[j]; e < sptr[j + 1]; ++e) w[scells[e]] = pval[e];
+            double *wt = w + (size_t)n * OR_TID();
+            for (int e = sptr[j]; e < sptr[j + 1]; ++e) wt[scells[e]] = pval[e];
             for (int e = sptr[j]; e < sptr[j + 1]; ++e) {
                 int i = scells[e];
                 double ap = 0.0;
-                for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) ap += val[p] * w[col[p]];
+                for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) ap += val[p] * wt[col[p]];
                 pn[e] = pval[e] - omega * ap / dg[i];
             }
-            for (int e = sptr[j]; e < sptr[j + 1]; ++e) w[scells[e]] = 0.0;
+            for (int e = sptr[j]; e < sptr[j + 1]; ++e) wt[scells[e]] = 0.0;
         }
-        for (int i = 0; i < n; ++i) rs[i] = 0.0;
-        for (int e = 0; e < nnzp; ++e) rs[scells[e]] += pn[e];
+        OR_PAR_FOR
+        for (int i = 0; i < n; ++i) {
+            double acc = 0.0;
+            for (int k = cp[i]; k < cp[i + 1]; ++k) acc += pn[ce[k]];
+            rs[i] = acc;
+        }
         double inc = 0.0;
+        OR_PAR_MAX(inc)
         for (int e = 0; e < nnzp; ++e) {
             double v = pn[e] / rs[scells[e]];
             double d = fabs(v - pval[e]);
@@ -609,7 +654,7 @@ int or_msrsb_basis(int n, const int *rowptr, const int *col, const double *val,
         ++it;
         if (inc < tol) break;
     }
-    free(dg); free(w); free(pn); free(rs);
+    free(dg); free(w); free(pn); free(rs); free(cp); free(ce);
     *iters_out = it;
     return OR_OK;
 }
@@ -638,11 +683,16 @@ int or_galerkin(int n, const int *rowptr, const int *col, const double *val,
         for (int e = sptr[j]; e < sptr[j + 1]; ++e) { int i = scells[e]; cb[f[i]] = j; cv[f[i]++] = pval[e]; }
     free(f);
     memset(Ac, 0, (size_t)M * M * sizeof(double));
-    double *w = (double *)xcalloc((size_t)n, sizeof(double));
-    int *mark = (int *)xmalloc((size_t)n * sizeof(int));
-    for (int i = 0; i < n; ++i) mark[i] = -1;
-    int *lst = (int *)xmalloc((size_t)n * sizeof(int));
-    for (int l = 0; l < M; ++l) {
+    const int nt = OR_THREADS();                          /* work arrays per thread */
+    double *w0 = (double *)xcalloc((size_t)n * nt, sizeof(double));
+    int *mark0 = (int *)xmalloc((size_t)n * nt * sizeof(int));
+    for (size_t i = 0; i < (size_t)n * nt; ++i) mark0[i] = -1;
+    int *lst0 = (int *)xmalloc((size_t)n * nt * sizeof(int));
+    OR_PAR_FOR_DYN
+    for (int l = 0; l < M; ++l) {                         /* column l of A_c */
+        double *w = w0 + (size_t)n * OR_TID();
+        int *mark = mark0 + (size_t)n * OR_TID();
+        int *lst = lst0 + (size_t)n * OR_TID();
         int nl = 0;
         for (int e = sptr[l]; e < sptr[l + 1]; ++e) w[scells[e]] = pval[e];
         /* cells where (A P_l) may be nonzero: the support and its neighbours */
@@ -661,7 +711,7 @@ int or_galerkin(int n, const int *rowptr, const int *col, const double *val,
         }
         for (int e = sptr[l]; e < sptr[l + 1]; ++e) w[scells[e]] = 0.0;
     }
-    free(cp); free(cb); free(cv); free(w); free(mark); free(lst);
+    free(cp); free(cb); free(cv); free(w0); free(mark0); free(lst0);
     return OR_OK;
 }
 
@@ -673,6 +723,7 @@ int or_cholesky(int M, double *L) {
         if (!(d > 0.0)) return OR_ESINGULAR;
         d = sqrt(d);
         L[(size_t)k * M + k] = d;
+        OR_PAR_FOR
         for (int i = k + 1; i < M; ++i) {
             double s = L[(size_t)i * M + k];
             for (int p = 0; p < k; ++p) s -= L[(size_t)i * M + p] * L[(size_t)k * M + p];
@@ -929,12 +980,14 @@ static int dyn_build(int n, const int *rp, const int *ci, const double *val, con
 
 static double nrm2(int n, const double *v) {
     double s = 0.0;
+    OR_PAR_SUM(s)
     for (int i = 0; i < n; ++i) s += v[i] * v[i];
     return sqrt(s);
 }
 
 static void residual(int n, const int *rp, const int *ci, const double *v, const double *q, const double *x, double *r) {
     csr_mv(n, rp, ci, v, x, r);
+    OR_PAR_FOR
     for (int i = 0; i < n; ++i) r[i] = q[i] - r[i];
 }
 
@@ -947,6 +1000,7 @@ static void coarse_correction(int n, const int *rp, const int *ci, const double 
         for (int i = 0; i < n; ++i) d[part[i]] += r[i];
         or_lu_solve(M, L, piv, d, xc);
     } else {
+        OR_PAR_FOR
         for (int j = 0; j < M; ++j) {                   /* d = P^T r */
             double s = 0.0;
             for (int e = sptr[j]; e < sptr[j + 1]; ++e) s += pval[e] * r[scells[e]];
@@ -992,6 +1046,7 @@ int or_ms_solve(int n, const int *rowptr, const int *col, const double *val,
             residual(n, rowptr, col, val, q, x, r);
             if (smoother == 0) or_ilu0_apply(n, rowptr, col, lu, r, z);
             else for (int i = 0; i < n; ++i) z[i] = jac_omega * r[i] / dg[i];
+            OR_PAR_FOR
             for (int i = 0; i < n; ++i) x[i] += z[i];
             if (s < n_stages)
                 coarse_correction(n, rowptr, col, val, q, stages[s].M, stages[s].sptr, stages[s].scells,
@@ -1030,6 +1085,7 @@ static void ms_cycle_from_zero(int n, const int *rp, const int *ci, const double
         residual(n, rp, ci, val, v, z, r);
         if (smoother == 0) or_ilu0_apply(n, rp, ci, lu, r, t);
         else for (int i = 0; i < n; ++i) t[i] = jac_omega * r[i] / dg[i];
+        OR_PAR_FOR
         for (int i = 0; i < n; ++i) z[i] += t[i];
         coarse_correction(n, rp, ci, val, v, stages[s].M, stages[s].sptr, stages[s].scells, stages[s].pval,
                           stages[s].L, stages[s].part, stages[s].piv, z, r, d, xc);
@@ -1076,6 +1132,7 @@ int or_ms_gmres(int n, const int *rowptr, const int *col, const double *val,
     int it = 0;
     while (res > tol && it < max_iter) {
         const double beta = nrm2(n, r);
+        OR_PAR_FOR
         for (int i = 0; i < n; ++i) V[i] = r[i] / beta;
         for (int i = 0; i <= m; ++i) g[i] = 0.0;
         g[0] = beta;
@@ -1090,11 +1147,13 @@ int or_ms_gmres(int n, const int *rowptr, const int *col, const double *val,
                 for (int i = 0; i <= k; ++i) {
                     const double *vi = V + (size_t)i * n;
                     double sdot = 0.0;
+                    OR_PAR_SUM(sdot)
                     for (int l = 0; l < n; ++l) sdot += vi[l] * w[l];
                     h2[i] = sdot;
                 }
                 for (int i = 0; i <= k; ++i) {
                     const double *vi = V + (size_t)i * n;
+                    OR_PAR_FOR
                     for (int l = 0; l < n; ++l) w[l] -= h2[i] * vi[l];
                     H[i * m + k] += h2[i];
                 }
@@ -1103,6 +1162,7 @@ int or_ms_gmres(int n, const int *rowptr, const int *col, const double *val,
             H[(k + 1) * m + k] = hn;
             if (hn > 0.0) {
                 double *vn = V + (size_t)(k + 1) * n;
+                OR_PAR_FOR
                 for (int l = 0; l < n; ++l) vn[l] = w[l] / hn;
             }
             for (int i = 0; i < k; ++i) {                 /* previous rotations on column k */
@@ -1131,6 +1191,7 @@ int or_ms_gmres(int n, const int *rowptr, const int *col, const double *val,
         }
         for (int i = 0; i < k; ++i) {
             const double *zi = Z + (size_t)i * n;
+            OR_PAR_FOR
             for (int l = 0; l < n; ++l) x[l] += y[i] * zi[l];
         }
         residual(n, rowptr, col, val, q, x, r);

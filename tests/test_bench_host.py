@@ -46,13 +46,13 @@ def test_peak_fallback_without_measured_file(tmp_path, monkeypatch):
     assert bench.measured_peak() == (6700.5, "measured")
 
 
-def test_reference_counts_from_the_stored_oracle_run():
-    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_c2_seed0_gmres.json")))
-    assert bench.full_counts() == (int(gold["basis_iters"]), int(gold["steps"]))
-    rich = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_c2_seed0.json")))
-    assert rich["basis_iters"] == gold["basis_iters"] == 338        # one basis, two outer iterations
-
-
-def test_reference_counts_absent(tmp_path, monkeypatch):
-    monkeypatch.setattr(bench, "ORACLE_GOLD_GMRES", str(tmp_path / "missing.json"))
-    assert bench.full_counts() is None
+def test_cpu_baseline_line_states_cores_and_host():
+    nproc, model = bench.host_cpu()
+    assert nproc >= 1 and model
+    res = {"seconds": 4.0, "phases": {"solve": 1.0}, "basis_iters": 338, "steps": 101, "threads": 16}
+    cb = bench.cpu_baseline_line(1_000_000, res)
+    assert cb["value"] == 250_000.0 and cb["cores"] == 16 and cb["kind"] == "oracle"
+    assert cb["nproc"] == nproc and cb["cpu_model"] == model
+    assert "nothing extrapolated" in cb["sample"] and "16 threads" in cb["sample"]
+    one = bench.cpu_baseline_line(1_000_000, dict(res, threads=1))
+    assert one["cores"] == 1 and "single-threaded" in one["sample"]
