@@ -320,8 +320,9 @@ def timed_steps(torch, plan, stream, K, dist, world, outer="gmres", coarse=None)
 
 
 ENSEMBLE = ("batched ensemble of {m} independent 3D TPFA systems of uneven size (nx, ny ~ U{{24..96}}, "
-            "nz ~ U{{8..48}}, 20k <= N <= 400k; lognormal K, correlation U[2,16] cells, sigma U[1,3], Kz = 0.1 Kx; "
-            "seed 1000+m); 8x8x4 coarse blocks; per step every member's MsRSB basis re-smoothed, Galerkin "
+            "nz ~ U{{8..48}}, 20k <= N <= 400k; lognormal K, correlation U[2,16] cells, sigma U[1,3], standard "
+            "field clipped to +-3, Kz = 0.1 Kx; seed 1000+m); 8x8x4 coarse blocks; per step every member's MsRSB "
+            "basis re-smoothed (all members in one persistent launch), Galerkin "
             "operator re-formed and GMRES(30) with the MS+ILU(0) cycle as preconditioner to 1e-6, FP32 bulk / FP64 "
             "residual")
 
@@ -380,6 +381,9 @@ def run_ensemble(args):
             t = R.max_over_ranks(dist, [t], dev)[0]
         return t, outs[-1]
 
+    # work-item shape of the batched basis smoothing: cached per device, tuned once
+    from paper_2001_01624_gb300 import autotune
+    tuning = autotune.tuned(ctx, [m["sys"] for m in mem], [m["rebuild"] for m in mem], local, workload="ensemble")
     for _ in range(args.warmup):
         step(args.workers)
     ms.ms_profile_reset()
@@ -414,6 +418,7 @@ def run_ensemble(args):
         "dtype": "f32 bulk + f64 residual/refinement", "data": "synthetic",
         "config": {"workload": ENSEMBLE.format(m=args.members), "members": args.members, "cells": cells,
                    "workers": args.workers, "parallelism": "replicas (one ensemble slice per GPU)",
+                   "batch_tuning": {"tile_cells": tuning["tile_cells"], "ctas_per_sm": tuning["ctas_per_sm"]},
                    "l2": "no flush: the step's working set (all members) exceeds the 129 MB L2"},
         "sequential": {"value": cells * world / (t_seq * 1e-3), "ms_per_step": t_seq, "workers": 1},
         "members": {"converged": sum(o["converged"] for o in out), "cycles_min": min(cyc), "cycles_max": max(cyc),
@@ -838,6 +843,12 @@ def main():
                          "kernels": {k: {"launches": v["timed_launches"], "ms": round(v["total_ms"], 3),
                                          "share": round(v["total_ms"] / tot, 4)}
                                      for k, v in sorted(pk.items(), key=lambda kv: -kv[1]["total_ms"])[:10]}}
+        cinv = ms.ms_coarse_get_inverse(ctx, plans[ms.MS_PREC_MIXED].coarse)
+        ck = rm["prof"].get("coarse_sweep_tc") or {}
+        line["mixed"]["coarse"] = {"inverse": "fp64" if cinv["fp64"] else "fp32 (tensor cores)",
+                                   "fp32_check": cinv["inv_error"], "refine_steps": cinv["refine_steps"],
+                                   "sweep_tc_ms": (ck["total_ms"] / ck["timed_launches"]) if ck.get("timed_launches")
+                                   else None}
         pm = plans[ms.MS_PREC_MIXED].p.cpu().numpy()
         p64 = plans[ms.MS_PREC_FP64].p.cpu().numpy()
         line["mixed"]["rel_err_vs_fp64"] = float(np.linalg.norm(pm - p64) / np.linalg.norm(p64))
@@ -866,7 +877,7 @@ def main():
                       "restriction": "finite volume (block sums)", "steps": fi["iters"],
                       "solve_ms": fi["seconds"] * 1e3, "rel_residual": fi["rel_residual"],
                       "gauss_jordan_ms": per_launch(pf, "coarse_gauss_jordan"),
-                      "cholesky_inverse_ms": per_launch(prof, "coarse_factor_inverse"),
+                      "cholesky_inverse_ms": per_launch(prof, "coarse_sweep64"),
                       "restrict_ms": per_launch(pf, "restrict"), "restrict_galerkin_ms": per_launch(prof, "restrict")}
         ms.ms_coarse_release(cfv)
 

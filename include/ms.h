@@ -50,7 +50,7 @@
 extern "C" {
 #endif
 
-#define MS_ABI_VERSION 7
+#define MS_ABI_VERSION 9
 
 typedef enum {
     MS_OK = 0,
@@ -378,6 +378,28 @@ ms_status ms_coarse_create(ms_ctx *ctx, ms_system *sys, const ms_basis *basis, i
  * column is zero.  For checking that kernel on arbitrary matrices; stages
  * reach it through ms_coarse_create. */
 ms_status ms_dense_inverse(ms_ctx *ctx, int32_t M, const double *A, double *X);
+/* Inverse of a symmetric positive definite matrix by the blocked symmetric
+ * sweep that inverts Galerkin coarse operators ((A_c)^{-1} of Eq. (11);
+ * Sec. 6.4 "solve for p_c"): each step sweeps a 32-wide pivot block (its
+ * Cholesky factor G, W = U G^{-T} for the column panel U) and applies the
+ * rank-32 update A <- mask(A) - W W^T to the whole matrix, all steps in one
+ * cooperative launch.  MS_PREC_FP64: FP64 on the CUDA cores.  MS_PREC_MIXED:
+ * the symmetrically equilibrated matrix in FP32 with the rank-32 updates on
+ * the tensor cores (tcgen05, TF32 operands split into high and low parts,
+ * FP32 accumulation), scaled back, returned widened to FP64.  A and X: host
+ * arrays of M*M row-major doubles; A must be symmetric (only the lower
+ * triangle is read).  A pivot block that is not positive definite is
+ * MS_ERR_COARSE_SINGULAR.  For checking the kernel on arbitrary matrices;
+ * stages reach it through ms_galerkin / ms_coarse_create. */
+ms_status ms_spd_inverse(ms_ctx *ctx, int32_t M, const double *A, double *X, int32_t precision);
+/* The coarse inverse a stage applies (host, M*M row-major doubles, may be
+ * NULL), whether it is FP64 (*fp64 = 1) or the FP32 inverse of a mixed
+ * stage, widened (*fp64 = 0); for a mixed stage *inv_error receives
+ * ||X A_c v - v|| / ||v|| on the stage's test vector and *refine_steps the
+ * FP64 refinement steps of each coarse solve (0 when the FP64 inverse is
+ * used).  Any output pointer may be NULL. */
+ms_status ms_coarse_get_inverse(ms_ctx *ctx, const ms_coarse *coarse, double *X, int32_t *M, int32_t *fp64,
+                                double *inv_error, int32_t *refine_steps);
 /* Recompute A_c and its factors in place from the basis and the current A. */
 ms_status ms_coarse_refresh(ms_ctx *ctx, ms_system *sys, ms_coarse *coarse);
 ms_status ms_coarse_release(ms_coarse *coarse);
@@ -461,7 +483,8 @@ typedef struct {
  * solves one system at a time): members run concurrently on `n_workers`
  * worker streams of this context's device (0: min(16, n_members)), each
  * worker taking the largest remaining member next, so the small kernels of
- * many members overlap on the GPU.  Each member computes exactly what
+ * many members overlap on the GPU; the bases of members with `rebuild` set
+ * are first re-smoothed together, as by ms_basis_rebuild_batch.  Each member computes exactly what
  * ms_solve (after ms_basis_rebuild / ms_coarse_refresh when `rebuild` is set)
  * computes for it alone.  The batch is ordered after earlier work on the
  * context's stream and later work on that stream is ordered after it; the
@@ -471,6 +494,25 @@ typedef struct {
  * distinct. */
 ms_status ms_solve_batch(ms_ctx *ctx, ms_batch_member *members, int32_t n_members, const ms_solve_opts *opts,
                          int32_t n_workers);
+
+/* Batched basis re-smoothing (no counterpart in the paper, which builds one
+ * basis at a time; Sec. 5.1 gives the smoothing): re-smooths every basis
+ * bases[m] of system sys[m] from its block indicator with the system's
+ * current A, in one persistent launch per precision that takes
+ * (member, tile) work items from a device queue, so many small systems fill
+ * the GPU together.  Results (values, iteration counts, stopping) are
+ * bitwise those of ms_basis_rebuild on each member.  Members the launch cannot
+ * take (constant bases, rows with more than 8 connections) are re-smoothed
+ * one by one.  iters (n entries, host, or NULL) receives the iteration
+ * counts.  Systems and bases must be distinct and assembled; ordered on the
+ * context's stream; returns after the smoothing. */
+ms_status ms_basis_rebuild_batch(ms_ctx *ctx, ms_system *const *sys, ms_basis *const *bases, int32_t n,
+                                 int32_t *iters);
+/* Work-item shape of the batched smoothing (used by ms_basis_rebuild_batch
+ * and ms_solve_batch): cells per item (a multiple of 256 in [256, 16384];
+ * default 1024) and resident blocks per SM of the persistent launch (1..8;
+ * default 4).  paper_2001_01624_gb300.autotune picks them per device. */
+ms_status ms_set_batch_tuning(ms_ctx *ctx, int32_t tile_cells, int32_t ctas_per_sm);
 
 /* ------------------------------------------------------------- two-phase */
 /* Water / oil fluid for sequential-implicit time steps (Sec. 2): Corey

@@ -142,6 +142,8 @@ def lib():
         "ms_coarse_create": ([_vp, _vp, _vp, _i32, _i32, P(_vp)], _i32),
         "ms_partition_wells": ([_vp, _vp, _i32, _vp, _vp, _vp, P(_i32)], _i32),
         "ms_dense_inverse": ([_vp, _i32, _vp, _vp], _i32),
+        "ms_spd_inverse": ([_vp, _i32, _vp, _vp, _i32], _i32),
+        "ms_coarse_get_inverse": ([_vp, _vp, _vp, P(_i32), P(_i32), P(_d), P(_i32)], _i32),
         "ms_cpr_pressure_system": ([_vp, _vp, _vp, P(ms_cpr_fluid), _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp],
                                    _i32),
         "ms_coarse_refresh": ([_vp, _vp, _vp], _i32),
@@ -149,6 +151,8 @@ def lib():
         "ms_coarse_get": ([_vp, _vp, _vp, P(_i32)], _i32),
         "ms_solve": ([_vp, _vp, P(_vp), _i32, _vp, _vp, P(ms_solve_opts), P(ms_solve_info)], _i32),
         "ms_solve_batch": ([_vp, P(ms_batch_member), _i32, P(ms_solve_opts), _i32], _i32),
+        "ms_basis_rebuild_batch": ([_vp, _vp, _vp, _i32, _vp], _i32),
+        "ms_set_batch_tuning": ([_vp, _i32, _i32], _i32),
         "ms_total_mobility": ([_vp, _vp, P(ms_fluid), _vp, _vp], _i32),
         "ms_transport_step": ([_vp, _vp, P(ms_fluid), _vp, _vp, _d, _vp, P(_i32)], _i32),
         "ms_profile_enable": ([_i32], _i32),
@@ -168,10 +172,12 @@ def exported_symbols() -> Sequence[str]:
             "ms_system_create", "ms_system_release", "ms_system_get_info", "ms_assemble_tpfa",
             "ms_system_get_matrix", "ms_spmv", "ms_ilu_apply", "ms_ilu_apply_noalloc", "ms_set_wait_limit",
             "ms_debug_withhold_segments", "ms_plan_segments", "ms_partition_cartesian", "ms_partition_components", "ms_partition_dynamic",
-            "ms_partition_wells", "ms_coarse_create", "ms_dense_inverse", "ms_cpr_pressure_system",
+            "ms_partition_wells", "ms_coarse_create", "ms_dense_inverse", "ms_spd_inverse",
+            "ms_coarse_get_inverse", "ms_cpr_pressure_system",
             "ms_build_basis", "ms_basis_rebuild", "ms_basis_update", "ms_basis_release", "ms_basis_get_info",
             "ms_basis_get", "ms_add_adaptive_basis", "ms_galerkin", "ms_coarse_refresh", "ms_coarse_release",
-            "ms_coarse_get", "ms_solve", "ms_solve_batch", "ms_total_mobility", "ms_transport_step", "ms_profile_enable", "ms_profile_reset", "ms_profile_read"]
+            "ms_coarse_get", "ms_solve", "ms_solve_batch", "ms_basis_rebuild_batch",
+            "ms_set_batch_tuning", "ms_total_mobility", "ms_transport_step", "ms_profile_enable", "ms_profile_reset", "ms_profile_read"]
 
 
 def _ptr(a):
@@ -430,6 +436,15 @@ def ms_dense_inverse(ctx, A):
     return X
 
 
+def ms_spd_inverse(ctx, A, precision=MS_PREC_FP64):
+    """A^{-1} of a symmetric positive definite matrix by the coarse stages'
+    blocked sweep (FP64, or FP32 on the tensor cores for MS_PREC_MIXED)."""
+    A = np.ascontiguousarray(A, np.float64)
+    X = np.empty_like(A)
+    _check(lib().ms_spd_inverse(ctx, A.shape[0], _ptr(A), _ptr(X), precision), ctx)
+    return X
+
+
 def ms_cpr_pressure_system(ctx, sys, perm, fluid, p, s, p0, s0, q_w, q_o, dt, rhs=None, weights=None):
     """Replace the system's matrix by the CPR pressure matrix J* (quasi-IMPES)
     of the compressible two-phase step; returns rhs = -(W_w R_w + W_o R_o)
@@ -457,6 +472,16 @@ def ms_coarse_get(ctx, coarse):
     Ac = np.empty((m.value, m.value))
     _check(lib().ms_coarse_get(ctx, coarse, _ptr(Ac), C.byref(m)), ctx)
     return Ac
+
+
+def ms_coarse_get_inverse(ctx, coarse):
+    """dict(X, fp64, inv_error, refine_steps): the coarse inverse the stage applies."""
+    m, f, k = _i32(), _i32(), _i32()
+    e = _d()
+    _check(lib().ms_coarse_get_inverse(ctx, coarse, None, C.byref(m), None, None, None), ctx)
+    X = np.empty((m.value, m.value))
+    _check(lib().ms_coarse_get_inverse(ctx, coarse, _ptr(X), C.byref(m), C.byref(f), C.byref(e), C.byref(k)), ctx)
+    return dict(X=X, fp64=bool(f.value), inv_error=e.value, refine_steps=k.value)
 
 
 # -------------------------------------------------------------------- solve
@@ -515,6 +540,25 @@ def ms_solve_batch(ctx, members: Sequence[dict], tol=1e-6, max_iter=500, smoothe
         out.append(dict(status=arr[k].status, iters=i.iters, converged=bool(i.converged), rel_residual=i.rel_residual,
                         history=hists[k][: i.iters + 1].copy(), basis_iters=arr[k].basis_iters, seconds=i.seconds))
     return out
+
+
+def _h(x):
+    return x.value if isinstance(x, _vp) else x
+
+
+def ms_basis_rebuild_batch(ctx, systems: Sequence, bases: Sequence) -> np.ndarray:
+    """Re-smooth bases[m] of systems[m] from the block indicator, all in one
+    persistent launch per precision; returns the iteration counts."""
+    n = len(systems)
+    sa = (_vp * max(n, 1))(*[_h(x) for x in systems])
+    ba = (_vp * max(n, 1))(*[_h(x) for x in bases])
+    it = np.zeros(max(n, 1), np.int32)
+    _check(lib().ms_basis_rebuild_batch(ctx, C.cast(sa, _vp), C.cast(ba, _vp), n, _ptr(it)), ctx)
+    return it[:n]
+
+
+def ms_set_batch_tuning(ctx, tile_cells: int, ctas_per_sm: int):
+    _check(lib().ms_set_batch_tuning(ctx, int(tile_cells), int(ctas_per_sm)), ctx)
 
 
 # ---------------------------------------------------------------- two-phase

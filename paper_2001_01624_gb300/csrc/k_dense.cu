@@ -15,6 +15,8 @@
 // symmetric) are inverted by Gauss-Jordan elimination with partial pivoting
 // in one cooperative launch (k_gauss_jordan).
 #include <cmath>
+#include <cstdint>
+#include <type_traits>
 
 #include "grid_sync.cuh"
 #include "ms_internal.h"
@@ -221,18 +223,53 @@ __global__ void k_check_diag(const double *A, int M, int *err) {
 }
 
 // y = A x, one warp per row.
-template <typename T>
-__global__ void k_gemv(const T *__restrict__ A, int M, const T *__restrict__ x, T *__restrict__ y) {
+// y = A x, one warp per row: 16-byte loads of the row (after the one to three
+// elements that bring it to a 16-byte boundary) with four loads in flight per
+// lane, so the row streams instead of waiting on one load at a time.
+// MODE 0: y = A x; 1: acc = (double)(A x); 2: acc += (double)(A x).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(128) k_gemv(const T *__restrict__ A, int M, const T *__restrict__ x,
+                                              T *__restrict__ y, double *__restrict__ acc) {
+    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    constexpr int VW = 16 / sizeof(T);
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= M) return;
-    T s = 0;
     const T *a = A + (int64_t)row * M;
-    for (int c = lane; c < M; c += 32) s += a[c] * x[c];
+    int pre = (int)(((16 - ((uintptr_t)a & 15)) & 15) / sizeof(T));
+    if (pre > M) pre = M;
+    T s[4] = {T(0), T(0), T(0), T(0)};
+    if (lane < pre) s[0] = a[lane] * x[lane];
+    const int nv = (M - pre) / VW;
+    const V *av = (const V *)(a + pre);
+    const T *xp = x + pre;
+    for (int v0 = lane; v0 < nv; v0 += 128) {
+        V q[4];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) y[row] = s;
+        for (int u = 0; u < 4; ++u)
+            if (v0 + 32 * u < nv) q[u] = __ldg(av + v0 + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int v = v0 + 32 * u;
+            if (v < nv) {
+                const T *xv = xp + (int64_t)v * VW;
+                if constexpr (VW == 4) s[u] += q[u].x * xv[0] + q[u].y * xv[1] + q[u].z * xv[2] + q[u].w * xv[3];
+                else s[u] += q[u].x * xv[0] + q[u].y * xv[1];
+            }
+        }
+    }
+    for (int c = pre + nv * VW + lane; c < M; c += 32) s[0] += a[c] * x[c];
+    T t = (s[0] + s[1]) + (s[2] + s[3]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) {
+        if constexpr (MODE == 0) y[row] = t;
+        else if constexpr (MODE == 1) acc[row] = (double)t;
+        else acc[row] += (double)t;
+    }
 }
+
+inline int gemv_blocks(int M) { return (M + 3) / 4; }
 
 // rc = d - A x (FP64), and its FP32 copy.
 __global__ void k_dense_residual(const double *__restrict__ A, int M, const double *__restrict__ d,
@@ -250,6 +287,58 @@ __global__ void k_dense_residual(const double *__restrict__ A, int M, const doub
         rc[row] = r;
         rc32[row] = (float)r;
     }
+}
+
+// Nonzeros of each row of A_c (one warp per row): the largest count goes to *wmax.
+__global__ void k_row_nnz(const double *__restrict__ A, int M, int *__restrict__ wmax) {
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= M) return;
+    int cnt = 0;
+    const double *a = A + (int64_t)row * M;
+    for (int c = lane; c < M; c += 32) cnt += a[c] != 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if (lane == 0) atomicMax(wmax, cnt);
+}
+
+// ELL copy of A_c: slot w of row r at [w M + r], columns ascending, padding
+// column r with value 0 (one warp per row, compaction by ballot).
+__global__ void k_ell_fill(const double *__restrict__ A, int M, int Wc, int *__restrict__ col,
+                           double *__restrict__ val) {
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= M) return;
+    const double *a = A + (int64_t)row * M;
+    int base = 0;
+    for (int c0 = 0; c0 < M; c0 += 32) {
+        const int c = c0 + lane;
+        const double v = c < M ? a[c] : 0.0;
+        const unsigned b = __ballot_sync(0xffffffffu, v != 0.0);
+        const int pos = base + __popc(b & ((1u << lane) - 1u));
+        if (v != 0.0 && pos < Wc) {
+            col[(int64_t)pos * M + row] = c;
+            val[(int64_t)pos * M + row] = v;
+        }
+        base += __popc(b);
+    }
+    for (int w = base + lane; w < Wc; w += 32) {
+        col[(int64_t)w * M + row] = row;
+        val[(int64_t)w * M + row] = 0.0;
+    }
+}
+
+// rc = d - A x with the ELL copy (FP64), and its FP32 copy.
+__global__ void k_ell_residual(const int *__restrict__ col, const double *__restrict__ val, int M, int Wc,
+                               const double *__restrict__ d, const double *__restrict__ x, double *__restrict__ rc,
+                               float *__restrict__ rc32) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= M) return;
+    double s = 0.0;
+    for (int w = 0; w < Wc; ++w) s += val[(int64_t)w * M + row] * x[col[(int64_t)w * M + row]];
+    const double r = d[row] - s;
+    rc[row] = r;
+    rc32[row] = (float)r;
 }
 
 __global__ void k_axpy_f32(int M, const float *t, double *x, int assign) {
@@ -602,9 +691,9 @@ double coarse_inverse_check32(const ms_coarse &c, double *host2, cudaStream_t st
     DBuf<float> d32, x32;
     v.alloc(M); d.alloc(M); out.alloc(2); d32.alloc(M); x32.alloc(M);
     k_test_vector<<<(M + 255) / 256, 256, 0, st>>>(M, v.p);
-    k_gemv<double><<<(M + 7) / 8, 256, 0, st>>>(c.Ac.p, M, v.p, d.p);
+    k_gemv<double, 0><<<gemv_blocks(M), 128, 0, st>>>(c.Ac.p, M, v.p, d.p, nullptr);
     k_d2f<<<(M + 255) / 256, 256, 0, st>>>(M, d.p, d32.p);
-    k_gemv<float><<<(M + 7) / 8, 256, 0, st>>>(c.inv32.p, M, d32.p, x32.p);
+    k_gemv<float, 0><<<gemv_blocks(M), 128, 0, st>>>(c.inv32.p, M, d32.p, x32.p, nullptr);
     k_err_norms<<<1, 256, 0, st>>>(M, x32.p, v.p, out.p);
     MS_CHECK_LAUNCH();
     MS_CUDA(cudaMemcpyAsync(host2, out.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -612,14 +701,35 @@ double coarse_inverse_check32(const ms_coarse &c, double *host2, cudaStream_t st
     return host2[1] > 0 ? std::sqrt(host2[0] / host2[1]) : 0.0;
 }
 
+// ELL copy of A_c for the refinement residuals (kept only when A_c is sparse:
+// at most M / 4 nonzeros per row).
+void coarse_sparse_copy(ms_coarse &c, int *scratch, int *host, cudaStream_t st) {
+    const int M = c.M;
+    MS_CUDA(cudaMemsetAsync(scratch, 0, sizeof(int), st));
+    k_row_nnz<<<(M + 7) / 8, 256, 0, st>>>(c.Ac.p, M, scratch);
+    MS_CHECK_LAUNCH();
+    MS_CUDA(cudaMemcpyAsync(host, scratch, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MS_CUDA(cudaStreamSynchronize(st));
+    const int Wc = *host;
+    if (Wc <= 0 || Wc > M / 4) {
+        c.sp_w = 0;
+        return;
+    }
+    c.sp_col.alloc((size_t)Wc * M);
+    c.sp_val.alloc((size_t)Wc * M);
+    k_ell_fill<<<(M + 7) / 8, 256, 0, st>>>(c.Ac.p, M, Wc, c.sp_col.p, c.sp_val.p);
+    MS_CHECK_LAUNCH();
+    c.sp_w = Wc;
+}
+
 void launch_gemv64(const double *A, int M, const double *x, double *y, cudaStream_t st) {
     KernelScope ks_(st, "coarse_gemv", (double)M * M * 8 + (double)M * 16);
-    k_gemv<double><<<(M + 7) / 8, 256, 0, st>>>(A, M, x, y);
+    k_gemv<double, 0><<<gemv_blocks(M), 128, 0, st>>>(A, M, x, y, nullptr);
     MS_CHECK_LAUNCH();
 }
 
 void launch_gemv32(const float *A, int M, const float *x, float *y, cudaStream_t st) {
-    k_gemv<float><<<(M + 7) / 8, 256, 0, st>>>(A, M, x, y);
+    k_gemv<float, 0><<<gemv_blocks(M), 128, 0, st>>>(A, M, x, y, nullptr);
     MS_CHECK_LAUNCH();
 }
 
@@ -628,14 +738,14 @@ void launch_gemv32(const float *A, int M, const float *x, float *y, cudaStream_t
 void launch_coarse_refine(const ms_coarse &c, const double *d, double *xc, double *rc, float *t32a, float *t32b,
                           int steps, cudaStream_t st) {
     const int M = c.M;
-    KernelScope ks_(st, "coarse_refine", (double)M * M * (4 + steps * 12));
+    const double resid = c.sp_w > 0 ? (double)c.sp_w * M * 12 + (double)M * 24 : (double)M * M * 8;
+    KernelScope ks_(st, "coarse_refine", (double)M * M * 4 * (1 + steps) + steps * resid);
     k_d2f<<<(M + 255) / 256, 256, 0, st>>>(M, d, t32a);
-    k_gemv<float><<<(M + 7) / 8, 256, 0, st>>>(c.inv32.p, M, t32a, t32b);
-    k_axpy_f32<<<(M + 255) / 256, 256, 0, st>>>(M, t32b, xc, 1);
+    k_gemv<float, 1><<<gemv_blocks(M), 128, 0, st>>>(c.inv32.p, M, t32a, t32b, xc);
     for (int s = 0; s < steps; ++s) {
-        k_dense_residual<<<(M + 7) / 8, 256, 0, st>>>(c.Ac.p, M, d, xc, rc, t32a);
-        k_gemv<float><<<(M + 7) / 8, 256, 0, st>>>(c.inv32.p, M, t32a, t32b);
-        k_axpy_f32<<<(M + 255) / 256, 256, 0, st>>>(M, t32b, xc, 0);
+        if (c.sp_w > 0) k_ell_residual<<<(M + 127) / 128, 128, 0, st>>>(c.sp_col.p, c.sp_val.p, M, c.sp_w, d, xc, rc, t32a);
+        else k_dense_residual<<<(M + 7) / 8, 256, 0, st>>>(c.Ac.p, M, d, xc, rc, t32a);
+        k_gemv<float, 2><<<gemv_blocks(M), 128, 0, st>>>(c.inv32.p, M, t32a, t32b, xc);
     }
     MS_CHECK_LAUNCH();
 }

@@ -251,6 +251,13 @@ ms_basis *create_basis(ms_ctx *ctx, ms_system &s, const std::vector<int> &part, 
     return b.release();
 }
 
+// Symmetric coarse inverses: the blocked sweep in one launch (default), or
+// MSGB_COARSE_INVERSE=chain for the Cholesky factor-and-invert kernel chain.
+bool coarse_chain() {
+    const char *e = std::getenv("MSGB_COARSE_INVERSE");
+    return e && std::string(e) == "chain";
+}
+
 // Error word of a coarse factorisation: a timeout of the Gauss-Jordan grid
 // barrier resets its counter before the error is raised.
 void coarse_error(ms_ctx *ctx, ms_coarse &c, int err) {
@@ -283,7 +290,12 @@ void galerkin_values(ms_ctx *ctx, ms_system &s, const ms_basis &b, ms_coarse &c)
     c.use64 = false;
     c.inv32_error = 0.0;
     const bool gj = c.nonsym;
-    auto inverse64 = [&]() { gj ? dense_gj_inverse64(c, s.w_i0.p, st) : dense_factor_inverse64(c, s.w_i0.p, st); };
+    const bool chain = coarse_chain();
+    auto inverse64 = [&]() {
+        if (gj) dense_gj_inverse64(c, s.w_i0.p, st);
+        else if (chain) dense_factor_inverse64(c, s.w_i0.p, st);
+        else dense_sweep_inverse64(c, s.w_i0.p, st);
+    };
     if (c.precision == MS_PREC_MIXED) {
         bool try32 = true;
         if (gj) {   // the FP32 path equilibrates with 1/sqrt(a_jj)
@@ -293,7 +305,8 @@ void galerkin_values(ms_ctx *ctx, ms_system &s, const ms_basis &b, ms_coarse &c)
         }
         if (try32) {
             if (gj) dense_gj_inverse32(c, s.w_i0.p, st);
-            else dense_factor_inverse32(c, s.w_i0.p, st);
+            else if (chain) dense_factor_inverse32(c, s.w_i0.p, st);
+            else dense_sweep_inverse32(c, s.w_i0.p, st);
             const int err32 = read_error_word(ctx, s.w_i0.p);
             if (err32 & kErrTimeout) coarse_error(ctx, c, err32);
             c.inv32_error = err32 ? INFINITY : coarse_inverse_check32(c, (double *)ctx->pinned.get(64), st);
@@ -301,13 +314,20 @@ void galerkin_values(ms_ctx *ctx, ms_system &s, const ms_basis &b, ms_coarse &c)
             c.inv32_error = INFINITY;
         }
         // each FP64 refinement step contracts the coarse error by about this
-        // factor (two steps: its square); fall back to an FP64 inverse when
-        // FP32 cannot resolve this coarse system to about 1e-3
-        if (!(c.inv32_error <= 0.03)) {
+        // factor e: take the steps that bring e^(steps+1) to 0.03^3 (2 steps up
+        // to e = 0.03, at most 5, up to e = 0.15); fall back to an FP64 inverse
+        // beyond that
+        const double e = c.inv32_error;
+        if (e <= 0.03) {
+            c.refine_steps = 2;
+        } else if (e <= 0.15) {
+            c.refine_steps = std::min(5, (int)std::ceil(std::log(2.7e-5) / std::log(e)) - 1);
+        } else {
             c.use64 = true;
             MS_CUDA(cudaMemsetAsync(s.w_i0.p, 0, sizeof(int), st));
             inverse64();
         }
+        if (!c.use64) coarse_sparse_copy(c, s.w_i0.p + 1, (int *)ctx->pinned.get(64), st);
     } else {
         inverse64();
     }
@@ -895,6 +915,64 @@ ms_status ms_dense_inverse(ms_ctx *ctx, int32_t M, const double *A, double *X) {
     API_CATCH(ctx)
 }
 
+ms_status ms_spd_inverse(ms_ctx *ctx, int32_t M, const double *A, double *X, int32_t precision) {
+    if (!ctx || !A || !X || M <= 0) return fail(ctx, MS_ERR_INVALID_ARG, "null argument or M <= 0");
+    if (precision != MS_PREC_FP64 && precision != MS_PREC_MIXED) return fail(ctx, MS_ERR_INVALID_ARG, "bad precision");
+    API_TRY
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const size_t MM = (size_t)M * M;
+    ms_coarse c;
+    c.M = M;
+    c.Ac.alloc(MM);
+    MS_CUDA(cudaMemcpyAsync(c.Ac.p, A, MM * sizeof(double), cudaMemcpyHostToDevice, st));
+    DBuf<int> err;
+    err.alloc(1);
+    err.zero(st);
+    if (precision == MS_PREC_FP64) {
+        dense_sweep_inverse64(c, err.p, st);
+        coarse_error(ctx, c, read_error_word(ctx, err.p));
+        MS_CUDA(cudaMemcpyAsync(X, c.inv64.p, MM * sizeof(double), cudaMemcpyDeviceToHost, st));
+    } else {
+        dense_sweep_inverse32(c, err.p, st);
+        coarse_error(ctx, c, read_error_word(ctx, err.p));
+        c.inv64.alloc(MM);
+        launch_widen(c.inv32.p, c.inv64.p, (int64_t)MM, st);
+        MS_CUDA(cudaMemcpyAsync(X, c.inv64.p, MM * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    sync(st);
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_coarse_get_inverse(ms_ctx *ctx, const ms_coarse *c, double *X, int32_t *M, int32_t *fp64,
+                                double *inv_error, int32_t *refine_steps) {
+    if (!ctx || !c) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    API_TRY
+    DeviceGuard g(ctx->device);
+    const bool d64 = c->precision != MS_PREC_MIXED || c->use64;
+    if (M) *M = c->M;
+    if (fp64) *fp64 = d64 ? 1 : 0;
+    if (inv_error) *inv_error = c->precision == MS_PREC_MIXED ? c->inv32_error : 0.0;
+    if (refine_steps) *refine_steps = d64 ? 0 : c->refine_steps;
+    if (X) {
+        const size_t MM = (size_t)c->M * c->M;
+        cudaStream_t st = ctx->stream;
+        if (d64) {
+            MS_CUDA(cudaMemcpyAsync(X, c->inv64.p, MM * sizeof(double), cudaMemcpyDeviceToHost, st));
+        } else {
+            DBuf<double> w;
+            w.alloc(MM);
+            launch_widen(c->inv32.p, w.p, (int64_t)MM, st);
+            MS_CUDA(cudaMemcpyAsync(X, w.p, MM * sizeof(double), cudaMemcpyDeviceToHost, st));
+            sync(st);
+        }
+        sync(st);
+    }
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
 ms_status ms_coarse_refresh(ms_ctx *ctx, ms_system *s, ms_coarse *c) {
     if (!ctx || !s || !c) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
     API_TRY
@@ -1032,7 +1110,7 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
                 // (or the FP64 inverse when FP32 cannot resolve this coarse system)
                 launch_widen(s->w_d32.p, s->w_d.p, M, st);
                 if (c.use64) launch_gemv64(c.inv64.p, M, s->w_d.p, s->w_xc.p, st);
-                else launch_coarse_refine(c, s->w_d.p, s->w_xc.p, s->w_rc.p, s->w_d32.p, s->w_xc32.p, 2, st);
+                else launch_coarse_refine(c, s->w_d.p, s->w_xc.p, s->w_rc.p, s->w_d32.p, s->w_xc32.p, c.refine_steps, st);
                 launch_narrow(s->w_xc.p, s->w_xc32.p, M, st);
                 launch_prolong32(b, n, s->w_xc32.p, s->w_x.p, st);
             } else {
@@ -1254,6 +1332,47 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
     API_CATCH(ctx)
 }
 
+// MSGB_BATCH_SMOOTH=0 re-smooths each member's basis on its own worker
+// instead of the batched launch (for comparison).
+bool batch_smoothing_enabled() {
+    const char *e = std::getenv("MSGB_BATCH_SMOOTH");
+    return !(e && std::string(e) == "0");
+}
+
+ms_status ms_set_batch_tuning(ms_ctx *ctx, int32_t tile_cells, int32_t ctas_per_sm) {
+    if (!ctx) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    if (tile_cells < 256 || tile_cells > 16384 || tile_cells % 256 != 0 || ctas_per_sm < 1 || ctas_per_sm > 8)
+        return fail(ctx, MS_ERR_INVALID_ARG, "tile_cells must be a multiple of 256 in [256, 16384], ctas_per_sm in [1, 8]");
+    ctx->batch_tile = tile_cells;
+    ctx->batch_ctas_per_sm = ctas_per_sm;
+    return MS_OK;
+}
+
+ms_status ms_basis_rebuild_batch(ms_ctx *ctx, ms_system *const *sys, ms_basis *const *bases, int32_t n,
+                                 int32_t *iters) {
+    if (!ctx || n < 0 || (n > 0 && (!sys || !bases))) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    if (n == 0) return MS_OK;
+    API_TRY
+    DeviceGuard g(ctx->device);
+    std::vector<ms_system *> vs(sys, sys + n);
+    std::vector<ms_basis *> vb(bases, bases + n);
+    for (int m = 0; m < n; ++m) {
+        MS_REQUIRE(vs[m] && vb[m], MS_ERR_INVALID_ARG, "null member");
+        MS_REQUIRE(vs[m]->assembled, MS_ERR_STATE, "system not assembled");
+        for (int k = 0; k < m; ++k)
+            MS_REQUIRE(vs[k] != vs[m] && vb[k] != vb[m], MS_ERR_INVALID_ARG, "members must be distinct");
+    }
+    std::vector<char> tk;
+    smooth_batch(ctx, vs, vb, tk);
+    for (int m = 0; m < n; ++m) {
+        if (!tk[m]) smooth_basis(ctx, *vs[m], *vb[m], true, vb[m]->tol, vb[m]->max_iter);
+        if (iters) iters[m] = vb[m]->iters;
+    }
+    sync(ctx->stream);
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
 ms_status ms_solve_batch(ms_ctx *ctx, ms_batch_member *members, int32_t n_members, const ms_solve_opts *opts,
                          int32_t n_workers) {
     if (!ctx || !opts || n_members < 0 || (n_members > 0 && !members))
@@ -1275,6 +1394,30 @@ ms_status ms_solve_batch(ms_ctx *ctx, ms_batch_member *members, int32_t n_member
         w->owns_stream = true;
         ctx->workers.push_back(std::move(w));
     }
+    // every member's basis re-smoothing in one persistent launch on the
+    // caller's stream (members it cannot take re-smooth on their worker)
+    std::vector<char> taken(n_members, 0);
+    {
+        std::vector<ms_system *> bs;
+        std::vector<ms_basis *> bb;
+        std::vector<int> at;
+        for (int m = 0; m < n_members; ++m)
+            if (members[m].rebuild) {
+                MS_REQUIRE(members[m].sys->assembled, MS_ERR_STATE, "member system not assembled");
+                bs.push_back(members[m].sys);
+                bb.push_back(members[m].rebuild);
+                at.push_back(m);
+            }
+        if (!bs.empty() && batch_smoothing_enabled()) {
+            std::vector<char> tk;
+            smooth_batch(ctx, bs, bb, tk);
+            for (size_t k = 0; k < at.size(); ++k)
+                if (tk[k]) {
+                    taken[at[k]] = 1;
+                    members[at[k]].basis_iters = bb[k]->iters;
+                }
+        }
+    }
     // order: earlier work on the caller's stream -> all workers -> later work on it
     cudaEvent_t ev;
     MS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -1292,7 +1435,7 @@ ms_status ms_solve_batch(ms_ctx *ctx, ms_batch_member *members, int32_t n_member
             ms_batch_member &mb = members[order[k]];
             ms_status st = MS_OK;
             if (mb.rebuild) {
-                st = ms_basis_rebuild(wc, mb.sys, mb.rebuild, &mb.basis_iters);
+                if (!taken[order[k]]) st = ms_basis_rebuild(wc, mb.sys, mb.rebuild, &mb.basis_iters);
                 for (int l = 0; st == MS_OK && l < mb.n_stages; ++l)
                     if (mb.stages[l] && mb.stages[l]->basis == mb.rebuild) st = ms_coarse_refresh(wc, mb.sys, mb.stages[l]);
             }

@@ -146,6 +146,15 @@ void profile_add_launches(const std::vector<std::string> &names, int64_t times);
 void profile_reset();
 int profile_read(ms_kernel_stat *out, int cap, int64_t *total);
 
+// Device scratch of the batched basis smoothing (k_msrsb_batch): member
+// descriptors, the work queue and its ring of slots, per-member tile counters
+// and iteration-control blocks.
+struct BatchScratch {
+    DBuf<unsigned char> jobs;
+    DBuf<unsigned long long> queue, slots, ctl;
+    DBuf<int> done;
+};
+
 }  // namespace msgb
 
 // ------------------------------------------------------------------ handles
@@ -163,6 +172,10 @@ struct ms_ctx {
     int sm_count = 0;
     std::string err;
     msgb::HostScratch pinned;
+    // batched smoothing: cells per work item and resident blocks per SM
+    // (ms_set_batch_tuning), and its device scratch
+    int batch_tile = 1024, batch_ctas_per_sm = 4;
+    std::unique_ptr<msgb::BatchScratch> batch;
 };
 
 // Host-side analysis products of a grid (built once per grid).
@@ -329,6 +342,10 @@ struct ms_coarse {
     msgb::DBuf<float> inv32;     // M*M inverse (FP32, mixed)
     bool use64 = false;          // mixed stage whose FP32 inverse was too inaccurate: FP64 inverse used
     double inv32_error = 0.0;    // ||inv32 A_c v - v|| / ||v|| on a test vector
+    int refine_steps = 2;        // FP64 refinement steps of a mixed stage's coarse solve
+    int sp_w = 0;                // ELL copy of A_c for the refinement residuals (0: dense)
+    msgb::DBuf<int> sp_col;
+    msgb::DBuf<double> sp_val;
     msgb::DBuf<double> work64;   // factor workspace
     msgb::DBuf<float> work32;
     // Galerkin column chunks (size gchunk, chosen so the partial rows of split
@@ -469,6 +486,11 @@ void launch_basis_scale(const ms_system &s, ms_basis &b, bool fp32, cudaStream_t
 void launch_msrsb_iter(const ms_system &s, ms_basis &b, bool fp32, unsigned long long *ctl, double tol, int max_iter,
                        cudaStream_t st);
 void launch_basis_columns(ms_basis &b, cudaStream_t st);
+// Re-smooth the bases of several systems from their block indicators in one
+// persistent launch per precision; members it cannot take (no slot maps, more
+// than 8 connections per row) get taken[m] = 0 and are left to the caller.
+void smooth_batch(ms_ctx *ctx, const std::vector<ms_system *> &sys, const std::vector<ms_basis *> &bases,
+                  std::vector<char> &taken);
 // Galerkin
 int launch_ap_count(const ms_system &s, const ms_basis &b, int *cnt_max, int *host_pinned, cudaStream_t st);
 void launch_ap_fill(const ms_system &s, const ms_basis &b, ms_coarse &c, cudaStream_t st);
@@ -479,6 +501,10 @@ void launch_rap(const ms_system &s, const std::vector<int> &h_cptr, const int *c
 // dense
 void dense_factor_inverse64(ms_coarse &c, int *err, cudaStream_t st);
 void dense_factor_inverse32(ms_coarse &c, int *err, cudaStream_t st);
+// blocked symmetric sweep in one launch (FP64 CUDA cores; FP32 on tcgen05)
+void dense_sweep_inverse64(ms_coarse &c, int *err, cudaStream_t st);
+void dense_sweep_inverse32(ms_coarse &c, int *err, cudaStream_t st);
+void coarse_sparse_copy(ms_coarse &c, int *scratch, int *host, cudaStream_t st);
 void dense_gj_inverse64(ms_coarse &c, int *err, cudaStream_t st);
 void dense_gj_inverse32(ms_coarse &c, int *err, cudaStream_t st);
 void launch_check_diag(const ms_coarse &c, int *err, cudaStream_t st);

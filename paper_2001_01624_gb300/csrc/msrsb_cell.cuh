@@ -1,0 +1,117 @@
+// The cell update of MsRSB basis smoothing (Sec. 5.1), shared by the
+// per-system smoothing kernel and the batched persistent kernel, so both
+// compute bitwise the same values.
+#pragma once
+
+#include "ms_internal.h"
+
+namespace msgb {
+
+// |x| as an integer key that orders like the value (IEEE bit patterns of
+// non-negative numbers; NaN above infinity), so the running maximum of the
+// basis increments stays off the FP64 pipe; key_value turns the key back.
+__device__ __forceinline__ unsigned long long abs_key(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ unsigned long long abs_key(float x) {
+    return (unsigned long long)(__float_as_uint(x) & 0x7fffffffu);
+}
+template <typename T>
+__device__ __forceinline__ double key_value(unsigned long long k);
+template <>
+__device__ __forceinline__ double key_value<double>(unsigned long long k) { return __longlong_as_double((long long)k); }
+template <>
+__device__ __forceinline__ double key_value<float>(unsigned long long k) { return (double)__uint_as_float((unsigned)k); }
+
+template <typename T, bool CG>
+__device__ __forceinline__ T ldp(const T *p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
+// One cell of the MsRSB iteration with precomputed neighbour slot maps,
+// slots below SB (at least the cell's count); returns the key of its largest
+// |increment|.
+// CG: read the slot values through L2 (values another block of the same
+// launch wrote; see k_msrsb_batch).
+// PRE: the rows come prescaled (diag = 1 - (omega / A_ii) A_ii, off = -(omega / A_ii) A_ij), so the
+// Jacobi update is already in the accumulated sum.
+template <typename T, int WM, int SB, bool PRE, bool CG = false>
+__device__ __forceinline__ unsigned long long msrsb_cell(int i, int cnt, int n, int W, const int *__restrict__ col,
+                                                         const T *__restrict__ off, const T *__restrict__ diag,
+                                                         const unsigned *__restrict__ nmap,
+                                                         const T *__restrict__ pin, T *__restrict__ pout,
+                                                         const T *__restrict__ odiag) {
+    unsigned long long inck = 0ull;
+    T v[SB], acc[SB];
+    const T d = diag[i];
+#pragma unroll
+    for (int s = 0; s < SB; ++s) {
+        v[s] = s < cnt ? ldp<T, CG>(pin + (int64_t)s * n + i) : T(0);
+        acc[s] = d * v[s];
+    }
+    if (WM > 0) {
+        // at most WM connections: every connection's column, coefficient and
+        // slot map are loaded first, then all the gathers, so the loads of
+        // different neighbours overlap (same order of the sums as below)
+        int kk[WM > 0 ? WM : 1];
+        T aw[WM > 0 ? WM : 1];
+        unsigned mw[WM > 0 ? WM : 1];
+#pragma unroll
+        for (int w = 0; w < WM; ++w) {
+            const int64_t at = (int64_t)w * n + i;
+            kk[w] = w < W ? col[at] : i;
+            aw[w] = w < W ? off[at] : T(0);
+            mw[w] = w < W ? nmap[at] : 0xffffffffu;
+        }
+#pragma unroll
+        for (int w = 0; w < WM; ++w) {
+            if (kk[w] == i) continue;
+#pragma unroll
+            for (int s = 0; s < SB; ++s) {
+                const unsigned t = (mw[w] >> (4 * s)) & 15u;
+                if (s < cnt && t != 15u) acc[s] += aw[w] * ldp<T, CG>(pin + (int64_t)t * n + kk[w]);
+            }
+        }
+    } else {
+        for (int w = 0; w < W; ++w) {
+            const int64_t at = (int64_t)w * n + i;
+            const int k = col[at];
+            if (k == i) continue;
+            const T a = off[at];
+            const unsigned m = nmap[at];
+#pragma unroll
+            for (int s = 0; s < SB; ++s) {
+                const unsigned t = (m >> (4 * s)) & 15u;
+                if (s < cnt && t != 15u) acc[s] += a * ldp<T, CG>(pin + (int64_t)t * n + k);
+            }
+        }
+    }
+    // omega / A_ii precomputed per smoothing run; one division for the
+    // partition-of-unity scale
+    T sum = 0;
+    if (PRE) {
+#pragma unroll
+        for (int s = 0; s < SB; ++s)
+            if (s < cnt) sum += acc[s];
+    } else {
+        const T od = odiag[i];
+#pragma unroll
+        for (int s = 0; s < SB; ++s)
+            if (s < cnt) {
+                acc[s] = v[s] - od * acc[s];
+                sum += acc[s];
+            }
+    }
+    const T rs = T(1) / sum;
+#pragma unroll
+    for (int s = 0; s < SB; ++s)
+        if (s < cnt) {
+            const T nv = acc[s] * rs;
+            inck = max(inck, abs_key(nv - v[s]));
+            pout[(int64_t)s * n + i] = nv;
+        }
+    return inck;
+}
+
+}  // namespace msgb
