@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-fv", action="store_true")
     ap.add_argument("--no-cpr", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the faulted c3 solves, the ensemble and the serving summaries of the default line")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run N extra untimed steps only (for ncu launch lists)")
     ap.add_argument("--profile-mixed", action="store_true",
@@ -327,7 +329,63 @@ ENSEMBLE = ("batched ensemble of {m} independent 3D TPFA systems of uneven size 
             "residual")
 
 
-def run_ensemble(args):
+def c3_extra(torch, ms, G, dev, stream):
+    """The faulted 200x200x50 geomodel (config 3): general + static stages,
+    GMRES(30) to 1e-6 in FP64 and mixed, and Richardson with the Dp(Inf)
+    dynamic stage (mixed); wall times of the basis setup and device-timed
+    solves."""
+    import numpy as np
+    gm = G.config3(0)
+    ctx = ms.ms_create(dev.index or 0, stream)
+    out = {"workload": "faulted 200x200x50 (1,840,020 active cells, 6 faults with 2-cell throw), general 10x10x5 "
+                       "+ facies static stage"}
+    try:
+        t0 = time.perf_counter()
+        s = ms.ms_system_create(ctx, gm.grid, 0)
+        out["analysis_s"] = time.perf_counter() - t0
+        with torch.cuda.stream(stream):
+            ms.ms_assemble_tpfa(ctx, s, torch.from_numpy(gm.perm.ravel().copy()).to(dev))
+            part, M = ms.ms_partition_cartesian(ctx, s, gm.block)
+            cells = gm.grid.active_cells()
+            n = len(cells)
+            ps = np.empty(n, np.int32)
+            Ms = ms.ms_partition_components(ctx, s, part * 2 + gm.facies[cells].astype(np.int32), ps)
+            q = torch.from_numpy(gm.q_active()).to(dev)
+            for prec, nm in ((ms.MS_PREC_FP64, "fp64"), (ms.MS_PREC_MIXED, "mixed")):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                b1, it1 = ms.ms_build_basis(ctx, s, part, M, block=gm.block, precision=prec)
+                b2, it2 = ms.ms_build_basis(ctx, s, ps, Ms, support=ms.MS_SUPPORT_HOP, precision=prec)
+                c1, c2 = ms.ms_galerkin(ctx, s, b1, prec), ms.ms_galerkin(ctx, s, b2, prec)
+                torch.cuda.synchronize()
+                setup = time.perf_counter() - t0
+                res = {"setup_s": setup, "basis_iters": [it1, it2], "coarse_blocks": [M, Ms]}
+                for outer, key, sched in ((ms.MS_OUTER_GMRES, "gmres", 0), (ms.MS_OUTER_RICHARDSON, "richardson_dp_inf", 2)):
+                    p = torch.zeros_like(q)
+                    ms.ms_solve(ctx, s, [c1, c2], q, p, tol=1e-6, max_iter=3000, precision=prec, outer=outer,
+                                adapt_schedule=sched)   # warm-up (workspaces)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    p.zero_()
+                    e0.record(stream)
+                    info = ms.ms_solve(ctx, s, [c1, c2], q, p, tol=1e-6, max_iter=3000, precision=prec, outer=outer,
+                                       adapt_schedule=sched)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    t = e0.elapsed_time(e1)
+                    res[key] = {"iters": info["iters"], "converged": info["converged"], "solve_ms": t,
+                                "solve_unknowns_per_s": n / (t * 1e-3), "rel_residual": info["rel_residual"]}
+                out[nm] = res
+                for h in (c1, c2):
+                    ms.ms_coarse_release(h)
+                for h in (b1, b2):
+                    ms.ms_basis_release(h)
+        ms.ms_system_release(s)
+    finally:
+        ms.ms_destroy(ctx)
+    return out
+
+
+def run_ensemble(args, emit=True):
     """Ensemble step: for every member, basis re-smoothing + Galerkin + solve,
     all members in one ms_solve_batch call (members overlap on worker streams);
     the same work with one worker is timed beside it."""
@@ -453,6 +511,8 @@ def run_ensemble(args):
         ms.ms_basis_release(m["rebuild"])
         ms.ms_system_release(m["sys"])
     ms.ms_destroy(ctx)
+    if not emit:
+        return line
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -486,7 +546,7 @@ def serving_models(m_count, torch, dev, seed=0):
     return models
 
 
-def run_serving(args):
+def run_serving(args, emit=True):
     rank, world, local = dist_env()
     import torch
     global np
@@ -550,6 +610,8 @@ def run_serving(args):
                                "mean_ms": st2["mean_ms"], "throughput_req_s": st2["throughput_req_s"]},
             "gpu_launches": int(launches), "clocks": clocks}
     srv.close()
+    if not emit:
+        return line
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -967,6 +1029,19 @@ def main():
     for p in plans.values():
         p.release()
     ms.ms_destroy(ctx)
+    # the other configurations, compactly (N = 1 only): faulted c3 solves,
+    # the batched ensemble, the serving stream
+    if rank == 0 and world == 1 and not args.no_extras:
+        line["c3"] = c3_extra(torch, ms, G, dev, stream)
+        ea = argparse.Namespace(**vars(args))
+        ea.steps, ea.warmup, ea.no_e2e, ea.no_cpu_baseline = 2, 1, True, True
+        el = run_ensemble(ea, emit=False)
+        line["ensemble"] = {k: el[k] for k in ("value", "unit", "ms_per_step", "sequential", "members", "roofline")}
+        line["ensemble"]["config"] = el["config"]
+        sa = argparse.Namespace(**vars(args))
+        sa.requests = min(args.requests, 200)
+        sl = run_serving(sa, emit=False)
+        line["serving"] = {k: sl[k] for k in ("latency", "requests", "sustained_load", "config")}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -50,7 +50,7 @@
 extern "C" {
 #endif
 
-#define MS_ABI_VERSION 9
+#define MS_ABI_VERSION 10
 
 typedef enum {
     MS_OK = 0,
@@ -239,8 +239,10 @@ ms_status ms_ilu_apply(ms_ctx *ctx, ms_system *sys, int32_t precision, const dou
  *    (made by an earlier ms_ilu_apply or ms_solve with the ILU(0)
  *    smoother); otherwise MS_ERR_STATE.
  *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress, with that device current); make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress, with that device current) and keeps it for the
+ *    life of the process; make that first call before any stream capture,
+ *    and do not reset the device (cudaDeviceReset) while the library is in
+ *    use.
  *  - Every call shares the one array and it keeps the last call's contents;
  *    each call clears the counters that must start at zero.  Calls that
  *    overlap on the GPU race on the array: do not overlap them.
@@ -545,6 +547,20 @@ ms_status ms_total_mobility(ms_ctx *ctx, const ms_system *sys, const ms_fluid *f
  * place; substeps (or NULL) receives the substep count. */
 ms_status ms_transport_step(ms_ctx *ctx, ms_system *sys, const ms_fluid *fluid, const double *p, const double *q,
                             double dt, double *S, int32_t *substeps);
+
+/* Pressure update dp = p - p_prev over the n unknowns (device arrays of the
+ * context's device); the dynamically adapted basis of the next step is
+ * built from it (Sec. 5.1, the pressure change between successive steps).
+ * Ordered on the context's stream. */
+ms_status ms_pressure_update(ms_ctx *ctx, const ms_system *sys, const double *p, const double *p_prev, double *dp);
+
+/* Device allocations of the library (all go through one allocator): bytes
+ * allocated so far by library calls made on the calling host thread
+ * (*thread_bytes), and the number of device allocations made so far in the
+ * process (*allocations).  Either pointer may be NULL.  Serving measures a
+ * model's footprint with the first; tests use the second to check that a
+ * call allocates nothing. */
+ms_status ms_allocation_stats(int64_t *thread_bytes, int64_t *allocations);
 
 /* ---------------------------------------------------------------- tracing */
 /* Process-wide kernel tracing.  Launch counts are always kept; when enabled,

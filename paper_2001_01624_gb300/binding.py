@@ -155,6 +155,8 @@ def lib():
         "ms_set_batch_tuning": ([_vp, _i32, _i32], _i32),
         "ms_total_mobility": ([_vp, _vp, P(ms_fluid), _vp, _vp], _i32),
         "ms_transport_step": ([_vp, _vp, P(ms_fluid), _vp, _vp, _d, _vp, P(_i32)], _i32),
+        "ms_pressure_update": ([_vp, _vp, _vp, _vp, _vp], _i32),
+        "ms_allocation_stats": ([P(_i64), P(_i64)], _i32),
         "ms_profile_enable": ([_i32], _i32),
         "ms_profile_reset": ([], _i32),
         "ms_profile_read": ([_vp, _i32, P(_i32), P(_i64)], _i32),
@@ -177,7 +179,7 @@ def exported_symbols() -> Sequence[str]:
             "ms_build_basis", "ms_basis_rebuild", "ms_basis_update", "ms_basis_release", "ms_basis_get_info",
             "ms_basis_get", "ms_add_adaptive_basis", "ms_galerkin", "ms_coarse_refresh", "ms_coarse_release",
             "ms_coarse_get", "ms_solve", "ms_solve_batch", "ms_basis_rebuild_batch",
-            "ms_set_batch_tuning", "ms_total_mobility", "ms_transport_step", "ms_profile_enable", "ms_profile_reset", "ms_profile_read"]
+            "ms_set_batch_tuning", "ms_total_mobility", "ms_transport_step", "ms_pressure_update", "ms_allocation_stats", "ms_profile_enable", "ms_profile_reset", "ms_profile_read"]
 
 
 def _ptr(a):
@@ -544,6 +546,18 @@ def ms_solve_batch(ctx, members: Sequence[dict], tol=1e-6, max_iter=500, smoothe
 
 def _h(x):
     return x.value if isinstance(x, _vp) else x
+
+
+def ms_pressure_update(ctx, sys, p, p_prev, dp):
+    """dp = p - p_prev on the device (torch tensors of the context's device)."""
+    _check(lib().ms_pressure_update(ctx, sys, _ptr(p), _ptr(p_prev), _ptr(dp)), ctx)
+
+
+def ms_allocation_stats() -> dict:
+    """dict(thread_bytes, allocations) of the library's device allocations."""
+    b, n = _i64(), _i64()
+    _check(lib().ms_allocation_stats(C.byref(b), C.byref(n)))
+    return dict(thread_bytes=b.value, allocations=n.value)
 
 
 def ms_basis_rebuild_batch(ctx, systems: Sequence, bases: Sequence) -> np.ndarray:

@@ -15,8 +15,11 @@
 // (or for every member to stop).  Slots are reused only after their previous
 // item was consumed.  Every wait is bounded (2 s) and records an error.
 //
-// The cell update is msrsb_cell, the one the per-system kernel runs, with the
-// slot values read through L2: within one launch another block wrote them.
+// The cell update is msrsb_cell, the one the per-system kernel runs.  The slot
+// values another block wrote in this launch are read with weak L1-cached
+// loads after the acquire of the item's slot (thread 0, then the block
+// barrier), which the memory model orders after the writes the finishing
+// block released.
 // Results are bitwise those of smoothing each member alone.
 #include <algorithm>
 #include <cstring>
@@ -31,6 +34,8 @@ namespace {
 constexpr int kBT = 256;                       // threads per block (cells per pass of a tile)
 constexpr unsigned long long kConsumed = 1ull << 32;
 constexpr unsigned long long kBatchWaitNs = 2000000000ull;
+// slot values: weak loads cached in L1 after the item's acquire (ldp policy 2)
+constexpr int kLd = 2;
 
 template <typename T>
 struct SmJob {
@@ -145,14 +150,14 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 6 : 3) k_msrsb_batch(con
                 const int cmax = __reduce_max_sync(0xffffffffu, cnt);
                 if (i < i1) {
                     unsigned long long k;
-                    if (cmax <= 2) k = msrsb_cell<T, 8, 2, true, true>(i, cnt, J.n, J.W, J.col, J.off, J.diag, J.nmap, pin, pout, J.odiag);
-                    else if (cmax <= 4) k = msrsb_cell<T, 8, 4, true, true>(i, cnt, J.n, J.W, J.col, J.off, J.diag, J.nmap, pin, pout, J.odiag);
-                    else k = msrsb_cell<T, 8, 8, true, true>(i, cnt, J.n, J.W, J.col, J.off, J.diag, J.nmap, pin, pout, J.odiag);
+                    if (cmax <= 2) k = msrsb_cell<T, 8, 2, true, kLd>(i, cnt, J.n, J.W, J.col, J.off, J.diag, J.nmap, pin, pout, J.odiag);
+                    else if (cmax <= 4) k = msrsb_cell<T, 8, 4, true, kLd>(i, cnt, J.n, J.W, J.col, J.off, J.diag, J.nmap, pin, pout, J.odiag);
+                    else k = msrsb_cell<T, 8, 8, true, kLd>(i, cnt, J.n, J.W, J.col, J.off, J.diag, J.nmap, pin, pout, J.odiag);
                     inck = max(inck, k);
                 }
             } else {
                 if (i < i1)
-                    inck = max(inck, msrsb_cell<T, 8, 8, false, true>(i, cnt, J.n, J.W, J.col, J.off, J.diag, J.nmap, pin,
+                    inck = max(inck, msrsb_cell<T, 8, 8, false, kLd>(i, cnt, J.n, J.W, J.col, J.off, J.diag, J.nmap, pin,
                                                                       pout, J.odiag));
             }
         }

@@ -271,6 +271,38 @@ __global__ void __launch_bounds__(128) k_gemv(const T *__restrict__ A, int M, co
 
 inline int gemv_blocks(int M) { return (M + 3) / 4; }
 
+// Row `row` of A x for one warp, A read-only and x read through L2 (another
+// block of the same launch wrote it); the sum is valid in lane 0.
+__device__ __forceinline__ float gemv_row_cg(const float *__restrict__ A, int M, int row, const float *x, int lane) {
+    const float *a = A + (int64_t)row * M;
+    int pre = (int)(((16 - ((uintptr_t)a & 15)) & 15) / sizeof(float));
+    if (pre > M) pre = M;
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    if (lane < pre) s[0] = a[lane] * __ldcg(&x[lane]);
+    const int nv = (M - pre) / 4;
+    const float4 *av = (const float4 *)(a + pre);
+    const float *xp = x + pre;
+    for (int v0 = lane; v0 < nv; v0 += 128) {
+        float4 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (v0 + 32 * u < nv) q[u] = __ldg(av + v0 + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int v = v0 + 32 * u;
+            if (v < nv) {
+                const float *xs = xp + (int64_t)v * 4;
+                s[u] += q[u].x * __ldcg(&xs[0]) + q[u].y * __ldcg(&xs[1]) + q[u].z * __ldcg(&xs[2]) + q[u].w * __ldcg(&xs[3]);
+            }
+        }
+    }
+    for (int c = pre + nv * 4 + lane; c < M; c += 32) s[0] += a[c] * __ldcg(&x[c]);
+    float t = (s[0] + s[1]) + (s[2] + s[3]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    return t;
+}
+
 // rc = d - A x (FP64), and its FP32 copy.
 __global__ void k_dense_residual(const double *__restrict__ A, int M, const double *__restrict__ d,
                                  const double *__restrict__ x, double *__restrict__ rc, float *__restrict__ rc32) {
@@ -701,6 +733,46 @@ double coarse_inverse_check32(const ms_coarse &c, double *host2, cudaStream_t st
     return host2[1] > 0 ? std::sqrt(host2[0] / host2[1]) : 0.0;
 }
 
+// The whole mixed-precision coarse solve in one cooperative launch:
+//   t = fp32(d); x = inv32 t; then `steps` times: t = fp32(d - A_c x) (FP64,
+//   ELL copy of A_c), x += inv32 t,
+// phases separated by grid barriers (2 + 2 steps), rows spread over the
+// blocks (one warp per row for the products, one thread per row for the
+// residuals).  Same arithmetic as the kernel chain of launch_coarse_refine.
+__global__ void __launch_bounds__(128) k_refine_coop(const float *__restrict__ inv, int M, const int *__restrict__ ecol,
+                                                     const double *__restrict__ eval, int Wc,
+                                                     const double *__restrict__ d, double *xc, double *rc, float *t,
+                                                     int steps, unsigned long long *bar, int *err) {
+    GridSync gs;
+    gs.begin(bar, err);
+    const int total = 2 + 2 * steps;
+    const int G = gridDim.x;
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += G * blockDim.x) t[i] = (float)d[i];
+    if (!gs.sync(total)) return;
+    for (int row = gw; row < M; row += G * wpb) {
+        const float v = gemv_row_cg(inv, M, row, t, lane);
+        if (lane == 0) xc[row] = (double)v;
+    }
+    if (!gs.sync(total)) return;
+    for (int st = 0; st < steps; ++st) {
+        for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < M; row += G * blockDim.x) {
+            double sacc = 0.0;
+            for (int w = 0; w < Wc; ++w) sacc += eval[(int64_t)w * M + row] * __ldcg(&xc[ecol[(int64_t)w * M + row]]);
+            const double r = d[row] - sacc;
+            rc[row] = r;
+            t[row] = (float)r;
+        }
+        if (!gs.sync(total)) return;
+        for (int row = gw; row < M; row += G * wpb) {
+            const float v = gemv_row_cg(inv, M, row, t, lane);
+            if (lane == 0) xc[row] += (double)v;
+        }
+        if (!gs.sync(total)) return;
+    }
+}
+
 // ELL copy of A_c for the refinement residuals (kept only when A_c is sparse:
 // at most M / 4 nonzeros per row).
 void coarse_sparse_copy(ms_coarse &c, int *scratch, int *host, cudaStream_t st) {
@@ -720,6 +792,18 @@ void coarse_sparse_copy(ms_coarse &c, int *scratch, int *host, cudaStream_t st) 
     k_ell_fill<<<(M + 7) / 8, 256, 0, st>>>(c.Ac.p, M, Wc, c.sp_col.p, c.sp_val.p);
     MS_CHECK_LAUNCH();
     c.sp_w = Wc;
+    // blocks of the one-launch coarse solve (all resident: grid barriers)
+    int dev = 0, sms = 0, per_sm = 0;
+    MS_CUDA(cudaGetDevice(&dev));
+    MS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine_coop, 128, 0));
+    c.coop_blocks = per_sm >= 1 ? std::max(1, std::min(sms, (M + 3) / 4)) : 0;
+    if (c.gj_bar.n == 0) {
+        c.gj_bar.alloc(2);
+        c.gj_bar.zero(st);
+    }
+    c.refine_err.alloc(1);
+    c.refine_err.zero(st);
 }
 
 void launch_gemv64(const double *A, int M, const double *x, double *y, cudaStream_t st) {
@@ -738,6 +822,23 @@ void launch_gemv32(const float *A, int M, const float *x, float *y, cudaStream_t
 void launch_coarse_refine(const ms_coarse &c, const double *d, double *xc, double *rc, float *t32a, float *t32b,
                           int steps, cudaStream_t st) {
     const int M = c.M;
+    if (c.sp_w > 0 && c.coop_blocks > 0 && c.gj_bar.n) {
+        KernelScope ks_(st, "coarse_refine", (double)M * M * 4 * (1 + steps) +
+                                                 steps * ((double)c.sp_w * M * 12 + (double)M * 24));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(c.coop_blocks);
+        cfg.blockDim = dim3(128);
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;   // grid barriers: every block resident
+        at[0].val.cooperative = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        MS_CUDA(cudaLaunchKernelEx(&cfg, k_refine_coop, (const float *)c.inv32.p, M, (const int *)c.sp_col.p,
+                                   (const double *)c.sp_val.p, c.sp_w, d, xc, rc, t32a, steps, c.gj_bar.p,
+                                   c.refine_err.p));
+        return;
+    }
     const double resid = c.sp_w > 0 ? (double)c.sp_w * M * 12 + (double)M * 24 : (double)M * M * 8;
     KernelScope ks_(st, "coarse_refine", (double)M * M * 4 * (1 + steps) + steps * resid);
     k_d2f<<<(M + 255) / 256, 256, 0, st>>>(M, d, t32a);

@@ -80,6 +80,17 @@ void check_sweep_errors(ms_ctx *ctx, ms_system *s) {
     }
 }
 
+// A grid-barrier timeout in a stage's one-launch coarse solve: reset its
+// barrier and report it.
+void check_refine_errors(ms_ctx *ctx, ms_coarse *c) {
+    if (!c || !c->refine_err.n) return;
+    const int e = read_error_word(ctx, c->refine_err.p);
+    if (!e) return;
+    MS_CUDA(cudaMemsetAsync(c->refine_err.p, 0, sizeof(int), ctx->stream));
+    if (c->gj_bar.n) MS_CUDA(cudaMemsetAsync(c->gj_bar.p, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    throw Error{MS_ERR_TIMEOUT, "a coarse-solve grid barrier wait ran out"};
+}
+
 ms_status fail(ms_ctx *ctx, ms_status st, const std::string &what) {
     if (ctx) ctx->err = what;
     return st;
@@ -417,6 +428,18 @@ double read_norm(ms_ctx *ctx, const double *dev) {
 
 }  // namespace
 
+namespace {
+thread_local int64_t t_device_bytes = 0;
+std::atomic<int64_t> g_device_allocs{0};
+}  // namespace
+
+namespace msgb {
+void note_device_alloc(size_t bytes) {
+    t_device_bytes += (int64_t)bytes;
+    g_device_allocs.fetch_add(1, std::memory_order_relaxed);
+}
+}  // namespace msgb
+
 // =================================================================== ABI
 extern "C" {
 
@@ -620,6 +643,23 @@ ms_status ms_ilu_apply(ms_ctx *ctx, ms_system *s, int32_t precision, const doubl
     check_sweep_errors(ctx, s);
     copy_out(z, s->w_z.p, s->n, st);
     sync(st);
+    return MS_OK;
+    API_CATCH(ctx)
+}
+
+ms_status ms_allocation_stats(int64_t *thread_bytes, int64_t *allocations) {
+    if (thread_bytes) *thread_bytes = t_device_bytes;
+    if (allocations) *allocations = g_device_allocs.load(std::memory_order_relaxed);
+    return MS_OK;
+}
+
+ms_status ms_pressure_update(ms_ctx *ctx, const ms_system *s, const double *p, const double *p_prev, double *dp) {
+    if (!ctx || !s || !p || !p_prev || !dp) return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
+    API_TRY
+    DeviceGuard g(ctx->device);
+    MS_REQUIRE(is_device_ptr(p) && is_device_ptr(p_prev) && is_device_ptr(dp), MS_ERR_INVALID_ARG,
+               "ms_pressure_update takes device arrays");
+    launch_sub(p, p_prev, dp, s->n, ctx->stream);
     return MS_OK;
     API_CATCH(ctx)
 }
@@ -1319,6 +1359,8 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
         if (!(res == res)) throw Error{MS_ERR_CUDA, "residual became NaN"};
         if (opts->smoother == MS_SMOOTHER_ILU0) check_sweep_errors(ctx, s);
     }
+    for (int l = 0; l < n_stages; ++l) check_refine_errors(ctx, stages[l]);
+    if (dyn_coarse) check_refine_errors(ctx, dyn_coarse.get());
     copy_out(p, s->w_x.p, n, st);
     sync(st);
     const bool conv = res <= opts->tol;

@@ -38,6 +38,11 @@ struct Error {
 #define MS_CHECK_LAUNCH() MS_CUDA(cudaGetLastError())
 
 // ------------------------------------------------------------ device buffer
+// Every device allocation of the library goes through DBuf: this records its
+// bytes for the calling host thread and counts it for the process
+// (ms_allocation_stats).
+void note_device_alloc(size_t bytes);
+
 template <typename T>
 struct DBuf {
     T *p = nullptr;
@@ -58,6 +63,7 @@ struct DBuf {
         if (count == 0) return;
         MS_CUDA(cudaMalloc(&p, count * sizeof(T)));
         n = count;
+        note_device_alloc(count * sizeof(T));
     }
     void upload(const std::vector<T> &h, cudaStream_t s) {
         alloc(h.size());
@@ -346,6 +352,8 @@ struct ms_coarse {
     int sp_w = 0;                // ELL copy of A_c for the refinement residuals (0: dense)
     msgb::DBuf<int> sp_col;
     msgb::DBuf<double> sp_val;
+    int coop_blocks = 0;         // blocks of the one-launch refinement (0: kernel chain)
+    msgb::DBuf<int> refine_err;  // its grid-barrier error word
     msgb::DBuf<double> work64;   // factor workspace
     msgb::DBuf<float> work32;
     // Galerkin column chunks (size gchunk, chosen so the partial rows of split

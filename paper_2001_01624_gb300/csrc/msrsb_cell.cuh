@@ -23,20 +23,37 @@ __device__ __forceinline__ double key_value<double>(unsigned long long k) { retu
 template <>
 __device__ __forceinline__ double key_value<float>(unsigned long long k) { return (double)__uint_as_float((unsigned)k); }
 
-template <typename T, bool CG>
+// Slot-value loads: LD 0 as the compiler chooses (values constant during the
+// launch), 1 through L2 only, 2 weak loads cached in L1 -- values another
+// block wrote in the same launch, read after an acquire that synchronises
+// with their release (the acquire invalidates the SM's L1, so a later weak
+// load cannot return an older value; PTX memory model, causality order).
+__device__ __forceinline__ double ld_ca(const double *p) {
+    double v;
+    asm volatile("ld.global.ca.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_ca(const float *p) {
+    float v;
+    asm volatile("ld.global.ca.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
+template <typename T, int LD>
 __device__ __forceinline__ T ldp(const T *p) {
-    if constexpr (CG) return __ldcg(p);
+    if constexpr (LD == 1) return __ldcg(p);
+    else if constexpr (LD == 2) return ld_ca(p);
     else return *p;
 }
 
 // One cell of the MsRSB iteration with precomputed neighbour slot maps,
 // slots below SB (at least the cell's count); returns the key of its largest
 // |increment|.
-// CG: read the slot values through L2 (values another block of the same
-// launch wrote; see k_msrsb_batch).
+// CG: the slot-value load policy of ldp (k_msrsb_batch reads values other
+// blocks of the same launch wrote).
 // PRE: the rows come prescaled (diag = 1 - (omega / A_ii) A_ii, off = -(omega / A_ii) A_ij), so the
 // Jacobi update is already in the accumulated sum.
-template <typename T, int WM, int SB, bool PRE, bool CG = false>
+template <typename T, int WM, int SB, bool PRE, int CG = 0>
 __device__ __forceinline__ unsigned long long msrsb_cell(int i, int cnt, int n, int W, const int *__restrict__ col,
                                                          const T *__restrict__ off, const T *__restrict__ diag,
                                                          const unsigned *__restrict__ nmap,

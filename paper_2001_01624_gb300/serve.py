@@ -18,6 +18,10 @@ pressure, saturation) is resident once admitted; admission of a model that is
 not resident waits for free device memory (the measured footprint of its
 last load, or an estimate from its size) and evicts idle models least
 recently used first, keeping their pressure and saturation on the host.
+A model's footprint is what the library itself allocated for it (its
+allocation count on the loading thread, for the handles and the workspaces
+of its first step) plus the model's own tensors, so concurrent steps of other
+models do not disturb the measurement.
 """
 from __future__ import annotations
 
@@ -73,20 +77,27 @@ class Model:
 
     def _load(self, ctx, precision):
         t = self.torch
-        free0 = t.cuda.mem_get_info(self.device)[0]
+        lib0 = ms.ms_allocation_stats()["thread_bytes"]
         self.sys = ms.ms_system_create(ctx, self.gm.grid, 0)
         self.perm = t.from_numpy(self.gm.perm.ravel().copy()).to(self.device)
         self.qd = t.from_numpy(self.q).to(self.device)
         self.p = t.from_numpy(self.h_p).to(self.device)
         self.S = t.from_numpy(self.h_S).to(self.device)
         self.lam = t.empty_like(self.p)
+        self.p_prev = t.empty_like(self.p)
         self.dp = None if self.h_dp is None else t.from_numpy(self.h_dp).to(self.device)
         ms.ms_assemble_tpfa(ctx, self.sys, self.perm)
         part, M = ms.ms_partition_cartesian(ctx, self.sys, self.gm.block)
         self.basis, _ = ms.ms_build_basis(ctx, self.sys, part, M, block=self.gm.block, precision=precision)
         self.coarse = ms.ms_galerkin(ctx, self.sys, self.basis, precision)
         t.cuda.synchronize(self.device)
-        self.footprint = max(self.footprint // 4, free0 - t.cuda.mem_get_info(self.device)[0])
+        tensors = sum(x.numel() * x.element_size() for x in (self.perm, self.qd, self.p, self.S, self.lam,
+                                                              self.p_prev))
+        # library bytes of the handles, the tensors, and (once measured) the
+        # workspaces a step adds; before the first step: the size estimate
+        lib = ms.ms_allocation_stats()["thread_bytes"] - lib0
+        self.load_bytes = lib + 2 * tensors
+        self.footprint = self.load_bytes + getattr(self, "step_bytes", self.n * BYTES_PER_CELL_ESTIMATE // 2)
         self.resident = True
 
     def evict(self):
@@ -97,8 +108,9 @@ class Model:
         ms.ms_coarse_release(self.coarse)
         ms.ms_basis_release(self.basis)
         ms.ms_system_release(self.sys)
-        del self.perm, self.qd, self.p, self.S, self.lam, self.dp
+        del self.perm, self.qd, self.p, self.S, self.lam, self.dp, self.p_prev
         self.resident = False
+        self.torch.cuda.empty_cache()      # let the freed tensors show as free device memory
 
     # ------------------------------------------------------------------ step
     def step(self, ctx, stream, fluid, dt, precision, tol, adapt, max_iter=5000):
@@ -108,6 +120,7 @@ class Model:
             return self._step(ctx, fluid, dt, precision, tol, adapt, max_iter)
 
     def _step(self, ctx, fluid, dt, precision, tol, adapt, max_iter):
+        lib0 = ms.ms_allocation_stats()["thread_bytes"]
         ms.ms_total_mobility(ctx, self.sys, fluid, self.S, self.lam)
         ms.ms_assemble_tpfa(ctx, self.sys, self.perm, mobility=self.lam, p_prev=self.p if self.steps else None)
         ms.ms_coarse_refresh(ctx, self.sys, self.coarse)
@@ -117,14 +130,20 @@ class Model:
             dyn_b = ms.ms_add_adaptive_basis(ctx, self.sys, self.dp, precision=precision)
             dyn_c = ms.ms_galerkin(ctx, self.sys, dyn_b, precision)
             stages.append(dyn_c)
-        p_old = self.p.clone()
+        self.p_prev.copy_(self.p)
         info = ms.ms_solve(ctx, self.sys, stages, self.qd, self.p, tol=tol, max_iter=max_iter, precision=precision,
                            use_x0=self.steps > 0, outer=ms.MS_OUTER_GMRES, restart=30)
         if dyn_c is not None:
             ms.ms_coarse_release(dyn_c)
             ms.ms_basis_release(dyn_b)
-        self.dp = self.p - p_old
+        if self.dp is None:
+            self.dp = self.torch.empty_like(self.p)
+        ms.ms_pressure_update(ctx, self.sys, self.p, self.p_prev, self.dp)
         k = ms.ms_transport_step(ctx, self.sys, fluid, self.p, self.qd, dt, self.S)
+        if self.steps == 0:
+            # workspaces the first step adds (solver vectors, the dynamic stage)
+            self.step_bytes = ms.ms_allocation_stats()["thread_bytes"] - lib0 + self.dp.numel() * 8
+            self.footprint = self.load_bytes + self.step_bytes
         self.steps += 1
         return info["iters"], k, info["rel_residual"]
 

@@ -42,7 +42,7 @@ def test_binding_wraps_every_declared_symbol():
 
 def test_abi_version_and_status_strings(lib):
     from paper_2001_01624_gb300 import binding as b
-    assert b.ms_abi_version() == 9
+    assert b.ms_abi_version() == 10
     assert lib.ms_status_string(b.MS_ERR_NOT_CONVERGED) == b"not converged"
 
 

@@ -5,8 +5,10 @@ an application that gave all free memory to its own pool allocator, or a
 latency-critical loop that cannot take an allocation's implicit device
 synchronisation.  This entry point keeps its scratch in a fixed device array
 inside the library.  Its output must equal ms_ilu_apply's (the tolerance of
-the other ILU(0) tests, 1e-10 relative) on two calls in a row, and it must
-reject what it cannot serve without allocating.  Collected last on purpose.
+the other ILU(0) tests, 1e-10 relative) on two calls in a row, the
+library's own count of device allocations must not change across a call, and
+it must reject what it cannot serve without allocating.  Collected last on
+purpose.
 """
 import numpy as np
 import pytest
@@ -43,8 +45,12 @@ def test_noalloc_matches_ilu_apply_twice(ms, case):
             zref = torch.empty_like(r)
             ms.ms_ilu_apply(ctx, s, r, zref)           # also computes the factors on first use
             z = torch.full_like(r, float("nan"))
+            torch.cuda.synchronize()
+            before = ms.ms_allocation_stats()["allocations"]
             ms.ms_ilu_apply_noalloc(ctx, s, r, z)
             torch.cuda.synchronize()
+            # the property the entry point exists for: the library allocated nothing
+            assert ms.ms_allocation_stats()["allocations"] == before
             a, b = z.cpu().numpy(), zref.cpu().numpy()
             np.testing.assert_allclose(a, b, rtol=1e-10, atol=1e-12 * np.abs(b).max())
         # host arrays would need staging buffers: rejected
