@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--nz", type=int, default=85, help="--profile-ilu: layers of the 60x220 grid")
     ap.add_argument("--faulted", action="store_true",
                     help="--profile-ilu: the faulted 200x200x50 geomodel instead (segment sweeps)")
+    ap.add_argument("--profile-coarse-sweep", action="store_true",
+                    help="only form the FP64 and mixed Galerkin coarse operators of the 60x220x85 geomodel (their "
+                         "sweep inverses; for ncu captures)")
     ap.add_argument("--profile-coarse", action="store_true",
                     help="only form the finite-volume coarse operator of the 60x220x85 geomodel (Gauss-Jordan "
                          "inverse; for ncu captures)")
@@ -451,16 +454,24 @@ def run_ensemble(args, emit=True):
     clocks = sampler.stop()
     launches = ms.ms_profile_read()["_total_launches"]
     t_seq, _ = timed(1, 1)
-    # traced step for per-kernel durations
+    # traced step for per-kernel durations, on one worker so that a launch's
+    # events time that launch alone (with concurrent members they also time
+    # the others): the GPU time of each kernel family over the whole ensemble
     ms.ms_profile_reset()
     ms.ms_profile_enable(True)
-    step(args.workers)
+    step(1)
     torch.cuda.synchronize()
     ms.ms_profile_enable(False)
     prof = ms.ms_profile_read()
     prof.pop("_total_launches")
     kernels = {k: v for k, v in prof.items() if v["timed_launches"] > 0}
-    dom = max(kernels, key=lambda k: kernels[k]["total_ms"])
+    # the roofline of the batched smoothing (one persistent launch over every
+    # member), else of the kernel family with the most GPU time
+    dom = ("msrsb_batch32" if "msrsb_batch32" in kernels else
+           max(kernels, key=lambda k: kernels[k]["total_ms"]))
+    gpu_ms = sum(v["total_ms"] for v in kernels.values())
+    top = {k: {"launches": v["timed_launches"], "ms": round(v["total_ms"], 2)}
+           for k, v in sorted(kernels.items(), key=lambda kv: -kv[1]["total_ms"])[:12]}
     dk = kernels[dom]
     peak, peak_src = measured_peak()
     avg_ms = dk["total_ms"] / dk["timed_launches"]
@@ -484,7 +495,9 @@ def run_ensemble(args, emit=True):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs", "traffic": ncu_traffic(dom),
                      "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": avg_ms,
-                     "timing": "CUDA events around every launch of one traced step (concurrent members)"},
+                     "timing": "CUDA events around every launch of one traced step on one worker"},
+        "gpu_time": {"kernels_ms": gpu_ms, "top": top,
+                     "note": "summed device time of every launch of one step, members one after another"},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
@@ -684,6 +697,34 @@ def run_profile_ilu(args):
     return 0
 
 
+def run_profile_coarse_sweep(args):
+    """Galerkin coarse operators of the 60x220x85 geomodel in FP64 and mixed
+    precision: the coarse inverse by the FP64 sweep and by the tensor-core
+    sweep (untimed; for ncu captures)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2001_01624_gb300 as ms
+    from paper_2001_01624_gb300 import geomodel as G
+    dev = torch.device("cuda:0")
+    gm = G.config2(0)
+    stream = torch.cuda.Stream(dev)
+    ctx = ms.ms_create(0, stream)
+    s = ms.ms_system_create(ctx, gm.grid, 0)
+    with torch.cuda.stream(stream):
+        ms.ms_assemble_tpfa(ctx, s, torch.from_numpy(gm.perm.ravel().copy()).to(dev))
+        part, M = ms.ms_partition_cartesian(ctx, s, gm.block)
+        for prec in (ms.MS_PREC_FP64, ms.MS_PREC_MIXED):
+            b, _ = ms.ms_build_basis(ctx, s, part, M, block=gm.block, precision=prec, max_iter=20)
+            c = ms.ms_galerkin(ctx, s, b, prec)
+            ms.ms_coarse_release(c)
+            ms.ms_basis_release(b)
+    torch.cuda.synchronize()
+    ms.ms_system_release(s)
+    ms.ms_destroy(ctx)
+    return 0
+
+
 def run_profile_coarse(args):
     """The finite-volume coarse stage of the 60x220x85 geomodel alone (untimed)."""
     import torch
@@ -753,6 +794,8 @@ def main():
         return run_profile_ilu(args)
     if args.profile_coarse:
         return run_profile_coarse(args)
+    if args.profile_coarse_sweep:
+        return run_profile_coarse_sweep(args)
     if args.workload == "ensemble":
         return run_ensemble(args)
     if args.workload == "serving":
@@ -1036,7 +1079,8 @@ def main():
         ea = argparse.Namespace(**vars(args))
         ea.steps, ea.warmup, ea.no_e2e, ea.no_cpu_baseline = 2, 1, True, True
         el = run_ensemble(ea, emit=False)
-        line["ensemble"] = {k: el[k] for k in ("value", "unit", "ms_per_step", "sequential", "members", "roofline")}
+        line["ensemble"] = {k: el[k] for k in ("value", "unit", "ms_per_step", "sequential", "members", "roofline",
+                                                "gpu_time")}
         line["ensemble"]["config"] = el["config"]
         sa = argparse.Namespace(**vars(args))
         sa.requests = min(args.requests, 200)

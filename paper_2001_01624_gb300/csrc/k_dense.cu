@@ -224,8 +224,9 @@ __global__ void k_check_diag(const double *A, int M, int *err) {
 
 // y = A x, one warp per row.
 // y = A x, one warp per row: 16-byte loads of the row (after the one to three
-// elements that bring it to a 16-byte boundary) with four loads in flight per
+// elements that bring it to a 16-byte boundary) with kGemvU loads in flight per
 // lane, so the row streams instead of waiting on one load at a time.
+constexpr int kGemvU = 4;
 // MODE 0: y = A x; 1: acc = (double)(A x); 2: acc += (double)(A x).
 template <typename T, int MODE>
 __global__ void __launch_bounds__(128) k_gemv(const T *__restrict__ A, int M, const T *__restrict__ x,
@@ -243,18 +244,18 @@ __global__ void __launch_bounds__(128) k_gemv(const T *__restrict__ A, int M, co
     const int nv = (M - pre) / VW;
     const V *av = (const V *)(a + pre);
     const T *xp = x + pre;
-    for (int v0 = lane; v0 < nv; v0 += 128) {
-        V q[4];
+    for (int v0 = lane; v0 < nv; v0 += 32 * kGemvU) {
+        V q[kGemvU];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < kGemvU; ++u)
             if (v0 + 32 * u < nv) q[u] = __ldg(av + v0 + 32 * u);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kGemvU; ++u) {
             const int v = v0 + 32 * u;
             if (v < nv) {
                 const T *xv = xp + (int64_t)v * VW;
-                if constexpr (VW == 4) s[u] += q[u].x * xv[0] + q[u].y * xv[1] + q[u].z * xv[2] + q[u].w * xv[3];
-                else s[u] += q[u].x * xv[0] + q[u].y * xv[1];
+                if constexpr (VW == 4) s[u & 3] += q[u].x * xv[0] + q[u].y * xv[1] + q[u].z * xv[2] + q[u].w * xv[3];
+                else s[u & 3] += q[u].x * xv[0] + q[u].y * xv[1];
             }
         }
     }
@@ -282,17 +283,17 @@ __device__ __forceinline__ float gemv_row_cg(const float *__restrict__ A, int M,
     const int nv = (M - pre) / 4;
     const float4 *av = (const float4 *)(a + pre);
     const float *xp = x + pre;
-    for (int v0 = lane; v0 < nv; v0 += 128) {
-        float4 q[4];
+    for (int v0 = lane; v0 < nv; v0 += 32 * kGemvU) {
+        float4 q[kGemvU];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < kGemvU; ++u)
             if (v0 + 32 * u < nv) q[u] = __ldg(av + v0 + 32 * u);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kGemvU; ++u) {
             const int v = v0 + 32 * u;
             if (v < nv) {
                 const float *xs = xp + (int64_t)v * 4;
-                s[u] += q[u].x * __ldcg(&xs[0]) + q[u].y * __ldcg(&xs[1]) + q[u].z * __ldcg(&xs[2]) + q[u].w * __ldcg(&xs[3]);
+                s[u & 3] += q[u].x * __ldcg(&xs[0]) + q[u].y * __ldcg(&xs[1]) + q[u].z * __ldcg(&xs[2]) + q[u].w * __ldcg(&xs[3]);
             }
         }
     }

@@ -33,6 +33,8 @@
 
 #include <cstdlib>
 
+#include <string>
+
 #include "ms_internal.h"
 
 namespace msgb {
@@ -1032,10 +1034,30 @@ bool plan_fits(ms_system &s, const int dims[3], int TK, int NK, int NC) {
 }
 
 template <typename T, typename TR>
-bool plan_precision(ms_system &s, int p, const int dims[3]) {
+bool plan_precision(ms_system &s, int p, const int dims[3], bool sweep_only = false) {
     if (dims[0] > 256 || dims[1] < 1 || dims[2] < 1) return false;
     const LineShape ls = line_shape(dims[0], sizeof(T) == 4);
     const int warps = (dims[2] + ls.G - 1) / ls.G;
+    if (sweep_only) {
+        // a sweep layout only (the factorisation keeps its own): rows over
+        // several clusters of the default warps per CTA
+        const int tk = sizeof(T) == 8 ? kClusterTK64 : kClusterTK32;
+        const int NKtot = (warps + tk - 1) / tk;
+        const int NC = (NKtot + 15) / 16;
+        const int NK = (NKtot + NC - 1) / NC;
+        const int TK = (warps + NK * NC - 1) / (NK * NC);
+        if (TK > 16 || TK * ls.G > 32 || !plan_fits<T, TR>(s, dims, TK, NK, NC)) return false;
+        s.cl_TK[p] = TK;
+        s.cl_NK[p] = NK;
+        s.cl_NC[p] = NC;
+        if (NC > 1) {
+            s.cl_ring[p].alloc((size_t)(NC - 1) * dims[1] * (32 / ls.G) * ls.E * (sizeof(T) == 8 ? 2 : 1));
+            s.cl_ring[p].zero(nullptr);
+        }
+        s.cl_tick.alloc(2);
+        s.cl_tick.zero(nullptr);
+        return true;
+    }
     // one cluster over all rows (also the factorisation's layout)
     bool one = false;
     for (int C : {16, 8}) {
@@ -1075,18 +1097,35 @@ bool plan_precision(ms_system &s, int p, const int dims[3]) {
 
 }  // namespace
 
-// Sweep layouts: x-lines (critical path ny + nz - 1 line steps), or, for FP32
-// with MSGB_ILU_LINES=y, y-lines on transposed vectors when ny > nx (critical
-// path nx + nz - 1).  x-lines are the default: with 8 cells per lane the
-// lanes' 128-byte strided reads of a y-line's packed coefficients serialise on
-// one shared-memory bank group, and the 60x220x85 FP32 sweep measured
-// 0.23 ms on y-lines against 0.19 ms on x-lines (2 cells per lane).
+// Sweep layouts: x-lines (critical path ny + nz - 1 line steps) or y-lines on
+// transposed vectors (critical path nx + nz - 1, 8 cells per lane when
+// ny > 128).  FP32 takes y-lines when ny > nx: on the 60x220x85 benchmark grid
+// its sweeps take 0.12 ms against 0.175 ms on x-lines.  FP64 keeps x-lines:
+// a y-line step's offset scan is about 3 E + 4 dependent FP64 instructions
+// per lane, and at this part's FP64 rate the longer steps cost more than the
+// fewer steps save (0.41 against 0.32 ms).  MSGB_ILU_LINES=x keeps FP32 on
+// x-lines, =yy puts both precisions on y-lines.
 void plan_ilu_cluster(ms_system &s) {
     const char *e = std::getenv("MSGB_ILU_LINES");
-    const bool want_y = e && e[0] == 'y';
+    const std::string lines_env = e ? std::string(e) : std::string();
+    const bool want_y = lines_env != "x";                            // FP32 sweeps on y-lines
+    const bool want_y64 = lines_env == "y64" || lines_env == "yy";  // FP64 sweeps on y-lines
     int d[3] = {s.nx, s.ny, s.nz};
     s.cl_T[0] = false;
-    s.cl_ok[0] = plan_precision<double, double>(s, 0, d);
+    s.cl_ok[0] = plan_precision<double, double>(s, 0, d);   // also the factorisation's layout
+    if (want_y64 && s.cl_ok[0] && s.ny > s.nx && s.ny <= 256) {
+        const int fTK = s.cl_fTK[0], fNK = s.cl_fNK[0];
+        int dt[3] = {s.ny, s.nx, s.nz};
+        if (plan_precision<double, double>(s, 0, dt, true)) {
+            s.cl_T[0] = true;
+            s.w_T64.alloc(s.n);
+            s.w_T64b.alloc(s.n);
+        } else {
+            s.cl_ok[0] = plan_precision<double, double>(s, 0, d);
+        }
+        s.cl_fTK[0] = fTK;   // the factorisation runs on x-lines
+        s.cl_fNK[0] = fNK;
+    }
     s.cl_T[1] = want_y && s.ny > s.nx && s.ny <= 256;
     if (s.cl_T[1]) {
         int dt[3] = {s.ny, s.nx, s.nz};

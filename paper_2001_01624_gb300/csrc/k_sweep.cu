@@ -503,7 +503,7 @@ void dense_sweep_inverse32(ms_coarse &c, int *err, cudaStream_t st) {
     c.work64.alloc(M);
     c.inv32.alloc((int64_t)M * M);
     sw_bar(c, st);
-    const int G = sw_blocks(nT * (nT + 1) / 2);
+    const int G = sw_blocks(1 << 30);   // one block per SM: the W rows of a step spread over all of them
     const size_t smem = 4 * (size_t)kTcOpBytes + (size_t)(kSwNB + 1) * (kSwNB + 1) * sizeof(float);
     static size_t cur = 0;
     MS_CUDA(raise_smem_limit(k_sweep_tc, smem, cur));
