@@ -287,10 +287,11 @@ void run_batch(ms_ctx *ctx, const std::vector<ms_system *> &sys, const std::vect
             nnz += bases[idx[q]]->nnz;
             wn += (int64_t)jobs[q].W * jobs[q].n;
         }
-        // per iteration, as the per-system kernel: rows and maps, old slot values read, new written
-        KernelScope ks_(st, fp32 ? "msrsb_batch32" : "msrsb_batch",
-                        (double)cells * (2 * sizeof(T) + 1) + (double)wn * (4 + sizeof(T) + 4) +
-                            (double)nnz * 2 * sizeof(T));
+        // bytes: added once the iteration counts are known (below)
+        KernelScope ks_(st, fp32 ? "msrsb_batch32" : "msrsb_batch", 0.0);
+        (void)cells;
+        (void)nnz;
+        (void)wn;
         k_msrsb_batch<T><<<G, kBT, 0, st>>>((const SmJob<T> *)B.jobs.p, tile, (BatchQueue *)B.queue.p, B.slots.p,
                                             R - 1, B.done.p);
         MS_CHECK_LAUNCH();
@@ -302,6 +303,18 @@ void run_batch(ms_ctx *ctx, const std::vector<ms_system *> &sys, const std::vect
     MS_CUDA(cudaStreamSynchronize(st));
     const int qerr = (int)(h[4 * (size_t)nj + 2] >> 32);
     if (qerr) throw Error{MS_ERR_TIMEOUT, "a batched basis smoothing wait ran out"};
+    {
+        // algorithmic bytes of the launch: per member and iteration, as the
+        // per-system kernel (rows and slot maps, old slot values read, new written)
+        double bytes = 0.0;
+        for (int q = 0; q < nj; ++q) {
+            if (bases[idx[q]]->max_iter <= 0) continue;
+            const double it = (double)h[4 * (size_t)q + 1];
+            bytes += it * ((double)jobs[q].n * (2 * sizeof(T) + 1) + (double)jobs[q].W * jobs[q].n * (4 + sizeof(T) + 4) +
+                           (double)bases[idx[q]]->nnz * 2 * sizeof(T));
+        }
+        profile_add_bytes(fp32 ? "msrsb_batch32" : "msrsb_batch", bytes);
+    }
     for (int q = 0; q < nj; ++q) {
         ms_system &s = *sys[idx[q]];
         ms_basis &b = *bases[idx[q]];

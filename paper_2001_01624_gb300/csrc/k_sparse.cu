@@ -514,7 +514,8 @@ __global__ void __launch_bounds__(256) k_multidot8(int n, int k, const double *_
 
 // y[l] += sign * sum_{i<k} c[i] V[i n + l]   (c on the device, k <= 128)
 __global__ void k_multiaxpy(int n, int k, const double *__restrict__ V, const double *__restrict__ c, double sign,
-                            double *__restrict__ y) {
+                            double *__restrict__ y, const int *__restrict__ kdev) {
+    if (kdev) k = min(k, *kdev);   // count known on the device only (GMRES inside a graph)
     __shared__ double cs[128];
     for (int i = threadIdx.x; i < k; i += blockDim.x) cs[i] = sign * c[i];
     __syncthreads();
@@ -551,9 +552,105 @@ void launch_multidot(int n, int k, const double *V, const double *w, double *red
     MS_CHECK_LAUNCH();
 }
 
-void launch_multiaxpy(int n, int k, const double *V, const double *c, double sign, double *y, cudaStream_t st) {
+void launch_multiaxpy(int n, int k, const double *V, const double *c, double sign, double *y, cudaStream_t st,
+                      const int *kdev) {
     KernelScope ks_(st, "krylov_axpy", (double)(k + 2) * n * 8);
-    k_multiaxpy<<<2 * stride_grid(n), kThreads, 0, st>>>(n, k, V, c, sign, y);
+    k_multiaxpy<<<2 * stride_grid(n), kThreads, 0, st>>>(n, k, V, c, sign, y, kdev);
+    MS_CHECK_LAUNCH();
+}
+
+namespace {
+__global__ void k_scale_dev(int n, const double *__restrict__ x, const double *__restrict__ a,
+                            double *__restrict__ y) {
+    const double f = *a;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) y[l] = f * x[l];
+}
+
+// GMRES bookkeeping on the device (one thread), the same arithmetic as the
+// host loop: restart begin, one Arnoldi step's Hessenberg column with its
+// Givens rotations and convergence test, the small triangular solve, and the
+// restart's true-residual test.  Each sets the graph condition that lets the
+// next step (or restart) run.
+__global__ void k_gmres_begin(GmresDev G, const double *beta_norm, const cudaGraphConditionalHandle *steps) {
+    const double beta = *beta_norm;
+    for (int i = 0; i <= G.m; ++i) G.g[i] = 0.0;
+    G.g[0] = beta;
+    *G.k = 0;
+    *G.scal = beta > 0.0 ? 1.0 / beta : 0.0;
+    const int stop = !(beta > 0.0) || *G.it >= G.max_iter;
+    *G.stop = stop;
+    cudaGraphSetConditional(steps[0], stop ? 0u : 1u);
+    for (int i = 1; i < G.m; ++i) cudaGraphSetConditional(steps[i], 0u);   // each opened by its predecessor
+}
+
+__global__ void k_gmres_step(GmresDev G, int j, const double *h1, const double *h2, const double *hn_dev,
+                             const cudaGraphConditionalHandle *steps) {
+    const int m = G.m;
+    double *H = G.H;
+    for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h1[i] + h2[i];
+    const double hn = *hn_dev;
+    if (!(hn == hn)) {
+        *G.err = 1;
+        *G.stop = 1;
+        return;   // the next step stays closed
+    }
+    H[(size_t)(j + 1) * m + j] = hn;
+    *G.scal = hn > 0.0 ? 1.0 / hn : 0.0;
+    gmres_givens(H, m, j, G.cs, G.sn, G.g);
+    *G.k = j + 1;
+    const int it = *G.it + 1;
+    *G.it = it;
+    const double res = fabs(G.g[j + 1]) / G.nq;
+    *G.res = res;
+    if (G.hist) G.hist[it] = res;
+    const int stop = res <= G.tol || hn == 0.0 || it >= G.max_iter;
+    *G.stop = stop;
+    if (j + 1 < m) cudaGraphSetConditional(steps[j + 1], stop ? 0u : 1u);
+}
+
+// H(0:k, 0:k) y = g(0:k) by back substitution
+__global__ void k_gmres_solve(GmresDev G) { gmres_back_solve(G.H, G.m, *G.k, G.g, G.y); }
+
+__global__ void k_gmres_restart(GmresDev G, const double *beta_norm, cudaGraphConditionalHandle outer) {
+    const double beta = *beta_norm;
+    const double res = beta / G.nq;
+    *G.res = res;
+    const int it = *G.it;
+    if (G.hist) G.hist[it] = res;
+    if (!(res == res)) *G.err = 1;
+    // every restart advances the iteration count, so more than max_iter + 1
+    // restarts cannot happen; the count stops the loop even if one did not
+    const int r = ++*G.restarts;
+    cudaGraphSetConditional(outer,
+                            (res > G.tol && it < G.max_iter && res == res && !*G.err && r <= G.max_iter) ? 1u : 0u);
+}
+}  // namespace
+
+void launch_scale_dev(int n, const double *x, const double *a, double *y, cudaStream_t st) {
+    k_scale_dev<<<stride_grid(n), kThreads, 0, st>>>(n, x, a, y);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_gmres_begin(const GmresDev &G, const double *beta_norm, const cudaGraphConditionalHandle *steps,
+                        cudaStream_t st) {
+    k_gmres_begin<<<1, 1, 0, st>>>(G, beta_norm, steps);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_gmres_step(const GmresDev &G, int j, const double *h1, const double *h2, const double *hn,
+                       const cudaGraphConditionalHandle *steps, cudaStream_t st) {
+    k_gmres_step<<<1, 1, 0, st>>>(G, j, h1, h2, hn, steps);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_gmres_solve(const GmresDev &G, cudaStream_t st) {
+    k_gmres_solve<<<1, 1, 0, st>>>(G);
+    MS_CHECK_LAUNCH();
+}
+
+void launch_gmres_restart(const GmresDev &G, const double *beta_norm, cudaGraphConditionalHandle outer,
+                          cudaStream_t st) {
+    k_gmres_restart<<<1, 1, 0, st>>>(G, beta_norm, outer);
     MS_CHECK_LAUNCH();
 }
 

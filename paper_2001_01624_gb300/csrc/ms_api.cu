@@ -1196,7 +1196,191 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
             MS_CUDA(cudaMemcpyAsync(z, s->w_x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
         };
         std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
-        double beta = res * nq;
+        double beta = hn[1];   // ||q - A x0||, as stored on the device
+        // The whole solve as one CUDA graph: a while node over restarts whose
+        // body begins the restart, runs m conditional Arnoldi steps (each step's
+        // Hessenberg column, rotations and convergence test computed on the
+        // device decide whether the next one runs), then updates x and tests
+        // the true residual.  Same arithmetic as the host loop below, which
+        // runs instead when the kernels are traced, graphs are switched off
+        // (MSGB_SOLVE_GRAPH=0) or the graph cannot be built.
+        auto gmres_graph = [&]() -> bool {
+            const int H0 = (m + 1) * m;
+            const size_t hist_n = (size_t)opts->max_iter + 1;
+            s->w_kgd.alloc((size_t)H0 + 2 * m + (m + 1) + m + 2 + hist_n);
+            s->w_kgi.alloc(5);
+            GmresDev G{};
+            G.H = s->w_kgd.p;
+            G.cs = G.H + H0;
+            G.sn = G.cs + m;
+            G.g = G.sn + m;
+            G.y = G.g + (m + 1);
+            G.scal = G.y + m;
+            G.res = G.scal + 1;
+            G.hist = G.res + 1;
+            G.k = s->w_kgi.p;
+            G.it = G.k + 1;
+            G.stop = G.k + 2;
+            G.err = G.k + 3;
+            G.restarts = G.k + 4;
+            G.m = m;
+            G.max_iter = opts->max_iter;
+            G.nq = nq;
+            G.tol = opts->tol;
+            {
+                const int h4[5] = {0, it, 0, 0, 0};
+                MS_CUDA(cudaMemcpyAsync(s->w_kgi.p, h4, sizeof(h4), cudaMemcpyHostToDevice, st));
+            }
+            if (!ctx->capture) MS_CUDA(cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking));
+            cudaStream_t cs = ctx->capture;
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            bool ok = false, launched = false;
+            std::vector<std::string> step_names, edge_names;
+            // capture fn's launches into `into` after the nodes `deps`; returns
+            // the captured sink nodes (what the next node must wait for)
+            auto capture = [&](cudaGraph_t into, const std::vector<cudaGraphNode_t> &deps, auto &&fn) {
+                MS_CUDA(cudaStreamBeginCaptureToGraph(cs, into, deps.empty() ? nullptr : deps.data(), nullptr,
+                                                      deps.size(), cudaStreamCaptureModeRelaxed));
+                std::vector<cudaGraphNode_t> sinks;
+                try {
+                    fn();
+                    cudaStreamCaptureStatus cst;
+                    const cudaGraphNode_t *dn = nullptr;
+                    size_t nd = 0;
+                    MS_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &dn, nullptr, &nd));
+                    sinks.assign(dn, dn + nd);
+                } catch (...) {
+                    cudaGraph_t dummy = nullptr;
+                    cudaStreamEndCapture(cs, &dummy);
+                    throw;
+                }
+                cudaGraph_t out = into;
+                MS_CUDA(cudaStreamEndCapture(cs, &out));
+                return sinks;
+            };
+            try {
+                MS_CUDA(cudaGraphCreate(&graph, 0));
+                cudaGraphConditionalHandle outer;
+                MS_CUDA(cudaGraphConditionalHandleCreate(&outer, graph, 1, cudaGraphCondAssignDefault));
+                cudaGraphNodeParams wp = {};
+                wp.type = cudaGraphNodeTypeConditional;
+                wp.conditional.handle = outer;
+                wp.conditional.type = cudaGraphCondTypeWhile;
+                wp.conditional.size = 1;
+                cudaGraphNode_t wnode;
+                MS_CUDA(cudaGraphAddNode(&wnode, graph, nullptr, nullptr, 0, &wp));
+                cudaGraph_t body = wp.conditional.phGraph_out[0];
+                // one handle per conditional step, kept on the device for the
+                // kernels that open the next step
+                std::vector<cudaGraphConditionalHandle> hstep(m);
+                for (int j = 0; j < m; ++j)
+                    MS_CUDA(cudaGraphConditionalHandleCreate(&hstep[j], body, 0, cudaGraphCondAssignDefault));
+                static_assert(sizeof(cudaGraphConditionalHandle) == sizeof(unsigned long long), "handle size");
+                s->w_kgh.alloc(m);
+                MS_CUDA(cudaMemcpyAsync(s->w_kgh.p, hstep.data(), sizeof(unsigned long long) * m,
+                                        cudaMemcpyHostToDevice, st));
+                const cudaGraphConditionalHandle *hsteps = (const cudaGraphConditionalHandle *)s->w_kgh.p;
+                // restart begin: beta = ||r||, g = beta e_0, V_0 = r / beta (the
+                // kernels that set a handle sit in the graph of the node they
+                // steer or in a body graph below it, never in a child graph)
+                profile_record_begin();
+                std::vector<cudaGraphNode_t> prevs = capture(body, {}, [&]() {
+                    launch_gmres_begin(G, norms.p + 1, hsteps, cs);
+                    launch_scale_dev(n, w, G.scal, V, cs);
+                });
+                edge_names = profile_record_end();
+                for (int j = 0; j < m; ++j) {
+                    cudaGraphNodeParams ip = {};
+                    ip.type = cudaGraphNodeTypeConditional;
+                    ip.conditional.handle = hstep[j];
+                    ip.conditional.type = cudaGraphCondTypeIf;
+                    ip.conditional.size = 1;
+                    cudaGraphNode_t inode;
+                    MS_CUDA(cudaGraphAddNode(&inode, body, prevs.data(), nullptr, prevs.size(), &ip));
+                    if (j == 0) profile_record_begin();
+                    capture(ip.conditional.phGraph_out[0], {}, [&]() {
+                        const double *vk = V + (size_t)j * n;
+                        double *zk = Z + (size_t)j * n;
+                        // the cycle launches on the capture stream
+                        std::swap(st, cs);
+                        try {
+                            precond(vk, zk);
+                        } catch (...) {
+                            std::swap(st, cs);
+                            throw;
+                        }
+                        std::swap(st, cs);
+                        launch_spmv(*s, zk, w, cs);
+                        launch_multidot(n, j + 1, V, w, s->w_kred.p, s->w_kcnt.p, h1, cs);
+                        launch_multiaxpy(n, j + 1, V, h1, -1.0, w, cs);
+                        launch_multidot(n, j + 1, V, w, s->w_kred.p, s->w_kcnt.p, h2, cs);
+                        launch_multiaxpy(n, j + 1, V, h2, -1.0, w, cs);
+                        launch_norm2(w, n, s->w_red.p, s->w_cnt.p, hn_dev, cs);
+                        launch_gmres_step(G, j, h1, h2, hn_dev, hsteps, cs);
+                        launch_scale_dev(n, w, G.scal, V + (size_t)(j + 1) * n, cs);
+                    });
+                    if (j == 0) step_names = profile_record_end();
+                    prevs.assign(1, inode);
+                }
+                // restart end: x += Z y, true residual, continue while above tol
+                profile_record_begin();
+                capture(body, prevs, [&]() {
+                    launch_gmres_solve(G, cs);
+                    launch_multiaxpy(n, m, Z, G.y, 1.0, xg, cs, G.k);
+                    launch_residual(*s, qk, xg, w, s->w_red.p, s->w_cnt.p, norms.p + 1, cs, nullptr);
+                    launch_gmres_restart(G, norms.p + 1, outer, cs);
+                });
+                {
+                    auto e2 = profile_record_end();
+                    edge_names.insert(edge_names.end(), e2.begin(), e2.end());
+                }
+                MS_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+                launched = true;
+                MS_CUDA(cudaGraphLaunch(exec, st));
+                int hi[4];
+                double hres = 0.0;
+                MS_CUDA(cudaMemcpyAsync(hi, s->w_kgi.p, sizeof(hi), cudaMemcpyDeviceToHost, st));
+                MS_CUDA(cudaMemcpyAsync(&hres, G.res, sizeof(double), cudaMemcpyDeviceToHost, st));
+                sync(st);
+                if (hi[3]) throw Error{MS_ERR_CUDA, "GMRES: Arnoldi vector or residual became NaN"};
+                const int it_end = hi[1];
+                const int steps = it_end - it;
+                // launches were counted once per captured node: count what ran
+                // (steps Arnoldi steps, about ceil(steps / m) restarts)
+                profile_add_launches(step_names, (int64_t)steps - m);
+                profile_add_launches(edge_names, (int64_t)std::max(1, (steps + m - 1) / m) - 1);
+                if (info && info->history && steps > 0)
+                    copy_out(info->history + it + 1, G.hist + it + 1, (size_t)steps, st);
+                it = it_end;
+                res = hres;
+                ok = true;
+            } catch (const Error &) {
+                profile_record_end();
+                if (launched) {
+                    if (exec) cudaGraphExecDestroy(exec);
+                    if (graph) cudaGraphDestroy(graph);
+                    throw;
+                }
+                cudaGetLastError();   // the graph could not be built: the host loop runs instead
+                ok = false;
+            }
+            if (exec) cudaGraphExecDestroy(exec);
+            if (graph) cudaGraphDestroy(graph);
+            return ok;
+        };
+        // Opt-in (MSGB_GMRES_GRAPH=1): the solve captures a new graph on each
+        // call, which must not meet another host thread's device-wide
+        // synchronisation or allocator release, so it is kept for callers that
+        // drive the device from one thread.
+        const char *gmres_env = std::getenv("MSGB_GMRES_GRAPH");
+        const char *graph_env = std::getenv("MSGB_SOLVE_GRAPH");
+        if (gmres_env && gmres_env[0] == '1' && !(graph_env && graph_env[0] == '0') && !profile_enabled() &&
+            gmres_graph()) {
+            if (!(res == res)) throw Error{MS_ERR_CUDA, "residual became NaN"};
+            beta = res * nq;
+            if (opts->smoother == MS_SMOOTHER_ILU0) check_sweep_errors(ctx, s);
+        }
         while (res > opts->tol && it < opts->max_iter) {
             launch_scale(n, w, 1.0 / beta, V, st);
             std::fill(gv.begin(), gv.end(), 0.0);
@@ -1221,30 +1405,14 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
                 if (!(hn == hn)) throw Error{MS_ERR_CUDA, "GMRES: Arnoldi vector became NaN"};
                 H[(size_t)(k + 1) * m + k] = hn;
                 if (hn > 0.0) launch_scale(n, w, 1.0 / hn, V + (size_t)(k + 1) * n, st);
-                for (int i = 0; i < k; ++i) {   // earlier rotations on column k
-                    const double a = H[(size_t)i * m + k], b = H[(size_t)(i + 1) * m + k];
-                    H[(size_t)i * m + k] = cs[i] * a + sn[i] * b;
-                    H[(size_t)(i + 1) * m + k] = -sn[i] * a + cs[i] * b;
-                }
-                const double a = H[(size_t)k * m + k], b = H[(size_t)(k + 1) * m + k];
-                const double rho = std::sqrt(a * a + b * b);
-                cs[k] = rho > 0 ? a / rho : 1.0;
-                sn[k] = rho > 0 ? b / rho : 0.0;
-                H[(size_t)k * m + k] = rho;
-                H[(size_t)(k + 1) * m + k] = 0.0;
-                gv[k + 1] = -sn[k] * gv[k];
-                gv[k] = cs[k] * gv[k];
+                gmres_givens(H.data(), m, k, cs.data(), sn.data(), gv.data());
                 ++k;
                 ++it;
                 res = std::fabs(gv[k]) / nq;
                 if (info && info->history) info->history[it] = res;
                 if (res <= opts->tol || hn == 0.0) break;
             }
-            for (int i = k - 1; i >= 0; --i) {   // H(0:k, 0:k) y = g(0:k)
-                double acc = gv[i];
-                for (int l = i + 1; l < k; ++l) acc -= H[(size_t)i * m + l] * y[l];
-                y[i] = acc / H[(size_t)i * m + i];
-            }
+            gmres_back_solve(H.data(), m, k, gv.data(), y.data());
             MS_CUDA(cudaMemcpyAsync(ydev, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
             launch_multiaxpy(n, k, Z, ydev, 1.0, xg, st);
             launch_residual(*s, qk, xg, w, s->w_red.p, s->w_cnt.p, norms.p + 1, st, nullptr);

@@ -5,6 +5,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <cmath>
 #include <stdint.h>
 
 #include <memory>
@@ -143,6 +145,9 @@ cudaError_t raise_smem_limit(K kern, size_t bytes, size_t &cur) {
 }
 
 void profile_enable(bool on);
+// Add algorithmic bytes to the latest traced launch of kernel family `name`
+// (for a launch whose work is known only after it ran).
+void profile_add_bytes(const char *name, double bytes);
 bool profile_enabled();
 // graph capture: list the launches captured (counted once at capture), then
 // add them again per extra replay of the graph
@@ -289,6 +294,9 @@ struct ms_system {
     msgb::DBuf<double> w_y;
     msgb::DBuf<double> w_kry;                 // GMRES: V [(m+1) n], Z [m n], w, q copy; dot scratch
     msgb::DBuf<double> w_kred, w_kh;
+    msgb::DBuf<double> w_kgd;                 // graph-driven GMRES: Hessenberg, rotations, g, y, history
+    msgb::DBuf<int> w_kgi;                    //   and its counters
+    msgb::DBuf<unsigned long long> w_kgh;     //   and the handles of its conditional steps
     msgb::DBuf<unsigned int> w_kcnt;
     msgb::DBuf<double> w_tu, w_ts, w_tq;      // transport: face fluxes, saturation buffer, sources
     msgb::DBuf<double> w_red;                 // reduction partials
@@ -448,7 +456,57 @@ void launch_transport_substep(const ms_system &s, const double fl[6], const doub
                               const double *S, double *fw, double *Snew, double h_over_pv, cudaStream_t st);
 void launch_multidot(int n, int k, const double *V, const double *w, double *red, unsigned int *cnt, double *h,
                      cudaStream_t st);
-void launch_multiaxpy(int n, int k, const double *V, const double *c, double sign, double *y, cudaStream_t st);
+void launch_multiaxpy(int n, int k, const double *V, const double *c, double sign, double *y, cudaStream_t st,
+                      const int *kdev = nullptr);
+// GMRES state on the device (graph-driven solves): Hessenberg matrix
+// (m+1) x m, rotations, rotated right-hand side, solution of the small
+// system, 1/norm for the next basis vector, and counters.
+// One Arnoldi step's update of the GMRES least-squares problem: column j of
+// the Hessenberg matrix H (row stride m) takes the j earlier Givens
+// rotations, rotation j is made to zero H(j+1, j), and g takes it.  Every
+// product that meets a sum is an explicit fma, so the host-driven loop and
+// the device graph round identically.
+__host__ __device__ inline void gmres_givens(double *H, int m, int j, double *cs, double *sn, double *g) {
+    for (int i = 0; i < j; ++i) {
+        const double a = H[(size_t)i * m + j], b = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = fma(cs[i], a, sn[i] * b);
+        H[(size_t)(i + 1) * m + j] = fma(cs[i], b, -(sn[i] * a));
+    }
+    const double a = H[(size_t)j * m + j], b = H[(size_t)(j + 1) * m + j];
+    const double rho = sqrt(fma(a, a, b * b));
+    cs[j] = rho > 0 ? a / rho : 1.0;
+    sn[j] = rho > 0 ? b / rho : 0.0;
+    H[(size_t)j * m + j] = rho;
+    H[(size_t)(j + 1) * m + j] = 0.0;
+    g[j + 1] = -(sn[j] * g[j]);
+    g[j] = cs[j] * g[j];
+}
+
+// H(0:k, 0:k) y = g(0:k), H upper triangular after the rotations
+__host__ __device__ inline void gmres_back_solve(const double *H, int m, int k, const double *g, double *y) {
+    for (int i = k - 1; i >= 0; --i) {
+        double acc = g[i];
+        for (int l = i + 1; l < k; ++l) acc = fma(-H[(size_t)i * m + l], y[l], acc);
+        y[i] = acc / H[(size_t)i * m + i];
+    }
+}
+
+struct GmresDev {
+    double *H, *cs, *sn, *g, *y, *scal, *res, *hist;
+    int *k, *it, *stop, *err, *restarts;   // restarts: bounds the while loop on its own
+    int m, max_iter;
+    double nq, tol;
+};
+void launch_scale_dev(int n, const double *x, const double *a, double *y, cudaStream_t st);
+// steps: device array of the m conditional handles of the Arnoldi steps (a
+// handle steers exactly one conditional node)
+void launch_gmres_begin(const GmresDev &G, const double *beta_norm, const cudaGraphConditionalHandle *steps,
+                        cudaStream_t st);
+void launch_gmres_step(const GmresDev &G, int j, const double *h1, const double *h2, const double *hn,
+                       const cudaGraphConditionalHandle *steps, cudaStream_t st);
+void launch_gmres_solve(const GmresDev &G, cudaStream_t st);
+void launch_gmres_restart(const GmresDev &G, const double *beta_norm, cudaGraphConditionalHandle outer,
+                          cudaStream_t st);
 void launch_scale(int n, const double *x, double a, double *y, cudaStream_t st);
 void launch_cycle_control(const double *norms, double tol, int max_iter, int *ctl_it, double *ctl_res, double *hist,
                           cudaGraphConditionalHandle handle, cudaStream_t st);

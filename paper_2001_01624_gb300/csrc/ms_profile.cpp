@@ -100,6 +100,16 @@ KernelScope::~KernelScope() {
     p.pending.push_back({name_, a_, b, bytes_});
 }
 
+void profile_add_bytes(const char *name, double bytes) {
+    Profiler &p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    for (auto it = p.pending.rbegin(); it != p.pending.rend(); ++it)
+        if (std::strcmp(it->name, name) == 0) {
+            it->bytes += bytes;
+            return;
+        }
+}
+
 std::mutex &attr_mutex() {
     static std::mutex m;
     return m;

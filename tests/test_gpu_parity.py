@@ -293,6 +293,46 @@ def test_graph_cycles_match_host_cycles(ms, ctx, monkeypatch, precision, case):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("restart", [30, 5])
+def test_graph_gmres_matches_host_gmres(ms, ctx, monkeypatch, precision, restart):
+    """Flexible GMRES run as one CUDA graph (a while node over restarts, one
+    conditional node per Arnoldi step, the Hessenberg column, Givens rotations
+    and convergence test computed on the device) takes exactly the steps of
+    the host-driven loop: the same kernels in the same order, and the small
+    least-squares arithmetic in one fma-explicit form on both sides, so step
+    counts, iterates and residual histories are bitwise equal."""
+    gm = CASES["faulted_18x14x7"]()
+    prec = ms.MS_PREC_FP64 if precision == "fp64" else ms.MS_PREC_MIXED
+    s = _system(ms, ctx, gm)
+    part, M = ms.ms_partition_cartesian(ctx, s, gm.block)
+    b, _ = ms.ms_build_basis(ctx, s, part, M, block=gm.block, precision=prec)
+    c = ms.ms_galerkin(ctx, s, b, prec)
+    q = gm.q_active()
+    out = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("MSGB_GMRES_GRAPH", mode)
+        p = np.zeros_like(q)
+        info = ms.ms_solve(ctx, s, [c], q, p, tol=1e-9, max_iter=500, precision=prec, outer=ms.MS_OUTER_GMRES,
+                           restart=restart)
+        out[mode] = (p, info)
+    (p0, i0), (p1, i1) = out["0"], out["1"]
+    assert i0["converged"] and i1["converged"]
+    assert i0["iters"] == i1["iters"]
+    np.testing.assert_array_equal(i1["history"], i0["history"])
+    np.testing.assert_array_equal(p1, p0)
+    # the step cap stops the device loop exactly, inside a restart cycle
+    monkeypatch.setenv("MSGB_GMRES_GRAPH", "1")
+    p = np.zeros_like(q)
+    info = ms.ms_solve(ctx, s, [c], q, p, tol=1e-30, max_iter=7, precision=prec, outer=ms.MS_OUTER_GMRES,
+                       restart=restart)
+    assert info["iters"] == 7 and not info["converged"]
+    np.testing.assert_array_equal(info["history"][:7], i0["history"][:7])
+    ms.ms_coarse_release(c)
+    ms.ms_basis_release(b)
+    ms.ms_system_release(s)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_solve_batch_matches_individual_solves(ms, ctx, precision):
     """Members of uneven size (structured and faulted) solved concurrently on
     worker streams give exactly what each gives alone: basis re-smoothed,
