@@ -250,6 +250,11 @@ struct ms_system {
     int cl_fTK[2] = {0, 0}, cl_fNK[2] = {0, 0};   // single-cluster layout (factorisation)
     msgb::DBuf<unsigned long long> cl_tick;   // cluster tickets per precision
     msgb::DBuf<unsigned long long> cl_ring[2];  // lines crossing cluster boundaries (tagged words)
+    // segmented line sweeps (lines cut into 64-cell segments, one warp each)
+    bool sg_ok[2] = {false, false};
+    int sg_S[2] = {1, 1}, sg_TK[2] = {0, 0}, sg_NK[2] = {0, 0}, sg_NC[2] = {1, 1};
+    msgb::DBuf<unsigned long long> sg_tick;   // cluster tickets per precision
+    msgb::DBuf<unsigned long long> sg_ring[2];
     msgb::DBuf<double> coef4_64;              // [2][n][4]: (Lx, Ly, Lz, 0), (Ux/d, Uy/d, Uz/d, 1/d) per cell, d = U_ii
     msgb::DBuf<float> coef4_32;
     msgb::DBuf<double> scan_64;               // [2][lines][levels][32]: scan multipliers of each FP64 sweep line
@@ -532,6 +537,14 @@ void launch_ilu_tiled64(ms_system &s, const double *r, double *y, double *z, cud
 void launch_ilu_tiled32(ms_system &s, const double *r, float *y, float *z, cudaStream_t st);
 void launch_ilu_tiled32f(ms_system &s, const float *r, float *y, float *z, cudaStream_t st);
 void plan_ilu_cluster(ms_system &s);
+// segmented line sweeps (k_ilu_seg.cu): layout, FP64 scan tables, the two sweeps
+bool plan_ilu_seg(ms_system &s, int p);
+size_t seg_table_size(const ms_system &s);
+void pack_seg_tables(ms_system &s, const double *coef4, double *table, cudaStream_t st);
+template <typename T, typename TR>
+void seg_fwd(ms_system &s, int p, const T *coef4, const T *scanm, const TR *rhs, T *out, cudaStream_t st);
+template <typename T>
+void seg_bwd(ms_system &s, int p, const T *coef4, const T *scanm, const T *rhs, T *out, cudaStream_t st);
 bool launch_ilu_factor_cluster(ms_system &s, cudaStream_t st);
 void launch_ilu_pack_coef4(ms_system &s, bool fp32, cudaStream_t st);
 void launch_ilu_cluster64(ms_system &s, const double *r, double *y, double *z, cudaStream_t st);

@@ -533,22 +533,33 @@ def test_tiled_ilu_sweeps_across_tiles(ms, ctx, monkeypatch, kernel, tile, shape
     _check_ilu_sweeps(ms, ctx, G.lognormal_box(*shape, seed=31, block=(3, 4, 2), kz_ratio=0.1))
 
 
+@pytest.mark.parametrize("kern", ["seg", "cluster"])
 @pytest.mark.parametrize("tk", ["", "3", "1"])
 @pytest.mark.parametrize("lines", ["y", "x"])
 @pytest.mark.parametrize("shape", [(9, 13, 1), (9, 13, 7), (70, 6, 17), (33, 20, 40), (200, 5, 11),
                                    (60, 9, 85), (12, 4, 200), (256, 3, 5), (20, 60, 17), (7, 256, 9),
-                                   (13, 100, 33)])
-def test_cluster_ilu_sweeps(ms, ctx, monkeypatch, shape, lines, tk):
+                                   (13, 100, 33), (129, 5, 6)])
+def test_cluster_ilu_sweeps(ms, ctx, monkeypatch, shape, lines, tk, kern):
     """Line scans pipelined across thread-block clusters: k-rows split over up
-    to 16 CTAs per cluster (rows per CTA from 1 to 13, ragged last CTA), 2, 4
-    and 8 cells per lane, one-layer and single-CTA grids; FP32 sweeps on
-    y-lines of transposed vectors where ny > nx (y) or on x-lines.  With few
-    warps per CTA (tk) the rows span several clusters, which hand lines over
-    through the global ring in ticket order (up to 13 clusters)."""
+    to 16 CTAs per cluster (rows per CTA from 1 to 13, ragged last CTA), on
+    y-lines of transposed vectors (y) or on x-lines, one-layer and single-CTA
+    grids.  With few rows per CTA (tk) the rows span several clusters, which
+    hand lines over through the global ring in ticket order (up to 13
+    clusters).  seg: lines cut into 1 to 4 segments of 64 cells (full,
+    ragged and single-cell last segments), one warp each, passing the value
+    that leaves a segment to the next; cluster: one warp per line, 2, 4 and 8
+    cells per lane."""
     monkeypatch.setenv("MSGB_ILU_KERNEL", "cluster")
-    monkeypatch.setenv("MSGB_ILU_LINES", lines)
-    if tk:
-        monkeypatch.setenv("MSGB_ILU_TK", tk)
+    if kern == "seg":
+        monkeypatch.setenv("MSGB_ILU_SEG", "2")
+        monkeypatch.setenv("MSGB_SEG_LINES", lines)
+        if tk:
+            monkeypatch.setenv("MSGB_SEG_TK", tk)
+    else:
+        monkeypatch.setenv("MSGB_ILU_SEG", "0")
+        monkeypatch.setenv("MSGB_ILU_LINES", lines)
+        if tk:
+            monkeypatch.setenv("MSGB_ILU_TK", tk)
     _check_ilu_sweeps(ms, ctx, G.lognormal_box(*shape, seed=37, block=(3, 2, 2), kz_ratio=0.1))
 
 
