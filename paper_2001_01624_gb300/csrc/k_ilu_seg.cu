@@ -47,10 +47,10 @@ namespace {
 
 constexpr int SE = 2;              // cells per lane
 constexpr int SLW = 32 * SE;       // cells per segment
-constexpr int SRF = 4;             // input slots per row
-constexpr int SRL = 2;             // lines per input slot
-constexpr int SNX = 4;             // k-exchange ring: lines a row may run ahead of the next
-constexpr int SNC = 4;             // carry ring: lines a segment may run ahead of the next
+constexpr int SRF = 2;             // input slots per row
+constexpr int SRL = 4;             // lines per input slot (one barrier wait per 4 line steps)
+constexpr int SNX = 8;             // k-exchange ring: lines a row may run ahead of the next
+constexpr int SNC = 8;             // carry ring: lines a segment may run ahead of the next
 constexpr int SNL = 5;             // scan levels over 32 lanes
 constexpr int kMaxSeg = 4;         // lines of up to 256 cells
 
@@ -59,30 +59,33 @@ constexpr int kMaxSeg = 4;         // lines of up to 256 cells
 __host__ __device__ constexpr int seg_span(int S) { return SNL * 32 + (S > 1 ? SLW : 0); }
 __host__ __device__ constexpr int seg_table(int S) { return S * seg_span(S); }
 
-// tagged words: payload in the low 32 bits, tag in the high 32
+// tagged words: payload in the low 32 bits, tag in the high 32.  The data a
+// word guards travels in the word itself, so these accesses need no ordering
+// against other memory operations (no memory clobber); being volatile they
+// keep their order among themselves.
 __device__ __forceinline__ unsigned long long tw_lo(unsigned payload, unsigned tag) {
     return (unsigned long long)payload | ((unsigned long long)tag << 32);
 }
 __device__ __forceinline__ void tw_put2(unsigned caddr, unsigned long long a, unsigned long long b) {
-    asm volatile("st.relaxed.cluster.shared::cluster.v2.u64 [%0], {%1, %2};" ::"r"(caddr), "l"(a), "l"(b) : "memory");
+    asm volatile("st.relaxed.cluster.shared::cluster.v2.u64 [%0], {%1, %2};" ::"r"(caddr), "l"(a), "l"(b));
 }
 __device__ __forceinline__ void tw_put1(unsigned caddr, unsigned long long a) {
-    asm volatile("st.relaxed.cluster.shared::cluster.u64 [%0], %1;" ::"r"(caddr), "l"(a) : "memory");
+    asm volatile("st.relaxed.cluster.shared::cluster.u64 [%0], %1;" ::"r"(caddr), "l"(a));
 }
 __device__ __forceinline__ void tw_get2(unsigned saddr, unsigned long long &a, unsigned long long &b) {
-    asm volatile("ld.relaxed.cluster.shared::cta.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(saddr) : "memory");
+    asm volatile("ld.relaxed.cluster.shared::cta.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(saddr));
 }
 __device__ __forceinline__ unsigned long long tw_get1(unsigned saddr) {
     unsigned long long a;
-    asm volatile("ld.relaxed.cluster.shared::cta.u64 %0, [%1];" : "=l"(a) : "r"(saddr) : "memory");
+    asm volatile("ld.relaxed.cluster.shared::cta.u64 %0, [%1];" : "=l"(a) : "r"(saddr));
     return a;
 }
 __device__ __forceinline__ void prog_put(unsigned caddr, unsigned v) {
-    asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;" ::"r"(caddr), "r"(v) : "memory");
+    asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;" ::"r"(caddr), "r"(v));
 }
 __device__ __forceinline__ unsigned prog_get(unsigned saddr) {
     unsigned v;
-    asm volatile("ld.relaxed.cluster.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(saddr) : "memory");
+    asm volatile("ld.relaxed.cluster.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(saddr));
     return v;
 }
 __device__ __forceinline__ bool tag_is(unsigned long long w, unsigned tag) { return (unsigned)(w >> 32) == tag; }
@@ -134,11 +137,13 @@ __device__ __forceinline__ bool tw_wait(unsigned saddr, unsigned tag, unsigned l
     }
 }
 
-// wait until the progress word at saddr reaches `need`
-__device__ __forceinline__ bool prog_wait(unsigned saddr, unsigned need, int *err) {
+// wait until the progress word at saddr reaches `need`; `seen` keeps the
+// last value read, so the word is read only when that is not enough
+__device__ __forceinline__ bool prog_wait(unsigned saddr, unsigned need, unsigned &seen, int *err) {
+    if (seen >= need) return true;
     unsigned long long t0 = 0;
     int spins = 0;
-    while (prog_get(saddr) < need) {
+    while ((seen = prog_get(saddr)) < need) {
         if ((++spins & 63) == 0) {
             const unsigned long long now = global_ns();
             if (t0 == 0) t0 = now;
@@ -154,10 +159,12 @@ __device__ __forceinline__ bool prog_wait(unsigned saddr, unsigned need, int *er
 // shared-memory layout of the segmented sweep (bytes), for a layout of
 // lines of Lx cells in S segments, TK rows per CTA
 struct SegSmem {
-    size_t coef, tab, rhs, xin, cin, prog, bars, total;
+    size_t coef, tab, rhs, xin, cin, pv, prog, bars, total;
 };
+// PP warps per segment take the lines in turn (PP = 2: one warp's bookkeeping
+// overlaps the other's dependency chain)
 template <typename T, typename TR>
-__host__ __device__ SegSmem seg_smem(int Lx, int S, int TK) {
+__host__ __device__ SegSmem seg_smem(int Lx, int S, int TK, int PP) {
     constexpr int RW = sizeof(T) == 8 ? 2 : 1;
     SegSmem m{};
     size_t off = 0;
@@ -167,12 +174,14 @@ __host__ __device__ SegSmem seg_smem(int Lx, int S, int TK) {
     off += sizeof(T) == 8 ? (size_t)SRF * TK * SRL * seg_table(S) * sizeof(T) : 0;
     m.rhs = off;
     off += (size_t)SRF * TK * rhs_win(SRL * Lx, sizeof(TR)) * sizeof(TR);
-    m.xin = off;
+    m.xin = off;                                   // [TK][S][SNX] lines from the previous row
     off += (size_t)TK * S * SNX * SLW * RW * 8;
-    m.cin = off;
-    off += (size_t)TK * S * SNC * 2 * 8;           // carry words padded to 16 bytes
-    m.prog = off;
-    off += ((size_t)(2 * TK * S + S) * 4 + 15) / 16 * 16;
+    m.cin = off;                                   // [TK][S][PP][SNC] carries, padded to 16 bytes
+    off += (size_t)TK * S * PP * SNC * 2 * 8;
+    m.pv = off;                                    // [TK][S][PP][2] the previous line, from the other warp
+    off += PP > 1 ? (size_t)TK * S * PP * 2 * SLW * RW * 8 : 0;
+    m.prog = off;                                  // progress: xprog [TK S PP] | cprog [TK S PP] | rprog [S PP]
+    off += ((size_t)(2 * TK * S + S) * PP * 4 + 15) / 16 * 16;
     m.bars = off;
     off += (size_t)2 * SRF * TK * 8;
     m.total = off;
@@ -183,15 +192,17 @@ __host__ __device__ SegSmem seg_smem(int Lx, int S, int TK) {
 
 namespace {
 
-// Warps: TK rows x S segments compute (warp r S + s: row r, segment s, so the
-// segments of a row sit on different sub-partitions), then the producer, then
-// the relay (rows spanning several clusters).  The rows may span NC clusters
-// of gridDim.x / NC CTAs; each cluster takes a ticket when it starts, and the
-// ticket decides its block of rows, so a cluster only waits for one that
-// started before it.
-constexpr int kSegMaxWarps = 12;   // compute warps (rows x segments) + producer + relay
+// Warps: PP x TK rows x S segments compute (warp (p TK + r) S + s: phase p,
+// row r, segment s, so the segments of a row, and the two phases of one
+// segment, sit on different sub-partitions' turns), then the producer, then
+// (rows spanning several clusters) one relay warp per segment.  Phase p takes
+// the lines tj = p, p + PP, ... of its row and segment.  The rows may span NC
+// clusters of gridDim.x / NC CTAs; each cluster takes a ticket when it
+// starts, and the ticket decides its block of rows, so a cluster only waits
+// for one that started before it.
+constexpr int kSegMaxWarps = 14;   // compute warps + producer + relays
 
-template <typename T, typename TR, bool BWD>
+template <typename T, typename TR, bool BWD, int PP>
 __global__ void __launch_bounds__(32 * kSegMaxWarps, 1)
     k_line_seg(int Lx, int Ny, int Nz, int S, int TK, int NC, const T *__restrict__ coef4, const T *__restrict__ scanm,
                const TR *__restrict__ rhs, T *__restrict__ out, unsigned long long *tick, unsigned long long *ring,
@@ -202,14 +213,16 @@ __global__ void __launch_bounds__(32 * kSegMaxWarps, 1)
     constexpr unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const unsigned K = cluster_rank();
-    const SegSmem lay = seg_smem<T, TR>(Lx, S, TK);
+    const SegSmem lay = seg_smem<T, TR>(Lx, S, TK, PP);
     extern __shared__ __align__(16) unsigned char smraw[];
     T *cwin = reinterpret_cast<T *>(smraw + lay.coef);
     T *twin = reinterpret_cast<T *>(smraw + lay.tab);
     TR *rwin = reinterpret_cast<TR *>(smraw + lay.rhs);
     unsigned long long *xin = reinterpret_cast<unsigned long long *>(smraw + lay.xin);
     unsigned long long *cin = reinterpret_cast<unsigned long long *>(smraw + lay.cin);
-    unsigned *prog = reinterpret_cast<unsigned *>(smraw + lay.prog);   // xprog [TK S] | cprog [TK S] | rprog [S]
+    unsigned long long *pvin = reinterpret_cast<unsigned long long *>(smraw + lay.pv);
+    unsigned *prog = reinterpret_cast<unsigned *>(smraw + lay.prog);   // xprog [TK S PP] | cprog | rprog [S PP]
+    const int NCW = TK * S * PP;   // compute warps
     const unsigned full_f = smem_u32(smraw + lay.bars);
     const unsigned empty_f = full_f + 8 * SRF * TK;
     const int CLN = Lx * 4;
@@ -219,11 +232,11 @@ __global__ void __launch_bounds__(32 * kSegMaxWarps, 1)
     // every hand-over word starts with a tag no line carries, every progress
     // word at zero; the cluster barrier below publishes them
     for (size_t i = tid; i < (lay.prog - lay.xin) / 8; i += blockDim.x) xin[i] = ~0ull;
-    for (int i = tid; i < 2 * TK * S + S; i += blockDim.x) prog[i] = 0u;
+    for (int i = tid; i < (2 * TK * S + S) * PP; i += blockDim.x) prog[i] = 0u;
     if (tid < TK) {
         for (int q = 0; q < SRF; ++q) {
             mb_init(full_f + 8 * (q * TK + tid), 1);
-            mb_init(empty_f + 8 * (q * TK + tid), (unsigned)S);   // each segment warp frees the slot
+            mb_init(empty_f + 8 * (q * TK + tid), (unsigned)(S * PP));   // each compute warp of the row frees it
         }
     }
     __shared__ unsigned long long s_tick;
@@ -243,7 +256,7 @@ __global__ void __launch_bounds__(32 * kSegMaxWarps, 1)
     const int nblk = (Ny + SRL - 1) / SRL;
     const int SW = S * SLW;                              // values of one line in the global ring
 
-    if (w == TK * S) {
+    if (w == NCW) {
         // producer warp: lane r streams the input blocks of row r (SRL lines each)
         const int g = KG * TK + lane;
         int tb = (lane < TK && g < Nz) ? 0 : nblk;
@@ -292,39 +305,36 @@ __global__ void __launch_bounds__(32 * kSegMaxWarps, 1)
                 }
             }
         }
-    } else if (w == TK * S + 1) {
-        // relay warp: the first CTA of a cluster other than the first takes the
-        // previous cluster's last row from the global ring (two lines per round
-        // trip, all segments at once) and forwards it, retagged, into its row
-        // 0's exchange slots
+    } else if (w > NCW && w <= NCW + S) {
+        // relay warps, one per segment: the first CTA of a cluster other than
+        // the first takes its segment of the previous cluster's last row from
+        // the global ring (two lines per round trip) and forwards it, retagged,
+        // into row 0's exchange slots, each segment as soon as it is there
         constexpr int D = 2;
-        constexpr int NWL = kMaxSeg * NW;   // a lane's words of one line, all segments
+        const int s2 = w - NCW - 1;
         if (NC > 1 && K == 0 && v > 0 && KG * TK < Nz) {
-            const unsigned long long *rin = ring + (size_t)(v - 1) * Ny * SW * RW;
+            const unsigned long long *rin =
+                ring + ((size_t)(v - 1) * Ny * SW + (size_t)s2 * SLW + (size_t)lane * SE) * RW;
+            const unsigned rp0 = smem_u32(prog + (2 * TK * S + s2) * PP);   // + 4 p: phase p's reads
+            const unsigned xo = map_cta(smem_u32(xin + (size_t)s2 * SNX * SLW * RW + (size_t)lane * NW), K);
             int tj = 0;
             unsigned long long t0 = 0;
+            unsigned rseen0 = 0, rseen1 = 0;   // per phase of the lines
             bool ok = true;
             while (tj < Ny && ok) {
-                unsigned long long wv[D][NWL];
+                unsigned long long wv[D][NW];
 #pragma unroll
                 for (int d = 0; d < D; ++d)
 #pragma unroll
-                    for (int s2 = 0; s2 < kMaxSeg; ++s2)
-#pragma unroll
-                        for (int k = 0; k < NW; ++k)
-                            wv[d][s2 * NW + k] =
-                                (tj + d < Ny && s2 < S)
-                                    ? *(const volatile unsigned long long *)(rin + ((size_t)(tj + d) * SW + (size_t)s2 * SLW +
-                                                                                    (size_t)lane * SE) * RW + k)
-                                    : 0ull;
+                    for (int k = 0; k < NW; ++k)
+                        wv[d][k] = tj + d < Ny ? *(const volatile unsigned long long *)(rin + (size_t)(tj + d) * SW * RW + k)
+                                               : 0ull;
                 int ready = 0;
 #pragma unroll
                 for (int d = 0; d < D; ++d) {
                     bool here = tj + d < Ny;
 #pragma unroll
-                    for (int s2 = 0; s2 < kMaxSeg; ++s2)
-#pragma unroll
-                        for (int k = 0; k < NW; ++k) here = here && (s2 >= S || tag_is(wv[d][s2 * NW + k], ltag));
+                    for (int k = 0; k < NW; ++k) here = here && tag_is(wv[d][k], ltag);
                     if (here && ready == d) ready = d + 1;
                 }
                 ready = (int)__reduce_min_sync(FULL, (unsigned)ready);
@@ -340,33 +350,33 @@ __global__ void __launch_bounds__(32 * kSegMaxWarps, 1)
                 t0 = 0;
 #pragma unroll
                 for (int d = 0; d < D; ++d) {
-                    if (d >= ready) break;
+                    if (d >= ready || !ok) continue;
                     const int line = tj + d;
-                    const unsigned xtag = (unsigned)line + 1u;
-#pragma unroll
-                    for (int s2 = 0; s2 < kMaxSeg; ++s2) {
-                        if (s2 >= S || !ok) continue;
-                        if (line >= SNX) ok = prog_wait(smem_u32(prog + 2 * TK * S + s2), (unsigned)(line - SNX + 1), err);
-                        if (!__all_sync(FULL, ok)) {
-                            ok = false;
-                            continue;
-                        }
-                        unsigned long long o[NW];
-#pragma unroll
-                        for (int k = 0; k < NW; ++k) o[k] = tw_lo((unsigned)wv[d][s2 * NW + k], xtag);
-                        const unsigned a = map_cta(smem_u32(xin + ((size_t)s2 * SNX + line % SNX) * SLW * RW +
-                                                            (size_t)lane * NW), K);
-                        tw_put2(a, o[0], o[1]);
-                        if constexpr (NW == 4) tw_put2(a + 16, o[2], o[3]);
+                    if (line >= SNX) {
+                        const bool odd = PP > 1 && (line & 1);
+                        unsigned sn = odd ? rseen1 : rseen0;
+                        ok = prog_wait(rp0 + (odd ? 4u : 0u), (unsigned)(line - SNX + 1), sn, err);
+                        if (odd) rseen1 = sn;
+                        else rseen0 = sn;
                     }
-                    if (!ok) break;
+                    if (!__all_sync(FULL, ok)) {
+                        ok = false;
+                        continue;
+                    }
+                    unsigned long long o[NW];
+#pragma unroll
+                    for (int k = 0; k < NW; ++k) o[k] = tw_lo((unsigned)wv[d][k], (unsigned)line + 1u);
+                    const unsigned a = xo + (unsigned)((line % SNX) * SLW * RW * 8);
+                    tw_put2(a, o[0], o[1]);
+                    if constexpr (NW == 4) tw_put2(a + 16, o[2], o[3]);
                 }
                 tj += ready;
             }
         }
-    } else if (w < TK * S) {
-        const int r = w / S, s = w % S;
+    } else if (w < NCW) {
+        const int p = w / (TK * S), r = (w % (TK * S)) / S, s = w % S;
         const int g = KG * TK + r;
+        const int rs = r * S + s;   // row and segment within the CTA
         if (g < Nz) {
             const int gl = lane;
             const int kr = BWD ? Nz - 1 - g : g;
@@ -377,37 +387,51 @@ __global__ void __launch_bounds__(32 * kSegMaxWarps, 1)
             // previous CTA of the cluster, or (first CTA of a cluster) from the relay
             const bool src_relay = has_src && src_remote && K == 0;
             const bool dst_global = has_dst && dst_remote && (int)K == NKC - 1;
-            const unsigned my_x = smem_u32(xin + (size_t)(r * S + s) * SNX * SLW * RW + (size_t)gl * NW);
-            const unsigned my_xprog = smem_u32(prog + r * S + s);   // how far the next row has read my lines
+            const unsigned my_x = smem_u32(xin + (size_t)rs * SNX * SLW * RW + (size_t)gl * NW);
+            const unsigned my_xprog = smem_u32(prog + rs * PP + p);   // how far the next row's phase p has read
             unsigned src_prog = 0u;                                   // where I report how far I have read
             if (has_src) {
-                if (src_relay) src_prog = map_cta(smem_u32(prog + 2 * TK * S + s), K);
-                else if (src_remote) src_prog = map_cta(smem_u32(prog + (TK - 1) * S + s), K - 1);
-                else src_prog = map_cta(smem_u32(prog + (r - 1) * S + s), K);
+                if (src_relay) src_prog = map_cta(smem_u32(prog + (2 * TK * S + s) * PP + p), K);
+                else if (src_remote) src_prog = map_cta(smem_u32(prog + ((TK - 1) * S + s) * PP + p), K - 1);
+                else src_prog = map_cta(smem_u32(prog + (rs - S) * PP + p), K);
             }
             unsigned dst_x = 0u;
             if (has_dst && !dst_global) {
-                const int dst_r = dst_remote ? 0 : r + 1;
-                dst_x = map_cta(smem_u32(xin + (size_t)(dst_r * S + s) * SNX * SLW * RW + (size_t)gl * NW),
-                                dst_remote ? K + 1 : K);
+                const int dst_rs = dst_remote ? s : rs + S;
+                dst_x = map_cta(smem_u32(xin + (size_t)dst_rs * SNX * SLW * RW + (size_t)gl * NW), dst_remote ? K + 1 : K);
             }
             unsigned long long *ring_out =
                 dst_global ? ring + ((size_t)v * Ny * SW + (size_t)s * SLW + (size_t)gl * SE) * RW : nullptr;
-            // the carry from segment s - 1 and to segment s + 1 of the same line
+            // the carry from segment s - 1 and to segment s + 1 (same phase: same lines)
             const bool has_cin = s > 0, has_cout = s + 1 < S;
-            const unsigned my_c = smem_u32(cin + (size_t)(r * S + s) * SNC * 2);
-            const unsigned nxt_c = has_cout ? map_cta(smem_u32(cin + (size_t)(r * S + s + 1) * SNC * 2), K) : 0u;
-            const unsigned my_cprog = smem_u32(prog + TK * S + r * S + s);    // how far segment s + 1 has read
-            const unsigned prv_cprog = has_cin ? map_cta(smem_u32(prog + TK * S + r * S + s - 1), K) : 0u;
+            const unsigned my_c = smem_u32(cin + (size_t)(rs * PP + p) * SNC * 2);
+            const unsigned nxt_c = has_cout ? map_cta(smem_u32(cin + (size_t)((rs + 1) * PP + p) * SNC * 2), K) : 0u;
+            const unsigned my_cprog = smem_u32(prog + (TK * S + rs) * PP + p);   // how far segment s + 1 has read
+            const unsigned prv_cprog = has_cin ? map_cta(smem_u32(prog + (TK * S + rs - 1) * PP + p), K) : 0u;
+            // the previous line of this segment, from the other phase (PP = 2)
+            const unsigned my_pv = smem_u32(pvin + (size_t)(rs * PP + p) * 2 * SLW * RW + (size_t)gl * NW);
+            const unsigned oth_pv =
+                PP > 1 ? map_cta(smem_u32(pvin + (size_t)(rs * PP + (PP - 1 - p)) * 2 * SLW * RW + (size_t)gl * NW), K)
+                       : 0u;
             T prev[SE];
 #pragma unroll
             for (int e = 0; e < SE; ++e) prev[e] = T(0);
-            for (int tj = 0; tj < Ny; ++tj) {
+            unsigned xseen = 0, cseen = 0;   // last progress read of my receivers
+            int cur_blk = -1;
+            bool done = true;
+            for (int tj = p; tj < Ny; tj += PP) {
                 const int blk = tj / SRL, q = blk % SRF;
                 const int nl = min(SRL, Ny - blk * SRL);
                 bool ok = true;
-                if (tj == blk * SRL) ok = wait_lane(full_f + 8 * (q * TK + r), (unsigned)(blk / SRF) & 1u, err);
-                if (!__all_sync(FULL, ok)) break;
+                if (blk != cur_blk) {   // a new input block: free the last one, wait for this one
+                    if (cur_blk >= 0 && gl == 0) mb_arrive_relaxed(empty_f + 8 * ((cur_blk % SRF) * TK + r));
+                    ok = wait_lane(full_f + 8 * (q * TK + r), (unsigned)(blk / SRF) & 1u, err);
+                    cur_blk = blk;
+                }
+                if (!__all_sync(FULL, ok)) {
+                    done = false;
+                    break;
+                }
                 // the slot keeps its lines in real order; this line's place in it
                 const int li = BWD ? nl - 1 - (tj - blk * SRL) : tj - blk * SRL;
                 const int j = BWD ? Ny - 1 - tj : tj;
@@ -416,8 +440,8 @@ __global__ void __launch_bounds__(32 * kSegMaxWarps, 1)
                 const int shr = (int)((((unsigned)(size_t)rhs + (unsigned)bbase * (unsigned)sizeof(TR)) & 15u) / sizeof(TR));
                 const T *cl = cwin + ((size_t)(q * TK + r) * SRL + li) * CLN;
                 const TR *rl = rwin + (size_t)(q * TK + r) * WR + shr + (size_t)li * Lx;
-                // what does not depend on the k-neighbour or the carry first
-                T A[SE], B[SE], CK[SE], P[SE];
+                // what does not depend on the neighbours or the carry first
+                T A[SE], B[SE], BR[SE], CB[SE], CK[SE], P[SE];
                 T sv[SNL];
                 if (TAB) {
                     const T *tl = twin + ((size_t)(q * TK + r) * SRL + li) * TBW + (size_t)s * seg_span(S);
@@ -430,22 +454,37 @@ __global__ void __launch_bounds__(32 * kSegMaxWarps, 1)
                 for (int e = 0; e < SE; ++e) {
                     const int at = s * SLW + gl * SE + e;
                     A[e] = T(1);
-                    B[e] = T(0);
+                    BR[e] = T(0);
+                    CB[e] = T(0);
                     CK[e] = T(0);
                     if (at < Lx) {
                         const int x = BWD ? Lx - 1 - at : at;   // real x of the cell
                         const Coef4<T> c = load_coef(cl + 4 * x);
                         // backward coefficients come scaled by 1 / U_ii (d = 1 / U_ii)
-                        B[e] = (BWD ? c.d * (T)rl[x] : (T)rl[x]) - c.b * prev[e];
+                        BR[e] = BWD ? c.d * (T)rl[x] : (T)rl[x];
                         A[e] = -c.a;
+                        CB[e] = c.b;
                         CK[e] = c.c;
                     }
                 }
-                // k-neighbour: the same segment of this line in the previous row
                 const unsigned xtag = (unsigned)tj + 1u;
+                // the previous line of this segment (the other phase's last line)
+                if (PP > 1 && tj > 0) {
+                    unsigned long long wv[NW];
+                    ok = tw_wait<NW>(my_pv + (unsigned)(((tj / PP) & 1) * SLW * RW * 8), (unsigned)tj, wv, err);
+#pragma unroll
+                    for (int e = 0; e < SE; ++e) {
+                        if constexpr (RW == 2) prev[e] = (T)tw_decode2(wv[2 * e], wv[2 * e + 1]);
+                        else prev[e] = (T)tw_decode1(wv[e]);
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < SE; ++e) B[e] = BR[e] - CB[e] * prev[e];
+                // k-neighbour: the same segment of this line in the previous row
                 if (has_src) {
                     unsigned long long wv[NW];
-                    ok = tw_wait<NW>(my_x + (unsigned)((tj % SNX) * SLW * RW * 8), xtag, wv, err);
+                    const bool okx = tw_wait<NW>(my_x + (unsigned)((tj % SNX) * SLW * RW * 8), xtag, wv, err);
+                    ok = ok && okx;
                     T nk[SE];
 #pragma unroll
                     for (int e = 0; e < SE; ++e) {
@@ -456,7 +495,10 @@ __global__ void __launch_bounds__(32 * kSegMaxWarps, 1)
                     for (int e = 0; e < SE; ++e)
                         if (s * SLW + gl * SE + e < Lx) B[e] = B[e] - CK[e] * nk[e];
                 }
-                if (!__all_sync(FULL, ok)) break;
+                if (!__all_sync(FULL, ok)) {
+                    done = false;
+                    break;
+                }
                 if (has_src && gl == 0) prog_put(src_prog, xtag);   // every lane has its words
                 // the segment's recurrence from a zero start: lanes compose their
                 // cells' maps, a shuffle scan composes the lanes (FP64: the scan's
@@ -503,8 +545,11 @@ __global__ void __launch_bounds__(32 * kSegMaxWarps, 1)
                 // the value entering the segment, from segment s - 1 of this line
                 if (has_cin) {
                     unsigned long long cw[2];
-                    ok = tw_wait<2>(my_c + (unsigned)((tj % SNC) * 16), xtag, cw, err);
-                    if (!__all_sync(FULL, ok)) break;
+                    ok = tw_wait<2>(my_c + (unsigned)(((tj / PP) % SNC) * 16), xtag, cw, err);
+                    if (!__all_sync(FULL, ok)) {
+                        done = false;
+                        break;
+                    }
                     T c;
                     if constexpr (RW == 2) c = (T)tw_decode2(cw[0], cw[1]);
                     else c = (T)tw_decode1(cw[0]);
@@ -515,7 +560,7 @@ __global__ void __launch_bounds__(32 * kSegMaxWarps, 1)
                 // the value leaving the segment, to segment s + 1 (its last lane's last cell)
                 bool okc = true;
                 if (has_cout && gl == 31) {
-                    if (tj >= SNC) okc = prog_wait(my_cprog, (unsigned)(tj - SNC + 1), err);
+                    if (tj >= PP * SNC) okc = prog_wait(my_cprog, (unsigned)(tj - PP * SNC + 1), cseen, err);
                     if (okc) {
                         unsigned long long cw[2];
                         if constexpr (RW == 2) {
@@ -525,11 +570,22 @@ __global__ void __launch_bounds__(32 * kSegMaxWarps, 1)
                         } else {
                             cw[0] = cw[1] = tw_lo(__float_as_uint((float)val[SE - 1]), xtag);
                         }
-                        tw_put2(nxt_c + (unsigned)((tj % SNC) * 16), cw[0], cw[1]);
+                        tw_put2(nxt_c + (unsigned)(((tj / PP) % SNC) * 16), cw[0], cw[1]);
                     }
                 }
-                if (!__all_sync(FULL, okc)) break;
-                // the line to the next row
+                if (!__all_sync(FULL, okc)) {
+                    done = false;
+                    break;
+                }
+                // this line to the other phase (its next line's j-neighbour), then
+                // to the next row
+                if (PP > 1 && tj + 1 < Ny) {
+                    unsigned long long wv[NW];
+                    tw_encode(val, xtag, wv);
+                    const unsigned a = oth_pv + (unsigned)((((tj + 1) / PP) & 1) * SLW * RW * 8);
+                    tw_put2(a, wv[0], wv[1]);
+                    if constexpr (NW == 4) tw_put2(a + 16, wv[2], wv[3]);
+                }
                 if (has_dst) {
                     unsigned long long wv[NW];
                     tw_encode(val, dst_global ? ltag : xtag, wv);
@@ -539,8 +595,11 @@ __global__ void __launch_bounds__(32 * kSegMaxWarps, 1)
                         for (int k = 0; k < NW; ++k) *(volatile unsigned long long *)(ro + k) = wv[k];
                     } else {
                         bool ok2 = true;
-                        if (tj >= SNX) ok2 = prog_wait(my_xprog, (unsigned)(tj - SNX + 1), err);
-                        if (!__all_sync(FULL, ok2)) break;
+                        if (tj >= SNX) ok2 = prog_wait(my_xprog, (unsigned)(tj - SNX + 1), xseen, err);
+                        if (!__all_sync(FULL, ok2)) {
+                            done = false;
+                            break;
+                        }
                         const unsigned a = dst_x + (unsigned)((tj % SNX) * SLW * RW * 8);
                         tw_put2(a, wv[0], wv[1]);
                         if constexpr (NW == 4) tw_put2(a + 16, wv[2], wv[3]);
@@ -551,11 +610,11 @@ __global__ void __launch_bounds__(32 * kSegMaxWarps, 1)
                 for (int e = 0; e < SE; ++e) {
                     const int at = s * SLW + gl * SE + e;
                     if (at < Lx) ob[BWD ? Lx - 1 - at : at] = val[e];
-                    prev[e] = val[e];
+                    if (PP == 1) prev[e] = val[e];
                 }
-                // the slot's last line: every lane's reads of it fed the scan
-                if (gl == 0 && tj - blk * SRL == nl - 1) mb_arrive_relaxed(empty_f + 8 * (q * TK + r));
             }
+            // the last block this warp read: every lane's reads of it fed a scan
+            if (done && cur_blk >= 0 && gl == 0) mb_arrive_relaxed(empty_f + 8 * ((cur_blk % SRF) * TK + r));
         }
     }
     cluster_sync_all();   // no CTA leaves while a neighbour may still touch its shared memory
@@ -608,12 +667,12 @@ __global__ void k_pack_seg_scan(int Lx, long long lines, int S, const double *__
     }
 }
 
-template <typename T, typename TR, bool BWD>
-cudaError_t launch_seg(const int dims[3], int S, int TK, int NK, int NC, const T *coef4, const T *scanm, const TR *rhs,
-                       T *out, unsigned long long *tick, unsigned long long *ring, int *err, cudaStream_t st,
-                       bool query_only = false, int *clusters = nullptr) {
-    auto kern = k_line_seg<T, TR, BWD>;
-    const size_t smem = seg_smem<T, TR>(dims[0], S, TK).total;
+template <typename T, typename TR, bool BWD, int PP>
+cudaError_t launch_seg_pp(const int dims[3], int S, int TK, int NK, int NC, const T *coef4, const T *scanm,
+                          const TR *rhs, T *out, unsigned long long *tick, unsigned long long *ring, int *err,
+                          cudaStream_t st, bool query_only, int *clusters) {
+    auto kern = k_line_seg<T, TR, BWD, PP>;
+    const size_t smem = seg_smem<T, TR>(dims[0], S, TK, PP).total;
     static size_t smem_set = 0;                      // per instantiation: attributes are raised once
     static std::atomic<bool> nonportable{false};
     cudaError_t e = raise_smem_limit(kern, smem, smem_set);
@@ -625,7 +684,7 @@ cudaError_t launch_seg(const int dims[3], int S, int TK, int NK, int NC, const T
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(NK * NC, 1, 1);
-    cfg.blockDim = dim3(32 * (TK * S + 1 + (NC > 1 ? 1 : 0)), 1, 1);   // + producer (+ relay)
+    cfg.blockDim = dim3(32 * (TK * S * PP + 1 + (NC > 1 ? S : 0)), 1, 1);   // + producer (+ relay per segment)
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -639,15 +698,25 @@ cudaError_t launch_seg(const int dims[3], int S, int TK, int NK, int NC, const T
     return cudaLaunchKernelEx(&cfg, kern, dims[0], dims[1], dims[2], S, TK, NC, coef4, scanm, rhs, out, tick, ring, err);
 }
 
+template <typename T, typename TR, bool BWD>
+cudaError_t launch_seg(const int dims[3], int S, int TK, int PP, int NK, int NC, const T *coef4, const T *scanm,
+                       const TR *rhs, T *out, unsigned long long *tick, unsigned long long *ring, int *err,
+                       cudaStream_t st, bool query_only = false, int *clusters = nullptr) {
+    return PP > 1 ? launch_seg_pp<T, TR, BWD, 2>(dims, S, TK, NK, NC, coef4, scanm, rhs, out, tick, ring, err, st,
+                                                 query_only, clusters)
+                  : launch_seg_pp<T, TR, BWD, 1>(dims, S, TK, NK, NC, coef4, scanm, rhs, out, tick, ring, err, st,
+                                                 query_only, clusters);
+}
+
 template <typename T, typename TR>
-bool seg_fits(const int dims[3], int S, int TK, int NK, int NC) {
-    if (TK * S + 2 > kSegMaxWarps) return false;
-    if (seg_smem<T, TR>(dims[0], S, TK).total > 220 * 1024 || seg_smem<T, T>(dims[0], S, TK).total > 220 * 1024)
+bool seg_fits(const int dims[3], int S, int TK, int PP, int NK, int NC) {
+    if (TK * S * PP + 1 + (NC > 1 ? S : 0) > kSegMaxWarps) return false;
+    if (seg_smem<T, TR>(dims[0], S, TK, PP).total > 220 * 1024 || seg_smem<T, T>(dims[0], S, TK, PP).total > 220 * 1024)
         return false;
     int c1 = 0, c2 = 0;
-    if (launch_seg<T, TR, false>(dims, S, TK, NK, NC, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+    if (launch_seg<T, TR, false>(dims, S, TK, PP, NK, NC, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                                  nullptr, true, &c1) != cudaSuccess ||
-        launch_seg<T, T, true>(dims, S, TK, NK, NC, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+        launch_seg<T, T, true>(dims, S, TK, PP, NK, NC, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                                nullptr, true, &c2) != cudaSuccess) {
         cudaGetLastError();
         return false;
@@ -676,16 +745,25 @@ bool plan_ilu_seg(ms_system &s, int p) {
     const int dims[3] = {ylines ? s.ny : s.nx, ylines ? s.nx : s.ny, s.nz};
     if (dims[0] > kMaxSeg * SLW || dims[1] < 1 || dims[2] < 1) return false;
     const int S = (dims[0] + SLW - 1) / SLW;
-    int tk = p == 0 && S > 1 ? 1 : 2;
+    // one warp per segment; MSGB_SEG_PP=2 gives each segment two warps that
+    // take the lines in turn (the previous line then travels between them
+    // through shared memory: on the 60x220x85 grid 0.189 / 0.189 ms FP64
+    // against 0.183 / 0.191 ms with one warp, as a hand-off between warps
+    // costs about what the bookkeeping it overlaps does)
+    int PP = 1;
+    if (const char *t = std::getenv("MSGB_SEG_PP")) PP = std::atoi(t) >= 2 ? 2 : 1;
+    int tk = (p == 0 && S > 1) || PP > 1 ? 1 : 2;
     if (const char *t = std::getenv("MSGB_SEG_TK")) tk = std::max(1, std::atoi(t));
     const int NKtot = (dims[2] + tk - 1) / tk;
     const int NC = (NKtot + 15) / 16;
     const int NK = (NKtot + NC - 1) / NC;
     const int TK = (dims[2] + NK * NC - 1) / (NK * NC);
-    const bool fits = p == 0 ? seg_fits<double, double>(dims, S, TK, NK, NC)
-                             : seg_fits<float, double>(dims, S, TK, NK, NC) && seg_fits<float, float>(dims, S, TK, NK, NC);
+    const bool fits = p == 0 ? seg_fits<double, double>(dims, S, TK, PP, NK, NC)
+                             : seg_fits<float, double>(dims, S, TK, PP, NK, NC) &&
+                                   seg_fits<float, float>(dims, S, TK, PP, NK, NC);
     if (!fits) return false;
     s.sg_S[p] = S;
+    s.sg_PP[p] = PP;
     s.sg_TK[p] = TK;
     s.sg_NK[p] = NK;
     s.sg_NC[p] = NC;
@@ -719,7 +797,7 @@ template <typename T, typename TR>
 void seg_fwd(ms_system &s, int p, const T *coef4, const T *scanm, const TR *rhs, T *out, cudaStream_t st) {
     const bool yl = s.cl_T[p];
     const int dims[3] = {yl ? s.ny : s.nx, yl ? s.nx : s.ny, s.nz};
-    MS_CUDA((launch_seg<T, TR, false>(dims, s.sg_S[p], s.sg_TK[p], s.sg_NK[p], s.sg_NC[p], coef4, scanm, rhs, out,
+    MS_CUDA((launch_seg<T, TR, false>(dims, s.sg_S[p], s.sg_TK[p], s.sg_PP[p], s.sg_NK[p], s.sg_NC[p], coef4, scanm, rhs, out,
                                       s.sg_tick.p + p, s.sg_ring[p].p, s.sync.p + 3, st)));
 }
 
@@ -727,7 +805,7 @@ template <typename T>
 void seg_bwd(ms_system &s, int p, const T *coef4, const T *scanm, const T *rhs, T *out, cudaStream_t st) {
     const bool yl = s.cl_T[p];
     const int dims[3] = {yl ? s.ny : s.nx, yl ? s.nx : s.ny, s.nz};
-    MS_CUDA((launch_seg<T, T, true>(dims, s.sg_S[p], s.sg_TK[p], s.sg_NK[p], s.sg_NC[p], coef4, scanm, rhs, out,
+    MS_CUDA((launch_seg<T, T, true>(dims, s.sg_S[p], s.sg_TK[p], s.sg_PP[p], s.sg_NK[p], s.sg_NC[p], coef4, scanm, rhs, out,
                                     s.sg_tick.p + p, s.sg_ring[p].p, s.sync.p + 3, st)));
 }
 

@@ -252,7 +252,7 @@ struct ms_system {
     msgb::DBuf<unsigned long long> cl_ring[2];  // lines crossing cluster boundaries (tagged words)
     // segmented line sweeps (lines cut into 64-cell segments, one warp each)
     bool sg_ok[2] = {false, false};
-    int sg_S[2] = {1, 1}, sg_TK[2] = {0, 0}, sg_NK[2] = {0, 0}, sg_NC[2] = {1, 1};
+    int sg_S[2] = {1, 1}, sg_PP[2] = {1, 1}, sg_TK[2] = {0, 0}, sg_NK[2] = {0, 0}, sg_NC[2] = {1, 1};
     msgb::DBuf<unsigned long long> sg_tick;   // cluster tickets per precision
     msgb::DBuf<unsigned long long> sg_ring[2];
     msgb::DBuf<double> coef4_64;              // [2][n][4]: (Lx, Ly, Lz, 0), (Ux/d, Uy/d, Uz/d, 1/d) per cell, d = U_ii

@@ -533,7 +533,7 @@ def test_tiled_ilu_sweeps_across_tiles(ms, ctx, monkeypatch, kernel, tile, shape
     _check_ilu_sweeps(ms, ctx, G.lognormal_box(*shape, seed=31, block=(3, 4, 2), kz_ratio=0.1))
 
 
-@pytest.mark.parametrize("kern", ["seg", "cluster"])
+@pytest.mark.parametrize("kern", ["seg", "seg_pp1", "seg_pp2", "cluster"])
 @pytest.mark.parametrize("tk", ["", "3", "1"])
 @pytest.mark.parametrize("lines", ["y", "x"])
 @pytest.mark.parametrize("shape", [(9, 13, 1), (9, 13, 7), (70, 6, 17), (33, 20, 40), (200, 5, 11),
@@ -546,12 +546,14 @@ def test_cluster_ilu_sweeps(ms, ctx, monkeypatch, shape, lines, tk, kern):
     grids.  With few rows per CTA (tk) the rows span several clusters, which
     hand lines over through the global ring in ticket order (up to 13
     clusters).  seg: lines cut into 1 to 4 segments of 64 cells (full,
-    ragged and single-cell last segments), one warp each, passing the value
-    that leaves a segment to the next; cluster: one warp per line, 2, 4 and 8
-    cells per lane."""
+    ragged and single-cell last segments), one warp each (pp1) or two warps
+    taking the lines in turn (pp2), passing the value that leaves a segment to
+    the next; cluster: one warp per line, 2, 4 and 8 cells per lane."""
     monkeypatch.setenv("MSGB_ILU_KERNEL", "cluster")
-    if kern == "seg":
+    if kern.startswith("seg"):
         monkeypatch.setenv("MSGB_ILU_SEG", "2")
+        if kern != "seg":
+            monkeypatch.setenv("MSGB_SEG_PP", kern[-1])
         monkeypatch.setenv("MSGB_SEG_LINES", lines)
         if tk:
             monkeypatch.setenv("MSGB_SEG_TK", tk)
