@@ -534,6 +534,31 @@ __global__ void k_multiaxpy(int n, int k, const double *__restrict__ V, const do
     }
 }
 
+// y[l] += sign * sum_{i<k} c[i] V[i n + l], then ||y||_2 (the last
+// Gram-Schmidt pass of an Arnoldi step and the new vector's norm in one read)
+__global__ void k_multiaxpy_norm(int n, int k, const double *__restrict__ V, const double *__restrict__ c,
+                                 double sign, double *__restrict__ y, double *red, unsigned int *cnt, double *norm_out) {
+    __shared__ double cs[128];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) cs[i] = sign * c[i];
+    __syncthreads();
+    double ss = 0.0;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
+        double a = y[l];
+        int i = 0;
+        for (; i + 8 <= k; i += 8) {   // eight vectors' loads in flight, summed in order
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldcs(V + (int64_t)(i + u) * n + l);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a += cs[i + u] * v[u];
+        }
+        for (; i < k; ++i) a += cs[i] * V[(int64_t)i * n + l];
+        y[l] = a;
+        ss += a * a;
+    }
+    finish_norm(block_sum(ss), red, cnt, norm_out);
+}
+
 __global__ void k_scale(int n, const double *__restrict__ x, double a, double *__restrict__ y) {
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) y[l] = a * x[l];
 }
@@ -625,6 +650,15 @@ __global__ void k_gmres_restart(GmresDev G, const double *beta_norm, cudaGraphCo
                             (res > G.tol && it < G.max_iter && res == res && !*G.err && r <= G.max_iter) ? 1u : 0u);
 }
 }  // namespace
+
+void launch_multiaxpy_norm(int n, int k, const double *V, const double *c, double sign, double *y, double *red,
+                           unsigned int *cnt, double *norm_out, cudaStream_t st) {
+    KernelScope ks_(st, "krylov_axpy", (double)(k + 2) * n * 8);
+    // one partial sum per block in red, which holds ceil(n / 256) of them:
+    // the grid is the reduction grid (never more blocks than that)
+    k_multiaxpy_norm<<<reduce_grid(n), kThreads, 0, st>>>(n, k, V, c, sign, y, red, cnt, norm_out);
+    MS_CHECK_LAUNCH();
+}
 
 void launch_scale_dev(int n, const double *x, const double *a, double *y, cudaStream_t st) {
     k_scale_dev<<<stride_grid(n), kThreads, 0, st>>>(n, x, a, y);

@@ -1315,8 +1315,7 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
                         launch_multidot(n, j + 1, V, w, s->w_kred.p, s->w_kcnt.p, h1, cs);
                         launch_multiaxpy(n, j + 1, V, h1, -1.0, w, cs);
                         launch_multidot(n, j + 1, V, w, s->w_kred.p, s->w_kcnt.p, h2, cs);
-                        launch_multiaxpy(n, j + 1, V, h2, -1.0, w, cs);
-                        launch_norm2(w, n, s->w_red.p, s->w_cnt.p, hn_dev, cs);
+                        launch_multiaxpy_norm(n, j + 1, V, h2, -1.0, w, s->w_red.p, s->w_cnt.p, hn_dev, cs);
                         launch_gmres_step(G, j, h1, h2, hn_dev, hsteps, cs);
                         launch_scale_dev(n, w, G.scal, V + (size_t)(j + 1) * n, cs);
                     });
@@ -1395,8 +1394,7 @@ ms_status ms_solve(ms_ctx *ctx, ms_system *s, ms_coarse *const *stages, int32_t 
                 launch_multidot(n, k + 1, V, w, s->w_kred.p, s->w_kcnt.p, h1, st);
                 launch_multiaxpy(n, k + 1, V, h1, -1.0, w, st);
                 launch_multidot(n, k + 1, V, w, s->w_kred.p, s->w_kcnt.p, h2, st);
-                launch_multiaxpy(n, k + 1, V, h2, -1.0, w, st);
-                launch_norm2(w, n, s->w_red.p, s->w_cnt.p, hn_dev, st);
+                launch_multiaxpy_norm(n, k + 1, V, h2, -1.0, w, s->w_red.p, s->w_cnt.p, hn_dev, st);
                 double *hh = (double *)ctx->pinned.get(sizeof(double) * (2 * (m + 1) + 1));
                 MS_CUDA(cudaMemcpyAsync(hh, h1, sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost, st));
                 sync(st);

@@ -461,6 +461,9 @@ void launch_transport_substep(const ms_system &s, const double fl[6], const doub
                               const double *S, double *fw, double *Snew, double h_over_pv, cudaStream_t st);
 void launch_multidot(int n, int k, const double *V, const double *w, double *red, unsigned int *cnt, double *h,
                      cudaStream_t st);
+// the same, then ||y||_2 into norm_out (red: at least ceil(n / 256) partials)
+void launch_multiaxpy_norm(int n, int k, const double *V, const double *c, double sign, double *y, double *red,
+                           unsigned int *cnt, double *norm_out, cudaStream_t st);
 void launch_multiaxpy(int n, int k, const double *V, const double *c, double sign, double *y, cudaStream_t st,
                       const int *kdev = nullptr);
 // GMRES state on the device (graph-driven solves): Hessenberg matrix

@@ -293,6 +293,32 @@ def test_graph_cycles_match_host_cycles(ms, ctx, monkeypatch, precision, case):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_gmres_mid_size_grid(ms, ctx, precision):
+    """A 40x40x20 grid (32,000 cells): the kernels that end in a reduction
+    (residual, norm, the last Gram-Schmidt pass with the new vector's norm)
+    launch at most one block per 256 rows, the size of the partial-sum
+    buffer; the solve reaches the direct solution."""
+    import scipy.sparse.linalg as spla
+    gm = G.lognormal_box(40, 40, 20, seed=5, block=(10, 10, 5), kz_ratio=0.1)
+    prec = ms.MS_PREC_FP64 if precision == "fp64" else ms.MS_PREC_MIXED
+    s = _system(ms, ctx, gm)
+    part, M = ms.ms_partition_cartesian(ctx, s, gm.block)
+    b, _ = ms.ms_build_basis(ctx, s, part, M, block=gm.block, precision=prec)
+    c = ms.ms_galerkin(ctx, s, b, prec)
+    q = gm.q_active()
+    p = np.zeros_like(q)
+    info = ms.ms_solve(ctx, s, [c], q, p, tol=1e-8, max_iter=500, precision=prec, outer=ms.MS_OUTER_GMRES)
+    assert info["converged"]
+    ref = O.assemble_tpfa(gm.grid, gm.perm)
+    Ap, qp = O.pin(ref.A, q, 0)
+    xd = spla.spsolve(Ap.to_scipy().tocsc(), qp)
+    assert np.linalg.norm(p - xd) <= 1e-5 * np.linalg.norm(xd)
+    ms.ms_coarse_release(c)
+    ms.ms_basis_release(b)
+    ms.ms_system_release(s)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("restart", [30, 5])
 def test_graph_gmres_matches_host_gmres(ms, ctx, monkeypatch, precision, restart):
     """Flexible GMRES run as one CUDA graph (a while node over restarts, one
