@@ -410,41 +410,67 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_sweep(int n, int nseg, int 
                     }
             }
         }
-        // couplings leaving the segment, in slot order, by groups of four: poll
-        // the tagged words of every coupling of the group until all carry this
-        // sweep's tag, then subtract the products
+        __syncwarp();
+        // each lane's run of rows (contiguous); the products of the chain
+        // coefficients the composition and the shuffle scan need depend only on
+        // the factor, so they are formed here, before the couplings arrive:
+        // the lane's product and the running product before each scan level
+        const int C = (len + 31) >> 5;
+        const int lo = lane * C, cnt = max(0, min(C, len - lo));
+        T Am[5];
+        {
+            T A = T(1);   // in the order the rows are composed
+            if (!BWD) {
+                for (int c = 0; c < cnt; ++c) A *= sa[lo + c];
+            } else {
+                for (int c = cnt - 1; c >= 0; --c) A *= sa[lo + c];
+            }
 #pragma unroll
-        for (int q0 = 0; q0 < KG; q0 += 4) {
-            T xv[kSegPer][4];
-            int jv[kSegPer][4];
+            for (int d = 1, lv = 0; d < 32; d <<= 1, ++lv) {
+                Am[lv] = A;
+                const T Ap = BWD ? __shfl_down_sync(0xffffffffu, A, d) : __shfl_up_sync(0xffffffffu, A, d);
+                if (BWD ? lane + d < 32 : lane >= d) A *= Ap;
+            }
+        }
+        // couplings leaving the segment, in slot order: poll the tagged words of
+        // every coupling of the lane's rows in one round of loads until all
+        // carry this sweep's tag, then subtract the products
+        {
+            static_assert(kSegPer * KG <= 32, "pending couplings fit one mask");
+            T xv[kSegPer][KG];
+            int jv[kSegPer][KG];
             unsigned pend = 0u;
+            int qn = 0;   // couplings fill slots from 0: the largest count of the warp's rows
 #pragma unroll
             for (int c = 0; c < kSegPer; ++c)
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int q = q0 + u, p = c * 32 + lane;
-                    jv[c][u] = (q < KG && q < kg && p < len) ? sc[q * kSegMax + p] : -1;
-                    xv[c][u] = T(0);
-                    if (jv[c][u] >= 0) pend |= 1u << (c * 4 + u);
+                for (int q = 0; q < KG; ++q) {
+                    const int p = c * 32 + lane;
+                    jv[c][q] = (q < kg && p < len) ? sc[q * kSegMax + p] : -1;
+                    xv[c][q] = T(0);
+                    if (jv[c][q] >= 0) {
+                        pend |= 1u << (c * KG + q);
+                        qn = max(qn, q + 1);
+                    }
                 }
+            qn = (int)__reduce_max_sync(0xffffffffu, (unsigned)qn);
             unsigned long long t0 = 0;
             for (int spins = 0; pend && !failed; ++spins) {
                 // all loads of the round first, then the tag checks
-                SegWord<T> wv[kSegPer][4];
+                SegWord<T> wv[kSegPer][KG];
 #pragma unroll
                 for (int c = 0; c < kSegPer; ++c)
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if ((pend >> (c * 4 + u)) & 1u) wv[c][u] = seg_load<T>(tw, jv[c][u]);
+                    for (int q = 0; q < KG; ++q)
+                        if ((pend >> (c * KG + q)) & 1u) wv[c][q] = seg_load<T>(tw, jv[c][q]);
                 const unsigned was = pend;
 #pragma unroll
                 for (int c = 0; c < kSegPer; ++c)
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if ((was >> (c * 4 + u)) & 1u)
-                            if (seg_check<T>(wv[c][u], tg, xv[c][u])) pend &= ~(1u << (c * 4 + u));
+                    for (int q = 0; q < KG; ++q)
+                        if ((was >> (c * KG + q)) & 1u)
+                            if (seg_check<T>(wv[c][q], tg, xv[c][q])) pend &= ~(1u << (c * KG + q));
                 if (!pend) break;
-                if (spins > 8) __nanosleep(32);
                 if ((spins & 31) == 31) {
                     if (*((volatile int *)&sync[3]) != 0) failed = true;
                     const unsigned long long now = gs_now_ns();
@@ -455,14 +481,16 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_sweep(int n, int nseg, int 
                     }
                 }
             }
+            // only the slots some row of the warp uses (an FP64 instruction takes
+            // the pipe for the whole warp, padding lanes included)
 #pragma unroll
             for (int c = 0; c < kSegPer; ++c) {
                 const int p = c * 32 + lane;
                 if (p < len) {
                     T s = sb[p];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (q0 + u < KG && q0 + u < kg) s -= sv[(q0 + u) * kSegMax + p] * xv[c][u];
+                    for (int q = 0; q < KG; ++q)
+                        if (q < qn) s -= sv[q * kSegMax + p] * xv[c][q];
                     sb[p] = s;
                 }
             }
@@ -475,11 +503,9 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_sweep(int n, int nseg, int 
             }
         }
         __syncwarp();
-        // each lane's run of rows: compose its maps, scan the compositions
-        // across the warp, apply
-        const int C = (len + 31) >> 5;
-        const int lo = lane * C, cnt = max(0, min(C, len - lo));
-        T A = T(1), Bc = T(0);
+        // compose the lane's maps (offsets only), scan the compositions across
+        // the warp with the products formed above, apply
+        T Bc = T(0);
         T av[kSegPer], bv[kSegPer];
         if constexpr (sizeof(T) == 4) {   // rows held in registers
 #pragma unroll
@@ -490,26 +516,19 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_sweep(int n, int nseg, int 
 #pragma unroll
             for (int k = 0; k < kSegPer; ++k) {
                 const int c = BWD ? kSegPer - 1 - k : k;
-                if (c < cnt) {
-                    Bc = seg_fma(av[c], Bc, bv[c]);
-                    A *= av[c];
-                }
+                if (c < cnt) Bc = seg_fma(av[c], Bc, bv[c]);
             }
         } else {                          // rows read from shared memory
             if (!BWD) {
-                for (int c = 0; c < cnt; ++c) { Bc = seg_fma(sa[lo + c], Bc, sb[lo + c]); A *= sa[lo + c]; }
+                for (int c = 0; c < cnt; ++c) Bc = seg_fma(sa[lo + c], Bc, sb[lo + c]);
             } else {
-                for (int c = cnt - 1; c >= 0; --c) { Bc = seg_fma(sa[lo + c], Bc, sb[lo + c]); A *= sa[lo + c]; }
+                for (int c = cnt - 1; c >= 0; --c) Bc = seg_fma(sa[lo + c], Bc, sb[lo + c]);
             }
         }
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const T Ap = BWD ? __shfl_down_sync(0xffffffffu, A, d) : __shfl_up_sync(0xffffffffu, A, d);
+        for (int d = 1, lv = 0; d < 32; d <<= 1, ++lv) {
             const T Bp = BWD ? __shfl_down_sync(0xffffffffu, Bc, d) : __shfl_up_sync(0xffffffffu, Bc, d);
-            if (BWD ? lane + d < 32 : lane >= d) {
-                Bc = seg_fma(A, Bp, Bc);
-                A *= Ap;
-            }
+            if (BWD ? lane + d < 32 : lane >= d) Bc = seg_fma(Am[lv], Bp, Bc);
         }
         T x = BWD ? __shfl_down_sync(0xffffffffu, Bc, 1) : __shfl_up_sync(0xffffffffu, Bc, 1);
         if (BWD ? lane == 31 : lane == 0) x = T(0);

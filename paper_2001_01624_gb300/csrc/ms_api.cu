@@ -701,7 +701,7 @@ ms_status ms_plan_segments(ms_ctx *ctx, int32_t n, const int32_t *rowptr, const 
     if (!rowptr || !col || !seg_off || !n_seg || !order || !kg || !width)
         return fail(ctx, MS_ERR_INVALID_ARG, "null argument");
     if (n < 1) return fail(ctx, MS_ERR_INVALID_ARG, "n must be >= 1");
-    if (max_len < 1 || max_len > kSegMax) return fail(ctx, MS_ERR_INVALID_ARG, "max_len must be in 1..256");
+    if (max_len < 1 || max_len > kSegPlanMax) return fail(ctx, MS_ERR_INVALID_ARG, "max_len must be in 1..256");
     API_TRY
     MS_REQUIRE(rowptr[0] == 0, MS_ERR_INVALID_ARG, "rowptr[0] must be 0");
     std::vector<int> deg(n + 1, 0), nb, rowlen(n);

@@ -111,7 +111,8 @@ __device__ __forceinline__ unsigned long long wait_limit_ns(const int *errw) {
     return us > 0 ? (unsigned long long)us * 1000ull : kDefaultWaitNs;
 }
 #endif
-constexpr int kSegMax = 256;       // rows per segment of the segment sweeps (8 per lane)
+constexpr int kSegMax = 64;        // rows per segment of the segment sweeps (2 per lane)
+constexpr int kSegPlanMax = 256;   // longest run the host analysis entry point accepts
 constexpr int kSegMaxKG = 8;       // couplings per row leaving its segment, per direction
 constexpr int kErrTimeout = 1;
 constexpr int kErrSingular = 2;
