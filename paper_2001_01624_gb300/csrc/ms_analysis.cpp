@@ -230,6 +230,8 @@ void analyse_grid(ms_system &s, const ms_grid &g) {
     std::vector<int> rf_ptr(s.n + 1, 0), rf_face(2 * (size_t)s.nf);
     std::vector<uint8_t> rf_slot(2 * (size_t)s.nf);
     for (const Conn &c : conns) { rf_ptr[c.a + 1]++; rf_ptr[c.b + 1]++; }
+    s.rf_max = 0;
+    for (int i = 0; i < s.n; ++i) s.rf_max = std::max(s.rf_max, rf_ptr[i + 1]);   // counts, before the scan
     for (int i = 0; i < s.n; ++i) rf_ptr[i + 1] += rf_ptr[i];
     {
         std::vector<int> fill(rf_ptr.begin(), rf_ptr.end() - 1);

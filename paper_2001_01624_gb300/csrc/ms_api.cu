@@ -1734,13 +1734,18 @@ ms_status ms_transport_step(ms_ctx *ctx, ms_system *s, const ms_fluid *fl, const
         nsub = std::max(1, (int)k);
     }
     const double hs = dt / nsub;
-    for (int k = 0; k < nsub; ++k) {
-        launch_transport_substep(*s, par, s->w_tu.p, qd, S0, fw, S1, hs / pv, st);
-        std::swap(S0, S1);
-    }
+    // the upstream weights once, then every substep (one launch where the
+    // grid can be resident at once)
+    launch_transport_coef(*s, s->w_tu.p, qd, st);
+    launch_transport_run(*s, par, nsub, hs / pv, S0, S1, fw, st);
     MS_CUDA(cudaMemcpyAsync(S, S0, n * sizeof(double), is_device_ptr(S) ? cudaMemcpyDeviceToDevice
                                                                          : cudaMemcpyDeviceToHost, st));
     sync(st);
+    if (const int e = read_error_word(ctx, s->sync.p + 3)) {
+        MS_CUDA(cudaMemsetAsync(s->sync.p + 3, 0, sizeof(int), st));
+        s->tbar_ready = false;   // a barrier that gave up: the counters start afresh next time
+        throw Error{(e & kErrTimeout) ? MS_ERR_TIMEOUT : MS_ERR_CUDA, "a transport substep barrier wait ran out"};
+    }
     if (substeps) *substeps = nsub;
     return MS_OK;
     API_CATCH(ctx)

@@ -305,6 +305,11 @@ struct ms_system {
     msgb::DBuf<unsigned long long> w_kgh;     //   and the handles of its conditional steps
     msgb::DBuf<unsigned int> w_kcnt;
     msgb::DBuf<double> w_tu, w_ts, w_tq;      // transport: face fluxes, saturation buffer, sources
+    msgb::DBuf<double> w_tc;                  //   upstream weights of a step: src [n], dg [n], inflow fluxes [W][n]
+    msgb::DBuf<int> w_tci;                    //   inflow counts [n], upstream cells [W][n]
+    msgb::DBuf<unsigned long long> w_tbar;    //   grid barrier of the one-launch substeps
+    bool tbar_ready = false;
+    int rf_max = 0;                           // most faces of one cell
     msgb::DBuf<double> w_red;                 // reduction partials
     msgb::DBuf<unsigned int> w_cnt;           // reduction counters
     msgb::DBuf<unsigned long long> w_max;     // max reductions
@@ -458,8 +463,13 @@ void launch_total_mobility(int n, const double fl[6], const double *S, double *l
 void launch_face_flux(const ms_system &s, const double *p, double *u, cudaStream_t st);
 void launch_outflow_limit(const ms_system &s, const double *u, const double *q, double pore_volume,
                           unsigned long long *min_bits, cudaStream_t st);
-void launch_transport_substep(const ms_system &s, const double fl[6], const double *u, const double *q,
-                              const double *S, double *fw, double *Snew, double h_over_pv, cudaStream_t st);
+// one transport step's upstream weights (fluxes u, sources q fixed over its substeps)
+void launch_transport_coef(ms_system &s, const double *u, const double *q, cudaStream_t st);
+// nsub substeps from S (in place), fractional flows through fwa / fwb; one
+// cooperative launch with a grid barrier per substep (MSGB_TRANSPORT_COOP=0:
+// one launch per substep)
+void launch_transport_run(ms_system &s, const double fl[6], int nsub, double h_over_pv, double *S, double *fwa,
+                          double *fwb, cudaStream_t st);
 void launch_multidot(int n, int k, const double *V, const double *w, double *red, unsigned int *cnt, double *h,
                      cudaStream_t st);
 // the same, then ||y||_2 into norm_out (red: at least ceil(n / 256) partials)

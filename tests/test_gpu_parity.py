@@ -694,7 +694,14 @@ def test_ilu_apply_full_size_config2(ms, ctx):
 
 # ---------------------------------------------------------------- two-phase
 @pytest.mark.parametrize("case", ["3d_10x10x4", "faulted_18x14x7"])
-def test_mobility_and_transport_match_oracle(ms, ctx, case):
+@pytest.mark.parametrize("coop", ["1", "0"])
+def test_mobility_and_transport_match_oracle(ms, ctx, monkeypatch, case, coop):
+    """Total mobility, and one explicit upstream transport step over many CFL
+    substeps: the upstream weights formed once per step, then every substep in
+    one cooperative launch with a grid barrier between substeps (coop 1) or one
+    launch per substep (coop 0); the substep count and saturations match the
+    oracle's face-by-face substeps."""
+    monkeypatch.setenv("MSGB_TRANSPORT_COOP", coop)
     gm = CASES[case]()
     n = gm.grid.n_active()
     rng = np.random.default_rng(11)
@@ -715,6 +722,12 @@ def test_mobility_and_transport_match_oracle(ms, ctx, case):
     S_ref, k_ref = O.transport_step(ref.A, p, q, S, dt, porosity=0.2, volume=vol, cfl=0.9)
     assert k == k_ref and k > 1
     np.testing.assert_allclose(S_gpu, S_ref, rtol=1e-11, atol=1e-12)
+    # a second step from there (the barrier counters carry over between launches)
+    S2 = S_gpu.copy()
+    k2 = ms.ms_transport_step(ctx, s, fl, p, q, dt, S2)
+    S2_ref, k2_ref = O.transport_step(ref.A, p, q, S_ref, dt, porosity=0.2, volume=vol, cfl=0.9)
+    assert k2 == k2_ref
+    np.testing.assert_allclose(S2, S2_ref, rtol=1e-10, atol=1e-12)
     ms.ms_system_release(s)
 
 
