@@ -14,6 +14,8 @@
 // merge of the slot lists of the cell and its neighbours; then row j of
 // A_c = P^T (A P) is accumulated by one warp over the support of block j in
 // shared memory, in a fixed order (deterministic), and A_c is symmetrised.
+#include <cstdlib>
+
 #include "ms_internal.h"
 #include "msrsb_cell.cuh"
 
@@ -74,7 +76,7 @@ __global__ void __launch_bounds__(kThreads) k_msrsb(int n, int W, int B, const i
                 }
             }
         }
-        // omega / A_ii precomputed per smoothing run; one division for the
+        // omega / A_ii precomputed per smoothing run; one reciprocal for the
         // partition-of-unity scale
         const T od = odiag[i];
         T sum = 0;
@@ -85,7 +87,9 @@ __global__ void __launch_bounds__(kThreads) k_msrsb(int n, int W, int B, const i
                 sum += acc[s];
             }
         }
-        const T rs = T(1) / sum;
+        T rs;
+        if constexpr (sizeof(T) == 8) rs = recip_series(sum);
+        else rs = T(1) / sum;
 #pragma unroll
         for (int s = 0; s < BM; ++s) {
             if (ids[s] != kSlotPad) {
@@ -144,6 +148,50 @@ __global__ void k_basis_maps(int n, int W, int B, const int *__restrict__ col, c
     }
 }
 
+// The smoothing's cell order: window w of kOrderWin cells (one CTA of 1024
+// threads, 4 consecutive cells each) lists its cells by descending slot
+// count, keeping the cell order within a count (a counting sort: one
+// block-wide exclusive scan per count).
+__global__ void __launch_bounds__(1024) k_slot_order(int n, const unsigned char *__restrict__ nslots,
+                                                     int *__restrict__ order) {
+    __shared__ int wsum[32];
+    __shared__ int base;
+    const int w0 = blockIdx.x * kOrderWin;
+    const int c0 = w0 + 4 * threadIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int cc[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) cc[e] = c0 + e < n ? (int)nslots[c0 + e] : -1;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int c = 8; c >= 0; --c) {
+        int mine = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) mine += cc[e] == c;
+        int inc = mine;   // inclusive warp scan
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += v;
+        }
+        if (lane == 31) wsum[wid] = inc;
+        __syncthreads();
+        int before = base;
+        for (int q = 0; q < wid; ++q) before += wsum[q];
+        int at = before + inc - mine;
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (cc[e] == c) order[w0 + at++] = c0 + e;
+        __syncthreads();   // every thread has read base and wsum
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int q = 0; q < 32; ++q) tot += wsum[q];
+            base += tot;
+        }
+        __syncthreads();
+    }
+}
+
 // MsRSB iteration with precomputed neighbour slot maps (B <= 8): every
 // neighbour contribution is an independent load.  FP64: the rows come
 // prescaled by omega / A_ii (diag and off hold 1 - omega-scaled diagonal and
@@ -156,13 +204,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 3) k_msrsb_mapp
                                                            const unsigned *__restrict__ nmap,
                                                            const unsigned char *__restrict__ nslots, T *bufA,
                                                            T *bufB, const T *__restrict__ odiag,
-                                                           unsigned long long *ctl) {
+                                                           unsigned long long *ctl, const int *__restrict__ order) {
     if (*(volatile const unsigned long long *)ctl) return;   // smoothing finished: no-op
     const bool odd = ctl[1] & 1ull;                            // iterations done so far
     const T *__restrict__ pin = odd ? bufB : bufA;
     T *__restrict__ pout = odd ? bufA : bufB;
     unsigned long long *maxinc = ctl + 2;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = order != nullptr && tix < n ? order[tix] : tix;   // the cell this thread updates
     const int cnt = i < n ? (int)nslots[i] : 0;
     unsigned long long inck = 0ull;   // key of the largest |increment|
     if constexpr (sizeof(T) == 8) {   // prescaled rows (one multiply-add less per entry)
@@ -364,6 +413,9 @@ void launch_basis_maps(const ms_system &s, ms_basis &b, cudaStream_t st) {
     b.nslots.alloc(s.n);
     k_basis_maps<<<blocks_for(s.n), kThreads, 0, st>>>(s.n, s.W, b.B, s.col.p, b.pid.p, b.nmap.p, b.nslots.p);
     MS_CHECK_LAUNCH();
+    b.order.alloc(s.n);
+    k_slot_order<<<(s.n + kOrderWin - 1) / kOrderWin, 1024, 0, st>>>(s.n, b.nslots.p, b.order.p);
+    MS_CHECK_LAUNCH();
     b.has_map = true;
 }
 
@@ -387,22 +439,25 @@ static void msrsb_dispatch(const ms_system &s, const ms_basis &b, const int *pid
                         (double)s.n * (2 * sizeof(T) + 1) + (double)s.W * s.n * (4 + sizeof(T) + 4) +
                             (double)b.nnz * 2 * sizeof(T));
         // maxinc: the control block.  FP64 takes the prescaled rows.
+        const int *order = nullptr;   // FP64: cells by slot count within windows
         if constexpr (sizeof(T) == 8) {
             off = b.pre_w64.p;
             diag = b.pre_c64.p;
+            const char *e = std::getenv("MSGB_SMOOTH_ORDER");   // "0": natural cell order
+            if (!(e && e[0] == '0')) order = b.order.p;
         }
         if (s.W <= 4)
             k_msrsb_mapped<T, 4><<<g, kThreads, 0, st>>>(s.n, s.W, s.col.p, off, diag, b.nmap.p, b.nslots.p, pin,
-                                                         pout, omega, maxinc);
+                                                         pout, omega, maxinc, order);
         else if (s.W <= 6)
             k_msrsb_mapped<T, 6><<<g, kThreads, 0, st>>>(s.n, s.W, s.col.p, off, diag, b.nmap.p, b.nslots.p, pin,
-                                                         pout, omega, maxinc);
+                                                         pout, omega, maxinc, order);
         else if (s.W <= 8)
             k_msrsb_mapped<T, 8><<<g, kThreads, 0, st>>>(s.n, s.W, s.col.p, off, diag, b.nmap.p, b.nslots.p, pin,
-                                                         pout, omega, maxinc);
+                                                         pout, omega, maxinc, order);
         else
             k_msrsb_mapped<T, 0><<<g, kThreads, 0, st>>>(s.n, s.W, s.col.p, off, diag, b.nmap.p, b.nslots.p, pin,
-                                                         pout, omega, maxinc);
+                                                         pout, omega, maxinc, order);
         MS_CHECK_LAUNCH();
         return;
     }

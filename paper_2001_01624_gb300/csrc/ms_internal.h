@@ -346,6 +346,11 @@ struct ms_basis {
     bool has_map = false;
     msgb::DBuf<unsigned> nmap;
     msgb::DBuf<unsigned char> nslots;    // number of real slots of each cell
+    // cells in the order the FP64 smoothing takes them: within each window of
+    // kOrderWin cells, by descending slot count (stable), so that the lanes
+    // of a warp mostly share a slot count (a multiply-add that only some
+    // lanes need still takes the FP64 pipe for all 32)
+    msgb::DBuf<int> order;
     // column chunks: each support cut into pieces of at most kColChunk entries
     // (chunk c covers entries [ch_beg[c], min(ch_beg[c] + kColChunk, cptr[j+1]))
     // of column j = ch_col[c]; column j owns chunks [ch_ptr[j], ch_ptr[j+1]));
@@ -357,6 +362,7 @@ struct ms_basis {
     msgb::DBuf<unsigned> ch_cnt;         // per-column arrival counters (back to 0 after each use)
 };
 constexpr int kColChunk = 1024;
+constexpr int kOrderWin = 4096;   // window of the smoothing's cell order (1024 threads x 4 cells)
 
 struct ms_coarse {
     int M = 0;

@@ -46,6 +46,28 @@ __device__ __forceinline__ T ldp(const T *p) {
     else return *p;
 }
 
+// 1 / x for a normal x of magnitude below 2^1021: a seed from the FP32
+// reciprocal of x's mantissa (exponent and sign set by integer arithmetic, so
+// no conversion runs on the FP64 pipe), then one third-order step of the
+// series 1 / x = r0 / (1 - e) = r0 (1 + e + e^2 + ...), e = 1 - x r0: with
+// |e| below 2^-21 the truncation error e^3 is below 2^-63 relative.  Other
+// x take the division.
+__device__ __forceinline__ double recip_series(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32);
+    const int ex = (int)((hi >> 20) & 0x7ffu);
+    if (ex == 0 || ex >= 0x7fd) return 1.0 / x;
+    const float m = __uint_as_float(0x3f800000u | ((hi & 0xfffffu) << 3) | (unsigned)((b >> 29) & 7u));
+    float rm;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rm) : "f"(m));   // 1 / m in (0.5, 1]
+    const unsigned rb = __float_as_uint(rm);
+    const long long de = (long long)(((int)((rb >> 23) & 0xffu) - 127) - (ex - 1023) + 1023);   // in [1, 2045]
+    const double r0 = __longlong_as_double((long long)((b & 0x8000000000000000ull) | ((unsigned long long)de << 52) |
+                                                       ((unsigned long long)(rb & 0x7fffffu) << 29)));
+    const double e = fma(-x, r0, 1.0);
+    return fma(r0, fma(e, e, e), r0);
+}
+
 // One cell of the MsRSB iteration with precomputed neighbour slot maps,
 // slots below SB (at least the cell's count); returns the key of its largest
 // |increment|.
@@ -104,7 +126,7 @@ __device__ __forceinline__ unsigned long long msrsb_cell(int i, int cnt, int n, 
             }
         }
     }
-    // omega / A_ii precomputed per smoothing run; one division for the
+    // omega / A_ii precomputed per smoothing run; one reciprocal for the
     // partition-of-unity scale
     T sum = 0;
     if (PRE) {
@@ -120,7 +142,9 @@ __device__ __forceinline__ unsigned long long msrsb_cell(int i, int cnt, int n, 
                 sum += acc[s];
             }
     }
-    const T rs = T(1) / sum;
+    T rs;
+    if constexpr (sizeof(T) == 8) rs = recip_series(sum);
+    else rs = T(1) / sum;
 #pragma unroll
     for (int s = 0; s < SB; ++s)
         if (s < cnt) {

@@ -200,6 +200,38 @@ def test_basis_update_continues_smoothing(ms, ctx):
     ms.ms_system_release(s)
 
 
+@pytest.mark.parametrize("rule", ["box", "hop"])
+def test_basis_cell_order_windows(ms, ctx, monkeypatch, rule):
+    """The FP64 smoothing takes its cells by slot count within windows of
+    4096 cells: 41x23x9 spans two full windows and a ragged one.  The values
+    and the iteration count are those of the natural cell order, bit for bit,
+    and those of the oracle."""
+    gm = G.lognormal_box(41, 23, 9, seed=33, block=(5, 4, 3), kz_ratio=0.1)
+    s = _system(ms, ctx, gm)
+    part, M = ms.ms_partition_cartesian(ctx, s, gm.block)
+    sup = ms.MS_SUPPORT_BOX if rule == "box" else ms.MS_SUPPORT_HOP
+    got = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("MSGB_SMOOTH_ORDER", flag)
+        b, it = ms.ms_build_basis(ctx, s, part, M, support=sup, block=gm.block)
+        got[flag] = (it, ms.ms_basis_get(ctx, b))
+        ms.ms_basis_release(b)
+    monkeypatch.delenv("MSGB_SMOOTH_ORDER")
+    (it1, (cp1, ce1, v1)), (it0, (cp0, ce0, v0)) = got["1"], got["0"]
+    assert it1 == it0
+    assert np.array_equal(cp1, cp0) and np.array_equal(ce1, ce0)
+    assert np.array_equal(v1.view(np.int64), v0.view(np.int64))
+    ref = O.assemble_tpfa(gm.grid, gm.perm)
+    if rule == "box":
+        sp, sc = O.support_box(gm.grid, ref.cells, ref.A, part, M, gm.block)
+    else:
+        sp, sc = O.support_hop(gm.grid, ref.cells, ref.A, part, M)
+    B = O.msrsb_basis(ref.A, part, M, sp, sc)
+    assert it1 == B.iters
+    np.testing.assert_allclose(v1, B.pval, rtol=0, atol=1e-12)
+    ms.ms_system_release(s)
+
+
 # -------------------------------------------------------------------- solve
 def _oracle_general(gm, rule="box"):
     return O.setup_general(gm, support=rule)
