@@ -557,28 +557,10 @@ __global__ void __launch_bounds__(32 * kSegMaxWarps, 1)
                     for (int e = 0; e < SE; ++e) val[e] = P[e] * c + val[e];
                     if (gl == 0) prog_put(prv_cprog, xtag);
                 }
-                // the value leaving the segment, to segment s + 1 (its last lane's last cell)
-                bool okc = true;
-                if (has_cout && gl == 31) {
-                    if (tj >= PP * SNC) okc = prog_wait(my_cprog, (unsigned)(tj - PP * SNC + 1), cseen, err);
-                    if (okc) {
-                        unsigned long long cw[2];
-                        if constexpr (RW == 2) {
-                            const unsigned long long b = (unsigned long long)__double_as_longlong((double)val[SE - 1]);
-                            cw[0] = tw_lo((unsigned)(b & 0xffffffffull), xtag);
-                            cw[1] = tw_lo((unsigned)(b >> 32), xtag);
-                        } else {
-                            cw[0] = cw[1] = tw_lo(__float_as_uint((float)val[SE - 1]), xtag);
-                        }
-                        tw_put2(nxt_c + (unsigned)(((tj / PP) % SNC) * 16), cw[0], cw[1]);
-                    }
-                }
-                if (!__all_sync(FULL, okc)) {
-                    done = false;
-                    break;
-                }
                 // this line to the other phase (its next line's j-neighbour), then
-                // to the next row
+                // to the next row, ahead of the carry: a row waits on the row
+                // before it once per row, on the segment before it only once
+                // per row of segments
                 if (PP > 1 && tj + 1 < Ny) {
                     unsigned long long wv[NW];
                     tw_encode(val, xtag, wv);
@@ -604,6 +586,26 @@ __global__ void __launch_bounds__(32 * kSegMaxWarps, 1)
                         tw_put2(a, wv[0], wv[1]);
                         if constexpr (NW == 4) tw_put2(a + 16, wv[2], wv[3]);
                     }
+                }
+                // the value leaving the segment, to segment s + 1 (its last lane's last cell)
+                bool okc = true;
+                if (has_cout && gl == 31) {
+                    if (tj >= PP * SNC) okc = prog_wait(my_cprog, (unsigned)(tj - PP * SNC + 1), cseen, err);
+                    if (okc) {
+                        unsigned long long cw[2];
+                        if constexpr (RW == 2) {
+                            const unsigned long long b = (unsigned long long)__double_as_longlong((double)val[SE - 1]);
+                            cw[0] = tw_lo((unsigned)(b & 0xffffffffull), xtag);
+                            cw[1] = tw_lo((unsigned)(b >> 32), xtag);
+                        } else {
+                            cw[0] = cw[1] = tw_lo(__float_as_uint((float)val[SE - 1]), xtag);
+                        }
+                        tw_put2(nxt_c + (unsigned)(((tj / PP) % SNC) * 16), cw[0], cw[1]);
+                    }
+                }
+                if (!__all_sync(FULL, okc)) {
+                    done = false;
+                    break;
                 }
                 T *ob = out + rowbase + (long long)Lx * j;
 #pragma unroll
