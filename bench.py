@@ -159,12 +159,15 @@ def ncu_traffic(kernel):
         return None
     for ln in open(path):
         f = ln.split()
-        if len(f) >= 4 and f[0] == kernel:
-            src = os.path.join(ROOT, "paper_2001_01624_gb300", "csrc", f[2])
-            if not os.path.exists(src):
-                return None
-            h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-            return float(f[1]) if h == f[3] else None
+        if len(f) >= 4 and len(f) % 2 == 0 and f[0] == kernel:
+            # then one or more (source file, sha256[:16] at capture) pairs
+            for name, sha in zip(f[2::2], f[3::2]):
+                src = os.path.join(ROOT, "paper_2001_01624_gb300", "csrc", name)
+                if not os.path.exists(src):
+                    return None
+                if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != sha:
+                    return None
+            return float(f[1])
     return None
 
 

@@ -538,10 +538,11 @@ __global__ void __launch_bounds__(32 * kSegMaxWarps, 1)
                 if (gl == 0) vin = T(0);
                 T val[SE];
 #pragma unroll
-                for (int e = 0; e < SE; ++e) {
+                for (int e = 0; e < SE - 1; ++e) {
                     vin = A[e] * vin + B[e];
                     val[e] = vin;
                 }
+                val[SE - 1] = LB;   // the scan's value at the lane's last cell (one dependent step fewer)
                 // the value entering the segment, from segment s - 1 of this line
                 if (has_cin) {
                     unsigned long long cw[2];

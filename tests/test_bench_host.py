@@ -30,13 +30,27 @@ def test_traffic_taken_only_for_the_captured_source(tmp_path, monkeypatch):
     assert bench.ncu_traffic("demo") is None                   # source changed since the capture
 
 
+def test_traffic_keyed_by_every_listed_source(tmp_path, monkeypatch):
+    import hashlib
+    src, hdr = "__global__ void k() {}\n", "// cell update\n"
+    sha = lambda s: hashlib.sha256(s.encode()).hexdigest()[:16]
+    _tree(tmp_path, src, f"demo 77 k_demo.cu {sha(src)} cell.cuh {sha(hdr)}")
+    (tmp_path / "paper_2001_01624_gb300" / "csrc" / "cell.cuh").write_text(hdr)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.ncu_traffic("demo") == 77.0
+    (tmp_path / "paper_2001_01624_gb300" / "csrc" / "cell.cuh").write_text(hdr + "// changed\n")
+    assert bench.ncu_traffic("demo") is None                   # the header changed since the capture
+
+
 def test_committed_traffic_lines_parse():
     for ln in open(os.path.join(ROOT, "profiles", "ncu_traffic.txt")):
         f = ln.split()
         if ln.startswith("#") or not f:
             continue
-        assert len(f) == 4 and float(f[1]) > 0 and len(f[3]) == 16
-        assert os.path.exists(os.path.join(ROOT, "paper_2001_01624_gb300", "csrc", f[2]))
+        assert len(f) >= 4 and len(f) % 2 == 0 and float(f[1]) > 0
+        for name, sha in zip(f[2::2], f[3::2]):
+            assert len(sha) == 16
+            assert os.path.exists(os.path.join(ROOT, "paper_2001_01624_gb300", "csrc", name))
 
 
 def test_peak_fallback_without_measured_file(tmp_path, monkeypatch):
