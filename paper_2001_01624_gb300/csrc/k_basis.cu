@@ -193,11 +193,12 @@ __global__ void __launch_bounds__(1024) k_slot_order(int n, const unsigned char 
 }
 
 // MsRSB iteration with precomputed neighbour slot maps (B <= 8): every
-// neighbour contribution is an independent load.  FP64: the rows come
-// prescaled by omega / A_ii (diag and off hold 1 - omega-scaled diagonal and
-// the negated scaled off-diagonals), and the slot loops of a warp stop at the
-// largest slot count among its cells (2, 4 or 8), since a multiply-add that
-// only some lanes need still takes the FP64 pipe for all.
+// neighbour contribution is an independent load.  The slot loops of a warp
+// stop at the largest slot count among its cells (2, 4 or 8): in FP64 a
+// multiply-add that only some lanes need still takes the FP64 pipe for all,
+// in FP32 the warp issues fewer instructions.  FP64: the rows come prescaled
+// by omega / A_ii (diag and off hold 1 - omega-scaled diagonal and the negated
+// scaled off-diagonals).
 template <typename T, int WM>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 3) k_msrsb_mapped(int n, int W, const int *__restrict__ col,
                                                            const T *__restrict__ off, const T *__restrict__ diag,
@@ -214,15 +215,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 3) k_msrsb_mapp
     const int i = order != nullptr && tix < n ? order[tix] : tix;   // the cell this thread updates
     const int cnt = i < n ? (int)nslots[i] : 0;
     unsigned long long inck = 0ull;   // key of the largest |increment|
-    if constexpr (sizeof(T) == 8) {   // prescaled rows (one multiply-add less per entry)
-        const int cmax = __reduce_max_sync(0xffffffffu, cnt);
-        if (i < n) {
-            if (cmax <= 2) inck = msrsb_cell<T, WM, 2, true>(i, cnt, n, W, col, off, diag, nmap, pin, pout, odiag);
-            else if (cmax <= 4) inck = msrsb_cell<T, WM, 4, true>(i, cnt, n, W, col, off, diag, nmap, pin, pout, odiag);
-            else inck = msrsb_cell<T, WM, 8, true>(i, cnt, n, W, col, off, diag, nmap, pin, pout, odiag);
-        }
-    } else {
-        if (i < n) inck = msrsb_cell<T, WM, 8, false>(i, cnt, n, W, col, off, diag, nmap, pin, pout, odiag);
+    constexpr bool PRE = sizeof(T) == 8;   // FP64: prescaled rows (one multiply-add less per entry)
+    const int cmax = __reduce_max_sync(0xffffffffu, cnt);
+    if (i < n) {
+        if (cmax <= 2) inck = msrsb_cell<T, WM, 2, PRE>(i, cnt, n, W, col, off, diag, nmap, pin, pout, odiag);
+        else if (cmax <= 4) inck = msrsb_cell<T, WM, 4, PRE>(i, cnt, n, W, col, off, diag, nmap, pin, pout, odiag);
+        else inck = msrsb_cell<T, WM, 8, PRE>(i, cnt, n, W, col, off, diag, nmap, pin, pout, odiag);
     }
     __shared__ unsigned long long wmax[kThreads / 32];
     unsigned long long m = abs_key(key_value<T>(inck));   // key of the value as a double

@@ -146,19 +146,15 @@ __global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 6 : 3) k_msrsb_batch(con
         for (int b0 = i0; b0 < i1; b0 += kBT) {
             const int i = b0 + tid;
             const int cnt = i < i1 ? (int)J.nslots[i] : 0;
-            if constexpr (sizeof(T) == 8) {
-                const int cmax = __reduce_max_sync(0xffffffffu, cnt);
-                if (i < i1) {
-                    unsigned long long k;
-                    if (cmax <= 2) k = msrsb_cell<T, 8, 2, true, kLd>(i, cnt, J.n, J.W, J.col, J.off, J.diag, J.nmap, pin, pout, J.odiag);
-                    else if (cmax <= 4) k = msrsb_cell<T, 8, 4, true, kLd>(i, cnt, J.n, J.W, J.col, J.off, J.diag, J.nmap, pin, pout, J.odiag);
-                    else k = msrsb_cell<T, 8, 8, true, kLd>(i, cnt, J.n, J.W, J.col, J.off, J.diag, J.nmap, pin, pout, J.odiag);
-                    inck = max(inck, k);
-                }
-            } else {
-                if (i < i1)
-                    inck = max(inck, msrsb_cell<T, 8, 8, false, kLd>(i, cnt, J.n, J.W, J.col, J.off, J.diag, J.nmap, pin,
-                                                                      pout, J.odiag));
+            // slot loops bounded by the warp's largest slot count; FP64 rows prescaled
+            constexpr bool PRE = sizeof(T) == 8;
+            const int cmax = __reduce_max_sync(0xffffffffu, cnt);
+            if (i < i1) {
+                unsigned long long k;
+                if (cmax <= 2) k = msrsb_cell<T, 8, 2, PRE, kLd>(i, cnt, J.n, J.W, J.col, J.off, J.diag, J.nmap, pin, pout, J.odiag);
+                else if (cmax <= 4) k = msrsb_cell<T, 8, 4, PRE, kLd>(i, cnt, J.n, J.W, J.col, J.off, J.diag, J.nmap, pin, pout, J.odiag);
+                else k = msrsb_cell<T, 8, 8, PRE, kLd>(i, cnt, J.n, J.W, J.col, J.off, J.diag, J.nmap, pin, pout, J.odiag);
+                inck = max(inck, k);
             }
         }
         unsigned long long km = abs_key(key_value<T>(inck));   // key of the value as a double

@@ -735,11 +735,12 @@ bool seg_fits(const int dims[3], int S, int TK, int PP, int NK, int NC) {
 // rows per CTA (FP64 rows of several segments one per CTA, so no two rows'
 // FP64 scans share a sub-partition), and the clusters the rows span.
 bool plan_ilu_seg(ms_system &s, int p) {
-    // FP64 by default; MSGB_ILU_SEG=0 never, =2 both precisions (on the
-    // 60x220x85 grid the FP32 sweeps gain nothing: 0.128 against 0.12 ms)
+    // both precisions by default (on the 60x220x85 grid FP32 0.110 / 0.111 ms
+    // per forward / backward sweep against 0.123 / 0.119 ms with one warp per
+    // line); MSGB_ILU_SEG=0 never, =1 FP64 only
     const char *e = std::getenv("MSGB_ILU_SEG");
     if (e && e[0] == '0') return false;
-    if (p == 1 && !(e && e[0] == '2')) return false;
+    if (p == 1 && e && e[0] == '1') return false;
     // MSGB_SEG_LINES=x or =y forces the walked direction (y: where ny <= 256)
     const char *ld = std::getenv("MSGB_SEG_LINES");
     bool ylines = s.ny > s.nx && s.ny <= kMaxSeg * SLW;

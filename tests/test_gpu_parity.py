@@ -609,7 +609,7 @@ def test_cluster_ilu_sweeps(ms, ctx, monkeypatch, shape, lines, tk, kern):
     the next; cluster: one warp per line, 2, 4 and 8 cells per lane."""
     monkeypatch.setenv("MSGB_ILU_KERNEL", "cluster")
     if kern.startswith("seg"):
-        monkeypatch.setenv("MSGB_ILU_SEG", "2")
+        monkeypatch.delenv("MSGB_ILU_SEG", raising=False)   # both precisions segmented (the default)
         if kern != "seg":
             monkeypatch.setenv("MSGB_SEG_PP", kern[-1])
         monkeypatch.setenv("MSGB_SEG_LINES", lines)
