@@ -126,30 +126,51 @@ __global__ void k_row_assemble(int n, int W, int ref, const int *__restrict__ rf
 }
 
 // ------------------------------------------------------------- SpMV family
+// Row i of A v in slot order (diagonal first).  WM > 0: at most WM
+// connections, every column and coefficient loaded before the gathers, so a
+// row's loads are in flight together (the sum keeps its order).
+template <int WM>
+__device__ __forceinline__ double row_av(int n, int W, int i, const int *__restrict__ col,
+                                         const double *__restrict__ off, double d, const double *__restrict__ v) {
+    double s = d * v[i];
+    if constexpr (WM > 0) {
+        int c[WM];
+        double a[WM];
+#pragma unroll
+        for (int w = 0; w < WM; ++w) {
+            const int64_t at = (int64_t)w * n + i;
+            c[w] = w < W ? col[at] : i;
+            a[w] = w < W ? off[at] : 0.0;
+        }
+#pragma unroll
+        for (int w = 0; w < WM; ++w)
+            if (w < W) s += a[w] * v[c[w]];
+    } else {
+        for (int w = 0; w < W; ++w) {
+            const int64_t at = (int64_t)w * n + i;
+            s += off[at] * v[col[at]];
+        }
+    }
+    return s;
+}
+
+template <int WM>
 __global__ void k_spmv(int n, int W, const int *__restrict__ col, const double *__restrict__ off,
                        const double *__restrict__ diag, const double *__restrict__ x, double *__restrict__ y) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double s = diag[i] * x[i];
-    for (int w = 0; w < W; ++w) {
-        const int64_t at = (int64_t)w * n + i;
-        s += off[at] * x[col[at]];
-    }
-    y[i] = s;
+    y[i] = row_av<WM>(n, W, i, col, off, diag[i], x);
 }
 
 // r = q - A x and ||r||_2
+template <int WM>
 __global__ void k_residual(int n, int W, const int *__restrict__ col, const double *__restrict__ off,
                            const double *__restrict__ diag, const double *__restrict__ q,
                            const double *__restrict__ x, double *__restrict__ r, float *__restrict__ r32,
                            double *red, unsigned int *cnt, double *norm_out) {
     double ss = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double s = diag[i] * x[i];
-        for (int w = 0; w < W; ++w) {
-            const int64_t at = (int64_t)w * n + i;
-            s += off[at] * x[col[at]];
-        }
+        const double s = row_av<WM>(n, W, i, col, off, diag[i], x);
         const double ri = q[i] - s;
         r[i] = ri;
         if (r32) r32[i] = (float)ri;
@@ -159,17 +180,14 @@ __global__ void k_residual(int n, int W, const int *__restrict__ col, const doub
 }
 
 // r -= A z ; x += z   (after a smoother correction z)
+template <int WM>
 __global__ void k_residual_update(int n, int W, const int *__restrict__ col, const double *__restrict__ off,
                                   const double *__restrict__ diag, double *__restrict__ r, double *__restrict__ x,
                                   const double *__restrict__ z) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double zi = z[i];
-    double s = diag[i] * zi;
-    for (int w = 0; w < W; ++w) {
-        const int64_t at = (int64_t)w * n + i;
-        s += off[at] * z[col[at]];
-    }
+    const double s = row_av<WM>(n, W, i, col, off, diag[i], z);
     r[i] -= s;
     x[i] += zi;
 }
@@ -328,21 +346,27 @@ void launch_row_assemble(ms_system &s, cudaStream_t st) {
 
 void launch_spmv(const ms_system &s, const double *x, double *y, cudaStream_t st) {
     KernelScope ks_(st, "spmv", (double)s.n * (8 + 8 + 8) + (double)s.W * s.n * (4 + 8));
-    k_spmv<<<blocks_for(s.n), kThreads, 0, st>>>(s.n, s.W, s.col.p, s.off_p.p, s.diag.p, x, y);
+    if (s.W <= 6) k_spmv<6><<<blocks_for(s.n), kThreads, 0, st>>>(s.n, s.W, s.col.p, s.off_p.p, s.diag.p, x, y);
+    else k_spmv<0><<<blocks_for(s.n), kThreads, 0, st>>>(s.n, s.W, s.col.p, s.off_p.p, s.diag.p, x, y);
     MS_CHECK_LAUNCH();
 }
 
 void launch_residual(const ms_system &s, const double *q, const double *x, double *r, double *red,
                      unsigned int *cnt, double *norm_out, cudaStream_t st, float *r32) {
     KernelScope ks_(st, "residual", (double)s.n * (8 + 8 + 8 + 8 + (r32 ? 4 : 0)) + (double)s.W * s.n * (4 + 8));
-    k_residual<<<reduce_grid(s.n), kThreads, 0, st>>>(s.n, s.W, s.col.p, s.off_p.p, s.diag.p, q, x, r, r32, red, cnt,
-                                                       norm_out);
+    if (s.W <= 6)
+        k_residual<6><<<reduce_grid(s.n), kThreads, 0, st>>>(s.n, s.W, s.col.p, s.off_p.p, s.diag.p, q, x, r, r32, red,
+                                                              cnt, norm_out);
+    else
+        k_residual<0><<<reduce_grid(s.n), kThreads, 0, st>>>(s.n, s.W, s.col.p, s.off_p.p, s.diag.p, q, x, r, r32, red,
+                                                              cnt, norm_out);
     MS_CHECK_LAUNCH();
 }
 
 void launch_residual_update(const ms_system &s, double *r, double *x, const double *z, cudaStream_t st) {
     KernelScope ks_(st, "residual_update", (double)s.n * (8 + 8 + 16 + 16) + (double)s.W * s.n * (4 + 8));
-    k_residual_update<<<blocks_for(s.n), kThreads, 0, st>>>(s.n, s.W, s.col.p, s.off_p.p, s.diag.p, r, x, z);
+    if (s.W <= 6) k_residual_update<6><<<blocks_for(s.n), kThreads, 0, st>>>(s.n, s.W, s.col.p, s.off_p.p, s.diag.p, r, x, z);
+    else k_residual_update<0><<<blocks_for(s.n), kThreads, 0, st>>>(s.n, s.W, s.col.p, s.off_p.p, s.diag.p, r, x, z);
     MS_CHECK_LAUNCH();
 }
 
